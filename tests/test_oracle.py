@@ -1,0 +1,355 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Every expected value here comes from a closed form, a brute-force enumeration, a
+library routine (networkx's Stoer-Wagner), a hand computation written out in the
+test, or a published constant (tests/golden/).  None comes from the GPU library.
+"""
+import os
+import random
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from tests import helpers as H
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+BIG_N0 = 1 << 40  # n0 above any n: the level loop is skipped, NOI alone runs
+
+
+def run(g, **kw):
+    return oracle.viecut(g.offsets, g.adj, g.w, **kw)
+
+
+def side_ok(g, res):
+    side = res.side(g.n)
+    assert not side[0], "side must be normalised so vertex 0 is outside"
+    assert side.any() and not side.all(), "side must be a proper non-empty subset"
+    assert H.cut_weight(g.offsets, g.adj, g.w, side) == res.cut
+
+
+# ------------------------------------------------------------------ hashing
+def test_splitmix64_published_vectors():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "splitmix64.txt")) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for state, out in rows:
+        assert oracle.mix64(int(state, 16)) == int(out, 16)
+    # the level key is the SplitMix64 output after (level + 1) gamma increments
+    assert oracle.level_key(0, 0) == int(rows[0][1], 16)
+    assert oracle.level_key(0, 2) == int(rows[2][1], 16)
+
+
+# --------------------------------------------------- exact step (NOI) pins
+@pytest.mark.parametrize("g,lam", [
+    (H.cycle(9), 2),
+    (H.cycle(40, wt=3), 6),
+    (H.complete(7), 6),
+    (H.complete_bipartite(3, 5), 3),
+    (H.hypercube(4), 4),
+    (H.grid(5, 7), 2),
+    (H.two_cliques(6, 2), 2),
+    (H.two_cliques(9, 1), 1),
+    (H.path([5, 7, 2, 9, 4]), 2),
+    (H.pr2_counterexample(), 1),
+    (gg.from_edges(2, [(0, 1, 13)]), 13),
+])
+def test_noi_closed_forms(g, lam):
+    res = run(g, n0=BIG_N0)
+    assert res.cut == lam
+    side_ok(g, res)
+
+
+def test_noi_disconnected_and_isolated():
+    g = gg.from_edges(6, [(0, 1, 2), (1, 2, 2), (3, 4, 1), (4, 5, 1)])
+    res = run(g, n0=BIG_N0)
+    assert res.cut == 0
+    assert H.cut_weight(g.offsets, g.adj, g.w, res.side(6)) == 0
+    # isolated vertex: immediate zero with the smallest isolated vertex as side
+    g2 = gg.from_edges(5, [(0, 1, 1), (1, 2, 1), (0, 2, 1)])
+    res2 = run(g2)
+    assert res2.cut == 0
+    assert list(np.flatnonzero(res2.side(5))) == [3]
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_noi_bruteforce_random(seed):
+    rnd = random.Random(seed)
+    n = rnd.randint(2, 14)
+    g = H.random_graph(n, rnd.uniform(0.15, 0.7), seed, wmax=rnd.choice([1, 3, 9]))
+    lam = H.brute_lambda(g.offsets, g.adj, g.w)
+    res = run(g, n0=BIG_N0)
+    assert res.cut == lam
+    if n >= 2 and lam > 0:
+        side_ok(g, res)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_noi_stoer_wagner(seed):
+    rnd = random.Random(100 + seed)
+    if seed % 2 == 0:
+        g = H.random_graph(rnd.randint(30, 120), rnd.uniform(0.03, 0.2), seed, wmax=20)
+    else:
+        g = gg.with_pair_weights(gg.core_lcc(gg.rhg(400, 12, seed), 4), seed, 1, 10)
+    res = run(g, n0=BIG_N0)
+    assert res.cut == H.stoer_wagner(g.offsets, g.adj, g.w)
+    side_ok(g, res)
+
+
+def test_noi_round_contracts_safely():
+    """Each NOI round contracts at least one edge (Sec. 3) and keeps a minimum cut
+    whenever one is below the bound."""
+    for seed in range(30):
+        rnd = random.Random(seed)
+        g = H.random_graph(rnd.randint(3, 11), 0.5, 500 + seed, wmax=6)
+        G = oracle.as_csr64(g.offsets, g.adj, g.w)
+        lam = H.brute_lambda(g.offsets, g.adj, g.w)
+        lhat = int(oracle.degrees(G).min())
+        labels, unions = oracle.noi_round(G, lhat)
+        assert unions >= 1
+        h, _ = oracle.contract(G, labels)
+        if h.n >= 2:
+            assert min(lhat, H.brute_lambda(h.offsets, h.adj, h.w)) == lam
+        else:
+            assert lam == lhat
+
+
+# ----------------------------------------------------- label propagation pins
+def test_lp_weighted_star_hand():
+    # centre 0, leaves 1..4 with weights 5, 3, 3, 1; no ties anywhere.
+    g = gg.from_edges(5, [(0, 1, 5), (0, 2, 3), (0, 3, 3), (0, 4, 1)])
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    l1 = oracle.lp_round(G, np.arange(5), key=123)
+    assert list(l1) == [1, 0, 0, 0, 0]
+    l2 = oracle.lp_round(G, l1, key=123)
+    assert list(l2) == [0, 1, 1, 1, 1]
+
+
+def two_triangles():
+    return gg.from_edges(6, [(0, 1, 5), (1, 2, 4), (0, 2, 3), (2, 3, 1), (3, 4, 5), (4, 5, 4), (3, 5, 3)])
+
+
+def test_lp_two_triangles_hand():
+    """Hand-computed synchronous rounds; the labels oscillate with period two."""
+    G = oracle.as_csr64(*(lambda g: (g.offsets, g.adj, g.w))(two_triangles()))
+    l1 = oracle.lp_round(G, np.arange(6), key=7)
+    assert list(l1) == [1, 0, 1, 4, 3, 4]
+    l2 = oracle.lp_round(G, l1, key=7)
+    assert list(l2) == [0, 1, 0, 3, 4, 3]
+    l3 = oracle.lp_round(G, l2, key=7)
+    assert list(l3) == list(l1)
+
+
+def test_lp_tie_break_by_hash():
+    # path 0 - 1 - 2, unit weights: vertex 1 sees labels 0 and 2 with equal weight
+    g = gg.from_edges(3, [(0, 1, 1), (1, 2, 1)])
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    for key in [0, 1, 99, 2**63 + 5]:
+        lab = oracle.lp_round(G, np.arange(3), key)
+        h0, h2 = oracle.mix64(key ^ 0), oracle.mix64(key ^ 2)
+        assert lab[1] == (0 if h0 > h2 else 2)
+        assert lab[0] == 1 and lab[2] == 1
+
+
+def test_lp_choice_is_a_strongest_label():
+    """Property: the chosen label maximises S(L); among maximisers it has the
+    largest tie hash."""
+    g = gg.with_pair_weights(gg.rhg(600, 10, 3), 3, 1, 4)
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    rnd = np.random.default_rng(0)
+    lab = rnd.integers(0, 40, g.n).astype(np.int32)
+    key = oracle.level_key(9, 1)
+    out = oracle.lp_round(G, lab, key)
+    for v in range(g.n):
+        S = {}
+        for e in range(G.offsets[v], G.offsets[v + 1]):
+            S[int(lab[G.adj[e]])] = S.get(int(lab[G.adj[e]]), 0) + int(G.w[e])
+        top = max(S.values())
+        cands = [L for L, s in S.items() if s == top]
+        assert out[v] == max(cands, key=lambda L: oracle.mix64(key ^ L))
+
+
+# ----------------------------------------------------------- contraction pins
+def test_contract_two_triangles_hand():
+    g = two_triangles()
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    h, cid = oracle.contract(G, np.array([0, 1, 0, 3, 4, 3]))
+    assert list(cid) == [0, 1, 0, 2, 3, 2]
+    assert list(h.offsets) == [0, 2, 3, 5, 6]
+    assert list(h.adj) == [1, 2, 0, 0, 3, 2]
+    assert list(h.w) == [9, 1, 9, 1, 9, 9]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_contract_invariants(seed):
+    rnd = np.random.default_rng(seed)
+    g = gg.with_pair_weights(gg.rhg(800, 14, seed), seed, 1, 9)
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    k = int(rnd.integers(2, 200))
+    labels = rnd.integers(0, 10 * k, g.n).astype(np.int32)
+    h, cid = oracle.contract(G, labels)
+    # ids are ranks of the distinct label values
+    vals = np.unique(labels)
+    assert h.n == len(vals)
+    assert np.array_equal(cid, np.searchsorted(vals, labels))
+    H.check_csr(h.offsets, h.adj, h.w, merged=True)
+    src = np.repeat(np.arange(g.n), np.diff(G.offsets))
+    intra = cid[src] == cid[G.adj]
+    assert h.w.sum() == G.w.sum() - G.w[intra].sum()
+    deg_f = oracle.degrees(G)
+    deg_c = oracle.degrees(h)
+    inside = np.zeros(h.n, np.int64)
+    np.add.at(inside, cid[src[intra]], G.w[intra])
+    expect = np.zeros(h.n, np.int64)
+    np.add.at(expect, cid, deg_f)
+    assert np.array_equal(deg_c, expect - inside)
+    # brute aggregation of the coarse edge weights
+    acc = {}
+    for e in np.flatnonzero(~intra):
+        key = (int(cid[src[e]]), int(cid[G.adj[e]]))
+        acc[key] = acc.get(key, 0) + int(G.w[e])
+    got = {}
+    for v in range(h.n):
+        for e in range(h.offsets[v], h.offsets[v + 1]):
+            got[(v, int(h.adj[e]))] = int(h.w[e])
+    assert got == acc
+
+
+# ----------------------------------------------------- Padberg-Rinaldi pins
+def test_pr2_counterexample_designated_partner():
+    g = H.pr2_counterexample()
+    assert H.brute_lambda(g.offsets, g.adj, g.w) == 1
+    # the designated-partner reading keeps the minimum cut through the whole method
+    for lp in (0, 1, 2):
+        res = run(g, lp_iters=lp, n0=1)
+        assert res.cut == 1
+        side_ok(g, res)
+    # pass A alone: triangle edges (c >= 2 = min degree) and only one of vertex 6's edges
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    labels, unions = oracle.pr_pass_a(G, 2)
+    assert list(labels) == [0, 0, 0, 3, 3, 3, 0]
+    # the literal bulk reading (every edge passing condition 2) merges everything
+    deg = oracle.degrees(G)
+    parent = list(range(7))
+
+    def find(x):
+        while parent[x] != x:
+            x = parent[x]
+        return x
+    for v in range(7):
+        for e in range(G.offsets[v], G.offsets[v + 1]):
+            u = int(G.adj[e])
+            if G.w[e] >= 2 or deg[v] <= 2 * G.w[e] or deg[u] <= 2 * G.w[e]:
+                a, b = find(v), find(u)
+                parent[max(a, b)] = min(a, b)
+    assert len({find(v) for v in range(7)}) == 1
+
+
+@pytest.mark.parametrize("which", ["a", "b"])
+def test_pr_passes_safe_bruteforce(which):
+    """min(lambda-hat, lambda(G / marked)) == lambda(G) for every pass on random
+    small weighted graphs (the Padberg-Rinaldi lemma with lambda-hat = min degree)."""
+    checked = 0
+    for seed in range(150):
+        rnd = random.Random(seed * 7 + (which == "b"))
+        n = rnd.randint(3, 12)
+        g = H.random_graph(n, rnd.uniform(0.2, 0.8), seed, wmax=rnd.choice([2, 4, 10]))
+        G = oracle.as_csr64(g.offsets, g.adj, g.w)
+        G, _ = oracle.contract(G, np.arange(n))  # merged lists
+        lam = H.brute_lambda(G.offsets, G.adj, G.w)
+        lhat = int(oracle.degrees(G).min())
+        f = oracle.pr_pass_a if which == "a" else oracle.pr_pass_b
+        labels, cnt = f(G, lhat)
+        if cnt == 0:
+            continue
+        checked += 1
+        h, _ = oracle.contract(G, labels)
+        if h.n >= 2:
+            assert min(lhat, H.brute_lambda(h.offsets, h.adj, h.w)) == lam, seed
+        else:
+            assert lam == lhat, seed
+    assert checked >= 20
+
+
+def test_pr_pass_b_conditions_hand():
+    # v=0, w=1 mutual partners (edge 4); common neighbours 2 (3 and 3) and 3 (1 and 2);
+    # 0 also tied to 4 (weight 2), 1 to 5 (weight 2).
+    E = [(0, 1, 4), (0, 2, 3), (1, 2, 3), (0, 3, 1), (1, 3, 2), (0, 4, 2), (1, 5, 2),
+         (2, 4, 1), (3, 5, 1), (4, 5, 1)]
+    g = gg.from_edges(6, E)
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    # c(0) = 10, c(1) = 11; condition 3 with u = 2: 10 <= 2(4 + 3) and 11 <= 2(4 + 3)
+    labels, pairs = oracle.pr_pass_b(G, 1000)
+    assert pairs == 1 and labels[1] == 0
+    # condition 4 alone: 4 + min(3,3) + min(1,2) = 8 >= 8 but condition 3 removed by
+    # making the common weights light
+    E2 = [(0, 1, 4), (0, 2, 1), (1, 2, 1), (0, 3, 1), (1, 3, 1), (0, 4, 5), (1, 5, 5), (4, 5, 1)]
+    g2 = gg.from_edges(6, E2)
+    G2 = oracle.as_csr64(g2.offsets, g2.adj, g2.w)
+    # partner of 0 is 4 (weight 5), so 0-1 is not a mutual pair: nothing happens
+    assert oracle.pr_pass_b(G2, 6)[1] == 0
+    E3 = [(0, 1, 6), (0, 2, 1), (1, 2, 1), (0, 3, 1), (1, 3, 1), (0, 4, 5), (0, 6, 4),
+          (1, 5, 5), (1, 7, 4), (4, 5, 1), (6, 7, 1)]
+    g3 = gg.from_edges(8, E3)
+    G3 = oracle.as_csr64(g3.offsets, g3.adj, g3.w)
+    # c(0) = c(1) = 17 > 2(6 + 1): condition 3 fails for both common neighbours;
+    # condition 4: 6 + min(1, 1) + min(1, 1) = 8
+    assert oracle.pr_pass_b(G3, 9)[1] == 0
+    labels, pairs = oracle.pr_pass_b(G3, 8)
+    assert pairs == 1 and labels[1] == 0
+
+
+# ------------------------------------------------------------- whole method
+@pytest.mark.parametrize("seed", range(30))
+def test_pipeline_upper_bound_bruteforce(seed):
+    rnd = random.Random(1000 + seed)
+    n = rnd.randint(4, 14)
+    g = H.random_graph(n, rnd.uniform(0.25, 0.7), 77 + seed, wmax=rnd.choice([1, 5]))
+    lam = H.brute_lambda(g.offsets, g.adj, g.w)
+    for lp in (1, 2, 3):
+        res = run(g, lp_iters=lp, n0=rnd.choice([1, 2, 3]), seed=seed)
+        assert res.cut >= lam
+        side_ok(g, res)
+
+
+def test_pipeline_trace_monotone():
+    g = gg.core_lcc(gg.rhg(1 << 12, 24, 5), 0)
+    res = run(g, n0=32)
+    lh = [s[4] for s in res.trace]
+    ns = [s[2] for s in res.trace]
+    assert all(a >= b for a, b in zip(lh, lh[1:]))
+    assert all(a >= b for a, b in zip(ns, ns[1:]))
+    assert res.trace[0][0] == 0 and res.trace[1][0] == 1
+    assert res.cut == lh[-1]
+    side_ok(g, res)
+    g2 = gg.core_lcc(gg.rhg(1 << 10, 16, 6), 0)
+    res2 = run(g2, n0=16)
+    side_ok(g2, res2)
+    assert res2.cut >= H.stoer_wagner(g2.offsets, g2.adj, g2.w)
+
+
+def planted_lambda(g, blocks, block_n):
+    """Cut value known from the construction: the smaller of the minimum weighted
+    degree and the lightest bridge set separating a union of blocks from the rest."""
+    n = g.n
+    src = np.repeat(np.arange(n), np.diff(g.offsets))
+    deg = np.zeros(n, np.int64)
+    np.add.at(deg, src, g.w.astype(np.int64))
+    bsrc, bdst = src // block_n, g.adj // block_n
+    cross = bsrc != bdst
+    best = int(deg.min())
+    for mask in range(1, 1 << (blocks - 1)):
+        inA = (mask >> np.arange(blocks)) & 1
+        sel = cross & (inA[bsrc] != inA[bdst])
+        best = min(best, int(g.w[sel].astype(np.int64).sum()) // 2)
+    return best
+
+
+def test_planted_small():
+    g = gg.planted(4, 1 << 8, 16, 6, 3, 1, 100)
+    lam = planted_lambda(g, 4, 1 << 8)
+    assert lam == H.stoer_wagner(g.offsets, g.adj, g.w)
+    assert run(g, n0=BIG_N0).cut == lam
+    res = run(g, n0=64)
+    assert res.cut >= lam
+    side_ok(g, res)
