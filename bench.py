@@ -1,0 +1,315 @@
+"""Benchmark: minimum-cut input edges/s on the RHG n=2^22 workload (one GB300).
+
+A step is one whole minimum-cut run (label propagation levels, cluster contraction,
+Padberg-Rinaldi runs, exact final step, side transfer) of the random hyperbolic
+graph n = 2^22, average degree 64, power-law exponent 5, reduced to its 16-core and
+largest component.  Edges are undirected input edges (m = nnz / 2), the paper's
+convention.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 is launched by torchrun: every rank solves its own replica (the method does
+not shard; independent graphs per GPU, no collective on the data path) and the
+value is the whole job's edges / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "min-cut input edges/s, RHG n=2^22 avg deg 64 exponent 5, 16-core"
+UNIT = "edges/s"
+WORKLOAD = "rhg(n=2^22, avg_deg=64, gamma=5) -> 16-core -> largest component, unit int32 weights"
+SAMPLE_N = 1 << 19  # the CPU oracle's bounded sample: same family, n = 2^19
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        # "under load": samples within 70% of the highest clock seen
+        top = max(sm) if sm else 0
+        loaded = [x for x in sm if x >= 0.7 * top] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def make_graph(n_log: int = 22, seed: int = 1):
+    import graphgen as gg
+    return gg.workload_rhg_large(seed, n=1 << n_log)
+
+
+def cpu_oracle_sample(seed: int = 1):
+    """Times the CPU oracle (as it stands, one host thread) on a bounded sample:
+    the whole method on the same RHG family at n = 2^19."""
+    import graphgen as gg
+    import oracle
+    g = gg.workload_rhg_large(seed, n=SAMPLE_N)
+    oracle.build()
+    t0 = time.perf_counter()
+    res = oracle.viecut(g.offsets, g.adj, g.w, seed=seed, lp_iters=2, n0=10000, pr_runs_max=8)
+    dt = time.perf_counter() - t0
+    return g, res, dt
+
+
+def run_reference(args):
+    """The oracle arm: each step is one oracle run of the bounded sample."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import graphgen as gg
+    import oracle
+    oracle.build()
+    g = gg.workload_rhg_large(1, n=SAMPLE_N)
+    for i in range(args.warmup):
+        oracle.viecut(g.offsets, g.adj, g.w, seed=1 + i, lp_iters=2, n0=10000, pr_runs_max=8)
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.viecut(g.offsets, g.adj, g.w, seed=1 + i, lp_iters=2, n0=10000, pr_runs_max=8)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = g.m * args.steps / tot
+    sample = f"whole method on rhg(n=2^19, avg_deg=64, gamma=5) -> 16-core -> lcc (m={g.m}), one oracle run per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("2^22", "2^19") + " (bounded CPU sample)", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nlog", type=int, default=22, help="log2 of the RHG vertex count")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+
+    import torch
+    import paper_1708_06127_gb300 as vc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    vc.build()
+    stream = torch.cuda.current_stream(dev)
+
+    # every rank solves its own replica (graph drawn with a rank-dependent seed)
+    g = make_graph(args.nlog, seed=1 + rank)
+    off = torch.from_numpy(g.offsets).to(dev)
+    adj = torch.from_numpy(g.adj).to(dev)
+    w = torch.from_numpy(g.w).to(dev)
+    mc = vc.MinCut(off, adj, w, on_device=True, device=local, stream=stream.cuda_stream, timing=True)
+    d_cut = torch.zeros(1, dtype=torch.int64, device=dev)
+    d_bits = torch.zeros((g.n + 63) // 64, dtype=torch.int64, device=dev)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+
+    for i in range(args.warmup):
+        vc.viecut_run_device(mc.h, 1 + i, 2, d_cut, d_bits)
+    barrier()
+
+    # ---------------- device-resident timed region
+    lp_ms = 0.0
+    lp_rounds = 0
+    lp_bytes = 0
+    launches = 0
+    phases = {"lp": 0.0, "contract": 0.0, "pr": 0.0, "noi": 0.0, "other": 0.0}
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for i in range(args.steps):
+            vc.viecut_run_device(mc.h, 100 + i, 2, d_cut, d_bits)
+            st = mc.stats()
+            lp_ms += st["ms_lp_kernel"]
+            lp_rounds += st["lp_launches"]
+            lp_bytes += st["lp_bytes"]
+            launches += st["kernel_launches"]
+            for k in phases:
+                phases[k] += st["ms_" + k]
+        ev1.record(stream)
+        barrier()
+    clocks = clk.summary()
+    ms = ev0.elapsed_time(ev1)
+    cut_value = int(d_cut.item())
+    if pg is not None:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    edges_total = g.m * args.steps * world
+    value = edges_total / (ms / 1000.0)
+
+    # label-propagation roofline: algorithmic bytes of every timed round (the library
+    # counts 8(n+1) + nnz (4 + 4 + 4 label gather, none in a level's first round) + 4n per
+    # round) over the rounds' summed CUDA-event time on the launching stream
+    peaks = load_peaks() or {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    lp_round_ms = lp_ms / max(1, lp_rounds)
+    lp_round_bytes = lp_bytes / max(1, lp_rounds)
+    achieved = lp_bytes / (lp_ms / 1000.0) / 1e9 if lp_ms > 0 else None
+
+    # ---------------- end to end through the C ABI with host buffers
+    h_off = torch.from_numpy(g.offsets).pin_memory()
+    h_adj = torch.from_numpy(g.adj).pin_memory()
+    h_w = torch.from_numpy(g.w).pin_memory()
+    bits_host = torch.zeros((g.n + 63) // 64, dtype=torch.int64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    opts = vc.viecut_opts_init(stream=stream.cuda_stream, device=local)
+    hh = vc.viecut_create(h_off, h_adj, g.n, g.nnz, h_w, opts)  # warm-up of the host path
+    vc.viecut_run(hh, 1, 2, bits_host)
+    vc.viecut_destroy(hh)
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        hh = vc.viecut_create(h_off, h_adj, g.n, g.nnz, h_w, opts)
+        vc.viecut_run(hh, 100 + i, 2, bits_host)
+        vc.viecut_destroy(hh)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if pg is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = g.m * e2e_steps * world / e2e_s
+    h2d = g.offsets.nbytes + g.adj.nbytes + g.w.nbytes
+    d2h = 8 + bits_host.numel() * 8
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.nlog == 22 else WORKLOAD.replace("2^22", f"2^{args.nlog}"),
+                   "n": g.n, "m": g.m, "nnz": g.nnz, "lp_iters": 2, "n0": 10000, "pr_runs_max": 8,
+                   "l2": "inputs larger than L2 (CSR %.2f GB)" % ((g.offsets.nbytes + g.adj.nbytes + g.w.nbytes) / 1e9),
+                   "parallelism": f"replicas x{world}", "cut_value": cut_value},
+        "roofline": {"kernel": "label-propagation round (agg_warp_k + block/global classes)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+                     "round_ms": lp_round_ms, "algorithmic_bytes_per_round": lp_round_bytes},
+        "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sg, sres, sdt = cpu_oracle_sample(1)
+        line["cpu_baseline"] = {"value": sg.m / sdt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"whole method on rhg(n=2^19, avg_deg=64, gamma=5) -> 16-core -> lcc, "
+                                          f"m={sg.m}, {sdt:.1f} s, one host thread"}
+    mc.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,159 @@
+/*
+ * viecut.h -- C ABI of the GB300 (sm_103a) implementation of VieCut, the inexact
+ * near-linear minimum-cut method of "Practical Minimum Cut Algorithms" (Henzinger,
+ * Noe, Schulz, Strash; arXiv 1708.06127).
+ *
+ * The method (Algorithm 1 of the paper, Appendix A): while the graph has more than n0
+ * vertices, cluster it by label propagation (Sec. 4.1), contract the clusters
+ * (Sec. 4.1, "contract it"), contract the edges that the Padberg-Rinaldi conditions
+ * mark (Lemma "Padberg-Rinaldi", Sec. 4.1); then solve the remaining graph exactly
+ * with the algorithm of Nagamochi, Ono and Ibaraki (Sec. 3).  Throughout, the bound
+ * lambda-hat is the smallest trivial cut (minimum weighted degree) seen after any
+ * contraction (Sec. 4, second paragraph).  The result is that bound and the side of
+ * the cut that realises it, transferred back to the input vertices.
+ *
+ * Deterministic variant: label propagation is synchronous with ties broken by
+ * mix64(key XOR label), key = mix64(seed + 0x9e3779b97f4a7c15 * (level + 1)),
+ * mix64 = SplitMix64's output function; condition 2 of Padberg-Rinaldi marks only the
+ * edge to each vertex's designated partner; conditions 3 and 4 run on mutual partner
+ * pairs.  For a fixed (graph, seed, lp_iters, n0, pr_runs_max) every call returns
+ * the same cut value and the same side, bit for bit.
+ *
+ * Conventions shared by all calls:
+ *   - Graphs are undirected CSR: offsets int64[n+1] (offsets[0] = 0, non-decreasing,
+ *     offsets[n] = m), adj int32[m] neighbour ids, weights int32[m] >= 1; every edge
+ *     appears in both directions with equal weight; m counts directed entries (twice
+ *     the paper's |E|).  Parallel entries are allowed and summed; self-loops are not.
+ *   - Every call returns 0 on success or a negative VIECUT_E* code; the message of the
+ *     last failure on the calling thread is available from viecut_last_error().
+ *   - "Host" pointers are ordinary CPU memory (pinned memory makes copies faster);
+ *     "device" pointers are CUDA global memory on the handle's device.
+ *   - The library allocates its own device work space (cudaMalloc) at create time and
+ *     grows it on first use; nothing is allocated by the caller except inputs/outputs.
+ *   - A handle is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef VIECUT_H_
+#define VIECUT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VIECUT_OK 0
+#define VIECUT_EINVAL (-1)    /* invalid argument or malformed graph */
+#define VIECUT_ENOMEM (-2)    /* device or host allocation failed */
+#define VIECUT_ECUDA (-3)     /* CUDA runtime error (message names the call) */
+#define VIECUT_ETIMEOUT (-4)  /* a bounded device wait ran out */
+#define VIECUT_ECANCELLED (-5)
+#define VIECUT_EBUSY (-6)     /* result not ready yet (server poll) */
+
+typedef struct viecut_handle viecut_t;
+
+/* Options fixed at create time.  viecut_opts_init fills the defaults. */
+typedef struct viecut_opts {
+  int64_t n0;          /* exact step once at most n0 vertices remain (default 10000, Sec. 5 setup) */
+  int32_t pr_runs_max; /* Padberg-Rinaldi runs per level (default 8) */
+  int32_t device;      /* CUDA device ordinal (default 0) */
+  void* stream;        /* cudaStream_t for all work; NULL = the library creates one */
+  int32_t validate;    /* 0 = trust input; 1 = range/loop/weight/offset checks (default);
+                          2 = also check symmetry on the host (create from host arrays only) */
+  int32_t timing;      /* 1 = record per-phase CUDA-event times (viecut_get_stats) */
+} viecut_opts;
+
+/* Per-run statistics (valid after viecut_run / viecut_run_device completes). */
+typedef struct viecut_stats {
+  double ms_total;       /* device time of the whole run (timing = 1) */
+  double ms_lp;          /* label-propagation rounds */
+  double ms_contract;    /* cluster and edge contractions */
+  double ms_pr;          /* Padberg-Rinaldi tests */
+  double ms_noi;         /* exact final step */
+  double ms_other;       /* bounds, side transfer */
+  double ms_lp_kernel;   /* summed duration of the label-propagation launches */
+  int64_t lp_launches;   /* label-propagation rounds timed in ms_lp_kernel */
+  int64_t lp_nnz;        /* adjacency entries read by the timed label-propagation rounds */
+  int64_t lp_n;          /* vertices processed by the timed label-propagation rounds */
+  int64_t kernel_launches; /* kernels launched by this run */
+  int64_t levels;        /* label-propagation levels run */
+  int64_t trace_len;     /* contraction steps recorded (viecut_get_trace) */
+  int64_t lp_bytes;      /* algorithmic bytes of the timed label-propagation rounds:
+                            8(n+1) offsets + nnz (4 id + weight bytes + 4 label gather,
+                            no gather in a level's first round) + 4n label writes */
+} viecut_stats;
+
+/* One contraction step: kind 0 initial graph, 1 label-propagation contraction,
+ * 2 Padberg-Rinaldi pass A, 3 pass B, 4 exact-step round; shape and bound after it. */
+typedef struct viecut_step {
+  int32_t kind, level;
+  int64_t n, nnz, lambda_hat;
+} viecut_step;
+
+int viecut_opts_init(viecut_opts* opts);
+
+/* Creates a handle from HOST arrays (copied to the device; the caller keeps them).
+ * opts may be NULL (defaults).  EINVAL for n < 2, m < 0 or a malformed graph. */
+int viecut_create(viecut_t** h, const int64_t* offsets, const int32_t* adj, int64_t n, int64_t m,
+                  const int32_t* weights, const viecut_opts* opts);
+
+/* Creates a handle over DEVICE arrays that stay owned by the caller and must
+ * outlive the handle (no copy).  validate 2 is treated as 1. */
+int viecut_create_device(viecut_t** h, const int64_t* d_offsets, const int32_t* d_adj, int64_t n, int64_t m,
+                         const int32_t* d_weights, const viecut_opts* opts);
+
+/* Runs the method and waits for it.  cut_value (host) receives the cut; side_bits
+ * (host, ceil(n/64) words, may be NULL) receives bit i = 1 iff input vertex i is on
+ * the returned side; vertex 0 is never on it.  lp_iters >= 0 (the paper uses 2). */
+int viecut_run(viecut_t* h, uint64_t seed, int32_t lp_iters, int64_t* cut_value, uint64_t* side_bits);
+
+/* As viecut_run, but the outputs are DEVICE pointers (d_side_bits may be NULL)
+ * written on the handle's stream.  The level loop reads small shape records from the
+ * device at its decision points, so the call returns when the last kernels are
+ * enqueued; synchronise the stream before reading the outputs. */
+int viecut_run_device(viecut_t* h, uint64_t seed, int32_t lp_iters, int64_t* d_cut_value,
+                      uint64_t* d_side_bits);
+
+int viecut_get_stats(const viecut_t* h, viecut_stats* stats);
+/* Copies up to cap steps of the last run's contraction trace; *len = steps made. */
+int viecut_get_trace(const viecut_t* h, viecut_step* steps, int64_t cap, int64_t* len);
+int viecut_destroy(viecut_t* h);
+const char* viecut_last_error(void);
+/* Kernels launched by this library in this process so far. */
+int64_t viecut_launch_count(void);
+
+/* ---------------------------------------------------------------------------
+ * Step entry points.  They run one step of the method on a device-resident graph,
+ * with host inputs/outputs, so every step can be compared with a reference alone.
+ * A viecut_graph owns its device CSR (int64 weights).
+ * ------------------------------------------------------------------------- */
+typedef struct viecut_graph viecut_graph;
+
+/* Copies a host CSR (int64 weights) to the device. */
+int viecut_graph_upload(viecut_graph** g, const int64_t* offsets, const int32_t* adj, const int64_t* weights,
+                        int64_t n, int64_t nnz, int32_t device);
+int viecut_graph_shape(const viecut_graph* g, int64_t* n, int64_t* nnz);
+/* Copies the CSR back (offsets n+1, adj nnz, weights nnz). */
+int viecut_graph_download(const viecut_graph* g, int64_t* offsets, int32_t* adj, int64_t* weights);
+int viecut_graph_free(viecut_graph* g);
+
+/* Weighted degrees c(v) (Sec. 3): deg[n]. */
+int viecut_step_degrees(viecut_graph* g, int64_t* deg);
+/* `rounds` synchronous label-propagation rounds (Sec. 4.1) from lab_in (NULL = the
+ * identity labelling) with tie-break key `key`; writes every round: lab_out[rounds*n]. */
+int viecut_step_lp(viecut_graph* g, const int32_t* lab_in, uint64_t key, int32_t rounds, int32_t* lab_out);
+/* Contraction by labels (Sec. 4.1, "contract it"): *out receives the coarse graph,
+ * cid[n] the coarse id (rank of the label value) of every vertex. */
+int viecut_step_contract(viecut_graph* g, const int32_t* labels, viecut_graph** out, int32_t* cid);
+/* Padberg-Rinaldi pass A (conditions 1, 2) / pass B (conditions 3, 4) with bound
+ * lambda_hat: labels[n] = union-find representative (smallest id of each merged
+ * group); *changed = 1 if anything merged.  The graph must have merged, sorted lists. */
+int viecut_step_pr_a(viecut_graph* g, int64_t lambda_hat, int32_t* labels, int32_t* changed);
+int viecut_step_pr_b(viecut_graph* g, int64_t lambda_hat, int32_t* labels, int32_t* changed);
+/* One Nagamochi-Ono-Ibaraki round (Sec. 3) with bound lambda_hat: labels[n] as above. */
+int viecut_step_noi_round(viecut_graph* g, int64_t lambda_hat, int32_t* labels, int32_t* changed);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VIECUT_H_ */

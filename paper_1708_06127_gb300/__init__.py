@@ -1,0 +1,291 @@
+"""GB300 (sm_103a) implementation of VieCut, the inexact minimum-cut method of
+"Practical Minimum Cut Algorithms" (Henzinger, Noe, Schulz, Strash; arXiv 1708.06127).
+
+This module is a thin ctypes binding of the C ABI declared in ``include/viecut.h``:
+the functions keep the C names and only marshal arguments.  Every step of the
+method runs in the CUDA kernels of ``libviecut.so``; there is no CPU fallback.  If the
+library is missing the import of any entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libviecut.so")
+_lock = threading.Lock()
+_lib = None
+
+VIECUT_OK = 0
+VIECUT_EINVAL = -1
+VIECUT_ENOMEM = -2
+VIECUT_ECUDA = -3
+VIECUT_ETIMEOUT = -4
+VIECUT_ECANCELLED = -5
+VIECUT_EBUSY = -6
+
+STEP_KINDS = {0: "initial", 1: "lp", 2: "pr_a", 3: "pr_b", 4: "noi"}
+
+
+class ViecutError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"viecut error {code}: {msg}")
+        self.code = code
+
+
+class viecut_opts(ctypes.Structure):
+    _fields_ = [("n0", ctypes.c_int64), ("pr_runs_max", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("stream", ctypes.c_void_p), ("validate", ctypes.c_int32), ("timing", ctypes.c_int32)]
+
+
+class viecut_stats(ctypes.Structure):
+    _fields_ = [("ms_total", ctypes.c_double), ("ms_lp", ctypes.c_double), ("ms_contract", ctypes.c_double),
+                ("ms_pr", ctypes.c_double), ("ms_noi", ctypes.c_double), ("ms_other", ctypes.c_double),
+                ("ms_lp_kernel", ctypes.c_double), ("lp_launches", ctypes.c_int64), ("lp_nnz", ctypes.c_int64),
+                ("lp_n", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("levels", ctypes.c_int64),
+                ("trace_len", ctypes.c_int64), ("lp_bytes", ctypes.c_int64)]
+
+
+class viecut_step(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("lambda_hat", ctypes.c_int64)]
+
+
+# (name, restype, argtypes) of every entry point declared in include/viecut.h
+_vp, _i64, _i32, _u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+_pvp = ctypes.POINTER(ctypes.c_void_p)
+SIGNATURES = [
+    ("viecut_opts_init", ctypes.c_int, [_vp]),
+    ("viecut_create", ctypes.c_int, [_pvp, _vp, _vp, _i64, _i64, _vp, _vp]),
+    ("viecut_create_device", ctypes.c_int, [_pvp, _vp, _vp, _i64, _i64, _vp, _vp]),
+    ("viecut_run", ctypes.c_int, [_vp, _u64, _i32, _vp, _vp]),
+    ("viecut_run_device", ctypes.c_int, [_vp, _u64, _i32, _vp, _vp]),
+    ("viecut_get_stats", ctypes.c_int, [_vp, _vp]),
+    ("viecut_get_trace", ctypes.c_int, [_vp, _vp, _i64, _vp]),
+    ("viecut_destroy", ctypes.c_int, [_vp]),
+    ("viecut_last_error", ctypes.c_char_p, []),
+    ("viecut_launch_count", ctypes.c_int64, []),
+    ("viecut_graph_upload", ctypes.c_int, [_pvp, _vp, _vp, _vp, _i64, _i64, _i32]),
+    ("viecut_graph_shape", ctypes.c_int, [_vp, _vp, _vp]),
+    ("viecut_graph_download", ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    ("viecut_graph_free", ctypes.c_int, [_vp]),
+    ("viecut_step_degrees", ctypes.c_int, [_vp, _vp]),
+    ("viecut_step_lp", ctypes.c_int, [_vp, _vp, _u64, _i32, _vp]),
+    ("viecut_step_contract", ctypes.c_int, [_vp, _vp, _pvp, _vp]),
+    ("viecut_step_pr_a", ctypes.c_int, [_vp, _i64, _vp, _vp]),
+    ("viecut_step_pr_b", ctypes.c_int, [_vp, _i64, _vp, _vp]),
+    ("viecut_step_noi_round", ctypes.c_int, [_vp, _i64, _vp, _vp]),
+]
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+    return _build.build(force=force)
+
+
+def lib():
+    """The loaded libviecut.so.  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build it with paper_1708_06127_gb300.build() "
+                                  "(there is no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, res, args in SIGNATURES:
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != VIECUT_OK:
+        raise ViecutError(rc, lib().viecut_last_error().decode())
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def viecut_opts_init(**kw) -> viecut_opts:
+    o = viecut_opts()
+    _check(lib().viecut_opts_init(ctypes.byref(o)))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def viecut_create(offsets, adj, n: int, m: int, weights, opts: viecut_opts | None = None):
+    h = ctypes.c_void_p()
+    _check(lib().viecut_create(ctypes.byref(h), _ptr(offsets), _ptr(adj), n, m, _ptr(weights),
+                               ctypes.byref(opts) if opts is not None else None))
+    return h
+
+
+def viecut_create_device(d_offsets, d_adj, n: int, m: int, d_weights, opts: viecut_opts | None = None):
+    h = ctypes.c_void_p()
+    _check(lib().viecut_create_device(ctypes.byref(h), _ptr(d_offsets), _ptr(d_adj), n, m, _ptr(d_weights),
+                                      ctypes.byref(opts) if opts is not None else None))
+    return h
+
+
+def viecut_run(h, seed: int, lp_iters: int, side_bits=None) -> int:
+    cut = ctypes.c_int64()
+    _check(lib().viecut_run(h, seed & (2**64 - 1), lp_iters, ctypes.byref(cut), _ptr(side_bits)))
+    return int(cut.value)
+
+
+def viecut_run_device(h, seed: int, lp_iters: int, d_cut, d_side_bits=None):
+    _check(lib().viecut_run_device(h, seed & (2**64 - 1), lp_iters, _ptr(d_cut), _ptr(d_side_bits)))
+
+
+def viecut_get_stats(h) -> dict:
+    s = viecut_stats()
+    _check(lib().viecut_get_stats(h, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in viecut_stats._fields_}
+
+
+def viecut_get_trace(h) -> list:
+    cap = 4096
+    buf = (viecut_step * cap)()
+    ln = ctypes.c_int64()
+    _check(lib().viecut_get_trace(h, buf, cap, ctypes.byref(ln)))
+    return [(buf[i].kind, buf[i].level, buf[i].n, buf[i].nnz, buf[i].lambda_hat) for i in range(min(cap, ln.value))]
+
+
+def viecut_destroy(h):
+    if h:
+        _check(lib().viecut_destroy(h))
+
+
+def viecut_launch_count() -> int:
+    return int(lib().viecut_launch_count())
+
+
+# ----------------------------------------------------------------- step API
+def viecut_graph_upload(offsets, adj, weights, device: int = 0):
+    off = np.ascontiguousarray(offsets, np.int64)
+    a = np.ascontiguousarray(adj, np.int32)
+    w = np.ascontiguousarray(weights, np.int64)
+    g = ctypes.c_void_p()
+    _check(lib().viecut_graph_upload(ctypes.byref(g), off.ctypes.data, a.ctypes.data, w.ctypes.data,
+                                     off.shape[0] - 1, a.shape[0], device))
+    return g
+
+
+def viecut_graph_shape(g):
+    n, nnz = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().viecut_graph_shape(g, ctypes.byref(n), ctypes.byref(nnz)))
+    return int(n.value), int(nnz.value)
+
+
+def viecut_graph_download(g):
+    n, nnz = viecut_graph_shape(g)
+    off = np.empty(n + 1, np.int64)
+    adj = np.empty(max(nnz, 1), np.int32)
+    w = np.empty(max(nnz, 1), np.int64)
+    _check(lib().viecut_graph_download(g, off.ctypes.data, adj.ctypes.data, w.ctypes.data))
+    return off, adj[:nnz], w[:nnz]
+
+
+def viecut_graph_free(g):
+    if g:
+        _check(lib().viecut_graph_free(g))
+
+
+def viecut_step_degrees(g) -> np.ndarray:
+    n, _ = viecut_graph_shape(g)
+    d = np.empty(n, np.int64)
+    _check(lib().viecut_step_degrees(g, d.ctypes.data))
+    return d
+
+
+def viecut_step_lp(g, lab_in, key: int, rounds: int) -> np.ndarray:
+    n, _ = viecut_graph_shape(g)
+    out = np.empty((rounds, n), np.int32)
+    li = None if lab_in is None else np.ascontiguousarray(lab_in, np.int32)
+    _check(lib().viecut_step_lp(g, None if li is None else li.ctypes.data, key & (2**64 - 1), rounds, out.ctypes.data))
+    return out
+
+
+def viecut_step_contract(g, labels):
+    n, _ = viecut_graph_shape(g)
+    lab = np.ascontiguousarray(labels, np.int32)
+    cid = np.empty(n, np.int32)
+    out = ctypes.c_void_p()
+    _check(lib().viecut_step_contract(g, lab.ctypes.data, ctypes.byref(out), cid.ctypes.data))
+    return out, cid
+
+
+def _step_labels(name, g, lambda_hat):
+    n, _ = viecut_graph_shape(g)
+    lab = np.empty(n, np.int32)
+    ch = ctypes.c_int32()
+    _check(getattr(lib(), name)(g, int(lambda_hat), lab.ctypes.data, ctypes.byref(ch)))
+    return lab, int(ch.value)
+
+
+def viecut_step_pr_a(g, lambda_hat):
+    return _step_labels("viecut_step_pr_a", g, lambda_hat)
+
+
+def viecut_step_pr_b(g, lambda_hat):
+    return _step_labels("viecut_step_pr_b", g, lambda_hat)
+
+
+def viecut_step_noi_round(g, lambda_hat):
+    return _step_labels("viecut_step_noi_round", g, lambda_hat)
+
+
+# ----------------------------------------------------------------- convenience
+class MinCut:
+    """Owns a handle over one graph; ``run`` returns (cut value, side bitmap)."""
+
+    def __init__(self, offsets, adj, weights, n0: int = 10000, pr_runs_max: int = 8, device: int = 0,
+                 stream=None, validate: int = 1, timing: bool = False, on_device: bool = False):
+        n = int(offsets.shape[0] - 1)
+        m = int(adj.shape[0])
+        o = viecut_opts_init(n0=n0, pr_runs_max=pr_runs_max, device=device, stream=stream,
+                             validate=validate, timing=int(timing))
+        self.n, self.m = n, m
+        self._keep = (offsets, adj, weights)
+        self.h = (viecut_create_device if on_device else viecut_create)(offsets, adj, n, m, weights, o)
+
+    def run(self, seed: int = 1, lp_iters: int = 2):
+        bits = np.zeros((self.n + 63) // 64, np.uint64)
+        cut = viecut_run(self.h, seed, lp_iters, bits)
+        return cut, bits
+
+    def stats(self) -> dict:
+        return viecut_get_stats(self.h)
+
+    def trace(self) -> list:
+        return viecut_get_trace(self.h)
+
+    def close(self):
+        if self.h:
+            viecut_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,113 @@
+// Host-side launchers of the library's kernels (one translation unit per family).
+#pragma once
+#include "common.cuh"
+
+namespace vc {
+
+// A CSR graph on the device.  Weights are int32 (input graphs, wbytes = 4) or int64
+// (every contracted graph, wbytes = 8).
+struct GraphView {
+  int64_t n = 0, nnz = 0;
+  const int64_t* off = nullptr;
+  const int32_t* adj = nullptr;
+  const void* w = nullptr;
+  int wbytes = 8;
+};
+
+// Degree classes of one graph: lists of vertices by neighbour-list length.
+//   warp class  : length <= kWarpMaxDeg  (every vertex not in a list below)
+//   block class : kWarpMaxDeg < length <= kBlockMaxDeg
+//   global class: length > kBlockMaxDeg (hash table in global scratch)
+constexpr int kWarpMaxDeg = 128;
+constexpr int kWarpCap = 256;
+constexpr int kBlockMaxDeg = 2048;
+constexpr int kBlockCap = 4096;
+
+struct Bins {
+  int32_t* block_list;   // [n]
+  int32_t* global_list;  // [n]
+  int* counts;           // device: [0] block count, [1] global count, [2] max length
+  int h_block = 0, h_global = 0, h_maxdeg = 0;  // host copies after bins_read
+};
+
+void bins_build(const GraphView& g, Bins& b, cudaStream_t s);
+
+// Scratch for the global-class tables: blocks x cap slots.
+struct GlobalTables {
+  int32_t* keys = nullptr;
+  long long* vals = nullptr;
+  int64_t cap = 0;  // slots per table (power of two)
+  int blocks = 0;
+};
+int64_t global_table_cap(int maxdeg);
+
+// One synchronous label-propagation round; lab_in == nullptr means the identity
+// labelling (first round of a level).
+void lp_round(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* lab_in,
+              int32_t* lab_out, uint64_t key, cudaStream_t s);
+
+// Pre-merge for contraction: for each vertex v, the distinct coarse neighbours cu =
+// cid[u] != cid[v] with summed weights, written at [off[v], off[v] + cnt[v]).
+void emit_cross(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* cid,
+                int32_t* tmp_key, long long* tmp_val, int32_t* cnt, cudaStream_t s);
+
+// ------------------------------------------------------------------ contraction
+struct ContractScratch {
+  int32_t* flags;        // [n]
+  int32_t* rank;         // [n]
+  int32_t* cnt;          // [n]
+  long long* pos;        // [n + 1]
+  int32_t* tmp_key;      // [nnz]
+  long long* tmp_val;    // [nnz]
+  long long* scan_scr;   // scan scratch (sized for max(n, nnz))
+  int* scan_scr32;
+};
+
+// Relabel: cid[v] = rank of lab[v] among the distinct labels; *c_dev = count.
+void relabel(const int32_t* lab, int64_t n, int32_t* cid, ContractScratch& cs, int* c_dev, cudaStream_t s);
+
+// Builds (cid[v] << bits | cu, weight) pairs from the pre-merged lists.
+void build_pairs(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int bits,
+                 unsigned long long* keys, long long* vals, cudaStream_t s);
+
+// From sorted pairs: merge equal keys, write the coarse CSR (offsets for c
+// vertices).  Uses heads/hpos scratch of `pairs` elements; *nnz_dev gets the count.
+void reduce_pairs(const unsigned long long* keys, const long long* vals, int64_t pairs, int bits,
+                  int64_t c, int32_t* heads, long long* hpos, long long* scan_scr, int64_t* coff,
+                  int32_t* cadj, long long* cw, int32_t* cv_tmp, long long* nnz_dev, cudaStream_t s);
+
+// ------------------------------------------------------------------ bounds
+void degrees(const GraphView& g, long long* deg, cudaStream_t s);
+// Minimum degree with smallest argmin; if below st->lambda_hat the bound improves
+// and st->improved is set (st->argmin/dmin always written).  partial: >= 1024 slots.
+void bound_update(const long long* deg, int64_t n, DevState* st, long long* partial, cudaStream_t s);
+// Initial bound on the input graph: lambda-hat = minimum degree, best = its argmin.
+void bound_init(const long long* deg, int64_t n, DevState* st, long long* partial, cudaStream_t s);
+// On improvement: side1[j] = (cur1[j] == st->argmin) and best_kind = 1.
+void snapshot_side(const int32_t* cur1, int64_t n1, unsigned char* side1, DevState* st, cudaStream_t s);
+void compose_map(int32_t* cur1, int64_t n1, const int32_t* cid, cudaStream_t s);
+void iota(int32_t* x, int64_t n, cudaStream_t s);
+// Final side bitmap of the input vertices (see side_of in bound.cu).
+void side_bits2(const int32_t* orig_map, int64_t n, const unsigned char* side1, const int32_t* cur1,
+                const unsigned char* sideK, const DevState* st, unsigned long long* bits, cudaStream_t s);
+void trace_push(DevState* st, TraceStep* trace, int cap, int kind, int level, cudaStream_t s);
+
+// ------------------------------------------------------------------ Padberg-Rinaldi
+void pr_partners(const GraphView& g, int32_t* partner, long long* pw, long long* deg, cudaStream_t s);
+// Pass A: PR1 edges and PR2 designated-partner edges, union-find, roots -> labels.
+void pr_pass_a(const GraphView& g, const int32_t* partner, const long long* pw, const long long* deg,
+               const DevState* st, int32_t* parent, int32_t* labels, int* changed, cudaStream_t s);
+// Pass B: PR3 / PR4 on mutual partner pairs.
+void pr_pass_b(const GraphView& g, const int32_t* partner, const long long* pw, const long long* deg,
+               const DevState* st, int32_t* labels, int* changed, cudaStream_t s);
+
+// ------------------------------------------------------------------ NOI
+constexpr int kDenseMax = 512;
+// All remaining rounds on a graph of n <= kDenseMax vertices inside one block.
+// sideK[k] snapshots improvements over the graph's vertices (best_kind = 2).
+void noi_dense(const GraphView& g, long long* M0, long long* M1, int32_t* curK, unsigned char* sideK,
+               DevState* st, TraceStep* trace, int trace_cap, int level, cudaStream_t s);
+// One round of the maximum-adjacency scan on a larger graph; labels = union-find roots.
+void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, unsigned char* seen,
+                      int32_t* parent, int32_t* labels, int* changed, cudaStream_t s);
+}  // namespace vc

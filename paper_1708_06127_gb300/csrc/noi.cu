@@ -1,0 +1,283 @@
+// Final exact step: the minimum-cut algorithm of Nagamochi, Ono and Ibaraki (Sec. 3,
+// "The Minimum Cut Algorithm of Nagamochi, Ono and Ibaraki"; used on the kernel in
+// Sec. 4.1, "Final Step", and Algorithm 1).  A round is a maximum-adjacency scan
+// from vertex 0 that always visits the unvisited vertex of largest attachment r
+// (ties: smallest id); when x is visited every unvisited neighbour y gets
+// r(y) += c(x,y) and q(x,y) = r(y) bounds the smallest x-y cut from below, so every
+// edge with q >= lambda-hat (fixed for the round) is contracted.  Rounds repeat on
+// the contracted graph until one vertex is left, the bound following the minimum
+// degree after each contraction.
+#include <limits.h>
+
+#include "kernels.cuh"
+
+namespace vc {
+
+constexpr int kNoiThreads = 512;
+
+__device__ __forceinline__ int sfind(volatile int* p, int x) {
+  for (;;) {
+    int px = p[x];
+    if (px == x) return x;
+    int ppx = p[px];
+    if (ppx != px) p[x] = ppx;
+    x = px;
+  }
+}
+
+__device__ __forceinline__ void sunite(int* p, int a, int b) {
+  for (;;) {
+    a = sfind(p, a);
+    b = sfind(p, b);
+    if (a == b) return;
+    if (a < b) { int t = a; a = b; b = t; }
+    if (atomicCAS(&p[a], a, b) == a) return;
+  }
+}
+
+// argmax of (r, -k) over unseen k < nk, by one warp
+__device__ __forceinline__ int warp_argmax_unseen(const long long* r, const int* seen, int nk) {
+  const int lane = threadIdx.x & 31;
+  long long br = -1;
+  int bx = INT_MAX;
+  for (int k = lane; k < nk; k += 32)
+    if (!seen[k]) {
+      long long rv = r[k];
+      if (rv > br || (rv == br && k < bx)) { br = rv; bx = k; }
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    long long orv = __shfl_xor_sync(0xffffffffu, br, o);
+    int ox = __shfl_xor_sync(0xffffffffu, bx, o);
+    if (orv > br || (orv == br && ox < bx)) { br = orv; bx = ox; }
+  }
+  return bx;
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(kNoiThreads) noi_dense_k(int n, const int64_t* __restrict__ off,
+                                                           const int32_t* __restrict__ adj, const WT* __restrict__ w,
+                                                           long long* M0, long long* M1, int32_t* curK,
+                                                           unsigned char* sideK, DevState* st, TraceStep* trace,
+                                                           int trace_cap, int level) {
+  __shared__ long long r[kDenseMax];
+  __shared__ int seen[kDenseMax];
+  __shared__ int parent[kDenseMax];
+  __shared__ int root[kDenseMax];
+  __shared__ int rr[kDenseMax];
+  __shared__ int wsum[kNoiThreads / 32];
+  __shared__ long long red_d[kNoiThreads / 32];
+  __shared__ int red_v[kNoiThreads / 32];
+  __shared__ long long red_c[kNoiThreads / 32];
+  __shared__ int s_x, s_stop, s_improved, s_nk2, s_arg;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int T = kNoiThreads;
+  int nk = n;
+  long long* M = M0;
+  long long* Mn = M1;
+  for (int i = tid; i < nk * nk; i += T) M[i] = 0;
+  for (int k = tid; k < n; k += T) curK[k] = k;
+  __syncthreads();
+  for (int v = tid; v < nk; v += T)
+    for (int64_t e = off[v]; e < off[v + 1]; ++e) M[v * nk + adj[e]] += (long long)w[e];
+  __syncthreads();
+  while (nk > 1) {
+    const long long lam = st->lambda_hat;
+    for (int k = tid; k < nk; k += T) { r[k] = 0; seen[k] = 0; parent[k] = k; }
+    __syncthreads();
+    for (int step = 0; step < nk; ++step) {
+      if (wid == 0) {
+        int x = warp_argmax_unseen(r, seen, nk);
+        if (lane == 0) { s_x = x; seen[x] = 1; }
+      }
+      __syncthreads();
+      const int x = s_x;
+      const long long* row = M + (int64_t)x * nk;
+      for (int y = tid; y < nk; y += T) {
+        if (!seen[y]) {
+          long long c = row[y];
+          if (c != 0) {
+            long long ry = r[y] + c;
+            r[y] = ry;
+            if (ry >= lam) sunite(parent, x, y);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // roots -> ranks (every root is the minimum of its component)
+    for (int k = tid; k < nk; k += T) root[k] = sfind(parent, k);
+    __syncthreads();
+    {
+      int flag = (tid < nk && root[tid] == tid) ? 1 : 0;  // nk <= T
+      int inc = flag;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (lane == 31) wsum[wid] = inc;
+      __syncthreads();
+      if (tid == 0) {
+        int acc = 0;
+        for (int q = 0; q < T / 32; ++q) { int t = wsum[q]; wsum[q] = acc; acc += t; }
+        s_nk2 = acc;
+      }
+      __syncthreads();
+      if (tid < nk) rr[tid] = wsum[wid] + inc - flag;
+      __syncthreads();
+    }
+    const int nk2 = s_nk2;
+    if (nk2 == nk) break;  // no contraction (cannot happen while lambda-hat <= min degree)
+    for (int i = tid; i < nk2 * nk2; i += T) Mn[i] = 0;
+    __syncthreads();
+    for (int i = tid; i < nk * nk; i += T) {
+      long long c = M[i];
+      if (c != 0) {
+        int a = rr[root[i / nk]], b = rr[root[i % nk]];
+        if (a != b) atomicAdd((unsigned long long*)&Mn[a * nk2 + b], (unsigned long long)c);
+      }
+    }
+    for (int k = tid; k < n; k += T) curK[k] = rr[root[curK[k]]];
+    __syncthreads();
+    { long long* t = M; M = Mn; Mn = t; }
+    nk = nk2;
+    // degrees, minimum with smallest argmin, and entry count of the contracted graph
+    long long bd = LLONG_MAX, cnt = 0;
+    int bv = INT_MAX;
+    for (int a = tid; a < nk; a += T) {
+      long long d = 0;
+      const long long* row = M + (int64_t)a * nk;
+      for (int b = 0; b < nk; ++b) {
+        long long c = row[b];
+        d += c;
+        cnt += c != 0;
+      }
+      if (d < bd || (d == bd && a < bv)) { bd = d; bv = a; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      long long od = __shfl_xor_sync(0xffffffffu, bd, o);
+      int ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+      if (od < bd || (od == bd && ov < bv)) { bd = od; bv = ov; }
+    }
+    if (lane == 0) { red_d[wid] = bd; red_v[wid] = bv; red_c[wid] = cnt; }
+    __syncthreads();
+    if (tid == 0) {
+      long long tot = 0;
+      for (int q = 0; q < T / 32; ++q) {
+        tot += red_c[q];
+        if (red_d[q] < bd || (red_d[q] == bd && red_v[q] < bv)) { bd = red_d[q]; bv = red_v[q]; }
+      }
+      s_stop = 0;
+      s_improved = 0;
+      st->n = nk;
+      st->nnz = tot;
+      if (nk > 1) {
+        st->dmin = bd;
+        st->argmin = bv;
+        if (bd < st->lambda_hat) {
+          st->lambda_hat = bd;
+          st->best_kind = 2;
+          s_improved = 1;
+          s_arg = bv;
+        }
+        if (st->lambda_hat == 0) s_stop = 1;
+      }
+      int i = st->trace_len;
+      if (i < trace_cap) trace[i] = TraceStep{4, level, (long long)nk, tot, st->lambda_hat};
+      st->trace_len = i + 1;
+    }
+    __syncthreads();
+    if (s_improved) {
+      const int b = s_arg;
+      for (int k = tid; k < n; k += T) sideK[k] = curK[k] == b ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_stop) break;
+  }
+}
+
+void noi_dense(const GraphView& g, long long* M0, long long* M1, int32_t* curK, unsigned char* sideK,
+               DevState* st, TraceStep* trace, int trace_cap, int level, cudaStream_t s) {
+  if (g.wbytes == 4)
+    noi_dense_k<int32_t><<<1, kNoiThreads, 0, s>>>((int)g.n, g.off, g.adj, (const int32_t*)g.w, M0, M1, curK,
+                                                   sideK, st, trace, trace_cap, level);
+  else
+    noi_dense_k<long long><<<1, kNoiThreads, 0, s>>>((int)g.n, g.off, g.adj, (const long long*)g.w, M0, M1, curK,
+                                                     sideK, st, trace, trace_cap, level);
+  count_launch();
+  VC_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------ sparse single round
+constexpr int kSparseThreads = 1024;
+
+template <typename WT>
+__global__ void __launch_bounds__(kSparseThreads) noi_round_k(int64_t n, const int64_t* __restrict__ off,
+                                                              const int32_t* __restrict__ adj,
+                                                              const WT* __restrict__ w, const DevState* st,
+                                                              long long* r, unsigned char* seen, int32_t* parent,
+                                                              int32_t* labels, int* changed) {
+  __shared__ long long red_r[kSparseThreads / 32];
+  __shared__ long long red_x[kSparseThreads / 32];
+  __shared__ long long s_x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const long long lam = st->lambda_hat;
+  for (int64_t k = tid; k < n; k += kSparseThreads) { r[k] = 0; seen[k] = 0; parent[k] = (int32_t)k; }
+  __syncthreads();
+  for (int64_t step = 0; step < n; ++step) {
+    long long br = -1, bx = LLONG_MAX;
+    for (int64_t k = tid; k < n; k += kSparseThreads)
+      if (!seen[k]) {
+        long long rv = r[k];
+        if (rv > br || (rv == br && k < bx)) { br = rv; bx = k; }
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      long long orv = __shfl_xor_sync(0xffffffffu, br, o);
+      long long ox = __shfl_xor_sync(0xffffffffu, bx, o);
+      if (orv > br || (orv == br && ox < bx)) { br = orv; bx = ox; }
+    }
+    if (lane == 0) { red_r[wid] = br; red_x[wid] = bx; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int q = 1; q < kSparseThreads / 32; ++q)
+        if (red_r[q] > br || (red_r[q] == br && red_x[q] < bx)) { br = red_r[q]; bx = red_x[q]; }
+      s_x = bx;
+      seen[bx] = 1;
+    }
+    __syncthreads();
+    const int64_t x = s_x;
+    for (int64_t e = off[x] + tid; e < off[x + 1]; e += kSparseThreads) {
+      const int y = adj[e];
+      if (seen[y]) continue;
+      const long long c = (long long)w[e];
+      const long long ry = (long long)atomicAdd((unsigned long long*)&r[y], (unsigned long long)c) + c;
+      if (ry >= lam) sunite(parent, (int)x, y);
+    }
+    __syncthreads();
+  }
+  int any = 0;
+  for (int64_t k = tid; k < n; k += kSparseThreads) {
+    int rt = sfind(parent, (int)k);
+    labels[k] = rt;
+    any |= rt != k;
+  }
+  if (__syncthreads_or(any) && tid == 0) atomicOr(changed, 1);
+}
+
+void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, unsigned char* seen,
+                      int32_t* parent, int32_t* labels, int* changed, cudaStream_t s) {
+  if (g.wbytes == 4)
+    noi_round_k<int32_t><<<1, kSparseThreads, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, st, r, seen, parent,
+                                                       labels, changed);
+  else
+    noi_round_k<long long><<<1, kSparseThreads, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, st, r, seen,
+                                                         parent, labels, changed);
+  count_launch();
+  VC_CHECK_LAUNCH();
+}
+
+}  // namespace vc

@@ -1,0 +1,180 @@
+// Padberg-Rinaldi reductions (Lemma "Padberg-Rinaldi", Sec. 4.1) with lock-free
+// union-find.  Pass A tests conditions 1 and 2, pass B conditions 3 and 4, as the
+// two passes of one "run" (Sec. 4.1, "Exact Reductions by Padberg and Rinaldi").
+// Condition 2 marks only the edge to the designated partner p(v) = argmax over
+// neighbours of (c(v,u), -u), and conditions 3/4 are checked on mutual partner
+// pairs; the union of the marked edges is contracted in one step.
+#include <limits.h>
+
+#include "kernels.cuh"
+
+namespace vc {
+
+// Union-find whose representative is the smallest id of the component: a root is
+// only ever linked below a smaller root (CAS on a root's own entry), so the final
+// root of a component is its minimum.  Path halving writes only ancestors.
+__device__ __forceinline__ int uf_find(volatile int32_t* p, int x) {
+  for (;;) {
+    int px = p[x];
+    if (px == x) return x;
+    int ppx = p[px];
+    if (ppx != px) p[x] = ppx;
+    x = px;
+  }
+}
+
+__device__ __forceinline__ void uf_unite(int32_t* p, int a, int b) {
+  for (;;) {
+    a = uf_find(p, a);
+    b = uf_find(p, b);
+    if (a == b) return;
+    if (a < b) { int t = a; a = b; b = t; }
+    if (atomicCAS(&p[a], a, b) == a) return;
+  }
+}
+
+template <typename WT>
+__global__ void partners_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                           const WT* __restrict__ w, int32_t* __restrict__ partner, long long* __restrict__ pw,
+                           long long* __restrict__ deg) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    long long s = 0, bw = -1;
+    int bu = INT_MAX;
+    for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32) {
+      long long x = (long long)w[e];
+      int u = adj[e];
+      s += x;
+      if (x > bw || (x == bw && u < bu)) { bw = x; bu = u; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+      long long ow = __shfl_xor_sync(0xffffffffu, bw, o);
+      int ou = __shfl_xor_sync(0xffffffffu, bu, o);
+      if (ow > bw || (ow == bw && ou < bu)) { bw = ow; bu = ou; }
+    }
+    if (lane == 0) {
+      deg[v] = s;
+      partner[v] = bw < 0 ? -1 : bu;
+      pw[v] = bw;
+    }
+  }
+}
+
+void pr_partners(const GraphView& g, int32_t* partner, long long* pw, long long* deg, cudaStream_t s) {
+  int grid = grid_for(g.n, 8, kSMs * 16);
+  if (g.wbytes == 4) partners_k<int32_t><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, partner, pw, deg);
+  else partners_k<long long><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, partner, pw, deg);
+  count_launch();
+  VC_CHECK_LAUNCH();
+}
+
+__global__ void uf_init_k(int32_t* __restrict__ p, int64_t n) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    p[v] = (int32_t)v;
+}
+
+// Condition 1 on every edge (once per undirected edge: u > v) and condition 2 on the
+// designated-partner edge; both ends must have at least two distinct neighbours.
+template <typename WT>
+__global__ void pr_a_mark_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                            const WT* __restrict__ w, const int32_t* __restrict__ partner,
+                            const long long* __restrict__ pw, const long long* __restrict__ deg,
+                            const DevState* st, int32_t* parent) {
+  const int lane = threadIdx.x & 31;
+  const long long lam = st->lambda_hat;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int64_t beg = off[v], end = off[v + 1];
+    if (end - beg < 2) continue;
+    for (int64_t e = beg + lane; e < end; e += 32) {
+      int u = adj[e];
+      if (u > v && (long long)w[e] >= lam && off[u + 1] - off[u] >= 2) uf_unite(parent, (int)v, u);
+    }
+    if (lane == 0) {
+      int p = partner[v];
+      if (p >= 0 && off[p + 1] - off[p] >= 2 && deg[v] <= 2 * pw[v]) uf_unite(parent, (int)v, p);
+    }
+  }
+}
+
+__global__ void uf_flatten_k(int32_t* parent, int64_t n, int32_t* __restrict__ labels, int* changed) {
+  int any = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int r = uf_find(parent, (int)v);
+    labels[v] = r;
+    any |= (r != v);
+  }
+  if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(changed, 1);
+}
+
+void pr_pass_a(const GraphView& g, const int32_t* partner, const long long* pw, const long long* deg,
+               const DevState* st, int32_t* parent, int32_t* labels, int* changed, cudaStream_t s) {
+  int grid1 = grid_for(g.n, 256, kSMs * 8);
+  uf_init_k<<<grid1, 256, 0, s>>>(parent, g.n);
+  int grid = grid_for(g.n, 8, kSMs * 16);
+  if (g.wbytes == 4)
+    pr_a_mark_k<int32_t><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, partner, pw, deg, st, parent);
+  else
+    pr_a_mark_k<long long><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, partner, pw, deg, st, parent);
+  uf_flatten_k<<<grid1, 256, 0, s>>>(parent, g.n, labels, changed);
+  count_launch(3);
+  VC_CHECK_LAUNCH();
+}
+
+// Conditions 3 and 4 on mutual partner pairs v < w = p(v), p(w) = v, through the
+// common neighbourhood (binary search of N(v)'s entries in w's sorted list).
+template <typename WT>
+__global__ void pr_b_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                       const WT* __restrict__ w, const int32_t* __restrict__ partner,
+                       const long long* __restrict__ pw, const long long* __restrict__ deg, const DevState* st,
+                       int32_t* __restrict__ labels, int* changed) {
+  const int lane = threadIdx.x & 31;
+  const long long lam = st->lambda_hat;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int p = partner[v];
+    if (p <= v || partner[p] != v) continue;
+    const int64_t vb = off[v], ve = off[v + 1], pb = off[p], pe = off[p + 1];
+    if (ve - vb < 2 || pe - pb < 2) continue;
+    const long long cvw = pw[v], dv = deg[v], dp = deg[p];
+    bool pr3 = false;
+    long long sum = 0;
+    for (int64_t e = vb + lane; e < ve; e += 32) {
+      const int u = adj[e];
+      int64_t lo = pb, hi = pe;
+      while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (adj[mid] < u) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo < pe && adj[lo] == u) {
+        const long long cvu = (long long)w[e], cwu = (long long)w[lo];
+        if (dv <= 2 * (cvw + cvu) && dp <= 2 * (cvw + cwu)) pr3 = true;
+        sum += cvu < cwu ? cvu : cwu;
+      }
+    }
+    pr3 = __any_sync(0xffffffffu, pr3);
+    sum = warp_sum(sum);
+    if (lane == 0 && (pr3 || cvw + sum >= lam)) {
+      labels[p] = (int32_t)v;
+      atomicOr(changed, 1);
+    }
+  }
+}
+
+void pr_pass_b(const GraphView& g, const int32_t* partner, const long long* pw, const long long* deg,
+               const DevState* st, int32_t* labels, int* changed, cudaStream_t s) {
+  iota(labels, g.n, s);
+  int grid = grid_for(g.n, 8, kSMs * 16);
+  if (g.wbytes == 4)
+    pr_b_k<int32_t><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, partner, pw, deg, st, labels, changed);
+  else
+    pr_b_k<long long><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, partner, pw, deg, st, labels, changed);
+  count_launch();
+  VC_CHECK_LAUNCH();
+}
+
+}  // namespace vc

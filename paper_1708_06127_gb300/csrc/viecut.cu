@@ -1,0 +1,947 @@
+// Host driver and C ABI of the GB300 VieCut library.
+//
+// Algorithm 1 of the paper (Appendix A) in the deterministic variant that
+// include/viecut.h describes: levels of label propagation + cluster contraction +
+// Padberg-Rinaldi runs while more than n0 vertices remain, then the exact step of
+// Nagamochi, Ono and Ibaraki, with the trivial-cut bound tracked after every
+// contraction.  Every step runs in this library's CUDA kernels; the host only
+// sequences launches and reads a small state record at decision points.
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "prims.cuh"
+#include "viecut.h"
+
+namespace vc {
+
+unsigned long long g_launches = 0;
+static thread_local std::string t_last_error;
+
+// ------------------------------------------------------------- device buffers
+struct Buf {
+  void* p = nullptr;
+  size_t cap = 0;
+  Buf() = default;
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  ~Buf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  void* ensure(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (bytes > cap) {
+      release();
+      cudaError_t e = cudaMalloc(&p, bytes);
+      if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        throw Error{VIECUT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e)};
+      }
+      cap = bytes;
+    }
+    return p;
+  }
+  template <typename T>
+  T* ensure_n(int64_t count) { return (T*)ensure(sizeof(T) * (size_t)(count > 0 ? count : 1)); }
+  template <typename T>
+  T* as() const { return (T*)p; }
+};
+
+struct Counters {
+  int c;
+  int pad;
+  long long pairs;
+  int changed;
+  int pad2;
+};
+
+enum Phase { kPhLP = 0, kPhContract, kPhPR, kPhNOI, kPhOther, kPhCount };
+
+// Everything one run needs on the device.
+struct Workspace {
+  cudaStream_t s = nullptr;
+  // vertex-sized
+  Buf deg, labA, labB, map0, cidT, cur1, side1, flags, rank, cnt, pos, scan64, scan32;
+  Buf partner, pw, parent, blist, glist, bcounts, noi_r, noi_seen;
+  // entry-sized
+  Buf tmpK, tmpV;
+  // pair-sized
+  Buf keysA, keysB, valsA, valsB, hist, heads, hpos, cvT;
+  // coarse graphs (ping-pong)
+  Buf coff[2], cadj[2], cw[2];
+  // global-class tables
+  Buf gkeys, gvals;
+  GlobalTables gt;
+  // exact step
+  Buf M0, M1, curK, sideK;
+  // state
+  Buf state, trace, partial, counters;
+  DevState* h_state = nullptr;
+  Counters* h_counters = nullptr;
+  int trace_cap = 4096;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> spans;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> lp_spans;
+  long long lp_bytes_acc = 0, lp_nnz_acc = 0, lp_n_acc = 0;
+
+  Workspace() {
+    VC_CUDA(cudaMallocHost(&h_state, sizeof(DevState)));
+    VC_CUDA(cudaMallocHost(&h_counters, sizeof(Counters)));
+    state.ensure(sizeof(DevState));
+    trace.ensure_n<TraceStep>(trace_cap);
+    partial.ensure_n<long long>(2 * 1024);
+    counters.ensure(sizeof(Counters));
+    bcounts.ensure_n<int>(4);
+  }
+  ~Workspace() {
+    if (h_state) cudaFreeHost(h_state);
+    if (h_counters) cudaFreeHost(h_counters);
+    for (auto e : ev_pool) cudaEventDestroy(e);
+  }
+  DevState* st() { return state.as<DevState>(); }
+  Counters* ctr() { return counters.as<Counters>(); }
+
+  void ensure_vertices(int64_t n) {
+    deg.ensure_n<long long>(n);
+    labA.ensure_n<int32_t>(n);
+    labB.ensure_n<int32_t>(n);
+    map0.ensure_n<int32_t>(n);
+    cidT.ensure_n<int32_t>(n);
+    cur1.ensure_n<int32_t>(n);
+    side1.ensure_n<unsigned char>(n);
+    flags.ensure_n<int32_t>(n);
+    rank.ensure_n<int32_t>(n);
+    cnt.ensure_n<int32_t>(n);
+    pos.ensure_n<long long>(n + 1);
+    partner.ensure_n<int32_t>(n);
+    pw.ensure_n<long long>(n);
+    parent.ensure_n<int32_t>(n);
+    blist.ensure_n<int32_t>(n);
+    glist.ensure_n<int32_t>(n);
+    scan32.ensure_n<int>(scan_scratch_elems(n) + 1);
+  }
+  void ensure_entries(int64_t nnz, int64_t n) {
+    tmpK.ensure_n<int32_t>(nnz);
+    tmpV.ensure_n<long long>(nnz);
+    scan64.ensure_n<long long>(scan_scratch_elems(std::max(nnz, n)) + 1);
+  }
+  void ensure_noi() {
+    M0.ensure_n<long long>((int64_t)kDenseMax * kDenseMax);
+    M1.ensure_n<long long>((int64_t)kDenseMax * kDenseMax);
+    curK.ensure_n<int32_t>(kDenseMax);
+    sideK.ensure_n<unsigned char>(kDenseMax);
+  }
+
+  void sync() { VC_CUDA(cudaStreamSynchronize(s)); }
+  void read_state() {
+    VC_CUDA(cudaMemcpyAsync(h_state, st(), sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    VC_CUDA(cudaMemcpyAsync(h_counters, ctr(), sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    sync();
+  }
+
+  // ---------------------------------------------------------------- timing
+  cudaEvent_t ev() {
+    if (ev_used == ev_pool.size()) {
+      cudaEvent_t e;
+      VC_CUDA(cudaEventCreate(&e));
+      ev_pool.push_back(e);
+    }
+    return ev_pool[ev_used++];
+  }
+  cudaEvent_t mark() {
+    if (!timing) return nullptr;
+    cudaEvent_t e = ev();
+    VC_CUDA(cudaEventRecord(e, s));
+    return e;
+  }
+  void span(int ph, cudaEvent_t a) {
+    if (!timing) return;
+    spans.push_back({ph, {a, mark()}});
+  }
+  void reset_timing() {
+    ev_used = 0;
+    spans.clear();
+    lp_spans.clear();
+    lp_bytes_acc = lp_nnz_acc = lp_n_acc = 0;
+  }
+
+  // ---------------------------------------------------------------- steps
+  Bins bins;
+  bool bins_valid = false;
+
+  void build_bins(const GraphView& g) {
+    bins.block_list = blist.as<int32_t>();
+    bins.global_list = glist.as<int32_t>();
+    bins.counts = bcounts.as<int>();
+    bins_build(g, bins, s);
+    int hc[3];
+    VC_CUDA(cudaMemcpyAsync(hc, bins.counts, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    sync();
+    bins.h_block = hc[0];
+    bins.h_global = hc[1];
+    bins.h_maxdeg = hc[2];
+    if (bins.h_global > 0) {
+      int64_t cap = global_table_cap(bins.h_maxdeg);
+      int blocks = std::min(bins.h_global, kSMs);
+      // keep the scratch under ~2 GiB
+      while (blocks > 1 && (int64_t)blocks * cap * 12 > (int64_t(2) << 30)) blocks /= 2;
+      gt.keys = gkeys.ensure_n<int32_t>(blocks * cap);
+      gt.vals = gvals.ensure_n<long long>(blocks * cap);
+      gt.cap = cap;
+      gt.blocks = blocks;
+    }
+    bins_valid = true;
+  }
+
+  void lp_rounds(const GraphView& g, uint64_t key, int rounds, int32_t** out_labels, int32_t* all_out) {
+    int32_t* in = nullptr;
+    int32_t* bufs[2] = {labA.as<int32_t>(), labB.as<int32_t>()};
+    for (int r = 0; r < rounds; ++r) {
+      int32_t* out = bufs[r & 1];
+      cudaEvent_t a = mark();
+      lp_round(g, bins, gt, in, out, key, s);
+      if (timing) {
+        lp_spans.push_back({a, mark()});
+        long long gather = in ? 4 : 0;
+        lp_bytes_acc += 8 * (g.n + 1) + g.nnz * (4 + g.wbytes + gather) + 4 * g.n;
+        lp_nnz_acc += g.nnz;
+        lp_n_acc += g.n;
+      }
+      if (all_out)
+        VC_CUDA(cudaMemcpyAsync(all_out + (int64_t)r * g.n, out, sizeof(int32_t) * g.n, cudaMemcpyDeviceToHost, s));
+      in = out;
+    }
+    *out_labels = in;
+  }
+
+  // Contracts g by labels into the coarse buffer `slot`; cid_out[n] receives the map.
+  // Returns the coarse view; h_counters holds c and the pair count afterwards.
+  GraphView contract(const GraphView& g, const int32_t* labels, int32_t* cid_out, int slot) {
+    if (!bins_valid) build_bins(g);
+    ContractScratch cs;
+    cs.flags = flags.as<int32_t>();
+    cs.rank = rank.as<int32_t>();
+    cs.cnt = cnt.as<int32_t>();
+    cs.pos = pos.as<long long>();
+    cs.tmp_key = tmpK.as<int32_t>();
+    cs.tmp_val = tmpV.as<long long>();
+    cs.scan_scr = scan64.as<long long>();
+    cs.scan_scr32 = scan32.as<int>();
+    relabel(labels, g.n, cid_out, cs, &ctr()->c, s);
+    emit_cross(g, bins, gt, cid_out, cs.tmp_key, cs.tmp_val, cs.cnt, s);
+    exclusive_scan<int, long long>(cs.cnt, cs.pos, g.n, &ctr()->pairs, cs.scan_scr, s);
+    VC_CUDA(cudaMemcpyAsync(h_counters, ctr(), sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    sync();
+    const int64_t c = h_counters->c;
+    const int64_t P = h_counters->pairs;
+    int bits = ceil_log2(c);
+    if (bits < 1) bits = 1;
+    auto* kA = keysA.ensure_n<unsigned long long>(P);
+    auto* kB = keysB.ensure_n<unsigned long long>(P);
+    auto* vA = valsA.ensure_n<long long>(P);
+    auto* vB = valsB.ensure_n<long long>(P);
+    auto* hs = hist.ensure_n<long long>(radix_hist_elems(P));
+    auto* hd = heads.ensure_n<int32_t>(P);
+    auto* hp = hpos.ensure_n<long long>(P + 1);
+    auto* cv = cvT.ensure_n<int32_t>(P);
+    scan64.ensure_n<long long>(scan_scratch_elems(std::max<int64_t>(P, 1)) + 1);
+    build_pairs(g, cid_out, cs, bits, kA, vA, s);
+    radix_sort_pairs(kA, vA, kB, vB, P, 2 * bits, hs, s);
+    int64_t* co = coff[slot].ensure_n<int64_t>(c + 1);
+    int32_t* ca = cadj[slot].ensure_n<int32_t>(P);
+    long long* cwp = cw[slot].ensure_n<long long>(P);
+    reduce_pairs(kA, vA, P, bits, c, hd, hp, scan64.as<long long>(), co, ca, cwp, cv, &st()->nnz, s);
+    GraphView h;
+    h.n = c;
+    h.nnz = P;  // upper bound until the state is read
+    h.off = co;
+    h.adj = ca;
+    h.w = cwp;
+    h.wbytes = 8;
+    bins_valid = false;
+    return h;
+  }
+};
+
+__global__ void set_n_k(DevState* st, long long n) { st->n = n; }
+
+__global__ void validate_k(int64_t n, int64_t m, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                           const int32_t* __restrict__ w, int* err) {
+  int bad = 0;
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t0 == 0 && (off[0] != 0 || off[n] != m)) bad |= 1;
+  for (int64_t v = t0; v < n; v += T)
+    if (off[v + 1] < off[v]) bad |= 2;
+  // per-entry checks need the owning vertex for self-loops: warp per vertex
+  const int lane = threadIdx.x & 31;
+  const int64_t W = T >> 5;
+  for (int64_t v = t0 >> 5; v < n; v += W) {
+    int64_t a = off[v], b = off[v + 1];
+    if (a < 0 || b > m || a > b) { bad |= 2; continue; }
+    for (int64_t e = a + lane; e < b; e += 32) {
+      int32_t u = adj[e];
+      if (u < 0 || u >= n) bad |= 4;
+      else if (u == v) bad |= 8;
+      if (w[e] < 1) bad |= 16;
+    }
+  }
+  if (bad) atomicOr(err, bad);
+}
+
+struct Handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t n = 0, m = 0;
+  int64_t n0 = 10000;
+  int pr_runs_max = 8;
+  int validate = 1;
+  const int64_t* off0 = nullptr;
+  const int32_t* adj0 = nullptr;
+  const int32_t* w0 = nullptr;
+  Buf in_off, in_adj, in_w, out_cut, out_bits;
+  Workspace* ws = nullptr;
+  viecut_stats stats{};
+  std::vector<viecut_step> last_trace;
+  ~Handle() {
+    delete ws;
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+};
+
+static void device_validate(Handle& H) {
+  Workspace& W = *H.ws;
+  int* err = &W.ctr()->changed;
+  VC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), H.stream));
+  validate_k<<<grid_for(H.n, 256, kSMs * 8), 256, 0, H.stream>>>(H.n, H.m, H.off0, H.adj0, H.w0, err);
+  count_launch();
+  VC_CHECK_LAUNCH();
+  W.read_state();
+  int bad = W.h_counters->changed;
+  if (bad) {
+    std::string why;
+    if (bad & 1) why += " offsets[0] != 0 or offsets[n] != m;";
+    if (bad & 2) why += " offsets decrease or leave [0, m];";
+    if (bad & 4) why += " neighbour id out of range;";
+    if (bad & 8) why += " self-loop;";
+    if (bad & 16) why += " weight < 1;";
+    throw Error{VIECUT_EINVAL, "invalid graph:" + why};
+  }
+}
+
+static void host_validate(const int64_t* off, const int32_t* adj, const int32_t* w, int64_t n, int64_t m,
+                          bool symmetric) {
+  if (off[0] != 0 || off[n] != m) throw Error{VIECUT_EINVAL, "invalid graph: offsets[0] != 0 or offsets[n] != m"};
+  for (int64_t v = 0; v < n; ++v) {
+    if (off[v + 1] < off[v]) throw Error{VIECUT_EINVAL, "invalid graph: offsets decrease at vertex " + std::to_string(v)};
+    for (int64_t e = off[v]; e < off[v + 1]; ++e) {
+      if (adj[e] < 0 || adj[e] >= n) throw Error{VIECUT_EINVAL, "invalid graph: neighbour id out of range"};
+      if (adj[e] == v) throw Error{VIECUT_EINVAL, "invalid graph: self-loop at vertex " + std::to_string(v)};
+      if (w[e] < 1) throw Error{VIECUT_EINVAL, "invalid graph: weight < 1"};
+    }
+  }
+  if (!symmetric) return;
+  struct E { int64_t a, b; int32_t w; };
+  std::vector<E> fwd, bwd;
+  fwd.reserve(m);
+  bwd.reserve(m);
+  for (int64_t v = 0; v < n; ++v)
+    for (int64_t e = off[v]; e < off[v + 1]; ++e) {
+      fwd.push_back({v, adj[e], w[e]});
+      bwd.push_back({adj[e], v, w[e]});
+    }
+  auto lt = [](const E& x, const E& y) { return x.a < y.a || (x.a == y.a && (x.b < y.b || (x.b == y.b && x.w < y.w))); };
+  std::sort(fwd.begin(), fwd.end(), lt);
+  std::sort(bwd.begin(), bwd.end(), lt);
+  for (int64_t i = 0; i < m; ++i)
+    if (fwd[i].a != bwd[i].a || fwd[i].b != bwd[i].b || fwd[i].w != bwd[i].w)
+      throw Error{VIECUT_EINVAL, "invalid graph: not symmetric (edge weights must match in both directions)"};
+}
+
+// ------------------------------------------------------------------- the run
+static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, unsigned long long* d_bits) {
+  if (lp_iters < 0) throw Error{VIECUT_EINVAL, "lp_iters must be >= 0"};
+  Workspace& W = *H.ws;
+  W.s = H.stream;
+  cudaStream_t s = H.stream;
+  const unsigned long long launches0 = g_launches;
+  W.reset_timing();
+  cudaEvent_t t_start = W.mark();
+  DevState init{};
+  init.n = H.n;
+  init.nnz = H.m;
+  VC_CUDA(cudaMemcpyAsync(W.st(), &init, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  VC_CUDA(cudaMemsetAsync(W.ctr(), 0, sizeof(Counters), s));
+  DevState* st = W.st();
+  TraceStep* tr = W.trace.as<TraceStep>();
+  const int tcap = W.trace_cap;
+
+  GraphView G;
+  G.n = H.n;
+  G.nnz = H.m;
+  G.off = H.off0;
+  G.adj = H.adj0;
+  G.w = H.w0;
+  G.wbytes = 4;
+  W.bins_valid = false;
+
+  cudaEvent_t a = W.mark();
+  degrees(G, W.deg.as<long long>(), s);
+  bound_init(W.deg.as<long long>(), G.n, st, W.partial.as<long long>(), s);
+  trace_push(st, tr, tcap, 0, 0, s);
+  W.span(kPhOther, a);
+  W.read_state();
+
+  int level = 0;
+  int slot = -1;          // coarse buffer holding G (-1: the input)
+  bool contracted = false;
+  int64_t n1 = 0;         // tier-1 vertex count
+  int64_t levels = 0;
+  bool done = W.h_state->lambda_hat == 0;
+
+  // contraction + bound update; returns false when the run ends
+  auto step = [&](const int32_t* labels, int kind) -> bool {
+    cudaEvent_t a0 = W.mark();
+    int32_t* cid = contracted ? W.cidT.as<int32_t>() : W.map0.as<int32_t>();
+    int dst = slot == 0 ? 1 : 0;
+    GraphView h = W.contract(G, labels, cid, dst);
+    set_n_k<<<1, 1, 0, s>>>(st, h.n);
+    count_launch();
+    if (!contracted) {
+      n1 = h.n;
+      iota(W.cur1.as<int32_t>(), n1, s);
+      contracted = true;
+    } else {
+      compose_map(W.cur1.as<int32_t>(), n1, cid, s);
+    }
+    G = h;
+    slot = dst;
+    W.span(kPhContract, a0);
+    cudaEvent_t a1 = W.mark();
+    if (G.n > 1) {
+      degrees(G, W.deg.as<long long>(), s);
+      bound_update(W.deg.as<long long>(), G.n, st, W.partial.as<long long>(), s);
+      snapshot_side(W.cur1.as<int32_t>(), n1, W.side1.as<unsigned char>(), st, s);
+    }
+    trace_push(st, tr, tcap, kind, level, s);
+    W.span(kPhOther, a1);
+    W.read_state();
+    G.nnz = W.h_state->nnz;
+    return G.n > 1 && W.h_state->lambda_hat > 0;
+  };
+
+  auto read_changed = [&]() -> int {
+    VC_CUDA(cudaMemcpyAsync(&W.h_counters->changed, &W.ctr()->changed, sizeof(int), cudaMemcpyDeviceToHost, s));
+    W.sync();
+    return W.h_counters->changed;
+  };
+
+  while (!done && G.n > H.n0) {
+    const int64_t n_start = G.n;
+    const uint64_t key = level_key(seed, level);
+    W.build_bins(G);
+    int32_t* labels = nullptr;
+    cudaEvent_t a0 = W.mark();
+    if (lp_iters > 0) {
+      W.lp_rounds(G, key, lp_iters, &labels, nullptr);
+    } else {
+      labels = W.labA.as<int32_t>();
+      iota(labels, G.n, s);
+    }
+    W.span(kPhLP, a0);
+    ++levels;
+    if (!step(labels, 1)) { done = true; break; }
+    for (int run = 0; run < H.pr_runs_max && !done; ++run) {
+      bool any = false;
+      for (int pass = 0; pass < 2; ++pass) {
+        cudaEvent_t ap = W.mark();
+        VC_CUDA(cudaMemsetAsync(&W.ctr()->changed, 0, sizeof(int), s));
+        pr_partners(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), s);
+        int32_t* lab = W.labA.as<int32_t>();
+        if (pass == 0)
+          pr_pass_a(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), st,
+                    W.parent.as<int32_t>(), lab, &W.ctr()->changed, s);
+        else
+          pr_pass_b(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), st, lab,
+                    &W.ctr()->changed, s);
+        W.span(kPhPR, ap);
+        if (read_changed()) {
+          any = true;
+          if (!step(lab, pass == 0 ? 2 : 3)) { done = true; break; }
+        }
+      }
+      if (!any) break;
+    }
+    level += 1;
+    if (done) break;
+    if (G.n == n_start) break;
+  }
+
+  if (!done && G.n > 1) {
+    cudaEvent_t a0 = W.mark();
+    if (!contracted) {
+      n1 = G.n;
+      iota(W.map0.as<int32_t>(), G.n, s);
+      iota(W.cur1.as<int32_t>(), G.n, s);
+      contracted = true;
+    }
+    W.span(kPhOther, a0);
+    while (!done && G.n > kDenseMax) {
+      cudaEvent_t an = W.mark();
+      W.noi_r.ensure_n<long long>(G.n);
+      W.noi_seen.ensure_n<unsigned char>(G.n);
+      VC_CUDA(cudaMemsetAsync(&W.ctr()->changed, 0, sizeof(int), s));
+      noi_round_sparse(G, st, W.noi_r.as<long long>(), W.noi_seen.as<unsigned char>(), W.parent.as<int32_t>(),
+                       W.labA.as<int32_t>(), &W.ctr()->changed, s);
+      W.span(kPhNOI, an);
+      if (!read_changed()) { done = true; break; }
+      if (!step(W.labA.as<int32_t>(), 4)) { done = true; break; }
+    }
+    if (!done && G.n > 1) {
+      cudaEvent_t an = W.mark();
+      W.ensure_noi();
+      noi_dense(G, W.M0.as<long long>(), W.M1.as<long long>(), W.curK.as<int32_t>(), W.sideK.as<unsigned char>(),
+                st, tr, tcap, level, s);
+      W.span(kPhNOI, an);
+    }
+  }
+
+  cudaEvent_t a1 = W.mark();
+  // without any contraction the side is a single original vertex (best_kind 0)
+  side_bits2(contracted ? W.map0.as<int32_t>() : nullptr, H.n, W.side1.as<unsigned char>(), W.cur1.as<int32_t>(),
+             W.sideK.as<unsigned char>(), st, d_bits, s);
+  VC_CUDA(cudaMemcpyAsync(d_cut, &st->lambda_hat, sizeof(long long), cudaMemcpyDeviceToDevice, s));
+  W.span(kPhOther, a1);
+  cudaEvent_t t_end = W.mark();
+
+  // statistics
+  viecut_stats& S = H.stats;
+  memset(&S, 0, sizeof(S));
+  S.levels = levels;
+  if (W.timing) {
+    VC_CUDA(cudaEventSynchronize(t_end));
+    float ms;
+    VC_CUDA(cudaEventElapsedTime(&ms, t_start, t_end));
+    S.ms_total = ms;
+    double ph[kPhCount] = {0, 0, 0, 0, 0};
+    for (auto& sp : W.spans) {
+      VC_CUDA(cudaEventElapsedTime(&ms, sp.second.first, sp.second.second));
+      ph[sp.first] += ms;
+    }
+    S.ms_lp = ph[kPhLP];
+    S.ms_contract = ph[kPhContract];
+    S.ms_pr = ph[kPhPR];
+    S.ms_noi = ph[kPhNOI];
+    S.ms_other = ph[kPhOther];
+    for (auto& sp : W.lp_spans) {
+      VC_CUDA(cudaEventElapsedTime(&ms, sp.first, sp.second));
+      S.ms_lp_kernel += ms;
+    }
+    S.lp_launches = (int64_t)W.lp_spans.size();
+    S.lp_nnz = W.lp_nnz_acc;
+    S.lp_n = W.lp_n_acc;
+    S.lp_bytes = W.lp_bytes_acc;
+  }
+  S.kernel_launches = (int64_t)(g_launches - launches0);
+  (void)t_start;
+}
+
+static void fetch_trace(Handle& H) {
+  Workspace& W = *H.ws;
+  W.read_state();
+  int len = W.h_state->trace_len;
+  int cnt = std::min(len, W.trace_cap);
+  std::vector<TraceStep> t(cnt);
+  if (cnt) VC_CUDA(cudaMemcpy(t.data(), W.trace.p, sizeof(TraceStep) * cnt, cudaMemcpyDeviceToHost));
+  H.last_trace.resize(cnt);
+  for (int i = 0; i < cnt; ++i) {
+    H.last_trace[i].kind = t[i].kind;
+    H.last_trace[i].level = t[i].level;
+    H.last_trace[i].n = t[i].n;
+    H.last_trace[i].nnz = t[i].nnz;
+    H.last_trace[i].lambda_hat = t[i].lambda_hat;
+  }
+  H.stats.trace_len = len;
+}
+
+// ---------------------------------------------------------------- step graphs
+struct StepGraph {
+  int device = 0;
+  int64_t n = 0, nnz = 0;
+  Buf off, adj, w;
+  GraphView view() const {
+    GraphView g;
+    g.n = n;
+    g.nnz = nnz;
+    g.off = off.as<int64_t>();
+    g.adj = adj.as<int32_t>();
+    g.w = w.p;
+    g.wbytes = 8;
+    return g;
+  }
+};
+
+}  // namespace vc
+
+struct viecut_handle {
+  vc::Handle h;
+};
+struct viecut_graph {
+  vc::StepGraph g;
+};
+
+using vc::Error;
+
+#define VC_API_BEGIN try {
+#define VC_API_END                                   \
+  }                                                  \
+  catch (const vc::Error& e) {                       \
+    vc::t_last_error = e.msg;                        \
+    return e.code;                                   \
+  }                                                  \
+  catch (const std::bad_alloc&) {                    \
+    vc::t_last_error = "host allocation failed";     \
+    return VIECUT_ENOMEM;                            \
+  }                                                  \
+  return VIECUT_OK;
+
+extern "C" {
+
+const char* viecut_last_error(void) { return vc::t_last_error.c_str(); }
+int64_t viecut_launch_count(void) { return (int64_t)vc::g_launches; }
+
+int viecut_opts_init(viecut_opts* o) {
+  if (!o) return VIECUT_EINVAL;
+  memset(o, 0, sizeof(*o));
+  o->n0 = 10000;
+  o->pr_runs_max = 8;
+  o->device = 0;
+  o->stream = nullptr;
+  o->validate = 1;
+  o->timing = 0;
+  return VIECUT_OK;
+}
+
+static int create_common(viecut_t** out, int64_t n, int64_t m, const viecut_opts* opts, bool host_input,
+                         const int64_t* off, const int32_t* adj, const int32_t* w) {
+  VC_API_BEGIN
+  if (!out) throw Error{VIECUT_EINVAL, "null handle pointer"};
+  *out = nullptr;
+  if (n < 2) throw Error{VIECUT_EINVAL, "n must be >= 2"};
+  if (n > 0x7fffffffLL) throw Error{VIECUT_EINVAL, "n must fit int32 vertex ids"};
+  if (m < 0) throw Error{VIECUT_EINVAL, "m must be >= 0"};
+  if (!off || (m > 0 && (!adj || !w))) throw Error{VIECUT_EINVAL, "null graph array"};
+  viecut_opts o;
+  viecut_opts_init(&o);
+  if (opts) o = *opts;
+  if (o.n0 < 1) throw Error{VIECUT_EINVAL, "n0 must be >= 1"};
+  if (o.pr_runs_max < 0) throw Error{VIECUT_EINVAL, "pr_runs_max must be >= 0"};
+  if (host_input && o.validate >= 1) vc::host_validate(off, adj, w, n, m, o.validate >= 2);
+  auto* hh = new viecut_handle;
+  vc::Handle& H = hh->h;
+  try {
+    H.device = o.device;
+    VC_CUDA(cudaSetDevice(H.device));
+    if (o.stream) {
+      H.stream = (cudaStream_t)o.stream;
+    } else {
+      VC_CUDA(cudaStreamCreateWithFlags(&H.stream, cudaStreamNonBlocking));
+      H.own_stream = true;
+    }
+    H.n = n;
+    H.m = m;
+    H.n0 = o.n0;
+    H.pr_runs_max = o.pr_runs_max;
+    H.validate = o.validate;
+    H.ws = new vc::Workspace;
+    H.ws->s = H.stream;
+    H.ws->timing = o.timing != 0;
+    if (host_input) {
+      H.off0 = H.in_off.ensure_n<int64_t>(n + 1);
+      H.adj0 = H.in_adj.ensure_n<int32_t>(m);
+      H.w0 = H.in_w.ensure_n<int32_t>(m);
+      VC_CUDA(cudaMemcpyAsync((void*)H.off0, off, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, H.stream));
+      if (m > 0) {
+        VC_CUDA(cudaMemcpyAsync((void*)H.adj0, adj, sizeof(int32_t) * m, cudaMemcpyHostToDevice, H.stream));
+        VC_CUDA(cudaMemcpyAsync((void*)H.w0, w, sizeof(int32_t) * m, cudaMemcpyHostToDevice, H.stream));
+      }
+    } else {
+      H.off0 = off;
+      H.adj0 = adj;
+      H.w0 = w;
+    }
+    H.ws->ensure_vertices(n);
+    H.ws->ensure_entries(m, n);
+    H.out_cut.ensure_n<long long>(1);
+    H.out_bits.ensure_n<unsigned long long>((n + 63) / 64);
+    if (!host_input && o.validate >= 1) vc::device_validate(H);
+    VC_CUDA(cudaStreamSynchronize(H.stream));
+  } catch (...) {
+    delete hh;
+    throw;
+  }
+  *out = hh;
+  VC_API_END
+}
+
+int viecut_create(viecut_t** h, const int64_t* offsets, const int32_t* adj, int64_t n, int64_t m,
+                  const int32_t* weights, const viecut_opts* opts) {
+  return create_common(h, n, m, opts, true, offsets, adj, weights);
+}
+
+int viecut_create_device(viecut_t** h, const int64_t* d_offsets, const int32_t* d_adj, int64_t n, int64_t m,
+                         const int32_t* d_weights, const viecut_opts* opts) {
+  return create_common(h, n, m, opts, false, d_offsets, d_adj, d_weights);
+}
+
+int viecut_run_device(viecut_t* h, uint64_t seed, int32_t lp_iters, int64_t* d_cut_value, uint64_t* d_side_bits) {
+  VC_API_BEGIN
+  if (!h || !d_cut_value) throw Error{VIECUT_EINVAL, "null argument"};
+  VC_CUDA(cudaSetDevice(h->h.device));
+  unsigned long long* bits = d_side_bits ? (unsigned long long*)d_side_bits : h->h.out_bits.as<unsigned long long>();
+  vc::run_impl(h->h, seed, lp_iters, (long long*)d_cut_value, bits);
+  VC_API_END
+}
+
+int viecut_run(viecut_t* h, uint64_t seed, int32_t lp_iters, int64_t* cut_value, uint64_t* side_bits) {
+  VC_API_BEGIN
+  if (!h || !cut_value) throw Error{VIECUT_EINVAL, "null argument"};
+  vc::Handle& H = h->h;
+  VC_CUDA(cudaSetDevice(H.device));
+  vc::run_impl(H, seed, lp_iters, H.out_cut.as<long long>(), H.out_bits.as<unsigned long long>());
+  VC_CUDA(cudaMemcpyAsync(cut_value, H.out_cut.p, sizeof(int64_t), cudaMemcpyDeviceToHost, H.stream));
+  if (side_bits)
+    VC_CUDA(cudaMemcpyAsync(side_bits, H.out_bits.p, sizeof(uint64_t) * ((H.n + 63) / 64), cudaMemcpyDeviceToHost,
+                            H.stream));
+  VC_CUDA(cudaStreamSynchronize(H.stream));
+  VC_API_END
+}
+
+int viecut_get_stats(const viecut_t* h, viecut_stats* stats) {
+  VC_API_BEGIN
+  if (!h || !stats) throw Error{VIECUT_EINVAL, "null argument"};
+  *stats = h->h.stats;
+  VC_API_END
+}
+
+int viecut_get_trace(const viecut_t* h, viecut_step* steps, int64_t cap, int64_t* len) {
+  VC_API_BEGIN
+  if (!h || !len) throw Error{VIECUT_EINVAL, "null argument"};
+  vc::Handle& H = const_cast<viecut_t*>(h)->h;
+  VC_CUDA(cudaSetDevice(H.device));
+  vc::fetch_trace(H);
+  *len = (int64_t)H.last_trace.size();
+  for (int64_t i = 0; i < cap && i < *len; ++i) steps[i] = H.last_trace[i];
+  VC_API_END
+}
+
+int viecut_destroy(viecut_t* h) {
+  VC_API_BEGIN
+  if (!h) return VIECUT_OK;
+  cudaSetDevice(h->h.device);
+  if (h->h.stream) cudaStreamSynchronize(h->h.stream);
+  delete h;
+  VC_API_END
+}
+
+// ------------------------------------------------------------------ step API
+int viecut_graph_upload(viecut_graph** g, const int64_t* offsets, const int32_t* adj, const int64_t* weights,
+                        int64_t n, int64_t nnz, int32_t device) {
+  VC_API_BEGIN
+  if (!g || !offsets || n < 1 || nnz < 0) throw Error{VIECUT_EINVAL, "bad graph arguments"};
+  VC_CUDA(cudaSetDevice(device));
+  auto* x = new viecut_graph;
+  try {
+    x->g.device = device;
+    x->g.n = n;
+    x->g.nnz = nnz;
+    VC_CUDA(cudaMemcpy(x->g.off.ensure_n<int64_t>(n + 1), offsets, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
+    x->g.adj.ensure_n<int32_t>(nnz);
+    x->g.w.ensure_n<long long>(nnz);
+    if (nnz > 0) {
+      VC_CUDA(cudaMemcpy(x->g.adj.p, adj, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
+      VC_CUDA(cudaMemcpy(x->g.w.p, weights, sizeof(int64_t) * nnz, cudaMemcpyHostToDevice));
+    }
+  } catch (...) {
+    delete x;
+    throw;
+  }
+  *g = x;
+  VC_API_END
+}
+
+int viecut_graph_shape(const viecut_graph* g, int64_t* n, int64_t* nnz) {
+  VC_API_BEGIN
+  if (!g) throw Error{VIECUT_EINVAL, "null graph"};
+  if (n) *n = g->g.n;
+  if (nnz) *nnz = g->g.nnz;
+  VC_API_END
+}
+
+int viecut_graph_download(const viecut_graph* g, int64_t* offsets, int32_t* adj, int64_t* weights) {
+  VC_API_BEGIN
+  if (!g) throw Error{VIECUT_EINVAL, "null graph"};
+  VC_CUDA(cudaSetDevice(g->g.device));
+  VC_CUDA(cudaMemcpy(offsets, g->g.off.p, sizeof(int64_t) * (g->g.n + 1), cudaMemcpyDeviceToHost));
+  if (g->g.nnz > 0) {
+    VC_CUDA(cudaMemcpy(adj, g->g.adj.p, sizeof(int32_t) * g->g.nnz, cudaMemcpyDeviceToHost));
+    VC_CUDA(cudaMemcpy(weights, g->g.w.p, sizeof(int64_t) * g->g.nnz, cudaMemcpyDeviceToHost));
+  }
+  VC_API_END
+}
+
+int viecut_graph_free(viecut_graph* g) {
+  VC_API_BEGIN
+  if (g) {
+    cudaSetDevice(g->g.device);
+    delete g;
+  }
+  VC_API_END
+}
+
+namespace {
+struct StepCtx {
+  cudaStream_t s = nullptr;
+  vc::Workspace* ws = nullptr;
+  explicit StepCtx(const vc::StepGraph& g) {
+    VC_CUDA(cudaSetDevice(g.device));
+    VC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    ws = new vc::Workspace;
+    ws->s = s;
+    ws->ensure_vertices(g.n);
+    ws->ensure_entries(g.nnz, g.n);
+    VC_CUDA(cudaMemsetAsync(ws->state.p, 0, sizeof(vc::DevState), s));
+    VC_CUDA(cudaMemsetAsync(ws->counters.p, 0, sizeof(vc::Counters), s));
+  }
+  ~StepCtx() {
+    if (s) cudaStreamSynchronize(s);
+    delete ws;
+    if (s) cudaStreamDestroy(s);
+  }
+  void set_lambda(int64_t lam) {
+    vc::DevState st{};
+    st.lambda_hat = lam;
+    VC_CUDA(cudaMemcpyAsync(ws->state.p, &st, sizeof(st), cudaMemcpyHostToDevice, s));
+  }
+};
+}  // namespace
+
+int viecut_step_degrees(viecut_graph* g, int64_t* deg) {
+  VC_API_BEGIN
+  if (!g || !deg) throw Error{VIECUT_EINVAL, "null argument"};
+  StepCtx c(g->g);
+  vc::degrees(g->g.view(), c.ws->deg.as<long long>(), c.s);
+  VC_CUDA(cudaMemcpyAsync(deg, c.ws->deg.p, sizeof(int64_t) * g->g.n, cudaMemcpyDeviceToHost, c.s));
+  VC_CUDA(cudaStreamSynchronize(c.s));
+  VC_API_END
+}
+
+int viecut_step_lp(viecut_graph* g, const int32_t* lab_in, uint64_t key, int32_t rounds, int32_t* lab_out) {
+  VC_API_BEGIN
+  if (!g || !lab_out || rounds < 1) throw Error{VIECUT_EINVAL, "bad argument"};
+  StepCtx c(g->g);
+  vc::GraphView v = g->g.view();
+  c.ws->build_bins(v);
+  int32_t* in = nullptr;
+  if (lab_in) {
+    vc::Buf tmp;
+    in = tmp.ensure_n<int32_t>(v.n);
+    VC_CUDA(cudaMemcpyAsync(in, lab_in, sizeof(int32_t) * v.n, cudaMemcpyHostToDevice, c.s));
+    int32_t* bufs[2] = {c.ws->labA.as<int32_t>(), c.ws->labB.as<int32_t>()};
+    for (int r = 0; r < rounds; ++r) {
+      vc::lp_round(v, c.ws->bins, c.ws->gt, in, bufs[r & 1], key, c.s);
+      VC_CUDA(cudaMemcpyAsync(lab_out + (int64_t)r * v.n, bufs[r & 1], sizeof(int32_t) * v.n, cudaMemcpyDeviceToHost, c.s));
+      in = bufs[r & 1];
+    }
+    VC_CUDA(cudaStreamSynchronize(c.s));
+  } else {
+    int32_t* last;
+    c.ws->lp_rounds(v, key, rounds, &last, lab_out);
+    VC_CUDA(cudaStreamSynchronize(c.s));
+  }
+  VC_API_END
+}
+
+int viecut_step_contract(viecut_graph* g, const int32_t* labels, viecut_graph** out, int32_t* cid) {
+  VC_API_BEGIN
+  if (!g || !labels || !out) throw Error{VIECUT_EINVAL, "null argument"};
+  *out = nullptr;
+  StepCtx c(g->g);
+  vc::GraphView v = g->g.view();
+  int32_t* lab = c.ws->labA.as<int32_t>();
+  VC_CUDA(cudaMemcpyAsync(lab, labels, sizeof(int32_t) * v.n, cudaMemcpyHostToDevice, c.s));
+  int32_t* cidd = c.ws->map0.as<int32_t>();
+  vc::GraphView h = c.ws->contract(v, lab, cidd, 0);
+  c.ws->read_state();
+  const int64_t nnz = c.ws->h_state->nnz;
+  auto* x = new viecut_graph;
+  try {
+    x->g.device = g->g.device;
+    x->g.n = h.n;
+    x->g.nnz = nnz;
+    VC_CUDA(cudaMemcpyAsync(x->g.off.ensure_n<int64_t>(h.n + 1), h.off, sizeof(int64_t) * (h.n + 1),
+                            cudaMemcpyDeviceToDevice, c.s));
+    VC_CUDA(cudaMemcpyAsync(x->g.adj.ensure_n<int32_t>(nnz), h.adj, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, c.s));
+    VC_CUDA(cudaMemcpyAsync(x->g.w.ensure_n<long long>(nnz), h.w, sizeof(int64_t) * nnz, cudaMemcpyDeviceToDevice, c.s));
+    if (cid) VC_CUDA(cudaMemcpyAsync(cid, cidd, sizeof(int32_t) * v.n, cudaMemcpyDeviceToHost, c.s));
+    VC_CUDA(cudaStreamSynchronize(c.s));
+  } catch (...) {
+    delete x;
+    throw;
+  }
+  *out = x;
+  VC_API_END
+}
+
+static int step_labels(viecut_graph* g, int64_t lambda_hat, int32_t* labels, int32_t* changed, int which) {
+  VC_API_BEGIN
+  if (!g || !labels) throw Error{VIECUT_EINVAL, "null argument"};
+  StepCtx c(g->g);
+  vc::GraphView v = g->g.view();
+  vc::Workspace& W = *c.ws;
+  c.set_lambda(lambda_hat);
+  int* chg = &W.ctr()->changed;
+  VC_CUDA(cudaMemsetAsync(chg, 0, sizeof(int), c.s));
+  int32_t* lab = W.labA.as<int32_t>();
+  if (which == 0 || which == 1) {
+    vc::pr_partners(v, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), c.s);
+    if (which == 0)
+      vc::pr_pass_a(v, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), W.st(),
+                    W.parent.as<int32_t>(), lab, chg, c.s);
+    else
+      vc::pr_pass_b(v, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), W.st(), lab, chg, c.s);
+  } else {
+    W.noi_r.ensure_n<long long>(v.n);
+    W.noi_seen.ensure_n<unsigned char>(v.n);
+    vc::noi_round_sparse(v, W.st(), W.noi_r.as<long long>(), W.noi_seen.as<unsigned char>(), W.parent.as<int32_t>(),
+                         lab, chg, c.s);
+  }
+  W.read_state();
+  VC_CUDA(cudaMemcpy(labels, lab, sizeof(int32_t) * v.n, cudaMemcpyDeviceToHost));
+  if (changed) *changed = W.h_counters->changed;
+  VC_API_END
+}
+
+int viecut_step_pr_a(viecut_graph* g, int64_t lambda_hat, int32_t* labels, int32_t* changed) {
+  return step_labels(g, lambda_hat, labels, changed, 0);
+}
+int viecut_step_pr_b(viecut_graph* g, int64_t lambda_hat, int32_t* labels, int32_t* changed) {
+  return step_labels(g, lambda_hat, labels, changed, 1);
+}
+int viecut_step_noi_round(viecut_graph* g, int64_t lambda_hat, int32_t* labels, int32_t* changed) {
+  return step_labels(g, lambda_hat, labels, changed, 2);
+}
+
+}  // extern "C"

@@ -1,0 +1,289 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+All arithmetic is integer, so the bar is bit-exact: same labels after every
+label-propagation round, same contracted CSR, same Padberg-Rinaldi and
+Nagamochi-Ono-Ibaraki merges, same cut value, same side bitmap and the same trace of
+(n, nnz, lambda-hat) after every contraction step.
+"""
+import random
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+import paper_1708_06127_gb300 as vc
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+BIG_N0 = 1 << 40
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    vc.build()
+    vc.lib()
+
+
+def gpu_run(g, seed=1, lp=2, n0=10000, pr=8):
+    with vc.MinCut(g.offsets, g.adj, g.w, n0=n0, pr_runs_max=pr, validate=2) as mc:
+        cut, bits = mc.run(seed, lp)
+        trace = mc.trace()
+    return cut, bits, trace
+
+
+def assert_same(g, seed=1, lp=2, n0=10000, pr=8):
+    ref = oracle.viecut(g.offsets, g.adj, g.w, seed=seed, lp_iters=lp, n0=n0, pr_runs_max=pr)
+    cut, bits, trace = gpu_run(g, seed, lp, n0, pr)
+    assert trace == ref.trace, (g.name, seed, lp, n0)
+    assert cut == ref.cut, (g.name, seed, lp, n0)
+    assert np.array_equal(bits, ref.side_bits), (g.name, seed, lp, n0)
+    return ref
+
+
+def hub_graph(seed=5):
+    """ER background plus one vertex of degree 3000 (global-table class) and a few of
+    degree 200-1500 (block class); weights in [1, 9]."""
+    rnd = random.Random(seed)
+    n = 6000
+    base = gg.er(n, 6, seed, 1, 9)
+    E = {}
+    for v in range(n):
+        for e in range(base.offsets[v], base.offsets[v + 1]):
+            u = int(base.adj[e])
+            if v < u:
+                E[(v, u)] = int(base.w[e])
+    for hub, deg in [(0, 3000), (1, 1500), (2, 700), (3, 200)]:
+        for u in rnd.sample(range(4, n), deg):
+            E[(hub, u)] = rnd.randint(1, 9)
+    return gg.from_edges(n, [(a, b, w) for (a, b), w in E.items()], "hubs")
+
+
+def multi_edge_graph():
+    E = [(0, 1, 2), (0, 1, 3), (1, 2, 1), (2, 3, 4), (2, 3, 4), (3, 0, 1), (1, 3, 2), (0, 2, 1), (2, 0, 5)]
+    return gg.from_edges(4, E, "parallel-edges")
+
+
+# ------------------------------------------------------------------ step parity
+STEP_GRAPHS = {
+    "rhg14": lambda: gg.workload_rhg_small(1),
+    "rhg12w": lambda: gg.with_pair_weights(gg.core_lcc(gg.rhg(1 << 12, 20, 7), 0), 7, 1, 50),
+    "er_w100": lambda: gg.er(3000, 12, 3, 1, 100),
+    "hubs": hub_graph,
+}
+
+
+@pytest.fixture(scope="module")
+def step_graphs():
+    return {k: f() for k, f in STEP_GRAPHS.items()}
+
+
+def upload(G):
+    return vc.viecut_graph_upload(G.offsets, G.adj, G.w)
+
+
+@pytest.mark.parametrize("name", list(STEP_GRAPHS))
+def test_degrees_parity(step_graphs, name):
+    g = step_graphs[name]
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    d = upload(G)
+    try:
+        assert np.array_equal(vc.viecut_step_degrees(d), oracle.degrees(G))
+    finally:
+        vc.viecut_graph_free(d)
+
+
+@pytest.mark.parametrize("name", list(STEP_GRAPHS))
+def test_lp_rounds_parity(step_graphs, name):
+    g = step_graphs[name]
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    d = upload(G)
+    try:
+        for seed, level in [(1, 0), (77, 3)]:
+            key = oracle.level_key(seed, level)
+            got = vc.viecut_step_lp(d, None, key, 3)
+            lab = np.arange(G.n, dtype=np.int32)
+            for r in range(3):
+                lab = oracle.lp_round(G, lab, key)
+                assert np.array_equal(got[r], lab), (name, seed, r)
+        # from arbitrary labels (coarse clusters), as later rounds see them
+        rnd = np.random.default_rng(3)
+        lab0 = rnd.integers(0, max(2, G.n // 50), G.n).astype(np.int32)
+        key = oracle.level_key(5, 1)
+        got = vc.viecut_step_lp(d, lab0, key, 2)
+        l1 = oracle.lp_round(G, lab0, key)
+        assert np.array_equal(got[0], l1)
+        assert np.array_equal(got[1], oracle.lp_round(G, l1, key))
+    finally:
+        vc.viecut_graph_free(d)
+
+
+def compare_contract(G, labels):
+    d = upload(G)
+    out = None
+    try:
+        out, cid = vc.viecut_step_contract(d, labels)
+        off, adj, w = vc.viecut_graph_download(out)
+        ref, rcid = oracle.contract(G, labels)
+        assert np.array_equal(cid, rcid)
+        assert np.array_equal(off, ref.offsets)
+        assert np.array_equal(adj, ref.adj)
+        assert np.array_equal(w, ref.w)
+        return ref
+    finally:
+        vc.viecut_graph_free(d)
+        vc.viecut_graph_free(out)
+
+
+@pytest.mark.parametrize("name", list(STEP_GRAPHS))
+def test_contract_parity(step_graphs, name):
+    g = step_graphs[name]
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    rnd = np.random.default_rng(11)
+    # clusterings from label propagation, random with few / many clusters, identity
+    key = oracle.level_key(2, 0)
+    lp = oracle.lp_round(G, oracle.lp_round(G, np.arange(G.n, dtype=np.int32), key), key)
+    for labels in [lp, rnd.integers(0, 7, G.n), rnd.integers(0, G.n, G.n), np.arange(G.n),
+                   np.zeros(G.n, np.int64)]:
+        compare_contract(G, labels.astype(np.int32))
+
+
+def coarse_graphs():
+    out = []
+    for seed in range(4):
+        g = gg.with_pair_weights(gg.core_lcc(gg.rhg(1 << 11, 16, 40 + seed), 0), seed, 1, 5 + 10 * seed)
+        G = oracle.as_csr64(g.offsets, g.adj, g.w)
+        key = oracle.level_key(seed, 0)
+        lab = oracle.lp_round(G, np.arange(G.n, dtype=np.int32), key)
+        if seed % 2:
+            lab = oracle.lp_round(G, lab, key)
+        h, _ = oracle.contract(G, lab)
+        out.append(h)
+    for seed in range(6):
+        g = H.random_graph(random.Random(seed).randint(5, 40), 0.3, 900 + seed, wmax=6)
+        G = oracle.as_csr64(g.offsets, g.adj, g.w)
+        h, _ = oracle.contract(G, np.arange(G.n, dtype=np.int32))
+        out.append(h)
+    return out
+
+
+@pytest.mark.parametrize("which", ["a", "b", "noi"])
+def test_label_steps_parity(which):
+    for h in coarse_graphs():
+        dmin = int(oracle.degrees(h).min())
+        d = upload(h)
+        try:
+            for lam in [dmin, max(1, dmin // 2), 2 * dmin, 1 << 50]:
+                if which == "a":
+                    got, ch = vc.viecut_step_pr_a(d, lam)
+                    ref, cnt = oracle.pr_pass_a(h, lam)
+                elif which == "b":
+                    got, ch = vc.viecut_step_pr_b(d, lam)
+                    ref, cnt = oracle.pr_pass_b(h, lam)
+                else:
+                    if lam > dmin:
+                        continue  # a round needs lambda-hat <= min degree
+                    got, ch = vc.viecut_step_noi_round(d, lam)
+                    ref, cnt = oracle.noi_round(h, lam)
+                assert np.array_equal(got, ref), (which, h.n, lam)
+                assert ch == (1 if cnt > 0 else 0)
+        finally:
+            vc.viecut_graph_free(d)
+
+
+# ------------------------------------------------------------- whole method
+@pytest.mark.parametrize("seed", range(24))
+def test_viecut_random_small(seed):
+    rnd = random.Random(seed)
+    g = H.random_graph(rnd.randint(2, 60), rnd.uniform(0.05, 0.6), 300 + seed, wmax=rnd.choice([1, 4, 30]))
+    for lp, n0 in [(0, 1), (1, 2), (2, 1), (3, 8), (2, BIG_N0)]:
+        assert_same(g, seed=seed, lp=lp, n0=n0)
+
+
+@pytest.mark.parametrize("make", [
+    H.pr2_counterexample, lambda: H.two_cliques(7, 2), lambda: H.cycle(50), lambda: H.grid(9, 11),
+    lambda: H.hypercube(6), lambda: H.complete(20), multi_edge_graph,
+    lambda: gg.from_edges(2, [(0, 1, 5)]),
+    lambda: gg.from_edges(6, [(0, 1, 2), (1, 2, 2), (3, 4, 1), (4, 5, 1)]),   # disconnected
+    lambda: gg.from_edges(5, [(0, 1, 1), (1, 2, 1), (0, 2, 1)]),              # isolated vertices
+])
+def test_viecut_special_graphs(make):
+    g = make()
+    for lp, n0 in [(0, 1), (2, 1), (2, 4), (2, BIG_N0)]:
+        assert_same(g, lp=lp, n0=n0)
+
+
+@pytest.mark.parametrize("n0", [10000, 64, 1])
+@pytest.mark.parametrize("seed", [1, 2])
+def test_viecut_rhg_small_workload(seed, n0):
+    """RHG n = 2^14, average degree 32, exponent 5, largest component."""
+    g = gg.workload_rhg_small(seed)
+    assert_same(g, seed=seed, lp=2, n0=n0)
+
+
+def test_viecut_weighted_and_hubs():
+    assert_same(gg.with_pair_weights(gg.core_lcc(gg.rhg(1 << 13, 24, 9), 0), 9, 1, 10), seed=4, n0=32)
+    assert_same(hub_graph(), seed=2, n0=16)
+    assert_same(gg.er(3000, 12, 3, 1, 100), seed=3, n0=16)
+    assert_same(gg.planted(4, 1 << 10, 16, 8, 5, 1, 100), seed=5, n0=64)
+
+
+def test_viecut_sparse_exact_step():
+    """Kernels above the dense limit take the sparse exact-step rounds first."""
+    for seed in range(3):
+        g = H.random_graph(700 + 100 * seed, 0.02, 50 + seed, wmax=5)
+        assert_same(g, seed=seed, lp=2, n0=BIG_N0)
+    g = gg.core_lcc(gg.rhg(3000, 10, 4), 0)
+    assert_same(g, seed=1, lp=1, n0=2000)
+
+
+def test_viecut_repeatable_and_seeded():
+    g = gg.workload_rhg_small(3)
+    with vc.MinCut(g.offsets, g.adj, g.w, n0=64) as mc:
+        a = mc.run(5, 2)
+        b = mc.run(5, 2)
+        c = mc.run(6, 2)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    ref = oracle.viecut(g.offsets, g.adj, g.w, seed=6, lp_iters=2, n0=64)
+    assert c[0] == ref.cut and np.array_equal(c[1], ref.side_bits)
+
+
+def test_device_resident_inputs_and_errors():
+    import torch
+    g = gg.workload_rhg_small(1)
+    dev = torch.device("cuda:0")
+    off = torch.from_numpy(g.offsets).to(dev)
+    adj = torch.from_numpy(g.adj).to(dev)
+    w = torch.from_numpy(g.w).to(dev)
+    ref = oracle.viecut(g.offsets, g.adj, g.w, seed=1, lp_iters=2, n0=10000)
+    with vc.MinCut(off, adj, w, on_device=True) as mc:
+        cut, bits = mc.run(1, 2)
+        d_cut = torch.zeros(1, dtype=torch.int64, device=dev)
+        d_bits = torch.zeros((g.n + 63) // 64, dtype=torch.int64, device=dev)
+        vc.viecut_run_device(mc.h, 1, 2, d_cut, d_bits)
+        torch.cuda.synchronize()
+    assert cut == ref.cut and np.array_equal(bits, ref.side_bits)
+    assert int(d_cut.item()) == ref.cut
+    assert np.array_equal(d_bits.cpu().numpy().view(np.uint64), ref.side_bits)
+    # device-side validation catches a self-loop
+    bad = adj.clone()
+    bad[int(g.offsets[5])] = 5
+    with pytest.raises(vc.ViecutError) as e:
+        vc.MinCut(off, bad, w, on_device=True)
+    assert e.value.code == vc.VIECUT_EINVAL and "self-loop" in str(e.value)
+    with pytest.raises(vc.ViecutError):
+        with vc.MinCut(g.offsets, g.adj, g.w) as mc:
+            mc.run(1, -1)
+
+
+def test_launches_counted():
+    g = gg.workload_rhg_small(1)
+    with vc.MinCut(g.offsets, g.adj, g.w, timing=True) as mc:
+        before = vc.viecut_launch_count()
+        mc.run(1, 2)
+        st = mc.stats()
+    assert st["kernel_launches"] == vc.viecut_launch_count() - before > 10
+    assert st["lp_launches"] == 2 and st["ms_lp_kernel"] > 0
