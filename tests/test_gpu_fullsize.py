@@ -50,11 +50,29 @@ def test_rhg_2_22_core16():
     check(g, seed=1)
 
 
-def test_planted_8x2_20():
-    """8 ER blocks of 2^20 vertices (average degree 48), 64 bridges, weights [1, 100]."""
-    g = gg.workload_planted(1)
+def test_planted_8x2_16_exact():
+    """The planted family at 8 blocks of 2^16 vertices (the oracle needs about a
+    minute): exact parity."""
+    g = gg.planted(8, 1 << 16, 48, 64, 1, 1, 100)
     ref = check(g, seed=1)
+    assert ref.cut >= planted_lambda(g, 8, 1 << 16)
+
+
+def test_planted_8x2_20_properties():
+    """8 ER blocks of 2^20 vertices (average degree 48), 64 bridges, weights [1, 100].
+    At this size the oracle needs tens of minutes (label propagation on ER blocks
+    only halves the graph per level), so the GPU result is checked by properties that
+    hold at any size: the value is at least the construction's cut value and equals
+    the weight of the returned side, which is a proper subset without vertex 0."""
+    g = gg.workload_planted(1)
+    cut, bits, trace = bench_config_run(g, seed=1)
+    side = np.unpackbits(bits.view(np.uint8), bitorder="little")[: g.n].astype(bool)
+    assert side.any() and not side.all() and not side[0]
+    src = np.repeat(np.arange(g.n, dtype=np.int32), np.diff(g.offsets))
+    cross = side[src] != side[g.adj]
+    assert int(g.w[cross].astype(np.int64).sum()) // 2 == cut
     lam = planted_lambda(g, 8, 1 << 20)
-    assert ref.cut >= lam
-    # The paper finds VieCut optimal on its planted-cluster ER family; reported here:
-    print(f"planted: value {ref.cut}, construction {lam}")
+    assert cut >= lam
+    lh = [s[4] for s in trace]
+    assert all(a >= b for a, b in zip(lh, lh[1:])) and lh[-1] == cut
+    print(f"planted 8x2^20: value {cut}, construction {lam}, steps {len(trace)}")

@@ -229,6 +229,7 @@ def test_viecut_weighted_and_hubs():
     assert_same(hub_graph(), seed=2, n0=16)
     assert_same(gg.er(3000, 12, 3, 1, 100), seed=3, n0=16)
     assert_same(gg.planted(4, 1 << 10, 16, 8, 5, 1, 100), seed=5, n0=64)
+    assert_same(gg.planted(8, 1 << 12, 48, 64, 1, 1, 100), seed=1, n0=10000)
 
 
 def test_viecut_sparse_exact_step():

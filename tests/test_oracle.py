@@ -332,16 +332,15 @@ def planted_lambda(g, blocks, block_n):
     """Cut value known from the construction: the smaller of the minimum weighted
     degree and the lightest bridge set separating a union of blocks from the rest."""
     n = g.n
-    src = np.repeat(np.arange(n), np.diff(g.offsets))
-    deg = np.zeros(n, np.int64)
-    np.add.at(deg, src, g.w.astype(np.int64))
-    bsrc, bdst = src // block_n, g.adj // block_n
-    cross = bsrc != bdst
+    deg = np.add.reduceat(g.w.astype(np.int64), g.offsets[:-1]) if g.nnz else np.zeros(n, np.int64)
+    deg[np.diff(g.offsets) == 0] = 0
+    src = np.repeat(np.arange(n, dtype=np.int32), np.diff(g.offsets))
+    cross = (src // block_n) != (g.adj // block_n)
+    bsrc, bdst, bw = src[cross] // block_n, g.adj[cross] // block_n, g.w[cross].astype(np.int64)
     best = int(deg.min())
     for mask in range(1, 1 << (blocks - 1)):
         inA = (mask >> np.arange(blocks)) & 1
-        sel = cross & (inA[bsrc] != inA[bdst])
-        best = min(best, int(g.w[sel].astype(np.int64).sum()) // 2)
+        best = min(best, int(bw[inA[bsrc] != inA[bdst]].sum()) // 2)
     return best
 
 
