@@ -57,8 +57,9 @@ typedef struct viecut_opts {
   int32_t pr_runs_max; /* Padberg-Rinaldi runs per level (default 8) */
   int32_t device;      /* CUDA device ordinal (default 0) */
   void* stream;        /* cudaStream_t for all work; NULL = the library creates one */
-  int32_t validate;    /* 0 = trust input; 1 = range/loop/weight/offset checks (default);
-                          2 = also check symmetry on the host (create from host arrays only) */
+  int32_t validate;    /* 0 = trust input; 1 = range/loop/weight/offset checks, one pass on
+                          the device (default); 2 = the same checks plus symmetry, on the
+                          host (create from host arrays; O(m log m)) */
   int32_t timing;      /* 1 = record per-phase CUDA-event times (viecut_get_stats) */
 } viecut_opts;
 

@@ -19,7 +19,7 @@ __global__ void degrees_k(int64_t n, const int64_t* __restrict__ off, const WT* 
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
     long long s = 0;
-    for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32) s += (long long)w[e];
+    for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32) s += ldw(w, e);
     s = warp_sum(s);
     if (lane == 0) deg[v] = s;
   }
@@ -27,7 +27,8 @@ __global__ void degrees_k(int64_t n, const int64_t* __restrict__ off, const WT* 
 
 void degrees(const GraphView& g, long long* deg, cudaStream_t s) {
   int grid = grid_for(g.n, 8, kSMs * 16);
-  if (g.wbytes == 4) degrees_k<int32_t><<<grid, 256, 0, s>>>(g.n, g.off, (const int32_t*)g.w, deg);
+  if (g.unit) degrees_k<UnitW><<<grid, 256, 0, s>>>(g.n, g.off, nullptr, deg);
+  else if (g.wbytes == 4) degrees_k<int32_t><<<grid, 256, 0, s>>>(g.n, g.off, (const int32_t*)g.w, deg);
   else degrees_k<long long><<<grid, 256, 0, s>>>(g.n, g.off, (const long long*)g.w, deg);
   count_launch();
   VC_CHECK_LAUNCH();

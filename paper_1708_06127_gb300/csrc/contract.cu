@@ -31,20 +31,19 @@ void relabel(const int32_t* lab, int64_t n, int32_t* cid, ContractScratch& cs, i
   VC_CHECK_LAUNCH();
 }
 
-// One warp per fine vertex copies its pre-merged list into the pair arrays.
+// One thread per fine vertex copies its pre-merged list (two entries on average at the
+// level-0 contraction) into the contiguous pair arrays.
 __global__ void build_pairs_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ cid,
                               const int32_t* __restrict__ cnt, const long long* __restrict__ pos,
                               const int32_t* __restrict__ tkey, const long long* __restrict__ tval, int bits,
                               unsigned long long* __restrict__ keys, long long* __restrict__ vals) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int k = cnt[v];
     if (k == 0) continue;
     const int64_t src = off[v];
     const long long dst = pos[v];
     const unsigned long long hi = (unsigned long long)cid[v] << bits;
-    for (int j = lane; j < k; j += 32) {
+    for (int j = 0; j < k; ++j) {
       keys[dst + j] = hi | (unsigned long long)(uint32_t)tkey[src + j];
       vals[dst + j] = tval[src + j];
     }
@@ -53,7 +52,7 @@ __global__ void build_pairs_k(int64_t n, const int64_t* __restrict__ off, const 
 
 void build_pairs(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int bits,
                  unsigned long long* keys, long long* vals, cudaStream_t s) {
-  build_pairs_k<<<grid_for(g.n, 8, kSMs * 8), 256, 0, s>>>(g.n, g.off, cid, cs.cnt, cs.pos, cs.tmp_key,
+  build_pairs_k<<<grid_for(g.n, 256, kSMs * 8), 256, 0, s>>>(g.n, g.off, cid, cs.cnt, cs.pos, cs.tmp_key,
                                                            cs.tmp_val, bits, keys, vals);
   count_launch();
   VC_CHECK_LAUNCH();

@@ -5,29 +5,41 @@
 namespace vc {
 
 // A CSR graph on the device.  Weights are int32 (input graphs, wbytes = 4) or int64
-// (every contracted graph, wbytes = 8).
+// (every contracted graph, wbytes = 8).  unit = every weight is 1: the kernels that
+// support it (label propagation, pre-merge, degrees) then read no weights at all.
 struct GraphView {
   int64_t n = 0, nnz = 0;
   const int64_t* off = nullptr;
   const int32_t* adj = nullptr;
   const void* w = nullptr;
   int wbytes = 8;
+  bool unit = false;
 };
 
-// Degree classes of one graph: lists of vertices by neighbour-list length.
-//   warp class  : length <= kWarpMaxDeg  (every vertex not in a list below)
-//   block class : kWarpMaxDeg < length <= kBlockMaxDeg
-//   global class: length > kBlockMaxDeg (hash table in global scratch)
+// Weight loads for the three storage cases (UnitW: implicit weight 1).
+struct UnitW {};
+__device__ __forceinline__ long long ldw(const int32_t* w, int64_t e) { return (long long)__ldg(w + e); }
+__device__ __forceinline__ long long ldw(const long long* w, int64_t e) { return __ldg(w + e); }
+__device__ __forceinline__ long long ldw(const UnitW*, int64_t) { return 1; }
+
+// Degree classes of one graph by neighbour-list length (see lp.cu):
+//   small : length <= kWarpMaxDeg (every vertex not listed below)
+//   mid   : kWarpMaxDeg < length <= kMidMaxDeg
+//   block : kMidMaxDeg < length <= kBlockMaxDeg
+//   global: length > kBlockMaxDeg (hash table in global scratch)
 constexpr int kWarpMaxDeg = 128;
 constexpr int kWarpCap = 256;
-constexpr int kBlockMaxDeg = 2048;
-constexpr int kBlockCap = 4096;
+constexpr int kMidMaxDeg = 512;
+constexpr int kMidCap = 1024;
+constexpr int kBlockMaxDeg = 4096;
+constexpr int kBlockCap = 8192;
 
 struct Bins {
+  int32_t* mid_list;     // [n]
   int32_t* block_list;   // [n]
   int32_t* global_list;  // [n]
-  int* counts;           // device: [0] block count, [1] global count, [2] max length
-  int h_block = 0, h_global = 0, h_maxdeg = 0;  // host copies after bins_read
+  int* counts;           // device: [0] mid, [1] block, [2] global count, [3] max length
+  int h_mid = 0, h_block = 0, h_global = 0, h_maxdeg = 0;  // host copies
 };
 
 void bins_build(const GraphView& g, Bins& b, cudaStream_t s);

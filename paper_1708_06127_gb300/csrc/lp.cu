@@ -1,16 +1,23 @@
 // Label propagation rounds and the pre-merge of cross-cluster edges.
 //
 // Both reduce, for every vertex v, the multiset {(key(u), c(v,u)) : u in N(v)} to
-// per-key weight sums in an open-addressing table:
+// per-key weight sums:
 //   * label propagation (Sec. 4.1, "label propagation algorithm"): key = label of u,
 //     then v takes the key of largest sum, ties by the larger tie hash;
 //   * contraction pre-merge (Sec. 4.1, "contract it"): key = cluster id of u, keys
 //     equal to v's own cluster dropped (intra-cluster edges vanish), every remaining
 //     (key, sum) written out.
-// Work is split by neighbour-list length: a warp per vertex with a shared-memory
-// table for short lists, a block per vertex with a larger shared table, and a block
-// per vertex with a table in global scratch for the few very long lists.
+// A warp reads 32 neighbours at a time, groups the lanes holding equal keys with
+// __match_any_sync and lets one leader per group add the group's weight to an
+// open-addressing table (with unit weights the group weight is the group size).
+// Lists of at most 32 entries need no table at all.  Work is split by list length:
+//   small  (<= 128)  : a warp per vertex, 256-slot table in shared memory
+//   mid    (<= 512)  : a warp per listed vertex, 1024-slot table in shared memory
+//   block  (<= 4096) : a block per listed vertex, 8192-slot table in shared memory
+//   global (larger)  : a block per listed vertex, table in global scratch.
 #include <limits.h>
+
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -22,21 +29,23 @@ constexpr int kEmptyKey = -1;
 
 enum { kModeLP = 0, kModeEmit = 1 };
 
-__global__ void bins_k(int64_t n, const int64_t* __restrict__ off, int32_t* __restrict__ blist,
-                       int32_t* __restrict__ glist, int* __restrict__ counts) {
+__global__ void bins_k(int64_t n, const int64_t* __restrict__ off, int32_t* __restrict__ mlist,
+                       int32_t* __restrict__ blist, int32_t* __restrict__ glist, int* __restrict__ counts) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     int64_t d = off[v + 1] - off[v];
     if (d > kWarpMaxDeg) {
-      if (d <= kBlockMaxDeg) blist[atomicAdd(&counts[0], 1)] = (int32_t)v;
-      else glist[atomicAdd(&counts[1], 1)] = (int32_t)v;
-      atomicMax(&counts[2], (int)(d < INT_MAX ? d : INT_MAX));
+      if (d <= kMidMaxDeg) mlist[atomicAdd(&counts[0], 1)] = (int32_t)v;
+      else if (d <= kBlockMaxDeg) blist[atomicAdd(&counts[1], 1)] = (int32_t)v;
+      else glist[atomicAdd(&counts[2], 1)] = (int32_t)v;
+      atomicMax(&counts[3], (int)(d < INT_MAX ? d : INT_MAX));
     }
   }
 }
 
 void bins_build(const GraphView& g, Bins& b, cudaStream_t s) {
-  VC_CUDA(cudaMemsetAsync(b.counts, 0, 3 * sizeof(int), s));
-  bins_k<<<grid_for(g.n, 256, kSMs * 8), 256, 0, s>>>(g.n, g.off, b.block_list, b.global_list, b.counts);
+  VC_CUDA(cudaMemsetAsync(b.counts, 0, 4 * sizeof(int), s));
+  bins_k<<<grid_for(g.n, 256, kSMs * 8), 256, 0, s>>>(g.n, g.off, b.mid_list, b.block_list, b.global_list,
+                                                       b.counts);
   count_launch();
   VC_CHECK_LAUNCH();
 }
@@ -47,23 +56,21 @@ int64_t global_table_cap(int maxdeg) {
   return c < 64 ? 64 : c;
 }
 
-// Adds wt to the slot of key k (linear probing; capacity >= 2 x distinct keys).
-__device__ __forceinline__ void tbl_add(int* tk, unsigned long long* tv, int lg, int k, long long wt) {
+// Adds wt to the slot of key k (linear probing; capacity >= 2 x distinct keys, so a
+// free slot always exists and the loop ends within one pass over the table).
+template <typename ACC>
+__device__ __forceinline__ void tbl_add(int* tk, ACC* tv, int lg, int k, long long wt) {
   const uint32_t mask = (1u << lg) - 1u;
   uint32_t h = slot_hash(k, lg);
-  // at most one probe per slot: the table always has room (capacity >= 2 x keys)
   for (uint32_t probe = 0; probe <= mask; ++probe) {
     int prev = atomicCAS(&tk[h], kEmptyKey, k);
     if (prev == kEmptyKey || prev == k) {
-      atomicAdd(&tv[h], (unsigned long long)wt);
+      atomicAdd(&tv[h], (ACC)wt);
       return;
     }
     h = (h + 1) & mask;
   }
 }
-
-template <typename WT>
-__device__ __forceinline__ long long ldw(const WT* w, int64_t e) { return (long long)__ldg(w + e); }
 
 // key of neighbour u for vertex v; returns false when the entry is skipped
 template <int MODE, bool FIRST>
@@ -77,24 +84,91 @@ __device__ __forceinline__ bool entry_key(const int32_t* __restrict__ lab, int32
   }
 }
 
-// ------------------------------------------------------------------ warp class
+// One chunk of up to 32 entries: every lane learns its key, whether it is used, and
+// (on group leaders) the summed weight of the lanes sharing the key.
+struct Chunk {
+  int32_t k;
+  bool use, leader;
+  long long sum;
+};
+
 template <typename WT, int MODE, bool FIRST>
+__device__ __forceinline__ Chunk load_chunk(int64_t e, int64_t end, const int32_t* __restrict__ adj,
+                                            const WT* __restrict__ w, const int32_t* __restrict__ lab, int32_t own,
+                                            long long* sw, int lane) {
+  Chunk c;
+  c.k = 0;
+  c.use = false;
+  long long wt = 0;
+  if (e < end) {
+    c.use = entry_key<MODE, FIRST>(lab, __ldg(adj + e), own, &c.k);
+    wt = ldw(w, e);
+  }
+  // unused lanes get a unique negative key so they form singleton groups
+  const int32_t km = c.use ? c.k : (-2 - lane);
+  const unsigned peers = __match_any_sync(0xffffffffu, km);
+  c.leader = c.use && (__ffs(peers) - 1) == lane;
+  if (std::is_same<WT, UnitW>::value) {
+    c.sum = __popc(peers);
+  } else {
+    sw[lane] = wt;
+    __syncwarp();
+    long long s = 0;
+    if (c.leader)
+      for (unsigned m = peers; m; m &= m - 1) s += sw[__ffs(m) - 1];
+    __syncwarp();
+    c.sum = s;
+  }
+  return c;
+}
+
+// Per-lane running best over (sum, hash, -label); the hash is computed only on ties.
+struct LaneBest {
+  long long s = -1;
+  int l = INT_MAX;
+  unsigned long long h = 0;
+  bool hashed = false;
+  __device__ __forceinline__ void add(long long sum, int L, uint64_t key) {
+    if (sum > s) {
+      s = sum;
+      l = L;
+      hashed = false;
+    } else if (sum == s) {
+      if (!hashed) { h = tie_hash(key, l); hashed = true; }
+      unsigned long long hl = tie_hash(key, L);
+      if (hl > h || (hl == h && L < l)) { l = L; h = hl; }
+    }
+  }
+  __device__ __forceinline__ Cand done(uint64_t key) {
+    if (!hashed && s >= 0) h = tie_hash(key, l);
+    return Cand{s, h, l};
+  }
+};
+
+// ------------------------------------------------------------------ warp classes
+// LISTED = false: every vertex of list length <= CAP/2 (grid-stride over all vertices);
+// LISTED = true : the listed vertices (count on the device).
+template <typename WT, typename ACC, int MODE, bool FIRST, int CAP, bool LISTED>
 __global__ void __launch_bounds__(kAggThreads) agg_warp_k(
-    int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj, const WT* __restrict__ w,
+    int64_t n, const int32_t* __restrict__ list, const int* __restrict__ count_ptr,
+    const int64_t* __restrict__ off, const int32_t* __restrict__ adj, const WT* __restrict__ w,
     const int32_t* __restrict__ lab, int32_t* __restrict__ lab_out, uint64_t key,
     int32_t* __restrict__ tkey, long long* __restrict__ tval, int32_t* __restrict__ cnt) {
-  __shared__ int s_keys[kWarpsPerBlock][kWarpCap];
-  __shared__ unsigned long long s_vals[kWarpsPerBlock][kWarpCap];
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ long long s_w[kWarpsPerBlock][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  int* tk = s_keys[wib];
-  unsigned long long* tv = s_vals[wib];
-  for (int i = lane; i < kWarpCap; i += 32) { tk[i] = kEmptyKey; tv[i] = 0ULL; }
+  ACC* tv = (ACC*)dyn + (size_t)wib * CAP;
+  int* tk = (int*)((ACC*)dyn + (size_t)kWarpsPerBlock * CAP) + (size_t)wib * CAP;
+  long long* sw = s_w[wib];
+  for (int i = lane; i < CAP; i += 32) { tk[i] = kEmptyKey; tv[i] = 0; }
   __syncwarp();
+  const int64_t total = LISTED ? (int64_t)*count_ptr : n;
   const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock;
-  for (int64_t v = (int64_t)blockIdx.x * kWarpsPerBlock + wib; v < n; v += stride) {
+  for (int64_t idx = (int64_t)blockIdx.x * kWarpsPerBlock + wib; idx < total; idx += stride) {
+    const int64_t v = LISTED ? (int64_t)list[idx] : idx;
     const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
     const int d = (int)(end - beg);
-    if (d > kWarpMaxDeg) continue;
+    if (!LISTED && d > CAP / 2) continue;
     const int32_t own = (MODE == kModeEmit) ? __ldg(lab + v) : 0;
     if (d == 0) {
       if (lane == 0) {
@@ -103,53 +177,69 @@ __global__ void __launch_bounds__(kAggThreads) agg_warp_k(
       }
       continue;
     }
-    int lg = ceil_log2(2 * (int64_t)d);
-    if (lg < 5) lg = 5;
+    if (d <= 32) {
+      // one chunk: the group sums are final, no table needed
+      Chunk c = load_chunk<WT, MODE, FIRST>(beg + lane, end, adj, w, lab, own, sw, lane);
+      if (MODE == kModeLP) {
+        Cand cd = c.leader ? Cand{c.sum, tie_hash(key, c.k), c.k} : Cand{-1LL, 0ULL, INT_MAX};
+        cd = warp_best(cd);
+        if (lane == 0) lab_out[v] = cd.l;
+      } else {
+        unsigned bal = __ballot_sync(0xffffffffu, c.leader);
+        if (c.leader) {
+          int j = __popc(bal & ((1u << lane) - 1u));
+          tkey[beg + j] = c.k;
+          tval[beg + j] = c.sum;
+        }
+        if (lane == 0) cnt[v] = __popc(bal);
+      }
+      continue;
+    }
+    const int lg = ceil_log2(2 * (int64_t)d);
     const int cap = 1 << lg;
-    for (int64_t e = beg + lane; e < end; e += 32) {
-      int32_t k;
-      if (entry_key<MODE, FIRST>(lab, __ldg(adj + e), own, &k)) tbl_add(tk, tv, lg, k, ldw(w, e));
+    for (int64_t base = beg; base < end; base += 32) {
+      Chunk c = load_chunk<WT, MODE, FIRST>(base + lane, end, adj, w, lab, own, sw, lane);
+      if (c.leader) tbl_add<ACC>(tk, tv, lg, c.k, c.sum);
     }
     __syncwarp();
     if (MODE == kModeLP) {
-      Cand best{-1LL, 0ULL, INT_MAX};
+      LaneBest lb;
       for (int i = lane; i < cap; i += 32) {
-        int L = tk[i];
+        const int L = tk[i];
         if (L != kEmptyKey) {
-          Cand c{(long long)tv[i], tie_hash(key, L), L};
-          if (better(c, best)) best = c;
+          lb.add((long long)tv[i], L, key);
           tk[i] = kEmptyKey;
-          tv[i] = 0ULL;
+          tv[i] = 0;
         }
       }
-      best = warp_best(best);
-      if (lane == 0) lab_out[v] = best.l;
+      Cand cd = warp_best(lb.done(key));
+      if (lane == 0) lab_out[v] = cd.l;
     } else {
-      int base = 0;
+      int basej = 0;
       for (int i0 = 0; i0 < cap; i0 += 32) {
-        int i = i0 + lane;
-        int L = tk[i];
-        bool occ = L != kEmptyKey;
-        unsigned bal = __ballot_sync(0xffffffffu, occ);
+        const int i = i0 + lane;
+        const int L = tk[i];
+        const bool occ = L != kEmptyKey;
+        const unsigned bal = __ballot_sync(0xffffffffu, occ);
         if (occ) {
-          int j = base + __popc(bal & ((1u << lane) - 1u));
+          const int j = basej + __popc(bal & ((1u << lane) - 1u));
           tkey[beg + j] = L;
           tval[beg + j] = (long long)tv[i];
           tk[i] = kEmptyKey;
-          tv[i] = 0ULL;
+          tv[i] = 0;
         }
-        base += __popc(bal);
+        basej += __popc(bal);
       }
-      if (lane == 0) cnt[v] = base;
+      if (lane == 0) cnt[v] = basej;
     }
     __syncwarp();
   }
 }
 
-// --------------------------------------------------------- block / global class
-// One block per listed vertex; the table is in shared memory (global == false) or
-// in this block's region of global scratch (global == true).
-template <typename WT, int MODE, bool FIRST, bool GLOBAL>
+// --------------------------------------------------------- block / global classes
+// One block per listed vertex; the table lives in shared memory (GLOBAL = false) or
+// in this block's region of global scratch (GLOBAL = true).
+template <typename WT, typename ACC, int MODE, bool FIRST, bool GLOBAL>
 __global__ void __launch_bounds__(kAggThreads) agg_block_k(
     const int32_t* __restrict__ list, const int* __restrict__ count_ptr, const int64_t* __restrict__ off,
     const int32_t* __restrict__ adj, const WT* __restrict__ w, const int32_t* __restrict__ lab,
@@ -157,21 +247,23 @@ __global__ void __launch_bounds__(kAggThreads) agg_block_k(
     int32_t* __restrict__ cnt, int32_t* __restrict__ gkeys, long long* __restrict__ gvals, int64_t gcap) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ Cand s_best[kWarpsPerBlock];
+  __shared__ long long s_w[kWarpsPerBlock][32];
   __shared__ int s_count;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int* tk;
-  unsigned long long* tv;
+  ACC* tv;
   int64_t table_cap;
   if (GLOBAL) {
     tk = gkeys + (int64_t)blockIdx.x * gcap;
-    tv = (unsigned long long*)gvals + (int64_t)blockIdx.x * gcap;
+    tv = (ACC*)gvals + (int64_t)blockIdx.x * gcap;
     table_cap = gcap;
   } else {
-    tv = (unsigned long long*)dyn;
-    tk = (int*)(dyn + sizeof(unsigned long long) * kBlockCap);
+    tv = (ACC*)dyn;
+    tk = (int*)((ACC*)dyn + kBlockCap);
     table_cap = kBlockCap;
   }
-  for (int64_t i = threadIdx.x; i < table_cap; i += kAggThreads) { tk[i] = kEmptyKey; tv[i] = 0ULL; }
+  long long* sw = s_w[wib];
+  for (int64_t i = threadIdx.x; i < table_cap; i += kAggThreads) { tk[i] = kEmptyKey; tv[i] = 0; }
   __syncthreads();
   const int count = *count_ptr;
   for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
@@ -179,28 +271,26 @@ __global__ void __launch_bounds__(kAggThreads) agg_block_k(
     const int64_t beg = off[v], end = off[v + 1];
     const int64_t d = end - beg;
     const int32_t own = (MODE == kModeEmit) ? lab[v] : 0;
-    int lg = ceil_log2(2 * d);
-    if (lg < 5) lg = 5;
+    const int lg = ceil_log2(2 * d);
     const int64_t cap = (int64_t)1 << lg;
-    for (int64_t e = beg + threadIdx.x; e < end; e += kAggThreads) {
-      int32_t k;
-      if (entry_key<MODE, FIRST>(lab, adj[e], own, &k)) tbl_add(tk, tv, lg, k, ldw(w, e));
+    for (int64_t base = beg + 32 * wib; base < end; base += 32 * kWarpsPerBlock) {
+      Chunk c = load_chunk<WT, MODE, FIRST>(base + lane, end, adj, w, lab, own, sw, lane);
+      if (c.leader) tbl_add<ACC>(tk, tv, lg, c.k, c.sum);
     }
     if (MODE == kModeEmit && threadIdx.x == 0) s_count = 0;
     __syncthreads();
     if (MODE == kModeLP) {
-      Cand best{-1LL, 0ULL, INT_MAX};
+      LaneBest lb;
       for (int64_t i = threadIdx.x; i < cap; i += kAggThreads) {
-        int L = tk[i];
+        const int L = tk[i];
         if (L != kEmptyKey) {
-          Cand c{(long long)tv[i], tie_hash(key, L), L};
-          if (better(c, best)) best = c;
+          lb.add((long long)tv[i], L, key);
           tk[i] = kEmptyKey;
-          tv[i] = 0ULL;
+          tv[i] = 0;
         }
       }
-      best = warp_best(best);
-      if (lane == 0) s_best[wib] = best;
+      Cand cd = warp_best(lb.done(key));
+      if (lane == 0) s_best[wib] = cd;
       __syncthreads();
       if (threadIdx.x == 0) {
         Cand b = s_best[0];
@@ -210,13 +300,13 @@ __global__ void __launch_bounds__(kAggThreads) agg_block_k(
       }
     } else {
       for (int64_t i = threadIdx.x; i < cap; i += kAggThreads) {
-        int L = tk[i];
+        const int L = tk[i];
         if (L != kEmptyKey) {
-          int j = atomicAdd(&s_count, 1);
+          const int j = atomicAdd(&s_count, 1);
           tkey[beg + j] = L;
           tval[beg + j] = (long long)tv[i];
           tk[i] = kEmptyKey;
-          tv[i] = 0ULL;
+          tv[i] = 0;
         }
       }
       __syncthreads();
@@ -226,58 +316,84 @@ __global__ void __launch_bounds__(kAggThreads) agg_block_k(
   }
 }
 
-constexpr size_t kBlockDynSmem = (sizeof(unsigned long long) + sizeof(int)) * kBlockCap;
+template <typename F>
+void set_smem(F kfn, size_t bytes) {
+  // once per kernel instantiation (single device per process)
+  static bool done = false;
+  if (!done) {
+    VC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    done = true;
+  }
+}
 
-template <typename WT, int MODE, bool FIRST>
+template <typename WT, typename ACC, int MODE, bool FIRST>
 void launch_agg(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* lab,
                 int32_t* lab_out, uint64_t key, int32_t* tkey, long long* tval, int32_t* cnt, cudaStream_t s) {
   const WT* w = (const WT*)g.w;
-  // residency: 8 warps x 3 KB of tables per block
-  int grid = grid_for(g.n, kWarpsPerBlock * 4, kSMs * 8);
-  agg_warp_k<WT, MODE, FIRST><<<grid, kAggThreads, 0, s>>>(g.n, g.off, g.adj, w, lab, lab_out, key, tkey, tval, cnt);
-  count_launch();
-  VC_CHECK_LAUNCH();
+  {
+    constexpr int CAP = kWarpCap;
+    const size_t smem = (size_t)kWarpsPerBlock * CAP * (sizeof(ACC) + sizeof(int));
+    auto kfn = agg_warp_k<WT, ACC, MODE, FIRST, CAP, false>;
+    set_smem(kfn, smem);
+    kfn<<<grid_for(g.n, kWarpsPerBlock * 4, kSMs * 8), kAggThreads, smem, s>>>(
+        g.n, nullptr, nullptr, g.off, g.adj, w, lab, lab_out, key, tkey, tval, cnt);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
+  if (b.h_mid > 0) {
+    constexpr int CAP = kMidCap;
+    const size_t smem = (size_t)kWarpsPerBlock * CAP * (sizeof(ACC) + sizeof(int));
+    auto kfn = agg_warp_k<WT, ACC, MODE, FIRST, CAP, true>;
+    set_smem(kfn, smem);
+    kfn<<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 2), kAggThreads, smem, s>>>(
+        0, b.mid_list, b.counts + 0, g.off, g.adj, w, lab, lab_out, key, tkey, tval, cnt);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
   if (b.h_block > 0) {
-    static bool attr_set = false;
-    auto kfn = agg_block_k<WT, MODE, FIRST, false>;
-    if (!attr_set) {
-      VC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlockDynSmem));
-      attr_set = true;
-    }
-    kfn<<<grid_for(b.h_block, 1, kSMs * 4), kAggThreads, kBlockDynSmem, s>>>(
-        b.block_list, b.counts + 0, g.off, g.adj, w, lab, lab_out, key, tkey, tval, cnt, nullptr, nullptr, 0);
+    const size_t smem = (size_t)kBlockCap * (sizeof(ACC) + sizeof(int));
+    auto kfn = agg_block_k<WT, ACC, MODE, FIRST, false>;
+    set_smem(kfn, smem);
+    kfn<<<grid_for(b.h_block, 1, kSMs * 2), kAggThreads, smem, s>>>(
+        b.block_list, b.counts + 1, g.off, g.adj, w, lab, lab_out, key, tkey, tval, cnt, nullptr, nullptr, 0);
     count_launch();
     VC_CHECK_LAUNCH();
   }
   if (b.h_global > 0) {
     int grid_g = b.h_global < gt.blocks ? b.h_global : gt.blocks;
-    agg_block_k<WT, MODE, FIRST, true><<<grid_g, kAggThreads, 0, s>>>(
-        b.global_list, b.counts + 1, g.off, g.adj, w, lab, lab_out, key, tkey, tval, cnt, gt.keys, gt.vals, gt.cap);
+    agg_block_k<WT, ACC, MODE, FIRST, true><<<grid_g, kAggThreads, 0, s>>>(
+        b.global_list, b.counts + 2, g.off, g.adj, w, lab, lab_out, key, tkey, tval, cnt, gt.keys, gt.vals, gt.cap);
     count_launch();
     VC_CHECK_LAUNCH();
   }
 }
 
+// Unit weights accumulate in 32 bits (a sum never exceeds the list length); stored
+// weights accumulate in 64 bits.
+template <int MODE, bool FIRST>
+void dispatch_agg(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* lab,
+                  int32_t* lab_out, uint64_t key, int32_t* tkey, long long* tval, int32_t* cnt, cudaStream_t s) {
+  if (g.unit)
+    launch_agg<UnitW, unsigned int, MODE, FIRST>(g, b, gt, lab, lab_out, key, tkey, tval, cnt, s);
+  else if (g.wbytes == 4)
+    launch_agg<int32_t, unsigned long long, MODE, FIRST>(g, b, gt, lab, lab_out, key, tkey, tval, cnt, s);
+  else
+    launch_agg<long long, unsigned long long, MODE, FIRST>(g, b, gt, lab, lab_out, key, tkey, tval, cnt, s);
+}
+
 void lp_round(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* lab_in,
               int32_t* lab_out, uint64_t key, cudaStream_t s) {
   if (g.n <= 0) return;
-  bool first = lab_in == nullptr;
-  if (g.wbytes == 4) {
-    if (first) launch_agg<int32_t, kModeLP, true>(g, b, gt, nullptr, lab_out, key, nullptr, nullptr, nullptr, s);
-    else launch_agg<int32_t, kModeLP, false>(g, b, gt, lab_in, lab_out, key, nullptr, nullptr, nullptr, s);
-  } else {
-    if (first) launch_agg<long long, kModeLP, true>(g, b, gt, nullptr, lab_out, key, nullptr, nullptr, nullptr, s);
-    else launch_agg<long long, kModeLP, false>(g, b, gt, lab_in, lab_out, key, nullptr, nullptr, nullptr, s);
-  }
+  if (lab_in == nullptr)
+    dispatch_agg<kModeLP, true>(g, b, gt, nullptr, lab_out, key, nullptr, nullptr, nullptr, s);
+  else
+    dispatch_agg<kModeLP, false>(g, b, gt, lab_in, lab_out, key, nullptr, nullptr, nullptr, s);
 }
 
 void emit_cross(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* cid,
                 int32_t* tmp_key, long long* tmp_val, int32_t* cnt, cudaStream_t s) {
   if (g.n <= 0) return;
-  if (g.wbytes == 4)
-    launch_agg<int32_t, kModeEmit, false>(g, b, gt, cid, nullptr, 0, tmp_key, tmp_val, cnt, s);
-  else
-    launch_agg<long long, kModeEmit, false>(g, b, gt, cid, nullptr, 0, tmp_key, tmp_val, cnt, s);
+  dispatch_agg<kModeEmit, false>(g, b, gt, cid, nullptr, 0, tmp_key, tmp_val, cnt, s);
 }
 
 }  // namespace vc

@@ -70,7 +70,7 @@ struct Workspace {
   cudaStream_t s = nullptr;
   // vertex-sized
   Buf deg, labA, labB, map0, cidT, cur1, side1, flags, rank, cnt, pos, scan64, scan32;
-  Buf partner, pw, parent, blist, glist, bcounts, noi_r, noi_seen;
+  Buf partner, pw, parent, mlist, blist, glist, bcounts, noi_r, noi_seen;
   // entry-sized
   Buf tmpK, tmpV;
   // pair-sized
@@ -102,7 +102,7 @@ struct Workspace {
     trace.ensure_n<TraceStep>(trace_cap);
     partial.ensure_n<long long>(2 * 1024);
     counters.ensure(sizeof(Counters));
-    bcounts.ensure_n<int>(4);
+    bcounts.ensure_n<int>(8);
   }
   ~Workspace() {
     if (h_state) cudaFreeHost(h_state);
@@ -127,6 +127,7 @@ struct Workspace {
     partner.ensure_n<int32_t>(n);
     pw.ensure_n<long long>(n);
     parent.ensure_n<int32_t>(n);
+    mlist.ensure_n<int32_t>(n);
     blist.ensure_n<int32_t>(n);
     glist.ensure_n<int32_t>(n);
     scan32.ensure_n<int>(scan_scratch_elems(n) + 1);
@@ -181,16 +182,18 @@ struct Workspace {
   bool bins_valid = false;
 
   void build_bins(const GraphView& g) {
+    bins.mid_list = mlist.as<int32_t>();
     bins.block_list = blist.as<int32_t>();
     bins.global_list = glist.as<int32_t>();
     bins.counts = bcounts.as<int>();
     bins_build(g, bins, s);
-    int hc[3];
-    VC_CUDA(cudaMemcpyAsync(hc, bins.counts, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    int hc[4];
+    VC_CUDA(cudaMemcpyAsync(hc, bins.counts, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
     sync();
-    bins.h_block = hc[0];
-    bins.h_global = hc[1];
-    bins.h_maxdeg = hc[2];
+    bins.h_mid = hc[0];
+    bins.h_block = hc[1];
+    bins.h_global = hc[2];
+    bins.h_maxdeg = hc[3];
     if (bins.h_global > 0) {
       int64_t cap = global_table_cap(bins.h_maxdeg);
       int blocks = std::min(bins.h_global, kSMs);
@@ -214,7 +217,7 @@ struct Workspace {
       if (timing) {
         lp_spans.push_back({a, mark()});
         long long gather = in ? 4 : 0;
-        lp_bytes_acc += 8 * (g.n + 1) + g.nnz * (4 + g.wbytes + gather) + 4 * g.n;
+        lp_bytes_acc += 8 * (g.n + 1) + g.nnz * (4 + (g.unit ? 0 : g.wbytes) + gather) + 4 * g.n;
         lp_nnz_acc += g.nnz;
         lp_n_acc += g.n;
       }
@@ -295,6 +298,7 @@ __global__ void validate_k(int64_t n, int64_t m, const int64_t* __restrict__ off
       if (u < 0 || u >= n) bad |= 4;
       else if (u == v) bad |= 8;
       if (w[e] < 1) bad |= 16;
+      if (w[e] != 1) bad |= 32;  // not an error: the weights are not all 1
     }
   }
   if (bad) atomicOr(err, bad);
@@ -308,6 +312,7 @@ struct Handle {
   int64_t n0 = 10000;
   int pr_runs_max = 8;
   int validate = 1;
+  bool unit = false;  // every input weight is 1 (found by validation)
   const int64_t* off0 = nullptr;
   const int32_t* adj0 = nullptr;
   const int32_t* w0 = nullptr;
@@ -330,6 +335,8 @@ static void device_validate(Handle& H) {
   VC_CHECK_LAUNCH();
   W.read_state();
   int bad = W.h_counters->changed;
+  H.unit = (bad & 32) == 0;
+  bad &= ~32;
   if (bad) {
     std::string why;
     if (bad & 1) why += " offsets[0] != 0 or offsets[n] != m;";
@@ -341,8 +348,10 @@ static void device_validate(Handle& H) {
   }
 }
 
-static void host_validate(const int64_t* off, const int32_t* adj, const int32_t* w, int64_t n, int64_t m,
+// Returns true when every weight is 1.
+static bool host_validate(const int64_t* off, const int32_t* adj, const int32_t* w, int64_t n, int64_t m,
                           bool symmetric) {
+  bool unit = true;
   if (off[0] != 0 || off[n] != m) throw Error{VIECUT_EINVAL, "invalid graph: offsets[0] != 0 or offsets[n] != m"};
   for (int64_t v = 0; v < n; ++v) {
     if (off[v + 1] < off[v]) throw Error{VIECUT_EINVAL, "invalid graph: offsets decrease at vertex " + std::to_string(v)};
@@ -350,9 +359,10 @@ static void host_validate(const int64_t* off, const int32_t* adj, const int32_t*
       if (adj[e] < 0 || adj[e] >= n) throw Error{VIECUT_EINVAL, "invalid graph: neighbour id out of range"};
       if (adj[e] == v) throw Error{VIECUT_EINVAL, "invalid graph: self-loop at vertex " + std::to_string(v)};
       if (w[e] < 1) throw Error{VIECUT_EINVAL, "invalid graph: weight < 1"};
+      unit = unit && w[e] == 1;
     }
   }
-  if (!symmetric) return;
+  if (!symmetric) return unit;
   struct E { int64_t a, b; int32_t w; };
   std::vector<E> fwd, bwd;
   fwd.reserve(m);
@@ -368,6 +378,7 @@ static void host_validate(const int64_t* off, const int32_t* adj, const int32_t*
   for (int64_t i = 0; i < m; ++i)
     if (fwd[i].a != bwd[i].a || fwd[i].b != bwd[i].b || fwd[i].w != bwd[i].w)
       throw Error{VIECUT_EINVAL, "invalid graph: not symmetric (edge weights must match in both directions)"};
+  return unit;
 }
 
 // ------------------------------------------------------------------- the run
@@ -395,6 +406,7 @@ static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, u
   G.adj = H.adj0;
   G.w = H.w0;
   G.wbytes = 4;
+  G.unit = H.unit;
   W.bins_valid = false;
 
   cudaEvent_t a = W.mark();
@@ -648,7 +660,10 @@ static int create_common(viecut_t** out, int64_t n, int64_t m, const viecut_opts
   if (opts) o = *opts;
   if (o.n0 < 1) throw Error{VIECUT_EINVAL, "n0 must be >= 1"};
   if (o.pr_runs_max < 0) throw Error{VIECUT_EINVAL, "pr_runs_max must be >= 0"};
-  if (host_input && o.validate >= 1) vc::host_validate(off, adj, w, n, m, o.validate >= 2);
+  // validate 2: full check on the host (symmetry needs a sort); validate 1: one pass
+  // on the device after the copy
+  bool unit = false;
+  if (host_input && o.validate >= 2) unit = vc::host_validate(off, adj, w, n, m, true);
   auto* hh = new viecut_handle;
   vc::Handle& H = hh->h;
   try {
@@ -665,6 +680,7 @@ static int create_common(viecut_t** out, int64_t n, int64_t m, const viecut_opts
     H.n0 = o.n0;
     H.pr_runs_max = o.pr_runs_max;
     H.validate = o.validate;
+    H.unit = unit;
     H.ws = new vc::Workspace;
     H.ws->s = H.stream;
     H.ws->timing = o.timing != 0;
@@ -686,7 +702,7 @@ static int create_common(viecut_t** out, int64_t n, int64_t m, const viecut_opts
     H.ws->ensure_entries(m, n);
     H.out_cut.ensure_n<long long>(1);
     H.out_bits.ensure_n<unsigned long long>((n + 63) / 64);
-    if (!host_input && o.validate >= 1) vc::device_validate(H);
+    if (o.validate == 1 || (!host_input && o.validate >= 1)) vc::device_validate(H);
     VC_CUDA(cudaStreamSynchronize(H.stream));
   } catch (...) {
     delete hh;

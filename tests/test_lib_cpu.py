@@ -45,8 +45,9 @@ def test_opts_defaults(lib):
 
 
 def test_host_validation_rejects_bad_graphs(lib):
-    """Validation of host arrays happens before any device call, so it is testable
-    here: every malformed input must give EINVAL with a message."""
+    """Full validation of host arrays (validate = 2) happens before any device call,
+    so it is testable here: every malformed input must give EINVAL with a message."""
+    full = vc.viecut_opts_init(validate=2)
     off = np.array([0, 1, 2], np.int64)
     adj = np.array([1, 0], np.int32)
     cases = [
@@ -57,7 +58,7 @@ def test_host_validation_rejects_bad_graphs(lib):
     ]
     for o, a, w, why in cases:
         with pytest.raises(vc.ViecutError) as e:
-            vc.viecut_create(o, a, 2, 2, w)
+            vc.viecut_create(o, a, 2, 2, w, full)
         assert e.value.code == vc.VIECUT_EINVAL and why in str(e.value), (why, str(e.value))
     # asymmetric weights are caught by the full check (validate = 2)
     with pytest.raises(vc.ViecutError) as e:
