@@ -25,9 +25,15 @@ __global__ void degrees_k(int64_t n, const int64_t* __restrict__ off, const WT* 
   }
 }
 
+// unit weights: the degree is the list length
+__global__ void degrees_unit_k(int64_t n, const int64_t* __restrict__ off, long long* __restrict__ deg) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    deg[v] = off[v + 1] - off[v];
+}
+
 void degrees(const GraphView& g, long long* deg, cudaStream_t s) {
   int grid = grid_for(g.n, 8, kSMs * 16);
-  if (g.unit) degrees_k<UnitW><<<grid, 256, 0, s>>>(g.n, g.off, nullptr, deg);
+  if (g.unit) degrees_unit_k<<<grid_for(g.n, 256, kSMs * 8), 256, 0, s>>>(g.n, g.off, deg);
   else if (g.wbytes == 4) degrees_k<int32_t><<<grid, 256, 0, s>>>(g.n, g.off, (const int32_t*)g.w, deg);
   else degrees_k<long long><<<grid, 256, 0, s>>>(g.n, g.off, (const long long*)g.w, deg);
   count_launch();

@@ -7,6 +7,7 @@ namespace vc {
 // A CSR graph on the device.  Weights are int32 (input graphs, wbytes = 4) or int64
 // (every contracted graph, wbytes = 8).  unit = every weight is 1: the kernels that
 // support it (label propagation, pre-merge, degrees) then read no weights at all.
+// simple = every list is strictly increasing (true for every contracted graph).
 struct GraphView {
   int64_t n = 0, nnz = 0;
   const int64_t* off = nullptr;
@@ -14,6 +15,7 @@ struct GraphView {
   const void* w = nullptr;
   int wbytes = 8;
   bool unit = false;
+  bool simple = false;  // every list strictly increasing (no parallel entries)
 };
 
 // Weight loads for the three storage cases (UnitW: implicit weight 1).

@@ -17,7 +17,9 @@
 //   global (larger)  : a block per listed vertex, table in global scratch.
 #include <limits.h>
 
+#include <mutex>
 #include <type_traits>
+#include <unordered_map>
 
 #include "kernels.cuh"
 
@@ -58,18 +60,20 @@ int64_t global_table_cap(int maxdeg) {
 
 // Adds wt to the slot of key k (linear probing; capacity >= 2 x distinct keys, so a
 // free slot always exists and the loop ends within one pass over the table).
+// Returns the slot index if this call created the key, otherwise -1.
 template <typename ACC>
-__device__ __forceinline__ void tbl_add(int* tk, ACC* tv, int lg, int k, long long wt) {
+__device__ __forceinline__ int tbl_add(int* tk, ACC* tv, int lg, int k, long long wt) {
   const uint32_t mask = (1u << lg) - 1u;
   uint32_t h = slot_hash(k, lg);
   for (uint32_t probe = 0; probe <= mask; ++probe) {
     int prev = atomicCAS(&tk[h], kEmptyKey, k);
     if (prev == kEmptyKey || prev == k) {
       atomicAdd(&tv[h], (ACC)wt);
-      return;
+      return prev == kEmptyKey ? (int)h : -1;
     }
     h = (h + 1) & mask;
   }
+  return -1;
 }
 
 // key of neighbour u for vertex v; returns false when the entry is skipped
@@ -146,19 +150,20 @@ struct LaneBest {
 };
 
 // ------------------------------------------------------------------ warp classes
-// LISTED = false: every vertex of list length <= CAP/2 (grid-stride over all vertices);
-// LISTED = true : the listed vertices (count on the device).
-template <typename WT, typename ACC, int MODE, bool FIRST, int CAP, bool LISTED>
-__global__ void __launch_bounds__(kAggThreads) agg_warp_k(
+// Label propagation with a per-warp table.  LISTED = false: every vertex of list
+// length <= CAP/2 (grid-stride over all vertices); LISTED = true: the listed vertices.
+// The slots a vertex creates are recorded, so the final argmax visits only them.
+template <typename WT, typename ACC, bool FIRST, int CAP, bool LISTED>
+__global__ void __launch_bounds__(kAggThreads) lp_warp_k(
     int64_t n, const int32_t* __restrict__ list, const int* __restrict__ count_ptr,
     const int64_t* __restrict__ off, const int32_t* __restrict__ adj, const WT* __restrict__ w,
-    const int32_t* __restrict__ lab, int32_t* __restrict__ lab_out, uint64_t key,
-    int32_t* __restrict__ tkey, long long* __restrict__ tval, int32_t* __restrict__ cnt) {
+    const int32_t* __restrict__ lab, int32_t* __restrict__ lab_out, uint64_t key) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ long long s_w[kWarpsPerBlock][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   ACC* tv = (ACC*)dyn + (size_t)wib * CAP;
   int* tk = (int*)((ACC*)dyn + (size_t)kWarpsPerBlock * CAP) + (size_t)wib * CAP;
+  int* slots = (int*)((ACC*)dyn + (size_t)kWarpsPerBlock * CAP) + (size_t)kWarpsPerBlock * CAP + (size_t)wib * (CAP / 2);
   long long* sw = s_w[wib];
   for (int i = lane; i < CAP; i += 32) { tk[i] = kEmptyKey; tv[i] = 0; }
   __syncwarp();
@@ -169,86 +174,186 @@ __global__ void __launch_bounds__(kAggThreads) agg_warp_k(
     const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
     const int d = (int)(end - beg);
     if (!LISTED && d > CAP / 2) continue;
-    const int32_t own = (MODE == kModeEmit) ? __ldg(lab + v) : 0;
     if (d == 0) {
-      if (lane == 0) {
-        if (MODE == kModeLP) lab_out[v] = FIRST ? (int32_t)v : __ldg(lab + v);
-        else cnt[v] = 0;
-      }
+      if (lane == 0) lab_out[v] = FIRST ? (int32_t)v : __ldg(lab + v);
       continue;
     }
     if (d <= 32) {
       // one chunk: the group sums are final, no table needed
-      Chunk c = load_chunk<WT, MODE, FIRST>(beg + lane, end, adj, w, lab, own, sw, lane);
-      if (MODE == kModeLP) {
-        Cand cd = c.leader ? Cand{c.sum, tie_hash(key, c.k), c.k} : Cand{-1LL, 0ULL, INT_MAX};
-        cd = warp_best(cd);
-        if (lane == 0) lab_out[v] = cd.l;
-      } else {
-        unsigned bal = __ballot_sync(0xffffffffu, c.leader);
-        if (c.leader) {
-          int j = __popc(bal & ((1u << lane) - 1u));
-          tkey[beg + j] = c.k;
-          tval[beg + j] = c.sum;
-        }
-        if (lane == 0) cnt[v] = __popc(bal);
-      }
+      Chunk c = load_chunk<WT, kModeLP, FIRST>(beg + lane, end, adj, w, lab, 0, sw, lane);
+      Cand cd = c.leader ? Cand{c.sum, tie_hash(key, c.k), c.k} : Cand{-1LL, 0ULL, INT_MAX};
+      cd = warp_best(cd);
+      if (lane == 0) lab_out[v] = cd.l;
       continue;
     }
     const int lg = ceil_log2(2 * (int64_t)d);
-    const int cap = 1 << lg;
+    int created = 0;  // warp-uniform count of recorded slots
     for (int64_t base = beg; base < end; base += 32) {
-      Chunk c = load_chunk<WT, MODE, FIRST>(base + lane, end, adj, w, lab, own, sw, lane);
-      if (c.leader) tbl_add<ACC>(tk, tv, lg, c.k, c.sum);
+      Chunk c = load_chunk<WT, kModeLP, FIRST>(base + lane, end, adj, w, lab, 0, sw, lane);
+      const int slot = c.leader ? tbl_add<ACC>(tk, tv, lg, c.k, c.sum) : -1;
+      const unsigned bal = __ballot_sync(0xffffffffu, slot >= 0);
+      if (slot >= 0) slots[created + __popc(bal & ((1u << lane) - 1u))] = slot;
+      created += __popc(bal);
     }
     __syncwarp();
-    if (MODE == kModeLP) {
-      LaneBest lb;
-      for (int i = lane; i < cap; i += 32) {
-        const int L = tk[i];
-        if (L != kEmptyKey) {
-          lb.add((long long)tv[i], L, key);
-          tk[i] = kEmptyKey;
-          tv[i] = 0;
-        }
-      }
-      Cand cd = warp_best(lb.done(key));
-      if (lane == 0) lab_out[v] = cd.l;
-    } else {
-      int basej = 0;
-      for (int i0 = 0; i0 < cap; i0 += 32) {
-        const int i = i0 + lane;
-        const int L = tk[i];
-        const bool occ = L != kEmptyKey;
-        const unsigned bal = __ballot_sync(0xffffffffu, occ);
-        if (occ) {
-          const int j = basej + __popc(bal & ((1u << lane) - 1u));
-          tkey[beg + j] = L;
-          tval[beg + j] = (long long)tv[i];
-          tk[i] = kEmptyKey;
-          tv[i] = 0;
-        }
-        basej += __popc(bal);
-      }
-      if (lane == 0) cnt[v] = basej;
+    LaneBest lb;
+    for (int i = lane; i < created; i += 32) {
+      const int slot = slots[i];
+      lb.add((long long)tv[slot], tk[slot], key);
+      tk[slot] = kEmptyKey;
+      tv[slot] = 0;
     }
+    Cand cd = warp_best(lb.done(key));
+    if (lane == 0) lab_out[v] = cd.l;
     __syncwarp();
   }
 }
 
+// First round on a graph whose lists are strictly increasing: every neighbour is its
+// own label, so S(u) = c(v,u) and the choice is the argmax of (c(v,u), hash(u), -u)
+// over the list; no accumulation needed.  A warp per vertex (lengths <= MAXD) or, for
+// the listed longer lists, a block per vertex.
+template <typename WT>
+__device__ __forceinline__ void first_scan(LaneBest& lb, int64_t a, int64_t end, int step,
+                                           const int32_t* __restrict__ adj, const WT* __restrict__ w,
+                                           uint64_t key) {
+  for (int64_t e = a; e < end; e += step) lb.add(ldw(w, e), __ldg(adj + e), key);
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(kAggThreads) lp_first_simple_k(int64_t n, int maxd,
+                                                                 const int64_t* __restrict__ off,
+                                                                 const int32_t* __restrict__ adj,
+                                                                 const WT* __restrict__ w,
+                                                                 int32_t* __restrict__ lab_out, uint64_t key) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
+    if (end - beg > maxd) continue;
+    if (end == beg) {
+      if (lane == 0) lab_out[v] = (int32_t)v;
+      continue;
+    }
+    LaneBest lb;
+    first_scan(lb, beg + lane, end, 32, adj, w, key);
+    Cand cd = warp_best(lb.done(key));
+    if (lane == 0) lab_out[v] = cd.l;
+  }
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(kAggThreads) lp_first_simple_block_k(const int32_t* __restrict__ list,
+                                                                       const int* __restrict__ count_ptr,
+                                                                       const int64_t* __restrict__ off,
+                                                                       const int32_t* __restrict__ adj,
+                                                                       const WT* __restrict__ w,
+                                                                       int32_t* __restrict__ lab_out,
+                                                                       uint64_t key) {
+  __shared__ Cand s_best[kWarpsPerBlock];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int count = *count_ptr;
+  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    const int32_t v = list[idx];
+    LaneBest lb;
+    first_scan(lb, off[v] + threadIdx.x, off[v + 1], kAggThreads, adj, w, key);
+    Cand cd = warp_best(lb.done(key));
+    if (lane == 0) s_best[wib] = cd;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Cand b = s_best[0];
+      for (int q = 1; q < kWarpsPerBlock; ++q)
+        if (better(s_best[q], b)) b = s_best[q];
+      lab_out[v] = b.l;
+    }
+    __syncthreads();
+  }
+}
+
+// Pre-merge without a table: each 32-entry chunk's groups are written out directly
+// (the sort that follows merges equal keys across chunks and across vertices).  A warp
+// per vertex of length <= MAXD, a block per listed longer vertex.
+template <typename WT>
+__global__ void __launch_bounds__(kAggThreads) emit_warp_k(int64_t n, int maxd, const int64_t* __restrict__ off,
+                                                           const int32_t* __restrict__ adj, const WT* __restrict__ w,
+                                                           const int32_t* __restrict__ cid, int32_t* __restrict__ tkey,
+                                                           long long* __restrict__ tval, int32_t* __restrict__ cnt) {
+  __shared__ long long s_w[kWarpsPerBlock][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  long long* sw = s_w[wib];
+  const int64_t warps = (int64_t)gridDim.x * kWarpsPerBlock;
+  for (int64_t v = (int64_t)blockIdx.x * kWarpsPerBlock + wib; v < n; v += warps) {
+    const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
+    if (end - beg > maxd) continue;
+    const int32_t own = __ldg(cid + v);
+    int made = 0;
+    if (own >= 0) {
+      for (int64_t base = beg; base < end; base += 32) {
+        Chunk c = load_chunk<WT, kModeEmit, false>(base + lane, end, adj, w, cid, own, sw, lane);
+        const unsigned bal = __ballot_sync(0xffffffffu, c.leader);
+        if (c.leader) {
+          const int64_t j = beg + made + __popc(bal & ((1u << lane) - 1u));
+          tkey[j] = c.k;
+          tval[j] = c.sum;
+        }
+        made += __popc(bal);
+      }
+    }
+    if (lane == 0) cnt[v] = made;
+  }
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(kAggThreads) emit_block_k(const int32_t* __restrict__ list,
+                                                            const int* __restrict__ count_ptr,
+                                                            const int64_t* __restrict__ off,
+                                                            const int32_t* __restrict__ adj,
+                                                            const WT* __restrict__ w, const int32_t* __restrict__ cid,
+                                                            int32_t* __restrict__ tkey, long long* __restrict__ tval,
+                                                            int32_t* __restrict__ cnt) {
+  __shared__ long long s_w[kWarpsPerBlock][32];
+  __shared__ int s_made;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  long long* sw = s_w[wib];
+  const int count = *count_ptr;
+  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    const int32_t v = list[idx];
+    const int64_t beg = off[v], end = off[v + 1];
+    const int32_t own = cid[v];
+    if (threadIdx.x == 0) s_made = 0;
+    __syncthreads();
+    if (own >= 0) {
+      for (int64_t base = beg + 32 * wib; base < end; base += 32 * kWarpsPerBlock) {
+        Chunk c = load_chunk<WT, kModeEmit, false>(base + lane, end, adj, w, cid, own, sw, lane);
+        const unsigned bal = __ballot_sync(0xffffffffu, c.leader);
+        int at = 0;
+        if (lane == 0 && bal) at = atomicAdd(&s_made, __popc(bal));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (c.leader) {
+          const int64_t j = beg + at + __popc(bal & ((1u << lane) - 1u));
+          tkey[j] = c.k;
+          tval[j] = c.sum;
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) cnt[v] = s_made;
+    __syncthreads();
+  }
+}
+
 // --------------------------------------------------------- block / global classes
-// One block per listed vertex; the table lives in shared memory (GLOBAL = false) or
-// in this block's region of global scratch (GLOBAL = true).
-template <typename WT, typename ACC, int MODE, bool FIRST, bool GLOBAL>
-__global__ void __launch_bounds__(kAggThreads) agg_block_k(
+// Label propagation, one block per listed vertex; the table lives in shared memory
+// (GLOBAL = false) or in this block's region of global scratch (GLOBAL = true).
+template <typename WT, typename ACC, bool FIRST, bool GLOBAL>
+__global__ void __launch_bounds__(kAggThreads) lp_block_k(
     const int32_t* __restrict__ list, const int* __restrict__ count_ptr, const int64_t* __restrict__ off,
     const int32_t* __restrict__ adj, const WT* __restrict__ w, const int32_t* __restrict__ lab,
-    int32_t* __restrict__ lab_out, uint64_t key, int32_t* __restrict__ tkey, long long* __restrict__ tval,
-    int32_t* __restrict__ cnt, int32_t* __restrict__ gkeys, long long* __restrict__ gvals, int64_t gcap) {
+    int32_t* __restrict__ lab_out, uint64_t key, int32_t* __restrict__ gkeys, long long* __restrict__ gvals,
+    int64_t gcap) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ Cand s_best[kWarpsPerBlock];
   __shared__ long long s_w[kWarpsPerBlock][32];
-  __shared__ int s_count;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int* tk;
   ACC* tv;
@@ -270,99 +375,118 @@ __global__ void __launch_bounds__(kAggThreads) agg_block_k(
     const int32_t v = list[idx];
     const int64_t beg = off[v], end = off[v + 1];
     const int64_t d = end - beg;
-    const int32_t own = (MODE == kModeEmit) ? lab[v] : 0;
     const int lg = ceil_log2(2 * d);
     const int64_t cap = (int64_t)1 << lg;
     for (int64_t base = beg + 32 * wib; base < end; base += 32 * kWarpsPerBlock) {
-      Chunk c = load_chunk<WT, MODE, FIRST>(base + lane, end, adj, w, lab, own, sw, lane);
+      Chunk c = load_chunk<WT, kModeLP, FIRST>(base + lane, end, adj, w, lab, 0, sw, lane);
       if (c.leader) tbl_add<ACC>(tk, tv, lg, c.k, c.sum);
     }
-    if (MODE == kModeEmit && threadIdx.x == 0) s_count = 0;
     __syncthreads();
-    if (MODE == kModeLP) {
-      LaneBest lb;
-      for (int64_t i = threadIdx.x; i < cap; i += kAggThreads) {
-        const int L = tk[i];
-        if (L != kEmptyKey) {
-          lb.add((long long)tv[i], L, key);
-          tk[i] = kEmptyKey;
-          tv[i] = 0;
-        }
+    LaneBest lb;
+    for (int64_t i = threadIdx.x; i < cap; i += kAggThreads) {
+      const int L = tk[i];
+      if (L != kEmptyKey) {
+        lb.add((long long)tv[i], L, key);
+        tk[i] = kEmptyKey;
+        tv[i] = 0;
       }
-      Cand cd = warp_best(lb.done(key));
-      if (lane == 0) s_best[wib] = cd;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        Cand b = s_best[0];
-        for (int q = 1; q < kWarpsPerBlock; ++q)
-          if (better(s_best[q], b)) b = s_best[q];
-        lab_out[v] = b.l;
-      }
-    } else {
-      for (int64_t i = threadIdx.x; i < cap; i += kAggThreads) {
-        const int L = tk[i];
-        if (L != kEmptyKey) {
-          const int j = atomicAdd(&s_count, 1);
-          tkey[beg + j] = L;
-          tval[beg + j] = (long long)tv[i];
-          tk[i] = kEmptyKey;
-          tv[i] = 0;
-        }
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) cnt[v] = s_count;
+    }
+    Cand cd = warp_best(lb.done(key));
+    if (lane == 0) s_best[wib] = cd;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Cand b = s_best[0];
+      for (int q = 1; q < kWarpsPerBlock; ++q)
+        if (better(s_best[q], b)) b = s_best[q];
+      lab_out[v] = b.l;
     }
     __syncthreads();
   }
 }
 
+// Opts a kernel into more than 48 KB of dynamic shared memory, once per kernel.
 template <typename F>
 void set_smem(F kfn, size_t bytes) {
-  // once per kernel instantiation (single device per process)
-  static bool done = false;
-  if (!done) {
-    VC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    done = true;
-  }
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> done;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find((const void*)kfn);
+  if (it != done.end() && it->second >= bytes) return;
+  VC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  done[(const void*)kfn] = bytes;
 }
 
-template <typename WT, typename ACC, int MODE, bool FIRST>
-void launch_agg(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* lab,
-                int32_t* lab_out, uint64_t key, int32_t* tkey, long long* tval, int32_t* cnt, cudaStream_t s) {
+template <int CAP, typename ACC>
+constexpr size_t warp_smem() {
+  return (size_t)kWarpsPerBlock * CAP * (sizeof(ACC) + sizeof(int)) + (size_t)kWarpsPerBlock * (CAP / 2) * sizeof(int);
+}
+
+template <typename WT, typename ACC, bool FIRST>
+void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* lab, int32_t* lab_out,
+               uint64_t key, cudaStream_t s) {
   const WT* w = (const WT*)g.w;
+  if (FIRST && g.simple) {
+    lp_first_simple_k<WT><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
+        g.n, kBlockMaxDeg, g.off, g.adj, w, lab_out, key);
+    count_launch();
+    VC_CHECK_LAUNCH();
+    if (b.h_global > 0) {
+      lp_first_simple_block_k<WT><<<grid_for(b.h_global, 1, kSMs * 4), kAggThreads, 0, s>>>(
+          b.global_list, b.counts + 2, g.off, g.adj, w, lab_out, key);
+      count_launch();
+      VC_CHECK_LAUNCH();
+    }
+    return;
+  }
   {
     constexpr int CAP = kWarpCap;
-    const size_t smem = (size_t)kWarpsPerBlock * CAP * (sizeof(ACC) + sizeof(int));
-    auto kfn = agg_warp_k<WT, ACC, MODE, FIRST, CAP, false>;
+    const size_t smem = warp_smem<CAP, ACC>();
+    auto kfn = lp_warp_k<WT, ACC, FIRST, CAP, false>;
     set_smem(kfn, smem);
-    kfn<<<grid_for(g.n, kWarpsPerBlock * 4, kSMs * 8), kAggThreads, smem, s>>>(
-        g.n, nullptr, nullptr, g.off, g.adj, w, lab, lab_out, key, tkey, tval, cnt);
+    kfn<<<grid_for(g.n, kWarpsPerBlock * 4, kSMs * 8), kAggThreads, smem, s>>>(g.n, nullptr, nullptr, g.off, g.adj,
+                                                                              w, lab, lab_out, key);
     count_launch();
     VC_CHECK_LAUNCH();
   }
   if (b.h_mid > 0) {
     constexpr int CAP = kMidCap;
-    const size_t smem = (size_t)kWarpsPerBlock * CAP * (sizeof(ACC) + sizeof(int));
-    auto kfn = agg_warp_k<WT, ACC, MODE, FIRST, CAP, true>;
+    const size_t smem = warp_smem<CAP, ACC>();
+    auto kfn = lp_warp_k<WT, ACC, FIRST, CAP, true>;
     set_smem(kfn, smem);
-    kfn<<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 2), kAggThreads, smem, s>>>(
-        0, b.mid_list, b.counts + 0, g.off, g.adj, w, lab, lab_out, key, tkey, tval, cnt);
+    kfn<<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 2), kAggThreads, smem, s>>>(0, b.mid_list, b.counts + 0, g.off,
+                                                                              g.adj, w, lab, lab_out, key);
     count_launch();
     VC_CHECK_LAUNCH();
   }
   if (b.h_block > 0) {
     const size_t smem = (size_t)kBlockCap * (sizeof(ACC) + sizeof(int));
-    auto kfn = agg_block_k<WT, ACC, MODE, FIRST, false>;
+    auto kfn = lp_block_k<WT, ACC, FIRST, false>;
     set_smem(kfn, smem);
-    kfn<<<grid_for(b.h_block, 1, kSMs * 2), kAggThreads, smem, s>>>(
-        b.block_list, b.counts + 1, g.off, g.adj, w, lab, lab_out, key, tkey, tval, cnt, nullptr, nullptr, 0);
+    kfn<<<grid_for(b.h_block, 1, kSMs * 2), kAggThreads, smem, s>>>(b.block_list, b.counts + 1, g.off, g.adj, w,
+                                                                   lab, lab_out, key, nullptr, nullptr, 0);
     count_launch();
     VC_CHECK_LAUNCH();
   }
   if (b.h_global > 0) {
     int grid_g = b.h_global < gt.blocks ? b.h_global : gt.blocks;
-    agg_block_k<WT, ACC, MODE, FIRST, true><<<grid_g, kAggThreads, 0, s>>>(
-        b.global_list, b.counts + 2, g.off, g.adj, w, lab, lab_out, key, tkey, tval, cnt, gt.keys, gt.vals, gt.cap);
+    lp_block_k<WT, ACC, FIRST, true><<<grid_g, kAggThreads, 0, s>>>(b.global_list, b.counts + 2, g.off, g.adj, w,
+                                                                    lab, lab_out, key, gt.keys, gt.vals, gt.cap);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
+}
+
+template <typename WT>
+void launch_emit(const GraphView& g, const Bins& b, const int32_t* cid, int32_t* tkey, long long* tval,
+                 int32_t* cnt, cudaStream_t s) {
+  const WT* w = (const WT*)g.w;
+  emit_warp_k<WT><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(g.n, kBlockMaxDeg, g.off, g.adj,
+                                                                                   w, cid, tkey, tval, cnt);
+  count_launch();
+  VC_CHECK_LAUNCH();
+  if (b.h_global > 0) {
+    emit_block_k<WT><<<grid_for(b.h_global, 1, kSMs * 4), kAggThreads, 0, s>>>(b.global_list, b.counts + 2, g.off,
+                                                                               g.adj, w, cid, tkey, tval, cnt);
     count_launch();
     VC_CHECK_LAUNCH();
   }
@@ -370,30 +494,29 @@ void launch_agg(const GraphView& g, const Bins& b, const GlobalTables& gt, const
 
 // Unit weights accumulate in 32 bits (a sum never exceeds the list length); stored
 // weights accumulate in 64 bits.
-template <int MODE, bool FIRST>
-void dispatch_agg(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* lab,
-                  int32_t* lab_out, uint64_t key, int32_t* tkey, long long* tval, int32_t* cnt, cudaStream_t s) {
-  if (g.unit)
-    launch_agg<UnitW, unsigned int, MODE, FIRST>(g, b, gt, lab, lab_out, key, tkey, tval, cnt, s);
-  else if (g.wbytes == 4)
-    launch_agg<int32_t, unsigned long long, MODE, FIRST>(g, b, gt, lab, lab_out, key, tkey, tval, cnt, s);
-  else
-    launch_agg<long long, unsigned long long, MODE, FIRST>(g, b, gt, lab, lab_out, key, tkey, tval, cnt, s);
-}
-
 void lp_round(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* lab_in,
               int32_t* lab_out, uint64_t key, cudaStream_t s) {
   if (g.n <= 0) return;
-  if (lab_in == nullptr)
-    dispatch_agg<kModeLP, true>(g, b, gt, nullptr, lab_out, key, nullptr, nullptr, nullptr, s);
-  else
-    dispatch_agg<kModeLP, false>(g, b, gt, lab_in, lab_out, key, nullptr, nullptr, nullptr, s);
+  const bool first = lab_in == nullptr;
+  if (g.unit) {
+    if (first) launch_lp<UnitW, unsigned int, true>(g, b, gt, nullptr, lab_out, key, s);
+    else launch_lp<UnitW, unsigned int, false>(g, b, gt, lab_in, lab_out, key, s);
+  } else if (g.wbytes == 4) {
+    if (first) launch_lp<int32_t, unsigned long long, true>(g, b, gt, nullptr, lab_out, key, s);
+    else launch_lp<int32_t, unsigned long long, false>(g, b, gt, lab_in, lab_out, key, s);
+  } else {
+    if (first) launch_lp<long long, unsigned long long, true>(g, b, gt, nullptr, lab_out, key, s);
+    else launch_lp<long long, unsigned long long, false>(g, b, gt, lab_in, lab_out, key, s);
+  }
 }
 
 void emit_cross(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* cid,
                 int32_t* tmp_key, long long* tmp_val, int32_t* cnt, cudaStream_t s) {
+  (void)gt;
   if (g.n <= 0) return;
-  dispatch_agg<kModeEmit, false>(g, b, gt, cid, nullptr, 0, tmp_key, tmp_val, cnt, s);
+  if (g.unit) launch_emit<UnitW>(g, b, cid, tmp_key, tmp_val, cnt, s);
+  else if (g.wbytes == 4) launch_emit<int32_t>(g, b, cid, tmp_key, tmp_val, cnt, s);
+  else launch_emit<long long>(g, b, cid, tmp_key, tmp_val, cnt, s);
 }
 
 }  // namespace vc

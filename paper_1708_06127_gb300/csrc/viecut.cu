@@ -272,6 +272,7 @@ struct Workspace {
     h.adj = ca;
     h.w = cwp;
     h.wbytes = 8;
+    h.simple = true;
     bins_valid = false;
     return h;
   }
@@ -299,6 +300,7 @@ __global__ void validate_k(int64_t n, int64_t m, const int64_t* __restrict__ off
       else if (u == v) bad |= 8;
       if (w[e] < 1) bad |= 16;
       if (w[e] != 1) bad |= 32;  // not an error: the weights are not all 1
+      if (e + 1 < b && adj[e + 1] <= u) bad |= 64;  // not an error: a list is not strictly increasing
     }
   }
   if (bad) atomicOr(err, bad);
@@ -312,7 +314,8 @@ struct Handle {
   int64_t n0 = 10000;
   int pr_runs_max = 8;
   int validate = 1;
-  bool unit = false;  // every input weight is 1 (found by validation)
+  bool unit = false;    // every input weight is 1 (found by validation)
+  bool simple = false;  // every input list strictly increasing (found by validation)
   const int64_t* off0 = nullptr;
   const int32_t* adj0 = nullptr;
   const int32_t* w0 = nullptr;
@@ -336,7 +339,8 @@ static void device_validate(Handle& H) {
   W.read_state();
   int bad = W.h_counters->changed;
   H.unit = (bad & 32) == 0;
-  bad &= ~32;
+  H.simple = (bad & 64) == 0;
+  bad &= ~(32 | 64);
   if (bad) {
     std::string why;
     if (bad & 1) why += " offsets[0] != 0 or offsets[n] != m;";
@@ -348,10 +352,11 @@ static void device_validate(Handle& H) {
   }
 }
 
-// Returns true when every weight is 1.
+// Returns true when every weight is 1; *simple = every list strictly increasing.
 static bool host_validate(const int64_t* off, const int32_t* adj, const int32_t* w, int64_t n, int64_t m,
-                          bool symmetric) {
+                          bool symmetric, bool* simple) {
   bool unit = true;
+  *simple = true;
   if (off[0] != 0 || off[n] != m) throw Error{VIECUT_EINVAL, "invalid graph: offsets[0] != 0 or offsets[n] != m"};
   for (int64_t v = 0; v < n; ++v) {
     if (off[v + 1] < off[v]) throw Error{VIECUT_EINVAL, "invalid graph: offsets decrease at vertex " + std::to_string(v)};
@@ -360,6 +365,7 @@ static bool host_validate(const int64_t* off, const int32_t* adj, const int32_t*
       if (adj[e] == v) throw Error{VIECUT_EINVAL, "invalid graph: self-loop at vertex " + std::to_string(v)};
       if (w[e] < 1) throw Error{VIECUT_EINVAL, "invalid graph: weight < 1"};
       unit = unit && w[e] == 1;
+      if (e + 1 < off[v + 1] && adj[e + 1] <= adj[e]) *simple = false;
     }
   }
   if (!symmetric) return unit;
@@ -407,6 +413,7 @@ static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, u
   G.w = H.w0;
   G.wbytes = 4;
   G.unit = H.unit;
+  G.simple = H.simple;
   W.bins_valid = false;
 
   cudaEvent_t a = W.mark();
@@ -592,6 +599,7 @@ static void fetch_trace(Handle& H) {
 struct StepGraph {
   int device = 0;
   int64_t n = 0, nnz = 0;
+  bool simple = false;
   Buf off, adj, w;
   GraphView view() const {
     GraphView g;
@@ -601,6 +609,7 @@ struct StepGraph {
     g.adj = adj.as<int32_t>();
     g.w = w.p;
     g.wbytes = 8;
+    g.simple = simple;
     return g;
   }
 };
@@ -662,8 +671,8 @@ static int create_common(viecut_t** out, int64_t n, int64_t m, const viecut_opts
   if (o.pr_runs_max < 0) throw Error{VIECUT_EINVAL, "pr_runs_max must be >= 0"};
   // validate 2: full check on the host (symmetry needs a sort); validate 1: one pass
   // on the device after the copy
-  bool unit = false;
-  if (host_input && o.validate >= 2) unit = vc::host_validate(off, adj, w, n, m, true);
+  bool unit = false, simple = false;
+  if (host_input && o.validate >= 2) unit = vc::host_validate(off, adj, w, n, m, true, &simple);
   auto* hh = new viecut_handle;
   vc::Handle& H = hh->h;
   try {
@@ -681,6 +690,7 @@ static int create_common(viecut_t** out, int64_t n, int64_t m, const viecut_opts
     H.pr_runs_max = o.pr_runs_max;
     H.validate = o.validate;
     H.unit = unit;
+    H.simple = simple;
     H.ws = new vc::Workspace;
     H.ws->s = H.stream;
     H.ws->timing = o.timing != 0;
@@ -783,6 +793,10 @@ int viecut_graph_upload(viecut_graph** g, const int64_t* offsets, const int32_t*
     x->g.device = device;
     x->g.n = n;
     x->g.nnz = nnz;
+    x->g.simple = true;
+    for (int64_t v = 0; v < n && x->g.simple; ++v)
+      for (int64_t e = offsets[v]; e + 1 < offsets[v + 1]; ++e)
+        if (adj[e + 1] <= adj[e]) { x->g.simple = false; break; }
     VC_CUDA(cudaMemcpy(x->g.off.ensure_n<int64_t>(n + 1), offsets, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
     x->g.adj.ensure_n<int32_t>(nnz);
     x->g.w.ensure_n<long long>(nnz);
@@ -907,6 +921,7 @@ int viecut_step_contract(viecut_graph* g, const int32_t* labels, viecut_graph** 
     x->g.device = g->g.device;
     x->g.n = h.n;
     x->g.nnz = nnz;
+    x->g.simple = true;
     VC_CUDA(cudaMemcpyAsync(x->g.off.ensure_n<int64_t>(h.n + 1), h.off, sizeof(int64_t) * (h.n + 1),
                             cudaMemcpyDeviceToDevice, c.s));
     VC_CUDA(cudaMemcpyAsync(x->g.adj.ensure_n<int32_t>(nnz), h.adj, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, c.s));
