@@ -55,10 +55,15 @@ struct GlobalTables {
 };
 int64_t global_table_cap(int maxdeg);
 
+// Tie-break table of a level: hv[L] = mix64(key XOR L) for every label L < n.  With
+// gid/gkey (batches) the key of label L is gkey[gid[L]].
+void hash_table(int64_t n, uint64_t key, const int32_t* gid, const unsigned long long* gkey,
+                unsigned long long* hv, cudaStream_t s);
+
 // One synchronous label-propagation round; lab_in == nullptr means the identity
-// labelling (first round of a level).
+// labelling (first round of a level).  hv: the level's tie-break table.
 void lp_round(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* lab_in,
-              int32_t* lab_out, uint64_t key, cudaStream_t s);
+              int32_t* lab_out, const unsigned long long* hv, cudaStream_t s);
 
 // Pre-merge for contraction: for each vertex v, the distinct coarse neighbours cu =
 // cid[u] != cid[v] with summed weights, written at [off[v], off[v] + cnt[v]).

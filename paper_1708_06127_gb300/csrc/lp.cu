@@ -52,6 +52,22 @@ void bins_build(const GraphView& g, Bins& b, cudaStream_t s) {
   VC_CHECK_LAUNCH();
 }
 
+__global__ void hash_table_k(int64_t n, uint64_t key, const int32_t* __restrict__ gid,
+                             const unsigned long long* __restrict__ gkey, unsigned long long* __restrict__ hv) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = gid ? gkey[gid[v]] : key;
+    hv[v] = tie_hash(k, (int32_t)v);
+  }
+}
+
+void hash_table(int64_t n, uint64_t key, const int32_t* gid, const unsigned long long* gkey,
+                unsigned long long* hv, cudaStream_t s) {
+  if (n <= 0) return;
+  hash_table_k<<<grid_for(n, 256, kSMs * 8), 256, 0, s>>>(n, key, gid, gkey, hv);
+  count_launch();
+  VC_CHECK_LAUNCH();
+}
+
 int64_t global_table_cap(int maxdeg) {
   int64_t c = 1;
   while (c < 2 * (int64_t)maxdeg) c <<= 1;
@@ -126,25 +142,26 @@ __device__ __forceinline__ Chunk load_chunk(int64_t e, int64_t end, const int32_
   return c;
 }
 
-// Per-lane running best over (sum, hash, -label); the hash is computed only on ties.
+// Per-lane running best over (sum, hash, -label); the tie hash of a label is read
+// from the level's table hv[L] = H(key, L), and only on ties.
 struct LaneBest {
   long long s = -1;
   int l = INT_MAX;
   unsigned long long h = 0;
   bool hashed = false;
-  __device__ __forceinline__ void add(long long sum, int L, uint64_t key) {
+  __device__ __forceinline__ void add(long long sum, int L, const unsigned long long* __restrict__ hv) {
     if (sum > s) {
       s = sum;
       l = L;
       hashed = false;
     } else if (sum == s) {
-      if (!hashed) { h = tie_hash(key, l); hashed = true; }
-      unsigned long long hl = tie_hash(key, L);
+      if (!hashed) { h = __ldg(hv + l); hashed = true; }
+      unsigned long long hl = __ldg(hv + L);
       if (hl > h || (hl == h && L < l)) { l = L; h = hl; }
     }
   }
-  __device__ __forceinline__ Cand done(uint64_t key) {
-    if (!hashed && s >= 0) h = tie_hash(key, l);
+  __device__ __forceinline__ Cand done(const unsigned long long* __restrict__ hv) {
+    if (!hashed && s >= 0) h = __ldg(hv + l);
     return Cand{s, h, l};
   }
 };
@@ -157,7 +174,7 @@ template <typename WT, typename ACC, bool FIRST, int CAP, bool LISTED>
 __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
     int64_t n, const int32_t* __restrict__ list, const int* __restrict__ count_ptr,
     const int64_t* __restrict__ off, const int32_t* __restrict__ adj, const WT* __restrict__ w,
-    const int32_t* __restrict__ lab, int32_t* __restrict__ lab_out, uint64_t key) {
+    const int32_t* __restrict__ lab, int32_t* __restrict__ lab_out, const unsigned long long* __restrict__ hv) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ long long s_w[kWarpsPerBlock][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -181,7 +198,7 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
     if (d <= 32) {
       // one chunk: the group sums are final, no table needed
       Chunk c = load_chunk<WT, kModeLP, FIRST>(beg + lane, end, adj, w, lab, 0, sw, lane);
-      Cand cd = c.leader ? Cand{c.sum, tie_hash(key, c.k), c.k} : Cand{-1LL, 0ULL, INT_MAX};
+      Cand cd = c.leader ? Cand{c.sum, __ldg(hv + c.k), c.k} : Cand{-1LL, 0ULL, INT_MAX};
       cd = warp_best(cd);
       if (lane == 0) lab_out[v] = cd.l;
       continue;
@@ -199,11 +216,11 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
     LaneBest lb;
     for (int i = lane; i < created; i += 32) {
       const int slot = slots[i];
-      lb.add((long long)tv[slot], tk[slot], key);
+      lb.add((long long)tv[slot], tk[slot], hv);
       tk[slot] = kEmptyKey;
       tv[slot] = 0;
     }
-    Cand cd = warp_best(lb.done(key));
+    Cand cd = warp_best(lb.done(hv));
     if (lane == 0) lab_out[v] = cd.l;
     __syncwarp();
   }
@@ -216,8 +233,8 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
 template <typename WT>
 __device__ __forceinline__ void first_scan(LaneBest& lb, int64_t a, int64_t end, int step,
                                            const int32_t* __restrict__ adj, const WT* __restrict__ w,
-                                           uint64_t key) {
-  for (int64_t e = a; e < end; e += step) lb.add(ldw(w, e), __ldg(adj + e), key);
+                                           const unsigned long long* __restrict__ hv) {
+  for (int64_t e = a; e < end; e += step) lb.add(ldw(w, e), __ldg(adj + e), hv);
 }
 
 template <typename WT>
@@ -225,7 +242,8 @@ __global__ void __launch_bounds__(kAggThreads) lp_first_simple_k(int64_t n, int 
                                                                  const int64_t* __restrict__ off,
                                                                  const int32_t* __restrict__ adj,
                                                                  const WT* __restrict__ w,
-                                                                 int32_t* __restrict__ lab_out, uint64_t key) {
+                                                                 int32_t* __restrict__ lab_out,
+                                                                 const unsigned long long* __restrict__ hv) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
@@ -236,8 +254,8 @@ __global__ void __launch_bounds__(kAggThreads) lp_first_simple_k(int64_t n, int 
       continue;
     }
     LaneBest lb;
-    first_scan(lb, beg + lane, end, 32, adj, w, key);
-    Cand cd = warp_best(lb.done(key));
+    first_scan(lb, beg + lane, end, 32, adj, w, hv);
+    Cand cd = warp_best(lb.done(hv));
     if (lane == 0) lab_out[v] = cd.l;
   }
 }
@@ -249,15 +267,15 @@ __global__ void __launch_bounds__(kAggThreads) lp_first_simple_block_k(const int
                                                                        const int32_t* __restrict__ adj,
                                                                        const WT* __restrict__ w,
                                                                        int32_t* __restrict__ lab_out,
-                                                                       uint64_t key) {
+                                                                       const unsigned long long* __restrict__ hv) {
   __shared__ Cand s_best[kWarpsPerBlock];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int count = *count_ptr;
   for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
     const int32_t v = list[idx];
     LaneBest lb;
-    first_scan(lb, off[v] + threadIdx.x, off[v + 1], kAggThreads, adj, w, key);
-    Cand cd = warp_best(lb.done(key));
+    first_scan(lb, off[v] + threadIdx.x, off[v + 1], kAggThreads, adj, w, hv);
+    Cand cd = warp_best(lb.done(hv));
     if (lane == 0) s_best[wib] = cd;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -270,35 +288,57 @@ __global__ void __launch_bounds__(kAggThreads) lp_first_simple_block_k(const int
   }
 }
 
-// Pre-merge without a table: each 32-entry chunk's groups are written out directly
-// (the sort that follows merges equal keys across chunks and across vertices).  A warp
-// per vertex of length <= MAXD, a block per listed longer vertex.
+// Pre-merge without a table: within each 32-entry chunk the warp walks the distinct
+// foreign cluster ids (a chunk touches few of them: most neighbours share v's own
+// cluster), summing each one's weight with a ballot (unit weights) or a warp sum, and
+// the first lane holding the id writes the pair; the sort that follows merges equal
+// ids across chunks and across vertices.  `next_slot` yields the output position.
+template <typename WT, typename SLOT>
+__device__ __forceinline__ void emit_chunk(int64_t e, int64_t end, const int32_t* __restrict__ adj,
+                                           const WT* __restrict__ w, const int32_t* __restrict__ cid, int32_t own,
+                                           int lane, int32_t* __restrict__ tkey, long long* __restrict__ tval,
+                                           SLOT next_slot) {
+  int32_t k = -1;
+  long long wt = 0;
+  bool use = false;
+  if (e < end) {
+    k = __ldg(cid + __ldg(adj + e));
+    use = k != own;
+    wt = ldw(w, e);
+  }
+  unsigned todo = __ballot_sync(0xffffffffu, use);
+  while (todo) {
+    const int leader = __ffs(todo) - 1;
+    const int32_t key = __shfl_sync(0xffffffffu, k, leader);
+    const bool mine = use && k == key;
+    const unsigned peers = __ballot_sync(0xffffffffu, mine);
+    long long sum;
+    if (std::is_same<WT, UnitW>::value) sum = __popc(peers);
+    else sum = warp_sum(mine ? wt : 0LL);
+    const int64_t j = next_slot(leader);
+    if (lane == leader) {
+      tkey[j] = key;
+      tval[j] = sum;
+    }
+    todo &= ~peers;
+  }
+}
+
 template <typename WT>
 __global__ void __launch_bounds__(kAggThreads) emit_warp_k(int64_t n, int maxd, const int64_t* __restrict__ off,
                                                            const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                            const int32_t* __restrict__ cid, int32_t* __restrict__ tkey,
                                                            long long* __restrict__ tval, int32_t* __restrict__ cnt) {
-  __shared__ long long s_w[kWarpsPerBlock][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  long long* sw = s_w[wib];
   const int64_t warps = (int64_t)gridDim.x * kWarpsPerBlock;
   for (int64_t v = (int64_t)blockIdx.x * kWarpsPerBlock + wib; v < n; v += warps) {
     const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
     if (end - beg > maxd) continue;
     const int32_t own = __ldg(cid + v);
-    int made = 0;
-    if (own >= 0) {
-      for (int64_t base = beg; base < end; base += 32) {
-        Chunk c = load_chunk<WT, kModeEmit, false>(base + lane, end, adj, w, cid, own, sw, lane);
-        const unsigned bal = __ballot_sync(0xffffffffu, c.leader);
-        if (c.leader) {
-          const int64_t j = beg + made + __popc(bal & ((1u << lane) - 1u));
-          tkey[j] = c.k;
-          tval[j] = c.sum;
-        }
-        made += __popc(bal);
-      }
-    }
+    int made = 0;  // warp-uniform
+    if (own >= 0)
+      for (int64_t base = beg; base < end; base += 32)
+        emit_chunk(base + lane, end, adj, w, cid, own, lane, tkey, tval, [&](int) { return beg + made++; });
     if (lane == 0) cnt[v] = made;
   }
 }
@@ -311,10 +351,8 @@ __global__ void __launch_bounds__(kAggThreads) emit_block_k(const int32_t* __res
                                                             const WT* __restrict__ w, const int32_t* __restrict__ cid,
                                                             int32_t* __restrict__ tkey, long long* __restrict__ tval,
                                                             int32_t* __restrict__ cnt) {
-  __shared__ long long s_w[kWarpsPerBlock][32];
   __shared__ int s_made;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  long long* sw = s_w[wib];
   const int count = *count_ptr;
   for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
     const int32_t v = list[idx];
@@ -322,20 +360,13 @@ __global__ void __launch_bounds__(kAggThreads) emit_block_k(const int32_t* __res
     const int32_t own = cid[v];
     if (threadIdx.x == 0) s_made = 0;
     __syncthreads();
-    if (own >= 0) {
-      for (int64_t base = beg + 32 * wib; base < end; base += 32 * kWarpsPerBlock) {
-        Chunk c = load_chunk<WT, kModeEmit, false>(base + lane, end, adj, w, cid, own, sw, lane);
-        const unsigned bal = __ballot_sync(0xffffffffu, c.leader);
-        int at = 0;
-        if (lane == 0 && bal) at = atomicAdd(&s_made, __popc(bal));
-        at = __shfl_sync(0xffffffffu, at, 0);
-        if (c.leader) {
-          const int64_t j = beg + at + __popc(bal & ((1u << lane) - 1u));
-          tkey[j] = c.k;
-          tval[j] = c.sum;
-        }
-      }
-    }
+    if (own >= 0)
+      for (int64_t base = beg + 32 * wib; base < end; base += 32 * kWarpsPerBlock)
+        emit_chunk(base + lane, end, adj, w, cid, own, lane, tkey, tval, [&](int leader) {
+          int at = 0;
+          if (lane == leader) at = atomicAdd(&s_made, 1);
+          return beg + __shfl_sync(0xffffffffu, at, leader);
+        });
     __syncthreads();
     if (threadIdx.x == 0) cnt[v] = s_made;
     __syncthreads();
@@ -349,8 +380,8 @@ template <typename WT, typename ACC, bool FIRST, bool GLOBAL>
 __global__ void __launch_bounds__(kAggThreads) lp_block_k(
     const int32_t* __restrict__ list, const int* __restrict__ count_ptr, const int64_t* __restrict__ off,
     const int32_t* __restrict__ adj, const WT* __restrict__ w, const int32_t* __restrict__ lab,
-    int32_t* __restrict__ lab_out, uint64_t key, int32_t* __restrict__ gkeys, long long* __restrict__ gvals,
-    int64_t gcap) {
+    int32_t* __restrict__ lab_out, const unsigned long long* __restrict__ hv, int32_t* __restrict__ gkeys,
+    long long* __restrict__ gvals, int64_t gcap) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ Cand s_best[kWarpsPerBlock];
   __shared__ long long s_w[kWarpsPerBlock][32];
@@ -386,12 +417,12 @@ __global__ void __launch_bounds__(kAggThreads) lp_block_k(
     for (int64_t i = threadIdx.x; i < cap; i += kAggThreads) {
       const int L = tk[i];
       if (L != kEmptyKey) {
-        lb.add((long long)tv[i], L, key);
+        lb.add((long long)tv[i], L, hv);
         tk[i] = kEmptyKey;
         tv[i] = 0;
       }
     }
-    Cand cd = warp_best(lb.done(key));
+    Cand cd = warp_best(lb.done(hv));
     if (lane == 0) s_best[wib] = cd;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -423,7 +454,7 @@ constexpr size_t warp_smem() {
 
 template <typename WT, typename ACC, bool FIRST>
 void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* lab, int32_t* lab_out,
-               uint64_t key, cudaStream_t s) {
+               const unsigned long long* key, cudaStream_t s) {
   const WT* w = (const WT*)g.w;
   if (FIRST && g.simple) {
     lp_first_simple_k<WT><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
@@ -495,7 +526,7 @@ void launch_emit(const GraphView& g, const Bins& b, const int32_t* cid, int32_t*
 // Unit weights accumulate in 32 bits (a sum never exceeds the list length); stored
 // weights accumulate in 64 bits.
 void lp_round(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* lab_in,
-              int32_t* lab_out, uint64_t key, cudaStream_t s) {
+              int32_t* lab_out, const unsigned long long* key, cudaStream_t s) {
   if (g.n <= 0) return;
   const bool first = lab_in == nullptr;
   if (g.unit) {

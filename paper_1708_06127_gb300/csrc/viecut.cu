@@ -69,7 +69,7 @@ enum Phase { kPhLP = 0, kPhContract, kPhPR, kPhNOI, kPhOther, kPhCount };
 struct Workspace {
   cudaStream_t s = nullptr;
   // vertex-sized
-  Buf deg, labA, labB, map0, cidT, cur1, side1, flags, rank, cnt, pos, scan64, scan32;
+  Buf deg, labA, labB, map0, cidT, cur1, side1, flags, rank, cnt, pos, scan64, scan32, hv;
   Buf partner, pw, parent, mlist, blist, glist, bcounts, noi_r, noi_seen;
   // entry-sized
   Buf tmpK, tmpV;
@@ -116,6 +116,7 @@ struct Workspace {
     deg.ensure_n<long long>(n);
     labA.ensure_n<int32_t>(n);
     labB.ensure_n<int32_t>(n);
+    hv.ensure_n<unsigned long long>(n);
     map0.ensure_n<int32_t>(n);
     cidT.ensure_n<int32_t>(n);
     cur1.ensure_n<int32_t>(n);
@@ -210,10 +211,11 @@ struct Workspace {
   void lp_rounds(const GraphView& g, uint64_t key, int rounds, int32_t** out_labels, int32_t* all_out) {
     int32_t* in = nullptr;
     int32_t* bufs[2] = {labA.as<int32_t>(), labB.as<int32_t>()};
+    hash_table(g.n, key, nullptr, nullptr, hv.as<unsigned long long>(), s);
     for (int r = 0; r < rounds; ++r) {
       int32_t* out = bufs[r & 1];
       cudaEvent_t a = mark();
-      lp_round(g, bins, gt, in, out, key, s);
+      lp_round(g, bins, gt, in, out, hv.as<unsigned long long>(), s);
       if (timing) {
         lp_spans.push_back({a, mark()});
         long long gather = in ? 4 : 0;
@@ -890,8 +892,9 @@ int viecut_step_lp(viecut_graph* g, const int32_t* lab_in, uint64_t key, int32_t
     in = tmp.ensure_n<int32_t>(v.n);
     VC_CUDA(cudaMemcpyAsync(in, lab_in, sizeof(int32_t) * v.n, cudaMemcpyHostToDevice, c.s));
     int32_t* bufs[2] = {c.ws->labA.as<int32_t>(), c.ws->labB.as<int32_t>()};
+    vc::hash_table(v.n, key, nullptr, nullptr, c.ws->hv.as<unsigned long long>(), c.s);
     for (int r = 0; r < rounds; ++r) {
-      vc::lp_round(v, c.ws->bins, c.ws->gt, in, bufs[r & 1], key, c.s);
+      vc::lp_round(v, c.ws->bins, c.ws->gt, in, bufs[r & 1], c.ws->hv.as<unsigned long long>(), c.s);
       VC_CUDA(cudaMemcpyAsync(lab_out + (int64_t)r * v.n, bufs[r & 1], sizeof(int32_t) * v.n, cudaMemcpyDeviceToHost, c.s));
       in = bufs[r & 1];
     }
