@@ -153,6 +153,42 @@ int viecut_step_pr_b(viecut_graph* g, int64_t lambda_hat, int32_t* labels, int32
 /* One Nagamochi-Ono-Ibaraki round (Sec. 3) with bound lambda_hat: labels[n] as above. */
 int viecut_step_noi_round(viecut_graph* g, int64_t lambda_hat, int32_t* labels, int32_t* changed);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent graphs solved together (same seed and options for all).
+ * The graphs are laid out as one disjoint union on the device; each graph follows its
+ * own sequence of steps (levels, Padberg-Rinaldi runs, exact step) and the union is
+ * contracted once per super-step for all of them, so every graph's result is bit for
+ * bit the result viecut_run gives for it alone.
+ * ------------------------------------------------------------------------- */
+typedef struct viecut_graph_desc {
+  const int64_t* offsets; /* host, n+1 */
+  const int32_t* adj;     /* host, m */
+  const int32_t* weights; /* host, m, >= 1 */
+  int64_t n, m;           /* vertices (>= 2), directed entries */
+} viecut_graph_desc;
+
+typedef struct viecut_batch_stats {
+  double ms_total;         /* device time of the last viecut_batch_run */
+  int64_t super_steps;     /* lock-step rounds the batch needed */
+  int64_t kernel_launches; /* kernels launched by the last run */
+  int64_t graphs, vertices, entries;
+} viecut_batch_stats;
+
+typedef struct viecut_batch viecut_batch;
+
+/* Copies k host graphs to the device as one union (the caller keeps its arrays).
+ * opts as for viecut_create (validate 2 acts as 1).  EINVAL names the bad graph. */
+int viecut_batch_create(viecut_batch** b, const viecut_graph_desc* graphs, int32_t k, const viecut_opts* opts);
+/* Solves all graphs: cut_values[k] (host); side_bits (host, may be NULL) receives the
+ * graphs' bitmaps back to back, graph g's ceil(n_g/64) words after those of graphs
+ * 0..g-1 (viecut_batch_side_words gives the total). */
+int viecut_batch_run(viecut_batch* b, uint64_t seed, int32_t lp_iters, int64_t* cut_values, uint64_t* side_bits);
+int viecut_batch_side_words(const viecut_batch* b, int64_t* words);
+/* Contraction trace of graph g in the last run (as viecut_get_trace). */
+int viecut_batch_get_trace(const viecut_batch* b, int32_t g, viecut_step* steps, int64_t cap, int64_t* len);
+int viecut_batch_get_stats(const viecut_batch* b, viecut_batch_stats* stats);
+int viecut_batch_destroy(viecut_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -49,6 +49,16 @@ class viecut_stats(ctypes.Structure):
                 ("trace_len", ctypes.c_int64), ("lp_bytes", ctypes.c_int64)]
 
 
+class viecut_graph_desc(ctypes.Structure):
+    _fields_ = [("offsets", ctypes.c_void_p), ("adj", ctypes.c_void_p), ("weights", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("m", ctypes.c_int64)]
+
+
+class viecut_batch_stats(ctypes.Structure):
+    _fields_ = [("ms_total", ctypes.c_double), ("super_steps", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("graphs", ctypes.c_int64), ("vertices", ctypes.c_int64), ("entries", ctypes.c_int64)]
+
+
 class viecut_step(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("n", ctypes.c_int64),
                 ("nnz", ctypes.c_int64), ("lambda_hat", ctypes.c_int64)]
@@ -78,6 +88,12 @@ SIGNATURES = [
     ("viecut_step_pr_a", ctypes.c_int, [_vp, _i64, _vp, _vp]),
     ("viecut_step_pr_b", ctypes.c_int, [_vp, _i64, _vp, _vp]),
     ("viecut_step_noi_round", ctypes.c_int, [_vp, _i64, _vp, _vp]),
+    ("viecut_batch_create", ctypes.c_int, [_pvp, _vp, _i32, _vp]),
+    ("viecut_batch_run", ctypes.c_int, [_vp, _u64, _i32, _vp, _vp]),
+    ("viecut_batch_side_words", ctypes.c_int, [_vp, _vp]),
+    ("viecut_batch_get_trace", ctypes.c_int, [_vp, _i32, _vp, _i64, _vp]),
+    ("viecut_batch_get_stats", ctypes.c_int, [_vp, _vp]),
+    ("viecut_batch_destroy", ctypes.c_int, [_vp]),
 ]
 
 
@@ -246,6 +262,97 @@ def viecut_step_pr_b(g, lambda_hat):
 
 def viecut_step_noi_round(g, lambda_hat):
     return _step_labels("viecut_step_noi_round", g, lambda_hat)
+
+
+# ----------------------------------------------------------------- batches
+def viecut_batch_create(graphs, opts: viecut_opts | None = None):
+    """graphs: sequence of (offsets int64, adj int32, weights int32) host arrays."""
+    descs = (viecut_graph_desc * len(graphs))()
+    keep = []
+    for i, (off, adj, w) in enumerate(graphs):
+        off = np.ascontiguousarray(off, np.int64)
+        adj = np.ascontiguousarray(adj, np.int32)
+        w = np.ascontiguousarray(w, np.int32)
+        keep.append((off, adj, w))
+        descs[i] = viecut_graph_desc(off.ctypes.data, adj.ctypes.data, w.ctypes.data, off.shape[0] - 1, adj.shape[0])
+    b = ctypes.c_void_p()
+    _check(lib().viecut_batch_create(ctypes.byref(b), descs, len(graphs), ctypes.byref(opts) if opts else None))
+    return b
+
+
+def viecut_batch_side_words(b) -> int:
+    w = ctypes.c_int64()
+    _check(lib().viecut_batch_side_words(b, ctypes.byref(w)))
+    return int(w.value)
+
+
+def viecut_batch_run(b, k: int, seed: int, lp_iters: int, side_bits=None) -> np.ndarray:
+    cuts = np.empty(k, np.int64)
+    _check(lib().viecut_batch_run(b, seed & (2**64 - 1), lp_iters, cuts.ctypes.data, _ptr(side_bits)))
+    return cuts
+
+
+def viecut_batch_get_trace(b, g: int) -> list:
+    cap = 4096
+    buf = (viecut_step * cap)()
+    ln = ctypes.c_int64()
+    _check(lib().viecut_batch_get_trace(b, g, buf, cap, ctypes.byref(ln)))
+    return [(buf[i].kind, buf[i].level, buf[i].n, buf[i].nnz, buf[i].lambda_hat) for i in range(min(cap, ln.value))]
+
+
+def viecut_batch_get_stats(b) -> dict:
+    st = viecut_batch_stats()
+    _check(lib().viecut_batch_get_stats(b, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in viecut_batch_stats._fields_}
+
+
+def viecut_batch_destroy(b):
+    if b:
+        _check(lib().viecut_batch_destroy(b))
+
+
+class Batch:
+    """Owns a batch of graphs; ``run`` returns (cut values, list of side bitmaps)."""
+
+    def __init__(self, graphs, n0: int = 10000, pr_runs_max: int = 8, device: int = 0, stream=None,
+                 validate: int = 1):
+        self.ns = [int(np.asarray(g[0]).shape[0] - 1) for g in graphs]
+        o = viecut_opts_init(n0=n0, pr_runs_max=pr_runs_max, device=device, stream=stream, validate=validate)
+        self.b = viecut_batch_create(graphs, o)
+        self.words = viecut_batch_side_words(self.b)
+
+    def run(self, seed: int = 1, lp_iters: int = 2):
+        bits = np.zeros(max(1, self.words), np.uint64)
+        cuts = viecut_batch_run(self.b, len(self.ns), seed, lp_iters, bits)
+        out, at = [], 0
+        for n in self.ns:
+            w = (n + 63) // 64
+            out.append(bits[at:at + w].copy())
+            at += w
+        return cuts, out
+
+    def trace(self, g: int) -> list:
+        return viecut_batch_get_trace(self.b, g)
+
+    def stats(self) -> dict:
+        return viecut_batch_get_stats(self.b)
+
+    def close(self):
+        if self.b:
+            viecut_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ----------------------------------------------------------------- convenience

@@ -12,7 +12,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libviecut.so")
 
-SOURCES = ["prims.cu", "lp.cu", "contract.cu", "bound.cu", "pr.cu", "noi.cu", "viecut.cu"]
+SOURCES = ["prims.cu", "lp.cu", "contract.cu", "bound.cu", "pr.cu", "noi.cu", "viecut.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -10,13 +10,13 @@ namespace vc {
 
 __global__ void mark_labels_k(const int32_t* __restrict__ lab, int64_t n, int32_t* __restrict__ flags) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    flags[lab[v]] = 1;
+    if (lab[v] >= 0) flags[lab[v]] = 1;  // label -1: the vertex is dropped (batches)
 }
 
 __global__ void apply_rank_k(const int32_t* __restrict__ lab, int64_t n, const int32_t* __restrict__ rank,
                              int32_t* __restrict__ cid) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    cid[v] = rank[lab[v]];
+    cid[v] = lab[v] >= 0 ? rank[lab[v]] : -1;
 }
 
 void relabel(const int32_t* lab, int64_t n, int32_t* cid, ContractScratch& cs, int* c_dev, cudaStream_t s) {

@@ -1,0 +1,291 @@
+// Host-side engine pieces shared by the single-graph driver and the batch driver:
+// grow-only device buffers and the workspace of device arrays one run needs.
+#pragma once
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "kernels.cuh"
+#include "prims.cuh"
+#include "viecut.h"
+
+namespace vc {
+
+// Records the message of the last failure on this thread (viecut_last_error).
+void set_last_error(const std::string& msg);
+
+// ------------------------------------------------------------- device buffers
+struct Buf {
+  void* p = nullptr;
+  size_t cap = 0;
+  Buf() = default;
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  ~Buf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  void* ensure(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (bytes > cap) {
+      release();
+      cudaError_t e = cudaMalloc(&p, bytes);
+      if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        throw Error{VIECUT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e)};
+      }
+      cap = bytes;
+    }
+    return p;
+  }
+  template <typename T>
+  T* ensure_n(int64_t count) { return (T*)ensure(sizeof(T) * (size_t)(count > 0 ? count : 1)); }
+  template <typename T>
+  T* as() const { return (T*)p; }
+};
+
+struct Counters {
+  int c;
+  int pad;
+  long long pairs;
+  int changed;
+  int pad2;
+};
+
+enum Phase { kPhLP = 0, kPhContract, kPhPR, kPhNOI, kPhOther, kPhCount };
+
+// Everything one run needs on the device.
+struct Workspace {
+  cudaStream_t s = nullptr;
+  // vertex-sized
+  Buf deg, labA, labB, map0, cidT, cur1, side1, flags, rank, cnt, pos, scan64, scan32, hv;
+  Buf partner, pw, parent, mlist, blist, glist, bcounts, noi_r, noi_seen;
+  // entry-sized
+  Buf tmpK, tmpV;
+  // pair-sized
+  Buf keysA, keysB, valsA, valsB, hist, heads, hpos, cvT;
+  // coarse graphs (ping-pong)
+  Buf coff[2], cadj[2], cw[2];
+  // global-class tables
+  Buf gkeys, gvals;
+  GlobalTables gt;
+  // exact step
+  Buf M0, M1, curK, sideK;
+  // state
+  Buf state, trace, partial, counters;
+  DevState* h_state = nullptr;
+  Counters* h_counters = nullptr;
+  int trace_cap = 4096;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> spans;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> lp_spans;
+  long long lp_bytes_acc = 0, lp_nnz_acc = 0, lp_n_acc = 0;
+
+  Workspace() {
+    VC_CUDA(cudaMallocHost(&h_state, sizeof(DevState)));
+    VC_CUDA(cudaMallocHost(&h_counters, sizeof(Counters)));
+    state.ensure(sizeof(DevState));
+    trace.ensure_n<TraceStep>(trace_cap);
+    partial.ensure_n<long long>(2 * 1024);
+    counters.ensure(sizeof(Counters));
+    bcounts.ensure_n<int>(8);
+  }
+  ~Workspace() {
+    if (h_state) cudaFreeHost(h_state);
+    if (h_counters) cudaFreeHost(h_counters);
+    for (auto e : ev_pool) cudaEventDestroy(e);
+  }
+  DevState* st() { return state.as<DevState>(); }
+  Counters* ctr() { return counters.as<Counters>(); }
+
+  void ensure_vertices(int64_t n) {
+    deg.ensure_n<long long>(n);
+    labA.ensure_n<int32_t>(n);
+    labB.ensure_n<int32_t>(n);
+    hv.ensure_n<unsigned long long>(n);
+    map0.ensure_n<int32_t>(n);
+    cidT.ensure_n<int32_t>(n);
+    cur1.ensure_n<int32_t>(n);
+    side1.ensure_n<unsigned char>(n);
+    flags.ensure_n<int32_t>(n);
+    rank.ensure_n<int32_t>(n);
+    cnt.ensure_n<int32_t>(n);
+    pos.ensure_n<long long>(n + 1);
+    partner.ensure_n<int32_t>(n);
+    pw.ensure_n<long long>(n);
+    parent.ensure_n<int32_t>(n);
+    mlist.ensure_n<int32_t>(n);
+    blist.ensure_n<int32_t>(n);
+    glist.ensure_n<int32_t>(n);
+    scan32.ensure_n<int>(scan_scratch_elems(n) + 1);
+  }
+  void ensure_entries(int64_t nnz, int64_t n) {
+    tmpK.ensure_n<int32_t>(nnz);
+    tmpV.ensure_n<long long>(nnz);
+    scan64.ensure_n<long long>(scan_scratch_elems(std::max(nnz, n)) + 1);
+  }
+  void ensure_noi() {
+    M0.ensure_n<long long>((int64_t)kDenseMax * kDenseMax);
+    M1.ensure_n<long long>((int64_t)kDenseMax * kDenseMax);
+    curK.ensure_n<int32_t>(kDenseMax);
+    sideK.ensure_n<unsigned char>(kDenseMax);
+  }
+
+  void sync() { VC_CUDA(cudaStreamSynchronize(s)); }
+  void read_state() {
+    VC_CUDA(cudaMemcpyAsync(h_state, st(), sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    VC_CUDA(cudaMemcpyAsync(h_counters, ctr(), sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    sync();
+  }
+
+  // ---------------------------------------------------------------- timing
+  cudaEvent_t ev() {
+    if (ev_used == ev_pool.size()) {
+      cudaEvent_t e;
+      VC_CUDA(cudaEventCreate(&e));
+      ev_pool.push_back(e);
+    }
+    return ev_pool[ev_used++];
+  }
+  cudaEvent_t mark() {
+    if (!timing) return nullptr;
+    cudaEvent_t e = ev();
+    VC_CUDA(cudaEventRecord(e, s));
+    return e;
+  }
+  void span(int ph, cudaEvent_t a) {
+    if (!timing) return;
+    spans.push_back({ph, {a, mark()}});
+  }
+  void reset_timing() {
+    ev_used = 0;
+    spans.clear();
+    lp_spans.clear();
+    lp_bytes_acc = lp_nnz_acc = lp_n_acc = 0;
+  }
+
+  // ---------------------------------------------------------------- steps
+  Bins bins;
+  bool bins_valid = false;
+
+  void build_bins(const GraphView& g) {
+    bins.mid_list = mlist.as<int32_t>();
+    bins.block_list = blist.as<int32_t>();
+    bins.global_list = glist.as<int32_t>();
+    bins.counts = bcounts.as<int>();
+    bins_build(g, bins, s);
+    int hc[4];
+    VC_CUDA(cudaMemcpyAsync(hc, bins.counts, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    sync();
+    bins.h_mid = hc[0];
+    bins.h_block = hc[1];
+    bins.h_global = hc[2];
+    bins.h_maxdeg = hc[3];
+    if (bins.h_global > 0) {
+      int64_t cap = global_table_cap(bins.h_maxdeg);
+      int blocks = std::min(bins.h_global, kSMs);
+      // keep the scratch under ~2 GiB
+      while (blocks > 1 && (int64_t)blocks * cap * 12 > (int64_t(2) << 30)) blocks /= 2;
+      gt.keys = gkeys.ensure_n<int32_t>(blocks * cap);
+      gt.vals = gvals.ensure_n<long long>(blocks * cap);
+      gt.cap = cap;
+      gt.blocks = blocks;
+    }
+    bins_valid = true;
+  }
+
+  void lp_rounds(const GraphView& g, uint64_t key, int rounds, int32_t** out_labels, int32_t* all_out) {
+    int32_t* in = nullptr;
+    int32_t* bufs[2] = {labA.as<int32_t>(), labB.as<int32_t>()};
+    hash_table(g.n, key, nullptr, nullptr, nullptr, hv.as<unsigned long long>(), s);
+    for (int r = 0; r < rounds; ++r) {
+      int32_t* out = bufs[r & 1];
+      cudaEvent_t a = mark();
+      lp_round(g, bins, gt, in, out, hv.as<unsigned long long>(), s);
+      if (timing) {
+        lp_spans.push_back({a, mark()});
+        long long gather = in ? 4 : 0;
+        lp_bytes_acc += 8 * (g.n + 1) + g.nnz * (4 + (g.unit ? 0 : g.wbytes) + gather) + 4 * g.n;
+        lp_nnz_acc += g.nnz;
+        lp_n_acc += g.n;
+      }
+      if (all_out)
+        VC_CUDA(cudaMemcpyAsync(all_out + (int64_t)r * g.n, out, sizeof(int32_t) * g.n, cudaMemcpyDeviceToHost, s));
+      in = out;
+    }
+    *out_labels = in;
+  }
+
+  // Contracts g by labels into the coarse buffer `slot`; cid_out[n] receives the map.
+  // Returns the coarse view; h_counters holds c and the pair count afterwards.
+  GraphView contract(const GraphView& g, const int32_t* labels, int32_t* cid_out, int slot) {
+    if (!bins_valid) build_bins(g);
+    ContractScratch cs;
+    cs.flags = flags.as<int32_t>();
+    cs.rank = rank.as<int32_t>();
+    cs.cnt = cnt.as<int32_t>();
+    cs.pos = pos.as<long long>();
+    cs.tmp_key = tmpK.as<int32_t>();
+    cs.tmp_val = tmpV.as<long long>();
+    cs.scan_scr = scan64.as<long long>();
+    cs.scan_scr32 = scan32.as<int>();
+    relabel(labels, g.n, cid_out, cs, &ctr()->c, s);
+    emit_cross(g, bins, gt, cid_out, cs.tmp_key, cs.tmp_val, cs.cnt, s);
+    exclusive_scan<int, long long>(cs.cnt, cs.pos, g.n, &ctr()->pairs, cs.scan_scr, s);
+    VC_CUDA(cudaMemcpyAsync(h_counters, ctr(), sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    sync();
+    const int64_t c = h_counters->c;
+    const int64_t P = h_counters->pairs;
+    int bits = ceil_log2(c);
+    if (bits < 1) bits = 1;
+    auto* kA = keysA.ensure_n<unsigned long long>(P);
+    auto* kB = keysB.ensure_n<unsigned long long>(P);
+    auto* vA = valsA.ensure_n<long long>(P);
+    auto* vB = valsB.ensure_n<long long>(P);
+    auto* hs = hist.ensure_n<long long>(radix_hist_elems(P));
+    auto* hd = heads.ensure_n<int32_t>(P);
+    auto* hp = hpos.ensure_n<long long>(P + 1);
+    auto* cv = cvT.ensure_n<int32_t>(P);
+    scan64.ensure_n<long long>(scan_scratch_elems(std::max<int64_t>(P, 1)) + 1);
+    build_pairs(g, cid_out, cs, bits, kA, vA, s);
+    radix_sort_pairs(kA, vA, kB, vB, P, 2 * bits, hs, s);
+    int64_t* co = coff[slot].ensure_n<int64_t>(c + 1);
+    int32_t* ca = cadj[slot].ensure_n<int32_t>(P);
+    long long* cwp = cw[slot].ensure_n<long long>(P);
+    reduce_pairs(kA, vA, P, bits, c, hd, hp, scan64.as<long long>(), co, ca, cwp, cv, &st()->nnz, s);
+    GraphView h;
+    h.n = c;
+    h.nnz = P;  // upper bound until the state is read
+    h.off = co;
+    h.adj = ca;
+    h.w = cwp;
+    h.wbytes = 8;
+    h.simple = true;
+    bins_valid = false;
+    return h;
+  }
+};
+
+}  // namespace vc
+
+#define VC_API_BEGIN try {
+#define VC_API_END                                   \
+  }                                                  \
+  catch (const vc::Error& e) {                       \
+    vc::set_last_error(e.msg);                       \
+    return e.code;                                   \
+  }                                                  \
+  catch (const std::bad_alloc&) {                    \
+    vc::set_last_error("host allocation failed");    \
+    return VIECUT_ENOMEM;                            \
+  }                                                  \
+  return VIECUT_OK;

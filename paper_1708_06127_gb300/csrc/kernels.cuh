@@ -16,6 +16,18 @@ struct GraphView {
   int wbytes = 8;
   bool unit = false;
   bool simple = false;  // every list strictly increasing (no parallel entries)
+  // batches: label propagation touches only vertices v with vact[v] != 0 (null: all)
+  const unsigned char* vact = nullptr;
+};
+
+// Per-graph view of a batch (a disjoint union of graphs): vertex v belongs to graph
+// gid[v]; the passes act only on graphs with gact[g] != 0, read their bound from
+// glam[g] and report merges in gchanged[g].  Null in single-graph runs.
+struct BatchCtx {
+  const int32_t* gid = nullptr;
+  const long long* glam = nullptr;
+  const unsigned char* gact = nullptr;
+  int* gchanged = nullptr;
 };
 
 // Weight loads for the three storage cases (UnitW: implicit weight 1).
@@ -56,8 +68,9 @@ struct GlobalTables {
 int64_t global_table_cap(int maxdeg);
 
 // Tie-break table of a level: hv[L] = mix64(key XOR L) for every label L < n.  With
-// gid/gkey (batches) the key of label L is gkey[gid[L]].
-void hash_table(int64_t n, uint64_t key, const int32_t* gid, const unsigned long long* gkey,
+// gid/gkey/gbase (batches) label L of graph g = gid[L] is hashed as mix64(gkey[g] XOR
+// (L - gbase[g])), its id inside its own graph.
+void hash_table(int64_t n, uint64_t key, const int32_t* gid, const unsigned long long* gkey, const long long* gbase,
                 unsigned long long* hv, cudaStream_t s);
 
 // One synchronous label-propagation round; lab_in == nullptr means the identity
@@ -114,11 +127,14 @@ void trace_push(DevState* st, TraceStep* trace, int cap, int kind, int level, cu
 // ------------------------------------------------------------------ Padberg-Rinaldi
 void pr_partners(const GraphView& g, int32_t* partner, long long* pw, long long* deg, cudaStream_t s);
 // Pass A: PR1 edges and PR2 designated-partner edges, union-find, roots -> labels.
+// With a batch context only active graphs are touched and `labels` must already
+// hold the identity for every other vertex.
 void pr_pass_a(const GraphView& g, const int32_t* partner, const long long* pw, const long long* deg,
-               const DevState* st, int32_t* parent, int32_t* labels, int* changed, cudaStream_t s);
+               const DevState* st, int32_t* parent, int32_t* labels, int* changed, cudaStream_t s,
+               const BatchCtx* bc = nullptr);
 // Pass B: PR3 / PR4 on mutual partner pairs.
 void pr_pass_b(const GraphView& g, const int32_t* partner, const long long* pw, const long long* deg,
-               const DevState* st, int32_t* labels, int* changed, cudaStream_t s);
+               const DevState* st, int32_t* labels, int* changed, cudaStream_t s, const BatchCtx* bc = nullptr);
 
 // ------------------------------------------------------------------ NOI
 constexpr int kDenseMax = 512;
@@ -129,4 +145,29 @@ void noi_dense(const GraphView& g, long long* M0, long long* M1, int32_t* curK, 
 // One round of the maximum-adjacency scan on a larger graph; labels = union-find roots.
 void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, unsigned char* seen,
                       int32_t* parent, int32_t* labels, int* changed, cudaStream_t s);
+
+// Per-graph result arrays of a batch's exact step (indexed by graph; trace holds
+// trace_cap steps per graph).
+struct BatchNoi {
+  long long* lam;
+  int* best_kind;
+  long long* n_out;
+  long long* nnz_out;
+  long long* dmin;
+  long long* argmin;
+  int* trace_len;
+  TraceStep* trace;
+  int trace_cap;
+  const int* level;
+};
+// Dense rounds for the listed graphs of a union u (vertex range [vbase[g], +nv[g])),
+// `blocks` persistent blocks with 2 x mcap matrix entries and kDenseMax curK each;
+// sideK holds kDenseMax bytes per graph.
+void noi_dense_batch(const GraphView& u, const int32_t* list, int count, const long long* vbase, const long long* nv,
+                     long long* M, int64_t mcap, int blocks, int32_t* curK, unsigned char* sideK, const BatchNoi& bn,
+                     cudaStream_t s);
+// One sparse round for each listed graph; labels and gchanged written per graph.
+void noi_round_batch(const GraphView& u, const int32_t* list, int count, const long long* vbase, const long long* nv,
+                     const long long* glam, long long* r, unsigned char* seen, int32_t* parent, int32_t* labels,
+                     int* gchanged, cudaStream_t s);
 }  // namespace vc

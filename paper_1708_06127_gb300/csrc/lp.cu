@@ -53,17 +53,23 @@ void bins_build(const GraphView& g, Bins& b, cudaStream_t s) {
 }
 
 __global__ void hash_table_k(int64_t n, uint64_t key, const int32_t* __restrict__ gid,
-                             const unsigned long long* __restrict__ gkey, unsigned long long* __restrict__ hv) {
+                             const unsigned long long* __restrict__ gkey, const long long* __restrict__ gbase,
+                             unsigned long long* __restrict__ hv) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = gid ? gkey[gid[v]] : key;
-    hv[v] = tie_hash(k, (int32_t)v);
+    if (gid) {
+      // batches: the label is hashed by its id inside its own graph
+      const int g = gid[v];
+      hv[v] = tie_hash(gkey[g], (int32_t)(v - gbase[g]));
+    } else {
+      hv[v] = tie_hash(key, (int32_t)v);
+    }
   }
 }
 
-void hash_table(int64_t n, uint64_t key, const int32_t* gid, const unsigned long long* gkey,
+void hash_table(int64_t n, uint64_t key, const int32_t* gid, const unsigned long long* gkey, const long long* gbase,
                 unsigned long long* hv, cudaStream_t s) {
   if (n <= 0) return;
-  hash_table_k<<<grid_for(n, 256, kSMs * 8), 256, 0, s>>>(n, key, gid, gkey, hv);
+  hash_table_k<<<grid_for(n, 256, kSMs * 8), 256, 0, s>>>(n, key, gid, gkey, gbase, hv);
   count_launch();
   VC_CHECK_LAUNCH();
 }
@@ -174,7 +180,8 @@ template <typename WT, typename ACC, bool FIRST, int CAP, bool LISTED>
 __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
     int64_t n, const int32_t* __restrict__ list, const int* __restrict__ count_ptr,
     const int64_t* __restrict__ off, const int32_t* __restrict__ adj, const WT* __restrict__ w,
-    const int32_t* __restrict__ lab, int32_t* __restrict__ lab_out, const unsigned long long* __restrict__ hv) {
+    const int32_t* __restrict__ lab, int32_t* __restrict__ lab_out, const unsigned long long* __restrict__ hv,
+    const unsigned char* __restrict__ vact) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ long long s_w[kWarpsPerBlock][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -188,6 +195,7 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
   const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock;
   for (int64_t idx = (int64_t)blockIdx.x * kWarpsPerBlock + wib; idx < total; idx += stride) {
     const int64_t v = LISTED ? (int64_t)list[idx] : idx;
+    if (vact && !vact[v]) continue;
     const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
     const int d = (int)(end - beg);
     if (!LISTED && d > CAP / 2) continue;
@@ -243,10 +251,12 @@ __global__ void __launch_bounds__(kAggThreads) lp_first_simple_k(int64_t n, int 
                                                                  const int32_t* __restrict__ adj,
                                                                  const WT* __restrict__ w,
                                                                  int32_t* __restrict__ lab_out,
-                                                                 const unsigned long long* __restrict__ hv) {
+                                                                 const unsigned long long* __restrict__ hv,
+                                                                 const unsigned char* __restrict__ vact) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    if (vact && !vact[v]) continue;
     const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
     if (end - beg > maxd) continue;
     if (end == beg) {
@@ -267,12 +277,14 @@ __global__ void __launch_bounds__(kAggThreads) lp_first_simple_block_k(const int
                                                                        const int32_t* __restrict__ adj,
                                                                        const WT* __restrict__ w,
                                                                        int32_t* __restrict__ lab_out,
-                                                                       const unsigned long long* __restrict__ hv) {
+                                                                       const unsigned long long* __restrict__ hv,
+                                                                       const unsigned char* __restrict__ vact) {
   __shared__ Cand s_best[kWarpsPerBlock];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int count = *count_ptr;
   for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
     const int32_t v = list[idx];
+    if (vact && !vact[v]) continue;
     LaneBest lb;
     first_scan(lb, off[v] + threadIdx.x, off[v + 1], kAggThreads, adj, w, hv);
     Cand cd = warp_best(lb.done(hv));
@@ -381,7 +393,7 @@ __global__ void __launch_bounds__(kAggThreads) lp_block_k(
     const int32_t* __restrict__ list, const int* __restrict__ count_ptr, const int64_t* __restrict__ off,
     const int32_t* __restrict__ adj, const WT* __restrict__ w, const int32_t* __restrict__ lab,
     int32_t* __restrict__ lab_out, const unsigned long long* __restrict__ hv, int32_t* __restrict__ gkeys,
-    long long* __restrict__ gvals, int64_t gcap) {
+    long long* __restrict__ gvals, int64_t gcap, const unsigned char* __restrict__ vact) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ Cand s_best[kWarpsPerBlock];
   __shared__ long long s_w[kWarpsPerBlock][32];
@@ -404,6 +416,7 @@ __global__ void __launch_bounds__(kAggThreads) lp_block_k(
   const int count = *count_ptr;
   for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
     const int32_t v = list[idx];
+    if (vact && !vact[v]) continue;
     const int64_t beg = off[v], end = off[v + 1];
     const int64_t d = end - beg;
     const int lg = ceil_log2(2 * d);
@@ -458,12 +471,12 @@ void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const 
   const WT* w = (const WT*)g.w;
   if (FIRST && g.simple) {
     lp_first_simple_k<WT><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
-        g.n, kBlockMaxDeg, g.off, g.adj, w, lab_out, key);
+        g.n, kBlockMaxDeg, g.off, g.adj, w, lab_out, key, g.vact);
     count_launch();
     VC_CHECK_LAUNCH();
     if (b.h_global > 0) {
       lp_first_simple_block_k<WT><<<grid_for(b.h_global, 1, kSMs * 4), kAggThreads, 0, s>>>(
-          b.global_list, b.counts + 2, g.off, g.adj, w, lab_out, key);
+          b.global_list, b.counts + 2, g.off, g.adj, w, lab_out, key, g.vact);
       count_launch();
       VC_CHECK_LAUNCH();
     }
@@ -475,7 +488,7 @@ void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const 
     auto kfn = lp_warp_k<WT, ACC, FIRST, CAP, false>;
     set_smem(kfn, smem);
     kfn<<<grid_for(g.n, kWarpsPerBlock * 4, kSMs * 8), kAggThreads, smem, s>>>(g.n, nullptr, nullptr, g.off, g.adj,
-                                                                              w, lab, lab_out, key);
+                                                                              w, lab, lab_out, key, g.vact);
     count_launch();
     VC_CHECK_LAUNCH();
   }
@@ -485,7 +498,7 @@ void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const 
     auto kfn = lp_warp_k<WT, ACC, FIRST, CAP, true>;
     set_smem(kfn, smem);
     kfn<<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 2), kAggThreads, smem, s>>>(0, b.mid_list, b.counts + 0, g.off,
-                                                                              g.adj, w, lab, lab_out, key);
+                                                                              g.adj, w, lab, lab_out, key, g.vact);
     count_launch();
     VC_CHECK_LAUNCH();
   }
@@ -494,14 +507,15 @@ void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const 
     auto kfn = lp_block_k<WT, ACC, FIRST, false>;
     set_smem(kfn, smem);
     kfn<<<grid_for(b.h_block, 1, kSMs * 2), kAggThreads, smem, s>>>(b.block_list, b.counts + 1, g.off, g.adj, w,
-                                                                   lab, lab_out, key, nullptr, nullptr, 0);
+                                                                   lab, lab_out, key, nullptr, nullptr, 0, g.vact);
     count_launch();
     VC_CHECK_LAUNCH();
   }
   if (b.h_global > 0) {
     int grid_g = b.h_global < gt.blocks ? b.h_global : gt.blocks;
     lp_block_k<WT, ACC, FIRST, true><<<grid_g, kAggThreads, 0, s>>>(b.global_list, b.counts + 2, g.off, g.adj, w,
-                                                                    lab, lab_out, key, gt.keys, gt.vals, gt.cap);
+                                                                    lab, lab_out, key, gt.keys, gt.vals, gt.cap,
+                                                                    g.vact);
     count_launch();
     VC_CHECK_LAUNCH();
   }

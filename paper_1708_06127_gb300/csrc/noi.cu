@@ -54,12 +54,27 @@ __device__ __forceinline__ int warp_argmax_unseen(const long long* r, const int*
   return bx;
 }
 
+// Where one graph's exact-step results go: its bound, best-side kind, shape and
+// trace (fields of DevState for single runs, per-graph arrays for batches).
+struct NoiIO {
+  long long* lam;
+  int* best_kind;
+  long long* n_out;
+  long long* nnz_out;
+  long long* dmin;
+  long long* argmin;
+  int* trace_len;
+  TraceStep* trace;
+  int trace_cap;
+  int level;
+};
+
+// All rounds on one graph of n <= kDenseMax vertices, by one block, on a dense matrix.
+// The graph's vertices are [base, base + n) of the CSR (off points at its first row).
 template <typename WT>
-__global__ void __launch_bounds__(kNoiThreads) noi_dense_k(int n, const int64_t* __restrict__ off,
-                                                           const int32_t* __restrict__ adj, const WT* __restrict__ w,
-                                                           long long* M0, long long* M1, int32_t* curK,
-                                                           unsigned char* sideK, DevState* st, TraceStep* trace,
-                                                           int trace_cap, int level) {
+__device__ __forceinline__ void noi_dense_body(int n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                                               const WT* __restrict__ w, int32_t base, long long* M0, long long* M1,
+                                               int32_t* curK, unsigned char* sideK, const NoiIO& io) {
   __shared__ long long r[kDenseMax];
   __shared__ int seen[kDenseMax];
   __shared__ int parent[kDenseMax];
@@ -79,10 +94,10 @@ __global__ void __launch_bounds__(kNoiThreads) noi_dense_k(int n, const int64_t*
   for (int k = tid; k < n; k += T) curK[k] = k;
   __syncthreads();
   for (int v = tid; v < nk; v += T)
-    for (int64_t e = off[v]; e < off[v + 1]; ++e) M[v * nk + adj[e]] += (long long)w[e];
+    for (int64_t e = off[v]; e < off[v + 1]; ++e) M[v * nk + (adj[e] - base)] += (long long)w[e];
   __syncthreads();
   while (nk > 1) {
-    const long long lam = st->lambda_hat;
+    const long long lam = *io.lam;
     for (int k = tid; k < nk; k += T) { r[k] = 0; seen[k] = 0; parent[k] = k; }
     __syncthreads();
     for (int step = 0; step < nk; ++step) {
@@ -172,22 +187,22 @@ __global__ void __launch_bounds__(kNoiThreads) noi_dense_k(int n, const int64_t*
       }
       s_stop = 0;
       s_improved = 0;
-      st->n = nk;
-      st->nnz = tot;
+      *io.n_out = nk;
+      *io.nnz_out = tot;
       if (nk > 1) {
-        st->dmin = bd;
-        st->argmin = bv;
-        if (bd < st->lambda_hat) {
-          st->lambda_hat = bd;
-          st->best_kind = 2;
+        *io.dmin = bd;
+        *io.argmin = bv;
+        if (bd < *io.lam) {
+          *io.lam = bd;
+          *io.best_kind = 2;
           s_improved = 1;
           s_arg = bv;
         }
-        if (st->lambda_hat == 0) s_stop = 1;
+        if (*io.lam == 0) s_stop = 1;
       }
-      int i = st->trace_len;
-      if (i < trace_cap) trace[i] = TraceStep{4, level, (long long)nk, tot, st->lambda_hat};
-      st->trace_len = i + 1;
+      int i = *io.trace_len;
+      if (i < io.trace_cap) io.trace[i] = TraceStep{4, io.level, (long long)nk, tot, *io.lam};
+      *io.trace_len = i + 1;
     }
     __syncthreads();
     if (s_improved) {
@@ -197,6 +212,17 @@ __global__ void __launch_bounds__(kNoiThreads) noi_dense_k(int n, const int64_t*
     __syncthreads();
     if (s_stop) break;
   }
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(kNoiThreads) noi_dense_k(int n, const int64_t* __restrict__ off,
+                                                           const int32_t* __restrict__ adj, const WT* __restrict__ w,
+                                                           long long* M0, long long* M1, int32_t* curK,
+                                                           unsigned char* sideK, DevState* st, TraceStep* trace,
+                                                           int trace_cap, int level) {
+  NoiIO io{&st->lambda_hat, &st->best_kind, &st->n, &st->nnz, &st->dmin, &st->argmin, &st->trace_len,
+           trace, trace_cap, level};
+  noi_dense_body<WT>(n, off, adj, w, 0, M0, M1, curK, sideK, io);
 }
 
 void noi_dense(const GraphView& g, long long* M0, long long* M1, int32_t* curK, unsigned char* sideK,
@@ -211,25 +237,61 @@ void noi_dense(const GraphView& g, long long* M0, long long* M1, int32_t* curK, 
   VC_CHECK_LAUNCH();
 }
 
+// Batches: a persistent grid pulls the listed graphs; each block solves one at a time
+// with its own matrices (mcap entries each).
+template <typename WT>
+__global__ void __launch_bounds__(kNoiThreads) noi_dense_batch_k(const int32_t* __restrict__ list, int count,
+                                                                 const int64_t* __restrict__ off,
+                                                                 const int32_t* __restrict__ adj,
+                                                                 const WT* __restrict__ w, const long long* vbase,
+                                                                 const long long* nv, long long* M, int64_t mcap,
+                                                                 int32_t* curK, unsigned char* sideK, BatchNoi bn) {
+  long long* M0 = M + (int64_t)blockIdx.x * 2 * mcap;
+  long long* M1 = M0 + mcap;
+  int32_t* ck = curK + (int64_t)blockIdx.x * kDenseMax;
+  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    const int g = list[idx];
+    const int32_t base = (int32_t)vbase[g];
+    NoiIO io{bn.lam + g, bn.best_kind + g, bn.n_out + g, bn.nnz_out + g, bn.dmin + g, bn.argmin + g,
+             bn.trace_len + g, bn.trace + (int64_t)g * bn.trace_cap, bn.trace_cap, bn.level[g]};
+    noi_dense_body<WT>((int)nv[g], off + base, adj, w, base, M0, M1, ck, sideK + (int64_t)g * kDenseMax, io);
+    __syncthreads();
+  }
+}
+
+void noi_dense_batch(const GraphView& u, const int32_t* list, int count, const long long* vbase, const long long* nv,
+                     long long* M, int64_t mcap, int blocks, int32_t* curK, unsigned char* sideK, const BatchNoi& bn,
+                     cudaStream_t s) {
+  if (count <= 0) return;
+  if (u.wbytes == 4)
+    noi_dense_batch_k<int32_t><<<blocks, kNoiThreads, 0, s>>>(list, count, u.off, u.adj, (const int32_t*)u.w, vbase,
+                                                               nv, M, mcap, curK, sideK, bn);
+  else
+    noi_dense_batch_k<long long><<<blocks, kNoiThreads, 0, s>>>(list, count, u.off, u.adj, (const long long*)u.w,
+                                                                 vbase, nv, M, mcap, curK, sideK, bn);
+  count_launch();
+  VC_CHECK_LAUNCH();
+}
+
 // ------------------------------------------------------------ sparse single round
 constexpr int kSparseThreads = 1024;
 
+// One round on the vertices [lo, hi) (ids are global: r, seen, parent, labels are
+// indexed by them); returns through *any whether something merged.
 template <typename WT>
-__global__ void __launch_bounds__(kSparseThreads) noi_round_k(int64_t n, const int64_t* __restrict__ off,
-                                                              const int32_t* __restrict__ adj,
-                                                              const WT* __restrict__ w, const DevState* st,
-                                                              long long* r, unsigned char* seen, int32_t* parent,
-                                                              int32_t* labels, int* changed) {
+__device__ __forceinline__ void noi_round_body(int64_t lo, int64_t hi, const int64_t* __restrict__ off,
+                                               const int32_t* __restrict__ adj, const WT* __restrict__ w,
+                                               long long lam, long long* r, unsigned char* seen, int32_t* parent,
+                                               int32_t* labels, int* any_out) {
   __shared__ long long red_r[kSparseThreads / 32];
   __shared__ long long red_x[kSparseThreads / 32];
   __shared__ long long s_x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const long long lam = st->lambda_hat;
-  for (int64_t k = tid; k < n; k += kSparseThreads) { r[k] = 0; seen[k] = 0; parent[k] = (int32_t)k; }
+  for (int64_t k = lo + tid; k < hi; k += kSparseThreads) { r[k] = 0; seen[k] = 0; parent[k] = (int32_t)k; }
   __syncthreads();
-  for (int64_t step = 0; step < n; ++step) {
+  for (int64_t step = lo; step < hi; ++step) {
     long long br = -1, bx = LLONG_MAX;
-    for (int64_t k = tid; k < n; k += kSparseThreads)
+    for (int64_t k = lo + tid; k < hi; k += kSparseThreads)
       if (!seen[k]) {
         long long rv = r[k];
         if (rv > br || (rv == br && k < bx)) { br = rv; bx = k; }
@@ -260,12 +322,22 @@ __global__ void __launch_bounds__(kSparseThreads) noi_round_k(int64_t n, const i
     __syncthreads();
   }
   int any = 0;
-  for (int64_t k = tid; k < n; k += kSparseThreads) {
+  for (int64_t k = lo + tid; k < hi; k += kSparseThreads) {
     int rt = sfind(parent, (int)k);
     labels[k] = rt;
     any |= rt != k;
   }
-  if (__syncthreads_or(any) && tid == 0) atomicOr(changed, 1);
+  if (__syncthreads_or(any) && tid == 0) atomicOr(any_out, 1);
+  __syncthreads();
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(kSparseThreads) noi_round_k(int64_t n, const int64_t* __restrict__ off,
+                                                              const int32_t* __restrict__ adj,
+                                                              const WT* __restrict__ w, const DevState* st,
+                                                              long long* r, unsigned char* seen, int32_t* parent,
+                                                              int32_t* labels, int* changed) {
+  noi_round_body<WT>(0, n, off, adj, w, st->lambda_hat, r, seen, parent, labels, changed);
 }
 
 void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, unsigned char* seen,
@@ -276,6 +348,37 @@ void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, unsi
   else
     noi_round_k<long long><<<1, kSparseThreads, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, st, r, seen,
                                                          parent, labels, changed);
+  count_launch();
+  VC_CHECK_LAUNCH();
+}
+
+// Batches: one round for each listed graph, a block per graph (persistent grid).
+template <typename WT>
+__global__ void __launch_bounds__(kSparseThreads) noi_round_batch_k(const int32_t* __restrict__ list, int count,
+                                                                    const int64_t* __restrict__ off,
+                                                                    const int32_t* __restrict__ adj,
+                                                                    const WT* __restrict__ w, const long long* vbase,
+                                                                    const long long* nv, const long long* glam,
+                                                                    long long* r, unsigned char* seen,
+                                                                    int32_t* parent, int32_t* labels, int* gchanged) {
+  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    const int g = list[idx];
+    noi_round_body<WT>(vbase[g], vbase[g] + nv[g], off, adj, w, glam[g], r, seen, parent, labels, gchanged + g);
+  }
+}
+
+void noi_round_batch(const GraphView& u, const int32_t* list, int count, const long long* vbase, const long long* nv,
+                     const long long* glam, long long* r, unsigned char* seen, int32_t* parent, int32_t* labels,
+                     int* gchanged, cudaStream_t s) {
+  if (count <= 0) return;
+  int blocks = count < kSMs ? count : kSMs;
+  if (u.wbytes == 4)
+    noi_round_batch_k<int32_t><<<blocks, kSparseThreads, 0, s>>>(list, count, u.off, u.adj, (const int32_t*)u.w,
+                                                                  vbase, nv, glam, r, seen, parent, labels, gchanged);
+  else
+    noi_round_batch_k<long long><<<blocks, kSparseThreads, 0, s>>>(list, count, u.off, u.adj,
+                                                                    (const long long*)u.w, vbase, nv, glam, r, seen,
+                                                                    parent, labels, gchanged);
   count_launch();
   VC_CHECK_LAUNCH();
 }

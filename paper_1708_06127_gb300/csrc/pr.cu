@@ -76,17 +76,30 @@ __global__ void uf_init_k(int32_t* __restrict__ p, int64_t n) {
     p[v] = (int32_t)v;
 }
 
+// Bound and activity of the graph vertex v belongs to (single graph: the run's bound).
+__device__ __forceinline__ bool pr_graph(const BatchCtx& bc, const DevState* st, int64_t v, long long* lam) {
+  if (!bc.gid) {
+    *lam = st->lambda_hat;
+    return true;
+  }
+  const int g = bc.gid[v];
+  if (!bc.gact[g]) return false;
+  *lam = bc.glam[g];
+  return true;
+}
+
 // Condition 1 on every edge (once per undirected edge: u > v) and condition 2 on the
 // designated-partner edge; both ends must have at least two distinct neighbours.
 template <typename WT>
 __global__ void pr_a_mark_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                             const WT* __restrict__ w, const int32_t* __restrict__ partner,
                             const long long* __restrict__ pw, const long long* __restrict__ deg,
-                            const DevState* st, int32_t* parent) {
+                            const DevState* st, int32_t* parent, BatchCtx bc) {
   const int lane = threadIdx.x & 31;
-  const long long lam = st->lambda_hat;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    long long lam;
+    if (!pr_graph(bc, st, v, &lam)) continue;
     const int64_t beg = off[v], end = off[v + 1];
     if (end - beg < 2) continue;
     for (int64_t e = beg + lane; e < end; e += 32) {
@@ -100,26 +113,33 @@ __global__ void pr_a_mark_k(int64_t n, const int64_t* __restrict__ off, const in
   }
 }
 
-__global__ void uf_flatten_k(int32_t* parent, int64_t n, int32_t* __restrict__ labels, int* changed) {
+__global__ void uf_flatten_k(int32_t* parent, int64_t n, int32_t* __restrict__ labels, int* changed, BatchCtx bc) {
   int any = 0;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (bc.gid && !bc.gact[bc.gid[v]]) continue;
     int r = uf_find(parent, (int)v);
     labels[v] = r;
-    any |= (r != v);
+    if (r != v) {
+      any = 1;
+      if (bc.gid) bc.gchanged[bc.gid[v]] = 1;
+    }
   }
-  if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(changed, 1);
+  if (__syncthreads_or(any) && threadIdx.x == 0 && changed) atomicOr(changed, 1);
 }
 
 void pr_pass_a(const GraphView& g, const int32_t* partner, const long long* pw, const long long* deg,
-               const DevState* st, int32_t* parent, int32_t* labels, int* changed, cudaStream_t s) {
+               const DevState* st, int32_t* parent, int32_t* labels, int* changed, cudaStream_t s,
+               const BatchCtx* bcp) {
+  BatchCtx bc = bcp ? *bcp : BatchCtx{};
   int grid1 = grid_for(g.n, 256, kSMs * 8);
   uf_init_k<<<grid1, 256, 0, s>>>(parent, g.n);
   int grid = grid_for(g.n, 8, kSMs * 16);
   if (g.wbytes == 4)
-    pr_a_mark_k<int32_t><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, partner, pw, deg, st, parent);
+    pr_a_mark_k<int32_t><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, partner, pw, deg, st, parent, bc);
   else
-    pr_a_mark_k<long long><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, partner, pw, deg, st, parent);
-  uf_flatten_k<<<grid1, 256, 0, s>>>(parent, g.n, labels, changed);
+    pr_a_mark_k<long long><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, partner, pw, deg, st,
+                                                parent, bc);
+  uf_flatten_k<<<grid1, 256, 0, s>>>(parent, g.n, labels, changed, bc);
   count_launch(3);
   VC_CHECK_LAUNCH();
 }
@@ -130,11 +150,12 @@ template <typename WT>
 __global__ void pr_b_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                        const WT* __restrict__ w, const int32_t* __restrict__ partner,
                        const long long* __restrict__ pw, const long long* __restrict__ deg, const DevState* st,
-                       int32_t* __restrict__ labels, int* changed) {
+                       int32_t* __restrict__ labels, int* changed, BatchCtx bc) {
   const int lane = threadIdx.x & 31;
-  const long long lam = st->lambda_hat;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    long long lam;
+    if (!pr_graph(bc, st, v, &lam)) continue;
     const int p = partner[v];
     if (p <= v || partner[p] != v) continue;
     const int64_t vb = off[v], ve = off[v + 1], pb = off[p], pe = off[p + 1];
@@ -160,19 +181,23 @@ __global__ void pr_b_k(int64_t n, const int64_t* __restrict__ off, const int32_t
     sum = warp_sum(sum);
     if (lane == 0 && (pr3 || cvw + sum >= lam)) {
       labels[p] = (int32_t)v;
-      atomicOr(changed, 1);
+      if (changed) atomicOr(changed, 1);
+      if (bc.gid) bc.gchanged[bc.gid[v]] = 1;
     }
   }
 }
 
 void pr_pass_b(const GraphView& g, const int32_t* partner, const long long* pw, const long long* deg,
-               const DevState* st, int32_t* labels, int* changed, cudaStream_t s) {
-  iota(labels, g.n, s);
+               const DevState* st, int32_t* labels, int* changed, cudaStream_t s, const BatchCtx* bcp) {
+  BatchCtx bc = bcp ? *bcp : BatchCtx{};
+  if (!bc.gid) iota(labels, g.n, s);
   int grid = grid_for(g.n, 8, kSMs * 16);
   if (g.wbytes == 4)
-    pr_b_k<int32_t><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, partner, pw, deg, st, labels, changed);
+    pr_b_k<int32_t><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, partner, pw, deg, st, labels,
+                                         changed, bc);
   else
-    pr_b_k<long long><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, partner, pw, deg, st, labels, changed);
+    pr_b_k<long long><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, partner, pw, deg, st, labels,
+                                           changed, bc);
   count_launch();
   VC_CHECK_LAUNCH();
 }
