@@ -153,6 +153,25 @@ int viecut_step_pr_b(viecut_graph* g, int64_t lambda_hat, int32_t* labels, int32
 /* One Nagamochi-Ono-Ibaraki round (Sec. 3) with bound lambda_hat: labels[n] as above. */
 int viecut_step_noi_round(viecut_graph* g, int64_t lambda_hat, int32_t* labels, int32_t* changed);
 
+/* One Nagamochi-Ono-Ibaraki round, like viecut_step_noi_round, that allocates no
+ * memory at all.  The paper has no counterpart: this entry point exists for callers
+ * that cannot call cudaMalloc -- code whose device memory is owned by another
+ * allocator (a host framework that reserved the GPU for its own pool), or a serving
+ * loop that must not hit cudaMalloc's implicit device synchronisation.  The caller
+ * passes the graph (DEVICE CSR of n vertices with merged, sorted lists and int64
+ * weights, as every contracted graph is), the bound, and the DEVICE outputs
+ * d_labels[n] (union-find representative, smallest id of each merged group) and
+ * *d_changed (1 if anything merged).  Work space is a static device array sized
+ * for n <= 65536 (about 0.8 MB, kept by every GPU that loads the library until the
+ * process exits); larger n is rejected with VIECUT_EINVAL and nothing is launched.
+ * The round runs on `stream` (NULL: the default stream) and the call returns without
+ * waiting.  The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress while that device is current; make that first call before any
+ * stream capture.  All calls share the one array (the kernel clears what it needs):
+ * calls whose executions overlap on the GPU race and their results are undefined. */
+int viecut_noi_round_noalloc(const int64_t* d_offsets, const int32_t* d_adj, const int64_t* d_weights, int64_t n,
+                             int64_t lambda_hat, int32_t* d_labels, int32_t* d_changed, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Batches: many independent graphs solved together (same seed and options for all).
  * The graphs are laid out as one disjoint union on the device; each graph follows its

@@ -88,6 +88,7 @@ SIGNATURES = [
     ("viecut_step_pr_a", ctypes.c_int, [_vp, _i64, _vp, _vp]),
     ("viecut_step_pr_b", ctypes.c_int, [_vp, _i64, _vp, _vp]),
     ("viecut_step_noi_round", ctypes.c_int, [_vp, _i64, _vp, _vp]),
+    ("viecut_noi_round_noalloc", ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     ("viecut_batch_create", ctypes.c_int, [_pvp, _vp, _i32, _vp]),
     ("viecut_batch_run", ctypes.c_int, [_vp, _u64, _i32, _vp, _vp]),
     ("viecut_batch_side_words", ctypes.c_int, [_vp, _vp]),
@@ -262,6 +263,13 @@ def viecut_step_pr_b(g, lambda_hat):
 
 def viecut_step_noi_round(g, lambda_hat):
     return _step_labels("viecut_step_noi_round", g, lambda_hat)
+
+
+def viecut_noi_round_noalloc(d_offsets, d_adj, d_weights, n: int, lambda_hat: int, d_labels, d_changed,
+                             stream=None):
+    """Allocation-free exact-step round on device tensors (see include/viecut.h)."""
+    _check(lib().viecut_noi_round_noalloc(_ptr(d_offsets), _ptr(d_adj), _ptr(d_weights), n, int(lambda_hat),
+                                          _ptr(d_labels), _ptr(d_changed), stream))
 
 
 # ----------------------------------------------------------------- batches

@@ -9,7 +9,11 @@
 // degree after each contraction.
 #include <limits.h>
 
+#include <mutex>
+#include <string>
+
 #include "kernels.cuh"
+#include "viecut.h"
 
 namespace vc {
 
@@ -383,4 +387,66 @@ void noi_round_batch(const GraphView& u, const int32_t* list, int count, const l
   VC_CHECK_LAUNCH();
 }
 
+// ------------------------------------------------------- allocation-free round
+// Scratch of viecut_noi_round_noalloc: r (int64), parent (int32) and seen (byte) for
+// at most kNoAllocMaxN vertices, in one array that every device loading the library
+// keeps until the process exits (about 0.8 MB).  Host code must not pass the array's
+// name to a kernel: on the host it is only a stand-in; its device address comes from
+// cudaGetSymbolAddress, looked up once per device.
+constexpr int64_t kNoAllocMaxN = 1 << 16;
+constexpr size_t kNoAllocBytes = (size_t)kNoAllocMaxN * (sizeof(long long) + sizeof(int32_t) + 1);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+__global__ void __launch_bounds__(kSparseThreads) noi_round_noalloc_k(int64_t n, const int64_t* __restrict__ off,
+                                                                      const int32_t* __restrict__ adj,
+                                                                      const long long* __restrict__ w, long long lam,
+                                                                      unsigned char* scratch, int32_t* labels,
+                                                                      int32_t* changed) {
+  long long* r = (long long*)scratch;
+  int32_t* parent = (int32_t*)(scratch + (size_t)kNoAllocMaxN * sizeof(long long));
+  unsigned char* seen = scratch + (size_t)kNoAllocMaxN * (sizeof(long long) + sizeof(int32_t));
+  if (threadIdx.x == 0) *changed = 0;
+  __syncthreads();
+  // the body clears r, seen and parent for [0, n) before using them
+  noi_round_body<long long>(0, n, off, adj, w, lam, r, seen, parent, labels, changed);
+}
+
+static unsigned char* noalloc_scratch_address() {
+  static std::mutex mu;
+  static unsigned char* addr[256] = {nullptr};
+  int dev = 0;
+  VC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) throw Error{VIECUT_EINVAL, "device ordinal out of range"};
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    VC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    addr[dev] = (unsigned char*)p;
+  }
+  return addr[dev];
+}
+
+void set_last_error(const std::string& msg);
+
 }  // namespace vc
+
+extern "C" int viecut_noi_round_noalloc(const int64_t* d_offsets, const int32_t* d_adj, const int64_t* d_weights,
+                                        int64_t n, int64_t lambda_hat, int32_t* d_labels, int32_t* d_changed,
+                                        void* stream) {
+  try {
+    if (n < 1 || n > vc::kNoAllocMaxN)
+      throw vc::Error{VIECUT_EINVAL, "viecut_noi_round_noalloc: n = " + std::to_string(n) + " is outside [1, " +
+                                         std::to_string(vc::kNoAllocMaxN) + "], the size of its static scratch"};
+    if (!d_offsets || !d_labels || !d_changed) throw vc::Error{VIECUT_EINVAL, "null device pointer"};
+    if (lambda_hat < 0) throw vc::Error{VIECUT_EINVAL, "lambda_hat must be >= 0"};
+    unsigned char* scratch = vc::noalloc_scratch_address();
+    vc::noi_round_noalloc_k<<<1, vc::kSparseThreads, 0, (cudaStream_t)stream>>>(
+        n, d_offsets, d_adj, (const long long*)d_weights, lambda_hat, scratch, d_labels, d_changed);
+    vc::count_launch();
+    VC_CHECK_LAUNCH();
+  } catch (const vc::Error& e) {
+    vc::set_last_error(e.msg);
+    return e.code;
+  }
+  return VIECUT_OK;
+}
