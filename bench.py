@@ -136,6 +136,55 @@ def cpu_oracle_sample(seed: int = 1):
     return g, res, dt
 
 
+def make_batch(count: int, seed: int = 1):
+    import graphgen as gg
+    from concurrent.futures import ThreadPoolExecutor
+    specs = gg.batch_specs(count, seed)
+    with ThreadPoolExecutor(min(32, os.cpu_count() or 4)) as ex:
+        return list(ex.map(gg.batch_graph, specs))
+
+
+def bench_batch(count: int, steps: int, warmup: int, stream, device: int, loop: bool = True):
+    """Batched workload: `count` graphs, n log-uniform in [2^6, 2^14], RHG (avg deg
+    16-64) or ER (avg deg 8-32), weights [1, 10].  Times viecut_batch_run on the whole
+    batch (inputs resident on the device) and, beside it, a loop of viecut_run over the
+    same graphs (one pre-created handle per graph), and checks that both give the same
+    cut values."""
+    import torch
+    import paper_1708_06127_gb300 as vc
+    graphs = make_batch(count)
+    tri = [(g.offsets, g.adj, g.w) for g in graphs]
+    b = vc.Batch(tri, device=device, stream=stream.cuda_stream)
+    for i in range(max(1, warmup)):
+        cuts, _ = b.run(1 + i, 2)
+    times = []
+    for i in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cuts, bits = b.run(7, 2)
+        times.append(time.perf_counter() - t0)
+    st = b.stats()
+    b.close()
+    out = {"metric": f"batched min-cut graphs/s ({count} graphs, n log-uniform 2^6..2^14, RHG/ER mix)",
+           "value": count / statistics.median(times), "unit": "graphs/s", "ms_per_batch": 1000 * statistics.median(times),
+           "device_ms_per_batch": st["ms_total"], "super_steps": st["super_steps"],
+           "kernel_launches": st["kernel_launches"], "graphs": count, "vertices": st["vertices"],
+           "entries": st["entries"]}
+    if loop:
+        handles = [vc.MinCut(g.offsets, g.adj, g.w, device=device, stream=stream.cuda_stream) for g in graphs]
+        handles[0].run(7, 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loop_cuts = [h.run(7, 2)[0] for h in handles]
+        t_loop = time.perf_counter() - t0
+        for h in handles:
+            h.close()
+        out["per_graph_loop"] = {"value": count / t_loop, "unit": "graphs/s", "ms": 1000 * t_loop}
+        out["speedup_vs_loop"] = (count / statistics.median(times)) / (count / t_loop)
+        out["identical_cut_values"] = bool(np.array_equal(np.asarray(loop_cuts), cuts))
+    return out
+
+
 def run_reference(args):
     """The oracle arm: each step is one oracle run of the bounded sample."""
     rank, world, _ = dist_env()
@@ -174,6 +223,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nlog", type=int, default=22, help="log2 of the RHG vertex count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="all", choices=["all", "single", "batch"],
+                    help="all: the headline line plus batch and serving summaries")
+    ap.add_argument("--batch-count", type=int, default=4096)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -184,6 +236,12 @@ def main():
     import paper_1708_06127_gb300 as vc
 
     rank, world, local = dist_env()
+    if args.mode == "batch":
+        torch.cuda.set_device(local)
+        vc.build()
+        res = bench_batch(args.batch_count, args.steps, args.warmup, torch.cuda.current_stream(), local)
+        print(json.dumps(res), flush=True)
+        return 0
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     pg = None
@@ -304,6 +362,8 @@ def main():
                                 "sample": f"whole method on rhg(n=2^19, avg_deg=64, gamma=5) -> 16-core -> lcc, "
                                           f"m={sg.m}, {sdt:.1f} s, one host thread"}
     mc.close()
+    if args.mode == "all" and rank == 0:
+        line["batch"] = bench_batch(args.batch_count, 3, 1, stream, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg is not None:

@@ -208,6 +208,43 @@ int viecut_batch_get_trace(const viecut_batch* b, int32_t g, viecut_step* steps,
 int viecut_batch_get_stats(const viecut_batch* b, viecut_batch_stats* stats);
 int viecut_batch_destroy(viecut_batch* b);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop that keeps solving while requests arrive.  A host thread
+ * admits submitted graphs whenever a slot is free and the memory budget allows,
+ * appends them to the graphs resident on the device at the next super-step (their
+ * contraction state stays on the device until they finish), advances all resident
+ * graphs together, and hands each result back as soon as its graph finishes
+ * (continuous batching).  Each result equals viecut_run's result for that graph with
+ * the same seed, options and lp_iters.
+ * ------------------------------------------------------------------------- */
+typedef struct viecut_server_opts {
+  viecut_opts base;         /* n0, pr_runs_max, device, stream (validate is not used) */
+  int64_t hbm_budget_bytes; /* admission budget for resident graphs (default 120 GiB) */
+  int32_t max_slots;        /* graphs resident at once (default 1024) */
+  int32_t lp_iters;         /* label-propagation rounds per level for every request (default 2) */
+} viecut_server_opts;
+
+typedef struct viecut_server_stats {
+  int64_t admitted, completed, pending, max_resident, super_steps, joins, budget_used;
+} viecut_server_stats;
+
+typedef struct viecut_server viecut_server;
+
+int viecut_server_opts_init(viecut_server_opts* o);
+/* Starts the server thread (allocations happen here and as the resident set grows). */
+int viecut_server_start(viecut_server** s, const viecut_server_opts* o);
+/* Queues a graph (host arrays, copied before the call returns; checked like
+ * validate 1) with its seed; *ticket identifies the request.  EINVAL if the graph is
+ * malformed or alone exceeds the budget. */
+int viecut_server_submit(viecut_server* s, const viecut_graph_desc* g, uint64_t seed, uint64_t* ticket);
+/* Non-blocking: VIECUT_EBUSY until the request finished; then writes the cut, the
+ * side bitmap (ceil(n/64) words, may be NULL) and the latency from submit to the
+ * moment the result reached the host, and forgets the ticket. */
+int viecut_server_poll(viecut_server* s, uint64_t ticket, int64_t* cut, uint64_t* side_bits, double* latency_ms);
+int viecut_server_get_stats(viecut_server* s, viecut_server_stats* st);
+/* Stops the thread (requests still queued or resident are abandoned) and frees all. */
+int viecut_server_stop(viecut_server* s);
+
 #ifdef __cplusplus
 }
 #endif

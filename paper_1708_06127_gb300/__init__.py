@@ -59,6 +59,17 @@ class viecut_batch_stats(ctypes.Structure):
                 ("graphs", ctypes.c_int64), ("vertices", ctypes.c_int64), ("entries", ctypes.c_int64)]
 
 
+class viecut_server_opts(ctypes.Structure):
+    _fields_ = [("base", viecut_opts), ("hbm_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32),
+                ("lp_iters", ctypes.c_int32)]
+
+
+class viecut_server_stats(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("max_resident", ctypes.c_int64), ("super_steps", ctypes.c_int64), ("joins", ctypes.c_int64),
+                ("budget_used", ctypes.c_int64)]
+
+
 class viecut_step(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("n", ctypes.c_int64),
                 ("nnz", ctypes.c_int64), ("lambda_hat", ctypes.c_int64)]
@@ -95,6 +106,12 @@ SIGNATURES = [
     ("viecut_batch_get_trace", ctypes.c_int, [_vp, _i32, _vp, _i64, _vp]),
     ("viecut_batch_get_stats", ctypes.c_int, [_vp, _vp]),
     ("viecut_batch_destroy", ctypes.c_int, [_vp]),
+    ("viecut_server_opts_init", ctypes.c_int, [_vp]),
+    ("viecut_server_start", ctypes.c_int, [_pvp, _vp]),
+    ("viecut_server_submit", ctypes.c_int, [_vp, _vp, _u64, _vp]),
+    ("viecut_server_poll", ctypes.c_int, [_vp, _u64, _vp, _vp, _vp]),
+    ("viecut_server_get_stats", ctypes.c_int, [_vp, _vp]),
+    ("viecut_server_stop", ctypes.c_int, [_vp]),
 ]
 
 
@@ -349,6 +366,110 @@ class Batch:
         if self.b:
             viecut_batch_destroy(self.b)
             self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------- serving
+def viecut_server_opts_init(**kw) -> viecut_server_opts:
+    o = viecut_server_opts()
+    _check(lib().viecut_server_opts_init(ctypes.byref(o)))
+    for k, v in kw.items():
+        if k in ("n0", "pr_runs_max", "device", "stream"):
+            setattr(o.base, k, v)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def viecut_server_start(opts: viecut_server_opts | None = None):
+    s = ctypes.c_void_p()
+    _check(lib().viecut_server_start(ctypes.byref(s), ctypes.byref(opts) if opts else None))
+    return s
+
+
+def viecut_server_submit(s, offsets, adj, weights, seed: int) -> int:
+    off = np.ascontiguousarray(offsets, np.int64)
+    a = np.ascontiguousarray(adj, np.int32)
+    w = np.ascontiguousarray(weights, np.int32)
+    d = viecut_graph_desc(off.ctypes.data, a.ctypes.data, w.ctypes.data, off.shape[0] - 1, a.shape[0])
+    t = ctypes.c_uint64()
+    _check(lib().viecut_server_submit(s, ctypes.byref(d), seed & (2**64 - 1), ctypes.byref(t)))
+    return int(t.value)
+
+
+def viecut_server_poll(s, ticket: int, n: int):
+    """None while the request runs, else (cut, side bitmap, latency in ms)."""
+    cut = ctypes.c_int64()
+    lat = ctypes.c_double()
+    bits = np.zeros(max(1, (n + 63) // 64), np.uint64)
+    rc = lib().viecut_server_poll(s, ticket, ctypes.byref(cut), bits.ctypes.data, ctypes.byref(lat))
+    if rc == VIECUT_EBUSY:
+        return None
+    _check(rc)
+    return int(cut.value), bits, float(lat.value)
+
+
+def viecut_server_get_stats(s) -> dict:
+    st = viecut_server_stats()
+    _check(lib().viecut_server_get_stats(s, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in viecut_server_stats._fields_}
+
+
+def viecut_server_stop(s):
+    if s:
+        _check(lib().viecut_server_stop(s))
+
+
+class Server:
+    """Continuous-batching min-cut server on one GPU."""
+
+    def __init__(self, hbm_budget_bytes: int = 120 << 30, max_slots: int = 1024, lp_iters: int = 2,
+                 n0: int = 10000, pr_runs_max: int = 8, device: int = 0):
+        o = viecut_server_opts_init(hbm_budget_bytes=hbm_budget_bytes, max_slots=max_slots, lp_iters=lp_iters,
+                                    n0=n0, pr_runs_max=pr_runs_max, device=device)
+        self.s = viecut_server_start(o)
+        self.sizes = {}
+
+    def submit(self, offsets, adj, weights, seed: int = 1) -> int:
+        t = viecut_server_submit(self.s, offsets, adj, weights, seed)
+        self.sizes[t] = int(np.asarray(offsets).shape[0] - 1)
+        return t
+
+    def poll(self, ticket: int):
+        r = viecut_server_poll(self.s, ticket, self.sizes[ticket])
+        if r is not None:
+            del self.sizes[ticket]
+        return r
+
+    def wait(self, ticket: int, timeout: float = 600.0, sleep: float = 0.0005):
+        import time
+        t0 = time.perf_counter()
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.perf_counter() - t0 > timeout:
+                raise TimeoutError(f"ticket {ticket} not done after {timeout} s")
+            time.sleep(sleep)
+
+    def stats(self) -> dict:
+        return viecut_server_get_stats(self.s)
+
+    def close(self):
+        if self.s:
+            viecut_server_stop(self.s)
+            self.s = None
 
     def __enter__(self):
         return self

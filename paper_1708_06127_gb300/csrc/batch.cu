@@ -14,7 +14,14 @@
 // single-graph run, so every result equals the graph's result alone.
 #include <string.h>
 
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <numeric>
+#include <thread>
 
 #include "engine.cuh"
 
@@ -29,7 +36,9 @@ struct BState {
   int *phase, *level, *run, *any, *changed, *contracted, *first, *did, *best_kind, *trace_len;
   long long *vbase, *vbase_new, *nv, *nnz, *n_start, *lam, *best_vertex, *argmin, *dmin, *obase, *norig, *n1,
       *noi_base;
+  long long* nv_new;
   unsigned long long* gkey;
+  unsigned long long* seed;
   unsigned char* gact;
   TraceStep* trace;
   int* summary;  // [0..6] phase counts, [7] max n among NOI_D graphs, [8] contract or drop count
@@ -68,9 +77,13 @@ __global__ void b_validate_k(int K, const long long* vbase, const long long* eba
   if (bad) atomicOr(err, bad);
 }
 
-__global__ void b_gid_init_k(int K, const long long* vbase, int32_t* gid) {
-  for (int g = blockIdx.x; g < K; g += gridDim.x)
-    for (long long v = vbase[g] + threadIdx.x; v < vbase[g + 1]; v += blockDim.x) gid[v] = g;
+// vertex -> graph map for the graphs that just joined the union (first & 8)
+__global__ void b_gid_init_k(int K, BState S, int32_t* gid) {
+  for (int g = blockIdx.x; g < K; g += gridDim.x) {
+    if (!(S.first[g] & 8)) continue;
+    const long long vb = S.vbase[g], ve = vb + S.nv[g];
+    for (long long v = vb + threadIdx.x; v < ve; v += blockDim.x) gid[v] = g;
+  }
 }
 
 // ---------------------------------------------------------------- per-graph steps
@@ -81,7 +94,7 @@ __global__ void b_segmin_k(int K, const long long* __restrict__ deg, BState S, i
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int g = blockIdx.x; g < K; g += gridDim.x) {
     if (mode == 1 && (!S.did[g] || S.nv[g] <= 1)) continue;
-    if (mode == 0 && S.nv[g] < 1) continue;
+    if (mode == 0 && (!(S.first[g] & 8) || S.nv[g] < 1)) continue;
     const long long vb = S.vbase[g], ve = vb + S.nv[g];
     long long bd = LLONG_MAX, bv = LLONG_MAX;
     for (long long v = vb + threadIdx.x; v < ve; v += blockDim.x) {
@@ -123,9 +136,10 @@ __device__ __forceinline__ void b_push(BState& S, int g, int kind) {
 
 __device__ __forceinline__ void b_enter_noi(BState& S, int g) { S.phase[g] = S.nv[g] > kDenseMax ? kBNoiS : kBNoiD; }
 
-// initial phase of every graph (after the initial bound)
+// initial phase of the graphs that just joined (first & 8), after their initial bound
 __global__ void b_init_k(int K, BState S, long long n0) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < K; g += gridDim.x * blockDim.x) {
+    if (!(S.first[g] & 8)) continue;
     S.level[g] = 0;
     S.run[g] = 0;
     S.any[g] = 0;
@@ -133,6 +147,8 @@ __global__ void b_init_k(int K, BState S, long long n0) {
     S.contracted[g] = 0;
     S.n1[g] = 0;
     S.first[g] = 0;
+    S.best_kind[g] = 0;
+    S.noi_base[g] = 0;
     b_push(S, g, 0);
     if (S.lam[g] == 0) {
       S.phase[g] = kBDone;
@@ -169,7 +185,7 @@ __global__ void b_tier1_k(int K, BState S, const int32_t* __restrict__ cid, int3
     if (ph == kBGone || ph == kBDone) continue;  // dropped in this contraction
     if (S.did[g] && !S.contracted[g]) {
       // first contraction: original vertex i sat at vbase[g] + i
-      const long long vb = S.vbase[g], nb = S.vbase_new[g], n = S.norig[g], c = S.nv[g];
+      const long long vb = S.vbase[g], nb = S.vbase_new[g], n = S.norig[g], c = S.nv_new[g];
       for (long long i = threadIdx.x; i < n; i += blockDim.x) map0[ob + i] = (int32_t)(cid[vb + i] - nb);
       for (long long j = threadIdx.x; j < c; j += blockDim.x) cur1[ob + j] = (int32_t)(nb + j);
       if (threadIdx.x == 0) {
@@ -195,11 +211,11 @@ __global__ void b_snapshot_k(int K, BState S, const int32_t* __restrict__ cur1, 
 }
 
 // per graph: activity for the pass of phase `ph`; LP also gets its level key
-__global__ void b_prepare_k(int K, BState S, int ph, uint64_t seed) {
+__global__ void b_prepare_k(int K, BState S, int ph) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < K; g += gridDim.x * blockDim.x) {
     const bool a = S.phase[g] == ph;
     S.gact[g] = a ? 1 : 0;
-    if (ph == kBLP) S.gkey[g] = level_key(seed, S.level[g]);
+    if (ph == kBLP) S.gkey[g] = level_key(S.seed[g], S.level[g]);
   }
 }
 
@@ -242,21 +258,21 @@ __global__ void b_drop_k(int64_t n, const int32_t* __restrict__ gid, const int* 
     if (phase[gid[v]] == kBDone) lab[v] = -1;
 }
 
-// new vertex ranges after a union contraction: the coarse base of graph g is the rank
-// of its first vertex's id among the kept labels (exclusive scan of the flags)
-__global__ void b_shape_k(int K, BState S, int64_t n_old, int64_t c_total, const int32_t* __restrict__ rank,
-                          const int64_t* __restrict__ coff) {
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g <= K; g += gridDim.x * blockDim.x) {
-    const long long vb = S.vbase[g];
-    S.vbase_new[g] = vb < n_old ? (long long)rank[vb] : c_total;
-  }
-}
-
-__global__ void b_shape2_k(int K, BState S, const int64_t* __restrict__ coff) {
+// new vertex ranges after a union contraction: a vertex id x of the old union maps to
+// the rank of x among the kept labels (exclusive scan of the flags), so graph g's new
+// range is [rank(vbase), rank(vbase + nv)); dropped graphs end up empty
+__global__ void b_shape_k(int K, BState S, int64_t n_old, int64_t c_total, const int32_t* __restrict__ rank) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < K; g += gridDim.x * blockDim.x) {
-    const long long a = S.vbase_new[g], b = S.vbase_new[g + 1];
-    S.nv[g] = b - a;
-    S.nnz[g] = coff[b] - coff[a];
+    if (S.phase[g] == kBGone) {
+      S.vbase_new[g] = 0;
+      S.nv_new[g] = 0;
+      continue;
+    }
+    const long long vb = S.vbase[g], ve = vb + S.nv[g];
+    const long long nb = vb < n_old ? (long long)rank[vb] : c_total;
+    const long long ne = ve < n_old ? (long long)rank[ve] : c_total;
+    S.vbase_new[g] = nb;
+    S.nv_new[g] = ne - nb;
   }
 }
 
@@ -268,8 +284,13 @@ __global__ void b_gid_update_k(int64_t n, const int32_t* __restrict__ cid, const
   }
 }
 
-__global__ void b_copy_vbase_k(int K, BState S) {
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g <= K; g += gridDim.x * blockDim.x) S.vbase[g] = S.vbase_new[g];
+__global__ void b_copy_shape_k(int K, BState S, const int64_t* __restrict__ coff) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < K; g += gridDim.x * blockDim.x) {
+    const long long a = S.vbase_new[g], n = S.nv_new[g];
+    S.vbase[g] = a;
+    S.nv[g] = n;
+    S.nnz[g] = n > 0 ? coff[a + n] - coff[a] : 0;
+  }
 }
 
 __global__ void b_trace_k(int K, BState S) {
@@ -313,11 +334,13 @@ __global__ void b_transition_k(int K, BState S, long long n0, int pr_runs_max) {
   }
 }
 
-// final side bitmaps: words of graph g start at wbase[g]
-__global__ void b_side_bits_k(int K, BState S, const long long* __restrict__ wbase, const int32_t* __restrict__ map0,
-                              const unsigned char* __restrict__ side1, const int32_t* __restrict__ cur1,
-                              const unsigned char* __restrict__ sideK, unsigned long long* bits) {
-  for (int g = blockIdx.x; g < K; g += gridDim.x) {
+// final side bitmaps of the listed slots: slot list[i]'s words start at wbase[i]
+__global__ void b_side_bits_k(const int32_t* __restrict__ list, int count, BState S, const long long* __restrict__ wbase,
+                              const int32_t* __restrict__ map0, const unsigned char* __restrict__ side1,
+                              const int32_t* __restrict__ cur1, const unsigned char* __restrict__ sideK,
+                              unsigned long long* bits) {
+  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    const int g = list ? list[idx] : idx;
     const long long n = S.norig[g], ob = S.obase[g];
     const int kind = S.best_kind[g];
     const long long bv = S.best_vertex[g], nb = S.noi_base[g];
@@ -335,34 +358,95 @@ __global__ void b_side_bits_k(int K, BState S, const long long* __restrict__ wba
       const long long lim = (wd + 1) * 64 < n ? (wd + 1) * 64 : n;
       for (long long i = wd * 64; i < lim; ++i)
         if (side_of(i) != flip) x |= 1ULL << (i & 63);
-      bits[wbase[g] + wd] = x;
+      bits[wbase[idx] + wd] = x;
     }
   }
 }
 
+// appends graphs to the union: graph j of the staged arrays (host CSR copied as is,
+// local ids, int32 weights) lands at vertex base jv[j] / entry base je[j]
+__global__ void b_join_k(int J, const long long* __restrict__ jv, const long long* __restrict__ je,
+                         const long long* __restrict__ sv, const long long* __restrict__ se,
+                         const int64_t* __restrict__ st_off, const int32_t* __restrict__ st_adj,
+                         const int32_t* __restrict__ st_w, int64_t* off, int32_t* adj, long long* w) {
+  for (int j = blockIdx.x; j < J; j += gridDim.x) {
+    const long long n = sv[j + 1] - sv[j], m = se[j + 1] - se[j];
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) off[jv[j] + i] = je[j] + st_off[sv[j] + i];
+    for (long long e = threadIdx.x; e < m; e += blockDim.x) {
+      adj[je[j] + e] = (int32_t)(jv[j] + st_adj[se[j] + e]);
+      w[je[j] + e] = (long long)st_w[se[j] + e];
+    }
+  }
+}
+
+// per-slot values of graphs joining the union
+struct SlotInit {
+  int slot;
+  int pad;
+  long long vbase, n, m, obase;
+  unsigned long long seed;
+};
+
+__global__ void b_slot_init_k(int J, const SlotInit* __restrict__ in, BState S) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < J; j += gridDim.x * blockDim.x) {
+    const SlotInit x = in[j];
+    S.vbase[x.slot] = x.vbase;
+    S.nv[x.slot] = x.n;
+    S.nnz[x.slot] = x.m;
+    S.norig[x.slot] = x.n;
+    S.obase[x.slot] = x.obase;
+    S.seed[x.slot] = x.seed;
+    S.first[x.slot] = 8;
+  }
+}
+
+__global__ void b_set_i64_k(int64_t* p, int64_t v) { *p = v; }
+
 // ------------------------------------------------------------------ host side
-struct Batch {
+// Grows a persistent device array, keeping its first `keep` bytes.
+static void grow_keep(Buf& b, size_t bytes, size_t keep, cudaStream_t s) {
+  if (bytes <= b.cap) return;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error{VIECUT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
+  }
+  if (keep && b.p) VC_CUDA(cudaMemcpyAsync(p, b.p, keep, cudaMemcpyDeviceToDevice, s));
+  VC_CUDA(cudaStreamSynchronize(s));
+  b.release();
+  b.p = p;
+  b.cap = bytes;
+}
+
+// The engine shared by batches and the server: K slots of per-graph state, the
+// current union, the per-original-vertex arrays (map0 / cur1 / side1, slot g's at
+// [obase, obase + norig)) and the workspace.
+struct Engine {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int K = 0;
-  int64_t n_u = 0, m_u = 0;
   int64_t n0 = 10000;
   int pr_runs_max = 8;
-  bool unit = false, simple = false;
-  std::vector<int64_t> h_vbase, h_ebase, h_wbase;
-  Buf in_off, in_adj, in_w;
-  Buf d_vbase0, d_ebase, d_wbase;
-  // per-graph state
+  int lp_iters = 2;
+  // per-slot state
   Buf phase, level, run, any, changed, contracted, first, did, best_kind, trace_len;
-  Buf vbase, vbase_new, nv, nnz, n_start, lam, best_vertex, argmin, dmin, obase, norig, n1, noi_base;
-  Buf gkey, gact, trace, summary, list_noid, list_nois;
-  // union-wide
-  Buf gid, gid2, vact, sideK, noiM, noiCurK, bits_out, cut_out;
+  Buf vbase, vbase_new, nv, nv_new, nnz, n_start, lam, best_vertex, argmin, dmin, obase, norig, n1, noi_base;
+  Buf gkey, seed, gact, trace, summary, list_noid, list_nois;
+  // union
+  GraphView G;
+  int slot = -1;  // coarse buffer of the workspace holding G (-1: in_*)
+  Buf in_off, in_adj, in_w;
+  Buf gidA, gidB;
+  int32_t* gid = nullptr;
+  Buf vact, sideK, noiM, noiCurK;
+  Buf om0, oc1, os1;  // per original vertex
+  int64_t ocap = 0;
   Workspace* ws = nullptr;
   int* h_summary = nullptr;
-  viecut_batch_stats stats{};
-  ~Batch() {
+  int64_t steps = 0;
+  ~Engine() {
     delete ws;
     if (h_summary) cudaFreeHost(h_summary);
     if (own_stream && stream) cudaStreamDestroy(stream);
@@ -373,29 +457,190 @@ struct Batch {
     S.changed = changed.as<int>(); S.contracted = contracted.as<int>(); S.first = first.as<int>();
     S.did = did.as<int>(); S.best_kind = best_kind.as<int>(); S.trace_len = trace_len.as<int>();
     S.vbase = vbase.as<long long>(); S.vbase_new = vbase_new.as<long long>(); S.nv = nv.as<long long>();
-    S.nnz = nnz.as<long long>(); S.n_start = n_start.as<long long>(); S.lam = lam.as<long long>();
-    S.best_vertex = best_vertex.as<long long>(); S.argmin = argmin.as<long long>(); S.dmin = dmin.as<long long>();
-    S.obase = obase.as<long long>(); S.norig = norig.as<long long>(); S.n1 = n1.as<long long>();
-    S.noi_base = noi_base.as<long long>(); S.gkey = gkey.as<unsigned long long>(); S.gact = gact.as<unsigned char>();
-    S.trace = trace.as<TraceStep>(); S.summary = summary.as<int>();
-    S.list_noid = list_noid.as<int32_t>(); S.list_nois = list_nois.as<int32_t>();
+    S.nv_new = nv_new.as<long long>(); S.nnz = nnz.as<long long>(); S.n_start = n_start.as<long long>();
+    S.lam = lam.as<long long>(); S.best_vertex = best_vertex.as<long long>(); S.argmin = argmin.as<long long>();
+    S.dmin = dmin.as<long long>(); S.obase = obase.as<long long>(); S.norig = norig.as<long long>();
+    S.n1 = n1.as<long long>(); S.noi_base = noi_base.as<long long>(); S.gkey = gkey.as<unsigned long long>();
+    S.seed = seed.as<unsigned long long>(); S.gact = gact.as<unsigned char>(); S.trace = trace.as<TraceStep>();
+    S.summary = summary.as<int>(); S.list_noid = list_noid.as<int32_t>(); S.list_nois = list_nois.as<int32_t>();
     return S;
   }
 };
 
-static void batch_create(Batch& B, const viecut_graph_desc* gs, int K, const viecut_opts& o) {
-  B.K = K;
-  B.n0 = o.n0;
-  B.pr_runs_max = o.pr_runs_max;
-  B.device = o.device;
-  VC_CUDA(cudaSetDevice(B.device));
+static void engine_setup(Engine& E, int K, const viecut_opts& o) {
+  E.K = K;
+  E.n0 = o.n0;
+  E.pr_runs_max = o.pr_runs_max;
+  E.device = o.device;
+  VC_CUDA(cudaSetDevice(E.device));
   if (o.stream) {
-    B.stream = (cudaStream_t)o.stream;
+    E.stream = (cudaStream_t)o.stream;
   } else {
-    VC_CUDA(cudaStreamCreateWithFlags(&B.stream, cudaStreamNonBlocking));
-    B.own_stream = true;
+    VC_CUDA(cudaStreamCreateWithFlags(&E.stream, cudaStreamNonBlocking));
+    E.own_stream = true;
   }
-  cudaStream_t s = B.stream;
+  for (Buf* b : {&E.phase, &E.level, &E.run, &E.any, &E.changed, &E.contracted, &E.first, &E.did, &E.best_kind,
+                 &E.trace_len})
+    b->ensure_n<int>(K);
+  for (Buf* b : {&E.nv, &E.nv_new, &E.nnz, &E.n_start, &E.lam, &E.best_vertex, &E.argmin, &E.dmin, &E.obase,
+                 &E.norig, &E.n1, &E.noi_base, &E.vbase, &E.vbase_new})
+    b->ensure_n<long long>(K);
+  E.gkey.ensure_n<unsigned long long>(K);
+  E.seed.ensure_n<unsigned long long>(K);
+  E.gact.ensure_n<unsigned char>(K);
+  E.trace.ensure_n<TraceStep>((int64_t)K * kBTraceCap);
+  E.summary.ensure_n<int>(kSummaryInts);
+  E.list_noid.ensure_n<int32_t>(K);
+  E.list_nois.ensure_n<int32_t>(K);
+  E.sideK.ensure_n<unsigned char>((int64_t)K * kDenseMax);
+  E.noiCurK.ensure_n<int32_t>((int64_t)kSMs * kDenseMax);
+  VC_CUDA(cudaMemsetAsync(E.phase.p, 0, sizeof(int) * K, E.stream));
+  {
+    std::vector<int> gone(K, kBGone);
+    VC_CUDA(cudaMemcpy(E.phase.p, gone.data(), sizeof(int) * K, cudaMemcpyHostToDevice));
+  }
+  VC_CUDA(cudaMallocHost(&E.h_summary, sizeof(int) * kSummaryInts));
+  E.ws = new Workspace;
+  E.ws->s = E.stream;
+}
+
+static void read_summary(Engine& E) {
+  VC_CUDA(cudaMemcpyAsync(E.h_summary, E.summary.p, sizeof(int) * kSummaryInts, cudaMemcpyDeviceToHost, E.stream));
+  VC_CUDA(cudaStreamSynchronize(E.stream));
+}
+
+// Bound, phase and tier-1 set-up of the slots flagged new (first & 8); the union,
+// gid, vbase, nv, nnz, norig, obase and seed of those slots must be in place.
+static void engine_start_new(Engine& E) {
+  cudaStream_t s = E.stream;
+  Workspace& W = *E.ws;
+  BState S = E.state();
+  const int K = E.K;
+  const int gK = (K + 255) / 256, gridK = K < 4 * kSMs ? K : 4 * kSMs;
+  degrees(E.G, W.deg.as<long long>(), s);
+  b_segmin_k<<<gridK, 256, 0, s>>>(K, W.deg.as<long long>(), S, 0);
+  b_init_k<<<gK, 256, 0, s>>>(K, S, E.n0);
+  b_tier1_k<<<gridK, 256, 0, s>>>(K, S, nullptr, E.om0.as<int32_t>(), E.oc1.as<int32_t>(), 0);
+  count_launch(3);
+  VC_CHECK_LAUNCH();
+}
+
+// One super-step for every slot; returns false when no slot is active.
+static bool engine_step(Engine& E) {
+  cudaStream_t s = E.stream;
+  Workspace& W = *E.ws;
+  BState S = E.state();
+  const int K = E.K;
+  const int gK = (K + 255) / 256, gridK = K < 4 * kSMs ? K : 4 * kSMs;
+  GraphView& G = E.G;
+  VC_CUDA(cudaMemsetAsync(S.summary, 0, sizeof(int) * kSummaryInts, s));
+  b_summary_k<<<gK, 256, 0, s>>>(K, S);
+  count_launch();
+  read_summary(E);
+  const int* cnt = E.h_summary;
+  if (cnt[kBLP] + cnt[kBPRA] + cnt[kBPRB] + cnt[kBNoiS] + cnt[kBNoiD] + cnt[kBDone] == 0) return false;
+  ++E.steps;
+  int32_t* A = W.labA.as<int32_t>();
+  int32_t* Bl = W.labB.as<int32_t>();
+  iota(A, G.n, s);
+  iota(Bl, G.n, s);
+  int32_t* F = A;
+  BatchCtx bc;
+  bc.gid = E.gid;
+  bc.glam = S.lam;
+  bc.gact = S.gact;
+  bc.gchanged = S.changed;
+  if (cnt[kBLP] > 0) {
+    b_prepare_k<<<gK, 256, 0, s>>>(K, S, kBLP);
+    b_vact_k<<<grid_for(G.n, 256, kSMs * 8), 256, 0, s>>>(G.n, E.gid, S.gact, E.vact.as<unsigned char>());
+    count_launch(2);
+    hash_table(G.n, 0, E.gid, S.gkey, S.vbase, W.hv.as<unsigned long long>(), s);
+    if (!W.bins_valid) W.build_bins(G);
+    GraphView Ga = G;
+    Ga.vact = E.vact.as<unsigned char>();
+    int32_t* in = nullptr;
+    int32_t* bufs[2] = {A, Bl};
+    for (int r = 0; r < E.lp_iters; ++r) {
+      lp_round(Ga, W.bins, W.gt, in, bufs[r & 1], W.hv.as<unsigned long long>(), s);
+      in = bufs[r & 1];
+    }
+    if (E.lp_iters > 0) F = in;
+  }
+  if (cnt[kBPRA] > 0) {
+    b_prepare_k<<<gK, 256, 0, s>>>(K, S, kBPRA);
+    count_launch();
+    pr_partners(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), s);
+    pr_pass_a(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), W.st(),
+              W.parent.as<int32_t>(), F, nullptr, s, &bc);
+  }
+  if (cnt[kBPRB] > 0) {
+    b_prepare_k<<<gK, 256, 0, s>>>(K, S, kBPRB);
+    count_launch();
+    pr_partners(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), s);
+    pr_pass_b(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), W.st(), F, nullptr, s, &bc);
+  }
+  if (cnt[kBNoiS] > 0) {
+    W.noi_r.ensure_n<long long>(G.n);
+    W.noi_seen.ensure_n<unsigned char>(G.n);
+    noi_round_batch(G, S.list_nois, cnt[10], S.vbase, S.nv, S.lam, W.noi_r.as<long long>(),
+                    W.noi_seen.as<unsigned char>(), W.parent.as<int32_t>(), F, S.changed, s);
+  }
+  if (cnt[kBNoiD] > 0) {
+    const int64_t mcap = (int64_t)cnt[7] * cnt[7];
+    const int blocks = cnt[kBNoiD] < kSMs ? cnt[kBNoiD] : kSMs;
+    long long* M = E.noiM.ensure_n<long long>(2 * mcap * blocks);
+    BatchNoi bn{S.lam, S.best_kind, S.nv, S.nnz, S.dmin, S.argmin, S.trace_len, S.trace, kBTraceCap, S.level};
+    noi_dense_batch(G, S.list_noid, cnt[kBNoiD], S.vbase, S.nv, M, mcap, blocks, E.noiCurK.as<int32_t>(),
+                    E.sideK.as<unsigned char>(), bn, s);
+  }
+  b_decide_k<<<gK, 256, 0, s>>>(K, S);
+  count_launch();
+  read_summary(E);
+  if (E.h_summary[8] > 0) {
+    b_drop_k<<<grid_for(G.n, 256, kSMs * 8), 256, 0, s>>>(G.n, E.gid, S.phase, F);
+    count_launch();
+    const int dst = E.slot == 0 ? 1 : 0;
+    int32_t* cid = W.cidT.as<int32_t>();
+    const int64_t n_old = G.n;
+    GraphView h = W.contract(G, F, cid, dst);
+    int32_t* gid_new = (E.gid == E.gidA.as<int32_t>()) ? E.gidB.as<int32_t>() : E.gidA.as<int32_t>();
+    b_shape_k<<<gK, 256, 0, s>>>(K, S, n_old, h.n, W.rank.as<int32_t>());
+    b_gid_update_k<<<grid_for(n_old, 256, kSMs * 8), 256, 0, s>>>(n_old, cid, E.gid, gid_new);
+    b_tier1_k<<<gridK, 256, 0, s>>>(K, S, cid, E.om0.as<int32_t>(), E.oc1.as<int32_t>(), 1);
+    b_copy_shape_k<<<gK, 256, 0, s>>>(K, S, h.off);
+    count_launch(4);
+    VC_CHECK_LAUNCH();
+    E.gid = gid_new;
+    G = h;
+    E.slot = dst;
+    if (G.n > 0) {
+      degrees(G, W.deg.as<long long>(), s);
+      b_segmin_k<<<gridK, 256, 0, s>>>(K, W.deg.as<long long>(), S, 1);
+      b_snapshot_k<<<gridK, 256, 0, s>>>(K, S, E.oc1.as<int32_t>(), E.os1.as<unsigned char>());
+      count_launch(2);
+    }
+    b_trace_k<<<gK, 256, 0, s>>>(K, S);
+    count_launch();
+  }
+  b_transition_k<<<gK, 256, 0, s>>>(K, S, E.n0, E.pr_runs_max);
+  count_launch();
+  VC_CHECK_LAUNCH();
+  return true;
+}
+
+// ------------------------------------------------------------------ batches
+struct Batch {
+  Engine E;
+  std::vector<int64_t> h_vbase, h_ebase, h_wbase;
+  Buf d_vbase0, d_ebase, d_wbase, bits_out;
+  bool unit = false, simple = false;
+  viecut_batch_stats stats{};
+};
+
+static void batch_create(Batch& B, const viecut_graph_desc* gs, int K, const viecut_opts& o) {
+  Engine& E = B.E;
+  engine_setup(E, K, o);
+  cudaStream_t s = E.stream;
   B.h_vbase.assign(K + 1, 0);
   B.h_ebase.assign(K + 1, 0);
   B.h_wbase.assign(K + 1, 0);
@@ -408,12 +653,11 @@ static void batch_create(Batch& B, const viecut_graph_desc* gs, int K, const vie
     B.h_ebase[g + 1] = B.h_ebase[g] + gs[g].m;
     B.h_wbase[g + 1] = B.h_wbase[g] + (gs[g].n + 63) / 64;
   }
-  B.n_u = B.h_vbase[K];
-  B.m_u = B.h_ebase[K];
-  if (B.n_u > 0x7fffffffLL) throw Error{VIECUT_EINVAL, "the batch must hold fewer than 2^31 vertices"};
-  int64_t* off = B.in_off.ensure_n<int64_t>(B.n_u + 1);
-  int32_t* adj = B.in_adj.ensure_n<int32_t>(B.m_u);
-  int32_t* w = B.in_w.ensure_n<int32_t>(B.m_u);
+  const int64_t n_u = B.h_vbase[K], m_u = B.h_ebase[K];
+  if (n_u > 0x7fffffffLL) throw Error{VIECUT_EINVAL, "the batch must hold fewer than 2^31 vertices"};
+  int64_t* off = E.in_off.ensure_n<int64_t>(n_u + 1);
+  int32_t* adj = E.in_adj.ensure_n<int32_t>(m_u);
+  int32_t* w = E.in_w.ensure_n<int32_t>(m_u);
   for (int g = 0; g < K; ++g) {
     VC_CUDA(cudaMemcpyAsync(off + B.h_vbase[g], gs[g].offsets, sizeof(int64_t) * gs[g].n, cudaMemcpyHostToDevice, s));
     if (gs[g].m > 0) {
@@ -421,19 +665,17 @@ static void batch_create(Batch& B, const viecut_graph_desc* gs, int K, const vie
       VC_CUDA(cudaMemcpyAsync(w + B.h_ebase[g], gs[g].weights, sizeof(int32_t) * gs[g].m, cudaMemcpyHostToDevice, s));
     }
   }
-  VC_CUDA(cudaMemcpyAsync(off + B.n_u, &B.m_u, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  VC_CUDA(cudaMemcpyAsync(off + n_u, &m_u, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   VC_CUDA(cudaMemcpyAsync(B.d_vbase0.ensure_n<long long>(K + 1), B.h_vbase.data(), sizeof(long long) * (K + 1),
                           cudaMemcpyHostToDevice, s));
   VC_CUDA(cudaMemcpyAsync(B.d_ebase.ensure_n<long long>(K + 1), B.h_ebase.data(), sizeof(long long) * (K + 1),
                           cudaMemcpyHostToDevice, s));
   VC_CUDA(cudaMemcpyAsync(B.d_wbase.ensure_n<long long>(K + 1), B.h_wbase.data(), sizeof(long long) * (K + 1),
                           cudaMemcpyHostToDevice, s));
-  B.ws = new Workspace;
-  B.ws->s = s;
-  Workspace& W = *B.ws;
+  Workspace& W = *E.ws;
   int* err = &W.ctr()->changed;
   VC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-  int gridK = K < 4 * kSMs ? K : 4 * kSMs;
+  const int gridK = K < 4 * kSMs ? K : 4 * kSMs;
   if (o.validate >= 1) {
     b_validate_k<<<gridK, 256, 0, s>>>(K, B.d_vbase0.as<long long>(), B.d_ebase.as<long long>(), off, adj, w, err);
     count_launch();
@@ -455,190 +697,75 @@ static void batch_create(Batch& B, const viecut_graph_desc* gs, int K, const vie
     if (bad & 16) why += " weight < 1;";
     throw Error{VIECUT_EINVAL, "invalid graph in batch:" + why};
   }
-  W.ensure_vertices(B.n_u);
-  W.ensure_entries(B.m_u, B.n_u);
-  for (Buf* b : {&B.phase, &B.level, &B.run, &B.any, &B.changed, &B.contracted, &B.first, &B.did, &B.best_kind,
-                 &B.trace_len})
-    b->ensure_n<int>(K);
-  for (Buf* b : {&B.nv, &B.nnz, &B.n_start, &B.lam, &B.best_vertex, &B.argmin, &B.dmin, &B.obase, &B.norig, &B.n1,
-                 &B.noi_base})
-    b->ensure_n<long long>(K);
-  B.vbase.ensure_n<long long>(K + 1);
-  B.vbase_new.ensure_n<long long>(K + 1);
-  B.gkey.ensure_n<unsigned long long>(K);
-  B.gact.ensure_n<unsigned char>(K);
-  B.trace.ensure_n<TraceStep>((int64_t)K * kBTraceCap);
-  B.summary.ensure_n<int>(kSummaryInts);
-  B.list_noid.ensure_n<int32_t>(K);
-  B.list_nois.ensure_n<int32_t>(K);
-  B.gid.ensure_n<int32_t>(B.n_u);
-  B.gid2.ensure_n<int32_t>(B.n_u);
-  B.vact.ensure_n<unsigned char>(B.n_u);
-  B.sideK.ensure_n<unsigned char>((int64_t)K * kDenseMax);
-  B.noiCurK.ensure_n<int32_t>((int64_t)kSMs * kDenseMax);
+  W.ensure_vertices(n_u);
+  W.ensure_entries(m_u, n_u);
+  E.gidA.ensure_n<int32_t>(n_u);
+  E.gidB.ensure_n<int32_t>(n_u);
+  E.vact.ensure_n<unsigned char>(n_u);
+  E.om0.ensure_n<int32_t>(n_u);
+  E.oc1.ensure_n<int32_t>(n_u);
+  E.os1.ensure_n<unsigned char>(n_u);
+  E.ocap = n_u;
   B.bits_out.ensure_n<unsigned long long>(B.h_wbase[K]);
-  B.cut_out.ensure_n<long long>(K);
-  VC_CUDA(cudaMallocHost(&B.h_summary, sizeof(int) * kSummaryInts));
-  // per-graph constants: original bases and sizes
   std::vector<long long> norig(K);
   for (int g = 0; g < K; ++g) norig[g] = gs[g].n;
-  VC_CUDA(cudaMemcpyAsync(B.obase.p, B.h_vbase.data(), sizeof(long long) * K, cudaMemcpyHostToDevice, s));
-  VC_CUDA(cudaMemcpyAsync(B.norig.p, norig.data(), sizeof(long long) * K, cudaMemcpyHostToDevice, s));
+  VC_CUDA(cudaMemcpyAsync(E.obase.p, B.h_vbase.data(), sizeof(long long) * K, cudaMemcpyHostToDevice, s));
+  VC_CUDA(cudaMemcpyAsync(E.norig.p, norig.data(), sizeof(long long) * K, cudaMemcpyHostToDevice, s));
   VC_CUDA(cudaStreamSynchronize(s));
-}
-
-static void read_summary(Batch& B) {
-  VC_CUDA(cudaMemcpyAsync(B.h_summary, B.summary.p, sizeof(int) * kSummaryInts, cudaMemcpyDeviceToHost, B.stream));
-  VC_CUDA(cudaStreamSynchronize(B.stream));
 }
 
 static void batch_run(Batch& B, uint64_t seed, int lp_iters) {
   if (lp_iters < 0) throw Error{VIECUT_EINVAL, "lp_iters must be >= 0"};
-  VC_CUDA(cudaSetDevice(B.device));
-  cudaStream_t s = B.stream;
-  Workspace& W = *B.ws;
-  W.s = s;
+  Engine& E = B.E;
+  VC_CUDA(cudaSetDevice(E.device));
+  cudaStream_t s = E.stream;
+  E.ws->s = s;
+  E.lp_iters = lp_iters;
+  E.steps = 0;
   const unsigned long long launches0 = g_launches;
   cudaEvent_t e0, e1;
   VC_CUDA(cudaEventCreate(&e0));
   VC_CUDA(cudaEventCreate(&e1));
   VC_CUDA(cudaEventRecord(e0, s));
-  const int K = B.K;
-  BState S = B.state();
-  const int gK = (K + 255) / 256;
-  const int gridK = K < 4 * kSMs ? K : 4 * kSMs;
-
-  // the input union
-  GraphView G;
-  G.n = B.n_u;
-  G.nnz = B.m_u;
-  G.off = B.in_off.as<int64_t>();
-  G.adj = B.in_adj.as<int32_t>();
-  G.w = B.in_w.p;
-  G.wbytes = 4;
-  G.unit = B.unit;
-  G.simple = B.simple;
-  W.bins_valid = false;
-  int slot = -1;
-  int32_t* gid = B.gid.as<int32_t>();
-  int32_t* gid2 = B.gid2.as<int32_t>();
-  VC_CUDA(cudaMemcpyAsync(S.vbase, B.d_vbase0.p, sizeof(long long) * (K + 1), cudaMemcpyDeviceToDevice, s));
+  const int K = E.K;
+  const int64_t n_u = B.h_vbase[K], m_u = B.h_ebase[K];
+  // every slot holds its graph of the input union
+  E.G = GraphView();
+  E.G.n = n_u;
+  E.G.nnz = m_u;
+  E.G.off = E.in_off.as<int64_t>();
+  E.G.adj = E.in_adj.as<int32_t>();
+  E.G.w = E.in_w.p;
+  E.G.wbytes = 4;
+  E.G.unit = B.unit;
+  E.G.simple = B.simple;
+  E.ws->bins_valid = false;
+  E.slot = -1;
+  E.gid = E.gidA.as<int32_t>();
   {
-    std::vector<long long> nv(K);
-    for (int g = 0; g < K; ++g) nv[g] = B.h_vbase[g + 1] - B.h_vbase[g];
-    VC_CUDA(cudaMemcpyAsync(S.nv, nv.data(), sizeof(long long) * K, cudaMemcpyHostToDevice, s));
-    std::vector<long long> ne(K);
-    for (int g = 0; g < K; ++g) ne[g] = B.h_ebase[g + 1] - B.h_ebase[g];
-    VC_CUDA(cudaMemcpyAsync(S.nnz, ne.data(), sizeof(long long) * K, cudaMemcpyHostToDevice, s));
-    VC_CUDA(cudaMemsetAsync(S.noi_base, 0, sizeof(long long) * K, s));
+    std::vector<long long> nv(K), ne(K);
+    std::vector<int> first(K, 8);
+    std::vector<unsigned long long> sd(K, seed);
+    for (int g = 0; g < K; ++g) {
+      nv[g] = B.h_vbase[g + 1] - B.h_vbase[g];
+      ne[g] = B.h_ebase[g + 1] - B.h_ebase[g];
+    }
+    VC_CUDA(cudaMemcpyAsync(E.vbase.p, B.d_vbase0.p, sizeof(long long) * K, cudaMemcpyDeviceToDevice, s));
+    VC_CUDA(cudaMemcpyAsync(E.nv.p, nv.data(), sizeof(long long) * K, cudaMemcpyHostToDevice, s));
+    VC_CUDA(cudaMemcpyAsync(E.nnz.p, ne.data(), sizeof(long long) * K, cudaMemcpyHostToDevice, s));
+    VC_CUDA(cudaMemcpyAsync(E.first.p, first.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
+    VC_CUDA(cudaMemcpyAsync(E.seed.p, sd.data(), sizeof(unsigned long long) * K, cudaMemcpyHostToDevice, s));
     VC_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
   }
-  b_gid_init_k<<<gridK, 256, 0, s>>>(K, S.vbase, gid);
-  degrees(G, W.deg.as<long long>(), s);
-  b_segmin_k<<<gridK, 256, 0, s>>>(K, W.deg.as<long long>(), S, 0);
-  b_init_k<<<gK, 256, 0, s>>>(K, S, B.n0);
-  b_tier1_k<<<gridK, 256, 0, s>>>(K, S, nullptr, W.map0.as<int32_t>(), W.cur1.as<int32_t>(), 0);
-  count_launch(4);
-  VC_CHECK_LAUNCH();
-
-  int64_t steps = 0;
-  for (;;) {
-    VC_CUDA(cudaMemsetAsync(S.summary, 0, sizeof(int) * kSummaryInts, s));
-    b_summary_k<<<gK, 256, 0, s>>>(K, S);
-    count_launch();
-    read_summary(B);
-    const int* cnt = B.h_summary;
-    if (cnt[kBLP] + cnt[kBPRA] + cnt[kBPRB] + cnt[kBNoiS] + cnt[kBNoiD] + cnt[kBDone] == 0) break;
-    if (++steps > (int64_t)64 * (B.n_u + 16)) throw Error{VIECUT_ECUDA, "batch did not converge"};
-    int32_t* A = W.labA.as<int32_t>();
-    int32_t* Bl = W.labB.as<int32_t>();
-    iota(A, G.n, s);
-    iota(Bl, G.n, s);
-    int32_t* F = A;
-    BatchCtx bc;
-    bc.gid = gid;
-    bc.glam = S.lam;
-    bc.gact = S.gact;
-    bc.gchanged = S.changed;
-    if (cnt[kBLP] > 0) {
-      b_prepare_k<<<gK, 256, 0, s>>>(K, S, kBLP, seed);
-      b_vact_k<<<grid_for(G.n, 256, kSMs * 8), 256, 0, s>>>(G.n, gid, S.gact, B.vact.as<unsigned char>());
-      count_launch(2);
-      hash_table(G.n, 0, gid, S.gkey, S.vbase, W.hv.as<unsigned long long>(), s);
-      if (!W.bins_valid) W.build_bins(G);
-      GraphView Ga = G;
-      Ga.vact = B.vact.as<unsigned char>();
-      int32_t* in = nullptr;
-      int32_t* bufs[2] = {A, Bl};
-      for (int r = 0; r < lp_iters; ++r) {
-        lp_round(Ga, W.bins, W.gt, in, bufs[r & 1], W.hv.as<unsigned long long>(), s);
-        in = bufs[r & 1];
-      }
-      if (lp_iters > 0) F = in;
-    }
-    if (cnt[kBPRA] > 0) {
-      b_prepare_k<<<gK, 256, 0, s>>>(K, S, kBPRA, seed);
-      count_launch();
-      pr_partners(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), s);
-      pr_pass_a(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), W.st(),
-                W.parent.as<int32_t>(), F, nullptr, s, &bc);
-    }
-    if (cnt[kBPRB] > 0) {
-      b_prepare_k<<<gK, 256, 0, s>>>(K, S, kBPRB, seed);
-      count_launch();
-      pr_partners(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), s);
-      pr_pass_b(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), W.st(), F, nullptr, s, &bc);
-    }
-    if (cnt[kBNoiS] > 0) {
-      W.noi_r.ensure_n<long long>(G.n);
-      W.noi_seen.ensure_n<unsigned char>(G.n);
-      noi_round_batch(G, S.list_nois, cnt[10], S.vbase, S.nv, S.lam, W.noi_r.as<long long>(),
-                      W.noi_seen.as<unsigned char>(), W.parent.as<int32_t>(), F, S.changed, s);
-    }
-    if (cnt[kBNoiD] > 0) {
-      const int64_t mcap = (int64_t)cnt[7] * cnt[7];
-      const int blocks = cnt[kBNoiD] < kSMs ? cnt[kBNoiD] : kSMs;
-      long long* M = B.noiM.ensure_n<long long>(2 * mcap * blocks);
-      BatchNoi bn{S.lam, S.best_kind, S.nv, S.nnz, S.dmin, S.argmin, S.trace_len, S.trace, kBTraceCap, S.level};
-      noi_dense_batch(G, S.list_noid, cnt[kBNoiD], S.vbase, S.nv, M, mcap, blocks, B.noiCurK.as<int32_t>(),
-                      B.sideK.as<unsigned char>(), bn, s);
-    }
-    b_decide_k<<<gK, 256, 0, s>>>(K, S);
-    count_launch();
-    read_summary(B);
-    if (B.h_summary[8] > 0) {
-      b_drop_k<<<grid_for(G.n, 256, kSMs * 8), 256, 0, s>>>(G.n, gid, S.phase, F);
-      count_launch();
-      int dst = slot == 0 ? 1 : 0;
-      int32_t* cid = W.cidT.as<int32_t>();
-      const int64_t n_old = G.n;
-      GraphView h = W.contract(G, F, cid, dst);
-      b_shape_k<<<(K + 1 + 255) / 256, 256, 0, s>>>(K, S, n_old, h.n, W.rank.as<int32_t>(), h.off);
-      b_shape2_k<<<gK, 256, 0, s>>>(K, S, h.off);
-      b_gid_update_k<<<grid_for(n_old, 256, kSMs * 8), 256, 0, s>>>(n_old, cid, gid, gid2);
-      b_tier1_k<<<gridK, 256, 0, s>>>(K, S, cid, W.map0.as<int32_t>(), W.cur1.as<int32_t>(), 1);
-      b_copy_vbase_k<<<(K + 1 + 255) / 256, 256, 0, s>>>(K, S);
-      count_launch(5);
-      VC_CHECK_LAUNCH();
-      std::swap(gid, gid2);
-      G = h;
-      G.nnz = W.h_counters->pairs;  // upper bound; lists are exact through the offsets
-      slot = dst;
-      if (G.n > 0) {
-        degrees(G, W.deg.as<long long>(), s);
-        b_segmin_k<<<gridK, 256, 0, s>>>(K, W.deg.as<long long>(), S, 1);
-        b_snapshot_k<<<gridK, 256, 0, s>>>(K, S, W.cur1.as<int32_t>(), W.side1.as<unsigned char>());
-        count_launch(2);
-      }
-      b_trace_k<<<gK, 256, 0, s>>>(K, S);
-      count_launch();
-    }
-    b_transition_k<<<gK, 256, 0, s>>>(K, S, B.n0, B.pr_runs_max);
-    count_launch();
-    VC_CHECK_LAUNCH();
-  }
-  b_side_bits_k<<<gridK, 256, 0, s>>>(K, S, B.d_wbase.as<long long>(), W.map0.as<int32_t>(),
-                                      W.side1.as<unsigned char>(), W.cur1.as<int32_t>(), B.sideK.as<unsigned char>(),
+  BState S = E.state();
+  const int gridK = K < 4 * kSMs ? K : 4 * kSMs;
+  b_gid_init_k<<<gridK, 256, 0, s>>>(K, S, E.gid);
+  count_launch();
+  engine_start_new(E);
+  while (engine_step(E))
+    if (E.steps > (int64_t)64 * (n_u + 16)) throw Error{VIECUT_ECUDA, "batch did not converge"};
+  b_side_bits_k<<<gridK, 256, 0, s>>>(nullptr, K, S, B.d_wbase.as<long long>(), E.om0.as<int32_t>(),
+                                      E.os1.as<unsigned char>(), E.oc1.as<int32_t>(), E.sideK.as<unsigned char>(),
                                       B.bits_out.as<unsigned long long>());
   count_launch();
   VC_CHECK_LAUNCH();
@@ -649,15 +776,295 @@ static void batch_run(Batch& B, uint64_t seed, int lp_iters) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   B.stats.ms_total = ms;
-  B.stats.super_steps = steps;
+  B.stats.super_steps = E.steps;
   B.stats.kernel_launches = (int64_t)(g_launches - launches0);
   B.stats.graphs = K;
-  B.stats.vertices = B.n_u;
-  B.stats.entries = B.m_u;
+  B.stats.vertices = n_u;
+  B.stats.entries = m_u;
+}
+
+static void copy_trace(Engine& E, int g, viecut_step* steps, int64_t cap, int64_t* len) {
+  int tl = 0;
+  VC_CUDA(cudaMemcpy(&tl, (int*)E.trace_len.p + g, sizeof(int), cudaMemcpyDeviceToHost));
+  int cnt = tl < kBTraceCap ? tl : kBTraceCap;
+  std::vector<TraceStep> t(cnt);
+  if (cnt)
+    VC_CUDA(cudaMemcpy(t.data(), (TraceStep*)E.trace.p + (int64_t)g * kBTraceCap, sizeof(TraceStep) * cnt,
+                       cudaMemcpyDeviceToHost));
+  *len = tl;
+  for (int64_t i = 0; i < cap && i < cnt; ++i)
+    steps[i] = viecut_step{t[i].kind, t[i].level, t[i].n, t[i].nnz, t[i].lambda_hat};
+}
+
+// ------------------------------------------------------------------ server
+// A request's copy of its graph lives on the host until it joins the union; its
+// results are kept until the caller polls them.
+struct Request {
+  uint64_t ticket = 0;
+  int64_t n = 0, m = 0;
+  uint64_t seed = 0;
+  std::vector<int64_t> off;
+  std::vector<int32_t> adj, w;
+  bool simple = true;
+  int64_t est = 0;
+  int slot = -1;
+  int64_t obase = -1;
+  std::chrono::steady_clock::time_point t_submit, t_done;
+  bool done = false;
+  int64_t cut = 0;
+  std::vector<uint64_t> bits;
+};
+
+struct Server {
+  Engine E;
+  int64_t budget = 0;
+  int lp_iters = 2;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stopping = false;
+  std::thread th;
+  std::string error;  // set once the loop failed
+  std::deque<std::shared_ptr<Request>> pending;
+  std::map<uint64_t, std::shared_ptr<Request>> tickets;
+  std::vector<std::shared_ptr<Request>> slot_req;
+  std::vector<int> free_slots;
+  std::map<int64_t, int64_t> free_ranges;  // original-vertex arena: start -> length
+  int64_t budget_used = 0;
+  uint64_t next_ticket = 1;
+  bool all_simple = true;
+  int64_t admitted = 0, completed = 0, max_resident = 0, joins = 0;
+  std::vector<int> h_phase;
+  Buf d_join, d_list, d_wbase, d_bits, d_init;
+  std::vector<long long> h_join;
+};
+
+static int64_t request_estimate(int64_t n, int64_t m) {
+  // union CSR + workspace share per entry and per vertex (see DESIGN: memory layout)
+  return 96 * (m + n) + 64 * n + (1 << 16);
+}
+
+static int64_t arena_alloc(Server& S, int64_t n) {
+  for (;;) {
+    for (auto it = S.free_ranges.begin(); it != S.free_ranges.end(); ++it) {
+      if (it->second >= n) {
+        const int64_t at = it->first, len = it->second;
+        S.free_ranges.erase(it);
+        if (len > n) S.free_ranges[at + n] = len - n;
+        return at;
+      }
+    }
+    Engine& E = S.E;
+    const int64_t old = E.ocap, cap = std::max<int64_t>(2 * old, old + n);
+    grow_keep(E.om0, sizeof(int32_t) * cap, sizeof(int32_t) * old, E.stream);
+    grow_keep(E.oc1, sizeof(int32_t) * cap, sizeof(int32_t) * old, E.stream);
+    grow_keep(E.os1, cap, old, E.stream);
+    E.ocap = cap;
+    // merge the new tail with a free range ending at the old capacity
+    int64_t start = old, len = cap - old;
+    auto it = S.free_ranges.lower_bound(old);
+    if (it != S.free_ranges.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == old) { start = pv->first; len += pv->second; S.free_ranges.erase(pv); }
+    }
+    S.free_ranges[start] = len;
+  }
+}
+
+static void arena_free(Server& S, int64_t at, int64_t n) {
+  auto it = S.free_ranges.emplace(at, n).first;
+  auto nx = std::next(it);
+  if (nx != S.free_ranges.end() && at + n == nx->first) { it->second += nx->second; S.free_ranges.erase(nx); }
+  if (it != S.free_ranges.begin()) {
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) { pv->second += it->second; S.free_ranges.erase(it); }
+  }
+}
+
+// Appends the admitted requests to the union (a new union in the other coarse buffer:
+// the old union first, unchanged, then the new graphs) and starts their state.
+static void server_join(Server& S, std::vector<std::shared_ptr<Request>>& add) {
+  Engine& E = S.E;
+  Workspace& W = *E.ws;
+  cudaStream_t s = E.stream;
+  const int J = (int)add.size();
+  const int64_t n_u = E.G.n;
+  int64_t m_u = 0;  // exact entry count of the resident union: its last offset
+  if (n_u > 0) {
+    VC_CUDA(cudaMemcpyAsync(&m_u, E.G.off + n_u, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    VC_CUDA(cudaStreamSynchronize(s));
+  }
+  int64_t sn = 0, sm = 0;
+  for (auto& r : add) { sn += r->n; sm += r->m; }
+  const int64_t n_new = n_u + sn, m_new = m_u + sm;
+  if (n_new > 0x7fffffffLL) throw Error{VIECUT_ENOMEM, "the resident graphs exceed 2^31 vertices"};
+  for (auto& r : add) r->obase = arena_alloc(S, r->n);
+  // staged host copies -> device
+  Buf st_off, st_adj, st_w;
+  int64_t* d_off = st_off.ensure_n<int64_t>(sn);
+  int32_t* d_adj = st_adj.ensure_n<int32_t>(sm);
+  int32_t* d_w = st_w.ensure_n<int32_t>(sm);
+  S.h_join.assign(4 * (J + 1), 0);
+  long long* jv = S.h_join.data();
+  long long* je = jv + (J + 1);
+  long long* sv = je + (J + 1);
+  long long* se = sv + (J + 1);
+  for (int j = 0; j < J; ++j) {
+    const auto& r = add[j];
+    jv[j] = n_u + sv[j];
+    je[j] = m_u + se[j];
+    sv[j + 1] = sv[j] + r->n;
+    se[j + 1] = se[j] + r->m;
+    VC_CUDA(cudaMemcpyAsync(d_off + sv[j], r->off.data(), sizeof(int64_t) * r->n, cudaMemcpyHostToDevice, s));
+    if (r->m > 0) {
+      VC_CUDA(cudaMemcpyAsync(d_adj + se[j], r->adj.data(), sizeof(int32_t) * r->m, cudaMemcpyHostToDevice, s));
+      VC_CUDA(cudaMemcpyAsync(d_w + se[j], r->w.data(), sizeof(int32_t) * r->m, cudaMemcpyHostToDevice, s));
+    }
+  }
+  long long* dj = S.d_join.ensure_n<long long>(4 * (J + 1));
+  VC_CUDA(cudaMemcpyAsync(dj, jv, sizeof(long long) * 4 * (J + 1), cudaMemcpyHostToDevice, s));
+  const int dst = E.slot == 0 ? 1 : 0;
+  int64_t* off = W.coff[dst].ensure_n<int64_t>(n_new + 1);
+  int32_t* adj = W.cadj[dst].ensure_n<int32_t>(m_new);
+  long long* w = W.cw[dst].ensure_n<long long>(m_new);
+  if (n_u > 0) {
+    VC_CUDA(cudaMemcpyAsync(off, E.G.off, sizeof(int64_t) * n_u, cudaMemcpyDeviceToDevice, s));
+    VC_CUDA(cudaMemcpyAsync(adj, E.G.adj, sizeof(int32_t) * m_u, cudaMemcpyDeviceToDevice, s));
+    VC_CUDA(cudaMemcpyAsync(w, E.G.w, sizeof(long long) * m_u, cudaMemcpyDeviceToDevice, s));
+  }
+  b_join_k<<<J < 4 * kSMs ? J : 4 * kSMs, 256, 0, s>>>(J, dj, dj + (J + 1), dj + 2 * (J + 1), dj + 3 * (J + 1), d_off,
+                                                      d_adj, d_w, off, adj, w);
+  b_set_i64_k<<<1, 1, 0, s>>>(off + n_new, m_new);
+  count_launch(2);
+  VC_CHECK_LAUNCH();
+  // vertex -> slot map: keep the old entries
+  const bool onA = E.gid == E.gidA.as<int32_t>() || E.gid == nullptr;
+  Buf& cur = onA ? E.gidA : E.gidB;
+  Buf& alt = onA ? E.gidB : E.gidA;
+  grow_keep(cur, sizeof(int32_t) * std::max<int64_t>(n_new, 1), sizeof(int32_t) * n_u, s);
+  alt.ensure_n<int32_t>(n_new);
+  E.gid = cur.as<int32_t>();
+  // slot records
+  std::vector<SlotInit> init(J);
+  for (int j = 0; j < J; ++j)
+    init[j] = SlotInit{add[j]->slot, 0, jv[j], add[j]->n, add[j]->m, add[j]->obase, add[j]->seed};
+  SlotInit* di = (SlotInit*)S.d_init.ensure(sizeof(SlotInit) * J);
+  VC_CUDA(cudaMemcpyAsync(di, init.data(), sizeof(SlotInit) * J, cudaMemcpyHostToDevice, s));
+  BState B = E.state();
+  b_slot_init_k<<<(J + 255) / 256, 256, 0, s>>>(J, di, B);
+  const int K = E.K, gridK = K < 4 * kSMs ? K : 4 * kSMs;
+  b_gid_init_k<<<gridK, 256, 0, s>>>(K, B, E.gid);
+  count_launch(2);
+  VC_CHECK_LAUNCH();
+  for (auto& r : add) S.all_simple = S.all_simple && r->simple;
+  E.G = GraphView();
+  E.G.n = n_new;
+  E.G.nnz = m_new;
+  E.G.off = off;
+  E.G.adj = adj;
+  E.G.w = w;
+  E.G.wbytes = 8;
+  E.G.simple = S.all_simple;
+  E.slot = dst;
+  W.bins_valid = false;
+  W.ensure_vertices(n_new);
+  W.ensure_entries(m_new, n_new);
+  E.vact.ensure_n<unsigned char>(n_new);
+  engine_start_new(E);
+  VC_CUDA(cudaStreamSynchronize(s));  // staging buffers and host vectors go out of scope
+  S.joins += 1;
+}
+
+// Reads out every slot whose graph finished in the last super-step.
+static void server_collect(Server& S) {
+  Engine& E = S.E;
+  cudaStream_t s = E.stream;
+  const int K = E.K;
+  S.h_phase.resize(K);
+  VC_CUDA(cudaMemcpyAsync(S.h_phase.data(), E.phase.p, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
+  VC_CUDA(cudaStreamSynchronize(s));
+  std::vector<int> fin;
+  for (int g = 0; g < K; ++g)
+    if (S.slot_req[g] && S.h_phase[g] == kBGone) fin.push_back(g);
+  if (fin.empty()) return;
+  const int F = (int)fin.size();
+  std::vector<long long> wb(F + 1, 0);
+  for (int i = 0; i < F; ++i) wb[i + 1] = wb[i] + (S.slot_req[fin[i]]->n + 63) / 64;
+  int32_t* dl = S.d_list.ensure_n<int32_t>(F);
+  long long* dw = S.d_wbase.ensure_n<long long>(F + 1);
+  unsigned long long* db = S.d_bits.ensure_n<unsigned long long>(wb[F]);
+  VC_CUDA(cudaMemcpyAsync(dl, fin.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, s));
+  VC_CUDA(cudaMemcpyAsync(dw, wb.data(), sizeof(long long) * (F + 1), cudaMemcpyHostToDevice, s));
+  BState B = E.state();
+  b_side_bits_k<<<F < 4 * kSMs ? F : 4 * kSMs, 256, 0, s>>>(dl, F, B, dw, E.om0.as<int32_t>(), E.os1.as<unsigned char>(),
+                                                           E.oc1.as<int32_t>(), E.sideK.as<unsigned char>(), db);
+  count_launch();
+  VC_CHECK_LAUNCH();
+  std::vector<uint64_t> bits(wb[F]);
+  std::vector<long long> lam(K);
+  VC_CUDA(cudaMemcpyAsync(bits.data(), db, sizeof(uint64_t) * wb[F], cudaMemcpyDeviceToHost, s));
+  VC_CUDA(cudaMemcpyAsync(lam.data(), E.lam.p, sizeof(long long) * K, cudaMemcpyDeviceToHost, s));
+  VC_CUDA(cudaStreamSynchronize(s));
+  const auto now = std::chrono::steady_clock::now();
+  std::lock_guard<std::mutex> lk(S.mu);
+  for (int i = 0; i < F; ++i) {
+    auto r = S.slot_req[fin[i]];
+    r->cut = lam[fin[i]];
+    r->bits.assign(bits.begin() + wb[i], bits.begin() + wb[i + 1]);
+    r->t_done = now;
+    r->done = true;
+    arena_free(S, r->obase, r->n);
+    S.budget_used -= r->est;
+    S.free_slots.push_back(fin[i]);
+    S.slot_req[fin[i]].reset();
+    S.completed += 1;
+  }
+}
+
+static void server_loop(Server& S) {
+  Engine& E = S.E;
+  try {
+    VC_CUDA(cudaSetDevice(E.device));
+    for (;;) {
+      std::vector<std::shared_ptr<Request>> add;
+      int resident = 0;
+      {
+        std::unique_lock<std::mutex> lk(S.mu);
+        if (S.stopping) break;
+        while (!S.pending.empty() && !S.free_slots.empty() && S.budget_used + S.pending.front()->est <= S.budget) {
+          auto r = S.pending.front();
+          S.pending.pop_front();
+          r->slot = S.free_slots.back();
+          S.free_slots.pop_back();
+          S.budget_used += r->est;
+          S.slot_req[r->slot] = r;
+          add.push_back(r);
+          S.admitted += 1;
+        }
+        for (auto& x : S.slot_req) resident += x ? 1 : 0;
+        S.max_resident = std::max<int64_t>(S.max_resident, resident);
+        if (add.empty() && resident == 0) {
+          S.cv.wait_for(lk, std::chrono::milliseconds(20));
+          continue;
+        }
+      }
+      if (!add.empty()) {
+        server_join(S, add);
+        for (auto& r : add) {  // the host copy is on the device now
+          std::vector<int64_t>().swap(r->off);
+          std::vector<int32_t>().swap(r->adj);
+          std::vector<int32_t>().swap(r->w);
+        }
+      }
+      engine_step(E);
+      server_collect(S);
+    }
+  } catch (const Error& e) {
+    std::lock_guard<std::mutex> lk(S.mu);
+    S.error = e.msg.empty() ? "server failed" : e.msg;
+  }
 }
 
 }  // namespace vc
-
 struct viecut_batch {
   vc::Batch b;
 };
@@ -690,36 +1097,27 @@ int viecut_batch_run(viecut_batch* bt, uint64_t seed, int32_t lp_iters, int64_t*
   if (!bt || !cut_values) throw Error{VIECUT_EINVAL, "null argument"};
   vc::Batch& B = bt->b;
   vc::batch_run(B, seed, lp_iters);
-  VC_CUDA(cudaMemcpyAsync(cut_values, B.lam.p, sizeof(int64_t) * B.K, cudaMemcpyDeviceToHost, B.stream));
+  VC_CUDA(cudaMemcpyAsync(cut_values, B.E.lam.p, sizeof(int64_t) * B.E.K, cudaMemcpyDeviceToHost, B.E.stream));
   if (side_bits)
-    VC_CUDA(cudaMemcpyAsync(side_bits, B.bits_out.p, sizeof(uint64_t) * B.h_wbase[B.K], cudaMemcpyDeviceToHost,
-                            B.stream));
-  VC_CUDA(cudaStreamSynchronize(B.stream));
+    VC_CUDA(cudaMemcpyAsync(side_bits, B.bits_out.p, sizeof(uint64_t) * B.h_wbase[B.E.K], cudaMemcpyDeviceToHost,
+                            B.E.stream));
+  VC_CUDA(cudaStreamSynchronize(B.E.stream));
   VC_API_END
 }
 
 int viecut_batch_side_words(const viecut_batch* bt, int64_t* words) {
   VC_API_BEGIN
   if (!bt || !words) throw Error{VIECUT_EINVAL, "null argument"};
-  *words = bt->b.h_wbase[bt->b.K];
+  *words = bt->b.h_wbase[bt->b.E.K];
   VC_API_END
 }
 
 int viecut_batch_get_trace(const viecut_batch* bt, int32_t g, viecut_step* steps, int64_t cap, int64_t* len) {
   VC_API_BEGIN
-  if (!bt || !len || g < 0 || g >= bt->b.K) throw Error{VIECUT_EINVAL, "bad graph index"};
-  const vc::Batch& B = bt->b;
-  VC_CUDA(cudaSetDevice(B.device));
-  int tl = 0;
-  VC_CUDA(cudaMemcpy(&tl, (int*)B.trace_len.p + g, sizeof(int), cudaMemcpyDeviceToHost));
-  int cnt = tl < vc::kBTraceCap ? tl : vc::kBTraceCap;
-  std::vector<vc::TraceStep> t(cnt);
-  if (cnt)
-    VC_CUDA(cudaMemcpy(t.data(), (vc::TraceStep*)B.trace.p + (int64_t)g * vc::kBTraceCap, sizeof(vc::TraceStep) * cnt,
-                       cudaMemcpyDeviceToHost));
-  *len = tl;
-  for (int64_t i = 0; i < cap && i < cnt; ++i)
-    steps[i] = viecut_step{t[i].kind, t[i].level, t[i].n, t[i].nnz, t[i].lambda_hat};
+  if (!bt || !len || g < 0 || g >= bt->b.E.K) throw Error{VIECUT_EINVAL, "bad graph index"};
+  vc::Engine& E = const_cast<viecut_batch*>(bt)->b.E;
+  VC_CUDA(cudaSetDevice(E.device));
+  vc::copy_trace(E, g, steps, cap, len);
   VC_API_END
 }
 
@@ -733,9 +1131,143 @@ int viecut_batch_get_stats(const viecut_batch* bt, viecut_batch_stats* st) {
 int viecut_batch_destroy(viecut_batch* bt) {
   VC_API_BEGIN
   if (!bt) return VIECUT_OK;
-  cudaSetDevice(bt->b.device);
-  if (bt->b.stream) cudaStreamSynchronize(bt->b.stream);
+  cudaSetDevice(bt->b.E.device);
+  if (bt->b.E.stream) cudaStreamSynchronize(bt->b.E.stream);
   delete bt;
+  VC_API_END
+}
+
+
+struct viecut_server {
+  vc::Server s;
+};
+
+int viecut_server_opts_init(viecut_server_opts* o) {
+  if (!o) return VIECUT_EINVAL;
+  memset(o, 0, sizeof(*o));
+  viecut_opts_init(&o->base);
+  o->hbm_budget_bytes = (int64_t)120 << 30;
+  o->max_slots = 1024;
+  o->lp_iters = 2;
+  return VIECUT_OK;
+}
+
+int viecut_server_start(viecut_server** out, const viecut_server_opts* opts) {
+  VC_API_BEGIN
+  if (!out) throw Error{VIECUT_EINVAL, "null server pointer"};
+  *out = nullptr;
+  viecut_server_opts o;
+  viecut_server_opts_init(&o);
+  if (opts) o = *opts;
+  if (o.max_slots < 1 || o.hbm_budget_bytes < 1 || o.lp_iters < 0 || o.base.n0 < 1 || o.base.pr_runs_max < 0)
+    throw Error{VIECUT_EINVAL, "bad server options"};
+  auto* x = new viecut_server;
+  try {
+    vc::Server& S = x->s;
+    vc::engine_setup(S.E, o.max_slots, o.base);
+    S.E.lp_iters = o.lp_iters;
+    S.lp_iters = o.lp_iters;
+    S.budget = o.hbm_budget_bytes;
+    S.slot_req.assign(o.max_slots, nullptr);
+    for (int g = o.max_slots - 1; g >= 0; --g) S.free_slots.push_back(g);
+    S.th = std::thread(vc::server_loop, std::ref(S));
+  } catch (...) {
+    delete x;
+    throw;
+  }
+  *out = x;
+  VC_API_END
+}
+
+int viecut_server_submit(viecut_server* sv, const viecut_graph_desc* g, uint64_t seed, uint64_t* ticket) {
+  VC_API_BEGIN
+  if (!sv || !g || !ticket) throw Error{VIECUT_EINVAL, "null argument"};
+  vc::Server& S = sv->s;
+  const int64_t n = g->n, m = g->m;
+  if (n < 2 || m < 0 || !g->offsets || (m > 0 && (!g->adj || !g->weights)))
+    throw Error{VIECUT_EINVAL, "graph: n must be >= 2 and arrays non-null"};
+  if (g->offsets[0] != 0 || g->offsets[n] != m) throw Error{VIECUT_EINVAL, "graph: offsets[0] != 0 or offsets[n] != m"};
+  auto r = std::make_shared<vc::Request>();
+  r->n = n;
+  r->m = m;
+  r->seed = seed;
+  r->off.assign(g->offsets, g->offsets + n);
+  r->adj.assign(g->adj, g->adj + m);
+  r->w.assign(g->weights, g->weights + m);
+  for (int64_t v = 0; v < n; ++v) {
+    if (g->offsets[v + 1] < g->offsets[v]) throw Error{VIECUT_EINVAL, "graph: offsets decrease"};
+    for (int64_t e = g->offsets[v]; e < g->offsets[v + 1]; ++e) {
+      const int32_t u = g->adj[e];
+      if (u < 0 || u >= n) throw Error{VIECUT_EINVAL, "graph: neighbour id out of range"};
+      if (u == v) throw Error{VIECUT_EINVAL, "graph: self-loop"};
+      if (g->weights[e] < 1) throw Error{VIECUT_EINVAL, "graph: weight < 1"};
+      if (e + 1 < g->offsets[v + 1] && g->adj[e + 1] <= u) r->simple = false;
+    }
+  }
+  r->est = vc::request_estimate(n, m);
+  if (r->est > S.budget) throw Error{VIECUT_EINVAL, "graph needs more than the server's memory budget"};
+  r->t_submit = std::chrono::steady_clock::now();
+  {
+    std::lock_guard<std::mutex> lk(S.mu);
+    if (!S.error.empty()) throw Error{VIECUT_ECUDA, S.error};
+    r->ticket = S.next_ticket++;
+    S.tickets[r->ticket] = r;
+    S.pending.push_back(r);
+  }
+  S.cv.notify_one();
+  *ticket = r->ticket;
+  VC_API_END
+}
+
+int viecut_server_poll(viecut_server* sv, uint64_t ticket, int64_t* cut, uint64_t* side_bits, double* latency_ms) {
+  VC_API_BEGIN
+  if (!sv) throw Error{VIECUT_EINVAL, "null server"};
+  vc::Server& S = sv->s;
+  std::shared_ptr<vc::Request> r;
+  {
+    std::lock_guard<std::mutex> lk(S.mu);
+    auto it = S.tickets.find(ticket);
+    if (it == S.tickets.end()) throw Error{VIECUT_EINVAL, "unknown ticket"};
+    if (!it->second->done) {
+      if (!S.error.empty()) throw Error{VIECUT_ECUDA, S.error};
+      return VIECUT_EBUSY;
+    }
+    r = it->second;
+    S.tickets.erase(it);
+  }
+  if (cut) *cut = r->cut;
+  if (side_bits && !r->bits.empty()) memcpy(side_bits, r->bits.data(), sizeof(uint64_t) * r->bits.size());
+  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  VC_API_END
+}
+
+int viecut_server_get_stats(viecut_server* sv, viecut_server_stats* st) {
+  VC_API_BEGIN
+  if (!sv || !st) throw Error{VIECUT_EINVAL, "null argument"};
+  vc::Server& S = sv->s;
+  std::lock_guard<std::mutex> lk(S.mu);
+  st->admitted = S.admitted;
+  st->completed = S.completed;
+  st->pending = (int64_t)S.pending.size();
+  st->max_resident = S.max_resident;
+  st->super_steps = S.E.steps;
+  st->joins = S.joins;
+  st->budget_used = S.budget_used;
+  VC_API_END
+}
+
+int viecut_server_stop(viecut_server* sv) {
+  VC_API_BEGIN
+  if (!sv) return VIECUT_OK;
+  {
+    std::lock_guard<std::mutex> lk(sv->s.mu);
+    sv->s.stopping = true;
+  }
+  sv->s.cv.notify_all();
+  if (sv->s.th.joinable()) sv->s.th.join();
+  cudaSetDevice(sv->s.E.device);
+  if (sv->s.E.stream) cudaStreamSynchronize(sv->s.E.stream);
+  delete sv;
   VC_API_END
 }
 

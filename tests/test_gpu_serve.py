@@ -1,0 +1,109 @@
+"""Serving with continuous batching: requests submitted while others are resident
+join the device-resident set at the next super-step; every result (cut value and side
+bitmap) equals the oracle's and the single-graph run's for that graph alone."""
+import random
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+import paper_1708_06127_gb300 as vc
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    vc.build()
+
+
+def request_mix(count, seed):
+    rnd = random.Random(seed)
+    out = []
+    for i in range(count):
+        r = rnd.random()
+        if r < 0.5:
+            g = gg.core_lcc(gg.rhg(int(2 ** rnd.uniform(10, 15)), 32, 1000 * seed + i), 0)
+        elif r < 0.8:
+            g = gg.with_pair_weights(gg.core_lcc(gg.er(rnd.randint(100, 3000), rnd.uniform(4, 12), 7 * i + seed), 0),
+                                     i, 1, 10)
+        else:
+            g = rnd.choice([H.pr2_counterexample(), H.two_cliques(9, 2), H.random_graph(40, 0.2, 5 * i + seed),
+                            gg.from_edges(5, [(0, 1, 1), (1, 2, 1), (0, 2, 1)])])
+        out.append((g, rnd.randint(1, 1 << 30)))
+    return out
+
+
+def check_result(g, seed, res, n0=10000):
+    cut, bits, lat = res
+    ref = oracle.viecut(g.offsets, g.adj, g.w, seed=seed, lp_iters=2, n0=n0)
+    assert cut == ref.cut, g.name
+    assert np.array_equal(bits[: len(ref.side_bits)], ref.side_bits), g.name
+    assert lat >= 0
+
+
+def test_serve_staggered_arrivals_equal_alone():
+    reqs = request_mix(40, 3)
+    with vc.Server(max_slots=64) as srv:
+        tickets = []
+        for i, (g, seed) in enumerate(reqs):
+            tickets.append(srv.submit(g.offsets, g.adj, g.w, seed))
+            if i % 5 == 4:
+                time.sleep(0.002)  # later requests arrive while earlier ones are resident
+        results = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+    for (g, seed), res in zip(reqs, results):
+        check_result(g, seed, res)
+    assert st["completed"] == len(reqs) and st["admitted"] == len(reqs)
+    assert st["joins"] >= 2, st          # admitted in several waves
+    assert st["max_resident"] >= 2, st   # work overlapped on the device
+    # alone: the plain single-graph path gives the same answers
+    for (g, seed), (cut, bits, _) in list(zip(reqs, results))[:8]:
+        with vc.MinCut(g.offsets, g.adj, g.w) as mc:
+            c, b = mc.run(seed, 2)
+        assert c == cut and np.array_equal(b, bits[: len(b)])
+
+
+def test_serve_concurrent_submitters_and_small_budget():
+    reqs = request_mix(24, 9)
+    budget = 3 * max(96 * (g.nnz + g.n) + 64 * g.n + (1 << 16) for g, _ in reqs)
+    out = {}
+    with vc.Server(hbm_budget_bytes=budget, max_slots=16, n0=64) as srv:
+        def submitter(part):
+            for g, seed in part:
+                t = srv.submit(g.offsets, g.adj, g.w, seed)
+                out[t] = (g, seed)
+                time.sleep(0.001)
+        th = [threading.Thread(target=submitter, args=(reqs[k::3],)) for k in range(3)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        results = {t: srv.wait(t) for t in list(out)}
+        st = srv.stats()
+    for t, res in results.items():
+        g, seed = out[t]
+        check_result(g, seed, res, n0=64)
+    assert st["completed"] == len(reqs) and st["budget_used"] == 0
+
+
+def test_serve_rejects_bad_requests():
+    with vc.Server(hbm_budget_bytes=1 << 20) as srv:
+        big = gg.core_lcc(gg.rhg(1 << 14, 32, 1), 0)
+        with pytest.raises(vc.ViecutError) as e:
+            srv.submit(big.offsets, big.adj, big.w, 1)
+        assert e.value.code == vc.VIECUT_EINVAL and "budget" in str(e.value)
+        bad = gg.from_edges(3, [(0, 1, 1), (1, 2, 1)])
+        bad.adj[0] = 0  # self-loop at vertex 0
+        with pytest.raises(vc.ViecutError) as e:
+            srv.submit(bad.offsets, bad.adj, bad.w, 1)
+        assert e.value.code == vc.VIECUT_EINVAL
+        with pytest.raises(vc.ViecutError):
+            vc.viecut_server_poll(srv.s, 12345, 3)
