@@ -263,10 +263,30 @@ __global__ void __launch_bounds__(kAggThreads) lp_first_simple_k(int64_t n, int 
       if (lane == 0) lab_out[v] = (int32_t)v;
       continue;
     }
-    LaneBest lb;
-    first_scan(lb, beg + lane, end, 32, adj, w, hv);
-    Cand cd = warp_best(lb.done(hv));
-    if (lane == 0) lab_out[v] = cd.l;
+    if (std::is_same<WT, UnitW>::value) {
+      // unit weights: every neighbour has strength 1, so the choice is the neighbour
+      // of largest tie hash (distinct labels have distinct hashes); bl = INT_MAX marks
+      // a lane without entries
+      unsigned long long bh = 0;
+      int bl = INT_MAX;
+      for (int64_t e = beg + lane; e < end; e += 32) {
+        const int u = __ldg(adj + e);
+        const unsigned long long h = __ldg(hv + u);
+        if (bl == INT_MAX || h > bh || (h == bh && u < bl)) { bh = h; bl = u; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long oh = __shfl_xor_sync(0xffffffffu, bh, o);
+        const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+        if (ol != INT_MAX && (bl == INT_MAX || oh > bh || (oh == bh && ol < bl))) { bh = oh; bl = ol; }
+      }
+      if (lane == 0) lab_out[v] = bl;
+    } else {
+      LaneBest lb;
+      first_scan(lb, beg + lane, end, 32, adj, w, hv);
+      Cand cd = warp_best(lb.done(hv));
+      if (lane == 0) lab_out[v] = cd.l;
+    }
   }
 }
 

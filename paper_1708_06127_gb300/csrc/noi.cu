@@ -335,39 +335,111 @@ __device__ __forceinline__ void noi_round_body(int64_t lo, int64_t hi, const int
   __syncthreads();
 }
 
+// ---- the same round by one warp, for any n (arrays in global memory).  The next
+// vertex is found in two levels: cmax[c] holds the largest attachment r of the
+// unvisited vertices of chunk c = 32 consecutive vertices (-1: all visited); the warp
+// picks the chunk of largest cmax (ties: lower chunk, hence smaller ids), then the
+// vertex of largest r in it (ties: smallest id).  Relaxing a neighbour raises its
+// chunk's maximum with atomicMax; visiting a vertex recomputes its chunk's maximum.
+
+// argmax over the warp of (val, -idx) for val >= 0 (val < 0: no candidate); returns
+// idx, or -1 if no lane has a candidate; *best = the value.
+__device__ __forceinline__ int warp_argmax_vi(long long val, int idx, long long* best) {
+  const unsigned long long u = (unsigned long long)(val + 1);  // 0 = none
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+  const unsigned long long mu = ((unsigned long long)mh << 32) | ml;
+  const unsigned wi = __reduce_min_sync(0xffffffffu, (u == mu && u != 0) ? (unsigned)idx : 0xffffffffu);
+  *best = (long long)mu - 1;
+  return mu == 0 ? -1 : (int)wi;
+}
+
 template <typename WT>
-__global__ void __launch_bounds__(kSparseThreads) noi_round_k(int64_t n, const int64_t* __restrict__ off,
-                                                              const int32_t* __restrict__ adj,
-                                                              const WT* __restrict__ w, const DevState* st,
-                                                              long long* r, unsigned char* seen, int32_t* parent,
-                                                              int32_t* labels, int* changed) {
-  noi_round_body<WT>(0, n, off, adj, w, st->lambda_hat, r, seen, parent, labels, changed);
+__device__ __forceinline__ void noi_round_warp(int64_t lo, int64_t hi, const int64_t* __restrict__ off,
+                                               const int32_t* __restrict__ adj, const WT* __restrict__ w,
+                                               long long lam, long long* r, unsigned char* seen, int32_t* parent,
+                                               long long* cmax, int32_t* labels, int* any_out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = hi - lo;
+  const int64_t nc = (n + 31) >> 5;
+  for (int64_t k = lane; k < n; k += 32) { r[lo + k] = 0; seen[lo + k] = 0; parent[lo + k] = (int32_t)(lo + k); }
+  for (int64_t c = lane; c < nc; c += 32) cmax[c] = 0;
+  __syncwarp();
+  long long best;
+  for (int64_t step = 0; step < n; ++step) {
+    long long bv = -1;
+    int bc = -1;
+    for (int64_t c = lane; c < nc; c += 32) {
+      const long long m = cmax[c];
+      if (m > bv) { bv = m; bc = (int)c; }
+    }
+    const int C = warp_argmax_vi(bv, bc, &best);
+    const int64_t k = (int64_t)C * 32 + lane;
+    const long long rv = (k < n && !seen[lo + k]) ? r[lo + k] : -1;
+    const int xl = warp_argmax_vi(rv, (int)k, &best);
+    const int64_t x = lo + xl;
+    if (k == xl) seen[x] = 1;
+    warp_argmax_vi(k == xl ? -1 : rv, (int)k, &best);  // the chunk's maximum without x
+    if (lane == 0) cmax[C] = best;
+    __syncwarp();
+    for (int64_t e = off[x] + lane; e < off[x + 1]; e += 32) {
+      const int y = adj[e];
+      if (seen[y]) continue;
+      const long long c = (long long)w[e];
+      const long long ry = (long long)atomicAdd((unsigned long long*)&r[y], (unsigned long long)c) + c;
+      atomicMax(&cmax[(y - lo) >> 5], ry);
+      if (ry >= lam) sunite(parent, (int)x, y);
+    }
+    __syncwarp();
+  }
+  int any = 0;
+  for (int64_t k = lane; k < n; k += 32) {
+    const int rt = sfind(parent, (int)(lo + k));
+    labels[lo + k] = rt;
+    any |= rt != lo + k;
+  }
+  if (__any_sync(0xffffffffu, any) && lane == 0) atomicOr(any_out, 1);
+  __syncwarp();
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(32) noi_round_k(int64_t n, const int64_t* __restrict__ off,
+                                                  const int32_t* __restrict__ adj, const WT* __restrict__ w,
+                                                  const DevState* st, long long* r, unsigned char* seen,
+                                                  int32_t* parent, long long* cmax, int32_t* labels, int* changed) {
+  noi_round_warp<WT>(0, n, off, adj, w, st->lambda_hat, r, seen, parent, cmax, labels, changed);
 }
 
 void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, unsigned char* seen,
                       int32_t* parent, int32_t* labels, int* changed, cudaStream_t s) {
+  // r holds 2n entries: the attachments, then the chunk maxima
+  long long* cmax = r + g.n;
   if (g.wbytes == 4)
-    noi_round_k<int32_t><<<1, kSparseThreads, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, st, r, seen, parent,
-                                                       labels, changed);
+    noi_round_k<int32_t><<<1, 32, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, st, r, seen, parent, cmax, labels,
+                                          changed);
   else
-    noi_round_k<long long><<<1, kSparseThreads, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, st, r, seen,
-                                                         parent, labels, changed);
+    noi_round_k<long long><<<1, 32, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, st, r, seen, parent, cmax,
+                                            labels, changed);
   count_launch();
   VC_CHECK_LAUNCH();
 }
 
-// Batches: one round for each listed graph, a block per graph (persistent grid).
+// Batches: one round for each listed graph, a warp per graph (persistent grid of
+// 8-warp blocks pulling graphs from the list).
 template <typename WT>
-__global__ void __launch_bounds__(kSparseThreads) noi_round_batch_k(const int32_t* __restrict__ list, int count,
-                                                                    const int64_t* __restrict__ off,
-                                                                    const int32_t* __restrict__ adj,
-                                                                    const WT* __restrict__ w, const long long* vbase,
-                                                                    const long long* nv, const long long* glam,
-                                                                    long long* r, unsigned char* seen,
-                                                                    int32_t* parent, int32_t* labels, int* gchanged) {
-  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+__global__ void __launch_bounds__(256) noi_round_batch_k(const int32_t* __restrict__ list, int count,
+                                                         const int64_t* __restrict__ off,
+                                                         const int32_t* __restrict__ adj, const WT* __restrict__ w,
+                                                         const long long* vbase, const long long* nv,
+                                                         const long long* glam, long long* r, unsigned char* seen,
+                                                         int32_t* parent, long long* cmax, int32_t* labels,
+                                                         int* gchanged) {
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < count; idx += warps) {
     const int g = list[idx];
-    noi_round_body<WT>(vbase[g], vbase[g] + nv[g], off, adj, w, glam[g], r, seen, parent, labels, gchanged + g);
+    const long long lo = vbase[g];
+    noi_round_warp<WT>(lo, lo + nv[g], off, adj, w, glam[g], r, seen, parent, cmax + lo, labels, gchanged + g);
   }
 }
 
@@ -375,14 +447,15 @@ void noi_round_batch(const GraphView& u, const int32_t* list, int count, const l
                      const long long* glam, long long* r, unsigned char* seen, int32_t* parent, int32_t* labels,
                      int* gchanged, cudaStream_t s) {
   if (count <= 0) return;
-  int blocks = count < kSMs ? count : kSMs;
+  // r holds 2 x (union size) entries: attachments, then each graph's chunk maxima at its own range
+  long long* cmax = r + u.n;
+  const int blocks = grid_for(count, 8, kSMs * 4);
   if (u.wbytes == 4)
-    noi_round_batch_k<int32_t><<<blocks, kSparseThreads, 0, s>>>(list, count, u.off, u.adj, (const int32_t*)u.w,
-                                                                  vbase, nv, glam, r, seen, parent, labels, gchanged);
+    noi_round_batch_k<int32_t><<<blocks, 256, 0, s>>>(list, count, u.off, u.adj, (const int32_t*)u.w, vbase, nv, glam,
+                                                      r, seen, parent, cmax, labels, gchanged);
   else
-    noi_round_batch_k<long long><<<blocks, kSparseThreads, 0, s>>>(list, count, u.off, u.adj,
-                                                                    (const long long*)u.w, vbase, nv, glam, r, seen,
-                                                                    parent, labels, gchanged);
+    noi_round_batch_k<long long><<<blocks, 256, 0, s>>>(list, count, u.off, u.adj, (const long long*)u.w, vbase, nv,
+                                                        glam, r, seen, parent, cmax, labels, gchanged);
   count_launch();
   VC_CHECK_LAUNCH();
 }
