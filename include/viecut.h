@@ -61,6 +61,10 @@ typedef struct viecut_opts {
                           the device (default); 2 = the same checks plus symmetry, on the
                           host (create from host arrays; O(m log m)) */
   int32_t timing;      /* 1 = record per-phase CUDA-event times (viecut_get_stats) */
+  int32_t lp_group;    /* lanes per vertex of the first-round label-propagation kernel:
+                          8, 16 or 32, or 0 = pick by timing once per handle (default);
+                          results never depend on it */
+  int32_t emit_group;  /* lanes per vertex of the contraction's pre-merge kernel (same) */
 } viecut_opts;
 
 /* Per-run statistics (valid after viecut_run / viecut_run_device completes). */
@@ -81,6 +85,9 @@ typedef struct viecut_stats {
   int64_t lp_bytes;      /* algorithmic bytes of the timed label-propagation rounds:
                             8(n+1) offsets + nnz (4 id + weight bytes + 4 label gather,
                             no gather in a level's first round) + 4n label writes */
+  int32_t first_group;   /* lanes per vertex of the first-round label-propagation kernel
+                            (8, 16 or 32; picked once per handle by timing each choice) */
+  int32_t emit_group;    /* lanes per vertex of the contraction's pre-merge kernel (same) */
 } viecut_stats;
 
 /* One contraction step: kind 0 initial graph, 1 label-propagation contraction,

@@ -38,7 +38,8 @@ class ViecutError(RuntimeError):
 
 class viecut_opts(ctypes.Structure):
     _fields_ = [("n0", ctypes.c_int64), ("pr_runs_max", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("stream", ctypes.c_void_p), ("validate", ctypes.c_int32), ("timing", ctypes.c_int32)]
+                ("stream", ctypes.c_void_p), ("validate", ctypes.c_int32), ("timing", ctypes.c_int32),
+                ("lp_group", ctypes.c_int32), ("emit_group", ctypes.c_int32)]
 
 
 class viecut_stats(ctypes.Structure):
@@ -46,7 +47,8 @@ class viecut_stats(ctypes.Structure):
                 ("ms_pr", ctypes.c_double), ("ms_noi", ctypes.c_double), ("ms_other", ctypes.c_double),
                 ("ms_lp_kernel", ctypes.c_double), ("lp_launches", ctypes.c_int64), ("lp_nnz", ctypes.c_int64),
                 ("lp_n", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("levels", ctypes.c_int64),
-                ("trace_len", ctypes.c_int64), ("lp_bytes", ctypes.c_int64)]
+                ("trace_len", ctypes.c_int64), ("lp_bytes", ctypes.c_int64),
+                ("first_group", ctypes.c_int32), ("emit_group", ctypes.c_int32)]
 
 
 class viecut_graph_desc(ctypes.Structure):
@@ -489,11 +491,12 @@ class MinCut:
     """Owns a handle over one graph; ``run`` returns (cut value, side bitmap)."""
 
     def __init__(self, offsets, adj, weights, n0: int = 10000, pr_runs_max: int = 8, device: int = 0,
-                 stream=None, validate: int = 1, timing: bool = False, on_device: bool = False):
+                 stream=None, validate: int = 1, timing: bool = False, on_device: bool = False,
+                 lp_group: int = 0, emit_group: int = 0):
         n = int(offsets.shape[0] - 1)
         m = int(adj.shape[0])
         o = viecut_opts_init(n0=n0, pr_runs_max=pr_runs_max, device=device, stream=stream,
-                             validate=validate, timing=int(timing))
+                             validate=validate, timing=int(timing), lp_group=lp_group, emit_group=emit_group)
         self.n, self.m = n, m
         self._keep = (offsets, adj, weights)
         self.h = (viecut_create_device if on_device else viecut_create)(offsets, adj, n, m, weights, o)

@@ -502,6 +502,7 @@ static void engine_setup(Engine& E, int K, const viecut_opts& o) {
   VC_CUDA(cudaMallocHost(&E.h_summary, sizeof(int) * kSummaryInts));
   E.ws = new Workspace;
   E.ws->s = E.stream;
+  E.ws->fix_groups(o.lp_group, o.emit_group);
 }
 
 static void read_summary(Engine& E) {
@@ -561,7 +562,8 @@ static bool engine_step(Engine& E) {
     int32_t* in = nullptr;
     int32_t* bufs[2] = {A, Bl};
     for (int r = 0; r < E.lp_iters; ++r) {
-      lp_round(Ga, W.bins, W.gt, in, bufs[r & 1], W.hv.as<unsigned long long>(), s);
+      if (!in) W.tune_first(Ga, bufs[r & 1]);
+      lp_round(Ga, W.bins, W.gt, in, bufs[r & 1], W.hv.as<unsigned long long>(), s, W.tune);
       in = bufs[r & 1];
     }
     if (E.lp_iters > 0) F = in;

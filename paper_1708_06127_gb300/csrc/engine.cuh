@@ -173,6 +173,66 @@ struct Workspace {
     lp_bytes_acc = lp_nnz_acc = lp_n_acc = 0;
   }
 
+  // ---------------------------------------------------------------- launch shapes
+  // Lanes per vertex of the first-round and pre-merge kernels, picked once per
+  // workspace by timing each candidate on the first graph large enough to tell them
+  // apart.  Every candidate writes the same output, so a trial run is repeated work.
+  LpTuning tune;
+  bool tuned_first = false, tuned_emit = false;
+  static constexpr int64_t kTuneMinN = int64_t(1) << 16;
+
+  template <typename F>
+  int pick_group(F run) {
+    cudaEvent_t a, b;
+    VC_CUDA(cudaEventCreate(&a));
+    VC_CUDA(cudaEventCreate(&b));
+    float best = 3.0e38f;
+    int pick = 32;
+    for (int G : {32, 16, 8}) {
+      run(G);  // warm-up
+      float t = 3.0e38f;
+      for (int rep = 0; rep < 2; ++rep) {
+        VC_CUDA(cudaEventRecord(a, s));
+        run(G);
+        VC_CUDA(cudaEventRecord(b, s));
+        VC_CUDA(cudaEventSynchronize(b));
+        float ms = 0;
+        VC_CUDA(cudaEventElapsedTime(&ms, a, b));
+        t = std::min(t, ms);
+      }
+      if (t < best) { best = t; pick = G; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return pick;
+  }
+  // Fixed choices from the caller's options (0 keeps the timed pick).
+  void fix_groups(int lp_group, int emit_group) {
+    auto ok = [](int G) { return G == 0 || G == 8 || G == 16 || G == 32; };
+    if (!ok(lp_group) || !ok(emit_group)) throw Error{VIECUT_EINVAL, "lp_group and emit_group must be 0, 8, 16 or 32"};
+    if (lp_group) { tune.first_group = lp_group; tuned_first = true; }
+    if (emit_group) { tune.emit_group = emit_group; tuned_emit = true; }
+  }
+  void tune_first(const GraphView& g, int32_t* out) {
+    if (tuned_first || !g.simple || g.n < kTuneMinN) return;
+    tuned_first = true;
+    const unsigned long long* h = hv.as<unsigned long long>();
+    tune.first_group = pick_group([&](int G) {
+      LpTuning t = tune;
+      t.first_group = G;
+      lp_round(g, bins, gt, nullptr, out, h, s, t);
+    });
+  }
+  void tune_emit(const GraphView& g, const int32_t* cid, int32_t* k, long long* v, int32_t* c) {
+    if (tuned_emit || g.n < kTuneMinN) return;
+    tuned_emit = true;
+    tune.emit_group = pick_group([&](int G) {
+      LpTuning t = tune;
+      t.emit_group = G;
+      emit_cross(g, bins, gt, cid, k, v, c, s, t);
+    });
+  }
+
   // ---------------------------------------------------------------- steps
   Bins bins;
   bool bins_valid = false;
@@ -209,8 +269,9 @@ struct Workspace {
     hash_table(g.n, key, nullptr, nullptr, nullptr, hv.as<unsigned long long>(), s);
     for (int r = 0; r < rounds; ++r) {
       int32_t* out = bufs[r & 1];
+      if (!in) tune_first(g, out);
       cudaEvent_t a = mark();
-      lp_round(g, bins, gt, in, out, hv.as<unsigned long long>(), s);
+      lp_round(g, bins, gt, in, out, hv.as<unsigned long long>(), s, tune);
       if (timing) {
         lp_spans.push_back({a, mark()});
         long long gather = in ? 4 : 0;
@@ -239,7 +300,8 @@ struct Workspace {
     cs.scan_scr = scan64.as<long long>();
     cs.scan_scr32 = scan32.as<int>();
     relabel(labels, g.n, cid_out, cs, &ctr()->c, s);
-    emit_cross(g, bins, gt, cid_out, cs.tmp_key, cs.tmp_val, cs.cnt, s);
+    tune_emit(g, cid_out, cs.tmp_key, cs.tmp_val, cs.cnt);
+    emit_cross(g, bins, gt, cid_out, cs.tmp_key, cs.tmp_val, cs.cnt, s, tune);
     exclusive_scan<int, long long>(cs.cnt, cs.pos, g.n, &ctr()->pairs, cs.scan_scr, s);
     VC_CUDA(cudaMemcpyAsync(h_counters, ctr(), sizeof(Counters), cudaMemcpyDeviceToHost, s));
     sync();

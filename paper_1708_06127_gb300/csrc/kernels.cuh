@@ -73,15 +73,22 @@ int64_t global_table_cap(int maxdeg);
 void hash_table(int64_t n, uint64_t key, const int32_t* gid, const unsigned long long* gkey, const long long* gbase,
                 unsigned long long* hv, cudaStream_t s);
 
+// Launch shapes an autotuner may change (results never depend on them).
+struct LpTuning {
+  int first_group = 32;  // lanes per vertex in the first round on simple graphs (8, 16, 32)
+  int emit_group = 32;   // lanes per vertex in the pre-merge of the contraction (8, 16, 32)
+};
+
 // One synchronous label-propagation round; lab_in == nullptr means the identity
 // labelling (first round of a level).  hv: the level's tie-break table.
 void lp_round(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* lab_in,
-              int32_t* lab_out, const unsigned long long* hv, cudaStream_t s);
+              int32_t* lab_out, const unsigned long long* hv, cudaStream_t s, const LpTuning& tune = LpTuning());
 
 // Pre-merge for contraction: for each vertex v, the distinct coarse neighbours cu =
 // cid[u] != cid[v] with summed weights, written at [off[v], off[v] + cnt[v]).
 void emit_cross(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* cid,
-                int32_t* tmp_key, long long* tmp_val, int32_t* cnt, cudaStream_t s);
+                int32_t* tmp_key, long long* tmp_val, int32_t* cnt, cudaStream_t s,
+                const LpTuning& tune = LpTuning());
 
 // ------------------------------------------------------------------ contraction
 struct ContractScratch {

@@ -245,7 +245,22 @@ __device__ __forceinline__ void first_scan(LaneBest& lb, int64_t a, int64_t end,
   for (int64_t e = a; e < end; e += step) lb.add(ldw(w, e), __ldg(adj + e), hv);
 }
 
-template <typename WT>
+// Group-wide best candidate over the G lanes of `gmask` (lane-local group of G lanes).
+template <int G>
+__device__ __forceinline__ Cand group_best(Cand c, unsigned gmask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    Cand d;
+    d.s = __shfl_xor_sync(gmask, c.s, o);
+    d.h = __shfl_xor_sync(gmask, c.h, o);
+    d.l = __shfl_xor_sync(gmask, c.l, o);
+    if (better(d, c)) c = d;
+  }
+  return c;
+}
+
+// G lanes per vertex (32 / G vertices per warp in flight).
+template <typename WT, int G>
 __global__ void __launch_bounds__(kAggThreads) lp_first_simple_k(int64_t n, int maxd,
                                                                  const int64_t* __restrict__ off,
                                                                  const int32_t* __restrict__ adj,
@@ -253,14 +268,15 @@ __global__ void __launch_bounds__(kAggThreads) lp_first_simple_k(int64_t n, int 
                                                                  int32_t* __restrict__ lab_out,
                                                                  const unsigned long long* __restrict__ hv,
                                                                  const unsigned char* __restrict__ vact) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+  const int lane = threadIdx.x & 31, glane = lane & (G - 1);
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
     if (vact && !vact[v]) continue;
     const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
     if (end - beg > maxd) continue;
     if (end == beg) {
-      if (lane == 0) lab_out[v] = (int32_t)v;
+      if (glane == 0) lab_out[v] = (int32_t)v;
       continue;
     }
     if (std::is_same<WT, UnitW>::value) {
@@ -269,23 +285,23 @@ __global__ void __launch_bounds__(kAggThreads) lp_first_simple_k(int64_t n, int 
       // a lane without entries
       unsigned long long bh = 0;
       int bl = INT_MAX;
-      for (int64_t e = beg + lane; e < end; e += 32) {
+      for (int64_t e = beg + glane; e < end; e += G) {
         const int u = __ldg(adj + e);
         const unsigned long long h = __ldg(hv + u);
         if (bl == INT_MAX || h > bh || (h == bh && u < bl)) { bh = h; bl = u; }
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long oh = __shfl_xor_sync(0xffffffffu, bh, o);
-        const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+      for (int o = G / 2; o > 0; o >>= 1) {
+        const unsigned long long oh = __shfl_xor_sync(gmask, bh, o);
+        const int ol = __shfl_xor_sync(gmask, bl, o);
         if (ol != INT_MAX && (bl == INT_MAX || oh > bh || (oh == bh && ol < bl))) { bh = oh; bl = ol; }
       }
-      if (lane == 0) lab_out[v] = bl;
+      if (glane == 0) lab_out[v] = bl;
     } else {
       LaneBest lb;
-      first_scan(lb, beg + lane, end, 32, adj, w, hv);
-      Cand cd = warp_best(lb.done(hv));
-      if (lane == 0) lab_out[v] = cd.l;
+      first_scan(lb, beg + glane, end, G, adj, w, hv);
+      Cand cd = group_best<G>(lb.done(hv), gmask);
+      if (glane == 0) lab_out[v] = cd.l;
     }
   }
 }
@@ -325,11 +341,11 @@ __global__ void __launch_bounds__(kAggThreads) lp_first_simple_block_k(const int
 // cluster), summing each one's weight with a ballot (unit weights) or a warp sum, and
 // the first lane holding the id writes the pair; the sort that follows merges equal
 // ids across chunks and across vertices.  `next_slot` yields the output position.
-template <typename WT, typename SLOT>
+template <typename WT, int G, typename SLOT>
 __device__ __forceinline__ void emit_chunk(int64_t e, int64_t end, const int32_t* __restrict__ adj,
                                            const WT* __restrict__ w, const int32_t* __restrict__ cid, int32_t own,
-                                           int lane, int32_t* __restrict__ tkey, long long* __restrict__ tval,
-                                           SLOT next_slot) {
+                                           int lane, unsigned gmask, int32_t* __restrict__ tkey,
+                                           long long* __restrict__ tval, SLOT next_slot) {
   int32_t k = -1;
   long long wt = 0;
   bool use = false;
@@ -338,15 +354,20 @@ __device__ __forceinline__ void emit_chunk(int64_t e, int64_t end, const int32_t
     use = k != own;
     wt = ldw(w, e);
   }
-  unsigned todo = __ballot_sync(0xffffffffu, use);
+  unsigned todo = __ballot_sync(gmask, use);
   while (todo) {
     const int leader = __ffs(todo) - 1;
-    const int32_t key = __shfl_sync(0xffffffffu, k, leader);
+    const int32_t key = __shfl_sync(gmask, k, leader);
     const bool mine = use && k == key;
-    const unsigned peers = __ballot_sync(0xffffffffu, mine);
+    const unsigned peers = __ballot_sync(gmask, mine);
     long long sum;
-    if (std::is_same<WT, UnitW>::value) sum = __popc(peers);
-    else sum = warp_sum(mine ? wt : 0LL);
+    if (std::is_same<WT, UnitW>::value) {
+      sum = __popc(peers);
+    } else {
+      sum = mine ? wt : 0LL;
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(gmask, sum, o);
+    }
     const int64_t j = next_slot(leader);
     if (lane == leader) {
       tkey[j] = key;
@@ -356,22 +377,26 @@ __device__ __forceinline__ void emit_chunk(int64_t e, int64_t end, const int32_t
   }
 }
 
-template <typename WT>
+// G lanes per vertex: 32 / G vertices per warp, each group walking its list in
+// G-entry chunks (a short list leaves fewer lanes idle with a smaller G).
+template <typename WT, int G>
 __global__ void __launch_bounds__(kAggThreads) emit_warp_k(int64_t n, int maxd, const int64_t* __restrict__ off,
                                                            const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                            const int32_t* __restrict__ cid, int32_t* __restrict__ tkey,
                                                            long long* __restrict__ tval, int32_t* __restrict__ cnt) {
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t warps = (int64_t)gridDim.x * kWarpsPerBlock;
-  for (int64_t v = (int64_t)blockIdx.x * kWarpsPerBlock + wib; v < n; v += warps) {
+  const int lane = threadIdx.x & 31, glane = lane & (G - 1);
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
     const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
     if (end - beg > maxd) continue;
     const int32_t own = __ldg(cid + v);
-    int made = 0;  // warp-uniform
+    int made = 0;  // group-uniform
     if (own >= 0)
-      for (int64_t base = beg; base < end; base += 32)
-        emit_chunk(base + lane, end, adj, w, cid, own, lane, tkey, tval, [&](int) { return beg + made++; });
-    if (lane == 0) cnt[v] = made;
+      for (int64_t base = beg; base < end; base += G)
+        emit_chunk<WT, G>(base + glane, end, adj, w, cid, own, lane, gmask, tkey, tval,
+                          [&](int) { return beg + made++; });
+    if (glane == 0) cnt[v] = made;
   }
 }
 
@@ -394,7 +419,7 @@ __global__ void __launch_bounds__(kAggThreads) emit_block_k(const int32_t* __res
     __syncthreads();
     if (own >= 0)
       for (int64_t base = beg + 32 * wib; base < end; base += 32 * kWarpsPerBlock)
-        emit_chunk(base + lane, end, adj, w, cid, own, lane, tkey, tval, [&](int leader) {
+        emit_chunk<WT, 32>(base + lane, end, adj, w, cid, own, lane, 0xffffffffu, tkey, tval, [&](int leader) {
           int at = 0;
           if (lane == leader) at = atomicAdd(&s_made, 1);
           return beg + __shfl_sync(0xffffffffu, at, leader);
@@ -487,11 +512,17 @@ constexpr size_t warp_smem() {
 
 template <typename WT, typename ACC, bool FIRST>
 void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* lab, int32_t* lab_out,
-               const unsigned long long* key, cudaStream_t s) {
+               const unsigned long long* key, const LpTuning& tune, cudaStream_t s) {
   const WT* w = (const WT*)g.w;
   if (FIRST && g.simple) {
-    lp_first_simple_k<WT><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
-        g.n, kBlockMaxDeg, g.off, g.adj, w, lab_out, key, g.vact);
+    const int G = tune.first_group;
+    const int grid = grid_for(g.n, kAggThreads / G, kSMs * 16);
+    if (G == 8)
+      lp_first_simple_k<WT, 8><<<grid, kAggThreads, 0, s>>>(g.n, kBlockMaxDeg, g.off, g.adj, w, lab_out, key, g.vact);
+    else if (G == 16)
+      lp_first_simple_k<WT, 16><<<grid, kAggThreads, 0, s>>>(g.n, kBlockMaxDeg, g.off, g.adj, w, lab_out, key, g.vact);
+    else
+      lp_first_simple_k<WT, 32><<<grid, kAggThreads, 0, s>>>(g.n, kBlockMaxDeg, g.off, g.adj, w, lab_out, key, g.vact);
     count_launch();
     VC_CHECK_LAUNCH();
     if (b.h_global > 0) {
@@ -543,10 +574,15 @@ void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const 
 
 template <typename WT>
 void launch_emit(const GraphView& g, const Bins& b, const int32_t* cid, int32_t* tkey, long long* tval,
-                 int32_t* cnt, cudaStream_t s) {
+                 int32_t* cnt, int G, cudaStream_t s) {
   const WT* w = (const WT*)g.w;
-  emit_warp_k<WT><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(g.n, kBlockMaxDeg, g.off, g.adj,
-                                                                                   w, cid, tkey, tval, cnt);
+  const int grid = grid_for(g.n, kAggThreads / G, kSMs * 16);
+  if (G == 8)
+    emit_warp_k<WT, 8><<<grid, kAggThreads, 0, s>>>(g.n, kBlockMaxDeg, g.off, g.adj, w, cid, tkey, tval, cnt);
+  else if (G == 16)
+    emit_warp_k<WT, 16><<<grid, kAggThreads, 0, s>>>(g.n, kBlockMaxDeg, g.off, g.adj, w, cid, tkey, tval, cnt);
+  else
+    emit_warp_k<WT, 32><<<grid, kAggThreads, 0, s>>>(g.n, kBlockMaxDeg, g.off, g.adj, w, cid, tkey, tval, cnt);
   count_launch();
   VC_CHECK_LAUNCH();
   if (b.h_global > 0) {
@@ -560,28 +596,29 @@ void launch_emit(const GraphView& g, const Bins& b, const int32_t* cid, int32_t*
 // Unit weights accumulate in 32 bits (a sum never exceeds the list length); stored
 // weights accumulate in 64 bits.
 void lp_round(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* lab_in,
-              int32_t* lab_out, const unsigned long long* key, cudaStream_t s) {
+              int32_t* lab_out, const unsigned long long* key, cudaStream_t s, const LpTuning& tune) {
   if (g.n <= 0) return;
   const bool first = lab_in == nullptr;
   if (g.unit) {
-    if (first) launch_lp<UnitW, unsigned int, true>(g, b, gt, nullptr, lab_out, key, s);
-    else launch_lp<UnitW, unsigned int, false>(g, b, gt, lab_in, lab_out, key, s);
+    if (first) launch_lp<UnitW, unsigned int, true>(g, b, gt, nullptr, lab_out, key, tune, s);
+    else launch_lp<UnitW, unsigned int, false>(g, b, gt, lab_in, lab_out, key, tune, s);
   } else if (g.wbytes == 4) {
-    if (first) launch_lp<int32_t, unsigned long long, true>(g, b, gt, nullptr, lab_out, key, s);
-    else launch_lp<int32_t, unsigned long long, false>(g, b, gt, lab_in, lab_out, key, s);
+    if (first) launch_lp<int32_t, unsigned long long, true>(g, b, gt, nullptr, lab_out, key, tune, s);
+    else launch_lp<int32_t, unsigned long long, false>(g, b, gt, lab_in, lab_out, key, tune, s);
   } else {
-    if (first) launch_lp<long long, unsigned long long, true>(g, b, gt, nullptr, lab_out, key, s);
-    else launch_lp<long long, unsigned long long, false>(g, b, gt, lab_in, lab_out, key, s);
+    if (first) launch_lp<long long, unsigned long long, true>(g, b, gt, nullptr, lab_out, key, tune, s);
+    else launch_lp<long long, unsigned long long, false>(g, b, gt, lab_in, lab_out, key, tune, s);
   }
 }
 
 void emit_cross(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* cid,
-                int32_t* tmp_key, long long* tmp_val, int32_t* cnt, cudaStream_t s) {
+                int32_t* tmp_key, long long* tmp_val, int32_t* cnt, cudaStream_t s, const LpTuning& tune) {
   (void)gt;
   if (g.n <= 0) return;
-  if (g.unit) launch_emit<UnitW>(g, b, cid, tmp_key, tmp_val, cnt, s);
-  else if (g.wbytes == 4) launch_emit<int32_t>(g, b, cid, tmp_key, tmp_val, cnt, s);
-  else launch_emit<long long>(g, b, cid, tmp_key, tmp_val, cnt, s);
+  const int G = tune.emit_group;
+  if (g.unit) launch_emit<UnitW>(g, b, cid, tmp_key, tmp_val, cnt, G, s);
+  else if (g.wbytes == 4) launch_emit<int32_t>(g, b, cid, tmp_key, tmp_val, cnt, G, s);
+  else launch_emit<long long>(g, b, cid, tmp_key, tmp_val, cnt, G, s);
 }
 
 }  // namespace vc

@@ -316,6 +316,8 @@ static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, u
     S.lp_n = W.lp_n_acc;
     S.lp_bytes = W.lp_bytes_acc;
   }
+  S.first_group = W.tune.first_group;
+  S.emit_group = W.tune.emit_group;
   S.kernel_launches = (int64_t)(g_launches - launches0);
   (void)t_start;
 }
@@ -399,6 +401,8 @@ static int create_common(viecut_t** out, int64_t n, int64_t m, const viecut_opts
   if (opts) o = *opts;
   if (o.n0 < 1) throw Error{VIECUT_EINVAL, "n0 must be >= 1"};
   if (o.pr_runs_max < 0) throw Error{VIECUT_EINVAL, "pr_runs_max must be >= 0"};
+  for (int G : {o.lp_group, o.emit_group})
+    if (G != 0 && G != 8 && G != 16 && G != 32) throw Error{VIECUT_EINVAL, "lp_group and emit_group must be 0, 8, 16 or 32"};
   // validate 2: full check on the host (symmetry needs a sort); validate 1: one pass
   // on the device after the copy
   bool unit = false, simple = false;
@@ -424,6 +428,7 @@ static int create_common(viecut_t** out, int64_t n, int64_t m, const viecut_opts
     H.ws = new vc::Workspace;
     H.ws->s = H.stream;
     H.ws->timing = o.timing != 0;
+    H.ws->fix_groups(o.lp_group, o.emit_group);
     if (host_input) {
       H.off0 = H.in_off.ensure_n<int64_t>(n + 1);
       H.adj0 = H.in_adj.ensure_n<int32_t>(m);
@@ -622,7 +627,7 @@ int viecut_step_lp(viecut_graph* g, const int32_t* lab_in, uint64_t key, int32_t
     int32_t* bufs[2] = {c.ws->labA.as<int32_t>(), c.ws->labB.as<int32_t>()};
     vc::hash_table(v.n, key, nullptr, nullptr, nullptr, c.ws->hv.as<unsigned long long>(), c.s);
     for (int r = 0; r < rounds; ++r) {
-      vc::lp_round(v, c.ws->bins, c.ws->gt, in, bufs[r & 1], c.ws->hv.as<unsigned long long>(), c.s);
+      vc::lp_round(v, c.ws->bins, c.ws->gt, in, bufs[r & 1], c.ws->hv.as<unsigned long long>(), c.s, c.ws->tune);
       VC_CUDA(cudaMemcpyAsync(lab_out + (int64_t)r * v.n, bufs[r & 1], sizeof(int32_t) * v.n, cudaMemcpyDeviceToHost, c.s));
       in = bufs[r & 1];
     }

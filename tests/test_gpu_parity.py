@@ -288,3 +288,32 @@ def test_launches_counted():
         st = mc.stats()
     assert st["kernel_launches"] == vc.viecut_launch_count() - before > 10
     assert st["lp_launches"] == 2 and st["ms_lp_kernel"] > 0
+
+
+@pytest.mark.parametrize("lp_group,emit_group", [(8, 8), (16, 16), (32, 32), (8, 32), (32, 16)])
+def test_group_sizes_give_identical_results(lp_group, emit_group):
+    """Lanes per vertex are a launch shape only: every choice gives the oracle's trace,
+    cut and side, on unit weights and on stored weights (different kernels)."""
+    graphs = [gg.workload_rhg_small(2), gg.with_pair_weights(gg.core_lcc(gg.rhg(1 << 13, 24, 9), 0), 9, 1, 10),
+              hub_graph()]
+    for g in graphs:
+        ref = oracle.viecut(g.offsets, g.adj, g.w, seed=3, lp_iters=2, n0=64)
+        with vc.MinCut(g.offsets, g.adj, g.w, n0=64, lp_group=lp_group, emit_group=emit_group) as mc:
+            cut, bits = mc.run(3, 2)
+            st = mc.stats()
+            trace = mc.trace()
+        assert (st["first_group"], st["emit_group"]) == (lp_group, emit_group)
+        assert trace == ref.trace and cut == ref.cut and np.array_equal(bits, ref.side_bits), g.name
+
+
+def test_autotuned_groups_on_a_large_graph():
+    """Above 2^16 vertices the handle times each choice once and keeps the fastest."""
+    g = gg.core_lcc(gg.rhg(1 << 17, 32, 6), 0)
+    ref = oracle.viecut(g.offsets, g.adj, g.w, seed=2, lp_iters=2, n0=10000)
+    with vc.MinCut(g.offsets, g.adj, g.w) as mc:
+        first = mc.run(2, 2)
+        st = mc.stats()
+        again = mc.run(2, 2)
+    assert st["first_group"] in (8, 16, 32) and st["emit_group"] in (8, 16, 32)
+    for cut, bits in (first, again):
+        assert cut == ref.cut and np.array_equal(bits, ref.side_bits)

@@ -42,6 +42,16 @@ def test_library_exports_every_declared_symbol(lib):
 def test_opts_defaults(lib):
     o = vc.viecut_opts_init()
     assert (o.n0, o.pr_runs_max, o.device, o.validate, o.timing) == (10000, 8, 0, 1, 0)
+    assert (o.lp_group, o.emit_group) == (0, 0)  # 0: picked by timing
+
+
+def test_group_options_are_checked_before_any_device_call(lib):
+    off = np.array([0, 1, 2], np.int64)
+    adj = np.array([1, 0], np.int32)
+    for bad in ({"lp_group": 4}, {"emit_group": 64}, {"lp_group": -8}):
+        with pytest.raises(vc.ViecutError) as e:
+            vc.viecut_create(off, adj, 2, 2, np.array([1, 1], np.int32), vc.viecut_opts_init(**bad))
+        assert e.value.code == vc.VIECUT_EINVAL and "lp_group" in str(e.value)
 
 
 def test_host_validation_rejects_bad_graphs(lib):
