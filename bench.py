@@ -222,22 +222,35 @@ def bench_serve(pool_size: int, requests: int, warm: int, device: int, budget_gb
     srv = vc.Server(hbm_budget_bytes=int(budget_gb * (1 << 30)), max_slots=1024, device=device)
 
     def drain(tickets):
-        lat = {}
+        res = {}
         pending = set(tickets)
         while pending:
             for t in list(pending):
                 r = srv.poll(t)
                 if r is not None:
-                    lat[t] = r[2]
+                    res[t] = r
                     pending.discard(t)
             time.sleep(0.0002)
-        return lat
+        return [res[t] for t in tickets]
 
     # closed burst: everything submitted at once
     burst = [pool[i % pool_size] for i in range(max(warm, 8))]
+    drain([srv.submit(g.offsets, g.adj, g.w, 1 + i) for i, g in enumerate(burst)])  # warm-up
+    burst = [pool[i] for i in rng.integers(0, pool_size, size=4 * pool_size)]
     t0 = time.perf_counter()
-    drain([srv.submit(g.offsets, g.adj, g.w, 1 + i) for i, g in enumerate(burst)])
+    served = drain([srv.submit(g.offsets, g.adj, g.w, 1 + i) for i, g in enumerate(burst)])
     sat = len(burst) / (time.perf_counter() - t0)
+    # the same burst through one reused single-graph handle, one request after another
+    # (viecut_load + viecut_run: the per-graph loop a caller writes without the server)
+    mc = vc.MinCut(burst[0].offsets, burst[0].adj, burst[0].w, device=device)
+    mc.run(1, 2)
+    t0 = time.perf_counter()
+    loop_cuts = []
+    for i, g in enumerate(burst):
+        mc.load(g.offsets, g.adj, g.w)
+        loop_cuts.append(mc.run(1 + i, 2)[0])
+    loop_rate = len(burst) / (time.perf_counter() - t0)
+    mc.close()
     rate = rho * sat
     # open loop: Poisson arrivals
     gaps = rng.exponential(1.0 / rate, size=warm + requests)
@@ -289,6 +302,9 @@ def bench_serve(pool_size: int, requests: int, warm: int, device: int, budget_gb
             "input_edges_per_s": edges / max(window, 1e-9), "saturation_graphs_per_s": sat, "rho": rho,
             "arrival_rate_per_s": rate, "requests": requests, "warmup_requests": warm,
             "pool": f"{pool_size} RHG graphs, n log-uniform 2^10..2^20, avg deg 32, exponent 5, unit weights, lcc",
+            "per_graph_loop_graphs_per_s": loop_rate, "saturation_vs_loop": sat / loop_rate,
+            "identical_cut_values": bool([r[0] for r in served] == loop_cuts),
+            "saturation_burst": len(burst), "solo_min_n": 1 << 16, "solo_completed": st["solo_completed"],
             "hbm_budget_gb": budget_gb, "max_resident": st["max_resident"], "joins": st["joins"],
             "super_steps": st["super_steps"], "wall_s": t_end - t_start}
 

@@ -109,6 +109,15 @@ int viecut_create(viecut_t** h, const int64_t* offsets, const int32_t* adj, int6
 int viecut_create_device(viecut_t** h, const int64_t* d_offsets, const int32_t* d_adj, int64_t n, int64_t m,
                          const int32_t* d_weights, const viecut_opts* opts);
 
+/* Replaces the graph of a handle made by viecut_create with another one from host
+ * arrays (same layout and ownership rules as viecut_create), keeping the handle's
+ * options, stream, chosen launch shapes and device buffers; buffers grow when the new
+ * graph is larger and are never shrunk, so a loop over many graphs allocates only
+ * while sizes grow.  Waits for the handle's previous work first.  EINVAL for a handle
+ * made by viecut_create_device or a malformed graph (checked as viecut_create). */
+int viecut_load(viecut_t* h, const int64_t* offsets, const int32_t* adj, int64_t n, int64_t m,
+                const int32_t* weights);
+
 /* Runs the method and waits for it.  cut_value (host) receives the cut; side_bits
  * (host, ceil(n/64) words, may be NULL) receives bit i = 1 iff input vertex i is on
  * the returned side; vertex 0 is never on it.  lp_iters >= 0 (the paper uses 2). */
@@ -229,10 +238,16 @@ typedef struct viecut_server_opts {
   int64_t hbm_budget_bytes; /* admission budget for resident graphs (default 120 GiB) */
   int32_t max_slots;        /* graphs resident at once (default 1024) */
   int32_t lp_iters;         /* label-propagation rounds per level for every request (default 2) */
+  int64_t solo_min_n;       /* requests of at least this many vertices skip the union and run
+                               one at a time on a handle of their own, on a second stream, beside
+                               the union (each has parallelism enough alone); 0 = never
+                               (default 65536) */
 } viecut_server_opts;
 
 typedef struct viecut_server_stats {
   int64_t admitted, completed, pending, max_resident, super_steps, joins, budget_used;
+  int64_t solo_completed;   /* requests served on the solo lane */
+  int64_t rejected;         /* requests refused by the device check (counted in completed) */
 } viecut_server_stats;
 
 typedef struct viecut_server viecut_server;
@@ -240,13 +255,18 @@ typedef struct viecut_server viecut_server;
 int viecut_server_opts_init(viecut_server_opts* o);
 /* Starts the server thread (allocations happen here and as the resident set grows). */
 int viecut_server_start(viecut_server** s, const viecut_server_opts* o);
-/* Queues a graph (host arrays, copied before the call returns; checked like
- * validate 1) with its seed; *ticket identifies the request.  EINVAL if the graph is
- * malformed or alone exceeds the budget. */
+/* Queues a graph (host arrays, copied into page-locked memory before the call
+ * returns) with its seed; *ticket identifies the request.  EINVAL at once if n < 2, an
+ * array is NULL, offsets[0] != 0, offsets[n] != m, or the graph alone exceeds the
+ * budget.  The per-entry checks of validate 1 (offsets order, id range, self-loops,
+ * weights >= 1) run on the device when the graph is copied there; a graph that fails
+ * them never runs, and polling its ticket returns EINVAL with the reason. */
 int viecut_server_submit(viecut_server* s, const viecut_graph_desc* g, uint64_t seed, uint64_t* ticket);
 /* Non-blocking: VIECUT_EBUSY until the request finished; then writes the cut, the
  * side bitmap (ceil(n/64) words, may be NULL) and the latency from submit to the
- * moment the result reached the host, and forgets the ticket. */
+ * moment the result reached the host, and forgets the ticket.  A request whose graph
+ * the device check refused returns EINVAL (viecut_last_error gives the reason) and its
+ * ticket is forgotten too. */
 int viecut_server_poll(viecut_server* s, uint64_t ticket, int64_t* cut, uint64_t* side_bits, double* latency_ms);
 int viecut_server_get_stats(viecut_server* s, viecut_server_stats* st);
 /* Stops the thread (requests still queued or resident are abandoned) and frees all. */

@@ -63,13 +63,13 @@ class viecut_batch_stats(ctypes.Structure):
 
 class viecut_server_opts(ctypes.Structure):
     _fields_ = [("base", viecut_opts), ("hbm_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32),
-                ("lp_iters", ctypes.c_int32)]
+                ("lp_iters", ctypes.c_int32), ("solo_min_n", ctypes.c_int64)]
 
 
 class viecut_server_stats(ctypes.Structure):
     _fields_ = [("admitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("pending", ctypes.c_int64),
                 ("max_resident", ctypes.c_int64), ("super_steps", ctypes.c_int64), ("joins", ctypes.c_int64),
-                ("budget_used", ctypes.c_int64)]
+                ("budget_used", ctypes.c_int64), ("solo_completed", ctypes.c_int64), ("rejected", ctypes.c_int64)]
 
 
 class viecut_step(ctypes.Structure):
@@ -85,6 +85,7 @@ SIGNATURES = [
     ("viecut_create", ctypes.c_int, [_pvp, _vp, _vp, _i64, _i64, _vp, _vp]),
     ("viecut_create_device", ctypes.c_int, [_pvp, _vp, _vp, _i64, _i64, _vp, _vp]),
     ("viecut_run", ctypes.c_int, [_vp, _u64, _i32, _vp, _vp]),
+    ("viecut_load", ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _vp]),
     ("viecut_run_device", ctypes.c_int, [_vp, _u64, _i32, _vp, _vp]),
     ("viecut_get_stats", ctypes.c_int, [_vp, _vp]),
     ("viecut_get_trace", ctypes.c_int, [_vp, _vp, _i64, _vp]),
@@ -174,6 +175,10 @@ def viecut_create_device(d_offsets, d_adj, n: int, m: int, d_weights, opts: viec
     _check(lib().viecut_create_device(ctypes.byref(h), _ptr(d_offsets), _ptr(d_adj), n, m, _ptr(d_weights),
                                       ctypes.byref(opts) if opts is not None else None))
     return h
+
+
+def viecut_load(h, offsets, adj, n: int, m: int, weights) -> None:
+    _check(lib().viecut_load(h, _ptr(offsets), _ptr(adj), n, m, _ptr(weights)))
 
 
 def viecut_run(h, seed: int, lp_iters: int, side_bits=None) -> int:
@@ -387,7 +392,7 @@ def viecut_server_opts_init(**kw) -> viecut_server_opts:
     o = viecut_server_opts()
     _check(lib().viecut_server_opts_init(ctypes.byref(o)))
     for k, v in kw.items():
-        if k in ("n0", "pr_runs_max", "device", "stream"):
+        if k in ("n0", "pr_runs_max", "device", "stream", "lp_group", "emit_group"):
             setattr(o.base, k, v)
         else:
             setattr(o, k, v)
@@ -437,9 +442,9 @@ class Server:
     """Continuous-batching min-cut server on one GPU."""
 
     def __init__(self, hbm_budget_bytes: int = 120 << 30, max_slots: int = 1024, lp_iters: int = 2,
-                 n0: int = 10000, pr_runs_max: int = 8, device: int = 0):
+                 n0: int = 10000, pr_runs_max: int = 8, device: int = 0, solo_min_n: int = 1 << 16):
         o = viecut_server_opts_init(hbm_budget_bytes=hbm_budget_bytes, max_slots=max_slots, lp_iters=lp_iters,
-                                    n0=n0, pr_runs_max=pr_runs_max, device=device)
+                                    n0=n0, pr_runs_max=pr_runs_max, device=device, solo_min_n=solo_min_n)
         self.s = viecut_server_start(o)
         self.sizes = {}
 
@@ -449,7 +454,11 @@ class Server:
         return t
 
     def poll(self, ticket: int):
-        r = viecut_server_poll(self.s, ticket, self.sizes[ticket])
+        try:
+            r = viecut_server_poll(self.s, ticket, self.sizes[ticket])
+        except ViecutError:
+            self.sizes.pop(ticket, None)  # a refused request is answered once
+            raise
         if r is not None:
             del self.sizes[ticket]
         return r
@@ -500,6 +509,14 @@ class MinCut:
         self.n, self.m = n, m
         self._keep = (offsets, adj, weights)
         self.h = (viecut_create_device if on_device else viecut_create)(offsets, adj, n, m, weights, o)
+
+    def load(self, offsets, adj, weights):
+        """Rebinds the handle to another host graph, reusing its device buffers."""
+        n = int(offsets.shape[0] - 1)
+        m = int(adj.shape[0])
+        viecut_load(self.h, offsets, adj, n, m, weights)
+        self.n, self.m = n, m
+        self._keep = (offsets, adj, weights)
 
     def run(self, seed: int = 1, lp_iters: int = 2):
         bits = np.zeros((self.n + 63) // 64, np.uint64)

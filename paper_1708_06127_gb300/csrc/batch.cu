@@ -367,15 +367,54 @@ __global__ void b_side_bits_k(const int32_t* __restrict__ list, int count, BStat
 // local ids, int32 weights) lands at vertex base jv[j] / entry base je[j]
 __global__ void b_join_k(int J, const long long* __restrict__ jv, const long long* __restrict__ je,
                          const long long* __restrict__ sv, const long long* __restrict__ se,
+                         const long long* __restrict__ nn, const long long* __restrict__ mm,
                          const int64_t* __restrict__ st_off, const int32_t* __restrict__ st_adj,
                          const int32_t* __restrict__ st_w, int64_t* off, int32_t* adj, long long* w) {
   for (int j = blockIdx.x; j < J; j += gridDim.x) {
-    const long long n = sv[j + 1] - sv[j], m = se[j + 1] - se[j];
+    const long long n = nn[j], m = mm[j];
     for (long long i = threadIdx.x; i < n; i += blockDim.x) off[jv[j] + i] = je[j] + st_off[sv[j] + i];
     for (long long e = threadIdx.x; e < m; e += blockDim.x) {
       adj[je[j] + e] = (int32_t)(jv[j] + st_adj[se[j] + e]);
       w[je[j] + e] = (long long)st_w[se[j] + e];
     }
+  }
+}
+
+// Staged vertex -> index of its joining request.
+__global__ void b_stage_gid_k(int J, const long long* __restrict__ sv, int32_t* __restrict__ sgid) {
+  for (int j = blockIdx.x; j < J; j += gridDim.x)
+    for (long long v = sv[j] + threadIdx.x; v < sv[j + 1]; v += blockDim.x) sgid[v] = j;
+}
+
+// Checks of the joining requests in the staging buffers (request-local offsets, n
+// per request, the end of the last list being m), a warp per vertex; err[j] gathers
+// request j's findings: 2 offsets, 4 id range, 8 self-loop, 16 weight < 1; 32 (not
+// all weights 1) and 64 (a list not strictly increasing) are facts, not errors.
+__global__ void b_validate_staged_k(long long sn, const int32_t* __restrict__ sgid, const long long* __restrict__ sv,
+                                    const long long* __restrict__ se, const int64_t* __restrict__ off,
+                                    const int32_t* __restrict__ adj, const int32_t* __restrict__ w, int* err) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < sn; v += warps) {
+    const int j = sgid[v];
+    const long long i = v - sv[j], n = sv[j + 1] - sv[j], m = se[j + 1] - se[j], eb = se[j];
+    const long long a = off[v], b = (i + 1 < n) ? off[v + 1] : m;
+    int bad = 0;
+    if (a > b || a < 0 || b > m) {
+      bad = 2;
+    } else {
+      for (long long e = a + lane; e < b; e += 32) {
+        const int32_t u = adj[eb + e];
+        if (u < 0 || u >= n) bad |= 4;
+        else if (u == i) bad |= 8;
+        const int32_t x = w[eb + e];
+        if (x < 1) bad |= 16;
+        if (x != 1) bad |= 32;
+        if (e + 1 < b && adj[eb + e + 1] <= u) bad |= 64;
+      }
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (lane == 0 && bad) atomicOr(err + j, bad);
   }
 }
 
@@ -799,15 +838,73 @@ static void copy_trace(Engine& E, int g, viecut_step* steps, int64_t cap, int64_
 }
 
 // ------------------------------------------------------------------ server
-// A request's copy of its graph lives on the host until it joins the union; its
-// results are kept until the caller polls them.
+// Page-locked host blocks holding the requests that wait for the device, in
+// power-of-two size classes reused across requests (pinning memory is slow, and a
+// copy from pageable memory runs through the driver's own staging at a fraction of
+// the bus rate).  Past `cap` pinned bytes a block comes from the ordinary heap.
+struct HostPool {
+  std::mutex mu;
+  std::map<int, std::vector<void*>> free_blocks;
+  std::vector<void*> pinned;
+  int64_t pinned_bytes = 0, cap = int64_t(16) << 30;
+  struct Block {
+    void* p = nullptr;
+    int cls = 0;
+    bool is_pinned = false;
+  };
+  Block get(int64_t bytes) {
+    int c = 20;
+    while ((int64_t(1) << c) < bytes) ++c;
+    std::lock_guard<std::mutex> lk(mu);
+    auto& fl = free_blocks[c];
+    if (!fl.empty()) {
+      Block b{fl.back(), c, true};
+      fl.pop_back();
+      return b;
+    }
+    if (pinned_bytes + (int64_t(1) << c) <= cap) {
+      void* p = nullptr;
+      if (cudaMallocHost(&p, size_t(1) << c) == cudaSuccess) {
+        pinned.push_back(p);
+        pinned_bytes += int64_t(1) << c;
+        return Block{p, c, true};
+      }
+      cudaGetLastError();
+    }
+    void* p = malloc(size_t(1) << c);
+    if (!p) throw Error{VIECUT_ENOMEM, "host memory for a request"};
+    return Block{p, c, false};
+  }
+  void put(Block& b) {
+    if (!b.p) return;
+    if (b.is_pinned) {
+      std::lock_guard<std::mutex> lk(mu);
+      free_blocks[b.cls].push_back(b.p);
+    } else {
+      free(b.p);
+    }
+    b.p = nullptr;
+  }
+  ~HostPool() {
+    for (void* p : pinned) cudaFreeHost(p);
+  }
+};
+
+// A request's copy of its graph lives in a host block until it reaches the device;
+// its results (or the reason it was refused) are kept until the caller polls them.
 struct Request {
   uint64_t ticket = 0;
   int64_t n = 0, m = 0;
   uint64_t seed = 0;
-  std::vector<int64_t> off;
-  std::vector<int32_t> adj, w;
-  bool simple = true;
+  HostPool::Block blk;
+  int64_t* off = nullptr;  // n + 1 entries
+  int32_t* adj = nullptr;
+  int32_t* w = nullptr;
+  int err = 0;             // VIECUT_EINVAL once the device check refused the graph
+  std::string err_msg;
+  ~Request() {
+    if (blk.p && !blk.is_pinned) free(blk.p);  // pinned blocks belong to the pool
+  }
   int64_t est = 0;
   int slot = -1;
   int64_t obase = -1;
@@ -836,8 +933,19 @@ struct Server {
   bool all_simple = true;
   int64_t admitted = 0, completed = 0, max_resident = 0, joins = 0;
   std::vector<int> h_phase;
-  Buf d_join, d_list, d_wbase, d_bits, d_init;
+  Buf d_join, d_list, d_wbase, d_bits, d_init, d_sgid, d_err;
+  Buf st_off, st_adj, st_w;  // staging of joining graphs (grow-only)
+  HostPool host;
+  int64_t rejected = 0;
   std::vector<long long> h_join;
+  // solo lane: requests of at least solo_min_n vertices, one at a time on a handle
+  // (and stream) of their own
+  int64_t solo_min_n = 0;
+  viecut_opts solo_opts{};
+  std::deque<std::shared_ptr<Request>> solo_pending;
+  std::condition_variable cv_solo;
+  std::thread th_solo;
+  int64_t solo_completed = 0;
 };
 
 static int64_t request_estimate(int64_t n, int64_t m) {
@@ -882,59 +990,133 @@ static void arena_free(Server& S, int64_t at, int64_t n) {
   }
 }
 
-// Appends the admitted requests to the union (a new union in the other coarse buffer:
-// the old union first, unchanged, then the new graphs) and starts their state.
+static std::string invalid_reason(int bad) {
+  std::string why = "invalid graph:";
+  if (bad & 2) why += " offsets decrease or leave [0, m];";
+  if (bad & 4) why += " neighbour id out of range;";
+  if (bad & 8) why += " self-loop;";
+  if (bad & 16) why += " weight < 1;";
+  return why;
+}
+
+// Marks a request as refused and gives back what admission took (under S.mu).
+static void refuse(Server& S, const std::shared_ptr<Request>& r, const std::string& why) {
+  r->err = VIECUT_EINVAL;
+  r->err_msg = why;
+  r->t_done = std::chrono::steady_clock::now();
+  r->done = true;
+  S.host.put(r->blk);
+  S.budget_used -= r->est;
+  S.rejected += 1;
+  S.completed += 1;
+}
+
+// Copies the admitted requests to the device, checks them there (a refused request is
+// answered with its reason and leaves the join), and appends the others to the union
+// (a new union in the other coarse buffer: the old union first, unchanged, then the
+// new graphs) and starts their state.
 static void server_join(Server& S, std::vector<std::shared_ptr<Request>>& add) {
   Engine& E = S.E;
   Workspace& W = *E.ws;
   cudaStream_t s = E.stream;
-  const int J = (int)add.size();
+  int J = (int)add.size();
+  // staged host copies -> device (request-local offsets, n per request)
+  std::vector<long long> sv(J + 1, 0), se(J + 1, 0);
+  for (int j = 0; j < J; ++j) {
+    sv[j + 1] = sv[j] + add[j]->n;
+    se[j + 1] = se[j] + add[j]->m;
+  }
+  const int64_t sn = sv[J], sm = se[J];
+  int64_t* d_off = S.st_off.ensure_n<int64_t>(sn);
+  int32_t* d_adj = S.st_adj.ensure_n<int32_t>(std::max<int64_t>(sm, 1));
+  int32_t* d_w = S.st_w.ensure_n<int32_t>(std::max<int64_t>(sm, 1));
+  for (int j = 0; j < J; ++j) {
+    const auto& r = add[j];
+    VC_CUDA(cudaMemcpyAsync(d_off + sv[j], r->off, sizeof(int64_t) * r->n, cudaMemcpyHostToDevice, s));
+    if (r->m > 0) {
+      VC_CUDA(cudaMemcpyAsync(d_adj + se[j], r->adj, sizeof(int32_t) * r->m, cudaMemcpyHostToDevice, s));
+      VC_CUDA(cudaMemcpyAsync(d_w + se[j], r->w, sizeof(int32_t) * r->m, cudaMemcpyHostToDevice, s));
+    }
+  }
+  long long* dsv = S.d_join.ensure_n<long long>(6 * (J + 1));
+  VC_CUDA(cudaMemcpyAsync(dsv, sv.data(), sizeof(long long) * (J + 1), cudaMemcpyHostToDevice, s));
+  VC_CUDA(cudaMemcpyAsync(dsv + (J + 1), se.data(), sizeof(long long) * (J + 1), cudaMemcpyHostToDevice, s));
+  int32_t* sgid = S.d_sgid.ensure_n<int32_t>(std::max<int64_t>(sn, 1));
+  int* derr = S.d_err.ensure_n<int>(J);
+  VC_CUDA(cudaMemsetAsync(derr, 0, sizeof(int) * J, s));
+  b_stage_gid_k<<<J < 4 * kSMs ? J : 4 * kSMs, 256, 0, s>>>(J, dsv, sgid);
+  b_validate_staged_k<<<grid_for(sn, 8, kSMs * 16), 256, 0, s>>>(sn, sgid, dsv, dsv + (J + 1), d_off, d_adj, d_w,
+                                                                 derr);
+  count_launch(2);
+  VC_CHECK_LAUNCH();
+  std::vector<int> herr(J);
+  VC_CUDA(cudaMemcpyAsync(herr.data(), derr, sizeof(int) * J, cudaMemcpyDeviceToHost, s));
+  VC_CUDA(cudaStreamSynchronize(s));
+  // the host blocks are free once the copies are done
+  std::vector<std::shared_ptr<Request>> keep;
+  std::vector<int> kj;
+  {
+    std::lock_guard<std::mutex> lk(S.mu);
+    for (int j = 0; j < J; ++j) {
+      S.host.put(add[j]->blk);
+      if (herr[j] & ~(32 | 64)) {
+        S.slot_req[add[j]->slot].reset();
+        S.free_slots.push_back(add[j]->slot);
+        refuse(S, add[j], invalid_reason(herr[j]));
+      } else {
+        keep.push_back(add[j]);
+        kj.push_back(j);
+      }
+    }
+  }
+  add.swap(keep);
+  J = (int)add.size();
+  if (J == 0) return;
   const int64_t n_u = E.G.n;
   int64_t m_u = 0;  // exact entry count of the resident union: its last offset
   if (n_u > 0) {
     VC_CUDA(cudaMemcpyAsync(&m_u, E.G.off + n_u, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     VC_CUDA(cudaStreamSynchronize(s));
   }
-  int64_t sn = 0, sm = 0;
-  for (auto& r : add) { sn += r->n; sm += r->m; }
-  const int64_t n_new = n_u + sn, m_new = m_u + sm;
+  int64_t kn = 0, km = 0;
+  for (auto& r : add) { kn += r->n; km += r->m; }
+  const int64_t n_new = n_u + kn, m_new = m_u + km;
   if (n_new > 0x7fffffffLL) throw Error{VIECUT_ENOMEM, "the resident graphs exceed 2^31 vertices"};
   for (auto& r : add) r->obase = arena_alloc(S, r->n);
-  // staged host copies -> device
-  Buf st_off, st_adj, st_w;
-  int64_t* d_off = st_off.ensure_n<int64_t>(sn);
-  int32_t* d_adj = st_adj.ensure_n<int32_t>(sm);
-  int32_t* d_w = st_w.ensure_n<int32_t>(sm);
-  S.h_join.assign(4 * (J + 1), 0);
+  // per kept request: union vertex and entry base, staged vertex and entry base, n, m
+  S.h_join.assign(6 * (J + 1), 0);
   long long* jv = S.h_join.data();
   long long* je = jv + (J + 1);
-  long long* sv = je + (J + 1);
-  long long* se = sv + (J + 1);
-  for (int j = 0; j < J; ++j) {
-    const auto& r = add[j];
-    jv[j] = n_u + sv[j];
-    je[j] = m_u + se[j];
-    sv[j + 1] = sv[j] + r->n;
-    se[j + 1] = se[j] + r->m;
-    VC_CUDA(cudaMemcpyAsync(d_off + sv[j], r->off.data(), sizeof(int64_t) * r->n, cudaMemcpyHostToDevice, s));
-    if (r->m > 0) {
-      VC_CUDA(cudaMemcpyAsync(d_adj + se[j], r->adj.data(), sizeof(int32_t) * r->m, cudaMemcpyHostToDevice, s));
-      VC_CUDA(cudaMemcpyAsync(d_w + se[j], r->w.data(), sizeof(int32_t) * r->m, cudaMemcpyHostToDevice, s));
-    }
+  long long* ksv = je + (J + 1);
+  long long* kse = ksv + (J + 1);
+  long long* kn_ = kse + (J + 1);
+  long long* km_ = kn_ + (J + 1);
+  long long at_v = n_u, at_e = m_u;
+  for (int i = 0; i < J; ++i) {
+    jv[i] = at_v;
+    je[i] = at_e;
+    ksv[i] = sv[kj[i]];
+    kse[i] = se[kj[i]];
+    kn_[i] = add[i]->n;
+    km_[i] = add[i]->m;
+    at_v += add[i]->n;
+    at_e += add[i]->m;
   }
-  long long* dj = S.d_join.ensure_n<long long>(4 * (J + 1));
-  VC_CUDA(cudaMemcpyAsync(dj, jv, sizeof(long long) * 4 * (J + 1), cudaMemcpyHostToDevice, s));
+  long long* dj = S.d_join.ensure_n<long long>(6 * (J + 1));  // the checks above are done with it
+  VC_CUDA(cudaMemcpyAsync(dj, jv, sizeof(long long) * 6 * (J + 1), cudaMemcpyHostToDevice, s));
   const int dst = E.slot == 0 ? 1 : 0;
   int64_t* off = W.coff[dst].ensure_n<int64_t>(n_new + 1);
-  int32_t* adj = W.cadj[dst].ensure_n<int32_t>(m_new);
-  long long* w = W.cw[dst].ensure_n<long long>(m_new);
+  int32_t* adj = W.cadj[dst].ensure_n<int32_t>(std::max<int64_t>(m_new, 1));
+  long long* w = W.cw[dst].ensure_n<long long>(std::max<int64_t>(m_new, 1));
   if (n_u > 0) {
     VC_CUDA(cudaMemcpyAsync(off, E.G.off, sizeof(int64_t) * n_u, cudaMemcpyDeviceToDevice, s));
     VC_CUDA(cudaMemcpyAsync(adj, E.G.adj, sizeof(int32_t) * m_u, cudaMemcpyDeviceToDevice, s));
     VC_CUDA(cudaMemcpyAsync(w, E.G.w, sizeof(long long) * m_u, cudaMemcpyDeviceToDevice, s));
   }
-  b_join_k<<<J < 4 * kSMs ? J : 4 * kSMs, 256, 0, s>>>(J, dj, dj + (J + 1), dj + 2 * (J + 1), dj + 3 * (J + 1), d_off,
-                                                      d_adj, d_w, off, adj, w);
+  long long* d6 = dj;
+  b_join_k<<<J < 4 * kSMs ? J : 4 * kSMs, 256, 0, s>>>(J, d6, d6 + (J + 1), d6 + 2 * (J + 1), d6 + 3 * (J + 1),
+                                                      d6 + 4 * (J + 1), d6 + 5 * (J + 1), d_off, d_adj, d_w, off,
+                                                      adj, w);
   b_set_i64_k<<<1, 1, 0, s>>>(off + n_new, m_new);
   count_launch(2);
   VC_CHECK_LAUNCH();
@@ -957,7 +1139,7 @@ static void server_join(Server& S, std::vector<std::shared_ptr<Request>>& add) {
   b_gid_init_k<<<gridK, 256, 0, s>>>(K, B, E.gid);
   count_launch(2);
   VC_CHECK_LAUNCH();
-  for (auto& r : add) S.all_simple = S.all_simple && r->simple;
+  for (int i = 0; i < J; ++i) S.all_simple = S.all_simple && !(herr[kj[i]] & 64);
   E.G = GraphView();
   E.G.n = n_new;
   E.G.nnz = m_new;
@@ -972,7 +1154,7 @@ static void server_join(Server& S, std::vector<std::shared_ptr<Request>>& add) {
   W.ensure_entries(m_new, n_new);
   E.vact.ensure_n<unsigned char>(n_new);
   engine_start_new(E);
-  VC_CUDA(cudaStreamSynchronize(s));  // staging buffers and host vectors go out of scope
+  VC_CUDA(cudaStreamSynchronize(s));
   S.joins += 1;
 }
 
@@ -1020,6 +1202,7 @@ static void server_collect(Server& S) {
     S.slot_req[fin[i]].reset();
     S.completed += 1;
   }
+  S.cv_solo.notify_one();  // budget came free
 }
 
 static void server_loop(Server& S) {
@@ -1049,14 +1232,7 @@ static void server_loop(Server& S) {
           continue;
         }
       }
-      if (!add.empty()) {
-        server_join(S, add);
-        for (auto& r : add) {  // the host copy is on the device now
-          std::vector<int64_t>().swap(r->off);
-          std::vector<int32_t>().swap(r->adj);
-          std::vector<int32_t>().swap(r->w);
-        }
-      }
+      if (!add.empty()) server_join(S, add);
       engine_step(E);
       server_collect(S);
     }
@@ -1064,6 +1240,64 @@ static void server_loop(Server& S) {
     std::lock_guard<std::mutex> lk(S.mu);
     S.error = e.msg.empty() ? "server failed" : e.msg;
   }
+}
+
+static void solo_check(int rc) {
+  if (rc != VIECUT_OK) throw Error{rc, viecut_last_error()};
+}
+
+// The solo lane: takes the large requests in arrival order (each within the shared
+// memory budget) and runs each alone through a reusable single-graph handle, whose
+// load checks the graph on the device (a refused graph is answered with the reason).
+static void solo_loop(Server& S) {
+  viecut_t* h = nullptr;
+  try {
+    VC_CUDA(cudaSetDevice(S.E.device));
+    for (;;) {
+      std::shared_ptr<Request> r;
+      {
+        std::unique_lock<std::mutex> lk(S.mu);
+        S.cv_solo.wait(lk, [&] {
+          return S.stopping || (!S.solo_pending.empty() && S.budget_used + S.solo_pending.front()->est <= S.budget);
+        });
+        if (S.stopping) break;
+        r = S.solo_pending.front();
+        S.solo_pending.pop_front();
+        S.budget_used += r->est;
+        S.admitted += 1;
+      }
+      int rc = h ? viecut_load(h, r->off, r->adj, r->n, r->m, r->w)
+                 : viecut_create(&h, r->off, r->adj, r->n, r->m, r->w, &S.solo_opts);
+      if (rc == VIECUT_EINVAL) {
+        const std::string why = viecut_last_error();
+        std::lock_guard<std::mutex> lk(S.mu);
+        refuse(S, r, why);
+        S.cv.notify_one();
+        continue;
+      }
+      solo_check(rc);
+      S.host.put(r->blk);  // the graph is on the device now
+      int64_t cut = 0;
+      std::vector<uint64_t> bits((r->n + 63) / 64);
+      solo_check(viecut_run(h, r->seed, S.lp_iters, &cut, bits.data()));
+      const auto now = std::chrono::steady_clock::now();
+      {
+        std::lock_guard<std::mutex> lk(S.mu);
+        r->cut = cut;
+        r->bits.swap(bits);
+        r->t_done = now;
+        r->done = true;
+        S.budget_used -= r->est;
+        S.completed += 1;
+        S.solo_completed += 1;
+      }
+      S.cv.notify_one();  // budget came free for the union
+    }
+  } catch (const Error& e) {
+    std::lock_guard<std::mutex> lk(S.mu);
+    S.error = e.msg.empty() ? "server solo lane failed" : e.msg;
+  }
+  if (h) viecut_destroy(h);
 }
 
 }  // namespace vc
@@ -1151,6 +1385,7 @@ int viecut_server_opts_init(viecut_server_opts* o) {
   o->hbm_budget_bytes = (int64_t)120 << 30;
   o->max_slots = 1024;
   o->lp_iters = 2;
+  o->solo_min_n = 65536;
   return VIECUT_OK;
 }
 
@@ -1161,7 +1396,8 @@ int viecut_server_start(viecut_server** out, const viecut_server_opts* opts) {
   viecut_server_opts o;
   viecut_server_opts_init(&o);
   if (opts) o = *opts;
-  if (o.max_slots < 1 || o.hbm_budget_bytes < 1 || o.lp_iters < 0 || o.base.n0 < 1 || o.base.pr_runs_max < 0)
+  if (o.max_slots < 1 || o.hbm_budget_bytes < 1 || o.lp_iters < 0 || o.base.n0 < 1 || o.base.pr_runs_max < 0 ||
+      o.solo_min_n < 0)
     throw Error{VIECUT_EINVAL, "bad server options"};
   auto* x = new viecut_server;
   try {
@@ -1172,7 +1408,13 @@ int viecut_server_start(viecut_server** out, const viecut_server_opts* opts) {
     S.budget = o.hbm_budget_bytes;
     S.slot_req.assign(o.max_slots, nullptr);
     for (int g = o.max_slots - 1; g >= 0; --g) S.free_slots.push_back(g);
+    S.solo_min_n = o.solo_min_n;
+    S.solo_opts = o.base;
+    S.solo_opts.stream = nullptr;  // a stream of its own, beside the union's
+    S.solo_opts.validate = 1;      // already checked on submit; the device pass finds unit / simple
+    S.solo_opts.timing = 0;
     S.th = std::thread(vc::server_loop, std::ref(S));
+    if (S.solo_min_n > 0) S.th_solo = std::thread(vc::solo_loop, std::ref(S));
   } catch (...) {
     delete x;
     throw;
@@ -1193,30 +1435,30 @@ int viecut_server_submit(viecut_server* sv, const viecut_graph_desc* g, uint64_t
   r->n = n;
   r->m = m;
   r->seed = seed;
-  r->off.assign(g->offsets, g->offsets + n);
-  r->adj.assign(g->adj, g->adj + m);
-  r->w.assign(g->weights, g->weights + m);
-  for (int64_t v = 0; v < n; ++v) {
-    if (g->offsets[v + 1] < g->offsets[v]) throw Error{VIECUT_EINVAL, "graph: offsets decrease"};
-    for (int64_t e = g->offsets[v]; e < g->offsets[v + 1]; ++e) {
-      const int32_t u = g->adj[e];
-      if (u < 0 || u >= n) throw Error{VIECUT_EINVAL, "graph: neighbour id out of range"};
-      if (u == v) throw Error{VIECUT_EINVAL, "graph: self-loop"};
-      if (g->weights[e] < 1) throw Error{VIECUT_EINVAL, "graph: weight < 1"};
-      if (e + 1 < g->offsets[v + 1] && g->adj[e + 1] <= u) r->simple = false;
-    }
-  }
   r->est = vc::request_estimate(n, m);
   if (r->est > S.budget) throw Error{VIECUT_EINVAL, "graph needs more than the server's memory budget"};
+  // one copy into a page-locked block; the per-entry checks run on the device
+  const size_t b_off = sizeof(int64_t) * (n + 1), b_adj = sizeof(int32_t) * m;
+  r->blk = S.host.get((int64_t)(b_off + 2 * b_adj));
+  r->off = (int64_t*)r->blk.p;
+  r->adj = (int32_t*)((char*)r->blk.p + b_off);
+  r->w = (int32_t*)((char*)r->blk.p + b_off + b_adj);
+  memcpy(r->off, g->offsets, b_off);
+  if (m > 0) {
+    memcpy(r->adj, g->adj, b_adj);
+    memcpy(r->w, g->weights, b_adj);
+  }
   r->t_submit = std::chrono::steady_clock::now();
   {
     std::lock_guard<std::mutex> lk(S.mu);
     if (!S.error.empty()) throw Error{VIECUT_ECUDA, S.error};
     r->ticket = S.next_ticket++;
     S.tickets[r->ticket] = r;
-    S.pending.push_back(r);
+    if (S.solo_min_n > 0 && n >= S.solo_min_n) S.solo_pending.push_back(r);
+    else S.pending.push_back(r);
   }
   S.cv.notify_one();
+  S.cv_solo.notify_one();
   *ticket = r->ticket;
   VC_API_END
 }
@@ -1237,6 +1479,7 @@ int viecut_server_poll(viecut_server* sv, uint64_t ticket, int64_t* cut, uint64_
     r = it->second;
     S.tickets.erase(it);
   }
+  if (r->err) throw Error{r->err, r->err_msg};
   if (cut) *cut = r->cut;
   if (side_bits && !r->bits.empty()) memcpy(side_bits, r->bits.data(), sizeof(uint64_t) * r->bits.size());
   if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
@@ -1250,11 +1493,13 @@ int viecut_server_get_stats(viecut_server* sv, viecut_server_stats* st) {
   std::lock_guard<std::mutex> lk(S.mu);
   st->admitted = S.admitted;
   st->completed = S.completed;
-  st->pending = (int64_t)S.pending.size();
+  st->pending = (int64_t)(S.pending.size() + S.solo_pending.size());
   st->max_resident = S.max_resident;
   st->super_steps = S.E.steps;
   st->joins = S.joins;
   st->budget_used = S.budget_used;
+  st->solo_completed = S.solo_completed;
+  st->rejected = S.rejected;
   VC_API_END
 }
 
@@ -1266,7 +1511,9 @@ int viecut_server_stop(viecut_server* sv) {
     sv->s.stopping = true;
   }
   sv->s.cv.notify_all();
+  sv->s.cv_solo.notify_all();
   if (sv->s.th.joinable()) sv->s.th.join();
+  if (sv->s.th_solo.joinable()) sv->s.th_solo.join();
   cudaSetDevice(sv->s.E.device);
   if (sv->s.E.stream) cudaStreamSynchronize(sv->s.E.stream);
   delete sv;

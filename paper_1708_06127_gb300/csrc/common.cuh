@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <atomic>
 #include <string>
 
 namespace vc {
@@ -35,7 +36,7 @@ inline int grid_for(int64_t work, int per_block, int max_blocks) {
 
 // Number of kernels this library launched (process-wide), for the launch count
 // reported beside timings.
-extern unsigned long long g_launches;
+extern std::atomic<unsigned long long> g_launches;  // host threads of servers count too
 inline void count_launch(int k = 1) { g_launches += (unsigned long long)k; }
 
 // ------------------------------------------------------------ device helpers

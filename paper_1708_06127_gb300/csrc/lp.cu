@@ -234,6 +234,154 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
   }
 }
 
+// ------------------------------------------------------------ register class
+// Lists of at most kWarpMaxDeg = 128 entries: a warp per vertex holding the whole
+// list's keys in registers (kRegSlots per lane, every load of the list issued before
+// the first is used).  The warp then visits the distinct keys one at a time: the
+// first lane with an unvisited key broadcasts it, each lane marks its entries holding
+// it, and a warp reduction gives the key's count (unit weights) or weight sum.  No
+// table and no shared memory: one short warp step per distinct key.
+constexpr int kRegSlots = kWarpMaxDeg / 32;
+static_assert(kRegSlots == 4, "the key selection below is written for 4 slots");
+
+struct RegList {
+  int32_t k[kRegSlots];
+  long long wt[kRegSlots];
+  unsigned todo;  // bit r: slot r holds a used entry not yet visited
+};
+
+template <typename WT, int MODE, bool FIRST>
+__device__ __forceinline__ void reg_load(RegList& L, int64_t beg, int64_t end, int lane,
+                                         const int32_t* __restrict__ adj, const WT* __restrict__ w,
+                                         const int32_t* __restrict__ lab, int32_t own) {
+  int32_t u[kRegSlots];
+#pragma unroll
+  for (int r = 0; r < kRegSlots; ++r) {
+    const int64_t e = beg + lane + 32 * r;
+    u[r] = e < end ? __ldg(adj + e) : -1;
+  }
+  L.todo = 0;
+#pragma unroll
+  for (int r = 0; r < kRegSlots; ++r) {
+    const int64_t e = beg + lane + 32 * r;
+    L.k[r] = -1;
+    L.wt[r] = 0;
+    if (e < end) {
+      int32_t kk;
+      if (entry_key<MODE, FIRST>(lab, u[r], own, &kk)) L.todo |= 1u << r;
+      L.k[r] = kk;
+      L.wt[r] = ldw(w, e);
+    }
+  }
+}
+
+// Visits the next distinct key: false once every key was visited.
+template <typename WT>
+__device__ __forceinline__ bool reg_next(RegList& L, int32_t* key, long long* total) {
+  const unsigned bal = __ballot_sync(0xffffffffu, L.todo != 0);
+  if (!bal) return false;
+  const int leader = __ffs(bal) - 1;
+  const int32_t mine_first = (L.todo & 1u) ? L.k[0] : (L.todo & 2u) ? L.k[1] : (L.todo & 4u) ? L.k[2] : L.k[3];
+  const int32_t kk = __shfl_sync(0xffffffffu, mine_first, leader);
+  unsigned hit = 0;
+#pragma unroll
+  for (int r = 0; r < kRegSlots; ++r)
+    if (L.k[r] == kk) hit |= 1u << r;
+  hit &= L.todo;
+  L.todo &= ~hit;
+  if (std::is_same<WT, UnitW>::value) {
+    *total = (long long)__reduce_add_sync(0xffffffffu, (unsigned)__popc(hit));
+  } else {
+    long long sum = 0;
+#pragma unroll
+    for (int r = 0; r < kRegSlots; ++r)
+      if (hit >> r & 1u) sum += L.wt[r];
+    *total = warp_sum(sum);
+  }
+  *key = kk;
+  return true;
+}
+
+template <typename WT, bool FIRST>
+__global__ void __launch_bounds__(kAggThreads) lp_reg_k(int64_t n, const int64_t* __restrict__ off,
+                                                        const int32_t* __restrict__ adj, const WT* __restrict__ w,
+                                                        const int32_t* __restrict__ lab, int32_t* __restrict__ lab_out,
+                                                        const unsigned long long* __restrict__ hv,
+                                                        const unsigned char* __restrict__ vact) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * kWarpsPerBlock;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    if (vact && !vact[v]) continue;
+    const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
+    if (end - beg > kWarpMaxDeg) continue;
+    if (end == beg) {
+      if (lane == 0) lab_out[v] = FIRST ? (int32_t)v : __ldg(lab + v);
+      continue;
+    }
+    RegList L;
+    reg_load<WT, kModeLP, FIRST>(L, beg, end, lane, adj, w, lab, 0);
+    // running best (sum, hash, -label), the same in every lane; the hash of the best
+    // is read only once a tie needs it
+    long long bs = -1;
+    int32_t bl = INT_MAX;
+    unsigned long long bh = 0;
+    bool hashed = false;
+    int32_t kk;
+    long long t;
+    while (reg_next<WT>(L, &kk, &t)) {
+      if (t > bs) {
+        bs = t;
+        bl = kk;
+        hashed = false;
+      } else if (t == bs) {
+        if (!hashed) { bh = __ldg(hv + bl); hashed = true; }
+        const unsigned long long h = __ldg(hv + kk);
+        if (h > bh || (h == bh && kk < bl)) { bh = h; bl = kk; }
+      }
+    }
+    if (lane == 0) lab_out[v] = bl;
+  }
+}
+
+// Pre-merge of the register class: one (key, sum) per distinct foreign cluster of the
+// whole list; lane i keeps the i-th pair of each group of 32 and the group is
+// written with one coalesced store.
+template <typename WT>
+__global__ void __launch_bounds__(kAggThreads) emit_reg_k(int64_t n, const int64_t* __restrict__ off,
+                                                          const int32_t* __restrict__ adj, const WT* __restrict__ w,
+                                                          const int32_t* __restrict__ cid,
+                                                          int32_t* __restrict__ tkey, long long* __restrict__ tval,
+                                                          int32_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * kWarpsPerBlock;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
+    if (end - beg > kWarpMaxDeg) continue;
+    const int32_t own = __ldg(cid + v);
+    int made = 0;  // warp-uniform
+    if (own >= 0 && end > beg) {
+      RegList L;
+      reg_load<WT, kModeEmit, false>(L, beg, end, lane, adj, w, cid, own);
+      int32_t pk = 0;
+      long long pv = 0;
+      int32_t kk;
+      long long t;
+      while (reg_next<WT>(L, &kk, &t)) {
+        if (lane == (made & 31)) { pk = kk; pv = t; }
+        if ((++made & 31) == 0) {
+          tkey[beg + made - 32 + lane] = pk;
+          tval[beg + made - 32 + lane] = pv;
+        }
+      }
+      if (lane < (made & 31)) {
+        tkey[beg + (made & ~31) + lane] = pk;
+        tval[beg + (made & ~31) + lane] = pv;
+      }
+    }
+    if (lane == 0) cnt[v] = made;
+  }
+}
+
 // First round on a graph whose lists are strictly increasing: every neighbour is its
 // own label, so S(u) = c(v,u) and the choice is the argmax of (c(v,u), hash(u), -u)
 // over the list; no accumulation needed.  A warp per vertex (lengths <= MAXD) or, for
@@ -285,10 +433,17 @@ __global__ void __launch_bounds__(kAggThreads) lp_first_simple_k(int64_t n, int 
       // a lane without entries
       unsigned long long bh = 0;
       int bl = INT_MAX;
-      for (int64_t e = beg + glane; e < end; e += G) {
-        const int u = __ldg(adj + e);
-        const unsigned long long h = __ldg(hv + u);
-        if (bl == INT_MAX || h > bh || (h == bh && u < bl)) { bh = h; bl = u; }
+      // four entries per lane in flight: ids first, then their hashes
+      for (int64_t e0 = beg + glane; e0 < end; e0 += 4 * G) {
+        int u[4];
+        unsigned long long h[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) u[r] = e0 + r * G < end ? __ldg(adj + e0 + r * G) : -1;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) h[r] = u[r] >= 0 ? __ldg(hv + u[r]) : 0ULL;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (u[r] >= 0 && (bl == INT_MAX || h[r] > bh || (h[r] == bh && u[r] < bl))) { bh = h[r]; bl = u[r]; }
       }
 #pragma unroll
       for (int o = G / 2; o > 0; o >>= 1) {
@@ -380,7 +535,7 @@ __device__ __forceinline__ void emit_chunk(int64_t e, int64_t end, const int32_t
 // G lanes per vertex: 32 / G vertices per warp, each group walking its list in
 // G-entry chunks (a short list leaves fewer lanes idle with a smaller G).
 template <typename WT, int G>
-__global__ void __launch_bounds__(kAggThreads) emit_warp_k(int64_t n, int maxd, const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(kAggThreads) emit_warp_k(int64_t n, int mind, int maxd, const int64_t* __restrict__ off,
                                                            const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                            const int32_t* __restrict__ cid, int32_t* __restrict__ tkey,
                                                            long long* __restrict__ tval, int32_t* __restrict__ cnt) {
@@ -389,7 +544,7 @@ __global__ void __launch_bounds__(kAggThreads) emit_warp_k(int64_t n, int maxd, 
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
   for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
     const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
-    if (end - beg > maxd) continue;
+    if (end - beg > maxd || end - beg <= mind) continue;
     const int32_t own = __ldg(cid + v);
     int made = 0;  // group-uniform
     if (own >= 0)
@@ -533,16 +688,10 @@ void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const 
     }
     return;
   }
-  {
-    constexpr int CAP = kWarpCap;
-    const size_t smem = warp_smem<CAP, ACC>();
-    auto kfn = lp_warp_k<WT, ACC, FIRST, CAP, false>;
-    set_smem(kfn, smem);
-    kfn<<<grid_for(g.n, kWarpsPerBlock * 4, kSMs * 8), kAggThreads, smem, s>>>(g.n, nullptr, nullptr, g.off, g.adj,
-                                                                              w, lab, lab_out, key, g.vact);
-    count_launch();
-    VC_CHECK_LAUNCH();
-  }
+  lp_reg_k<WT, FIRST><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(g.n, g.off, g.adj, w, lab,
+                                                                                       lab_out, key, g.vact);
+  count_launch();
+  VC_CHECK_LAUNCH();
   if (b.h_mid > 0) {
     constexpr int CAP = kMidCap;
     const size_t smem = warp_smem<CAP, ACC>();
@@ -576,15 +725,22 @@ template <typename WT>
 void launch_emit(const GraphView& g, const Bins& b, const int32_t* cid, int32_t* tkey, long long* tval,
                  int32_t* cnt, int G, cudaStream_t s) {
   const WT* w = (const WT*)g.w;
-  const int grid = grid_for(g.n, kAggThreads / G, kSMs * 16);
-  if (G == 8)
-    emit_warp_k<WT, 8><<<grid, kAggThreads, 0, s>>>(g.n, kBlockMaxDeg, g.off, g.adj, w, cid, tkey, tval, cnt);
-  else if (G == 16)
-    emit_warp_k<WT, 16><<<grid, kAggThreads, 0, s>>>(g.n, kBlockMaxDeg, g.off, g.adj, w, cid, tkey, tval, cnt);
-  else
-    emit_warp_k<WT, 32><<<grid, kAggThreads, 0, s>>>(g.n, kBlockMaxDeg, g.off, g.adj, w, cid, tkey, tval, cnt);
+  emit_reg_k<WT><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(g.n, g.off, g.adj, w, cid, tkey,
+                                                                                  tval, cnt);
   count_launch();
   VC_CHECK_LAUNCH();
+  if (b.h_mid + b.h_block > 0) {
+    const int grid = grid_for(g.n, kAggThreads / G, kSMs * 16);
+    const int lo = kWarpMaxDeg, hi = kBlockMaxDeg;
+    if (G == 8)
+      emit_warp_k<WT, 8><<<grid, kAggThreads, 0, s>>>(g.n, lo, hi, g.off, g.adj, w, cid, tkey, tval, cnt);
+    else if (G == 16)
+      emit_warp_k<WT, 16><<<grid, kAggThreads, 0, s>>>(g.n, lo, hi, g.off, g.adj, w, cid, tkey, tval, cnt);
+    else
+      emit_warp_k<WT, 32><<<grid, kAggThreads, 0, s>>>(g.n, lo, hi, g.off, g.adj, w, cid, tkey, tval, cnt);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
   if (b.h_global > 0) {
     emit_block_k<WT><<<grid_for(b.h_global, 1, kSMs * 4), kAggThreads, 0, s>>>(b.global_list, b.counts + 2, g.off,
                                                                                g.adj, w, cid, tkey, tval, cnt);

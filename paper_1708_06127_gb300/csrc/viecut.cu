@@ -17,7 +17,7 @@
 
 namespace vc {
 
-unsigned long long g_launches = 0;
+std::atomic<unsigned long long> g_launches{0};
 static thread_local std::string t_last_error;
 void set_last_error(const std::string& msg) { t_last_error = msg; }
 
@@ -59,6 +59,8 @@ struct Handle {
   int validate = 1;
   bool unit = false;    // every input weight is 1 (found by validation)
   bool simple = false;  // every input list strictly increasing (found by validation)
+  bool host_input = false;  // the graph was copied from host arrays into in_*
+  bool bound = false;       // a graph passed validation and may run
   const int64_t* off0 = nullptr;
   const int32_t* adj0 = nullptr;
   const int32_t* w0 = nullptr;
@@ -133,6 +135,7 @@ static bool host_validate(const int64_t* off, const int32_t* adj, const int32_t*
 // ------------------------------------------------------------------- the run
 static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, unsigned long long* d_bits) {
   if (lp_iters < 0) throw Error{VIECUT_EINVAL, "lp_iters must be >= 0"};
+  if (!H.bound) throw Error{VIECUT_EINVAL, "the handle holds no valid graph (its last viecut_load failed)"};
   Workspace& W = *H.ws;
   W.s = H.stream;
   cudaStream_t s = H.stream;
@@ -387,15 +390,56 @@ int viecut_opts_init(viecut_opts* o) {
   return VIECUT_OK;
 }
 
+static void check_shape(int64_t n, int64_t m, const int64_t* off, const int32_t* adj, const int32_t* w) {
+  if (n < 2) throw Error{VIECUT_EINVAL, "n must be >= 2"};
+  if (n > 0x7fffffffLL) throw Error{VIECUT_EINVAL, "n must fit int32 vertex ids"};
+  if (m < 0) throw Error{VIECUT_EINVAL, "m must be >= 0"};
+  if (!off || (m > 0 && (!adj || !w))) throw Error{VIECUT_EINVAL, "null graph array"};
+}
+
+// Points the handle at a graph: host arrays are copied into the handle's grow-only
+// input buffers, device arrays are used in place; then validated per the handle's
+// option (2: on the host before any copy; 1: one pass on the device).
+// checked: the host check already ran (its findings in unit / simple).
+static void bind_graph(vc::Handle& H, bool host_input, const int64_t* off, const int32_t* adj, const int32_t* w,
+                       int64_t n, int64_t m, bool checked = false, bool unit = false, bool simple = false) {
+  H.bound = false;
+  if (host_input && H.validate >= 2 && !checked) unit = vc::host_validate(off, adj, w, n, m, true, &simple);
+  VC_CUDA(cudaSetDevice(H.device));
+  H.n = n;
+  H.m = m;
+  H.unit = unit;
+  H.simple = simple;
+  H.host_input = host_input;
+  if (host_input) {
+    H.off0 = H.in_off.ensure_n<int64_t>(n + 1);
+    H.adj0 = H.in_adj.ensure_n<int32_t>(std::max<int64_t>(m, 1));
+    H.w0 = H.in_w.ensure_n<int32_t>(std::max<int64_t>(m, 1));
+    VC_CUDA(cudaMemcpyAsync((void*)H.off0, off, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, H.stream));
+    if (m > 0) {
+      VC_CUDA(cudaMemcpyAsync((void*)H.adj0, adj, sizeof(int32_t) * m, cudaMemcpyHostToDevice, H.stream));
+      VC_CUDA(cudaMemcpyAsync((void*)H.w0, w, sizeof(int32_t) * m, cudaMemcpyHostToDevice, H.stream));
+    }
+  } else {
+    H.off0 = off;
+    H.adj0 = adj;
+    H.w0 = w;
+  }
+  H.ws->ensure_vertices(n);
+  H.ws->ensure_entries(m, n);
+  H.out_cut.ensure_n<long long>(1);
+  H.out_bits.ensure_n<unsigned long long>((n + 63) / 64);
+  if (H.validate == 1 || (!host_input && H.validate >= 1)) vc::device_validate(H);
+  VC_CUDA(cudaStreamSynchronize(H.stream));
+  H.bound = true;
+}
+
 static int create_common(viecut_t** out, int64_t n, int64_t m, const viecut_opts* opts, bool host_input,
                          const int64_t* off, const int32_t* adj, const int32_t* w) {
   VC_API_BEGIN
   if (!out) throw Error{VIECUT_EINVAL, "null handle pointer"};
   *out = nullptr;
-  if (n < 2) throw Error{VIECUT_EINVAL, "n must be >= 2"};
-  if (n > 0x7fffffffLL) throw Error{VIECUT_EINVAL, "n must fit int32 vertex ids"};
-  if (m < 0) throw Error{VIECUT_EINVAL, "m must be >= 0"};
-  if (!off || (m > 0 && (!adj || !w))) throw Error{VIECUT_EINVAL, "null graph array"};
+  check_shape(n, m, off, adj, w);
   viecut_opts o;
   viecut_opts_init(&o);
   if (opts) o = *opts;
@@ -403,10 +447,10 @@ static int create_common(viecut_t** out, int64_t n, int64_t m, const viecut_opts
   if (o.pr_runs_max < 0) throw Error{VIECUT_EINVAL, "pr_runs_max must be >= 0"};
   for (int G : {o.lp_group, o.emit_group})
     if (G != 0 && G != 8 && G != 16 && G != 32) throw Error{VIECUT_EINVAL, "lp_group and emit_group must be 0, 8, 16 or 32"};
-  // validate 2: full check on the host (symmetry needs a sort); validate 1: one pass
-  // on the device after the copy
+  // validate 2 rejects a malformed host graph before any device call
+  const bool checked = host_input && o.validate >= 2;
   bool unit = false, simple = false;
-  if (host_input && o.validate >= 2) unit = vc::host_validate(off, adj, w, n, m, true, &simple);
+  if (checked) unit = vc::host_validate(off, adj, w, n, m, true, &simple);
   auto* hh = new viecut_handle;
   vc::Handle& H = hh->h;
   try {
@@ -418,42 +462,31 @@ static int create_common(viecut_t** out, int64_t n, int64_t m, const viecut_opts
       VC_CUDA(cudaStreamCreateWithFlags(&H.stream, cudaStreamNonBlocking));
       H.own_stream = true;
     }
-    H.n = n;
-    H.m = m;
     H.n0 = o.n0;
     H.pr_runs_max = o.pr_runs_max;
     H.validate = o.validate;
-    H.unit = unit;
-    H.simple = simple;
     H.ws = new vc::Workspace;
     H.ws->s = H.stream;
     H.ws->timing = o.timing != 0;
     H.ws->fix_groups(o.lp_group, o.emit_group);
-    if (host_input) {
-      H.off0 = H.in_off.ensure_n<int64_t>(n + 1);
-      H.adj0 = H.in_adj.ensure_n<int32_t>(m);
-      H.w0 = H.in_w.ensure_n<int32_t>(m);
-      VC_CUDA(cudaMemcpyAsync((void*)H.off0, off, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, H.stream));
-      if (m > 0) {
-        VC_CUDA(cudaMemcpyAsync((void*)H.adj0, adj, sizeof(int32_t) * m, cudaMemcpyHostToDevice, H.stream));
-        VC_CUDA(cudaMemcpyAsync((void*)H.w0, w, sizeof(int32_t) * m, cudaMemcpyHostToDevice, H.stream));
-      }
-    } else {
-      H.off0 = off;
-      H.adj0 = adj;
-      H.w0 = w;
-    }
-    H.ws->ensure_vertices(n);
-    H.ws->ensure_entries(m, n);
-    H.out_cut.ensure_n<long long>(1);
-    H.out_bits.ensure_n<unsigned long long>((n + 63) / 64);
-    if (o.validate == 1 || (!host_input && o.validate >= 1)) vc::device_validate(H);
-    VC_CUDA(cudaStreamSynchronize(H.stream));
+    bind_graph(H, host_input, off, adj, w, n, m, checked, unit, simple);
   } catch (...) {
     delete hh;
     throw;
   }
   *out = hh;
+  VC_API_END
+}
+
+int viecut_load(viecut_t* h, const int64_t* offsets, const int32_t* adj, int64_t n, int64_t m,
+                const int32_t* weights) {
+  VC_API_BEGIN
+  if (!h) throw Error{VIECUT_EINVAL, "null handle"};
+  if (!h->h.host_input) throw Error{VIECUT_EINVAL, "viecut_load needs a handle made by viecut_create"};
+  check_shape(n, m, offsets, adj, weights);
+  VC_CUDA(cudaSetDevice(h->h.device));
+  VC_CUDA(cudaStreamSynchronize(h->h.stream));  // a previous run may still read the inputs
+  bind_graph(h->h, true, offsets, adj, weights, n, m);
   VC_API_END
 }
 

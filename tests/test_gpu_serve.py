@@ -95,15 +95,85 @@ def test_serve_concurrent_submitters_and_small_budget():
 
 
 def test_serve_rejects_bad_requests():
+    """Shape and budget faults fail the submit; per-entry faults are found by the device
+    check on either lane and answered through poll, while the other requests are served."""
     with vc.Server(hbm_budget_bytes=1 << 20) as srv:
         big = gg.core_lcc(gg.rhg(1 << 14, 32, 1), 0)
         with pytest.raises(vc.ViecutError) as e:
             srv.submit(big.offsets, big.adj, big.w, 1)
         assert e.value.code == vc.VIECUT_EINVAL and "budget" in str(e.value)
         bad = gg.from_edges(3, [(0, 1, 1), (1, 2, 1)])
-        bad.adj[0] = 0  # self-loop at vertex 0
+        bad.offsets[3] = 5  # offsets[n] != m
         with pytest.raises(vc.ViecutError) as e:
             srv.submit(bad.offsets, bad.adj, bad.w, 1)
         assert e.value.code == vc.VIECUT_EINVAL
         with pytest.raises(vc.ViecutError):
             vc.viecut_server_poll(srv.s, 12345, 3)
+    for solo_min_n in (0, 3):  # union lane, then solo lane for graphs of >= 3 vertices
+        with vc.Server(solo_min_n=solo_min_n) as srv:
+            good = H.pr2_counterexample()
+            loop = gg.from_edges(3, [(0, 1, 1), (1, 2, 1)])
+            loop.adj[0] = 0  # self-loop at vertex 0
+            far = gg.from_edges(4, [(0, 1, 1), (2, 3, 2)])
+            far.adj[1] = 9   # neighbour id out of range
+            zero = gg.from_edges(3, [(0, 1, 1), (1, 2, 1)])
+            zero.w[:] = 0    # weight < 1
+            tickets = [srv.submit(x.offsets, x.adj, x.w, 3) for x in (good, loop, far, zero, good)]
+            for t, why in zip(tickets[1:4], ("self-loop", "out of range", "weight")):
+                with pytest.raises(vc.ViecutError) as e:
+                    srv.wait(t)
+                assert e.value.code == vc.VIECUT_EINVAL and why in str(e.value), (solo_min_n, str(e.value))
+            for t in (tickets[0], tickets[4]):
+                check_result(good, 3, srv.wait(t))
+            st = srv.stats()
+            assert st["rejected"] == 3 and st["completed"] == 5 and st["budget_used"] == 0, st
+
+
+def test_serve_solo_lane_beside_the_union():
+    """Requests at or above solo_min_n vertices run alone on their own handle and stream
+    while the rest share the union; both lanes give the oracle's results."""
+    reqs = request_mix(30, 21)
+    big = [gg.core_lcc(gg.rhg(1 << 13, 32, 77 + i), 0) for i in range(4)]
+    reqs[3:3] = [(g, 50 + i) for i, g in enumerate(big)]
+    with vc.Server(max_slots=32, solo_min_n=4000) as srv:
+        tickets = [srv.submit(g.offsets, g.adj, g.w, seed) for g, seed in reqs]
+        results = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+    for (g, seed), res in zip(reqs, results):
+        check_result(g, seed, res)
+    n_solo = sum(1 for g, _ in reqs if g.n >= 4000)
+    assert st["solo_completed"] == n_solo >= 4, st
+    assert st["completed"] == len(reqs) and st["budget_used"] == 0
+
+
+def test_load_reuses_a_handle_across_graphs():
+    """viecut_load rebinds a host-made handle to other graphs (larger, then smaller);
+    every run equals the oracle's; a device-made handle refuses it."""
+    import torch
+    gs = [H.random_graph(50, 0.2, 3, wmax=4), gg.workload_rhg_small(4), H.pr2_counterexample(),
+          gg.with_pair_weights(gg.core_lcc(gg.er(3000, 8, 2), 0), 2, 1, 9)]
+    with vc.MinCut(gs[0].offsets, gs[0].adj, gs[0].w, n0=64) as mc:
+        for i, g in enumerate(gs + gs[::-1]):
+            mc.load(g.offsets, g.adj, g.w)
+            cut, bits = mc.run(7 + i, 2)
+            ref = oracle.viecut(g.offsets, g.adj, g.w, seed=7 + i, lp_iters=2, n0=64)
+            assert cut == ref.cut and np.array_equal(bits, ref.side_bits), (i, g.name)
+        bad = gg.from_edges(3, [(0, 1, 1), (1, 2, 1)])
+        bad.adj[0] = 0
+        with pytest.raises(vc.ViecutError) as e:
+            mc.load(bad.offsets, bad.adj, bad.w)
+        assert e.value.code == vc.VIECUT_EINVAL
+        with pytest.raises(vc.ViecutError) as e:  # nothing runs on a graph that failed its check
+            mc.run(1, 2)
+        assert e.value.code == vc.VIECUT_EINVAL
+        g = gs[2]
+        mc.load(g.offsets, g.adj, g.w)  # a good graph makes the handle usable again
+        ref = oracle.viecut(g.offsets, g.adj, g.w, seed=1, lp_iters=2, n0=64)
+        assert mc.run(1, 2)[0] == ref.cut
+    g = gs[1]
+    dev = torch.device("cuda:0")
+    d = [torch.from_numpy(x).to(dev) for x in (g.offsets, g.adj, g.w)]
+    with vc.MinCut(*d, on_device=True) as mc:
+        with pytest.raises(vc.ViecutError) as e:
+            mc.load(g.offsets, g.adj, g.w)
+        assert e.value.code == vc.VIECUT_EINVAL and "viecut_create" in str(e.value)
