@@ -235,42 +235,37 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
 }
 
 // ------------------------------------------------------------ register class
-// Lists of at most kWarpMaxDeg = 128 entries.  A group of G lanes (G = 8, 16, 32;
-// 32 / G vertices per warp) takes one vertex of at most 4G entries and holds the
-// whole list's keys in registers (kRegSlots per lane; every load of the list is
-// issued before the first is used).  The group then visits the distinct keys one at
-// a time: the first lane with an unvisited key broadcasts it, each lane marks its
-// entries holding it, and a group reduction gives the key's count (unit weights) or
-// weight sum.  No table and no shared memory: one short step per distinct key, and a
-// short list occupies only a short group.
+// Lists of at most kWarpMaxDeg = 128 entries: a warp per vertex holding the whole
+// list's keys in registers (slot r of lane i holds entry 32r + i; every load of the
+// list is issued before the first is used).  The warp then visits the distinct keys
+// one at a time, slot by slot: the first lane whose slot r is still unvisited
+// broadcasts its key, every lane marks its entries holding it (only slots >= r can),
+// and a warp reduction gives the key's count (unit weights) or weight sum.  No table
+// and no shared memory: one short warp step per distinct key.
 constexpr int kRegSlots = kWarpMaxDeg / 32;
-static_assert(kRegSlots == 4, "the key selection below is written for 4 slots");
 
 struct RegList {
   int32_t k[kRegSlots];
   long long wt[kRegSlots];
   unsigned todo;  // bit r: slot r holds a used entry not yet visited
+  int slots;      // slots in use: ceil(deg / 32), the same in every lane
 };
 
-template <int G>
-__device__ __forceinline__ unsigned group_mask(int lane) {
-  return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-}
-
-template <typename WT, int MODE, bool FIRST, int G>
-__device__ __forceinline__ void reg_load(RegList& L, int64_t beg, int64_t end, int glane,
+template <typename WT, int MODE, bool FIRST>
+__device__ __forceinline__ void reg_load(RegList& L, int64_t beg, int64_t end, int lane,
                                          const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                          const int32_t* __restrict__ lab, int32_t own) {
   int32_t u[kRegSlots];
+  L.slots = (int)((end - beg + 31) >> 5);
 #pragma unroll
   for (int r = 0; r < kRegSlots; ++r) {
-    const int64_t e = beg + glane + G * r;
+    const int64_t e = beg + lane + 32 * r;
     u[r] = e < end ? __ldg(adj + e) : -1;
   }
   L.todo = 0;
 #pragma unroll
   for (int r = 0; r < kRegSlots; ++r) {
-    const int64_t e = beg + glane + G * r;
+    const int64_t e = beg + lane + 32 * r;
     L.k[r] = -1;
     L.wt[r] = 0;
     if (e < end) {
@@ -282,65 +277,64 @@ __device__ __forceinline__ void reg_load(RegList& L, int64_t beg, int64_t end, i
   }
 }
 
-// Visits the group's next distinct key: false once every key was visited.
-template <typename WT, int G>
-__device__ __forceinline__ bool reg_next(RegList& L, unsigned gmask, int32_t* key, long long* total) {
-  const unsigned bal = __ballot_sync(gmask, L.todo != 0) & gmask;
-  if (!bal) return false;
-  const int leader = __ffs(bal) - 1;
-  const int32_t mine_first = (L.todo & 1u) ? L.k[0] : (L.todo & 2u) ? L.k[1] : (L.todo & 4u) ? L.k[2] : L.k[3];
-  const int32_t kk = __shfl_sync(gmask, mine_first, leader);
-  unsigned hit = 0;
+// Calls visit(key, total) once per distinct used key, in slot-then-lane order of
+// first occurrence; total is warp-uniform.
+template <typename WT, typename ACC, typename F>
+__device__ __forceinline__ void reg_visit(RegList& L, F visit) {
 #pragma unroll
-  for (int r = 0; r < kRegSlots; ++r)
-    if (L.k[r] == kk) hit |= 1u << r;
-  hit &= L.todo;
-  L.todo &= ~hit;
-  if (std::is_same<WT, UnitW>::value) {
-    *total = (long long)__reduce_add_sync(gmask, (unsigned)__popc(hit));
-  } else {
-    long long sum = 0;
+  for (int r = 0; r < kRegSlots; ++r) {
+    if (r >= L.slots) break;
+    for (;;) {
+      const unsigned bal = __ballot_sync(0xffffffffu, (L.todo >> r) & 1u);
+      if (!bal) break;
+      const int32_t kk = __shfl_sync(0xffffffffu, L.k[r], __ffs(bal) - 1);
+      unsigned hit = 0;
 #pragma unroll
-    for (int r = 0; r < kRegSlots; ++r)
-      if (hit >> r & 1u) sum += L.wt[r];
+      for (int q = r; q < kRegSlots; ++q)
+        if (q < L.slots && L.k[q] == kk) hit |= 1u << q;
+      hit &= L.todo;
+      L.todo &= ~hit;
+      ACC total;
+      if (std::is_same<WT, UnitW>::value) {
+        total = (ACC)__reduce_add_sync(0xffffffffu, (unsigned)__popc(hit));
+      } else {
+        long long sum = 0;
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(gmask, sum, o);
-    *total = sum;
+        for (int q = r; q < kRegSlots; ++q)
+          if (hit >> q & 1u) sum += L.wt[q];
+        total = (ACC)warp_sum(sum);
+      }
+      visit(kk, total);
+    }
   }
-  *key = kk;
-  return true;
 }
 
-// Vertices with lo < deg <= 4G (and lo < 0 also takes the empty lists).
-template <typename WT, bool FIRST, int G>
-__global__ void __launch_bounds__(kAggThreads) lp_reg_k(int64_t n, int lo, const int64_t* __restrict__ off,
+template <typename WT, typename ACC, bool FIRST>
+__global__ void __launch_bounds__(kAggThreads) lp_reg_k(int64_t n, const int64_t* __restrict__ off,
                                                         const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                         const int32_t* __restrict__ lab, int32_t* __restrict__ lab_out,
                                                         const unsigned long long* __restrict__ hv,
                                                         const unsigned char* __restrict__ vact) {
-  const int lane = threadIdx.x & 31, glane = lane & (G - 1);
-  const unsigned gmask = group_mask<G>(lane);
-  const int64_t groups = (int64_t)gridDim.x * (kAggThreads / G);
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * kWarpsPerBlock;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
     if (vact && !vact[v]) continue;
     const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
-    if (end - beg > 4 * G || end - beg <= lo) continue;
+    if (end - beg > kWarpMaxDeg) continue;
     if (end == beg) {
-      if (glane == 0) lab_out[v] = FIRST ? (int32_t)v : __ldg(lab + v);
+      if (lane == 0) lab_out[v] = FIRST ? (int32_t)v : __ldg(lab + v);
       continue;
     }
     RegList L;
-    reg_load<WT, kModeLP, FIRST, G>(L, beg, end, glane, adj, w, lab, 0);
-    // running best (sum, hash, -label), the same in every lane of the group; the
-    // hash of the best is read only once a tie needs it
-    long long bs = -1;
-    int32_t bl = INT_MAX;
+    reg_load<WT, kModeLP, FIRST>(L, beg, end, lane, adj, w, lab, 0);
+    // running best (sum, hash, -label), the same in every lane; the hash of the best
+    // is read only once a tie needs it
+    ACC bs = 0;
+    int32_t bl = -1;
     unsigned long long bh = 0;
     bool hashed = false;
-    int32_t kk;
-    long long t;
-    while (reg_next<WT, G>(L, gmask, &kk, &t)) {
-      if (t > bs) {
+    reg_visit<WT, ACC>(L, [&](int32_t kk, ACC t) {
+      if (bl < 0 || t > bs) {
         bs = t;
         bl = kk;
         hashed = false;
@@ -349,77 +343,46 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(int64_t n, int lo, const
         const unsigned long long h = __ldg(hv + kk);
         if (h > bh || (h == bh && kk < bl)) { bh = h; bl = kk; }
       }
-    }
-    if (glane == 0) lab_out[v] = bl;
+    });
+    if (lane == 0) lab_out[v] = bl;
   }
 }
 
 // Pre-merge of the register class: one (key, sum) per distinct foreign cluster of the
-// whole list; lane i of the group keeps the i-th pair of each run of G pairs, and a
-// full run is written with one coalesced store.
-template <typename WT, int G>
-__global__ void __launch_bounds__(kAggThreads) emit_reg_k(int64_t n, int lo, const int64_t* __restrict__ off,
+// whole list; lane i keeps the i-th pair of each run of 32 pairs, and a full run is
+// written with one coalesced store.
+template <typename WT>
+__global__ void __launch_bounds__(kAggThreads) emit_reg_k(int64_t n, const int64_t* __restrict__ off,
                                                           const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                           const int32_t* __restrict__ cid,
                                                           int32_t* __restrict__ tkey, long long* __restrict__ tval,
                                                           int32_t* __restrict__ cnt) {
-  const int lane = threadIdx.x & 31, glane = lane & (G - 1);
-  const unsigned gmask = group_mask<G>(lane);
-  const int64_t groups = (int64_t)gridDim.x * (kAggThreads / G);
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * kWarpsPerBlock;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
     const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
-    if (end - beg > 4 * G || end - beg <= lo) continue;
+    if (end - beg > kWarpMaxDeg) continue;
     const int32_t own = __ldg(cid + v);
-    int made = 0;  // group-uniform
+    int made = 0;  // warp-uniform
     if (own >= 0 && end > beg) {
       RegList L;
-      reg_load<WT, kModeEmit, false, G>(L, beg, end, glane, adj, w, cid, own);
+      reg_load<WT, kModeEmit, false>(L, beg, end, lane, adj, w, cid, own);
       int32_t pk = 0;
       long long pv = 0;
-      int32_t kk;
-      long long t;
-      while (reg_next<WT, G>(L, gmask, &kk, &t)) {
-        if (glane == (made & (G - 1))) { pk = kk; pv = t; }
-        if ((++made & (G - 1)) == 0) {
-          tkey[beg + made - G + glane] = pk;
-          tval[beg + made - G + glane] = pv;
+      reg_visit<WT, long long>(L, [&](int32_t kk, long long t) {
+        if (lane == (made & 31)) { pk = kk; pv = t; }
+        if ((++made & 31) == 0) {
+          tkey[beg + made - 32 + lane] = pk;
+          tval[beg + made - 32 + lane] = pv;
         }
-      }
-      if (glane < (made & (G - 1))) {
-        tkey[beg + (made & ~(G - 1)) + glane] = pk;
-        tval[beg + (made & ~(G - 1)) + glane] = pv;
+      });
+      if (lane < (made & 31)) {
+        tkey[beg + (made & ~31) + lane] = pk;
+        tval[beg + (made & ~31) + lane] = pv;
       }
     }
-    if (glane == 0) cnt[v] = made;
+    if (lane == 0) cnt[v] = made;
   }
-}
-
-// The register class in three launches by list length: (-, 32] in groups of 8,
-// (32, 64] in groups of 16, (64, 128] in groups of 32.
-template <typename WT, bool FIRST>
-void launch_lp_reg(const GraphView& g, const WT* w, const int32_t* lab, int32_t* lab_out,
-                   const unsigned long long* hv, cudaStream_t s) {
-  lp_reg_k<WT, FIRST, 8><<<grid_for(g.n, kAggThreads / 8, kSMs * 16), kAggThreads, 0, s>>>(g.n, -1, g.off, g.adj, w,
-                                                                                          lab, lab_out, hv, g.vact);
-  lp_reg_k<WT, FIRST, 16><<<grid_for(g.n, kAggThreads / 16, kSMs * 16), kAggThreads, 0, s>>>(g.n, 32, g.off, g.adj, w,
-                                                                                            lab, lab_out, hv, g.vact);
-  lp_reg_k<WT, FIRST, 32><<<grid_for(g.n, kAggThreads / 32, kSMs * 16), kAggThreads, 0, s>>>(g.n, 64, g.off, g.adj, w,
-                                                                                            lab, lab_out, hv, g.vact);
-  count_launch(3);
-  VC_CHECK_LAUNCH();
-}
-
-template <typename WT>
-void launch_emit_reg(const GraphView& g, const WT* w, const int32_t* cid, int32_t* tkey, long long* tval,
-                     int32_t* cnt, cudaStream_t s) {
-  emit_reg_k<WT, 8><<<grid_for(g.n, kAggThreads / 8, kSMs * 16), kAggThreads, 0, s>>>(g.n, -1, g.off, g.adj, w, cid,
-                                                                                      tkey, tval, cnt);
-  emit_reg_k<WT, 16><<<grid_for(g.n, kAggThreads / 16, kSMs * 16), kAggThreads, 0, s>>>(g.n, 32, g.off, g.adj, w, cid,
-                                                                                        tkey, tval, cnt);
-  emit_reg_k<WT, 32><<<grid_for(g.n, kAggThreads / 32, kSMs * 16), kAggThreads, 0, s>>>(g.n, 64, g.off, g.adj, w, cid,
-                                                                                        tkey, tval, cnt);
-  count_launch(3);
-  VC_CHECK_LAUNCH();
 }
 
 // First round on a graph whose lists are strictly increasing: every neighbour is its
@@ -728,7 +691,10 @@ void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const 
     }
     return;
   }
-  launch_lp_reg<WT, FIRST>(g, w, lab, lab_out, key, s);
+  lp_reg_k<WT, ACC, FIRST><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(g.n, g.off, g.adj, w,
+                                                                                             lab, lab_out, key, g.vact);
+  count_launch();
+  VC_CHECK_LAUNCH();
   if (b.h_mid > 0) {
     constexpr int CAP = kMidCap;
     const size_t smem = warp_smem<CAP, ACC>();
@@ -762,7 +728,10 @@ template <typename WT>
 void launch_emit(const GraphView& g, const Bins& b, const int32_t* cid, int32_t* tkey, long long* tval,
                  int32_t* cnt, int G, cudaStream_t s) {
   const WT* w = (const WT*)g.w;
-  launch_emit_reg<WT>(g, w, cid, tkey, tval, cnt, s);
+  emit_reg_k<WT><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(g.n, g.off, g.adj, w, cid, tkey,
+                                                                                  tval, cnt);
+  count_launch();
+  VC_CHECK_LAUNCH();
   if (b.h_mid + b.h_block > 0) {
     const int grid = grid_for(g.n, kAggThreads / G, kSMs * 16);
     const int lo = kWarpMaxDeg, hi = kBlockMaxDeg;
