@@ -236,13 +236,36 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
 
 // ------------------------------------------------------------ register class
 // Lists of at most kWarpMaxDeg = 128 entries: a warp per vertex holding the whole
-// list's keys in registers (slot r of lane i holds entry 32r + i; every load of the
-// list is issued before the first is used).  The warp then visits the distinct keys
-// one at a time, slot by slot: the first lane whose slot r is still unvisited
-// broadcasts its key, every lane marks its entries holding it (only slots >= r can),
-// and a warp reduction gives the key's count (unit weights) or weight sum.  No table
-// and no shared memory: one short warp step per distinct key.
+// list in registers (slot r of lane i holds entry 32r + i).  The warp visits the
+// distinct keys one at a time, slot by slot: the first lane whose slot r is still
+// unvisited broadcasts its key, every lane marks its entries holding it (only slots
+// >= r can), and a warp reduction gives the key's count (unit weights) or weight sum.
+// No table and no shared memory: one short warp step per distinct key.
+//
+// A vertex needs three dependent reads (its offsets, its neighbour ids, their
+// labels), so the warp software-pipelines its vertices: while it works on one vertex
+// it already holds the next vertex's ids and the offsets of the one after.
 constexpr int kRegSlots = kWarpMaxDeg / 32;
+
+// Neighbour ids (and weights) of one list in registers; lists longer than the class
+// load nothing (another kernel takes them).
+struct RegIds {
+  int32_t u[kRegSlots];
+  long long wt[kRegSlots];
+};
+
+template <typename WT>
+__device__ __forceinline__ void reg_ids(RegIds& R, int64_t beg, int64_t end, int lane,
+                                        const int32_t* __restrict__ adj, const WT* __restrict__ w) {
+  const int d = end - beg > kWarpMaxDeg ? 0 : (int)(end - beg);
+  const int32_t* a = adj + beg;
+#pragma unroll
+  for (int r = 0; r < kRegSlots; ++r) {
+    const int i = lane + 32 * r;
+    R.u[r] = i < d ? __ldg(a + i) : -1;
+    R.wt[r] = i < d ? ldw(w, beg + i) : 0;
+  }
+}
 
 struct RegList {
   int32_t k[kRegSlots];
@@ -251,28 +274,19 @@ struct RegList {
   int slots;      // slots in use: ceil(deg / 32), the same in every lane
 };
 
-template <typename WT, int MODE, bool FIRST>
-__device__ __forceinline__ void reg_load(RegList& L, int64_t beg, int64_t end, int lane,
-                                         const int32_t* __restrict__ adj, const WT* __restrict__ w,
-                                         const int32_t* __restrict__ lab, int32_t own) {
-  int32_t u[kRegSlots];
-  L.slots = (int)((end - beg + 31) >> 5);
-#pragma unroll
-  for (int r = 0; r < kRegSlots; ++r) {
-    const int64_t e = beg + lane + 32 * r;
-    u[r] = e < end ? __ldg(adj + e) : -1;
-  }
+template <int MODE, bool FIRST>
+__device__ __forceinline__ void reg_keys(RegList& L, const RegIds& R, int deg, const int32_t* __restrict__ lab,
+                                         int32_t own) {
+  L.slots = (deg + 31) >> 5;
   L.todo = 0;
 #pragma unroll
   for (int r = 0; r < kRegSlots; ++r) {
-    const int64_t e = beg + lane + 32 * r;
     L.k[r] = -1;
-    L.wt[r] = 0;
-    if (e < end) {
+    L.wt[r] = R.wt[r];
+    if (R.u[r] >= 0) {
       int32_t kk;
-      if (entry_key<MODE, FIRST>(lab, u[r], own, &kk)) L.todo |= 1u << r;
+      if (entry_key<MODE, FIRST>(lab, R.u[r], own, &kk)) L.todo |= 1u << r;
       L.k[r] = kk;
-      L.wt[r] = ldw(w, e);
     }
   }
 }
@@ -309,6 +323,37 @@ __device__ __forceinline__ void reg_visit(RegList& L, F visit) {
   }
 }
 
+// The pipelined vertex loop of a warp: body(v, beg, end, ids) runs for every vertex
+// v = first, first + stride, ... < n, with v's ids already in registers; `pre(v)`
+// is read with the offsets one vertex ahead (e.g. v's own cluster id).
+template <typename WT, typename PRE, typename BODY>
+__device__ __forceinline__ void reg_pipeline(int64_t n, int64_t first, int64_t stride, int lane,
+                                             const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                                             const WT* __restrict__ w, PRE pre, BODY body) {
+  int64_t v = first;
+  if (v >= n) return;
+  int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
+  int32_t x = pre(v);
+  RegIds cur;
+  reg_ids(cur, beg, end, lane, adj, w);
+  int64_t vn = v + stride, nbeg = 0, nend = 0;
+  int32_t xn = 0;
+  if (vn < n) { nbeg = __ldg(off + vn); nend = __ldg(off + vn + 1); xn = pre(vn); }
+  for (;;) {
+    RegIds nxt;
+    int64_t vnn = vn + stride, nnbeg = 0, nnend = 0;
+    int32_t xnn = 0;
+    if (vn < n) {
+      reg_ids(nxt, nbeg, nend, lane, adj, w);
+      if (vnn < n) { nnbeg = __ldg(off + vnn); nnend = __ldg(off + vnn + 1); xnn = pre(vnn); }
+    }
+    body(v, beg, end, x, cur);
+    if (vn >= n) break;
+    v = vn; beg = nbeg; end = nend; x = xn; cur = nxt;
+    vn = vnn; nbeg = nnbeg; nend = nnend; xn = xnn;
+  }
+}
+
 template <typename WT, typename ACC, bool FIRST>
 __global__ void __launch_bounds__(kAggThreads) lp_reg_k(int64_t n, const int64_t* __restrict__ off,
                                                         const int32_t* __restrict__ adj, const WT* __restrict__ w,
@@ -317,16 +362,17 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(int64_t n, const int64_t
                                                         const unsigned char* __restrict__ vact) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * kWarpsPerBlock;
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
-    if (vact && !vact[v]) continue;
-    const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
-    if (end - beg > kWarpMaxDeg) continue;
+  const int64_t first = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  reg_pipeline<WT>(n, first, warps, lane, off, adj, w,
+                   [&](int64_t v) { return vact ? (int32_t)vact[v] : 1; },
+                   [&](int64_t v, int64_t beg, int64_t end, int32_t active, const RegIds& ids) {
+    if (!active || end - beg > kWarpMaxDeg) return;
     if (end == beg) {
       if (lane == 0) lab_out[v] = FIRST ? (int32_t)v : __ldg(lab + v);
-      continue;
+      return;
     }
     RegList L;
-    reg_load<WT, kModeLP, FIRST>(L, beg, end, lane, adj, w, lab, 0);
+    reg_keys<kModeLP, FIRST>(L, ids, (int)(end - beg), lab, 0);
     // running best (sum, hash, -label), the same in every lane; the hash of the best
     // is read only once a tie needs it
     ACC bs = 0;
@@ -345,7 +391,7 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(int64_t n, const int64_t
       }
     });
     if (lane == 0) lab_out[v] = bl;
-  }
+  });
 }
 
 // Pre-merge of the register class: one (key, sum) per distinct foreign cluster of the
@@ -359,14 +405,14 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(int64_t n, const int64
                                                           int32_t* __restrict__ cnt) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * kWarpsPerBlock;
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
-    const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
-    if (end - beg > kWarpMaxDeg) continue;
-    const int32_t own = __ldg(cid + v);
+  const int64_t first = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  reg_pipeline<WT>(n, first, warps, lane, off, adj, w, [&](int64_t v) { return __ldg(cid + v); },
+                   [&](int64_t v, int64_t beg, int64_t end, int32_t own, const RegIds& ids) {
+    if (end - beg > kWarpMaxDeg) return;
     int made = 0;  // warp-uniform
     if (own >= 0 && end > beg) {
       RegList L;
-      reg_load<WT, kModeEmit, false>(L, beg, end, lane, adj, w, cid, own);
+      reg_keys<kModeEmit, false>(L, ids, (int)(end - beg), cid, own);
       int32_t pk = 0;
       long long pv = 0;
       reg_visit<WT, long long>(L, [&](int32_t kk, long long t) {
@@ -382,7 +428,7 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(int64_t n, const int64
       }
     }
     if (lane == 0) cnt[v] = made;
-  }
+  });
 }
 
 // First round on a graph whose lists are strictly increasing: every neighbour is its
