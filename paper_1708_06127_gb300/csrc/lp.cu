@@ -33,14 +33,27 @@ enum { kModeLP = 0, kModeEmit = 1 };
 
 __global__ void bins_k(int64_t n, const int64_t* __restrict__ off, int32_t* __restrict__ mlist,
                        int32_t* __restrict__ blist, int32_t* __restrict__ glist, int* __restrict__ counts) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    int64_t d = off[v + 1] - off[v];
-    if (d > kWarpMaxDeg) {
-      if (d <= kMidMaxDeg) mlist[atomicAdd(&counts[0], 1)] = (int32_t)v;
-      else if (d <= kBlockMaxDeg) blist[atomicAdd(&counts[1], 1)] = (int32_t)v;
-      else glist[atomicAdd(&counts[2], 1)] = (int32_t)v;
-      atomicMax(&counts[3], (int)(d < INT_MAX ? d : INT_MAX));
+  // grid-stride in whole warps so that every lane reaches the ballots below; one
+  // atomic per warp and class reserves the warp's positions
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t v = base + lane;
+    const int64_t d = v < n ? off[v + 1] - off[v] : 0;
+    const int cls = d <= kWarpMaxDeg ? -1 : d <= kMidMaxDeg ? 0 : d <= kBlockMaxDeg ? 1 : 2;
+    int32_t* lists[3] = {mlist, blist, glist};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const unsigned m = __ballot_sync(0xffffffffu, cls == c);
+      if (!m) continue;
+      int at = 0;
+      if (lane == __ffs(m) - 1) at = atomicAdd(&counts[c], __popc(m));
+      at = __shfl_sync(0xffffffffu, at, __ffs(m) - 1);
+      if (cls == c) lists[c][at + __popc(m & ((1u << lane) - 1u))] = (int32_t)v;
     }
+    const int dm = (int)(d < INT_MAX ? d : INT_MAX);
+    const int wmax = __reduce_max_sync(0xffffffffu, cls >= 0 ? (unsigned)dm : 0u);
+    if (lane == 0 && wmax > kWarpMaxDeg) atomicMax(&counts[3], wmax);
   }
 }
 
@@ -261,9 +274,15 @@ __device__ __forceinline__ void reg_ids(RegIds& R, int64_t beg, int64_t end, int
   const int32_t* a = adj + beg;
 #pragma unroll
   for (int r = 0; r < kRegSlots; ++r) {
-    const int i = lane + 32 * r;
-    R.u[r] = i < d ? __ldg(a + i) : -1;
-    R.wt[r] = i < d ? ldw(w, beg + i) : 0;
+    R.u[r] = -1;
+    R.wt[r] = 0;
+    if (32 * r < d) {  // the same in every lane: unused slots cost nothing
+      const int i = lane + 32 * r;
+      if (i < d) {
+        R.u[r] = __ldg(a + i);
+        R.wt[r] = ldw(w, beg + i);
+      }
+    }
   }
 }
 
@@ -283,7 +302,7 @@ __device__ __forceinline__ void reg_keys(RegList& L, const RegIds& R, int deg, c
   for (int r = 0; r < kRegSlots; ++r) {
     L.k[r] = -1;
     L.wt[r] = R.wt[r];
-    if (R.u[r] >= 0) {
+    if (r < L.slots && R.u[r] >= 0) {
       int32_t kk;
       if (entry_key<MODE, FIRST>(lab, R.u[r], own, &kk)) L.todo |= 1u << r;
       L.k[r] = kk;
@@ -373,23 +392,26 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(int64_t n, const int64_t
     }
     RegList L;
     reg_keys<kModeLP, FIRST>(L, ids, (int)(end - beg), lab, 0);
-    // running best (sum, hash, -label), the same in every lane; the hash of the best
-    // is read only once a tie needs it
-    ACC bs = 0;
-    int32_t bl = -1;
-    unsigned long long bh = 0;
-    bool hashed = false;
+    // lane i collects the i-th distinct label of each run of 32 with its sum; a full
+    // run (and the last) is folded into the lane's best with its hash, all lanes
+    // reading their hashes at once; a warp reduction picks (sum, hash, -label)
+    int made = 0;  // warp-uniform
+    int32_t pk = -1;
+    ACC pt = 0;
+    Cand best{-1LL, 0ULL, INT_MAX};
     reg_visit<WT, ACC>(L, [&](int32_t kk, ACC t) {
-      if (bl < 0 || t > bs) {
-        bs = t;
-        bl = kk;
-        hashed = false;
-      } else if (t == bs) {
-        if (!hashed) { bh = __ldg(hv + bl); hashed = true; }
-        const unsigned long long h = __ldg(hv + kk);
-        if (h > bh || (h == bh && kk < bl)) { bh = h; bl = kk; }
+      if (lane == (made & 31)) { pk = kk; pt = t; }
+      if ((++made & 31) == 0) {
+        const Cand c{(long long)pt, __ldg(hv + pk), pk};
+        if (better(c, best)) best = c;
+        pk = -1;
       }
     });
+    if (pk >= 0) {
+      const Cand c{(long long)pt, __ldg(hv + pk), pk};
+      if (better(c, best)) best = c;
+    }
+    const int32_t bl = warp_best(best).l;
     if (lane == 0) lab_out[v] = bl;
   });
 }
@@ -478,27 +500,30 @@ __global__ void __launch_bounds__(kAggThreads) lp_first_simple_k(int64_t n, int 
     }
     if (std::is_same<WT, UnitW>::value) {
       // unit weights: every neighbour has strength 1, so the choice is the neighbour
-      // of largest tie hash (distinct labels have distinct hashes); bl = INT_MAX marks
-      // a lane without entries
+      // of largest tie hash
+      // distinct ids have distinct hashes (mix64 is a bijection), so the largest
+      // hash alone decides; bl < 0 marks a lane without entries.  Four entries per
+      // lane in flight: ids first, then their hashes.
       unsigned long long bh = 0;
-      int bl = INT_MAX;
-      // four entries per lane in flight: ids first, then their hashes
-      for (int64_t e0 = beg + glane; e0 < end; e0 += 4 * G) {
+      int bl = -1;
+      const int d = (int)(end - beg);
+      const int32_t* a = adj + beg;
+      for (int i0 = glane; i0 < d; i0 += 4 * G) {
         int u[4];
         unsigned long long h[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) u[r] = e0 + r * G < end ? __ldg(adj + e0 + r * G) : -1;
+        for (int r = 0; r < 4; ++r) u[r] = i0 + r * G < d ? __ldg(a + i0 + r * G) : -1;
 #pragma unroll
         for (int r = 0; r < 4; ++r) h[r] = u[r] >= 0 ? __ldg(hv + u[r]) : 0ULL;
 #pragma unroll
         for (int r = 0; r < 4; ++r)
-          if (u[r] >= 0 && (bl == INT_MAX || h[r] > bh || (h[r] == bh && u[r] < bl))) { bh = h[r]; bl = u[r]; }
+          if (u[r] >= 0 && (h[r] > bh || bl < 0)) { bh = h[r]; bl = u[r]; }
       }
 #pragma unroll
       for (int o = G / 2; o > 0; o >>= 1) {
         const unsigned long long oh = __shfl_xor_sync(gmask, bh, o);
         const int ol = __shfl_xor_sync(gmask, bl, o);
-        if (ol != INT_MAX && (bl == INT_MAX || oh > bh || (oh == bh && ol < bl))) { bh = oh; bl = ol; }
+        if (ol >= 0 && (bl < 0 || oh > bh)) { bh = oh; bl = ol; }
       }
       if (glane == 0) lab_out[v] = bl;
     } else {
