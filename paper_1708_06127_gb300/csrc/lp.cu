@@ -392,26 +392,23 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(int64_t n, const int64_t
     }
     RegList L;
     reg_keys<kModeLP, FIRST>(L, ids, (int)(end - beg), lab, 0);
-    // lane i collects the i-th distinct label of each run of 32 with its sum; a full
-    // run (and the last) is folded into the lane's best with its hash, all lanes
-    // reading their hashes at once; a warp reduction picks (sum, hash, -label)
-    int made = 0;  // warp-uniform
-    int32_t pk = -1;
-    ACC pt = 0;
-    Cand best{-1LL, 0ULL, INT_MAX};
+    // running best (sum, hash, -label), the same in every lane; the hash of the best
+    // is read only once a tie needs it
+    ACC bs = 0;
+    int32_t bl = -1;
+    unsigned long long bh = 0;
+    bool hashed = false;
     reg_visit<WT, ACC>(L, [&](int32_t kk, ACC t) {
-      if (lane == (made & 31)) { pk = kk; pt = t; }
-      if ((++made & 31) == 0) {
-        const Cand c{(long long)pt, __ldg(hv + pk), pk};
-        if (better(c, best)) best = c;
-        pk = -1;
+      if (bl < 0 || t > bs) {
+        bs = t;
+        bl = kk;
+        hashed = false;
+      } else if (t == bs) {
+        if (!hashed) { bh = __ldg(hv + bl); hashed = true; }
+        const unsigned long long h = __ldg(hv + kk);
+        if (h > bh || (h == bh && kk < bl)) { bh = h; bl = kk; }
       }
     });
-    if (pk >= 0) {
-      const Cand c{(long long)pt, __ldg(hv + pk), pk};
-      if (better(c, best)) best = c;
-    }
-    const int32_t bl = warp_best(best).l;
     if (lane == 0) lab_out[v] = bl;
   });
 }
