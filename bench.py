@@ -35,6 +35,22 @@ WORKLOAD = "rhg(n=2^22, avg_deg=64, gamma=5) -> 16-core -> largest component, un
 SAMPLE_N = 1 << 19  # the CPU oracle's bounded sample: same family, n = 2^19
 
 
+def committed_lp_traffic():
+    """DRAM bytes per label-propagation round from the committed ncu summary, or None when
+    the kernels' source changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "lp_round_traffic_rhg_n1048576.md")
+    src = os.path.join(ROOT, "paper_1708_06127_gb300", "csrc", "lp.cu")
+    try:
+        fields = dict(line.split("=", 1) for line in open(path).read().splitlines() if "=" in line and " " not in line)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if fields.get("kernel_sha256_prefix") != sha:
+        return None
+    return int(fields["traffic_bytes_per_round_n2p22"])
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -435,6 +451,7 @@ def main():
     # counts 8(n+1) + nnz (4 + 4 + 4 label gather, none in a level's first round) + 4n per
     # round) over the rounds' summed CUDA-event time on the launching stream
     peaks = load_peaks() or {}
+    traffic = committed_lp_traffic() if args.nlog == 22 else None
     peak = peaks.get("hbm_gbs", 6800.0)
     lp_round_ms = lp_ms / max(1, lp_rounds)
     lp_round_bytes = lp_bytes / max(1, lp_rounds)
@@ -479,7 +496,9 @@ def main():
         "roofline": {"kernel": "label-propagation round (lp_first_simple_k, lp_warp_k and the block/global classes)",
                      "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "traffic_source": "profiles/lp_round_traffic_rhg_n1048576.md (ncu DRAM bytes of a level-0 "
+                                       "round at n=2^20, scaled by entries; null once lp.cu changed)",
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
                      "round_ms": lp_round_ms, "algorithmic_bytes_per_round": lp_round_bytes},
         "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
