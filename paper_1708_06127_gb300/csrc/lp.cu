@@ -248,40 +248,47 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
 }
 
 // ------------------------------------------------------------ register class
-// Lists of at most kWarpMaxDeg = 128 entries: a warp per vertex holding the whole
-// list in registers (slot r of lane i holds entry 32r + i).  The warp visits the
+// Lists of at most kWarpMaxDeg = 128 entries.  A group of G lanes (G = 16 for lists
+// of at most 64 entries, two vertices per warp; G = 32 for 65..128) holds the whole
+// list in registers (slot r of group lane i holds entry G r + i) and visits its
 // distinct keys one at a time, slot by slot: the first lane whose slot r is still
 // unvisited broadcasts its key, every lane marks its entries holding it (only slots
-// >= r can), and a warp reduction gives the key's count (unit weights) or weight sum.
-// No table and no shared memory: one short warp step per distinct key.
+// >= r can), and a group reduction gives the key's count (unit weights) or weight
+// sum.  No table and no shared memory: one short step per distinct key.  The groups
+// of a warp step in lockstep (the loops run while any group has work; a group
+// without work idles), so every warp-wide vote and shuffle has all lanes present.
 //
-// A vertex needs three dependent reads (its offsets, its neighbour ids, their
-// labels), so the warp software-pipelines its vertices: while it works on one vertex
-// it already holds the next vertex's ids and the offsets of the one after.
-constexpr int kRegSlots = kWarpMaxDeg / 32;
+// A vertex needs three dependent reads (its offsets, its neighbour ids, their keys),
+// so the warp software-pipelines its vertices: while it works on one vertex per
+// group it already holds the next vertex's ids and the offsets of the one after.
+constexpr int kRegSlots = 4;
 
-// Neighbour ids (and weights) of one list in registers; lists longer than the class
-// load nothing (another kernel takes them).
+template <int G>
+__device__ __forceinline__ unsigned group_mask(int lane) {
+  return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+}
+
+// Neighbour ids (and weights) of one list in registers; lists outside (lo, 4G] load
+// nothing (another launch takes them).
 struct RegIds {
   int32_t u[kRegSlots];
   long long wt[kRegSlots];
 };
 
-template <typename WT>
-__device__ __forceinline__ void reg_ids(RegIds& R, int64_t beg, int64_t end, int lane,
+template <typename WT, int G>
+__device__ __forceinline__ void reg_ids(RegIds& R, int64_t beg, int64_t end, int lo, int glane,
                                         const int32_t* __restrict__ adj, const WT* __restrict__ w) {
-  const int d = end - beg > kWarpMaxDeg ? 0 : (int)(end - beg);
+  const int64_t dd = end - beg;
+  const int d = (dd > 4 * G || dd <= lo) ? 0 : (int)dd;
   const int32_t* a = adj + beg;
 #pragma unroll
   for (int r = 0; r < kRegSlots; ++r) {
+    const int i = glane + G * r;
     R.u[r] = -1;
     R.wt[r] = 0;
-    if (32 * r < d) {  // the same in every lane: unused slots cost nothing
-      const int i = lane + 32 * r;
-      if (i < d) {
-        R.u[r] = __ldg(a + i);
-        R.wt[r] = ldw(w, beg + i);
-      }
+    if (i < d) {
+      R.u[r] = __ldg(a + i);
+      R.wt[r] = ldw(w, beg + i);
     }
   }
 }
@@ -290,19 +297,19 @@ struct RegList {
   int32_t k[kRegSlots];
   long long wt[kRegSlots];
   unsigned todo;  // bit r: slot r holds a used entry not yet visited
-  int slots;      // slots in use: ceil(deg / 32), the same in every lane
+  int slots;      // slots in use: ceil(deg / G), the same in every lane of the group
 };
 
-template <int MODE, bool FIRST>
+template <int MODE, bool FIRST, int G>
 __device__ __forceinline__ void reg_keys(RegList& L, const RegIds& R, int deg, const int32_t* __restrict__ lab,
                                          int32_t own) {
-  L.slots = (deg + 31) >> 5;
+  L.slots = (deg + G - 1) / G;
   L.todo = 0;
 #pragma unroll
   for (int r = 0; r < kRegSlots; ++r) {
     L.k[r] = -1;
     L.wt[r] = R.wt[r];
-    if (r < L.slots && R.u[r] >= 0) {
+    if (R.u[r] >= 0) {
       int32_t kk;
       if (entry_key<MODE, FIRST>(lab, R.u[r], own, &kk)) L.todo |= 1u << r;
       L.k[r] = kk;
@@ -310,95 +317,111 @@ __device__ __forceinline__ void reg_keys(RegList& L, const RegIds& R, int deg, c
   }
 }
 
-// Calls visit(key, total) once per distinct used key, in slot-then-lane order of
-// first occurrence; total is warp-uniform.
-template <typename WT, typename ACC, typename F>
-__device__ __forceinline__ void reg_visit(RegList& L, F visit) {
+// Calls visit(key, total) once per distinct used key of the group's list, in
+// slot-then-lane order of first occurrence; total is the same in the group's lanes.
+// Every lane of the warp must call it (groups without a list pass slots = todo = 0).
+template <typename WT, typename ACC, int G, typename F>
+__device__ __forceinline__ void reg_visit(RegList& L, unsigned gmask, F visit) {
 #pragma unroll
   for (int r = 0; r < kRegSlots; ++r) {
-    if (r >= L.slots) break;
+    if (!__any_sync(0xffffffffu, r < L.slots)) break;
     for (;;) {
       const unsigned bal = __ballot_sync(0xffffffffu, (L.todo >> r) & 1u);
       if (!bal) break;
-      const int32_t kk = __shfl_sync(0xffffffffu, L.k[r], __ffs(bal) - 1);
+      const unsigned gb = bal & gmask;
+      const int32_t kk = __shfl_sync(0xffffffffu, L.k[r], gb ? __ffs(gb) - 1 : 0);
       unsigned hit = 0;
 #pragma unroll
       for (int q = r; q < kRegSlots; ++q)
-        if (q < L.slots && L.k[q] == kk) hit |= 1u << q;
-      hit &= L.todo;
+        if (L.k[q] == kk) hit |= 1u << q;
+      hit = gb ? hit & L.todo : 0u;
       L.todo &= ~hit;
       ACC total;
       if (std::is_same<WT, UnitW>::value) {
-        total = (ACC)__reduce_add_sync(0xffffffffu, (unsigned)__popc(hit));
+        total = (ACC)__reduce_add_sync(gmask, (unsigned)__popc(hit));
       } else {
         long long sum = 0;
 #pragma unroll
         for (int q = r; q < kRegSlots; ++q)
           if (hit >> q & 1u) sum += L.wt[q];
-        total = (ACC)warp_sum(sum);
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        total = (ACC)sum;
       }
-      visit(kk, total);
+      if (gb) visit(kk, total);
     }
   }
 }
 
-// The pipelined vertex loop of a warp: body(v, beg, end, ids) runs for every vertex
-// v = first, first + stride, ... < n, with v's ids already in registers; `pre(v)`
-// is read with the offsets one vertex ahead (e.g. v's own cluster id).
-template <typename WT, typename PRE, typename BODY>
-__device__ __forceinline__ void reg_pipeline(int64_t n, int64_t first, int64_t stride, int lane,
+// The pipelined vertex loop of a warp.  Group g of the warp takes vertex
+// base + g for base = first, first + stride, ... (the trip count is the same for all
+// lanes); body(v, valid, beg, end, pre, ids) runs with v's ids already in registers.
+// `pre(v)` is read with the offsets one vertex ahead (e.g. v's own cluster id).
+template <typename WT, int G, typename PRE, typename BODY>
+__device__ __forceinline__ void reg_pipeline(int64_t n, int lo, int64_t first, int64_t stride, int glane, int gi,
                                              const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                                              const WT* __restrict__ w, PRE pre, BODY body) {
-  int64_t v = first;
-  if (v >= n) return;
-  int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
-  int32_t x = pre(v);
+  int64_t base = first;
+  if (base >= n) return;  // the same in every lane (base is per warp)
+  auto fetch = [&](int64_t b, int64_t& bg, int64_t& en, int32_t& x) {
+    const int64_t v = b + gi;
+    bg = en = 0;
+    x = 0;
+    if (v < n) { bg = __ldg(off + v); en = __ldg(off + v + 1); x = pre(v); }
+  };
+  int64_t beg, end, nbeg, nend;
+  int32_t x, xn;
+  fetch(base, beg, end, x);
   RegIds cur;
-  reg_ids(cur, beg, end, lane, adj, w);
-  int64_t vn = v + stride, nbeg = 0, nend = 0;
-  int32_t xn = 0;
-  if (vn < n) { nbeg = __ldg(off + vn); nend = __ldg(off + vn + 1); xn = pre(vn); }
+  reg_ids<WT, G>(cur, beg, end, lo, glane, adj, w);
+  int64_t bn = base + stride;
+  fetch(bn, nbeg, nend, xn);
   for (;;) {
     RegIds nxt;
-    int64_t vnn = vn + stride, nnbeg = 0, nnend = 0;
+    int64_t nnbeg = 0, nnend = 0;
     int32_t xnn = 0;
-    if (vn < n) {
-      reg_ids(nxt, nbeg, nend, lane, adj, w);
-      if (vnn < n) { nnbeg = __ldg(off + vnn); nnend = __ldg(off + vnn + 1); xnn = pre(vnn); }
+    const int64_t bnn = bn + stride;
+    if (bn < n) {
+      reg_ids<WT, G>(nxt, nbeg, nend, lo, glane, adj, w);
+      fetch(bnn, nnbeg, nnend, xnn);
     }
-    body(v, beg, end, x, cur);
-    if (vn >= n) break;
-    v = vn; beg = nbeg; end = nend; x = xn; cur = nxt;
-    vn = vnn; nbeg = nnbeg; nend = nnend; xn = xnn;
+    body(base + gi, base + gi < n, beg, end, x, cur);
+    if (bn >= n) break;
+    base = bn; beg = nbeg; end = nend; x = xn; cur = nxt;
+    bn = bnn; nbeg = nnbeg; nend = nnend; xn = xnn;
   }
 }
 
-template <typename WT, typename ACC, bool FIRST>
-__global__ void __launch_bounds__(kAggThreads) lp_reg_k(int64_t n, const int64_t* __restrict__ off,
+// Vertices with lo < deg <= 4G; the launch with lo < 0 also writes the empty lists.
+template <typename WT, typename ACC, bool FIRST, int G>
+__global__ void __launch_bounds__(kAggThreads) lp_reg_k(int64_t n, int lo, const int64_t* __restrict__ off,
                                                         const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                         const int32_t* __restrict__ lab, int32_t* __restrict__ lab_out,
                                                         const unsigned long long* __restrict__ hv,
                                                         const unsigned char* __restrict__ vact) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * kWarpsPerBlock;
-  const int64_t first = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  reg_pipeline<WT>(n, first, warps, lane, off, adj, w,
-                   [&](int64_t v) { return vact ? (int32_t)vact[v] : 1; },
-                   [&](int64_t v, int64_t beg, int64_t end, int32_t active, const RegIds& ids) {
-    if (!active || end - beg > kWarpMaxDeg) return;
-    if (end == beg) {
-      if (lane == 0) lab_out[v] = FIRST ? (int32_t)v : __ldg(lab + v);
-      return;
+  const int lane = threadIdx.x & 31, glane = lane & (G - 1), gi = lane / G;
+  const unsigned gmask = group_mask<G>(lane);
+  constexpr int kPer = 32 / G;  // vertices per warp
+  const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock * kPer;
+  const int64_t first = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kPer;
+  reg_pipeline<WT, G>(n, lo, first, stride, glane, gi, off, adj, w,
+                      [&](int64_t v) { return vact ? (int32_t)vact[v] : 1; },
+                      [&](int64_t v, bool valid, int64_t beg, int64_t end, int32_t active, const RegIds& ids) {
+    const int64_t d = end - beg;
+    const bool mine = valid && active && d > lo && d <= 4 * G;
+    if (mine && d == 0) {
+      if (glane == 0) lab_out[v] = FIRST ? (int32_t)v : __ldg(lab + v);
     }
     RegList L;
-    reg_keys<kModeLP, FIRST>(L, ids, (int)(end - beg), lab, 0);
-    // running best (sum, hash, -label), the same in every lane; the hash of the best
-    // is read only once a tie needs it
+    reg_keys<kModeLP, FIRST, G>(L, ids, mine ? (int)d : 0, lab, 0);
+    if (!mine) L.todo = 0;
+    // running best (sum, hash, -label), the same in the group's lanes; the hash of
+    // the best is read only once a tie needs it
     ACC bs = 0;
     int32_t bl = -1;
     unsigned long long bh = 0;
     bool hashed = false;
-    reg_visit<WT, ACC>(L, [&](int32_t kk, ACC t) {
+    reg_visit<WT, ACC, G>(L, gmask, [&](int32_t kk, ACC t) {
       if (bl < 0 || t > bs) {
         bs = t;
         bl = kk;
@@ -409,45 +432,69 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(int64_t n, const int64_t
         if (h > bh || (h == bh && kk < bl)) { bh = h; bl = kk; }
       }
     });
-    if (lane == 0) lab_out[v] = bl;
+    if (mine && d > 0 && glane == 0) lab_out[v] = bl;
   });
 }
 
 // Pre-merge of the register class: one (key, sum) per distinct foreign cluster of the
-// whole list; lane i keeps the i-th pair of each run of 32 pairs, and a full run is
-// written with one coalesced store.
-template <typename WT>
-__global__ void __launch_bounds__(kAggThreads) emit_reg_k(int64_t n, const int64_t* __restrict__ off,
+// whole list; group lane i keeps the i-th pair of each run of G pairs, and a full run
+// is written with one coalesced store.
+template <typename WT, int G>
+__global__ void __launch_bounds__(kAggThreads) emit_reg_k(int64_t n, int lo, const int64_t* __restrict__ off,
                                                           const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                           const int32_t* __restrict__ cid,
                                                           int32_t* __restrict__ tkey, long long* __restrict__ tval,
                                                           int32_t* __restrict__ cnt) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * kWarpsPerBlock;
-  const int64_t first = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  reg_pipeline<WT>(n, first, warps, lane, off, adj, w, [&](int64_t v) { return __ldg(cid + v); },
-                   [&](int64_t v, int64_t beg, int64_t end, int32_t own, const RegIds& ids) {
-    if (end - beg > kWarpMaxDeg) return;
-    int made = 0;  // warp-uniform
-    if (own >= 0 && end > beg) {
-      RegList L;
-      reg_keys<kModeEmit, false>(L, ids, (int)(end - beg), cid, own);
-      int32_t pk = 0;
-      long long pv = 0;
-      reg_visit<WT, long long>(L, [&](int32_t kk, long long t) {
-        if (lane == (made & 31)) { pk = kk; pv = t; }
-        if ((++made & 31) == 0) {
-          tkey[beg + made - 32 + lane] = pk;
-          tval[beg + made - 32 + lane] = pv;
-        }
-      });
-      if (lane < (made & 31)) {
-        tkey[beg + (made & ~31) + lane] = pk;
-        tval[beg + (made & ~31) + lane] = pv;
+  const int lane = threadIdx.x & 31, glane = lane & (G - 1), gi = lane / G;
+  const unsigned gmask = group_mask<G>(lane);
+  constexpr int kPer = 32 / G;
+  const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock * kPer;
+  const int64_t first = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kPer;
+  reg_pipeline<WT, G>(n, lo, first, stride, glane, gi, off, adj, w, [&](int64_t v) { return __ldg(cid + v); },
+                      [&](int64_t v, bool valid, int64_t beg, int64_t end, int32_t own, const RegIds& ids) {
+    const int64_t d = end - beg;
+    const bool mine = valid && d > lo && d <= 4 * G;
+    RegList L;
+    reg_keys<kModeEmit, false, G>(L, ids, (mine && own >= 0) ? (int)d : 0, cid, own);
+    if (!(mine && own >= 0)) L.todo = 0;
+    int made = 0;  // the same in the group's lanes
+    int32_t pk = 0;
+    long long pv = 0;
+    reg_visit<WT, long long, G>(L, gmask, [&](int32_t kk, long long t) {
+      if (glane == (made & (G - 1))) { pk = kk; pv = t; }
+      if ((++made & (G - 1)) == 0) {
+        tkey[beg + made - G + glane] = pk;
+        tval[beg + made - G + glane] = pv;
       }
+    });
+    if (glane < (made & (G - 1))) {
+      tkey[beg + (made & ~(G - 1)) + glane] = pk;
+      tval[beg + (made & ~(G - 1)) + glane] = pv;
     }
-    if (lane == 0) cnt[v] = made;
+    if (mine && glane == 0) cnt[v] = made;
   });
+}
+
+template <typename WT, typename ACC, bool FIRST>
+void launch_lp_reg(const GraphView& g, const WT* w, const int32_t* lab, int32_t* lab_out,
+                   const unsigned long long* hv, cudaStream_t s) {
+  lp_reg_k<WT, ACC, FIRST, 16><<<grid_for(g.n, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
+      g.n, -1, g.off, g.adj, w, lab, lab_out, hv, g.vact);
+  lp_reg_k<WT, ACC, FIRST, 32><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
+      g.n, 64, g.off, g.adj, w, lab, lab_out, hv, g.vact);
+  count_launch(2);
+  VC_CHECK_LAUNCH();
+}
+
+template <typename WT>
+void launch_emit_reg(const GraphView& g, const WT* w, const int32_t* cid, int32_t* tkey, long long* tval,
+                     int32_t* cnt, cudaStream_t s) {
+  emit_reg_k<WT, 16><<<grid_for(g.n, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(g.n, -1, g.off, g.adj, w,
+                                                                                          cid, tkey, tval, cnt);
+  emit_reg_k<WT, 32><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(g.n, 64, g.off, g.adj, w, cid,
+                                                                                      tkey, tval, cnt);
+  count_launch(2);
+  VC_CHECK_LAUNCH();
 }
 
 // First round on a graph whose lists are strictly increasing: every neighbour is its
@@ -759,10 +806,7 @@ void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const 
     }
     return;
   }
-  lp_reg_k<WT, ACC, FIRST><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(g.n, g.off, g.adj, w,
-                                                                                             lab, lab_out, key, g.vact);
-  count_launch();
-  VC_CHECK_LAUNCH();
+  launch_lp_reg<WT, ACC, FIRST>(g, w, lab, lab_out, key, s);
   if (b.h_mid > 0) {
     constexpr int CAP = kMidCap;
     const size_t smem = warp_smem<CAP, ACC>();
@@ -796,10 +840,7 @@ template <typename WT>
 void launch_emit(const GraphView& g, const Bins& b, const int32_t* cid, int32_t* tkey, long long* tval,
                  int32_t* cnt, int G, cudaStream_t s) {
   const WT* w = (const WT*)g.w;
-  emit_reg_k<WT><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(g.n, g.off, g.adj, w, cid, tkey,
-                                                                                  tval, cnt);
-  count_launch();
-  VC_CHECK_LAUNCH();
+  launch_emit_reg<WT>(g, w, cid, tkey, tval, cnt, s);
   if (b.h_mid + b.h_block > 0) {
     const int grid = grid_for(g.n, kAggThreads / G, kSMs * 16);
     const int lo = kWarpMaxDeg, hi = kBlockMaxDeg;
