@@ -65,7 +65,7 @@ struct Workspace {
   cudaStream_t s = nullptr;
   // vertex-sized
   Buf deg, labA, labB, map0, cidT, cur1, side1, flags, rank, cnt, pos, scan64, scan32, hv;
-  Buf partner, pw, parent, mlist, blist, glist, bcounts, noi_r, noi_seen;
+  Buf partner, pw, parent, slist, rlist, mlist, blist, glist, bcounts, noi_r, noi_seen;
   // entry-sized
   Buf tmpK, tmpV;
   // pair-sized
@@ -123,6 +123,8 @@ struct Workspace {
     partner.ensure_n<int32_t>(n);
     pw.ensure_n<long long>(n);
     parent.ensure_n<int32_t>(n);
+    slist.ensure_n<int32_t>(n);
+    rlist.ensure_n<int32_t>(n);
     mlist.ensure_n<int32_t>(n);
     blist.ensure_n<int32_t>(n);
     glist.ensure_n<int32_t>(n);
@@ -224,7 +226,7 @@ struct Workspace {
     });
   }
   void tune_emit(const GraphView& g, const int32_t* cid, int32_t* k, long long* v, int32_t* c) {
-    if (tuned_emit || g.n < kTuneMinN) return;
+    if (tuned_emit || g.n < kTuneMinN || bins.h_mid + bins.h_block == 0) return;
     tuned_emit = true;
     tune.emit_group = pick_group([&](int G) {
       LpTuning t = tune;
@@ -238,18 +240,22 @@ struct Workspace {
   bool bins_valid = false;
 
   void build_bins(const GraphView& g) {
+    bins.small_list = slist.as<int32_t>();
+    bins.reg_list = rlist.as<int32_t>();
     bins.mid_list = mlist.as<int32_t>();
     bins.block_list = blist.as<int32_t>();
     bins.global_list = glist.as<int32_t>();
     bins.counts = bcounts.as<int>();
     bins_build(g, bins, s);
-    int hc[4];
-    VC_CUDA(cudaMemcpyAsync(hc, bins.counts, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    int hc[6];
+    VC_CUDA(cudaMemcpyAsync(hc, bins.counts, 6 * sizeof(int), cudaMemcpyDeviceToHost, s));
     sync();
     bins.h_mid = hc[0];
     bins.h_block = hc[1];
     bins.h_global = hc[2];
     bins.h_maxdeg = hc[3];
+    bins.h_small = hc[4];
+    bins.h_reg = hc[5];
     if (bins.h_global > 0) {
       int64_t cap = global_table_cap(bins.h_maxdeg);
       int blocks = std::min(bins.h_global, kSMs);

@@ -48,12 +48,17 @@ constexpr int kMidCap = 1024;
 constexpr int kBlockMaxDeg = 4096;
 constexpr int kBlockCap = 8192;
 
+// Vertices by list length: small (<= 64), reg (65..128), mid (129..512), block
+// (513..4096), global (longer); each list in vertex order.
 struct Bins {
+  int32_t* small_list;   // [n]
+  int32_t* reg_list;     // [n]
   int32_t* mid_list;     // [n]
   int32_t* block_list;   // [n]
   int32_t* global_list;  // [n]
-  int* counts;           // device: [0] mid, [1] block, [2] global count, [3] max length
-  int h_mid = 0, h_block = 0, h_global = 0, h_maxdeg = 0;  // host copies
+  int* counts;           // device: [0] mid, [1] block, [2] global count, [3] max length above
+                         // 128, [4] small, [5] reg count
+  int h_mid = 0, h_block = 0, h_global = 0, h_maxdeg = 0, h_small = 0, h_reg = 0;  // host copies
 };
 
 void bins_build(const GraphView& g, Bins& b, cudaStream_t s);

@@ -17,6 +17,7 @@
 //   global (larger)  : a block per listed vertex, table in global scratch.
 #include <limits.h>
 
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
 #include <unordered_map>
@@ -31,36 +32,80 @@ constexpr int kEmptyKey = -1;
 
 enum { kModeLP = 0, kModeEmit = 1 };
 
-__global__ void bins_k(int64_t n, const int64_t* __restrict__ off, int32_t* __restrict__ mlist,
-                       int32_t* __restrict__ blist, int32_t* __restrict__ glist, int* __restrict__ counts) {
-  // grid-stride in whole warps so that every lane reaches the ballots below; one
-  // atomic per warp and class reserves the warp's positions
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-    const int64_t v = base + lane;
-    const int64_t d = v < n ? off[v + 1] - off[v] : 0;
-    const int cls = d <= kWarpMaxDeg ? -1 : d <= kMidMaxDeg ? 0 : d <= kBlockMaxDeg ? 1 : 2;
-    int32_t* lists[3] = {mlist, blist, glist};
+// Binning in vertex order: each block takes a contiguous chunk, counts its classes
+// (one global atomic per class and block reserves its positions), then writes the
+// chunk's ids in order.
+constexpr int kBinClasses = 5;  // small, reg, mid, block, global
+__device__ __forceinline__ int bin_class(int64_t d) {
+  return d <= 64 ? 0 : d <= kWarpMaxDeg ? 1 : d <= kMidMaxDeg ? 2 : d <= kBlockMaxDeg ? 3 : 4;
+}
+struct BinOut {
+  int32_t* list[kBinClasses];
+  int slot[kBinClasses];  // index of the class's count in Bins::counts
+};
+
+__global__ void __launch_bounds__(256) bins_k(int64_t n, int64_t chunk, const int64_t* __restrict__ off, BinOut out,
+                                              int* __restrict__ counts) {
+  __shared__ int s_cnt[kBinClasses], s_base[kBinClasses], s_run[kBinClasses], s_max;
+  __shared__ int s_warp[8][kBinClasses];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t lo = (int64_t)blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+  if (tid < kBinClasses) { s_cnt[tid] = 0; s_run[tid] = 0; s_base[tid] = 0; }
+  if (tid == 0) s_max = 0;
+  __syncthreads();
+  int c[kBinClasses] = {0, 0, 0, 0, 0};
+  int dmax = 0;
+  for (int64_t v = lo + tid; v < hi; v += 256) {
+    const int64_t d = off[v + 1] - off[v];
+    const int k = bin_class(d);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const unsigned m = __ballot_sync(0xffffffffu, cls == c);
-      if (!m) continue;
-      int at = 0;
-      if (lane == __ffs(m) - 1) at = atomicAdd(&counts[c], __popc(m));
-      at = __shfl_sync(0xffffffffu, at, __ffs(m) - 1);
-      if (cls == c) lists[c][at + __popc(m & ((1u << lane) - 1u))] = (int32_t)v;
+    for (int q = 0; q < kBinClasses; ++q) c[q] += k == q;
+    if (k >= 2) dmax = max(dmax, (int)(d < INT_MAX ? d : INT_MAX));
+  }
+#pragma unroll
+  for (int q = 0; q < kBinClasses; ++q) {
+    const unsigned x = __reduce_add_sync(0xffffffffu, (unsigned)c[q]);
+    if (lane == 0 && x) atomicAdd(&s_cnt[q], (int)x);
+  }
+  const unsigned m = __reduce_max_sync(0xffffffffu, (unsigned)dmax);
+  if (lane == 0 && m) atomicMax(&s_max, (int)m);
+  __syncthreads();
+  if (tid < kBinClasses && s_cnt[tid]) s_base[tid] = atomicAdd(&counts[out.slot[tid]], s_cnt[tid]);
+  if (tid == 0 && s_max) atomicMax(&counts[3], s_max);
+  __syncthreads();
+  for (int64_t b0 = lo; b0 < hi; b0 += 256) {  // the same trip count in every thread
+    const int64_t v = b0 + tid;
+    const int k = v < hi ? bin_class(off[v + 1] - off[v]) : -1;
+    unsigned mine = 0;
+#pragma unroll
+    for (int q = 0; q < kBinClasses; ++q) {
+      const unsigned bq = __ballot_sync(0xffffffffu, k == q);
+      if (k == q) mine = bq;
+      if (lane == 0) s_warp[wid][q] = __popc(bq);
     }
-    const int dm = (int)(d < INT_MAX ? d : INT_MAX);
-    const int wmax = __reduce_max_sync(0xffffffffu, cls >= 0 ? (unsigned)dm : 0u);
-    if (lane == 0 && wmax > kWarpMaxDeg) atomicMax(&counts[3], wmax);
+    __syncthreads();
+    if (k >= 0) {
+      int pos = s_base[k] + s_run[k] + __popc(mine & ((1u << lane) - 1u));
+      for (int w2 = 0; w2 < wid; ++w2) pos += s_warp[w2][k];
+      out.list[k][pos] = (int32_t)v;
+    }
+    __syncthreads();
+    if (tid < kBinClasses) {
+      int t = 0;
+      for (int w2 = 0; w2 < 8; ++w2) t += s_warp[w2][tid];
+      s_run[tid] += t;
+    }
+    __syncthreads();
   }
 }
 
 void bins_build(const GraphView& g, Bins& b, cudaStream_t s) {
-  VC_CUDA(cudaMemsetAsync(b.counts, 0, 4 * sizeof(int), s));
-  bins_k<<<grid_for(g.n, 256, kSMs * 8), 256, 0, s>>>(g.n, g.off, b.mid_list, b.block_list, b.global_list,
-                                                       b.counts);
+  VC_CUDA(cudaMemsetAsync(b.counts, 0, 6 * sizeof(int), s));
+  if (g.n <= 0) return;
+  const int64_t blocks = std::min<int64_t>((g.n + 255) / 256, (int64_t)kSMs * 8);
+  const int64_t chunk = (g.n + blocks - 1) / blocks;
+  BinOut out{{b.small_list, b.reg_list, b.mid_list, b.block_list, b.global_list}, {4, 5, 0, 1, 2}};
+  bins_k<<<(int)blocks, 256, 0, s>>>(g.n, chunk, g.off, out, b.counts);
   count_launch();
   VC_CHECK_LAUNCH();
 }
@@ -268,18 +313,17 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
   return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
 }
 
-// Neighbour ids (and weights) of one list in registers; lists outside (lo, 4G] load
-// nothing (another launch takes them).
+// Neighbour ids (and weights) of one list in registers.
 struct RegIds {
   int32_t u[kRegSlots];
   long long wt[kRegSlots];
 };
 
 template <typename WT, int G>
-__device__ __forceinline__ void reg_ids(RegIds& R, int64_t beg, int64_t end, int lo, int glane,
+__device__ __forceinline__ void reg_ids(RegIds& R, int64_t beg, int64_t end, int glane,
                                         const int32_t* __restrict__ adj, const WT* __restrict__ w) {
   const int64_t dd = end - beg;
-  const int d = (dd > 4 * G || dd <= lo) ? 0 : (int)dd;
+  const int d = dd > 4 * G ? 0 : (int)dd;
   const int32_t* a = adj + beg;
 #pragma unroll
   for (int r = 0; r < kRegSlots; ++r) {
@@ -353,48 +397,57 @@ __device__ __forceinline__ void reg_visit(RegList& L, unsigned gmask, F visit) {
   }
 }
 
-// The pipelined vertex loop of a warp.  Group g of the warp takes vertex
-// base + g for base = first, first + stride, ... (the trip count is the same for all
-// lanes); body(v, valid, beg, end, pre, ids) runs with v's ids already in registers.
-// `pre(v)` is read with the offsets one vertex ahead (e.g. v's own cluster id).
+// The pipelined vertex loop of a warp over a vertex list.  Group g of the warp takes
+// list entry i + g for i = first, first + stride, ... < total (the trip count is the
+// same in every lane); body(v, valid, beg, end, pre, ids) runs with v's ids already
+// in registers.  `pre(v)` is read with the offsets one entry ahead (e.g. v's own
+// cluster id).
 template <typename WT, int G, typename PRE, typename BODY>
-__device__ __forceinline__ void reg_pipeline(int64_t n, int lo, int64_t first, int64_t stride, int glane, int gi,
-                                             const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
-                                             const WT* __restrict__ w, PRE pre, BODY body) {
+__device__ __forceinline__ void reg_pipeline(const int32_t* __restrict__ list, int64_t total, int64_t first,
+                                             int64_t stride, int glane, int gi, const int64_t* __restrict__ off,
+                                             const int32_t* __restrict__ adj, const WT* __restrict__ w, PRE pre,
+                                             BODY body) {
   int64_t base = first;
-  if (base >= n) return;  // the same in every lane (base is per warp)
-  auto fetch = [&](int64_t b, int64_t& bg, int64_t& en, int32_t& x) {
-    const int64_t v = b + gi;
+  if (base >= total) return;  // the same in every lane (base is per warp)
+  auto fetch = [&](int64_t b, int64_t& v, int64_t& bg, int64_t& en, int32_t& x) {
+    v = -1;
     bg = en = 0;
     x = 0;
-    if (v < n) { bg = __ldg(off + v); en = __ldg(off + v + 1); x = pre(v); }
+    if (b + gi < total) {
+      v = __ldg(list + b + gi);
+      bg = __ldg(off + v);
+      en = __ldg(off + v + 1);
+      x = pre(v);
+    }
   };
-  int64_t beg, end, nbeg, nend;
+  int64_t v, beg, end, vn, nbeg, nend;
   int32_t x, xn;
-  fetch(base, beg, end, x);
+  fetch(base, v, beg, end, x);
   RegIds cur;
-  reg_ids<WT, G>(cur, beg, end, lo, glane, adj, w);
+  reg_ids<WT, G>(cur, beg, end, glane, adj, w);
   int64_t bn = base + stride;
-  fetch(bn, nbeg, nend, xn);
+  fetch(bn, vn, nbeg, nend, xn);
   for (;;) {
     RegIds nxt;
-    int64_t nnbeg = 0, nnend = 0;
+    int64_t vnn = -1, nnbeg = 0, nnend = 0;
     int32_t xnn = 0;
     const int64_t bnn = bn + stride;
-    if (bn < n) {
-      reg_ids<WT, G>(nxt, nbeg, nend, lo, glane, adj, w);
-      fetch(bnn, nnbeg, nnend, xnn);
+    if (bn < total) {
+      reg_ids<WT, G>(nxt, nbeg, nend, glane, adj, w);
+      fetch(bnn, vnn, nnbeg, nnend, xnn);
     }
-    body(base + gi, base + gi < n, beg, end, x, cur);
-    if (bn >= n) break;
-    base = bn; beg = nbeg; end = nend; x = xn; cur = nxt;
-    bn = bnn; nbeg = nnbeg; nend = nnend; xn = xnn;
+    body(v, v >= 0, beg, end, x, cur);
+    if (bn >= total) break;
+    base = bn; v = vn; beg = nbeg; end = nend; x = xn; cur = nxt;
+    bn = bnn; vn = vnn; nbeg = nnbeg; nend = nnend; xn = xnn;
   }
 }
 
-// Vertices with lo < deg <= 4G; the launch with lo < 0 also writes the empty lists.
+// The listed vertices (all of length <= 4G), G lanes each.
 template <typename WT, typename ACC, bool FIRST, int G>
-__global__ void __launch_bounds__(kAggThreads) lp_reg_k(int64_t n, int lo, const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restrict__ list,
+                                                        const int* __restrict__ count_ptr,
+                                                        const int64_t* __restrict__ off,
                                                         const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                         const int32_t* __restrict__ lab, int32_t* __restrict__ lab_out,
                                                         const unsigned long long* __restrict__ hv,
@@ -404,11 +457,11 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(int64_t n, int lo, const
   constexpr int kPer = 32 / G;  // vertices per warp
   const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock * kPer;
   const int64_t first = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kPer;
-  reg_pipeline<WT, G>(n, lo, first, stride, glane, gi, off, adj, w,
+  reg_pipeline<WT, G>(list, *count_ptr, first, stride, glane, gi, off, adj, w,
                       [&](int64_t v) { return vact ? (int32_t)vact[v] : 1; },
                       [&](int64_t v, bool valid, int64_t beg, int64_t end, int32_t active, const RegIds& ids) {
     const int64_t d = end - beg;
-    const bool mine = valid && active && d > lo && d <= 4 * G;
+    const bool mine = valid && active;
     if (mine && d == 0) {
       if (glane == 0) lab_out[v] = FIRST ? (int32_t)v : __ldg(lab + v);
     }
@@ -440,7 +493,9 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(int64_t n, int lo, const
 // whole list; group lane i keeps the i-th pair of each run of G pairs, and a full run
 // is written with one coalesced store.
 template <typename WT, int G>
-__global__ void __launch_bounds__(kAggThreads) emit_reg_k(int64_t n, int lo, const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restrict__ list,
+                                                          const int* __restrict__ count_ptr,
+                                                          const int64_t* __restrict__ off,
                                                           const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                           const int32_t* __restrict__ cid,
                                                           int32_t* __restrict__ tkey, long long* __restrict__ tval,
@@ -450,10 +505,11 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(int64_t n, int lo, con
   constexpr int kPer = 32 / G;
   const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock * kPer;
   const int64_t first = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kPer;
-  reg_pipeline<WT, G>(n, lo, first, stride, glane, gi, off, adj, w, [&](int64_t v) { return __ldg(cid + v); },
+  reg_pipeline<WT, G>(list, *count_ptr, first, stride, glane, gi, off, adj, w,
+                      [&](int64_t v) { return __ldg(cid + v); },
                       [&](int64_t v, bool valid, int64_t beg, int64_t end, int32_t own, const RegIds& ids) {
     const int64_t d = end - beg;
-    const bool mine = valid && d > lo && d <= 4 * G;
+    const bool mine = valid;
     RegList L;
     reg_keys<kModeEmit, false, G>(L, ids, (mine && own >= 0) ? (int)d : 0, cid, own);
     if (!(mine && own >= 0)) L.todo = 0;
@@ -476,25 +532,37 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(int64_t n, int lo, con
 }
 
 template <typename WT, typename ACC, bool FIRST>
-void launch_lp_reg(const GraphView& g, const WT* w, const int32_t* lab, int32_t* lab_out,
+void launch_lp_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t* lab, int32_t* lab_out,
                    const unsigned long long* hv, cudaStream_t s) {
-  lp_reg_k<WT, ACC, FIRST, 16><<<grid_for(g.n, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
-      g.n, -1, g.off, g.adj, w, lab, lab_out, hv, g.vact);
-  lp_reg_k<WT, ACC, FIRST, 32><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
-      g.n, 64, g.off, g.adj, w, lab, lab_out, hv, g.vact);
-  count_launch(2);
-  VC_CHECK_LAUNCH();
+  if (b.h_small > 0) {
+    lp_reg_k<WT, ACC, FIRST, 16><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
+        b.small_list, b.counts + 4, g.off, g.adj, w, lab, lab_out, hv, g.vact);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
+  if (b.h_reg > 0) {
+    lp_reg_k<WT, ACC, FIRST, 32><<<grid_for(b.h_reg, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
+        b.reg_list, b.counts + 5, g.off, g.adj, w, lab, lab_out, hv, g.vact);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
 }
 
 template <typename WT>
-void launch_emit_reg(const GraphView& g, const WT* w, const int32_t* cid, int32_t* tkey, long long* tval,
-                     int32_t* cnt, cudaStream_t s) {
-  emit_reg_k<WT, 16><<<grid_for(g.n, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(g.n, -1, g.off, g.adj, w,
-                                                                                          cid, tkey, tval, cnt);
-  emit_reg_k<WT, 32><<<grid_for(g.n, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(g.n, 64, g.off, g.adj, w, cid,
-                                                                                      tkey, tval, cnt);
-  count_launch(2);
-  VC_CHECK_LAUNCH();
+void launch_emit_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t* cid, int32_t* tkey,
+                     long long* tval, int32_t* cnt, cudaStream_t s) {
+  if (b.h_small > 0) {
+    emit_reg_k<WT, 16><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
+        b.small_list, b.counts + 4, g.off, g.adj, w, cid, tkey, tval, cnt);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
+  if (b.h_reg > 0) {
+    emit_reg_k<WT, 32><<<grid_for(b.h_reg, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
+        b.reg_list, b.counts + 5, g.off, g.adj, w, cid, tkey, tval, cnt);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
 }
 
 // First round on a graph whose lists are strictly increasing: every neighbour is its
@@ -650,19 +718,22 @@ __device__ __forceinline__ void emit_chunk(int64_t e, int64_t end, const int32_t
   }
 }
 
-// G lanes per vertex: 32 / G vertices per warp, each group walking its list in
-// G-entry chunks (a short list leaves fewer lanes idle with a smaller G).
+// Listed vertices (the mid and block classes), G lanes per vertex: 32 / G vertices
+// per warp, each group walking its list in G-entry chunks.
 template <typename WT, int G>
-__global__ void __launch_bounds__(kAggThreads) emit_warp_k(int64_t n, int mind, int maxd, const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(kAggThreads) emit_warp_k(const int32_t* __restrict__ list,
+                                                           const int* __restrict__ count_ptr,
+                                                           const int64_t* __restrict__ off,
                                                            const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                            const int32_t* __restrict__ cid, int32_t* __restrict__ tkey,
                                                            long long* __restrict__ tval, int32_t* __restrict__ cnt) {
   const int lane = threadIdx.x & 31, glane = lane & (G - 1);
   const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
+  const int64_t total = *count_ptr;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; i < total; i += groups) {
+    const int32_t v = __ldg(list + i);
     const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
-    if (end - beg > maxd || end - beg <= mind) continue;
     const int32_t own = __ldg(cid + v);
     int made = 0;  // group-uniform
     if (own >= 0)
@@ -806,7 +877,7 @@ void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const 
     }
     return;
   }
-  launch_lp_reg<WT, ACC, FIRST>(g, w, lab, lab_out, key, s);
+  launch_lp_reg<WT, ACC, FIRST>(g, b, w, lab, lab_out, key, s);
   if (b.h_mid > 0) {
     constexpr int CAP = kMidCap;
     const size_t smem = warp_smem<CAP, ACC>();
@@ -840,16 +911,19 @@ template <typename WT>
 void launch_emit(const GraphView& g, const Bins& b, const int32_t* cid, int32_t* tkey, long long* tval,
                  int32_t* cnt, int G, cudaStream_t s) {
   const WT* w = (const WT*)g.w;
-  launch_emit_reg<WT>(g, w, cid, tkey, tval, cnt, s);
-  if (b.h_mid + b.h_block > 0) {
-    const int grid = grid_for(g.n, kAggThreads / G, kSMs * 16);
-    const int lo = kWarpMaxDeg, hi = kBlockMaxDeg;
+  launch_emit_reg<WT>(g, b, w, cid, tkey, tval, cnt, s);
+  const int32_t* lists[2] = {b.mid_list, b.block_list};
+  const int hcount[2] = {b.h_mid, b.h_block};
+  for (int c = 0; c < 2; ++c) {
+    if (hcount[c] == 0) continue;
+    const int grid = grid_for(hcount[c], kAggThreads / G, kSMs * 16);
+    const int* cp = b.counts + c;  // [0] mid, [1] block
     if (G == 8)
-      emit_warp_k<WT, 8><<<grid, kAggThreads, 0, s>>>(g.n, lo, hi, g.off, g.adj, w, cid, tkey, tval, cnt);
+      emit_warp_k<WT, 8><<<grid, kAggThreads, 0, s>>>(lists[c], cp, g.off, g.adj, w, cid, tkey, tval, cnt);
     else if (G == 16)
-      emit_warp_k<WT, 16><<<grid, kAggThreads, 0, s>>>(g.n, lo, hi, g.off, g.adj, w, cid, tkey, tval, cnt);
+      emit_warp_k<WT, 16><<<grid, kAggThreads, 0, s>>>(lists[c], cp, g.off, g.adj, w, cid, tkey, tval, cnt);
     else
-      emit_warp_k<WT, 32><<<grid, kAggThreads, 0, s>>>(g.n, lo, hi, g.off, g.adj, w, cid, tkey, tval, cnt);
+      emit_warp_k<WT, 32><<<grid, kAggThreads, 0, s>>>(lists[c], cp, g.off, g.adj, w, cid, tkey, tval, cnt);
     count_launch();
     VC_CHECK_LAUNCH();
   }
