@@ -226,7 +226,7 @@ struct Workspace {
     });
   }
   void tune_emit(const GraphView& g, const int32_t* cid, int32_t* k, long long* v, int32_t* c) {
-    if (tuned_emit || g.n < kTuneMinN || bins.h_mid + bins.h_block == 0) return;
+    if (tuned_emit || g.n < kTuneMinN || bins.h_block == 0) return;
     tuned_emit = true;
     tune.emit_group = pick_group([&](int G) {
       LpTuning t = tune;

@@ -306,7 +306,6 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
 // A vertex needs three dependent reads (its offsets, its neighbour ids, their keys),
 // so the warp software-pipelines its vertices: while it works on one vertex per
 // group it already holds the next vertex's ids and the offsets of the one after.
-constexpr int kRegSlots = 4;
 
 template <int G>
 __device__ __forceinline__ unsigned group_mask(int lane) {
@@ -314,19 +313,20 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
 }
 
 // Neighbour ids (and weights) of one list in registers.
+template <int S>
 struct RegIds {
-  int32_t u[kRegSlots];
-  long long wt[kRegSlots];
+  int32_t u[S];
+  long long wt[S];
 };
 
-template <typename WT, int G>
-__device__ __forceinline__ void reg_ids(RegIds& R, int64_t beg, int64_t end, int glane,
+template <typename WT, int G, int S>
+__device__ __forceinline__ void reg_ids(RegIds<S>& R, int64_t beg, int64_t end, int glane,
                                         const int32_t* __restrict__ adj, const WT* __restrict__ w) {
   const int64_t dd = end - beg;
-  const int d = dd > 4 * G ? 0 : (int)dd;
+  const int d = dd > S * G ? 0 : (int)dd;
   const int32_t* a = adj + beg;
 #pragma unroll
-  for (int r = 0; r < kRegSlots; ++r) {
+  for (int r = 0; r < S; ++r) {
     const int i = glane + G * r;
     R.u[r] = -1;
     R.wt[r] = 0;
@@ -337,20 +337,21 @@ __device__ __forceinline__ void reg_ids(RegIds& R, int64_t beg, int64_t end, int
   }
 }
 
+template <int S>
 struct RegList {
-  int32_t k[kRegSlots];
-  long long wt[kRegSlots];
+  int32_t k[S];
+  long long wt[S];
   unsigned todo;  // bit r: slot r holds a used entry not yet visited
   int slots;      // slots in use: ceil(deg / G), the same in every lane of the group
 };
 
-template <int MODE, bool FIRST, int G>
-__device__ __forceinline__ void reg_keys(RegList& L, const RegIds& R, int deg, const int32_t* __restrict__ lab,
+template <int MODE, bool FIRST, int G, int S>
+__device__ __forceinline__ void reg_keys(RegList<S>& L, const RegIds<S>& R, int deg, const int32_t* __restrict__ lab,
                                          int32_t own) {
   L.slots = (deg + G - 1) / G;
   L.todo = 0;
 #pragma unroll
-  for (int r = 0; r < kRegSlots; ++r) {
+  for (int r = 0; r < S; ++r) {
     L.k[r] = -1;
     L.wt[r] = R.wt[r];
     if (R.u[r] >= 0) {
@@ -364,10 +365,10 @@ __device__ __forceinline__ void reg_keys(RegList& L, const RegIds& R, int deg, c
 // Calls visit(key, total) once per distinct used key of the group's list, in
 // slot-then-lane order of first occurrence; total is the same in the group's lanes.
 // Every lane of the warp must call it (groups without a list pass slots = todo = 0).
-template <typename WT, typename ACC, int G, typename F>
-__device__ __forceinline__ void reg_visit(RegList& L, unsigned gmask, F visit) {
+template <typename WT, typename ACC, int G, int S, typename F>
+__device__ __forceinline__ void reg_visit(RegList<S>& L, unsigned gmask, F visit) {
 #pragma unroll
-  for (int r = 0; r < kRegSlots; ++r) {
+  for (int r = 0; r < S; ++r) {
     if (!__any_sync(0xffffffffu, r < L.slots)) break;
     for (;;) {
       const unsigned bal = __ballot_sync(0xffffffffu, (L.todo >> r) & 1u);
@@ -376,7 +377,7 @@ __device__ __forceinline__ void reg_visit(RegList& L, unsigned gmask, F visit) {
       const int32_t kk = __shfl_sync(0xffffffffu, L.k[r], gb ? __ffs(gb) - 1 : 0);
       unsigned hit = 0;
 #pragma unroll
-      for (int q = r; q < kRegSlots; ++q)
+      for (int q = r; q < S; ++q)
         if (L.k[q] == kk) hit |= 1u << q;
       hit = gb ? hit & L.todo : 0u;
       L.todo &= ~hit;
@@ -386,7 +387,7 @@ __device__ __forceinline__ void reg_visit(RegList& L, unsigned gmask, F visit) {
       } else {
         long long sum = 0;
 #pragma unroll
-        for (int q = r; q < kRegSlots; ++q)
+        for (int q = r; q < S; ++q)
           if (hit >> q & 1u) sum += L.wt[q];
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -402,7 +403,7 @@ __device__ __forceinline__ void reg_visit(RegList& L, unsigned gmask, F visit) {
 // same in every lane); body(v, valid, beg, end, pre, ids) runs with v's ids already
 // in registers.  `pre(v)` is read with the offsets one entry ahead (e.g. v's own
 // cluster id).
-template <typename WT, int G, typename PRE, typename BODY>
+template <typename WT, int G, int S, typename PRE, typename BODY>
 __device__ __forceinline__ void reg_pipeline(const int32_t* __restrict__ list, int64_t total, int64_t first,
                                              int64_t stride, int glane, int gi, const int64_t* __restrict__ off,
                                              const int32_t* __restrict__ adj, const WT* __restrict__ w, PRE pre,
@@ -423,17 +424,17 @@ __device__ __forceinline__ void reg_pipeline(const int32_t* __restrict__ list, i
   int64_t v, beg, end, vn, nbeg, nend;
   int32_t x, xn;
   fetch(base, v, beg, end, x);
-  RegIds cur;
-  reg_ids<WT, G>(cur, beg, end, glane, adj, w);
+  RegIds<S> cur;
+  reg_ids<WT, G, S>(cur, beg, end, glane, adj, w);
   int64_t bn = base + stride;
   fetch(bn, vn, nbeg, nend, xn);
   for (;;) {
-    RegIds nxt;
+    RegIds<S> nxt;
     int64_t vnn = -1, nnbeg = 0, nnend = 0;
     int32_t xnn = 0;
     const int64_t bnn = bn + stride;
     if (bn < total) {
-      reg_ids<WT, G>(nxt, nbeg, nend, glane, adj, w);
+      reg_ids<WT, G, S>(nxt, nbeg, nend, glane, adj, w);
       fetch(bnn, vnn, nnbeg, nnend, xnn);
     }
     body(v, v >= 0, beg, end, x, cur);
@@ -443,8 +444,8 @@ __device__ __forceinline__ void reg_pipeline(const int32_t* __restrict__ list, i
   }
 }
 
-// The listed vertices (all of length <= 4G), G lanes each.
-template <typename WT, typename ACC, bool FIRST, int G>
+// The listed vertices (all of length <= S G), G lanes each, S slots per lane.
+template <typename WT, typename ACC, bool FIRST, int G, int S>
 __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restrict__ list,
                                                         const int* __restrict__ count_ptr,
                                                         const int64_t* __restrict__ off,
@@ -457,16 +458,16 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
   constexpr int kPer = 32 / G;  // vertices per warp
   const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock * kPer;
   const int64_t first = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kPer;
-  reg_pipeline<WT, G>(list, *count_ptr, first, stride, glane, gi, off, adj, w,
+  reg_pipeline<WT, G, S>(list, *count_ptr, first, stride, glane, gi, off, adj, w,
                       [&](int64_t v) { return vact ? (int32_t)vact[v] : 1; },
-                      [&](int64_t v, bool valid, int64_t beg, int64_t end, int32_t active, const RegIds& ids) {
+                      [&](int64_t v, bool valid, int64_t beg, int64_t end, int32_t active, const RegIds<S>& ids) {
     const int64_t d = end - beg;
     const bool mine = valid && active;
     if (mine && d == 0) {
       if (glane == 0) lab_out[v] = FIRST ? (int32_t)v : __ldg(lab + v);
     }
-    RegList L;
-    reg_keys<kModeLP, FIRST, G>(L, ids, mine ? (int)d : 0, lab, 0);
+    RegList<S> L;
+    reg_keys<kModeLP, FIRST, G, S>(L, ids, mine ? (int)d : 0, lab, 0);
     if (!mine) L.todo = 0;
     // running best (sum, hash, -label), the same in the group's lanes; the hash of
     // the best is read only once a tie needs it
@@ -474,7 +475,7 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
     int32_t bl = -1;
     unsigned long long bh = 0;
     bool hashed = false;
-    reg_visit<WT, ACC, G>(L, gmask, [&](int32_t kk, ACC t) {
+    reg_visit<WT, ACC, G, S>(L, gmask, [&](int32_t kk, ACC t) {
       if (bl < 0 || t > bs) {
         bs = t;
         bl = kk;
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
 // Pre-merge of the register class: one (key, sum) per distinct foreign cluster of the
 // whole list; group lane i keeps the i-th pair of each run of G pairs, and a full run
 // is written with one coalesced store.
-template <typename WT, int G>
+template <typename WT, int G, int S>
 __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restrict__ list,
                                                           const int* __restrict__ count_ptr,
                                                           const int64_t* __restrict__ off,
@@ -505,18 +506,18 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restr
   constexpr int kPer = 32 / G;
   const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock * kPer;
   const int64_t first = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kPer;
-  reg_pipeline<WT, G>(list, *count_ptr, first, stride, glane, gi, off, adj, w,
+  reg_pipeline<WT, G, S>(list, *count_ptr, first, stride, glane, gi, off, adj, w,
                       [&](int64_t v) { return __ldg(cid + v); },
-                      [&](int64_t v, bool valid, int64_t beg, int64_t end, int32_t own, const RegIds& ids) {
+                      [&](int64_t v, bool valid, int64_t beg, int64_t end, int32_t own, const RegIds<S>& ids) {
     const int64_t d = end - beg;
     const bool mine = valid;
-    RegList L;
-    reg_keys<kModeEmit, false, G>(L, ids, (mine && own >= 0) ? (int)d : 0, cid, own);
+    RegList<S> L;
+    reg_keys<kModeEmit, false, G, S>(L, ids, (mine && own >= 0) ? (int)d : 0, cid, own);
     if (!(mine && own >= 0)) L.todo = 0;
     int made = 0;  // the same in the group's lanes
     int32_t pk = 0;
     long long pv = 0;
-    reg_visit<WT, long long, G>(L, gmask, [&](int32_t kk, long long t) {
+    reg_visit<WT, long long, G, S>(L, gmask, [&](int32_t kk, long long t) {
       if (glane == (made & (G - 1))) { pk = kk; pv = t; }
       if ((++made & (G - 1)) == 0) {
         tkey[beg + made - G + glane] = pk;
@@ -535,14 +536,20 @@ template <typename WT, typename ACC, bool FIRST>
 void launch_lp_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t* lab, int32_t* lab_out,
                    const unsigned long long* hv, cudaStream_t s) {
   if (b.h_small > 0) {
-    lp_reg_k<WT, ACC, FIRST, 16><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
+    lp_reg_k<WT, ACC, FIRST, 16, 4><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
         b.small_list, b.counts + 4, g.off, g.adj, w, lab, lab_out, hv, g.vact);
     count_launch();
     VC_CHECK_LAUNCH();
   }
   if (b.h_reg > 0) {
-    lp_reg_k<WT, ACC, FIRST, 32><<<grid_for(b.h_reg, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
+    lp_reg_k<WT, ACC, FIRST, 32, 4><<<grid_for(b.h_reg, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
         b.reg_list, b.counts + 5, g.off, g.adj, w, lab, lab_out, hv, g.vact);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
+  if (b.h_mid > 0) {
+    lp_reg_k<WT, ACC, FIRST, 32, kMidMaxDeg / 32><<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
+        b.mid_list, b.counts + 0, g.off, g.adj, w, lab, lab_out, hv, g.vact);
     count_launch();
     VC_CHECK_LAUNCH();
   }
@@ -552,14 +559,20 @@ template <typename WT>
 void launch_emit_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t* cid, int32_t* tkey,
                      long long* tval, int32_t* cnt, cudaStream_t s) {
   if (b.h_small > 0) {
-    emit_reg_k<WT, 16><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
+    emit_reg_k<WT, 16, 4><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
         b.small_list, b.counts + 4, g.off, g.adj, w, cid, tkey, tval, cnt);
     count_launch();
     VC_CHECK_LAUNCH();
   }
   if (b.h_reg > 0) {
-    emit_reg_k<WT, 32><<<grid_for(b.h_reg, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
+    emit_reg_k<WT, 32, 4><<<grid_for(b.h_reg, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
         b.reg_list, b.counts + 5, g.off, g.adj, w, cid, tkey, tval, cnt);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
+  if (b.h_mid > 0) {
+    emit_reg_k<WT, 32, kMidMaxDeg / 32><<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
+        b.mid_list, b.counts + 0, g.off, g.adj, w, cid, tkey, tval, cnt);
     count_launch();
     VC_CHECK_LAUNCH();
   }
@@ -878,16 +891,6 @@ void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const 
     return;
   }
   launch_lp_reg<WT, ACC, FIRST>(g, b, w, lab, lab_out, key, s);
-  if (b.h_mid > 0) {
-    constexpr int CAP = kMidCap;
-    const size_t smem = warp_smem<CAP, ACC>();
-    auto kfn = lp_warp_k<WT, ACC, FIRST, CAP, true>;
-    set_smem(kfn, smem);
-    kfn<<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 2), kAggThreads, smem, s>>>(0, b.mid_list, b.counts + 0, g.off,
-                                                                              g.adj, w, lab, lab_out, key, g.vact);
-    count_launch();
-    VC_CHECK_LAUNCH();
-  }
   if (b.h_block > 0) {
     const size_t smem = (size_t)kBlockCap * (sizeof(ACC) + sizeof(int));
     auto kfn = lp_block_k<WT, ACC, FIRST, false>;
@@ -912,18 +915,15 @@ void launch_emit(const GraphView& g, const Bins& b, const int32_t* cid, int32_t*
                  int32_t* cnt, int G, cudaStream_t s) {
   const WT* w = (const WT*)g.w;
   launch_emit_reg<WT>(g, b, w, cid, tkey, tval, cnt, s);
-  const int32_t* lists[2] = {b.mid_list, b.block_list};
-  const int hcount[2] = {b.h_mid, b.h_block};
-  for (int c = 0; c < 2; ++c) {
-    if (hcount[c] == 0) continue;
-    const int grid = grid_for(hcount[c], kAggThreads / G, kSMs * 16);
-    const int* cp = b.counts + c;  // [0] mid, [1] block
+  if (b.h_block > 0) {  // 513..4096 entries: G lanes per vertex, in G-entry chunks
+    const int grid = grid_for(b.h_block, kAggThreads / G, kSMs * 16);
+    const int* cp = b.counts + 1;
     if (G == 8)
-      emit_warp_k<WT, 8><<<grid, kAggThreads, 0, s>>>(lists[c], cp, g.off, g.adj, w, cid, tkey, tval, cnt);
+      emit_warp_k<WT, 8><<<grid, kAggThreads, 0, s>>>(b.block_list, cp, g.off, g.adj, w, cid, tkey, tval, cnt);
     else if (G == 16)
-      emit_warp_k<WT, 16><<<grid, kAggThreads, 0, s>>>(lists[c], cp, g.off, g.adj, w, cid, tkey, tval, cnt);
+      emit_warp_k<WT, 16><<<grid, kAggThreads, 0, s>>>(b.block_list, cp, g.off, g.adj, w, cid, tkey, tval, cnt);
     else
-      emit_warp_k<WT, 32><<<grid, kAggThreads, 0, s>>>(lists[c], cp, g.off, g.adj, w, cid, tkey, tval, cnt);
+      emit_warp_k<WT, 32><<<grid, kAggThreads, 0, s>>>(b.block_list, cp, g.off, g.adj, w, cid, tkey, tval, cnt);
     count_launch();
     VC_CHECK_LAUNCH();
   }
