@@ -2,9 +2,16 @@
 // every block of a labelling becomes one vertex, intra-block edges vanish and
 // parallel edges between two blocks merge with summed weight.  Block ids are the
 // ranks of the label values.  Steps: relabel (flag + scan), pre-merge per fine
-// vertex (lp.cu), pair build, LSD radix sort on (cid v, cid u), run reduction.
+// vertex (lp.cu), then either
+//   * the cluster merge: a counting sort of the pre-merged pairs by source cluster
+//     and a warp per cluster that merges its pairs in registers and writes the
+//     distinct targets in ascending order (every cluster holding <= kMergeMax pairs), or
+//   * pair build, LSD radix sort on (cid v, cid u) and a run reduction (otherwise).
+#include <algorithm>
+
 #include "kernels.cuh"
 #include "prims.cuh"
+#include "regvisit.cuh"
 
 namespace vc {
 
@@ -118,6 +125,174 @@ void reduce_pairs(const unsigned long long* keys, const long long* vals, int64_t
   build_offsets_k<<<grid_for(pairs + c + 1, 256, kSMs * 8), 256, 0, s>>>(cv_tmp, nnz_dev, c, (int64_t*)coff);
   count_launch();
   VC_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------- cluster merge
+// Warp-level grouping of the lanes whose vertices share a cluster (consecutive
+// vertices often do), so that one atomic per group and warp moves its counter.
+// Returns the sum of k over the lane's group and the sum over the group's lower
+// lanes; sk is the warp's 32-entry scratch.
+__device__ __forceinline__ void group_sums(int32_t c, int k, int lane, int* sk, unsigned* peers_out, int* total,
+                                           int* below) {
+  const unsigned peers = __match_any_sync(0xffffffffu, c);
+  sk[lane] = k;
+  __syncwarp();
+  int t = 0, b = 0;
+  for (unsigned m = peers; m; m &= m - 1) {
+    const int j = __ffs(m) - 1;
+    t += sk[j];
+    if (j < lane) b += sk[j];
+  }
+  __syncwarp();
+  *peers_out = peers;
+  *total = t;
+  *below = b;
+}
+
+// Pairs per source cluster; *maxt = the largest count, *pairs = their total.
+__global__ void __launch_bounds__(256) cluster_count_k(int64_t n, const int32_t* __restrict__ cid,
+                                                       const int32_t* __restrict__ cnt, int32_t* __restrict__ ccount,
+                                                       int* maxt, long long* pairs) {
+  __shared__ int s_k[8][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  long long mine = 0;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t v = base + lane;
+    const int k = v < n ? cnt[v] : 0;
+    const int32_t c = k > 0 ? cid[v] : -1;
+    unsigned peers;
+    int t, b;
+    group_sums(c, k, lane, s_k[wid], &peers, &t, &b);
+    if (c >= 0 && lane == __ffs(peers) - 1) {
+      const int old = atomicAdd(&ccount[c], t);
+      atomicMax(maxt, old + t);
+    }
+    mine += k;
+  }
+  const long long w = warp_sum(mine);
+  if (lane == 0 && w) atomicAdd((unsigned long long*)pairs, (unsigned long long)w);
+}
+
+// Counting-sort scatter: the pre-merged pairs of fine vertex v move, in one piece,
+// into their cluster's segment (cursor = the segments' running write positions).
+__global__ void __launch_bounds__(256) cluster_scatter_k(int64_t n, const int64_t* __restrict__ off,
+                                                         const int32_t* __restrict__ cid,
+                                                         const int32_t* __restrict__ cnt,
+                                                         const int32_t* __restrict__ tkey,
+                                                         const long long* __restrict__ tval,
+                                                         long long* __restrict__ cursor, int32_t* __restrict__ seg_key,
+                                                         long long* __restrict__ seg_val) {
+  __shared__ int s_k[8][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t v = base + lane;
+    const int k = v < n ? cnt[v] : 0;
+    const int32_t c = k > 0 ? cid[v] : -1;
+    unsigned peers;
+    int t, b;
+    group_sums(c, k, lane, s_k[wid], &peers, &t, &b);
+    const int leader = __ffs(peers) - 1;
+    long long at = 0;
+    if (c >= 0 && lane == leader) at = atomicAdd((unsigned long long*)&cursor[c], (unsigned long long)t);
+    at = __shfl_sync(0xffffffffu, at, leader);
+    if (c >= 0) {
+      const int64_t src = off[v];
+      const long long dst = at + b;
+      for (int j = 0; j < k; ++j) {
+        seg_key[dst + j] = tkey[src + j];
+        seg_val[dst + j] = tval[src + j];
+      }
+    }
+  }
+}
+
+// A warp per cluster: its (at most kMergeMax) pairs into registers, one step per
+// distinct target (summing its weights), the distinct targets written back in place
+// at the front of the segment; dcount[c] = their number.
+__global__ void __launch_bounds__(256) cluster_merge_k(int64_t c, const long long* __restrict__ cbase,
+                                                       int32_t* __restrict__ seg_key, long long* __restrict__ seg_val,
+                                                       int32_t* __restrict__ dcount) {
+  constexpr int S = kMergeMax / 32;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < c; x += warps) {
+    const long long b = cbase[x];
+    const int T = (int)(cbase[x + 1] - b);
+    RegList<S> L;
+    L.slots = (T + 31) >> 5;
+    L.todo = 0;
+#pragma unroll
+    for (int r = 0; r < S; ++r) {
+      const int i = lane + 32 * r;
+      L.k[r] = -1;
+      L.wt[r] = 0;
+      if (i < T) {
+        L.k[r] = seg_key[b + i];
+        L.wt[r] = seg_val[b + i];
+        L.todo |= 1u << r;
+      }
+    }
+    int made = 0;  // warp-uniform
+    reg_visit<long long, long long, 32, S>(L, 0xffffffffu, [&](int32_t key, long long total) {
+      if (lane == 0) {
+        seg_key[b + made] = key;
+        seg_val[b + made] = total;
+      }
+      ++made;
+    });
+    if (lane == 0) dcount[x] = made;
+  }
+}
+
+// A warp per cluster: its distinct targets land at coff[c] + their rank (targets are
+// distinct, so ranks are a permutation), i.e. in ascending order.
+__global__ void __launch_bounds__(256) cluster_place_k(int64_t c, const long long* __restrict__ cbase,
+                                                       const int64_t* __restrict__ coff,
+                                                       const int32_t* __restrict__ seg_key,
+                                                       const long long* __restrict__ seg_val,
+                                                       int32_t* __restrict__ cadj, long long* __restrict__ cw) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < c; x += warps) {
+    const long long b = cbase[x];
+    const int64_t o = coff[x];
+    const int D = (int)(coff[x + 1] - o);
+    for (int i = lane; i < D; i += 32) {
+      const int32_t key = seg_key[b + i];
+      int rank = 0;
+      for (int j = 0; j < D; ++j) rank += seg_key[b + j] < key;
+      cadj[o + rank] = key;
+      cw[o + rank] = seg_val[b + i];
+    }
+  }
+}
+
+void cluster_count(const GraphView& g, const int32_t* cid, const int32_t* cnt, int32_t* ccount, int* maxt,
+                   long long* pairs, cudaStream_t s) {
+  VC_CUDA(cudaMemsetAsync(ccount, 0, sizeof(int32_t) * std::max<int64_t>(g.n, 1), s));
+  if (g.n <= 0) return;
+  cluster_count_k<<<grid_for(g.n, 256, kSMs * 8), 256, 0, s>>>(g.n, cid, cnt, ccount, maxt, pairs);
+  count_launch();
+  VC_CHECK_LAUNCH();
+}
+
+void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int32_t* ccount, int64_t c,
+                   long long* cbase, long long* cursor, int32_t* seg_key, long long* seg_val, int64_t* coff,
+                   int32_t* cadj, long long* cw, long long* nnz_dev, cudaStream_t s) {
+  exclusive_scan<int, long long>(ccount, cbase, c, cbase + c, cs.scan_scr, s);
+  VC_CUDA(cudaMemcpyAsync(cursor, cbase, sizeof(long long) * c, cudaMemcpyDeviceToDevice, s));
+  const int gv = grid_for(g.n, 256, kSMs * 8), gc = grid_for(c, 8, kSMs * 16);
+  cluster_scatter_k<<<gv, 256, 0, s>>>(g.n, g.off, cid, cs.cnt, cs.tmp_key, cs.tmp_val, cursor, seg_key, seg_val);
+  cluster_merge_k<<<gc, 256, 0, s>>>(c, cbase, seg_key, seg_val, ccount);
+  count_launch(2);
+  VC_CHECK_LAUNCH();
+  exclusive_scan<int, long long>(ccount, (long long*)coff, c, (long long*)coff + c, cs.scan_scr, s);
+  cluster_place_k<<<gc, 256, 0, s>>>(c, cbase, coff, seg_key, seg_val, cadj, cw);
+  count_launch();
+  VC_CHECK_LAUNCH();
+  VC_CUDA(cudaMemcpyAsync(nnz_dev, coff + c, sizeof(long long), cudaMemcpyDeviceToDevice, s));
 }
 
 }  // namespace vc

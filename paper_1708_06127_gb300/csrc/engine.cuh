@@ -52,7 +52,7 @@ struct Buf {
 
 struct Counters {
   int c;
-  int pad;
+  int maxt;  // largest pre-merged pair count of one cluster
   long long pairs;
   int changed;
   int pad2;
@@ -69,7 +69,7 @@ struct Workspace {
   // entry-sized
   Buf tmpK, tmpV;
   // pair-sized
-  Buf keysA, keysB, valsA, valsB, hist, heads, hpos, cvT;
+  Buf keysA, keysB, valsA, valsB, hist, heads, hpos, cvT, ccur;
   // coarse graphs (ping-pong)
   Buf coff[2], cadj[2], cw[2];
   // global-class tables
@@ -308,28 +308,43 @@ struct Workspace {
     relabel(labels, g.n, cid_out, cs, &ctr()->c, s);
     tune_emit(g, cid_out, cs.tmp_key, cs.tmp_val, cs.cnt);
     emit_cross(g, bins, gt, cid_out, cs.tmp_key, cs.tmp_val, cs.cnt, s, tune);
-    exclusive_scan<int, long long>(cs.cnt, cs.pos, g.n, &ctr()->pairs, cs.scan_scr, s);
+    // pairs per cluster (flags is free again after the relabel)
+    int32_t* ccount = cs.flags;
+    VC_CUDA(cudaMemsetAsync(&ctr()->maxt, 0, sizeof(int), s));
+    VC_CUDA(cudaMemsetAsync(&ctr()->pairs, 0, sizeof(long long), s));
+    cluster_count(g, cid_out, cs.cnt, ccount, &ctr()->maxt, &ctr()->pairs, s);
     VC_CUDA(cudaMemcpyAsync(h_counters, ctr(), sizeof(Counters), cudaMemcpyDeviceToHost, s));
     sync();
     const int64_t c = h_counters->c;
     const int64_t P = h_counters->pairs;
-    int bits = ceil_log2(c);
-    if (bits < 1) bits = 1;
-    auto* kA = keysA.ensure_n<unsigned long long>(P);
-    auto* kB = keysB.ensure_n<unsigned long long>(P);
-    auto* vA = valsA.ensure_n<long long>(P);
-    auto* vB = valsB.ensure_n<long long>(P);
-    auto* hs = hist.ensure_n<long long>(radix_hist_elems(P));
-    auto* hd = heads.ensure_n<int32_t>(P);
-    auto* hp = hpos.ensure_n<long long>(P + 1);
-    auto* cv = cvT.ensure_n<int32_t>(P);
-    scan64.ensure_n<long long>(scan_scratch_elems(std::max<int64_t>(P, 1)) + 1);
-    build_pairs(g, cid_out, cs, bits, kA, vA, s);
-    radix_sort_pairs(kA, vA, kB, vB, P, 2 * bits, hs, s);
     int64_t* co = coff[slot].ensure_n<int64_t>(c + 1);
-    int32_t* ca = cadj[slot].ensure_n<int32_t>(P);
-    long long* cwp = cw[slot].ensure_n<long long>(P);
-    reduce_pairs(kA, vA, P, bits, c, hd, hp, scan64.as<long long>(), co, ca, cwp, cv, &st()->nnz, s);
+    int32_t* ca = cadj[slot].ensure_n<int32_t>(std::max<int64_t>(P, 1));
+    long long* cwp = cw[slot].ensure_n<long long>(std::max<int64_t>(P, 1));
+    if (h_counters->maxt <= kMergeMax) {
+      long long* cbase = pos.as<long long>();  // n + 1 >= c + 1 entries
+      long long* cur = ccur.ensure_n<long long>(std::max<int64_t>(c, 1));
+      auto* sk = (int32_t*)keysA.ensure_n<unsigned long long>(std::max<int64_t>(P, 1));
+      auto* sv = valsA.ensure_n<long long>(std::max<int64_t>(P, 1));
+      scan64.ensure_n<long long>(scan_scratch_elems(std::max<int64_t>(c, 1)) + 1);
+      cs.scan_scr = scan64.as<long long>();
+      cluster_merge(g, cid_out, cs, ccount, c, cbase, cur, sk, sv, co, ca, cwp, &st()->nnz, s);
+    } else {
+      exclusive_scan<int, long long>(cs.cnt, cs.pos, g.n, &ctr()->pairs, cs.scan_scr, s);
+      int bits = ceil_log2(c);
+      if (bits < 1) bits = 1;
+      auto* kA = keysA.ensure_n<unsigned long long>(P);
+      auto* kB = keysB.ensure_n<unsigned long long>(P);
+      auto* vA = valsA.ensure_n<long long>(P);
+      auto* vB = valsB.ensure_n<long long>(P);
+      auto* hs = hist.ensure_n<long long>(radix_hist_elems(P));
+      auto* hd = heads.ensure_n<int32_t>(P);
+      auto* hp = hpos.ensure_n<long long>(P + 1);
+      auto* cv = cvT.ensure_n<int32_t>(P);
+      scan64.ensure_n<long long>(scan_scratch_elems(std::max<int64_t>(P, 1)) + 1);
+      build_pairs(g, cid_out, cs, bits, kA, vA, s);
+      radix_sort_pairs(kA, vA, kB, vB, P, 2 * bits, hs, s);
+      reduce_pairs(kA, vA, P, bits, c, hd, hp, scan64.as<long long>(), co, ca, cwp, cv, &st()->nnz, s);
+    }
     GraphView h;
     h.n = c;
     h.nnz = P;  // upper bound until the state is read

@@ -23,6 +23,7 @@
 #include <unordered_map>
 
 #include "kernels.cuh"
+#include "regvisit.cuh"
 
 namespace vc {
 
@@ -307,11 +308,6 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
 // so the warp software-pipelines its vertices: while it works on one vertex per
 // group it already holds the next vertex's ids and the offsets of the one after.
 
-template <int G>
-__device__ __forceinline__ unsigned group_mask(int lane) {
-  return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-}
-
 // Neighbour ids (and weights) of one list in registers.
 template <int S>
 struct RegIds {
@@ -337,14 +333,6 @@ __device__ __forceinline__ void reg_ids(RegIds<S>& R, int64_t beg, int64_t end, 
   }
 }
 
-template <int S>
-struct RegList {
-  int32_t k[S];
-  long long wt[S];
-  unsigned todo;  // bit r: slot r holds a used entry not yet visited
-  int slots;      // slots in use: ceil(deg / G), the same in every lane of the group
-};
-
 template <int MODE, bool FIRST, int G, int S>
 __device__ __forceinline__ void reg_keys(RegList<S>& L, const RegIds<S>& R, int deg, const int32_t* __restrict__ lab,
                                          int32_t own) {
@@ -358,42 +346,6 @@ __device__ __forceinline__ void reg_keys(RegList<S>& L, const RegIds<S>& R, int 
       int32_t kk;
       if (entry_key<MODE, FIRST>(lab, R.u[r], own, &kk)) L.todo |= 1u << r;
       L.k[r] = kk;
-    }
-  }
-}
-
-// Calls visit(key, total) once per distinct used key of the group's list, in
-// slot-then-lane order of first occurrence; total is the same in the group's lanes.
-// Every lane of the warp must call it (groups without a list pass slots = todo = 0).
-template <typename WT, typename ACC, int G, int S, typename F>
-__device__ __forceinline__ void reg_visit(RegList<S>& L, unsigned gmask, F visit) {
-#pragma unroll
-  for (int r = 0; r < S; ++r) {
-    if (!__any_sync(0xffffffffu, r < L.slots)) break;
-    for (;;) {
-      const unsigned bal = __ballot_sync(0xffffffffu, (L.todo >> r) & 1u);
-      if (!bal) break;
-      const unsigned gb = bal & gmask;
-      const int32_t kk = __shfl_sync(0xffffffffu, L.k[r], gb ? __ffs(gb) - 1 : 0);
-      unsigned hit = 0;
-#pragma unroll
-      for (int q = r; q < S; ++q)
-        if (L.k[q] == kk) hit |= 1u << q;
-      hit = gb ? hit & L.todo : 0u;
-      L.todo &= ~hit;
-      ACC total;
-      if (std::is_same<WT, UnitW>::value) {
-        total = (ACC)__reduce_add_sync(gmask, (unsigned)__popc(hit));
-      } else {
-        long long sum = 0;
-#pragma unroll
-        for (int q = r; q < S; ++q)
-          if (hit >> q & 1u) sum += L.wt[q];
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        total = (ACC)sum;
-      }
-      if (gb) visit(kk, total);
     }
   }
 }

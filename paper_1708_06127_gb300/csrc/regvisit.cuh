@@ -1,0 +1,65 @@
+// Distinct-key aggregation in registers (shared by label propagation, the
+// contraction pre-merge and the cluster merge).  A group of G lanes holds a list of
+// at most S G (key, weight) entries, slot r of group lane i holding entry G r + i,
+// and visits its distinct keys one at a time: the first lane whose slot r is still
+// unvisited broadcasts its key, every lane marks its entries holding it (only slots
+// >= r can), and a group reduction gives the key's count (unit weights) or weight
+// sum.  The groups of a warp step in lockstep, so warp-wide votes and shuffles always
+// have every lane present.
+#pragma once
+#include <type_traits>
+
+#include "kernels.cuh"
+
+namespace vc {
+
+template <int G>
+__device__ __forceinline__ unsigned group_mask(int lane) {
+  return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+}
+
+template <int S>
+struct RegList {
+  int32_t k[S];
+  long long wt[S];
+  unsigned todo;  // bit r: slot r holds a used entry not yet visited
+  int slots;      // slots in use: ceil(deg / G), the same in every lane of the group
+};
+
+// Calls visit(key, total) once per distinct used key of the group's list, in
+// slot-then-lane order of first occurrence; total is the same in the group's lanes.
+// Every lane of the warp must call it (groups without a list pass slots = todo = 0).
+template <typename WT, typename ACC, int G, int S, typename F>
+__device__ __forceinline__ void reg_visit(RegList<S>& L, unsigned gmask, F visit) {
+#pragma unroll
+  for (int r = 0; r < S; ++r) {
+    if (!__any_sync(0xffffffffu, r < L.slots)) break;
+    for (;;) {
+      const unsigned bal = __ballot_sync(0xffffffffu, (L.todo >> r) & 1u);
+      if (!bal) break;
+      const unsigned gb = bal & gmask;
+      const int32_t kk = __shfl_sync(0xffffffffu, L.k[r], gb ? __ffs(gb) - 1 : 0);
+      unsigned hit = 0;
+#pragma unroll
+      for (int q = r; q < S; ++q)
+        if (L.k[q] == kk) hit |= 1u << q;
+      hit = gb ? hit & L.todo : 0u;
+      L.todo &= ~hit;
+      ACC total;
+      if (std::is_same<WT, UnitW>::value) {
+        total = (ACC)__reduce_add_sync(gmask, (unsigned)__popc(hit));
+      } else {
+        long long sum = 0;
+#pragma unroll
+        for (int q = r; q < S; ++q)
+          if (hit >> q & 1u) sum += L.wt[q];
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        total = (ACC)sum;
+      }
+      if (gb) visit(kk, total);
+    }
+  }
+}
+
+}  // namespace vc
