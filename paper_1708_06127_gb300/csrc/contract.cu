@@ -154,9 +154,14 @@ __global__ void __launch_bounds__(256) cluster_count_k(int64_t n, const int32_t*
                                                        const int32_t* __restrict__ cnt, int32_t* __restrict__ ccount,
                                                        int* maxt, long long* pairs) {
   __shared__ int s_k[8][32];
+  __shared__ int s_max;
+  __shared__ unsigned long long s_pairs;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) { s_max = 0; s_pairs = 0; }
+  __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   long long mine = 0;
+  int top = 0;  // largest running count this lane saw
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
     const int64_t v = base + lane;
     const int k = v < n ? cnt[v] : 0;
@@ -164,14 +169,22 @@ __global__ void __launch_bounds__(256) cluster_count_k(int64_t n, const int32_t*
     unsigned peers;
     int t, b;
     group_sums(c, k, lane, s_k[wid], &peers, &t, &b);
-    if (c >= 0 && lane == __ffs(peers) - 1) {
-      const int old = atomicAdd(&ccount[c], t);
-      atomicMax(maxt, old + t);
-    }
+    if (c >= 0 && lane == __ffs(peers) - 1) top = max(top, atomicAdd(&ccount[c], t) + t);
     mine += k;
   }
+  // the last addition to a cluster returns its final count, so the maximum of the
+  // running counts is the largest final count
+  const unsigned wtop = __reduce_max_sync(0xffffffffu, (unsigned)top);
   const long long w = warp_sum(mine);
-  if (lane == 0 && w) atomicAdd((unsigned long long*)pairs, (unsigned long long)w);
+  if (lane == 0) {
+    if (wtop) atomicMax(&s_max, (int)wtop);
+    if (w) atomicAdd(&s_pairs, (unsigned long long)w);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_max) atomicMax(maxt, s_max);
+    if (s_pairs) atomicAdd((unsigned long long*)pairs, s_pairs);
+  }
 }
 
 // Counting-sort scatter: the pre-merged pairs of fine vertex v move, in one piece,
@@ -200,9 +213,16 @@ __global__ void __launch_bounds__(256) cluster_scatter_k(int64_t n, const int64_
     if (c >= 0) {
       const int64_t src = off[v];
       const long long dst = at + b;
-      for (int j = 0; j < k; ++j) {
-        seg_key[dst + j] = tkey[src + j];
-        seg_val[dst + j] = tval[src + j];
+      // four pairs in flight at a time (most vertices have one to four)
+      for (int j0 = 0; j0 < k; j0 += 4) {
+        int32_t kk[4];
+        long long vv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (j0 + j < k) { kk[j] = tkey[src + j0 + j]; vv[j] = tval[src + j0 + j]; }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (j0 + j < k) { seg_key[dst + j0 + j] = kk[j]; seg_val[dst + j0 + j] = vv[j]; }
       }
     }
   }
@@ -228,7 +248,7 @@ __global__ void __launch_bounds__(256) cluster_merge_k(int64_t c, const long lon
       const int i = lane + 32 * r;
       L.k[r] = -1;
       L.wt[r] = 0;
-      if (i < T) {
+      if (32 * r < T && i < T) {  // 32 r < T is the same in every lane
         L.k[r] = seg_key[b + i];
         L.wt[r] = seg_val[b + i];
         L.todo |= 1u << r;
