@@ -90,6 +90,29 @@ __device__ __forceinline__ bool pr_graph(const BatchCtx& bc, const DevState* st,
 
 // Condition 1 on every edge (once per undirected edge: u > v) and condition 2 on the
 // designated-partner edge; both ends must have at least two distinct neighbours.
+// Union-find finds are chains of dependent loads, so short lists take a thread each
+// (all of them in flight at once) and only lists longer than kPrThreadMax a warp.
+constexpr int kPrThreadMax = 64;
+
+template <typename WT>
+__global__ void pr_a_mark_thread_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                                   const WT* __restrict__ w, const int32_t* __restrict__ partner,
+                                   const long long* __restrict__ pw, const long long* __restrict__ deg,
+                                   const DevState* st, int32_t* parent, BatchCtx bc) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    long long lam;
+    if (!pr_graph(bc, st, v, &lam)) continue;
+    const int64_t beg = off[v], end = off[v + 1];
+    if (end - beg < 2 || end - beg > kPrThreadMax) continue;
+    for (int64_t e = beg; e < end; ++e) {
+      const int u = adj[e];
+      if (u > v && (long long)w[e] >= lam && off[u + 1] - off[u] >= 2) uf_unite(parent, (int)v, u);
+    }
+    const int p = partner[v];
+    if (p >= 0 && off[p + 1] - off[p] >= 2 && deg[v] <= 2 * pw[v]) uf_unite(parent, (int)v, p);
+  }
+}
+
 template <typename WT>
 __global__ void pr_a_mark_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                             const WT* __restrict__ w, const int32_t* __restrict__ partner,
@@ -101,7 +124,7 @@ __global__ void pr_a_mark_k(int64_t n, const int64_t* __restrict__ off, const in
     long long lam;
     if (!pr_graph(bc, st, v, &lam)) continue;
     const int64_t beg = off[v], end = off[v + 1];
-    if (end - beg < 2) continue;
+    if (end - beg <= kPrThreadMax) continue;
     for (int64_t e = beg + lane; e < end; e += 32) {
       int u = adj[e];
       if (u > v && (long long)w[e] >= lam && off[u + 1] - off[u] >= 2) uf_unite(parent, (int)v, u);
@@ -134,13 +157,18 @@ void pr_pass_a(const GraphView& g, const int32_t* partner, const long long* pw, 
   int grid1 = grid_for(g.n, 256, kSMs * 8);
   uf_init_k<<<grid1, 256, 0, s>>>(parent, g.n);
   int grid = grid_for(g.n, 8, kSMs * 16);
-  if (g.wbytes == 4)
+  if (g.wbytes == 4) {
+    pr_a_mark_thread_k<int32_t><<<grid1, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, partner, pw, deg, st,
+                                                      parent, bc);
     pr_a_mark_k<int32_t><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, partner, pw, deg, st, parent, bc);
-  else
+  } else {
+    pr_a_mark_thread_k<long long><<<grid1, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, partner, pw, deg,
+                                                        st, parent, bc);
     pr_a_mark_k<long long><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, partner, pw, deg, st,
                                                 parent, bc);
+  }
   uf_flatten_k<<<grid1, 256, 0, s>>>(parent, g.n, labels, changed, bc);
-  count_launch(3);
+  count_launch(4);
   VC_CHECK_LAUNCH();
 }
 
