@@ -272,7 +272,8 @@ __global__ void __launch_bounds__(256) cluster_place_k(int64_t c, const long lon
                                                        const int64_t* __restrict__ coff,
                                                        const int32_t* __restrict__ seg_key,
                                                        const long long* __restrict__ seg_val,
-                                                       int32_t* __restrict__ cadj, long long* __restrict__ cw) {
+                                                       int32_t* __restrict__ cadj, long long* __restrict__ cw,
+                                                       int32_t* __restrict__ csrc) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < c; x += warps) {
@@ -285,6 +286,7 @@ __global__ void __launch_bounds__(256) cluster_place_k(int64_t c, const long lon
       for (int j = 0; j < D; ++j) rank += seg_key[b + j] < key;
       cadj[o + rank] = key;
       cw[o + rank] = seg_val[b + i];
+      csrc[o + rank] = (int32_t)x;
     }
   }
 }
@@ -300,7 +302,7 @@ void cluster_count(const GraphView& g, const int32_t* cid, const int32_t* cnt, i
 
 void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int32_t* ccount, int64_t c,
                    long long* cbase, long long* cursor, int32_t* seg_key, long long* seg_val, int64_t* coff,
-                   int32_t* cadj, long long* cw, long long* nnz_dev, cudaStream_t s) {
+                   int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, cudaStream_t s) {
   exclusive_scan<int, long long>(ccount, cbase, c, cbase + c, cs.scan_scr, s);
   VC_CUDA(cudaMemcpyAsync(cursor, cbase, sizeof(long long) * c, cudaMemcpyDeviceToDevice, s));
   const int gv = grid_for(g.n, 256, kSMs * 8), gc = grid_for(c, 8, kSMs * 16);
@@ -309,7 +311,7 @@ void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch
   count_launch(2);
   VC_CHECK_LAUNCH();
   exclusive_scan<int, long long>(ccount, (long long*)coff, c, (long long*)coff + c, cs.scan_scr, s);
-  cluster_place_k<<<gc, 256, 0, s>>>(c, cbase, coff, seg_key, seg_val, cadj, cw);
+  cluster_place_k<<<gc, 256, 0, s>>>(c, cbase, coff, seg_key, seg_val, cadj, cw, csrc);
   count_launch();
   VC_CHECK_LAUNCH();
   VC_CUDA(cudaMemcpyAsync(nnz_dev, coff + c, sizeof(long long), cudaMemcpyDeviceToDevice, s));

@@ -71,7 +71,7 @@ struct Workspace {
   // pair-sized
   Buf keysA, keysB, valsA, valsB, hist, heads, hpos, cvT, ccur;
   // coarse graphs (ping-pong)
-  Buf coff[2], cadj[2], cw[2];
+  Buf coff[2], cadj[2], cw[2], csrc[2];
   // global-class tables
   Buf gkeys, gvals;
   GlobalTables gt;
@@ -320,6 +320,7 @@ struct Workspace {
     int64_t* co = coff[slot].ensure_n<int64_t>(c + 1);
     int32_t* ca = cadj[slot].ensure_n<int32_t>(std::max<int64_t>(P, 1));
     long long* cwp = cw[slot].ensure_n<long long>(std::max<int64_t>(P, 1));
+    int32_t* csp = csrc[slot].ensure_n<int32_t>(std::max<int64_t>(P, 1));
     if (h_counters->maxt <= kMergeMax) {
       long long* cbase = pos.as<long long>();  // n + 1 >= c + 1 entries
       long long* cur = ccur.ensure_n<long long>(std::max<int64_t>(c, 1));
@@ -327,7 +328,7 @@ struct Workspace {
       auto* sv = valsA.ensure_n<long long>(std::max<int64_t>(P, 1));
       scan64.ensure_n<long long>(scan_scratch_elems(std::max<int64_t>(c, 1)) + 1);
       cs.scan_scr = scan64.as<long long>();
-      cluster_merge(g, cid_out, cs, ccount, c, cbase, cur, sk, sv, co, ca, cwp, &st()->nnz, s);
+      cluster_merge(g, cid_out, cs, ccount, c, cbase, cur, sk, sv, co, ca, cwp, csp, &st()->nnz, s);
     } else {
       exclusive_scan<int, long long>(cs.cnt, cs.pos, g.n, &ctr()->pairs, cs.scan_scr, s);
       int bits = ceil_log2(c);
@@ -339,11 +340,10 @@ struct Workspace {
       auto* hs = hist.ensure_n<long long>(radix_hist_elems(P));
       auto* hd = heads.ensure_n<int32_t>(P);
       auto* hp = hpos.ensure_n<long long>(P + 1);
-      auto* cv = cvT.ensure_n<int32_t>(P);
       scan64.ensure_n<long long>(scan_scratch_elems(std::max<int64_t>(P, 1)) + 1);
       build_pairs(g, cid_out, cs, bits, kA, vA, s);
       radix_sort_pairs(kA, vA, kB, vB, P, 2 * bits, hs, s);
-      reduce_pairs(kA, vA, P, bits, c, hd, hp, scan64.as<long long>(), co, ca, cwp, cv, &st()->nnz, s);
+      reduce_pairs(kA, vA, P, bits, c, hd, hp, scan64.as<long long>(), co, ca, cwp, csp, &st()->nnz, s);
     }
     GraphView h;
     h.n = c;
@@ -351,6 +351,7 @@ struct Workspace {
     h.off = co;
     h.adj = ca;
     h.w = cwp;
+    h.src = csp;
     h.wbytes = 8;
     h.simple = true;
     bins_valid = false;

@@ -18,6 +18,8 @@ struct GraphView {
   bool simple = false;  // every list strictly increasing (no parallel entries)
   // batches: label propagation touches only vertices v with vact[v] != 0 (null: all)
   const unsigned char* vact = nullptr;
+  // source vertex of every entry (contracted graphs; null when not built)
+  const int32_t* src = nullptr;
 };
 
 // Per-graph view of a batch (a disjoint union of graphs): vertex v belongs to graph
@@ -118,7 +120,7 @@ void cluster_count(const GraphView& g, const int32_t* cid, const int32_t* cnt, i
                    long long* pairs, cudaStream_t s);
 void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int32_t* ccount, int64_t c,
                    long long* cbase, long long* cursor, int32_t* seg_key, long long* seg_val, int64_t* coff,
-                   int32_t* cadj, long long* cw, long long* nnz_dev, cudaStream_t s);
+                   int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, cudaStream_t s);
 
 // Builds (cid[v] << bits | cu, weight) pairs from the pre-merged lists.
 void build_pairs(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int bits,

@@ -11,6 +11,7 @@
 
 #include <mutex>
 #include <string>
+#include <unordered_map>
 
 #include "kernels.cuh"
 #include "viecut.h"
@@ -223,22 +224,49 @@ __global__ void __launch_bounds__(kNoiThreads) noi_dense_k(int n, const int64_t*
                                                            const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                            long long* M0, long long* M1, int32_t* curK,
                                                            unsigned char* sideK, DevState* st, TraceStep* trace,
-                                                           int trace_cap, int level) {
+                                                           int trace_cap, int level, int in_smem) {
+  // small kernels keep both matrices in shared memory (each round reads a matrix row
+  // per scan step; shared memory answers in a few cycles)
+  extern __shared__ __align__(16) long long noi_dyn[];
+  if (in_smem) {
+    M0 = noi_dyn;
+    M1 = noi_dyn + (int64_t)n * n;
+  }
   NoiIO io{&st->lambda_hat, &st->best_kind, &st->n, &st->nnz, &st->dmin, &st->argmin, &st->trace_len,
            trace, trace_cap, level};
   noi_dense_body<WT>(n, off, adj, w, 0, M0, M1, curK, sideK, io);
 }
 
-void noi_dense(const GraphView& g, long long* M0, long long* M1, int32_t* curK, unsigned char* sideK,
-               DevState* st, TraceStep* trace, int trace_cap, int level, cudaStream_t s) {
-  if (g.wbytes == 4)
-    noi_dense_k<int32_t><<<1, kNoiThreads, 0, s>>>((int)g.n, g.off, g.adj, (const int32_t*)g.w, M0, M1, curK,
-                                                   sideK, st, trace, trace_cap, level);
-  else
-    noi_dense_k<long long><<<1, kNoiThreads, 0, s>>>((int)g.n, g.off, g.adj, (const long long*)g.w, M0, M1, curK,
-                                                     sideK, st, trace, trace_cap, level);
+constexpr int kNoiSmemMaxN = 96;  // 2 x 96^2 x 8 B = 144 KiB of shared memory
+
+template <typename WT>
+static void noi_dense_launch(const GraphView& g, long long* M0, long long* M1, int32_t* curK, unsigned char* sideK,
+                             DevState* st, TraceStep* trace, int trace_cap, int level, cudaStream_t s) {
+  static std::mutex mu;
+  static std::unordered_map<int, bool> ready;  // per device: the shared-memory limit was raised
+  const int n = (int)g.n;
+  const bool small = n <= kNoiSmemMaxN;
+  const size_t smem = small ? sizeof(long long) * 2 * (size_t)n * n : 0;
+  if (small) {
+    int dev = 0;
+    VC_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ready[dev]) {
+      VC_CUDA(cudaFuncSetAttribute(noi_dense_k<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(long long) * 2 * kNoiSmemMaxN * kNoiSmemMaxN)));
+      ready[dev] = true;
+    }
+  }
+  noi_dense_k<WT><<<1, kNoiThreads, smem, s>>>(n, g.off, g.adj, (const WT*)g.w, M0, M1, curK, sideK, st, trace,
+                                               trace_cap, level, small ? 1 : 0);
   count_launch();
   VC_CHECK_LAUNCH();
+}
+
+void noi_dense(const GraphView& g, long long* M0, long long* M1, int32_t* curK, unsigned char* sideK,
+               DevState* st, TraceStep* trace, int trace_cap, int level, cudaStream_t s) {
+  if (g.wbytes == 4) noi_dense_launch<int32_t>(g, M0, M1, curK, sideK, st, trace, trace_cap, level, s);
+  else noi_dense_launch<long long>(g, M0, M1, curK, sideK, st, trace, trace_cap, level, s);
 }
 
 // Batches: a persistent grid pulls the listed graphs; each block solves one at a time

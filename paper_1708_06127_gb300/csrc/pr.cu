@@ -113,6 +113,37 @@ __global__ void pr_a_mark_thread_k(int64_t n, const int64_t* __restrict__ off, c
   }
 }
 
+// Contracted graphs carry each entry's source, so every entry takes a thread.
+// The entry count is the graph's last offset, read on the device (a host-side count
+// may be an upper bound).
+template <typename WT>
+__global__ void pr_a_edge_k(int64_t n, const int32_t* __restrict__ src, const int64_t* __restrict__ off,
+                            const int32_t* __restrict__ adj, const WT* __restrict__ w, const DevState* st,
+                            int32_t* parent, BatchCtx bc) {
+  const int64_t nnz = off[n];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    const int v = src[e], u = adj[e];
+    if (u <= v) continue;
+    long long lam;
+    if (!pr_graph(bc, st, v, &lam)) continue;
+    if ((long long)w[e] < lam) continue;
+    if (off[v + 1] - off[v] < 2 || off[u + 1] - off[u] < 2) continue;
+    uf_unite(parent, v, u);
+  }
+}
+
+__global__ void pr_a_partner_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ partner,
+                               const long long* __restrict__ pw, const long long* __restrict__ deg,
+                               const DevState* st, int32_t* parent, BatchCtx bc) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    long long lam;
+    if (!pr_graph(bc, st, v, &lam)) continue;
+    if (off[v + 1] - off[v] < 2) continue;
+    const int p = partner[v];
+    if (p >= 0 && off[p + 1] - off[p] >= 2 && deg[v] <= 2 * pw[v]) uf_unite(parent, (int)v, p);
+  }
+}
+
 template <typename WT>
 __global__ void pr_a_mark_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                             const WT* __restrict__ w, const int32_t* __restrict__ partner,
@@ -157,7 +188,14 @@ void pr_pass_a(const GraphView& g, const int32_t* partner, const long long* pw, 
   int grid1 = grid_for(g.n, 256, kSMs * 8);
   uf_init_k<<<grid1, 256, 0, s>>>(parent, g.n);
   int grid = grid_for(g.n, 8, kSMs * 16);
-  if (g.wbytes == 4) {
+  if (g.src) {
+    const int ge = grid_for(g.nnz, 256, kSMs * 16);
+    if (g.wbytes == 4)
+      pr_a_edge_k<int32_t><<<ge, 256, 0, s>>>(g.n, g.src, g.off, g.adj, (const int32_t*)g.w, st, parent, bc);
+    else
+      pr_a_edge_k<long long><<<ge, 256, 0, s>>>(g.n, g.src, g.off, g.adj, (const long long*)g.w, st, parent, bc);
+    pr_a_partner_k<<<grid1, 256, 0, s>>>(g.n, g.off, partner, pw, deg, st, parent, bc);
+  } else if (g.wbytes == 4) {
     pr_a_mark_thread_k<int32_t><<<grid1, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, partner, pw, deg, st,
                                                       parent, bc);
     pr_a_mark_k<int32_t><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, partner, pw, deg, st, parent, bc);
