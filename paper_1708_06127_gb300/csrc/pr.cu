@@ -132,6 +132,29 @@ __global__ void pr_a_edge_k(int64_t n, const int32_t* __restrict__ src, const in
   }
 }
 
+// Union-find start for pass A on sorted lists: each vertex points at its smallest
+// marked neighbour below it (or at itself).  Every such pointer is a union of a
+// marked edge towards a smaller id, so this is a valid forest with min-id roots,
+// shallow from the start; the per-entry pass then finds short paths.
+template <typename WT>
+__global__ void uf_init_min_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                              const WT* __restrict__ w, const DevState* st, int32_t* __restrict__ parent,
+                              BatchCtx bc) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t p = (int32_t)v;
+    long long lam;
+    const int64_t beg = off[v], end = off[v + 1];
+    if (end - beg >= 2 && pr_graph(bc, st, v, &lam)) {
+      for (int64_t e = beg; e < end; ++e) {
+        const int u = adj[e];
+        if (u >= v) break;  // sorted: no smaller neighbour follows
+        if ((long long)w[e] >= lam && off[u + 1] - off[u] >= 2) { p = u; break; }
+      }
+    }
+    parent[v] = p;
+  }
+}
+
 __global__ void pr_a_partner_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ partner,
                                const long long* __restrict__ pw, const long long* __restrict__ deg,
                                const DevState* st, int32_t* parent, BatchCtx bc) {
@@ -186,10 +209,14 @@ void pr_pass_a(const GraphView& g, const int32_t* partner, const long long* pw, 
                const BatchCtx* bcp) {
   BatchCtx bc = bcp ? *bcp : BatchCtx{};
   int grid1 = grid_for(g.n, 256, kSMs * 8);
-  uf_init_k<<<grid1, 256, 0, s>>>(parent, g.n);
+  if (!g.src) uf_init_k<<<grid1, 256, 0, s>>>(parent, g.n);
   int grid = grid_for(g.n, 8, kSMs * 16);
-  if (g.src) {
+  if (g.src) {  // contracted graph: sorted lists and entry sources
     const int ge = grid_for(g.nnz, 256, kSMs * 16);
+    if (g.wbytes == 4)
+      uf_init_min_k<int32_t><<<grid1, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, st, parent, bc);
+    else
+      uf_init_min_k<long long><<<grid1, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, st, parent, bc);
     if (g.wbytes == 4)
       pr_a_edge_k<int32_t><<<ge, 256, 0, s>>>(g.n, g.src, g.off, g.adj, (const int32_t*)g.w, st, parent, bc);
     else
