@@ -7,7 +7,11 @@
 //     and a warp per cluster that merges its pairs in registers and writes the
 //     distinct targets in ascending order (every cluster holding <= kMergeMax pairs), or
 //   * pair build, LSD radix sort on (cid v, cid u) and a run reduction (otherwise).
+#include <limits.h>
+
 #include <algorithm>
+#include <mutex>
+#include <unordered_map>
 
 #include "kernels.cuh"
 #include "prims.cuh"
@@ -240,6 +244,7 @@ __global__ void __launch_bounds__(256) cluster_merge_k(int64_t c, const long lon
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < c; x += warps) {
     const long long b = cbase[x];
     const int T = (int)(cbase[x + 1] - b);
+    if (T > kMergeMax) continue;  // the block kernel takes it
     RegList<S> L;
     L.slots = (T + 31) >> 5;
     L.todo = 0;
@@ -263,6 +268,86 @@ __global__ void __launch_bounds__(256) cluster_merge_k(int64_t c, const long lon
       ++made;
     });
     if (lane == 0) dcount[x] = made;
+  }
+}
+
+// Clusters of kMergeMax < T <= kMergeBlockMax pairs: a block per cluster sorts the
+// pairs by target in shared memory (bitonic network over the next power of two,
+// padding keys INT_MAX), then every run head sums its run; the distinct targets are
+// written back in ascending order at the front of the segment.
+__global__ void __launch_bounds__(256) cluster_merge_block_k(int64_t c, const long long* __restrict__ cbase,
+                                                             int32_t* __restrict__ seg_key,
+                                                             long long* __restrict__ seg_val,
+                                                             int32_t* __restrict__ dcount) {
+  extern __shared__ __align__(16) unsigned char mb_dyn[];
+  long long* sv = (long long*)mb_dyn;
+  int32_t* sk = (int32_t*)(sv + kMergeBlockMax);
+  __shared__ int s_warp[8];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int64_t x = blockIdx.x; x < c; x += gridDim.x) {
+    const long long b = cbase[x];
+    const int T = (int)(cbase[x + 1] - b);
+    if (T <= kMergeMax) continue;  // the same in every thread of the block
+    int N = 1;
+    while (N < T) N <<= 1;
+    for (int i = tid; i < N; i += 256) {
+      sk[i] = i < T ? seg_key[b + i] : INT_MAX;
+      sv[i] = i < T ? seg_val[b + i] : 0;
+    }
+    __syncthreads();
+    for (int k = 2; k <= N; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < N; i += 256) {
+          const int l = i ^ j;
+          if (l > i) {
+            const bool up = (i & k) == 0;
+            const int32_t a = sk[i], bb = sk[l];
+            if ((a > bb) == up) {
+              sk[i] = bb;
+              sk[l] = a;
+              const long long t = sv[i];
+              sv[i] = sv[l];
+              sv[l] = t;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // run heads, numbered by a block scan; each head sums its run
+    constexpr int kPer = kMergeBlockMax / 256;
+    int cnt = 0;
+    for (int q = 0; q < kPer; ++q) {
+      const int i = tid * kPer + q;
+      if (i < N && sk[i] != INT_MAX && (i == 0 || sk[i] != sk[i - 1])) ++cnt;
+    }
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[wid] = inc;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w2 = 0; w2 < 8; ++w2) {
+      if (w2 < wid) before += s_warp[w2];
+      total += s_warp[w2];
+    }
+    int at = before + inc - cnt;
+    // the sorted copy is in shared memory, so the segment can be overwritten
+    for (int q = 0; q < kPer; ++q) {
+      const int i = tid * kPer + q;
+      if (i < N && sk[i] != INT_MAX && (i == 0 || sk[i] != sk[i - 1])) {
+        long long sum = sv[i];
+        for (int j = i + 1; j < N && sk[j] == sk[i]; ++j) sum += sv[j];
+        seg_key[b + at] = sk[i];
+        seg_val[b + at] = sum;
+        ++at;
+      }
+    }
+    if (tid == 0) dcount[x] = total;
+    __syncthreads();
   }
 }
 
@@ -302,7 +387,7 @@ void cluster_count(const GraphView& g, const int32_t* cid, const int32_t* cnt, i
 
 void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int32_t* ccount, int64_t c,
                    long long* cbase, long long* cursor, int32_t* seg_key, long long* seg_val, int64_t* coff,
-                   int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, cudaStream_t s) {
+                   int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, bool big, cudaStream_t s) {
   exclusive_scan<int, long long>(ccount, cbase, c, cbase + c, cs.scan_scr, s);
   VC_CUDA(cudaMemcpyAsync(cursor, cbase, sizeof(long long) * c, cudaMemcpyDeviceToDevice, s));
   const int gv = grid_for(g.n, 256, kSMs * 8), gc = grid_for(c, 8, kSMs * 16);
@@ -310,6 +395,23 @@ void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch
   cluster_merge_k<<<gc, 256, 0, s>>>(c, cbase, seg_key, seg_val, ccount);
   count_launch(2);
   VC_CHECK_LAUNCH();
+  if (big) {
+    static std::mutex mu;
+    static std::unordered_map<int, bool> ready;  // per device: the shared-memory limit was raised
+    const int smem = kMergeBlockMax * (int)(sizeof(long long) + sizeof(int32_t));
+    {
+      int dev = 0;
+      VC_CUDA(cudaGetDevice(&dev));
+      std::lock_guard<std::mutex> lk(mu);
+      if (!ready[dev]) {
+        VC_CUDA(cudaFuncSetAttribute(cluster_merge_block_k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        ready[dev] = true;
+      }
+    }
+    cluster_merge_block_k<<<grid_for(c, 1, kSMs * 2), 256, smem, s>>>(c, cbase, seg_key, seg_val, ccount);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
   exclusive_scan<int, long long>(ccount, (long long*)coff, c, (long long*)coff + c, cs.scan_scr, s);
   cluster_place_k<<<gc, 256, 0, s>>>(c, cbase, coff, seg_key, seg_val, cadj, cw, csrc);
   count_launch();

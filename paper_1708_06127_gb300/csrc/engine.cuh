@@ -321,14 +321,15 @@ struct Workspace {
     int32_t* ca = cadj[slot].ensure_n<int32_t>(std::max<int64_t>(P, 1));
     long long* cwp = cw[slot].ensure_n<long long>(std::max<int64_t>(P, 1));
     int32_t* csp = csrc[slot].ensure_n<int32_t>(std::max<int64_t>(P, 1));
-    if (h_counters->maxt <= kMergeMax) {
+    if (h_counters->maxt <= kMergeBlockMax) {
       long long* cbase = pos.as<long long>();  // n + 1 >= c + 1 entries
       long long* cur = ccur.ensure_n<long long>(std::max<int64_t>(c, 1));
       auto* sk = (int32_t*)keysA.ensure_n<unsigned long long>(std::max<int64_t>(P, 1));
       auto* sv = valsA.ensure_n<long long>(std::max<int64_t>(P, 1));
       scan64.ensure_n<long long>(scan_scratch_elems(std::max<int64_t>(c, 1)) + 1);
       cs.scan_scr = scan64.as<long long>();
-      cluster_merge(g, cid_out, cs, ccount, c, cbase, cur, sk, sv, co, ca, cwp, csp, &st()->nnz, s);
+      cluster_merge(g, cid_out, cs, ccount, c, cbase, cur, sk, sv, co, ca, cwp, csp, &st()->nnz,
+                    h_counters->maxt > kMergeMax, s);
     } else {
       exclusive_scan<int, long long>(cs.cnt, cs.pos, g.n, &ctr()->pairs, cs.scan_scr, s);
       int bits = ceil_log2(c);

@@ -112,15 +112,18 @@ struct ContractScratch {
 // Relabel: cid[v] = rank of lab[v] among the distinct labels; *c_dev = count.
 void relabel(const int32_t* lab, int64_t n, int32_t* cid, ContractScratch& cs, int* c_dev, cudaStream_t s);
 
-// Cluster merge (every cluster holding at most kMergeMax pre-merged pairs):
+// Cluster merge (every cluster holding at most kMergeBlockMax pre-merged pairs; a
+// warp merges clusters of at most kMergeMax in registers, a block the larger ones):
 // cluster_count fills ccount[cid] (n entries zeroed first), *maxt and *pairs;
-// cluster_merge writes the coarse CSR (coff[c + 1], sorted cadj, cw) and *nnz_dev.
+// cluster_merge writes the coarse CSR (coff[c + 1], sorted cadj, cw, entry sources
+// csrc) and *nnz_dev; big = some cluster holds more than kMergeMax pairs.
 constexpr int kMergeMax = 512;
+constexpr int kMergeBlockMax = 4096;
 void cluster_count(const GraphView& g, const int32_t* cid, const int32_t* cnt, int32_t* ccount, int* maxt,
                    long long* pairs, cudaStream_t s);
 void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int32_t* ccount, int64_t c,
                    long long* cbase, long long* cursor, int32_t* seg_key, long long* seg_val, int64_t* coff,
-                   int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, cudaStream_t s);
+                   int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, bool big, cudaStream_t s);
 
 // Builds (cid[v] << bits | cu, weight) pairs from the pre-merged lists.
 void build_pairs(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int bits,
