@@ -363,6 +363,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nlog", type=int, default=22, help="log2 of the RHG vertex count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lp-group", type=int, default=0,
+                    help="lanes per vertex of the first label-propagation round (0: picked by timing)")
+    ap.add_argument("--emit-group", type=int, default=0,
+                    help="lanes per vertex of the block-class pre-merge (0: picked by timing)")
     ap.add_argument("--mode", default="all", choices=["all", "single", "batch", "serve"],
                     help="all: the headline line plus batch and serving summaries")
     ap.add_argument("--batch-count", type=int, default=4096)
@@ -405,7 +409,8 @@ def main():
     off = torch.from_numpy(g.offsets).to(dev)
     adj = torch.from_numpy(g.adj).to(dev)
     w = torch.from_numpy(g.w).to(dev)
-    mc = vc.MinCut(off, adj, w, on_device=True, device=local, stream=stream.cuda_stream, timing=True)
+    mc = vc.MinCut(off, adj, w, on_device=True, device=local, stream=stream.cuda_stream, timing=True,
+                   lp_group=args.lp_group, emit_group=args.emit_group)
     d_cut = torch.zeros(1, dtype=torch.int64, device=dev)
     d_bits = torch.zeros((g.n + 63) // 64, dtype=torch.int64, device=dev)
 
