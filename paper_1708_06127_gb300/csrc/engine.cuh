@@ -65,7 +65,7 @@ struct Workspace {
   cudaStream_t s = nullptr;
   // vertex-sized
   Buf deg, labA, labB, map0, cidT, cur1, side1, flags, rank, cnt, pos, scan64, scan32, hv;
-  Buf partner, pw, parent, slist, rlist, mlist, blist, glist, olist, bcounts, noi_r, noi_seen;
+  Buf partner, pw, parent, slist, rlist, mlist, blist, glist, bcounts, noi_r, noi_seen;
   // entry-sized
   Buf tmpK, tmpV;
   // pair-sized
@@ -125,7 +125,6 @@ struct Workspace {
     parent.ensure_n<int32_t>(n);
     slist.ensure_n<int32_t>(n);
     rlist.ensure_n<int32_t>(n);
-    olist.ensure_n<int32_t>(n);
     mlist.ensure_n<int32_t>(n);
     blist.ensure_n<int32_t>(n);
     glist.ensure_n<int32_t>(n);
@@ -246,7 +245,6 @@ struct Workspace {
     bins.mid_list = mlist.as<int32_t>();
     bins.block_list = blist.as<int32_t>();
     bins.global_list = glist.as<int32_t>();
-    bins.ovf_list = olist.as<int32_t>();
     bins.counts = bcounts.as<int>();
     bins_build(g, bins, s);
     int hc[6];

@@ -58,9 +58,8 @@ struct Bins {
   int32_t* mid_list;     // [n]
   int32_t* block_list;   // [n]
   int32_t* global_list;  // [n]
-  int32_t* ovf_list;     // [n] vertices a per-thread table could not hold (rebuilt per pass)
   int* counts;           // device: [0] mid, [1] block, [2] global count, [3] max length above
-                         // 128, [4] small, [5] reg, [6] overflow count
+                         // 128, [4] small, [5] reg count
   int h_mid = 0, h_block = 0, h_global = 0, h_maxdeg = 0, h_small = 0, h_reg = 0;  // host copies
 };
 

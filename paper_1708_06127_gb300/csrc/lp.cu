@@ -484,112 +484,18 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restr
   });
 }
 
-// ------------------------------------------------------------ thread class
-// Lists of at most kWarpMaxDeg entries, one thread per vertex: the thread walks its
-// list and sums per key in a private open-addressing table of kTSlots slots in
-// shared memory (slot-major, so the threads of a warp touching the same slot index
-// hit distinct banks).  Per entry this is a gather and a probe or two: no warp-wide
-// steps at all.  A list with more than kTSlots distinct keys cannot be held; the
-// thread appends its vertex to an overflow list that the warp kernel takes after.
-constexpr int kTSlots = 16;
-constexpr int kTThreads = 128;
-
-template <typename WT, typename ACC, bool FIRST>
-__global__ void __launch_bounds__(kTThreads) lp_thread_k(const int32_t* __restrict__ list,
-                                                         const int* __restrict__ count_ptr,
-                                                         const int64_t* __restrict__ off,
-                                                         const int32_t* __restrict__ adj, const WT* __restrict__ w,
-                                                         const int32_t* __restrict__ lab,
-                                                         int32_t* __restrict__ lab_out,
-                                                         const unsigned long long* __restrict__ hv,
-                                                         const unsigned char* __restrict__ vact,
-                                                         int32_t* __restrict__ ovf_list, int* __restrict__ ovf_count) {
-  __shared__ int32_t tk[kTSlots][kTThreads];
-  __shared__ ACC tv[kTSlots][kTThreads];
-  const int tid = threadIdx.x;
-#pragma unroll
-  for (int q = 0; q < kTSlots; ++q) tk[q][tid] = -1;
-  const int64_t total = *count_ptr;
-  for (int64_t i = (int64_t)blockIdx.x * kTThreads + tid; i < total; i += (int64_t)gridDim.x * kTThreads) {
-    const int32_t v = __ldg(list + i);
-    if (vact && !vact[v]) continue;
-    const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
-    if (beg == end) {
-      lab_out[v] = FIRST ? v : __ldg(lab + v);
-      continue;
-    }
-    bool full = false;
-    for (int64_t e0 = beg; e0 < end && !full; e0 += 4) {
-      int32_t k[4];
-      ACC x[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        k[r] = -1;
-        if (e0 + r < end) {
-          const int32_t u = __ldg(adj + e0 + r);
-          k[r] = FIRST ? u : __ldg(lab + u);
-          x[r] = (ACC)ldw(w, e0 + r);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        if (k[r] < 0) continue;
-        uint32_t h = slot_hash(k[r], 4);
-        int p = 0;
-        for (; p < kTSlots; ++p) {
-          const int32_t cur = tk[h][tid];
-          if (cur == k[r]) { tv[h][tid] += x[r]; break; }
-          if (cur < 0) { tk[h][tid] = k[r]; tv[h][tid] = x[r]; break; }
-          h = (h + 1) & (kTSlots - 1);
-        }
-        if (p == kTSlots) full = true;
-      }
-    }
-    // best (sum, hash, -label) over the used slots, clearing them; ties read hashes
-    ACC bs = 0;
-    int32_t bl = -1;
-    unsigned long long bh = 0;
-    bool hashed = false;
-#pragma unroll
-    for (int q = 0; q < kTSlots; ++q) {
-      const int32_t kk = tk[q][tid];
-      if (kk < 0) continue;
-      tk[q][tid] = -1;
-      if (full) continue;
-      const ACC t = tv[q][tid];
-      if (bl < 0 || t > bs) {
-        bs = t;
-        bl = kk;
-        hashed = false;
-      } else if (t == bs) {
-        if (!hashed) { bh = __ldg(hv + bl); hashed = true; }
-        const unsigned long long hk = __ldg(hv + kk);
-        if (hk > bh || (hk == bh && kk < bl)) { bh = hk; bl = kk; }
-      }
-    }
-    if (full) ovf_list[atomicAdd(ovf_count, 1)] = v;
-    else lab_out[v] = bl;
-  }
-}
-
 template <typename WT, typename ACC, bool FIRST>
 void launch_lp_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t* lab, int32_t* lab_out,
                    const unsigned long long* hv, cudaStream_t s) {
-  // lists of <= 128 entries: a thread each; the few whose keys overflow the thread's
-  // table go to the warp kernel afterwards
-  VC_CUDA(cudaMemsetAsync(b.counts + 6, 0, sizeof(int), s));
-  const int32_t* lists[2] = {b.small_list, b.reg_list};
-  const int hc[2] = {b.h_small, b.h_reg};
-  for (int c = 0; c < 2; ++c) {
-    if (hc[c] == 0) continue;
-    lp_thread_k<WT, ACC, FIRST><<<grid_for(hc[c], kTThreads, kSMs * 16), kTThreads, 0, s>>>(
-        lists[c], b.counts + 4 + c, g.off, g.adj, w, lab, lab_out, hv, g.vact, b.ovf_list, b.counts + 6);
+  if (b.h_small > 0) {
+    lp_reg_k<WT, ACC, FIRST, 16, 4><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
+        b.small_list, b.counts + 4, g.off, g.adj, w, lab, lab_out, hv, g.vact);
     count_launch();
     VC_CHECK_LAUNCH();
   }
-  if (b.h_small + b.h_reg > 0) {
-    lp_reg_k<WT, ACC, FIRST, 32, 4><<<kSMs * 4, kAggThreads, 0, s>>>(b.ovf_list, b.counts + 6, g.off, g.adj, w, lab,
-                                                                   lab_out, hv, g.vact);
+  if (b.h_reg > 0) {
+    lp_reg_k<WT, ACC, FIRST, 32, 4><<<grid_for(b.h_reg, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
+        b.reg_list, b.counts + 5, g.off, g.adj, w, lab, lab_out, hv, g.vact);
     count_launch();
     VC_CHECK_LAUNCH();
   }
