@@ -472,15 +472,14 @@ def main():
     # the handles below skip the one-time trial launches
     opts = vc.viecut_opts_init(stream=stream.cuda_stream, device=local, lp_group=st["first_group"],
                                emit_group=st["emit_group"])
-    # (a) the serving pattern: one handle, every step loads that step's graph from pinned
-    # host memory (viecut_load: copy + device check), runs, and reads cut and side back
+    # (a) the serving pattern: one handle, every step hands that step's graph from pinned
+    # host memory to viecut_solve (copy, device check, run; cut and side read back)
     hh = vc.viecut_create(h_off, h_adj, g.n, g.nnz, h_w, opts)
-    vc.viecut_run(hh, 1, 2, bits_host)  # warm-up
+    vc.viecut_solve(hh, h_off, h_adj, g.n, g.nnz, h_w, 1, 2, bits_host)  # warm-up
     barrier()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
-        vc.viecut_load(hh, h_off, h_adj, g.n, g.nnz, h_w)
-        vc.viecut_run(hh, 100 + i, 2, bits_host)
+        vc.viecut_solve(hh, h_off, h_adj, g.n, g.nnz, h_w, 100 + i, 2, bits_host)
     barrier()
     e2e_s = time.perf_counter() - t0
     vc.viecut_destroy(hh)
@@ -518,7 +517,7 @@ def main():
                      "round_ms": lp_round_ms, "algorithmic_bytes_per_round": lp_round_bytes},
         "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": e2e_steps, "api": "viecut_load + viecut_run on one handle, pinned host arrays",
+                "steps": e2e_steps, "api": "viecut_solve on one handle, pinned host arrays",
                 "fresh_handle_value": whole_job_rate(g.m, e2e_steps, world, fresh_s),
                 "fresh_handle_api": "viecut_create + viecut_run + viecut_destroy per step"},
         "gpu_launches": launches,

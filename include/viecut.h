@@ -118,6 +118,16 @@ int viecut_create_device(viecut_t** h, const int64_t* d_offsets, const int32_t* 
 int viecut_load(viecut_t* h, const int64_t* offsets, const int32_t* adj, int64_t n, int64_t m,
                 const int32_t* weights);
 
+/* viecut_load + viecut_run in one call, for a handle made by viecut_create: the host
+ * arrays are read only during the call.  With validate = 1 and weights that look
+ * like all 1 (the first 256 and 4096 evenly spaced ones are), the method runs with
+ * unit weights while the weights are copied and checked on a second stream, and runs
+ * again with the weights if the check finds one that is not 1; results are those of
+ * viecut_load + viecut_run either way.  EINVAL as viecut_load (the handle then holds
+ * no graph). */
+int viecut_solve(viecut_t* h, const int64_t* offsets, const int32_t* adj, int64_t n, int64_t m,
+                 const int32_t* weights, uint64_t seed, int32_t lp_iters, int64_t* cut_value, uint64_t* side_bits);
+
 /* Runs the method and waits for it.  cut_value (host) receives the cut; side_bits
  * (host, ceil(n/64) words, may be NULL) receives bit i = 1 iff input vertex i is on
  * the returned side; vertex 0 is never on it.  lp_iters >= 0 (the paper uses 2). */

@@ -86,6 +86,7 @@ SIGNATURES = [
     ("viecut_create_device", ctypes.c_int, [_pvp, _vp, _vp, _i64, _i64, _vp, _vp]),
     ("viecut_run", ctypes.c_int, [_vp, _u64, _i32, _vp, _vp]),
     ("viecut_load", ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _vp]),
+    ("viecut_solve", ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _vp, _u64, _i32, _vp, _vp]),
     ("viecut_run_device", ctypes.c_int, [_vp, _u64, _i32, _vp, _vp]),
     ("viecut_get_stats", ctypes.c_int, [_vp, _vp]),
     ("viecut_get_trace", ctypes.c_int, [_vp, _vp, _i64, _vp]),
@@ -179,6 +180,13 @@ def viecut_create_device(d_offsets, d_adj, n: int, m: int, d_weights, opts: viec
 
 def viecut_load(h, offsets, adj, n: int, m: int, weights) -> None:
     _check(lib().viecut_load(h, _ptr(offsets), _ptr(adj), n, m, _ptr(weights)))
+
+
+def viecut_solve(h, offsets, adj, n: int, m: int, weights, seed: int, lp_iters: int, side_bits=None) -> int:
+    cut = ctypes.c_int64()
+    _check(lib().viecut_solve(h, _ptr(offsets), _ptr(adj), n, m, _ptr(weights), seed & (2**64 - 1), lp_iters,
+                              ctypes.byref(cut), _ptr(side_bits)))
+    return int(cut.value)
 
 
 def viecut_run(h, seed: int, lp_iters: int, side_bits=None) -> int:
@@ -517,6 +525,16 @@ class MinCut:
         viecut_load(self.h, offsets, adj, n, m, weights)
         self.n, self.m = n, m
         self._keep = (offsets, adj, weights)
+
+    def solve(self, offsets, adj, weights, seed: int = 1, lp_iters: int = 2):
+        """Loads another host graph and runs on it in one call."""
+        n = int(offsets.shape[0] - 1)
+        m = int(adj.shape[0])
+        bits = np.zeros((n + 63) // 64, np.uint64)
+        cut = viecut_solve(self.h, offsets, adj, n, m, weights, seed, lp_iters, bits)
+        self.n, self.m = n, m
+        self._keep = (offsets, adj, weights)
+        return cut, bits
 
     def run(self, seed: int = 1, lp_iters: int = 2):
         bits = np.zeros((self.n + 63) // 64, np.uint64)

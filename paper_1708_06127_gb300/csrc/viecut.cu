@@ -41,12 +41,26 @@ __global__ void validate_k(int64_t n, int64_t m, const int64_t* __restrict__ off
       int32_t u = adj[e];
       if (u < 0 || u >= n) bad |= 4;
       else if (u == v) bad |= 8;
-      if (w[e] < 1) bad |= 16;
-      if (w[e] != 1) bad |= 32;  // not an error: the weights are not all 1
+      if (w) {  // null: the weights are checked apart (weight_check_k)
+        if (w[e] < 1) bad |= 16;
+        if (w[e] != 1) bad |= 32;  // not an error: the weights are not all 1
+      }
       if (e + 1 < b && adj[e + 1] <= u) bad |= 64;  // not an error: a list is not strictly increasing
     }
   }
   if (bad) atomicOr(err, bad);
+}
+
+// Weights alone, an entry per thread: 16 = a weight < 1, 32 = not all weights 1.
+__global__ void weight_check_k(int64_t m, const int32_t* __restrict__ w, int* err) {
+  int bad = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = w[e];
+    if (x < 1) bad |= 16;
+    if (x != 1) bad |= 32;
+  }
+  bad = (int)__reduce_or_sync(0xffffffffu, (unsigned)bad);
+  if ((threadIdx.x & 31) == 0 && bad) atomicOr(err, bad);
 }
 
 struct Handle {
@@ -61,6 +75,9 @@ struct Handle {
   bool simple = false;  // every input list strictly increasing (found by validation)
   bool host_input = false;  // the graph was copied from host arrays into in_*
   bool bound = false;       // a graph passed validation and may run
+  cudaStream_t cstream = nullptr;  // viecut_solve: the weights' copy and check
+  cudaEvent_t wdone = nullptr;
+  Buf werr;
   const int64_t* off0 = nullptr;
   const int32_t* adj0 = nullptr;
   const int32_t* w0 = nullptr;
@@ -70,20 +87,25 @@ struct Handle {
   std::vector<viecut_step> last_trace;
   ~Handle() {
     delete ws;
+    if (wdone) cudaEventDestroy(wdone);
+    if (cstream) cudaStreamDestroy(cstream);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
 };
 
-static void device_validate(Handle& H) {
+// with_weights = false: the weights are checked apart (viecut_solve); unit is then
+// left as the caller set it.
+static void device_validate(Handle& H, bool with_weights = true) {
   Workspace& W = *H.ws;
   int* err = &W.ctr()->changed;
   VC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), H.stream));
-  validate_k<<<grid_for(H.n, 256, kSMs * 8), 256, 0, H.stream>>>(H.n, H.m, H.off0, H.adj0, H.w0, err);
+  validate_k<<<grid_for(H.n, 256, kSMs * 8), 256, 0, H.stream>>>(H.n, H.m, H.off0, H.adj0,
+                                                                with_weights ? H.w0 : nullptr, err);
   count_launch();
   VC_CHECK_LAUNCH();
   W.read_state();
   int bad = W.h_counters->changed;
-  H.unit = (bad & 32) == 0;
+  if (with_weights) H.unit = (bad & 32) == 0;
   H.simple = (bad & 64) == 0;
   bad &= ~(32 | 64);
   if (bad) {
@@ -518,6 +540,84 @@ int viecut_run(viecut_t* h, uint64_t seed, int32_t lp_iters, int64_t* cut_value,
   VC_CUDA(cudaMemcpyAsync(cut_value, H.out_cut.p, sizeof(int64_t), cudaMemcpyDeviceToHost, H.stream));
   if (side_bits)
     VC_CUDA(cudaMemcpyAsync(side_bits, H.out_bits.p, sizeof(uint64_t) * ((H.n + 63) / 64), cudaMemcpyDeviceToHost,
+                            H.stream));
+  VC_CUDA(cudaStreamSynchronize(H.stream));
+  VC_API_END
+}
+
+// True when the first 256 weights and 4096 evenly spaced ones are all 1.
+static bool sampled_unit(const int32_t* w, int64_t m) {
+  for (int64_t e = 0; e < m && e < 256; ++e)
+    if (w[e] != 1) return false;
+  const int64_t stride = m / 4096 > 0 ? m / 4096 : 1;
+  for (int64_t e = 0; e < m; e += stride)
+    if (w[e] != 1) return false;
+  return true;
+}
+
+int viecut_solve(viecut_t* h, const int64_t* offsets, const int32_t* adj, int64_t n, int64_t m,
+                 const int32_t* weights, uint64_t seed, int32_t lp_iters, int64_t* cut_value, uint64_t* side_bits) {
+  VC_API_BEGIN
+  if (!h || !cut_value) throw Error{VIECUT_EINVAL, "null argument"};
+  vc::Handle& H = h->h;
+  if (!H.host_input) throw Error{VIECUT_EINVAL, "viecut_solve needs a handle made by viecut_create"};
+  if (lp_iters < 0) throw Error{VIECUT_EINVAL, "lp_iters must be >= 0"};
+  check_shape(n, m, offsets, adj, weights);
+  VC_CUDA(cudaSetDevice(H.device));
+  VC_CUDA(cudaStreamSynchronize(H.stream));
+  long long* d_cut = H.out_cut.ensure_n<long long>(1);
+  if (H.validate != 1 || m == 0 || !sampled_unit(weights, m)) {
+    bind_graph(H, true, offsets, adj, weights, n, m);
+    vc::run_impl(H, seed, lp_iters, d_cut, H.out_bits.ensure_n<unsigned long long>((n + 63) / 64));
+  } else {
+    // the weights look like all 1: run with unit weights while they are copied and
+    // checked on a second stream; run again with weights if the check disagrees
+    H.bound = false;
+    H.n = n;
+    H.m = m;
+    H.host_input = true;
+    H.off0 = H.in_off.ensure_n<int64_t>(n + 1);
+    H.adj0 = H.in_adj.ensure_n<int32_t>(m);
+    H.w0 = H.in_w.ensure_n<int32_t>(m);
+    if (!H.cstream) VC_CUDA(cudaStreamCreateWithFlags(&H.cstream, cudaStreamNonBlocking));
+    if (!H.wdone) VC_CUDA(cudaEventCreateWithFlags(&H.wdone, cudaEventDisableTiming));
+    int* werr = H.werr.ensure_n<int>(1);
+    VC_CUDA(cudaMemcpyAsync((void*)H.off0, offsets, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, H.stream));
+    VC_CUDA(cudaMemcpyAsync((void*)H.adj0, adj, sizeof(int32_t) * m, cudaMemcpyHostToDevice, H.stream));
+    VC_CUDA(cudaMemsetAsync(werr, 0, sizeof(int), H.cstream));
+    VC_CUDA(cudaMemcpyAsync((void*)H.w0, weights, sizeof(int32_t) * m, cudaMemcpyHostToDevice, H.cstream));
+    vc::weight_check_k<<<vc::grid_for(m, 256, vc::kSMs * 8), 256, 0, H.cstream>>>(m, H.w0, werr);
+    vc::count_launch();
+    VC_CHECK_LAUNCH();
+    VC_CUDA(cudaEventRecord(H.wdone, H.cstream));
+    int h_werr = 0;
+    try {
+      H.ws->ensure_vertices(n);
+      H.ws->ensure_entries(m, n);
+      H.out_bits.ensure_n<unsigned long long>((n + 63) / 64);
+      vc::device_validate(H, false);
+      H.unit = true;
+      H.bound = true;
+      vc::run_impl(H, seed, lp_iters, d_cut, H.out_bits.as<unsigned long long>());
+      VC_CUDA(cudaMemcpyAsync(&h_werr, werr, sizeof(int), cudaMemcpyDeviceToHost, H.cstream));
+      VC_CUDA(cudaStreamSynchronize(H.cstream));
+    } catch (...) {
+      cudaStreamSynchronize(H.cstream);  // the copy reads the caller's array
+      H.bound = false;
+      throw;
+    }
+    if (h_werr & 16) {
+      H.bound = false;
+      throw Error{VIECUT_EINVAL, "invalid graph: weight < 1;"};
+    }
+    if (h_werr & 32) {
+      H.unit = false;
+      vc::run_impl(H, seed, lp_iters, d_cut, H.out_bits.as<unsigned long long>());
+    }
+  }
+  VC_CUDA(cudaMemcpyAsync(cut_value, d_cut, sizeof(int64_t), cudaMemcpyDeviceToHost, H.stream));
+  if (side_bits)
+    VC_CUDA(cudaMemcpyAsync(side_bits, H.out_bits.p, sizeof(uint64_t) * ((n + 63) / 64), cudaMemcpyDeviceToHost,
                             H.stream));
   VC_CUDA(cudaStreamSynchronize(H.stream));
   VC_API_END

@@ -317,3 +317,42 @@ def test_autotuned_groups_on_a_large_graph():
     assert st["first_group"] in (8, 16, 32) and st["emit_group"] in (8, 16, 32)
     for cut, bits in (first, again):
         assert cut == ref.cut and np.array_equal(bits, ref.side_bits)
+
+
+def hidden_pair(g, value, stride):
+    """A copy of g whose one symmetric entry pair (both positions >= 256 and off the
+    multiples of stride) gets weight value."""
+    w = g.w.copy()
+    for v in range(g.n // 2, g.n):
+        for e in range(g.offsets[v], g.offsets[v + 1]):
+            u = int(g.adj[e])
+            r = [x for x in range(g.offsets[u], g.offsets[u + 1]) if g.adj[x] == v][0]
+            if min(e, r) >= 256 and e % stride and r % stride:
+                w[e] = w[r] = value
+                return gg.Graph(g.offsets, g.adj, w, g.name + f"+pair{value}")
+    raise AssertionError("no pair found")
+
+
+def test_solve_equals_load_and_run():
+    """viecut_solve on unit weights runs with unit weights while the weights are checked;
+    on weighted graphs it does not speculate; a unit-looking graph with one hidden
+    heavier pair is run again with weights; a hidden zero weight is refused and leaves
+    the handle without a graph.  Results always equal the oracle's."""
+    g_unit = gg.workload_rhg_small(5)
+    stride = max(1, g_unit.nnz // 4096)
+    cases = [g_unit, gg.with_pair_weights(gg.core_lcc(gg.rhg(1 << 13, 24, 9), 0), 9, 1, 10),
+             hidden_pair(g_unit, 3, stride), H.pr2_counterexample()]
+    with vc.MinCut(cases[0].offsets, cases[0].adj, cases[0].w, n0=64) as mc:
+        for i, g in enumerate(cases + cases[::-1]):
+            cut, bits = mc.solve(g.offsets, g.adj, g.w, 11 + i, 2)
+            ref = oracle.viecut(g.offsets, g.adj, g.w, seed=11 + i, lp_iters=2, n0=64)
+            assert cut == ref.cut and np.array_equal(bits, ref.side_bits), (i, g.name)
+            st = mc.stats()
+            assert st["trace_len"] == len(ref.trace)
+        bad = hidden_pair(g_unit, 0, stride)
+        with pytest.raises(vc.ViecutError) as e:
+            mc.solve(bad.offsets, bad.adj, bad.w, 1, 2)
+        assert e.value.code == vc.VIECUT_EINVAL and "weight" in str(e.value)
+        with pytest.raises(vc.ViecutError) as e:
+            mc.run(1, 2)
+        assert e.value.code == vc.VIECUT_EINVAL
