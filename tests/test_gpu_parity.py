@@ -347,8 +347,7 @@ def test_solve_equals_load_and_run():
             cut, bits = mc.solve(g.offsets, g.adj, g.w, 11 + i, 2)
             ref = oracle.viecut(g.offsets, g.adj, g.w, seed=11 + i, lp_iters=2, n0=64)
             assert cut == ref.cut and np.array_equal(bits, ref.side_bits), (i, g.name)
-            st = mc.stats()
-            assert st["trace_len"] == len(ref.trace)
+            assert mc.trace() == ref.trace, (i, g.name)
         bad = hidden_pair(g_unit, 0, stride)
         with pytest.raises(vc.ViecutError) as e:
             mc.solve(bad.offsets, bad.adj, bad.w, 1, 2)
