@@ -950,7 +950,7 @@ struct Server {
 
 static int64_t request_estimate(int64_t n, int64_t m) {
   // union CSR + workspace share per entry and per vertex (see DESIGN: memory layout)
-  return 96 * (m + n) + 64 * n + (1 << 16);
+  return 96 * (m + n) + 112 * n + (1 << 16);
 }
 
 static int64_t arena_alloc(Server& S, int64_t n) {

@@ -45,9 +45,8 @@ void relabel(const int32_t* lab, int64_t n, int32_t* cid, ContractScratch& cs, i
 // One thread per fine vertex copies its pre-merged list (two entries on average at the
 // level-0 contraction) into the contiguous pair arrays.
 __global__ void build_pairs_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ cid,
-                              const int32_t* __restrict__ cnt, const long long* __restrict__ pos,
-                              const int32_t* __restrict__ tkey, const long long* __restrict__ tval, int bits,
-                              unsigned long long* __restrict__ keys, long long* __restrict__ vals) {
+                              const int32_t* __restrict__ cnt, const long long* __restrict__ pos, PairOut in,
+                              int bits, unsigned long long* __restrict__ keys, long long* __restrict__ vals) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int k = cnt[v];
     if (k == 0) continue;
@@ -55,16 +54,19 @@ __global__ void build_pairs_k(int64_t n, const int64_t* __restrict__ off, const 
     const long long dst = pos[v];
     const unsigned long long hi = (unsigned long long)cid[v] << bits;
     for (int j = 0; j < k; ++j) {
-      keys[dst + j] = hi | (unsigned long long)(uint32_t)tkey[src + j];
-      vals[dst + j] = tval[src + j];
+      int32_t kk;
+      long long x;
+      in.get(v, src, j, &kk, &x);
+      keys[dst + j] = hi | (unsigned long long)(uint32_t)kk;
+      vals[dst + j] = x;
     }
   }
 }
 
 void build_pairs(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int bits,
                  unsigned long long* keys, long long* vals, cudaStream_t s) {
-  build_pairs_k<<<grid_for(g.n, 256, kSMs * 8), 256, 0, s>>>(g.n, g.off, cid, cs.cnt, cs.pos, cs.tmp_key,
-                                                           cs.tmp_val, bits, keys, vals);
+  const PairOut in{cs.tmp_key, cs.tmp_val, cs.cmp_key, cs.cmp_val};
+  build_pairs_k<<<grid_for(g.n, 256, kSMs * 8), 256, 0, s>>>(g.n, g.off, cid, cs.cnt, cs.pos, in, bits, keys, vals);
   count_launch();
   VC_CHECK_LAUNCH();
 }
@@ -195,9 +197,7 @@ __global__ void __launch_bounds__(256) cluster_count_k(int64_t n, const int32_t*
 // into their cluster's segment (cursor = the segments' running write positions).
 __global__ void __launch_bounds__(256) cluster_scatter_k(int64_t n, const int64_t* __restrict__ off,
                                                          const int32_t* __restrict__ cid,
-                                                         const int32_t* __restrict__ cnt,
-                                                         const int32_t* __restrict__ tkey,
-                                                         const long long* __restrict__ tval,
+                                                         const int32_t* __restrict__ cnt, PairOut in,
                                                          long long* __restrict__ cursor, int32_t* __restrict__ seg_key,
                                                          long long* __restrict__ seg_val) {
   __shared__ int s_k[8][32];
@@ -215,18 +215,22 @@ __global__ void __launch_bounds__(256) cluster_scatter_k(int64_t n, const int64_
     if (c >= 0 && lane == leader) at = atomicAdd((unsigned long long*)&cursor[c], (unsigned long long)t);
     at = __shfl_sync(0xffffffffu, at, leader);
     if (c >= 0) {
-      const int64_t src = off[v];
       const long long dst = at + b;
-      // four pairs in flight at a time (most vertices have one to four)
-      for (int j0 = 0; j0 < k; j0 += 4) {
-        int32_t kk[4];
-        long long vv[4];
+      // the first kPairSlots pairs from the dense strip, all in flight at once
+      int32_t kk[kPairSlots];
+      long long vv[kPairSlots];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (j0 + j < k) { kk[j] = tkey[src + j0 + j]; vv[j] = tval[src + j0 + j]; }
+      for (int j = 0; j < kPairSlots; ++j)
+        if (j < k) { kk[j] = in.ckey[v * kPairSlots + j]; vv[j] = in.cval[v * kPairSlots + j]; }
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (j0 + j < k) { seg_key[dst + j0 + j] = kk[j]; seg_val[dst + j0 + j] = vv[j]; }
+      for (int j = 0; j < kPairSlots; ++j)
+        if (j < k) { seg_key[dst + j] = kk[j]; seg_val[dst + j] = vv[j]; }
+      if (k > kPairSlots) {
+        const int64_t src = off[v];
+        for (int j = kPairSlots; j < k; ++j) {
+          seg_key[dst + j] = in.tkey[src + j];
+          seg_val[dst + j] = in.tval[src + j];
+        }
       }
     }
   }
@@ -391,7 +395,8 @@ void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch
   exclusive_scan<int, long long>(ccount, cbase, c, cbase + c, cs.scan_scr, s);
   VC_CUDA(cudaMemcpyAsync(cursor, cbase, sizeof(long long) * c, cudaMemcpyDeviceToDevice, s));
   const int gv = grid_for(g.n, 256, kSMs * 8), gc = grid_for(c, 8, kSMs * 16);
-  cluster_scatter_k<<<gv, 256, 0, s>>>(g.n, g.off, cid, cs.cnt, cs.tmp_key, cs.tmp_val, cursor, seg_key, seg_val);
+  const PairOut in{cs.tmp_key, cs.tmp_val, cs.cmp_key, cs.cmp_val};
+  cluster_scatter_k<<<gv, 256, 0, s>>>(g.n, g.off, cid, cs.cnt, in, cursor, seg_key, seg_val);
   cluster_merge_k<<<gc, 256, 0, s>>>(c, cbase, seg_key, seg_val, ccount);
   count_launch(2);
   VC_CHECK_LAUNCH();

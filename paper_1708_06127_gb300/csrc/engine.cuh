@@ -67,7 +67,7 @@ struct Workspace {
   Buf deg, labA, labB, map0, cidT, cur1, side1, flags, rank, cnt, pos, scan64, scan32, hv;
   Buf partner, pw, parent, slist, rlist, mlist, blist, glist, bcounts, noi_r, noi_seen;
   // entry-sized
-  Buf tmpK, tmpV;
+  Buf tmpK, tmpV, cmpK, cmpV;
   // pair-sized
   Buf keysA, keysB, valsA, valsB, hist, heads, hpos, cvT, ccur;
   // coarse graphs (ping-pong)
@@ -125,6 +125,8 @@ struct Workspace {
     parent.ensure_n<int32_t>(n);
     slist.ensure_n<int32_t>(n);
     rlist.ensure_n<int32_t>(n);
+    cmpK.ensure_n<int32_t>(kPairSlots * n);
+    cmpV.ensure_n<long long>(kPairSlots * n);
     mlist.ensure_n<int32_t>(n);
     blist.ensure_n<int32_t>(n);
     glist.ensure_n<int32_t>(n);
@@ -225,13 +227,13 @@ struct Workspace {
       lp_round(g, bins, gt, nullptr, out, h, s, t);
     });
   }
-  void tune_emit(const GraphView& g, const int32_t* cid, int32_t* k, long long* v, int32_t* c) {
+  void tune_emit(const GraphView& g, const int32_t* cid, const PairOut& po, int32_t* c) {
     if (tuned_emit || g.n < kTuneMinN || bins.h_block == 0) return;
     tuned_emit = true;
     tune.emit_group = pick_group([&](int G) {
       LpTuning t = tune;
       t.emit_group = G;
-      emit_cross(g, bins, gt, cid, k, v, c, s, t);
+      emit_cross(g, bins, gt, cid, po, c, s, t);
     });
   }
 
@@ -303,11 +305,14 @@ struct Workspace {
     cs.pos = pos.as<long long>();
     cs.tmp_key = tmpK.as<int32_t>();
     cs.tmp_val = tmpV.as<long long>();
+    cs.cmp_key = cmpK.as<int32_t>();
+    cs.cmp_val = cmpV.as<long long>();
     cs.scan_scr = scan64.as<long long>();
     cs.scan_scr32 = scan32.as<int>();
     relabel(labels, g.n, cid_out, cs, &ctr()->c, s);
-    tune_emit(g, cid_out, cs.tmp_key, cs.tmp_val, cs.cnt);
-    emit_cross(g, bins, gt, cid_out, cs.tmp_key, cs.tmp_val, cs.cnt, s, tune);
+    const PairOut po{cs.tmp_key, cs.tmp_val, cs.cmp_key, cs.cmp_val};
+    tune_emit(g, cid_out, po, cs.cnt);
+    emit_cross(g, bins, gt, cid_out, po, cs.cnt, s, tune);
     // pairs per cluster (flags is free again after the relabel)
     int32_t* ccount = cs.flags;
     VC_CUDA(cudaMemsetAsync(&ctr()->maxt, 0, sizeof(int), s));

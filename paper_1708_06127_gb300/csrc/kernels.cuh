@@ -91,11 +91,40 @@ struct LpTuning {
 void lp_round(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* lab_in,
               int32_t* lab_out, const unsigned long long* hv, cudaStream_t s, const LpTuning& tune = LpTuning());
 
+// Where the pre-merged pairs of fine vertex v go: pair i < kPairSlots at
+// v kPairSlots + i of a dense strip (ckey, cval), so that readers of the few pairs of
+// consecutive vertices touch consecutive memory; pair i >= kPairSlots at off[v] + i of
+// (tkey, tval), which always has room (v has at most deg(v) pairs).
+constexpr int kPairSlots = 4;
+struct PairOut {
+  int32_t* tkey;
+  long long* tval;
+  int32_t* ckey;
+  long long* cval;
+  __device__ __forceinline__ void put(int64_t v, int64_t beg, int i, int32_t k, long long x) const {
+    if (i < kPairSlots) {
+      ckey[v * kPairSlots + i] = k;
+      cval[v * kPairSlots + i] = x;
+    } else {
+      tkey[beg + i] = k;
+      tval[beg + i] = x;
+    }
+  }
+  __device__ __forceinline__ void get(int64_t v, int64_t beg, int i, int32_t* k, long long* x) const {
+    if (i < kPairSlots) {
+      *k = ckey[v * kPairSlots + i];
+      *x = cval[v * kPairSlots + i];
+    } else {
+      *k = tkey[beg + i];
+      *x = tval[beg + i];
+    }
+  }
+};
+
 // Pre-merge for contraction: for each vertex v, the distinct coarse neighbours cu =
-// cid[u] != cid[v] with summed weights, written at [off[v], off[v] + cnt[v]).
-void emit_cross(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* cid,
-                int32_t* tmp_key, long long* tmp_val, int32_t* cnt, cudaStream_t s,
-                const LpTuning& tune = LpTuning());
+// cid[u] != cid[v] with summed weights, cnt[v] pairs placed as PairOut says.
+void emit_cross(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* cid, const PairOut& out,
+                int32_t* cnt, cudaStream_t s, const LpTuning& tune = LpTuning());
 
 // ------------------------------------------------------------------ contraction
 struct ContractScratch {
@@ -105,6 +134,8 @@ struct ContractScratch {
   long long* pos;        // [n + 1]
   int32_t* tmp_key;      // [nnz]
   long long* tmp_val;    // [nnz]
+  int32_t* cmp_key;      // [kPairSlots n]
+  long long* cmp_val;    // [kPairSlots n]
   long long* scan_scr;   // scan scratch (sized for max(n, nnz))
   int* scan_scr32;
 };

@@ -450,8 +450,7 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restr
                                                           const int* __restrict__ count_ptr,
                                                           const int64_t* __restrict__ off,
                                                           const int32_t* __restrict__ adj, const WT* __restrict__ w,
-                                                          const int32_t* __restrict__ cid,
-                                                          int32_t* __restrict__ tkey, long long* __restrict__ tval,
+                                                          const int32_t* __restrict__ cid, PairOut out,
                                                           int32_t* __restrict__ cnt) {
   const int lane = threadIdx.x & 31, glane = lane & (G - 1), gi = lane / G;
   const unsigned gmask = group_mask<G>(lane);
@@ -471,15 +470,9 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restr
     long long pv = 0;
     reg_visit<WT, long long, G, S>(L, gmask, [&](int32_t kk, long long t) {
       if (glane == (made & (G - 1))) { pk = kk; pv = t; }
-      if ((++made & (G - 1)) == 0) {
-        tkey[beg + made - G + glane] = pk;
-        tval[beg + made - G + glane] = pv;
-      }
+      if ((++made & (G - 1)) == 0) out.put(v, beg, made - G + glane, pk, pv);
     });
-    if (glane < (made & (G - 1))) {
-      tkey[beg + (made & ~(G - 1)) + glane] = pk;
-      tval[beg + (made & ~(G - 1)) + glane] = pv;
-    }
+    if (glane < (made & (G - 1))) out.put(v, beg, (made & ~(G - 1)) + glane, pk, pv);
     if (mine && glane == 0) cnt[v] = made;
   });
 }
@@ -508,23 +501,23 @@ void launch_lp_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t
 }
 
 template <typename WT>
-void launch_emit_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t* cid, int32_t* tkey,
-                     long long* tval, int32_t* cnt, cudaStream_t s) {
+void launch_emit_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t* cid, const PairOut& out,
+                     int32_t* cnt, cudaStream_t s) {
   if (b.h_small > 0) {
     emit_reg_k<WT, 16, 4><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
-        b.small_list, b.counts + 4, g.off, g.adj, w, cid, tkey, tval, cnt);
+        b.small_list, b.counts + 4, g.off, g.adj, w, cid, out, cnt);
     count_launch();
     VC_CHECK_LAUNCH();
   }
   if (b.h_reg > 0) {
     emit_reg_k<WT, 32, 4><<<grid_for(b.h_reg, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
-        b.reg_list, b.counts + 5, g.off, g.adj, w, cid, tkey, tval, cnt);
+        b.reg_list, b.counts + 5, g.off, g.adj, w, cid, out, cnt);
     count_launch();
     VC_CHECK_LAUNCH();
   }
   if (b.h_mid > 0) {
     emit_reg_k<WT, 32, kMidMaxDeg / 32><<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
-        b.mid_list, b.counts + 0, g.off, g.adj, w, cid, tkey, tval, cnt);
+        b.mid_list, b.counts + 0, g.off, g.adj, w, cid, out, cnt);
     count_launch();
     VC_CHECK_LAUNCH();
   }
@@ -645,13 +638,13 @@ __global__ void __launch_bounds__(kAggThreads) lp_first_simple_block_k(const int
 // Pre-merge without a table: within each 32-entry chunk the warp walks the distinct
 // foreign cluster ids (a chunk touches few of them: most neighbours share v's own
 // cluster), summing each one's weight with a ballot (unit weights) or a warp sum, and
-// the first lane holding the id writes the pair; the sort that follows merges equal
-// ids across chunks and across vertices.  `next_slot` yields the output position.
+// the first lane holding the id writes the pair; the cluster merge that follows merges
+// equal ids across chunks and across vertices.  `next_slot` yields the pair's index.
 template <typename WT, int G, typename SLOT>
 __device__ __forceinline__ void emit_chunk(int64_t e, int64_t end, const int32_t* __restrict__ adj,
                                            const WT* __restrict__ w, const int32_t* __restrict__ cid, int32_t own,
-                                           int lane, unsigned gmask, int32_t* __restrict__ tkey,
-                                           long long* __restrict__ tval, SLOT next_slot) {
+                                           int lane, unsigned gmask, const PairOut& out, int64_t v, int64_t beg,
+                                           SLOT next_slot) {
   int32_t k = -1;
   long long wt = 0;
   bool use = false;
@@ -674,11 +667,8 @@ __device__ __forceinline__ void emit_chunk(int64_t e, int64_t end, const int32_t
 #pragma unroll
       for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(gmask, sum, o);
     }
-    const int64_t j = next_slot(leader);
-    if (lane == leader) {
-      tkey[j] = key;
-      tval[j] = sum;
-    }
+    const int i = next_slot(leader);
+    if (lane == leader) out.put(v, beg, i, key, sum);
     todo &= ~peers;
   }
 }
@@ -690,8 +680,8 @@ __global__ void __launch_bounds__(kAggThreads) emit_warp_k(const int32_t* __rest
                                                            const int* __restrict__ count_ptr,
                                                            const int64_t* __restrict__ off,
                                                            const int32_t* __restrict__ adj, const WT* __restrict__ w,
-                                                           const int32_t* __restrict__ cid, int32_t* __restrict__ tkey,
-                                                           long long* __restrict__ tval, int32_t* __restrict__ cnt) {
+                                                           const int32_t* __restrict__ cid, PairOut out,
+                                                           int32_t* __restrict__ cnt) {
   const int lane = threadIdx.x & 31, glane = lane & (G - 1);
   const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
@@ -703,8 +693,8 @@ __global__ void __launch_bounds__(kAggThreads) emit_warp_k(const int32_t* __rest
     int made = 0;  // group-uniform
     if (own >= 0)
       for (int64_t base = beg; base < end; base += G)
-        emit_chunk<WT, G>(base + glane, end, adj, w, cid, own, lane, gmask, tkey, tval,
-                          [&](int) { return beg + made++; });
+        emit_chunk<WT, G>(base + glane, end, adj, w, cid, own, lane, gmask, out, v, beg,
+                          [&](int) { return made++; });
     if (glane == 0) cnt[v] = made;
   }
 }
@@ -715,8 +705,7 @@ __global__ void __launch_bounds__(kAggThreads) emit_block_k(const int32_t* __res
                                                             const int64_t* __restrict__ off,
                                                             const int32_t* __restrict__ adj,
                                                             const WT* __restrict__ w, const int32_t* __restrict__ cid,
-                                                            int32_t* __restrict__ tkey, long long* __restrict__ tval,
-                                                            int32_t* __restrict__ cnt) {
+                                                            PairOut out, int32_t* __restrict__ cnt) {
   __shared__ int s_made;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int count = *count_ptr;
@@ -728,10 +717,10 @@ __global__ void __launch_bounds__(kAggThreads) emit_block_k(const int32_t* __res
     __syncthreads();
     if (own >= 0)
       for (int64_t base = beg + 32 * wib; base < end; base += 32 * kWarpsPerBlock)
-        emit_chunk<WT, 32>(base + lane, end, adj, w, cid, own, lane, 0xffffffffu, tkey, tval, [&](int leader) {
+        emit_chunk<WT, 32>(base + lane, end, adj, w, cid, own, lane, 0xffffffffu, out, v, beg, [&](int leader) {
           int at = 0;
           if (lane == leader) at = atomicAdd(&s_made, 1);
-          return beg + __shfl_sync(0xffffffffu, at, leader);
+          return __shfl_sync(0xffffffffu, at, leader);
         });
     __syncthreads();
     if (threadIdx.x == 0) cnt[v] = s_made;
@@ -863,25 +852,25 @@ void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const 
 }
 
 template <typename WT>
-void launch_emit(const GraphView& g, const Bins& b, const int32_t* cid, int32_t* tkey, long long* tval,
-                 int32_t* cnt, int G, cudaStream_t s) {
+void launch_emit(const GraphView& g, const Bins& b, const int32_t* cid, const PairOut& out, int32_t* cnt, int G,
+                 cudaStream_t s) {
   const WT* w = (const WT*)g.w;
-  launch_emit_reg<WT>(g, b, w, cid, tkey, tval, cnt, s);
+  launch_emit_reg<WT>(g, b, w, cid, out, cnt, s);
   if (b.h_block > 0) {  // 513..4096 entries: G lanes per vertex, in G-entry chunks
     const int grid = grid_for(b.h_block, kAggThreads / G, kSMs * 16);
     const int* cp = b.counts + 1;
     if (G == 8)
-      emit_warp_k<WT, 8><<<grid, kAggThreads, 0, s>>>(b.block_list, cp, g.off, g.adj, w, cid, tkey, tval, cnt);
+      emit_warp_k<WT, 8><<<grid, kAggThreads, 0, s>>>(b.block_list, cp, g.off, g.adj, w, cid, out, cnt);
     else if (G == 16)
-      emit_warp_k<WT, 16><<<grid, kAggThreads, 0, s>>>(b.block_list, cp, g.off, g.adj, w, cid, tkey, tval, cnt);
+      emit_warp_k<WT, 16><<<grid, kAggThreads, 0, s>>>(b.block_list, cp, g.off, g.adj, w, cid, out, cnt);
     else
-      emit_warp_k<WT, 32><<<grid, kAggThreads, 0, s>>>(b.block_list, cp, g.off, g.adj, w, cid, tkey, tval, cnt);
+      emit_warp_k<WT, 32><<<grid, kAggThreads, 0, s>>>(b.block_list, cp, g.off, g.adj, w, cid, out, cnt);
     count_launch();
     VC_CHECK_LAUNCH();
   }
   if (b.h_global > 0) {
     emit_block_k<WT><<<grid_for(b.h_global, 1, kSMs * 4), kAggThreads, 0, s>>>(b.global_list, b.counts + 2, g.off,
-                                                                               g.adj, w, cid, tkey, tval, cnt);
+                                                                               g.adj, w, cid, out, cnt);
     count_launch();
     VC_CHECK_LAUNCH();
   }
@@ -905,14 +894,14 @@ void lp_round(const GraphView& g, const Bins& b, const GlobalTables& gt, const i
   }
 }
 
-void emit_cross(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* cid,
-                int32_t* tmp_key, long long* tmp_val, int32_t* cnt, cudaStream_t s, const LpTuning& tune) {
+void emit_cross(const GraphView& g, const Bins& b, const GlobalTables& gt, const int32_t* cid, const PairOut& out,
+                int32_t* cnt, cudaStream_t s, const LpTuning& tune) {
   (void)gt;
   if (g.n <= 0) return;
   const int G = tune.emit_group;
-  if (g.unit) launch_emit<UnitW>(g, b, cid, tmp_key, tmp_val, cnt, G, s);
-  else if (g.wbytes == 4) launch_emit<int32_t>(g, b, cid, tmp_key, tmp_val, cnt, G, s);
-  else launch_emit<long long>(g, b, cid, tmp_key, tmp_val, cnt, G, s);
+  if (g.unit) launch_emit<UnitW>(g, b, cid, out, cnt, G, s);
+  else if (g.wbytes == 4) launch_emit<int32_t>(g, b, cid, out, cnt, G, s);
+  else launch_emit<long long>(g, b, cid, out, cnt, G, s);
 }
 
 }  // namespace vc

@@ -19,6 +19,7 @@
 namespace vc {
 
 constexpr int kNoiThreads = 512;
+constexpr int kNoiWarpMax = 256;  // kernels up to this size scan with one warp
 
 __device__ __forceinline__ int sfind(volatile int* p, int x) {
   for (;;) {
@@ -105,25 +106,50 @@ __device__ __forceinline__ void noi_dense_body(int n, const int64_t* __restrict_
     const long long lam = *io.lam;
     for (int k = tid; k < nk; k += T) { r[k] = 0; seen[k] = 0; parent[k] = k; }
     __syncthreads();
-    for (int step = 0; step < nk; ++step) {
+    if (nk <= kNoiWarpMax) {
+      // small kernels: warp 0 alone runs the scan (no block barrier per step)
       if (wid == 0) {
-        int x = warp_argmax_unseen(r, seen, nk);
-        if (lane == 0) { s_x = x; seen[x] = 1; }
-      }
-      __syncthreads();
-      const int x = s_x;
-      const long long* row = M + (int64_t)x * nk;
-      for (int y = tid; y < nk; y += T) {
-        if (!seen[y]) {
-          long long c = row[y];
-          if (c != 0) {
-            long long ry = r[y] + c;
-            r[y] = ry;
-            if (ry >= lam) sunite(parent, x, y);
+        for (int step = 0; step < nk; ++step) {
+          const int x = warp_argmax_unseen(r, seen, nk);
+          __syncwarp();
+          if (lane == 0) seen[x] = 1;
+          __syncwarp();
+          const long long* row = M + (int64_t)x * nk;
+          for (int y = lane; y < nk; y += 32) {
+            if (!seen[y]) {
+              const long long c = row[y];
+              if (c != 0) {
+                const long long ry = r[y] + c;
+                r[y] = ry;
+                if (ry >= lam) sunite(parent, x, y);
+              }
+            }
           }
+          __syncwarp();
         }
       }
       __syncthreads();
+    } else {
+      for (int step = 0; step < nk; ++step) {
+        if (wid == 0) {
+          int x = warp_argmax_unseen(r, seen, nk);
+          if (lane == 0) { s_x = x; seen[x] = 1; }
+        }
+        __syncthreads();
+        const int x = s_x;
+        const long long* row = M + (int64_t)x * nk;
+        for (int y = tid; y < nk; y += T) {
+          if (!seen[y]) {
+            long long c = row[y];
+            if (c != 0) {
+              long long ry = r[y] + c;
+              r[y] = ry;
+              if (ry >= lam) sunite(parent, x, y);
+            }
+          }
+        }
+        __syncthreads();
+      }
     }
     // roots -> ranks (every root is the minimum of its component)
     for (int k = tid; k < nk; k += T) root[k] = sfind(parent, k);

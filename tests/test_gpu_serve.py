@@ -73,7 +73,7 @@ def test_serve_staggered_arrivals_equal_alone():
 
 def test_serve_concurrent_submitters_and_small_budget():
     reqs = request_mix(24, 9)
-    budget = 3 * max(96 * (g.nnz + g.n) + 64 * g.n + (1 << 16) for g, _ in reqs)
+    budget = 3 * max(96 * (g.nnz + g.n) + 112 * g.n + (1 << 16) for g, _ in reqs)
     out = {}
     with vc.Server(hbm_budget_bytes=budget, max_slots=16, n0=64) as srv:
         def submitter(part):
