@@ -19,7 +19,7 @@
 namespace vc {
 
 constexpr int kNoiThreads = 512;
-constexpr int kNoiWarpMax = 256;  // kernels up to this size scan with one warp
+constexpr int kNoiWarpMax = 32;  // kernels up to this size scan with one warp
 
 __device__ __forceinline__ int sfind(volatile int* p, int x) {
   for (;;) {
@@ -251,19 +251,17 @@ __global__ void __launch_bounds__(kNoiThreads) noi_dense_k(int n, const int64_t*
                                                            long long* M0, long long* M1, int32_t* curK,
                                                            unsigned char* sideK, DevState* st, TraceStep* trace,
                                                            int trace_cap, int level, int in_smem) {
-  // small kernels keep both matrices in shared memory (each round reads a matrix row
-  // per scan step; shared memory answers in a few cycles)
+  // small kernels keep the first round's matrix in shared memory (a round reads one
+  // matrix row per scan step; shared memory answers in a few cycles); later rounds
+  // are smaller and alternate between it and the global one
   extern __shared__ __align__(16) long long noi_dyn[];
-  if (in_smem) {
-    M0 = noi_dyn;
-    M1 = noi_dyn + (int64_t)n * n;
-  }
+  if (in_smem) M0 = noi_dyn;
   NoiIO io{&st->lambda_hat, &st->best_kind, &st->n, &st->nnz, &st->dmin, &st->argmin, &st->trace_len,
            trace, trace_cap, level};
   noi_dense_body<WT>(n, off, adj, w, 0, M0, M1, curK, sideK, io);
 }
 
-constexpr int kNoiSmemMaxN = 96;  // 2 x 96^2 x 8 B = 144 KiB of shared memory
+constexpr int kNoiSmemMaxN = 160;  // 160^2 x 8 B = 200 KiB of shared memory
 
 template <typename WT>
 static void noi_dense_launch(const GraphView& g, long long* M0, long long* M1, int32_t* curK, unsigned char* sideK,
@@ -272,14 +270,14 @@ static void noi_dense_launch(const GraphView& g, long long* M0, long long* M1, i
   static std::unordered_map<int, bool> ready;  // per device: the shared-memory limit was raised
   const int n = (int)g.n;
   const bool small = n <= kNoiSmemMaxN;
-  const size_t smem = small ? sizeof(long long) * 2 * (size_t)n * n : 0;
+  const size_t smem = small ? sizeof(long long) * (size_t)n * n : 0;
   if (small) {
     int dev = 0;
     VC_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lk(mu);
     if (!ready[dev]) {
       VC_CUDA(cudaFuncSetAttribute(noi_dense_k<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(sizeof(long long) * 2 * kNoiSmemMaxN * kNoiSmemMaxN)));
+                                   (int)(sizeof(long long) * kNoiSmemMaxN * kNoiSmemMaxN)));
       ready[dev] = true;
     }
   }
