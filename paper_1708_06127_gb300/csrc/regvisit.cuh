@@ -31,9 +31,10 @@ struct RegList {
 // Every lane of the warp must call it (groups without a list pass slots = todo = 0).
 template <typename WT, typename ACC, int G, int S, typename F>
 __device__ __forceinline__ void reg_visit(RegList<S>& L, unsigned gmask, F visit) {
+  const int slots = (int)__reduce_max_sync(0xffffffffu, (unsigned)L.slots);  // the warp's longest list
 #pragma unroll
   for (int r = 0; r < S; ++r) {
-    if (!__any_sync(0xffffffffu, r < L.slots)) break;
+    if (r >= slots) break;
     for (;;) {
       const unsigned bal = __ballot_sync(0xffffffffu, (L.todo >> r) & 1u);
       if (!bal) break;
