@@ -270,6 +270,7 @@ __global__ void __launch_bounds__(256) cluster_merge_k(int64_t c, const long lon
         seg_val[b + made] = total;
       }
       ++made;
+      return false;
     });
     if (lane == 0) dcount[x] = made;
   }

@@ -422,12 +422,27 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
     reg_keys<kModeLP, FIRST, G, S>(L, ids, mine ? (int)d : 0, lab, 0);
     if (!mine) L.todo = 0;
     // running best (sum, hash, -label), the same in the group's lanes; the hash of
-    // the best is read only once a tie needs it
+    // the best is read only once a tie needs it.  `left` is the weight of the keys not
+    // visited yet: once the best exceeds it, no other key can reach the best, and the
+    // walk stops (a majority label usually ends it after its own visit).
+    ACC left;
+    if (std::is_same<WT, UnitW>::value) {
+      left = (ACC)(mine ? d : 0);
+    } else {
+      long long sum = 0;
+#pragma unroll
+      for (int r = 0; r < S; ++r)
+        if (L.todo >> r & 1u) sum += L.wt[r];
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      left = (ACC)sum;
+    }
     ACC bs = 0;
     int32_t bl = -1;
     unsigned long long bh = 0;
     bool hashed = false;
     reg_visit<WT, ACC, G, S>(L, gmask, [&](int32_t kk, ACC t) {
+      left -= t;
       if (bl < 0 || t > bs) {
         bs = t;
         bl = kk;
@@ -437,6 +452,7 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
         const unsigned long long h = __ldg(hv + kk);
         if (h > bh || (h == bh && kk < bl)) { bh = h; bl = kk; }
       }
+      return bs > left;
     });
     if (mine && d > 0 && glane == 0) lab_out[v] = bl;
   });
@@ -471,6 +487,7 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restr
     reg_visit<WT, long long, G, S>(L, gmask, [&](int32_t kk, long long t) {
       if (glane == (made & (G - 1))) { pk = kk; pv = t; }
       if ((++made & (G - 1)) == 0) out.put(v, beg, made - G + glane, pk, pv);
+      return false;
     });
     if (glane < (made & (G - 1))) out.put(v, beg, (made & ~(G - 1)) + glane, pk, pv);
     if (mine && glane == 0) cnt[v] = made;

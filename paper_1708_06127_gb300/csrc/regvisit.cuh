@@ -28,6 +28,7 @@ struct RegList {
 
 // Calls visit(key, total) once per distinct used key of the group's list, in
 // slot-then-lane order of first occurrence; total is the same in the group's lanes.
+// A visit returning true ends the group's walk (its remaining keys are not visited).
 // Every lane of the warp must call it (groups without a list pass slots = todo = 0).
 template <typename WT, typename ACC, int G, int S, typename F>
 __device__ __forceinline__ void reg_visit(RegList<S>& L, unsigned gmask, F visit) {
@@ -58,7 +59,7 @@ __device__ __forceinline__ void reg_visit(RegList<S>& L, unsigned gmask, F visit
         for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         total = (ACC)sum;
       }
-      if (gb) visit(kk, total);
+      if (gb && visit(kk, total)) L.todo = 0;
     }
   }
 }
