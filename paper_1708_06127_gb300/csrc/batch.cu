@@ -238,6 +238,7 @@ __global__ void b_summary_k(int K, BState S) {
       S.noi_base[g] = S.vbase[g];
     } else if (ph == kBNoiS) {
       S.list_nois[atomicAdd(&S.summary[10], 1)] = g;
+      atomicMax(&S.summary[11], (int)S.nv[g]);
     }
   }
 }
@@ -624,7 +625,7 @@ static bool engine_step(Engine& E) {
     W.noi_r.ensure_n<long long>(2 * G.n + 64);
     W.noi_seen.ensure_n<unsigned char>(G.n);
     noi_round_batch(G, S.list_nois, cnt[10], S.vbase, S.nv, S.lam, W.noi_r.as<long long>(),
-                    W.noi_seen.as<unsigned char>(), W.parent.as<int32_t>(), F, S.changed, s);
+                    W.noi_seen.as<unsigned char>(), W.parent.as<int32_t>(), F, S.changed, cnt[11], s);
   }
   if (cnt[kBNoiD] > 0) {
     const int64_t mcap = (int64_t)cnt[7] * cnt[7];

@@ -225,7 +225,8 @@ void noi_dense_batch(const GraphView& u, const int32_t* list, int count, const l
                      long long* M, int64_t mcap, int blocks, int32_t* curK, unsigned char* sideK, const BatchNoi& bn,
                      cudaStream_t s);
 // One sparse round for each listed graph; labels and gchanged written per graph.
+// max_n: the largest listed graph (its state then fits in shared memory; 0 = unknown)
 void noi_round_batch(const GraphView& u, const int32_t* list, int count, const long long* vbase, const long long* nv,
                      const long long* glam, long long* r, unsigned char* seen, int32_t* parent, int32_t* labels,
-                     int* gchanged, cudaStream_t s);
+                     int* gchanged, int max_n, cudaStream_t s);
 }  // namespace vc

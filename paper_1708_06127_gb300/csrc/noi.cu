@@ -9,6 +9,7 @@
 // degree after each contraction.
 #include <limits.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -411,11 +412,17 @@ template <typename WT>
 __device__ __forceinline__ void noi_round_warp(int64_t lo, int64_t hi, const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                long long lam, long long* r, unsigned char* seen, int32_t* parent,
-                                               long long* cmax, int32_t* labels, int* any_out) {
+                                               long long* cmax, int32_t* labels, int* any_out, int64_t sb) {
+  // r, seen and parent hold vertex v at v - sb (sb = 0: arrays over the whole graph;
+  // sb = lo: this graph's own arrays, e.g. in shared memory)
   const int lane = threadIdx.x & 31;
   const int64_t n = hi - lo;
   const int64_t nc = (n + 31) >> 5;
-  for (int64_t k = lane; k < n; k += 32) { r[lo + k] = 0; seen[lo + k] = 0; parent[lo + k] = (int32_t)(lo + k); }
+  for (int64_t k = lane; k < n; k += 32) {
+    r[lo + k - sb] = 0;
+    seen[lo + k - sb] = 0;
+    parent[lo + k - sb] = (int32_t)(lo + k - sb);
+  }
   for (int64_t c = lane; c < nc; c += 32) cmax[c] = 0;
   __syncwarp();
   long long best;
@@ -428,31 +435,84 @@ __device__ __forceinline__ void noi_round_warp(int64_t lo, int64_t hi, const int
     }
     const int C = warp_argmax_vi(bv, bc, &best);
     const int64_t k = (int64_t)C * 32 + lane;
-    const long long rv = (k < n && !seen[lo + k]) ? r[lo + k] : -1;
+    const long long rv = (k < n && !seen[lo + k - sb]) ? r[lo + k - sb] : -1;
     const int xl = warp_argmax_vi(rv, (int)k, &best);
     const int64_t x = lo + xl;
-    if (k == xl) seen[x] = 1;
+    if (k == xl) seen[x - sb] = 1;
     warp_argmax_vi(k == xl ? -1 : rv, (int)k, &best);  // the chunk's maximum without x
     if (lane == 0) cmax[C] = best;
     __syncwarp();
     for (int64_t e = off[x] + lane; e < off[x + 1]; e += 32) {
       const int y = adj[e];
-      if (seen[y]) continue;
+      if (seen[y - sb]) continue;
       const long long c = (long long)w[e];
-      const long long ry = (long long)atomicAdd((unsigned long long*)&r[y], (unsigned long long)c) + c;
+      const long long ry = (long long)atomicAdd((unsigned long long*)&r[y - sb], (unsigned long long)c) + c;
       atomicMax(&cmax[(y - lo) >> 5], ry);
-      if (ry >= lam) sunite(parent, (int)x, y);
+      if (ry >= lam) sunite(parent, (int)(x - sb), (int)(y - sb));
     }
     __syncwarp();
   }
   int any = 0;
   for (int64_t k = lane; k < n; k += 32) {
-    const int rt = sfind(parent, (int)(lo + k));
-    labels[lo + k] = rt;
+    const int64_t rt = sfind(parent, (int)(lo + k - sb)) + sb;
+    labels[lo + k] = (int32_t)rt;
     any |= rt != lo + k;
   }
   if (__any_sync(0xffffffffu, any) && lane == 0) atomicOr(any_out, 1);
   __syncwarp();
+}
+
+// The same round with the graph's state (attachments, chunk maxima, parents, seen
+// flags) in shared memory: a scan step then waits on one global read (the chosen
+// vertex's list) instead of several.  One warp per block; ncap = the largest graph.
+constexpr int kNoiSmemRoundMaxN = 15360;  // 15360 x 13 B + chunk maxima < 227 KB
+__host__ __device__ constexpr size_t noi_round_smem(int ncap) {
+  return (size_t)ncap * 13 + ((size_t)ncap / 32 + 1) * 8;
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(32) noi_round_smem_k(const int32_t* __restrict__ list, int count,
+                                                       const int64_t* __restrict__ off,
+                                                       const int32_t* __restrict__ adj, const WT* __restrict__ w,
+                                                       const long long* vbase, const long long* nv,
+                                                       const long long* glam, const DevState* st, int ncap,
+                                                       int32_t* labels, int* gchanged) {
+  extern __shared__ __align__(16) unsigned char noi_rs[];
+  long long* r = (long long*)noi_rs;
+  long long* cmax = r + ncap;
+  int32_t* parent = (int32_t*)(cmax + ncap / 32 + 1);
+  unsigned char* seen = (unsigned char*)(parent + ncap);
+  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+    const int g = list ? list[idx] : 0;
+    const long long lo = vbase ? vbase[g] : 0;
+    const long long n = nv ? nv[g] : (long long)ncap;
+    const long long lam = glam ? glam[g] : st->lambda_hat;
+    noi_round_warp<WT>(lo, lo + n, off, adj, w, lam, r, seen, parent, cmax, labels, gchanged + g, lo);
+  }
+}
+
+template <typename WT>
+static void noi_round_smem_launch(const int32_t* list, int count, const int64_t* off, const int32_t* adj,
+                                  const WT* w, const long long* vbase, const long long* nv, const long long* glam,
+                                  const DevState* st, int ncap, int32_t* labels, int* gchanged, cudaStream_t s) {
+  static std::mutex mu;
+  static std::unordered_map<int, bool> ready;  // per device: the shared-memory limit was raised
+  {
+    int dev = 0;
+    VC_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ready[dev]) {
+      VC_CUDA(cudaFuncSetAttribute(noi_round_smem_k<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)noi_round_smem(kNoiSmemRoundMaxN)));
+      ready[dev] = true;
+    }
+  }
+  const size_t smem = noi_round_smem(ncap);
+  const int per_sm = (int)std::max<size_t>(1, (size_t)(227 * 1024) / (smem + 1024));
+  const int blocks = std::min(count, kSMs * std::min(per_sm, 32));
+  noi_round_smem_k<WT><<<blocks, 32, smem, s>>>(list, count, off, adj, w, vbase, nv, glam, st, ncap, labels, gchanged);
+  count_launch();
+  VC_CHECK_LAUNCH();
 }
 
 template <typename WT>
@@ -460,11 +520,20 @@ __global__ void __launch_bounds__(32) noi_round_k(int64_t n, const int64_t* __re
                                                   const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                   const DevState* st, long long* r, unsigned char* seen,
                                                   int32_t* parent, long long* cmax, int32_t* labels, int* changed) {
-  noi_round_warp<WT>(0, n, off, adj, w, st->lambda_hat, r, seen, parent, cmax, labels, changed);
+  noi_round_warp<WT>(0, n, off, adj, w, st->lambda_hat, r, seen, parent, cmax, labels, changed, 0);
 }
 
 void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, unsigned char* seen,
                       int32_t* parent, int32_t* labels, int* changed, cudaStream_t s) {
+  if (g.n <= kNoiSmemRoundMaxN) {
+    if (g.wbytes == 4)
+      noi_round_smem_launch<int32_t>(nullptr, 1, g.off, g.adj, (const int32_t*)g.w, nullptr, nullptr, nullptr, st,
+                                     (int)g.n, labels, changed, s);
+    else
+      noi_round_smem_launch<long long>(nullptr, 1, g.off, g.adj, (const long long*)g.w, nullptr, nullptr, nullptr, st,
+                                       (int)g.n, labels, changed, s);
+    return;
+  }
   // r holds 2n entries: the attachments, then the chunk maxima
   long long* cmax = r + g.n;
   if (g.wbytes == 4)
@@ -491,14 +560,23 @@ __global__ void __launch_bounds__(256) noi_round_batch_k(const int32_t* __restri
   for (int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < count; idx += warps) {
     const int g = list[idx];
     const long long lo = vbase[g];
-    noi_round_warp<WT>(lo, lo + nv[g], off, adj, w, glam[g], r, seen, parent, cmax + lo, labels, gchanged + g);
+    noi_round_warp<WT>(lo, lo + nv[g], off, adj, w, glam[g], r, seen, parent, cmax + lo, labels, gchanged + g, 0);
   }
 }
 
 void noi_round_batch(const GraphView& u, const int32_t* list, int count, const long long* vbase, const long long* nv,
                      const long long* glam, long long* r, unsigned char* seen, int32_t* parent, int32_t* labels,
-                     int* gchanged, cudaStream_t s) {
+                     int* gchanged, int max_n, cudaStream_t s) {
   if (count <= 0) return;
+  if (max_n > 0 && max_n <= kNoiSmemRoundMaxN) {
+    if (u.wbytes == 4)
+      noi_round_smem_launch<int32_t>(list, count, u.off, u.adj, (const int32_t*)u.w, vbase, nv, glam, nullptr, max_n,
+                                     labels, gchanged, s);
+    else
+      noi_round_smem_launch<long long>(list, count, u.off, u.adj, (const long long*)u.w, vbase, nv, glam, nullptr,
+                                       max_n, labels, gchanged, s);
+    return;
+  }
   // r holds 2 x (union size) entries: attachments, then each graph's chunk maxima at its own range
   long long* cmax = r + u.n;
   const int blocks = grid_for(count, 8, kSMs * 4);
