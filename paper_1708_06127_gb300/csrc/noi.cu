@@ -466,17 +466,21 @@ __device__ __forceinline__ void noi_round_warp(int64_t lo, int64_t hi, const int
 // flags) in shared memory: a scan step then waits on one global read (the chosen
 // vertex's list) instead of several.  One warp per block; ncap = the largest graph.
 constexpr int kNoiSmemRoundMaxN = 15360;  // 15360 x 13 B + chunk maxima < 227 KB
+constexpr int kNoiBatchSmemN = 2048;      // batches: 27 KB per graph, eight blocks per SM
 __host__ __device__ constexpr size_t noi_round_smem(int ncap) {
   return (size_t)ncap * 13 + ((size_t)ncap / 32 + 1) * 8;
 }
 
+// Graphs above ncap vertices take the global arrays (gr: attachments then chunk
+// maxima over the whole union, gseen, gparent), as noi_round_batch_k does.
 template <typename WT>
 __global__ void __launch_bounds__(32) noi_round_smem_k(const int32_t* __restrict__ list, int count,
                                                        const int64_t* __restrict__ off,
                                                        const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                        const long long* vbase, const long long* nv,
                                                        const long long* glam, const DevState* st, int ncap,
-                                                       int32_t* labels, int* gchanged) {
+                                                       int64_t un, long long* gr, unsigned char* gseen,
+                                                       int32_t* gparent, int32_t* labels, int* gchanged) {
   extern __shared__ __align__(16) unsigned char noi_rs[];
   long long* r = (long long*)noi_rs;
   long long* cmax = r + ncap;
@@ -487,14 +491,18 @@ __global__ void __launch_bounds__(32) noi_round_smem_k(const int32_t* __restrict
     const long long lo = vbase ? vbase[g] : 0;
     const long long n = nv ? nv[g] : (long long)ncap;
     const long long lam = glam ? glam[g] : st->lambda_hat;
-    noi_round_warp<WT>(lo, lo + n, off, adj, w, lam, r, seen, parent, cmax, labels, gchanged + g, lo);
+    if (n <= ncap)
+      noi_round_warp<WT>(lo, lo + n, off, adj, w, lam, r, seen, parent, cmax, labels, gchanged + g, lo);
+    else
+      noi_round_warp<WT>(lo, lo + n, off, adj, w, lam, gr, gseen, gparent, gr + un + lo, labels, gchanged + g, 0);
   }
 }
 
 template <typename WT>
 static void noi_round_smem_launch(const int32_t* list, int count, const int64_t* off, const int32_t* adj,
                                   const WT* w, const long long* vbase, const long long* nv, const long long* glam,
-                                  const DevState* st, int ncap, int32_t* labels, int* gchanged, cudaStream_t s) {
+                                  const DevState* st, int ncap, int64_t un, long long* gr, unsigned char* gseen,
+                                  int32_t* gparent, int32_t* labels, int* gchanged, cudaStream_t s) {
   static std::mutex mu;
   static std::unordered_map<int, bool> ready;  // per device: the shared-memory limit was raised
   {
@@ -510,7 +518,8 @@ static void noi_round_smem_launch(const int32_t* list, int count, const int64_t*
   const size_t smem = noi_round_smem(ncap);
   const int per_sm = (int)std::max<size_t>(1, (size_t)(227 * 1024) / (smem + 1024));
   const int blocks = std::min(count, kSMs * std::min(per_sm, 32));
-  noi_round_smem_k<WT><<<blocks, 32, smem, s>>>(list, count, off, adj, w, vbase, nv, glam, st, ncap, labels, gchanged);
+  noi_round_smem_k<WT><<<blocks, 32, smem, s>>>(list, count, off, adj, w, vbase, nv, glam, st, ncap, un, gr, gseen,
+                                                gparent, labels, gchanged);
   count_launch();
   VC_CHECK_LAUNCH();
 }
@@ -528,10 +537,10 @@ void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, unsi
   if (g.n <= kNoiSmemRoundMaxN) {
     if (g.wbytes == 4)
       noi_round_smem_launch<int32_t>(nullptr, 1, g.off, g.adj, (const int32_t*)g.w, nullptr, nullptr, nullptr, st,
-                                     (int)g.n, labels, changed, s);
+                                     (int)g.n, g.n, r, seen, parent, labels, changed, s);
     else
       noi_round_smem_launch<long long>(nullptr, 1, g.off, g.adj, (const long long*)g.w, nullptr, nullptr, nullptr, st,
-                                       (int)g.n, labels, changed, s);
+                                       (int)g.n, g.n, r, seen, parent, labels, changed, s);
     return;
   }
   // r holds 2n entries: the attachments, then the chunk maxima
@@ -568,13 +577,16 @@ void noi_round_batch(const GraphView& u, const int32_t* list, int count, const l
                      const long long* glam, long long* r, unsigned char* seen, int32_t* parent, int32_t* labels,
                      int* gchanged, int max_n, cudaStream_t s) {
   if (count <= 0) return;
-  if (max_n > 0 && max_n <= kNoiSmemRoundMaxN) {
+  {
+    // graphs up to kNoiBatchSmemN vertices keep their state in shared memory (several
+    // blocks per SM); larger ones, in the same launch, the global arrays
+    const int ncap = std::min(std::max(max_n, 1), kNoiBatchSmemN);
     if (u.wbytes == 4)
-      noi_round_smem_launch<int32_t>(list, count, u.off, u.adj, (const int32_t*)u.w, vbase, nv, glam, nullptr, max_n,
-                                     labels, gchanged, s);
+      noi_round_smem_launch<int32_t>(list, count, u.off, u.adj, (const int32_t*)u.w, vbase, nv, glam, nullptr, ncap,
+                                     u.n, r, seen, parent, labels, gchanged, s);
     else
       noi_round_smem_launch<long long>(list, count, u.off, u.adj, (const long long*)u.w, vbase, nv, glam, nullptr,
-                                       max_n, labels, gchanged, s);
+                                       ncap, u.n, r, seen, parent, labels, gchanged, s);
     return;
   }
   // r holds 2 x (union size) entries: attachments, then each graph's chunk maxima at its own range
