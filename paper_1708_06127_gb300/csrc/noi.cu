@@ -466,7 +466,6 @@ __device__ __forceinline__ void noi_round_warp(int64_t lo, int64_t hi, const int
 // flags) in shared memory: a scan step then waits on one global read (the chosen
 // vertex's list) instead of several.  One warp per block; ncap = the largest graph.
 constexpr int kNoiSmemRoundMaxN = 15360;  // 15360 x 13 B + chunk maxima < 227 KB
-constexpr int kNoiBatchSmemN = 2048;      // batches: 27 KB per graph, eight blocks per SM
 __host__ __device__ constexpr size_t noi_round_smem(int ncap) {
   return (size_t)ncap * 13 + ((size_t)ncap / 32 + 1) * 8;
 }
@@ -577,18 +576,7 @@ void noi_round_batch(const GraphView& u, const int32_t* list, int count, const l
                      const long long* glam, long long* r, unsigned char* seen, int32_t* parent, int32_t* labels,
                      int* gchanged, int max_n, cudaStream_t s) {
   if (count <= 0) return;
-  {
-    // graphs up to kNoiBatchSmemN vertices keep their state in shared memory (several
-    // blocks per SM); larger ones, in the same launch, the global arrays
-    const int ncap = std::min(std::max(max_n, 1), kNoiBatchSmemN);
-    if (u.wbytes == 4)
-      noi_round_smem_launch<int32_t>(list, count, u.off, u.adj, (const int32_t*)u.w, vbase, nv, glam, nullptr, ncap,
-                                     u.n, r, seen, parent, labels, gchanged, s);
-    else
-      noi_round_smem_launch<long long>(list, count, u.off, u.adj, (const long long*)u.w, vbase, nv, glam, nullptr,
-                                       ncap, u.n, r, seen, parent, labels, gchanged, s);
-    return;
-  }
+  (void)max_n;  // the global-array kernel: every listed graph in flight at once measured faster
   // r holds 2 x (union size) entries: attachments, then each graph's chunk maxima at its own range
   long long* cmax = r + u.n;
   const int blocks = grid_for(count, 8, kSMs * 4);
