@@ -155,41 +155,30 @@ __device__ __forceinline__ void group_sums(int32_t c, int k, int lane, int* sk, 
   *below = b;
 }
 
-// Pairs per source cluster; *maxt = the largest count, *pairs = their total.
-__global__ void __launch_bounds__(256) cluster_count_k(int64_t n, const int32_t* __restrict__ cid,
-                                                       const int32_t* __restrict__ cnt, int32_t* __restrict__ ccount,
-                                                       int* maxt, long long* pairs) {
-  __shared__ int s_k[8][32];
+// The largest pairs-per-cluster count and the total, over ccount[0, n).
+__global__ void __launch_bounds__(256) cluster_stats_k(int64_t n, const int32_t* __restrict__ ccount, int* maxt,
+                                                       long long* pairs) {
   __shared__ int s_max;
-  __shared__ unsigned long long s_pairs;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) { s_max = 0; s_pairs = 0; }
+  __shared__ unsigned long long s_sum;
+  if (threadIdx.x == 0) { s_max = 0; s_sum = 0; }
   __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  long long mine = 0;
-  int top = 0;  // largest running count this lane saw
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-    const int64_t v = base + lane;
-    const int k = v < n ? cnt[v] : 0;
-    const int32_t c = k > 0 ? cid[v] : -1;
-    unsigned peers;
-    int t, b;
-    group_sums(c, k, lane, s_k[wid], &peers, &t, &b);
-    if (c >= 0 && lane == __ffs(peers) - 1) top = max(top, atomicAdd(&ccount[c], t) + t);
-    mine += k;
+  int top = 0;
+  long long sum = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = ccount[i];
+    top = max(top, x);
+    sum += x;
   }
-  // the last addition to a cluster returns its final count, so the maximum of the
-  // running counts is the largest final count
   const unsigned wtop = __reduce_max_sync(0xffffffffu, (unsigned)top);
-  const long long w = warp_sum(mine);
-  if (lane == 0) {
+  const long long w = warp_sum(sum);
+  if ((threadIdx.x & 31) == 0) {
     if (wtop) atomicMax(&s_max, (int)wtop);
-    if (w) atomicAdd(&s_pairs, (unsigned long long)w);
+    if (w) atomicAdd(&s_sum, (unsigned long long)w);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     if (s_max) atomicMax(maxt, s_max);
-    if (s_pairs) atomicAdd((unsigned long long*)pairs, s_pairs);
+    if (s_sum) atomicAdd((unsigned long long*)pairs, s_sum);
   }
 }
 
@@ -381,11 +370,9 @@ __global__ void __launch_bounds__(256) cluster_place_k(int64_t c, const long lon
   }
 }
 
-void cluster_count(const GraphView& g, const int32_t* cid, const int32_t* cnt, int32_t* ccount, int* maxt,
-                   long long* pairs, cudaStream_t s) {
-  VC_CUDA(cudaMemsetAsync(ccount, 0, sizeof(int32_t) * std::max<int64_t>(g.n, 1), s));
-  if (g.n <= 0) return;
-  cluster_count_k<<<grid_for(g.n, 256, kSMs * 8), 256, 0, s>>>(g.n, cid, cnt, ccount, maxt, pairs);
+void cluster_stats(int64_t n, const int32_t* ccount, int* maxt, long long* pairs, cudaStream_t s) {
+  if (n <= 0) return;
+  cluster_stats_k<<<grid_for(n, 256, kSMs * 4), 256, 0, s>>>(n, ccount, maxt, pairs);
   count_launch();
   VC_CHECK_LAUNCH();
 }

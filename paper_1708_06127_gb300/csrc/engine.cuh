@@ -310,14 +310,16 @@ struct Workspace {
     cs.scan_scr = scan64.as<long long>();
     cs.scan_scr32 = scan32.as<int>();
     relabel(labels, g.n, cid_out, cs, &ctr()->c, s);
-    const PairOut po{cs.tmp_key, cs.tmp_val, cs.cmp_key, cs.cmp_val};
-    tune_emit(g, cid_out, po, cs.cnt);
-    emit_cross(g, bins, gt, cid_out, po, cs.cnt, s, tune);
-    // pairs per cluster (flags is free again after the relabel)
+    PairOut po{cs.tmp_key, cs.tmp_val, cs.cmp_key, cs.cmp_val};
+    tune_emit(g, cid_out, po, cs.cnt);  // trials: no counting
+    // the pre-merge also counts pairs per cluster (flags is free again after the relabel)
     int32_t* ccount = cs.flags;
+    VC_CUDA(cudaMemsetAsync(ccount, 0, sizeof(int32_t) * std::max<int64_t>(g.n, 1), s));
+    po.ccount = ccount;
+    emit_cross(g, bins, gt, cid_out, po, cs.cnt, s, tune);
     VC_CUDA(cudaMemsetAsync(&ctr()->maxt, 0, sizeof(int), s));
     VC_CUDA(cudaMemsetAsync(&ctr()->pairs, 0, sizeof(long long), s));
-    cluster_count(g, cid_out, cs.cnt, ccount, &ctr()->maxt, &ctr()->pairs, s);
+    cluster_stats(g.n, ccount, &ctr()->maxt, &ctr()->pairs, s);
     VC_CUDA(cudaMemcpyAsync(h_counters, ctr(), sizeof(Counters), cudaMemcpyDeviceToHost, s));
     sync();
     const int64_t c = h_counters->c;

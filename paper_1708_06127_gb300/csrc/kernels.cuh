@@ -101,6 +101,7 @@ struct PairOut {
   long long* tval;
   int32_t* ckey;
   long long* cval;
+  int32_t* ccount = nullptr;  // if set: ccount[cid[v]] += the pairs of v (pairs per cluster)
   __device__ __forceinline__ void put(int64_t v, int64_t beg, int i, int32_t k, long long x) const {
     if (i < kPairSlots) {
       ckey[v * kPairSlots + i] = k;
@@ -145,13 +146,13 @@ void relabel(const int32_t* lab, int64_t n, int32_t* cid, ContractScratch& cs, i
 
 // Cluster merge (every cluster holding at most kMergeBlockMax pre-merged pairs; a
 // warp merges clusters of at most kMergeMax in registers, a block the larger ones):
-// cluster_count fills ccount[cid] (n entries zeroed first), *maxt and *pairs;
+// the pre-merge fills ccount[cid] (PairOut::ccount); cluster_stats reads its n entries
+// (zero beyond the c clusters) into *maxt and *pairs;
 // cluster_merge writes the coarse CSR (coff[c + 1], sorted cadj, cw, entry sources
 // csrc) and *nnz_dev; big = some cluster holds more than kMergeMax pairs.
 constexpr int kMergeMax = 512;
 constexpr int kMergeBlockMax = 4096;
-void cluster_count(const GraphView& g, const int32_t* cid, const int32_t* cnt, int32_t* ccount, int* maxt,
-                   long long* pairs, cudaStream_t s);
+void cluster_stats(int64_t n, const int32_t* ccount, int* maxt, long long* pairs, cudaStream_t s);
 void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int32_t* ccount, int64_t c,
                    long long* cbase, long long* cursor, int32_t* seg_key, long long* seg_val, int64_t* coff,
                    int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, bool big, cudaStream_t s);

@@ -490,7 +490,10 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restr
       return false;
     });
     if (glane < (made & (G - 1))) out.put(v, beg, (made & ~(G - 1)) + glane, pk, pv);
-    if (mine && glane == 0) cnt[v] = made;
+    if (mine && glane == 0) {
+      cnt[v] = made;
+      if (out.ccount && made) atomicAdd(&out.ccount[own], made);
+    }
   });
 }
 
@@ -712,7 +715,10 @@ __global__ void __launch_bounds__(kAggThreads) emit_warp_k(const int32_t* __rest
       for (int64_t base = beg; base < end; base += G)
         emit_chunk<WT, G>(base + glane, end, adj, w, cid, own, lane, gmask, out, v, beg,
                           [&](int) { return made++; });
-    if (glane == 0) cnt[v] = made;
+    if (glane == 0) {
+      cnt[v] = made;
+      if (out.ccount && made) atomicAdd(&out.ccount[own], made);
+    }
   }
 }
 
@@ -740,7 +746,10 @@ __global__ void __launch_bounds__(kAggThreads) emit_block_k(const int32_t* __res
           return __shfl_sync(0xffffffffu, at, leader);
         });
     __syncthreads();
-    if (threadIdx.x == 0) cnt[v] = s_made;
+    if (threadIdx.x == 0) {
+      cnt[v] = s_made;
+      if (out.ccount && s_made) atomicAdd(&out.ccount[own], s_made);
+    }
     __syncthreads();
   }
 }
