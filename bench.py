@@ -325,6 +325,63 @@ def bench_serve(pool_size: int, requests: int, warm: int, device: int, budget_gb
             "super_steps": st["super_steps"], "wall_s": t_end - t_start}
 
 
+def planted_construction_cut(g, blocks: int, block_n: int) -> int:
+    """The planted graph's cut value from its construction: the smaller of the minimum
+    weighted degree and the lightest bridge set separating a union of blocks."""
+    deg = np.add.reduceat(g.w.astype(np.int64), g.offsets[:-1])
+    src = np.repeat(np.arange(g.n, dtype=np.int32), np.diff(g.offsets))
+    cross = (src // block_n) != (g.adj // block_n)
+    bs, bd, bw = src[cross] // block_n, g.adj[cross] // block_n, g.w[cross].astype(np.int64)
+    best = int(deg.min())
+    for mask in range(1, 1 << (blocks - 1)):
+        side = (mask >> np.arange(blocks)) & 1
+        best = min(best, int(bw[side[bs] != side[bd]].sum()) // 2)
+    return best
+
+
+def bench_configs(device: int):
+    """The small and the planted configurations: device-resident run time (median),
+    the oracle's single-thread time on the small one (a CPU baseline), and the value
+    against the construction's cut on the planted one."""
+    import torch
+    import graphgen as gg
+    import oracle
+    import paper_1708_06127_gb300 as vc
+    oracle.build()
+    dev = torch.device("cuda", device)
+
+    def gpu_times(g, reps, warm):
+        d = [torch.from_numpy(x).to(dev) for x in (g.offsets, g.adj, g.w)]
+        with vc.MinCut(*d, on_device=True, device=device) as mc:
+            for i in range(warm):
+                mc.run(1, 2)
+            ts = []
+            for i in range(reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                cut, bits = mc.run(1, 2)
+                ts.append(time.perf_counter() - t0)
+            trace = mc.trace()
+        return statistics.median(ts), cut, bits, trace
+
+    out = {}
+    g = gg.workload_rhg_small(1)
+    t, cut, bits, trace = gpu_times(g, 10, 3)
+    # cpu_baseline leg: the oracle timed on one host thread (agreement is tests' job)
+    t0 = time.perf_counter()
+    oracle.viecut(g.offsets, g.adj, g.w, seed=1, lp_iters=2, n0=10000)
+    t_cpu = time.perf_counter() - t0
+    out["rhg_2^14_deg32_lcc"] = {
+        "n": g.n, "m": g.m, "gpu_ms": 1e3 * t, "gpu_edges_per_s": g.m / t, "cut": cut,
+        "cpu_baseline": {"value": g.m / t_cpu, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": f"the same graph, {1e3 * t_cpu:.1f} ms"}}
+    g = gg.workload_planted(1)
+    t, cut, bits, trace = gpu_times(g, 3, 1)
+    out["planted_8x2^20_deg48"] = {"n": g.n, "m": g.m, "gpu_ms": 1e3 * t, "gpu_edges_per_s": g.m / t, "cut": cut,
+                                   "construction_cut": planted_construction_cut(g, 8, 1 << 20)}
+    return out
+
+
 def run_reference(args):
     """The oracle arm: each step is one oracle run of the bounded sample."""
     rank, world, _ = dist_env()
@@ -367,7 +424,7 @@ def main():
                     help="lanes per vertex of the first label-propagation round (0: picked by timing)")
     ap.add_argument("--emit-group", type=int, default=0,
                     help="lanes per vertex of the block-class pre-merge (0: picked by timing)")
-    ap.add_argument("--mode", default="all", choices=["all", "single", "batch", "serve"],
+    ap.add_argument("--mode", default="all", choices=["all", "single", "batch", "serve", "configs"],
                     help="all: the headline line plus batch and serving summaries")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=300)
@@ -387,6 +444,11 @@ def main():
         vc.build()
         res = bench_batch(args.batch_count, args.steps, args.warmup, torch.cuda.current_stream(), local)
         print(json.dumps(res), flush=True)
+        return 0
+    if args.mode == "configs":
+        torch.cuda.set_device(local)
+        vc.build()
+        print(json.dumps(bench_configs(local)), flush=True)
         return 0
     if args.mode == "serve":
         torch.cuda.set_device(local)
