@@ -225,8 +225,6 @@ __global__ void __launch_bounds__(256) cluster_scatter_k(int64_t n, const int64_
   }
 }
 
-constexpr int kMergeWarpKeys = 32;  // distinct targets a warp walk takes before handing on
-
 // A warp per cluster: its (at most kMergeMax) pairs into registers, one step per
 // distinct target (summing its weights), the distinct targets written back in place
 // at the front of the segment; dcount[c] = their number.
@@ -254,26 +252,20 @@ __global__ void __launch_bounds__(256) cluster_merge_k(int64_t c, const long lon
         L.todo |= 1u << r;
       }
     }
-    // lane i keeps the i-th distinct target; past kMergeWarpKeys targets the cluster
-    // is handed to the block kernel (a step per key costs slots x compares)
     int made = 0;  // warp-uniform
-    int32_t ok = 0;
-    long long ov = 0;
     reg_visit<long long, long long, 32, S>(L, 0xffffffffu, [&](int32_t key, long long total) {
-      if (lane == made) { ok = key; ov = total; }
-      return ++made >= kMergeWarpKeys;
+      if (lane == 0) {
+        seg_key[b + made] = key;
+        seg_val[b + made] = total;
+      }
+      ++made;
+      return false;
     });
-    const bool bailed = made >= kMergeWarpKeys;  // (exactly kMergeWarpKeys targets also hand on)
-    if (!bailed && lane < made) {
-      seg_key[b + lane] = ok;
-      seg_val[b + lane] = ov;
-    }
-    if (lane == 0) dcount[x] = bailed ? -1 : made;
+    if (lane == 0) dcount[x] = made;
   }
 }
 
-// Clusters of kMergeMax < T <= kMergeBlockMax pairs, and the ones whose warp walk met
-// kMergeWarpKeys distinct targets (dcount < 0): a block per cluster sorts the
+// Clusters of kMergeMax < T <= kMergeBlockMax pairs: a block per cluster sorts the
 // pairs by target in shared memory (bitonic network over the next power of two,
 // padding keys INT_MAX), then every run head sums its run; the distinct targets are
 // written back in ascending order at the front of the segment.
@@ -289,7 +281,7 @@ __global__ void __launch_bounds__(256) cluster_merge_block_k(int64_t c, const lo
   for (int64_t x = blockIdx.x; x < c; x += gridDim.x) {
     const long long b = cbase[x];
     const int T = (int)(cbase[x + 1] - b);
-    if (T <= kMergeMax && dcount[x] >= 0) continue;  // the same in every thread of the block
+    if (T <= kMergeMax) continue;  // the same in every thread of the block
     int N = 1;
     while (N < T) N <<= 1;
     for (int i = tid; i < N; i += 256) {
@@ -396,8 +388,7 @@ void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch
   cluster_merge_k<<<gc, 256, 0, s>>>(c, cbase, seg_key, seg_val, ccount);
   count_launch(2);
   VC_CHECK_LAUNCH();
-  {  // clusters above kMergeMax pairs and the ones the warp kernel handed on
-    (void)big;
+  if (big) {
     static std::mutex mu;
     static std::unordered_map<int, bool> ready;  // per device: the shared-memory limit was raised
     const int smem = kMergeBlockMax * (int)(sizeof(long long) + sizeof(int32_t));

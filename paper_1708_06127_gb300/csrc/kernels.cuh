@@ -58,10 +58,8 @@ struct Bins {
   int32_t* mid_list;     // [n]
   int32_t* block_list;   // [n]
   int32_t* global_list;  // [n]
-  int32_t* bail_list;    // [n] lists the register walk of a label round handed on (per pass)
-  int32_t* bail_list2;   // [n] the same for the pre-merge
   int* counts;           // device: [0] mid, [1] block, [2] global count, [3] max length above
-                         // 128, [4] small, [5] reg, [6] / [7] bail counts of bail_list / 2
+                         // 128, [4] small, [5] reg count
   int h_mid = 0, h_block = 0, h_global = 0, h_maxdeg = 0, h_small = 0, h_reg = 0;  // host copies
 };
 

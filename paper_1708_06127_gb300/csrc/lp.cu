@@ -308,11 +308,6 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
 // so the warp software-pipelines its vertices: while it works on one vertex per
 // group it already holds the next vertex's ids and the offsets of the one after.
 
-// A list whose walk reaches kRegBailVisits distinct keys without finishing goes to a
-// table (label propagation) or chunk (pre-merge) kernel: a step per key costs slots x
-// compares, which only pays while keys are few.
-constexpr int kRegBailVisits = 32;
-
 // Neighbour ids (and weights) of one list in registers.
 template <int S>
 struct RegIds {
@@ -409,8 +404,7 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
                                                         const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                         const int32_t* __restrict__ lab, int32_t* __restrict__ lab_out,
                                                         const unsigned long long* __restrict__ hv,
-                                                        const unsigned char* __restrict__ vact,
-                                                        int32_t* __restrict__ bail_list, int* __restrict__ bail_count) {
+                                                        const unsigned char* __restrict__ vact) {
   const int lane = threadIdx.x & 31, glane = lane & (G - 1), gi = lane / G;
   const unsigned gmask = group_mask<G>(lane);
   constexpr int kPer = 32 / G;  // vertices per warp
@@ -447,8 +441,6 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
     int32_t bl = -1;
     unsigned long long bh = 0;
     bool hashed = false;
-    int visits = 0;
-    bool bailed = false;  // too many distinct labels for steps: the table kernel takes v
     reg_visit<WT, ACC, G, S>(L, gmask, [&](int32_t kk, ACC t) {
       left -= t;
       if (bl < 0 || t > bs) {
@@ -460,14 +452,9 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
         const unsigned long long h = __ldg(hv + kk);
         if (h > bh || (h == bh && kk < bl)) { bh = h; bl = kk; }
       }
-      if (bs > left) return true;
-      if (++visits >= kRegBailVisits) { bailed = true; return true; }
-      return false;
+      return bs > left;
     });
-    if (mine && d > 0 && glane == 0) {
-      if (bailed) bail_list[atomicAdd(bail_count, 1)] = (int32_t)v;
-      else lab_out[v] = bl;
-    }
+    if (mine && d > 0 && glane == 0) lab_out[v] = bl;
   });
 }
 
@@ -480,8 +467,7 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restr
                                                           const int64_t* __restrict__ off,
                                                           const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                           const int32_t* __restrict__ cid, PairOut out,
-                                                          int32_t* __restrict__ cnt, int32_t* __restrict__ bail_list,
-                                                          int* __restrict__ bail_count) {
+                                                          int32_t* __restrict__ cnt) {
   const int lane = threadIdx.x & 31, glane = lane & (G - 1), gi = lane / G;
   const unsigned gmask = group_mask<G>(lane);
   constexpr int kPer = 32 / G;
@@ -498,25 +484,64 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restr
     int made = 0;  // the same in the group's lanes
     int32_t pk = 0;
     long long pv = 0;
-    bool bailed = false;  // too many distinct clusters for steps: the chunk kernel takes v
     reg_visit<WT, long long, G, S>(L, gmask, [&](int32_t kk, long long t) {
       if (glane == (made & (G - 1))) { pk = kk; pv = t; }
       if ((++made & (G - 1)) == 0) out.put(v, beg, made - G + glane, pk, pv);
-      if (made >= kRegBailVisits) { bailed = true; return true; }
       return false;
     });
-    if (bailed) {
-      if (glane == 0) bail_list[atomicAdd(bail_count, 1)] = (int32_t)v;
-    } else {
-      if (glane < (made & (G - 1))) out.put(v, beg, (made & ~(G - 1)) + glane, pk, pv);
-      if (mine && glane == 0) {
-        cnt[v] = made;
-        if (out.ccount && made) atomicAdd(&out.ccount[own], made);
-      }
+    if (glane < (made & (G - 1))) out.put(v, beg, (made & ~(G - 1)) + glane, pk, pv);
+    if (mine && glane == 0) {
+      cnt[v] = made;
+      if (out.ccount && made) atomicAdd(&out.ccount[own], made);
     }
   });
 }
 
+template <typename WT, typename ACC, bool FIRST>
+void launch_lp_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t* lab, int32_t* lab_out,
+                   const unsigned long long* hv, cudaStream_t s) {
+  if (b.h_small > 0) {
+    lp_reg_k<WT, ACC, FIRST, 16, 4><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
+        b.small_list, b.counts + 4, g.off, g.adj, w, lab, lab_out, hv, g.vact);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
+  if (b.h_reg > 0) {
+    lp_reg_k<WT, ACC, FIRST, 32, 4><<<grid_for(b.h_reg, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
+        b.reg_list, b.counts + 5, g.off, g.adj, w, lab, lab_out, hv, g.vact);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
+  if (b.h_mid > 0) {
+    lp_reg_k<WT, ACC, FIRST, 32, kMidMaxDeg / 32><<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
+        b.mid_list, b.counts + 0, g.off, g.adj, w, lab, lab_out, hv, g.vact);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
+}
+
+template <typename WT>
+void launch_emit_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t* cid, const PairOut& out,
+                     int32_t* cnt, cudaStream_t s) {
+  if (b.h_small > 0) {
+    emit_reg_k<WT, 16, 4><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
+        b.small_list, b.counts + 4, g.off, g.adj, w, cid, out, cnt);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
+  if (b.h_reg > 0) {
+    emit_reg_k<WT, 32, 4><<<grid_for(b.h_reg, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
+        b.reg_list, b.counts + 5, g.off, g.adj, w, cid, out, cnt);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
+  if (b.h_mid > 0) {
+    emit_reg_k<WT, 32, kMidMaxDeg / 32><<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
+        b.mid_list, b.counts + 0, g.off, g.adj, w, cid, out, cnt);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
+}
 
 // First round on a graph whose lists are strictly increasing: every neighbour is its
 // own label, so S(u) = c(v,u) and the choice is the argmax of (c(v,u), hash(u), -u)
@@ -807,68 +832,6 @@ void set_smem(F kfn, size_t bytes) {
 template <int CAP, typename ACC>
 constexpr size_t warp_smem() {
   return (size_t)kWarpsPerBlock * CAP * (sizeof(ACC) + sizeof(int)) + (size_t)kWarpsPerBlock * (CAP / 2) * sizeof(int);
-}
-
-template <typename WT, typename ACC, bool FIRST>
-void launch_lp_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t* lab, int32_t* lab_out,
-                   const unsigned long long* hv, cudaStream_t s) {
-  VC_CUDA(cudaMemsetAsync(b.counts + 6, 0, sizeof(int), s));
-  if (b.h_small > 0) {
-    lp_reg_k<WT, ACC, FIRST, 16, 4><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
-        b.small_list, b.counts + 4, g.off, g.adj, w, lab, lab_out, hv, g.vact, b.bail_list, b.counts + 6);
-    count_launch();
-    VC_CHECK_LAUNCH();
-  }
-  if (b.h_reg > 0) {
-    lp_reg_k<WT, ACC, FIRST, 32, 4><<<grid_for(b.h_reg, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
-        b.reg_list, b.counts + 5, g.off, g.adj, w, lab, lab_out, hv, g.vact, b.bail_list, b.counts + 6);
-    count_launch();
-    VC_CHECK_LAUNCH();
-  }
-  if (b.h_mid > 0) {
-    lp_reg_k<WT, ACC, FIRST, 32, kMidMaxDeg / 32><<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
-        b.mid_list, b.counts + 0, g.off, g.adj, w, lab, lab_out, hv, g.vact, b.bail_list, b.counts + 6);
-    count_launch();
-    VC_CHECK_LAUNCH();
-  }
-  if (b.h_small + b.h_reg + b.h_mid > 0) {  // the lists the walk handed on, a shared table each
-    constexpr int CAP = kMidCap;
-    const size_t smem = warp_smem<CAP, ACC>();
-    auto kfn = lp_warp_k<WT, ACC, FIRST, CAP, true>;
-    set_smem(kfn, smem);
-    kfn<<<kSMs * 2, kAggThreads, smem, s>>>(0, b.bail_list, b.counts + 6, g.off, g.adj, w, lab, lab_out, hv, g.vact);
-    count_launch();
-    VC_CHECK_LAUNCH();
-  }
-}
-
-template <typename WT>
-void launch_emit_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t* cid, const PairOut& out,
-                     int32_t* cnt, cudaStream_t s) {
-  VC_CUDA(cudaMemsetAsync(b.counts + 7, 0, sizeof(int), s));
-  if (b.h_small > 0) {
-    emit_reg_k<WT, 16, 4><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
-        b.small_list, b.counts + 4, g.off, g.adj, w, cid, out, cnt, b.bail_list2, b.counts + 7);
-    count_launch();
-    VC_CHECK_LAUNCH();
-  }
-  if (b.h_reg > 0) {
-    emit_reg_k<WT, 32, 4><<<grid_for(b.h_reg, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
-        b.reg_list, b.counts + 5, g.off, g.adj, w, cid, out, cnt, b.bail_list2, b.counts + 7);
-    count_launch();
-    VC_CHECK_LAUNCH();
-  }
-  if (b.h_mid > 0) {
-    emit_reg_k<WT, 32, kMidMaxDeg / 32><<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
-        b.mid_list, b.counts + 0, g.off, g.adj, w, cid, out, cnt, b.bail_list2, b.counts + 7);
-    count_launch();
-    VC_CHECK_LAUNCH();
-  }
-  if (b.h_small + b.h_reg + b.h_mid > 0) {  // the lists the walk handed on, in chunks
-    emit_warp_k<WT, 32><<<kSMs * 4, kAggThreads, 0, s>>>(b.bail_list2, b.counts + 7, g.off, g.adj, w, cid, out, cnt);
-    count_launch();
-    VC_CHECK_LAUNCH();
-  }
 }
 
 template <typename WT, typename ACC, bool FIRST>
