@@ -225,14 +225,24 @@ __global__ void __launch_bounds__(256) cluster_scatter_k(int64_t n, const int64_
   }
 }
 
-// A warp per cluster: its (at most kMergeMax) pairs into registers, one step per
-// distinct target (summing its weights), the distinct targets written back in place
-// at the front of the segment; dcount[c] = their number.
+// A warp per cluster of at most kMergeMax pairs, the distinct targets written back in
+// ascending order at the front of the segment; dcount[c] = their number.  The pairs go
+// into registers and the warp takes one step per distinct target (summing its
+// weights) while targets are few; a cluster reaching kMergeWarpKeys targets is sorted
+// instead, in the warp's shared-memory buffer (bitonic network), and every run head
+// sums its run (a step per target costs slots x compares, which only pays while
+// targets are few).
+constexpr int kMergeWarpKeys = 32;
+
 __global__ void __launch_bounds__(256) cluster_merge_k(int64_t c, const long long* __restrict__ cbase,
                                                        int32_t* __restrict__ seg_key, long long* __restrict__ seg_val,
                                                        int32_t* __restrict__ dcount) {
   constexpr int S = kMergeMax / 32;
-  const int lane = threadIdx.x & 31;
+  __shared__ int32_t sk_all[8][kMergeMax];
+  __shared__ long long sv_all[8][kMergeMax];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t* sk = sk_all[wid];
+  long long* sv = sv_all[wid];
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < c; x += warps) {
     const long long b = cbase[x];
@@ -253,15 +263,73 @@ __global__ void __launch_bounds__(256) cluster_merge_k(int64_t c, const long lon
       }
     }
     int made = 0;  // warp-uniform
+    int32_t ok = INT_MAX;
+    long long ov = 0;
     reg_visit<long long, long long, 32, S>(L, 0xffffffffu, [&](int32_t key, long long total) {
-      if (lane == 0) {
-        seg_key[b + made] = key;
-        seg_val[b + made] = total;
-      }
-      ++made;
-      return false;
+      if (lane == made) { ok = key; ov = total; }
+      return ++made >= kMergeWarpKeys;
     });
-    if (lane == 0) dcount[x] = made;
+    if (made < kMergeWarpKeys) {
+      // lane i holds target i: its rank among the made targets places it
+      int rank = 0;
+      for (int j = 0; j < made; ++j) rank += __shfl_sync(0xffffffffu, ok, j) < ok;
+      if (lane < made) {
+        seg_key[b + rank] = ok;
+        seg_val[b + rank] = ov;
+      }
+      if (lane == 0) dcount[x] = made;
+      continue;
+    }
+    // many targets: sort the pairs (from registers) in shared memory
+    int N = 32;
+    while (N < T) N <<= 1;
+#pragma unroll
+    for (int r = 0; r < S; ++r) {
+      const int i = lane + 32 * r;
+      if (i < N) {
+        sk[i] = i < T ? L.k[r] : INT_MAX;
+        sv[i] = i < T ? L.wt[r] : 0;
+      }
+    }
+    __syncwarp();
+    for (int k = 2; k <= N; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = lane; i < N; i += 32) {
+          const int l = i ^ j;
+          if (l > i) {
+            const bool up = (i & k) == 0;
+            const int32_t p = sk[i], q = sk[l];
+            if ((p > q) == up) {
+              sk[i] = q;
+              sk[l] = p;
+              const long long t = sv[i];
+              sv[i] = sv[l];
+              sv[l] = t;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    int out = 0;
+    for (int c0 = 0; c0 < T; c0 += 32) {
+      const int i = c0 + lane;
+      const bool head = i < T && (i == 0 || sk[i - 1] != sk[i]);
+      long long sum = 0;
+      if (head) {
+        sum = sv[i];
+        for (int j = i + 1; j < T && sk[j] == sk[i]; ++j) sum += sv[j];
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, head);
+      if (head) {
+        const int at = out + __popc(bal & ((1u << lane) - 1u));
+        seg_key[b + at] = sk[i];
+        seg_val[b + at] = sum;
+      }
+      out += __popc(bal);
+    }
+    if (lane == 0) dcount[x] = out;
+    __syncwarp();
   }
 }
 
@@ -345,8 +413,8 @@ __global__ void __launch_bounds__(256) cluster_merge_block_k(int64_t c, const lo
   }
 }
 
-// A warp per cluster: its distinct targets land at coff[c] + their rank (targets are
-// distinct, so ranks are a permutation), i.e. in ascending order.
+// The sorted distinct targets of every cluster, copied from the front of its segment
+// to coff[c] (a warp per cluster).
 __global__ void __launch_bounds__(256) cluster_place_k(int64_t c, const long long* __restrict__ cbase,
                                                        const int64_t* __restrict__ coff,
                                                        const int32_t* __restrict__ seg_key,
@@ -360,12 +428,9 @@ __global__ void __launch_bounds__(256) cluster_place_k(int64_t c, const long lon
     const int64_t o = coff[x];
     const int D = (int)(coff[x + 1] - o);
     for (int i = lane; i < D; i += 32) {
-      const int32_t key = seg_key[b + i];
-      int rank = 0;
-      for (int j = 0; j < D; ++j) rank += seg_key[b + j] < key;
-      cadj[o + rank] = key;
-      cw[o + rank] = seg_val[b + i];
-      csrc[o + rank] = (int32_t)x;
+      cadj[o + i] = seg_key[b + i];
+      cw[o + i] = seg_val[b + i];
+      csrc[o + i] = (int32_t)x;
     }
   }
 }
