@@ -42,18 +42,20 @@ void relabel(const int32_t* lab, int64_t n, int32_t* cid, ContractScratch& cs, i
   VC_CHECK_LAUNCH();
 }
 
-// One thread per fine vertex copies its pre-merged list (two entries on average at the
-// level-0 contraction) into the contiguous pair arrays.
+// A warp per fine vertex copies its pre-merged list into the contiguous pair arrays
+// (lists are short on clustered graphs and up to the degree on unclustered ones).
 __global__ void build_pairs_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ cid,
                               const int32_t* __restrict__ cnt, const long long* __restrict__ pos, PairOut in,
                               int bits, unsigned long long* __restrict__ keys, long long* __restrict__ vals) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
     const int k = cnt[v];
     if (k == 0) continue;
     const int64_t src = off[v];
     const long long dst = pos[v];
     const unsigned long long hi = (unsigned long long)cid[v] << bits;
-    for (int j = 0; j < k; ++j) {
+    for (int j = lane; j < k; j += 32) {
       int32_t kk;
       long long x;
       in.get(v, src, j, &kk, &x);
@@ -66,7 +68,7 @@ __global__ void build_pairs_k(int64_t n, const int64_t* __restrict__ off, const 
 void build_pairs(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int bits,
                  unsigned long long* keys, long long* vals, cudaStream_t s) {
   const PairOut in{cs.tmp_key, cs.tmp_val, cs.cmp_key, cs.cmp_val};
-  build_pairs_k<<<grid_for(g.n, 256, kSMs * 8), 256, 0, s>>>(g.n, g.off, cid, cs.cnt, cs.pos, in, bits, keys, vals);
+  build_pairs_k<<<grid_for(g.n, 8, kSMs * 16), 256, 0, s>>>(g.n, g.off, cid, cs.cnt, cs.pos, in, bits, keys, vals);
   count_launch();
   VC_CHECK_LAUNCH();
 }

@@ -65,7 +65,7 @@ struct Workspace {
   cudaStream_t s = nullptr;
   // vertex-sized
   Buf deg, labA, labB, map0, cidT, cur1, side1, flags, rank, cnt, pos, scan64, scan32, hv;
-  Buf partner, pw, parent, slist, rlist, mlist, blist, glist, bcounts, noi_r, noi_seen;
+  Buf partner, pw, parent, slist, rlist, mlist, blist, glist, bl1, bcounts, noi_r, noi_seen;
   // entry-sized
   Buf tmpK, tmpV, cmpK, cmpV;
   // pair-sized
@@ -125,6 +125,7 @@ struct Workspace {
     parent.ensure_n<int32_t>(n);
     slist.ensure_n<int32_t>(n);
     rlist.ensure_n<int32_t>(n);
+    bl1.ensure_n<int32_t>(n);
     cmpK.ensure_n<int32_t>(kPairSlots * n);
     cmpV.ensure_n<long long>(kPairSlots * n);
     mlist.ensure_n<int32_t>(n);
@@ -247,6 +248,7 @@ struct Workspace {
     bins.mid_list = mlist.as<int32_t>();
     bins.block_list = blist.as<int32_t>();
     bins.global_list = glist.as<int32_t>();
+    bins.bail_list = bl1.as<int32_t>();
     bins.counts = bcounts.as<int>();
     bins_build(g, bins, s);
     int hc[6];

@@ -58,8 +58,9 @@ struct Bins {
   int32_t* mid_list;     // [n]
   int32_t* block_list;   // [n]
   int32_t* global_list;  // [n]
+  int32_t* bail_list;    // [n] mid-class lists the pre-merge's register walk handed on
   int* counts;           // device: [0] mid, [1] block, [2] global count, [3] max length above
-                         // 128, [4] small, [5] reg count
+                         // 128, [4] small, [5] reg, [7] bail count
   int h_mid = 0, h_block = 0, h_global = 0, h_maxdeg = 0, h_small = 0, h_reg = 0;  // host copies
 };
 

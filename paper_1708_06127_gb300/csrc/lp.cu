@@ -308,6 +308,8 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
 // so the warp software-pipelines its vertices: while it works on one vertex per
 // group it already holds the next vertex's ids and the offsets of the one after.
 
+constexpr int kEmitBailKeys = 64;
+
 // Neighbour ids (and weights) of one list in registers.
 template <int S>
 struct RegIds {
@@ -467,7 +469,8 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restr
                                                           const int64_t* __restrict__ off,
                                                           const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                           const int32_t* __restrict__ cid, PairOut out,
-                                                          int32_t* __restrict__ cnt) {
+                                                          int32_t* __restrict__ cnt, int32_t* __restrict__ bail_list,
+                                                          int* __restrict__ bail_count) {
   const int lane = threadIdx.x & 31, glane = lane & (G - 1), gi = lane / G;
   const unsigned gmask = group_mask<G>(lane);
   constexpr int kPer = 32 / G;
@@ -484,15 +487,24 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restr
     int made = 0;  // the same in the group's lanes
     int32_t pk = 0;
     long long pv = 0;
+    // with a bail list, a list reaching kEmitBailKeys foreign clusters is handed to the
+    // chunk kernel (a step per key costs slots x compares: long lists with many keys
+    // run faster in chunks)
+    bool bailed = false;
     reg_visit<WT, long long, G, S>(L, gmask, [&](int32_t kk, long long t) {
       if (glane == (made & (G - 1))) { pk = kk; pv = t; }
       if ((++made & (G - 1)) == 0) out.put(v, beg, made - G + glane, pk, pv);
+      if (bail_list && made >= kEmitBailKeys) { bailed = true; return true; }
       return false;
     });
-    if (glane < (made & (G - 1))) out.put(v, beg, (made & ~(G - 1)) + glane, pk, pv);
-    if (mine && glane == 0) {
-      cnt[v] = made;
-      if (out.ccount && made) atomicAdd(&out.ccount[own], made);
+    if (bailed) {
+      if (glane == 0) bail_list[atomicAdd(bail_count, 1)] = (int32_t)v;
+    } else {
+      if (glane < (made & (G - 1))) out.put(v, beg, (made & ~(G - 1)) + glane, pk, pv);
+      if (mine && glane == 0) {
+        cnt[v] = made;
+        if (out.ccount && made) atomicAdd(&out.ccount[own], made);
+      }
     }
   });
 }
@@ -520,28 +532,6 @@ void launch_lp_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t
   }
 }
 
-template <typename WT>
-void launch_emit_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t* cid, const PairOut& out,
-                     int32_t* cnt, cudaStream_t s) {
-  if (b.h_small > 0) {
-    emit_reg_k<WT, 16, 4><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
-        b.small_list, b.counts + 4, g.off, g.adj, w, cid, out, cnt);
-    count_launch();
-    VC_CHECK_LAUNCH();
-  }
-  if (b.h_reg > 0) {
-    emit_reg_k<WT, 32, 4><<<grid_for(b.h_reg, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
-        b.reg_list, b.counts + 5, g.off, g.adj, w, cid, out, cnt);
-    count_launch();
-    VC_CHECK_LAUNCH();
-  }
-  if (b.h_mid > 0) {
-    emit_reg_k<WT, 32, kMidMaxDeg / 32><<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
-        b.mid_list, b.counts + 0, g.off, g.adj, w, cid, out, cnt);
-    count_launch();
-    VC_CHECK_LAUNCH();
-  }
-}
 
 // First round on a graph whose lists are strictly increasing: every neighbour is its
 // own label, so S(u) = c(v,u) and the choice is the argmax of (c(v,u), hash(u), -u)
@@ -873,6 +863,32 @@ void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const 
                                                                     lab, lab_out, key, gt.keys, gt.vals, gt.cap,
                                                                     g.vact);
     count_launch();
+    VC_CHECK_LAUNCH();
+  }
+}
+
+template <typename WT>
+void launch_emit_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t* cid, const PairOut& out,
+                     int32_t* cnt, cudaStream_t s) {
+  if (b.h_small > 0) {
+    emit_reg_k<WT, 16, 4><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
+        b.small_list, b.counts + 4, g.off, g.adj, w, cid, out, cnt, nullptr, nullptr);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
+  if (b.h_reg > 0) {
+    emit_reg_k<WT, 32, 4><<<grid_for(b.h_reg, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
+        b.reg_list, b.counts + 5, g.off, g.adj, w, cid, out, cnt, nullptr, nullptr);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  }
+  if (b.h_mid > 0) {
+    VC_CUDA(cudaMemsetAsync(b.counts + 7, 0, sizeof(int), s));
+    emit_reg_k<WT, 32, kMidMaxDeg / 32><<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
+        b.mid_list, b.counts + 0, g.off, g.adj, w, cid, out, cnt, b.bail_list, b.counts + 7);
+    emit_warp_k<WT, 32><<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 4), kAggThreads, 0, s>>>(
+        b.bail_list, b.counts + 7, g.off, g.adj, w, cid, out, cnt);
+    count_launch(2);
     VC_CHECK_LAUNCH();
   }
 }
