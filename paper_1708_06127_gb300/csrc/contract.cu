@@ -42,20 +42,22 @@ void relabel(const int32_t* lab, int64_t n, int32_t* cid, ContractScratch& cs, i
   VC_CHECK_LAUNCH();
 }
 
-// A warp per fine vertex copies its pre-merged list into the contiguous pair arrays
-// (lists are short on clustered graphs and up to the degree on unclustered ones).
+// W lanes per fine vertex copy its pre-merged list into the contiguous pair arrays: a
+// thread per vertex where lists are short (two entries on average on clustered graphs),
+// wider groups where they run up to the degree (unclustered graphs).
+template <int W>
 __global__ void build_pairs_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ cid,
                               const int32_t* __restrict__ cnt, const long long* __restrict__ pos, PairOut in,
                               int bits, unsigned long long* __restrict__ keys, long long* __restrict__ vals) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+  const int lane = threadIdx.x & (W - 1);
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / W);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W; v < n; v += groups) {
     const int k = cnt[v];
     if (k == 0) continue;
     const int64_t src = off[v];
     const long long dst = pos[v];
     const unsigned long long hi = (unsigned long long)cid[v] << bits;
-    for (int j = lane; j < k; j += 32) {
+    for (int j = lane; j < k; j += W) {
       int32_t kk;
       long long x;
       in.get(v, src, j, &kk, &x);
@@ -65,10 +67,15 @@ __global__ void build_pairs_k(int64_t n, const int64_t* __restrict__ off, const 
   }
 }
 
-void build_pairs(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int bits,
+void build_pairs(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int bits, int64_t pairs,
                  unsigned long long* keys, long long* vals, cudaStream_t s) {
   const PairOut in{cs.tmp_key, cs.tmp_val, cs.cmp_key, cs.cmp_val};
-  build_pairs_k<<<grid_for(g.n, 8, kSMs * 16), 256, 0, s>>>(g.n, g.off, cid, cs.cnt, cs.pos, in, bits, keys, vals);
+  if (pairs <= 2 * g.n)
+    build_pairs_k<1><<<grid_for(g.n, 256, kSMs * 8), 256, 0, s>>>(g.n, g.off, cid, cs.cnt, cs.pos, in, bits, keys, vals);
+  else if (pairs <= 16 * g.n)
+    build_pairs_k<8><<<grid_for(g.n, 32, kSMs * 16), 256, 0, s>>>(g.n, g.off, cid, cs.cnt, cs.pos, in, bits, keys, vals);
+  else
+    build_pairs_k<32><<<grid_for(g.n, 8, kSMs * 16), 256, 0, s>>>(g.n, g.off, cid, cs.cnt, cs.pos, in, bits, keys, vals);
   count_launch();
   VC_CHECK_LAUNCH();
 }
@@ -233,12 +240,15 @@ __global__ void __launch_bounds__(256) cluster_scatter_k(int64_t n, const int64_
 // weights) while targets are few; a cluster reaching kMergeWarpKeys targets is sorted
 // instead, in the warp's shared-memory buffer (bitonic network), and every run head
 // sums its run (a step per target costs slots x compares, which only pays while
-// targets are few).
+// targets are few).  With sort_first (a contraction whose clusters are mostly one or
+// two vertices: nearly every pair its own target) a cluster of at least kMergeSortMin
+// pairs is sorted without walking first.
 constexpr int kMergeWarpKeys = 32;
+constexpr int kMergeSortMin = 12;
 
 __global__ void __launch_bounds__(256) cluster_merge_k(int64_t c, const long long* __restrict__ cbase,
                                                        int32_t* __restrict__ seg_key, long long* __restrict__ seg_val,
-                                                       int32_t* __restrict__ dcount) {
+                                                       int32_t* __restrict__ dcount, bool sort_first) {
   constexpr int S = kMergeMax / 32;
   __shared__ int32_t sk_all[8][kMergeMax];
   __shared__ long long sv_all[8][kMergeMax];
@@ -264,23 +274,25 @@ __global__ void __launch_bounds__(256) cluster_merge_k(int64_t c, const long lon
         L.todo |= 1u << r;
       }
     }
-    int made = 0;  // warp-uniform
-    int32_t ok = INT_MAX;
-    long long ov = 0;
-    reg_visit<long long, long long, 32, S>(L, 0xffffffffu, [&](int32_t key, long long total) {
-      if (lane == made) { ok = key; ov = total; }
-      return ++made >= kMergeWarpKeys;
-    });
-    if (made < kMergeWarpKeys) {
-      // lane i holds target i: its rank among the made targets places it
-      int rank = 0;
-      for (int j = 0; j < made; ++j) rank += __shfl_sync(0xffffffffu, ok, j) < ok;
-      if (lane < made) {
-        seg_key[b + rank] = ok;
-        seg_val[b + rank] = ov;
+    if (!sort_first || T < kMergeSortMin) {
+      int made = 0;  // warp-uniform
+      int32_t ok = INT_MAX;
+      long long ov = 0;
+      reg_visit<long long, long long, 32, S>(L, 0xffffffffu, [&](int32_t key, long long total) {
+        if (lane == made) { ok = key; ov = total; }
+        return ++made >= kMergeWarpKeys;
+      });
+      if (made < kMergeWarpKeys) {
+        // lane i holds target i: its rank among the made targets places it
+        int rank = 0;
+        for (int j = 0; j < made; ++j) rank += __shfl_sync(0xffffffffu, ok, j) < ok;
+        if (lane < made) {
+          seg_key[b + rank] = ok;
+          seg_val[b + rank] = ov;
+        }
+        if (lane == 0) dcount[x] = made;
+        continue;
       }
-      if (lane == 0) dcount[x] = made;
-      continue;
     }
     // many targets: sort the pairs (from registers) in shared memory
     int N = 32;
@@ -446,13 +458,14 @@ void cluster_stats(int64_t n, const int32_t* ccount, int* maxt, long long* pairs
 
 void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int32_t* ccount, int64_t c,
                    long long* cbase, long long* cursor, int32_t* seg_key, long long* seg_val, int64_t* coff,
-                   int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, bool big, cudaStream_t s) {
+                   int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, bool big, bool sort_first,
+                   cudaStream_t s) {
   exclusive_scan<int, long long>(ccount, cbase, c, cbase + c, cs.scan_scr, s);
   VC_CUDA(cudaMemcpyAsync(cursor, cbase, sizeof(long long) * c, cudaMemcpyDeviceToDevice, s));
   const int gv = grid_for(g.n, 256, kSMs * 8), gc = grid_for(c, 8, kSMs * 16);
   const PairOut in{cs.tmp_key, cs.tmp_val, cs.cmp_key, cs.cmp_val};
   cluster_scatter_k<<<gv, 256, 0, s>>>(g.n, g.off, cid, cs.cnt, in, cursor, seg_key, seg_val);
-  cluster_merge_k<<<gc, 256, 0, s>>>(c, cbase, seg_key, seg_val, ccount);
+  cluster_merge_k<<<gc, 256, 0, s>>>(c, cbase, seg_key, seg_val, ccount, sort_first);
   count_launch(2);
   VC_CHECK_LAUNCH();
   if (big) {

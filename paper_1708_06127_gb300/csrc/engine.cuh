@@ -313,6 +313,8 @@ struct Workspace {
     cs.scan_scr32 = scan32.as<int>();
     relabel(labels, g.n, cid_out, cs, &ctr()->c, s);
     PairOut po{cs.tmp_key, cs.tmp_val, cs.cmp_key, cs.cmp_val};
+    po.nclust = &ctr()->c;
+    po.nfine = g.n;
     tune_emit(g, cid_out, po, cs.cnt);  // trials: no counting
     // the pre-merge also counts pairs per cluster (flags is free again after the relabel)
     int32_t* ccount = cs.flags;
@@ -338,7 +340,7 @@ struct Workspace {
       scan64.ensure_n<long long>(scan_scratch_elems(std::max<int64_t>(c, 1)) + 1);
       cs.scan_scr = scan64.as<long long>();
       cluster_merge(g, cid_out, cs, ccount, c, cbase, cur, sk, sv, co, ca, cwp, csp, &st()->nnz,
-                    h_counters->maxt > kMergeMax, s);
+                    h_counters->maxt > kMergeMax, 2 * c >= g.n, s);
     } else {
       exclusive_scan<int, long long>(cs.cnt, cs.pos, g.n, &ctr()->pairs, cs.scan_scr, s);
       int bits = ceil_log2(c);
@@ -351,7 +353,7 @@ struct Workspace {
       auto* hd = heads.ensure_n<int32_t>(P);
       auto* hp = hpos.ensure_n<long long>(P + 1);
       scan64.ensure_n<long long>(scan_scratch_elems(std::max<int64_t>(P, 1)) + 1);
-      build_pairs(g, cid_out, cs, bits, kA, vA, s);
+      build_pairs(g, cid_out, cs, bits, P, kA, vA, s);
       radix_sort_pairs(kA, vA, kB, vB, P, 2 * bits, hs, s);
       reduce_pairs(kA, vA, P, bits, c, hd, hp, scan64.as<long long>(), co, ca, cwp, csp, &st()->nnz, s);
     }

@@ -103,6 +103,14 @@ struct PairOut {
   int32_t* ckey;
   long long* cval;
   int32_t* ccount = nullptr;  // if set: ccount[cid[v]] += the pairs of v (pairs per cluster)
+  // If set: *nclust is the cluster count of this contraction (on the device), and a
+  // contraction with at least nfine / 2 clusters (most clusters one or two vertices:
+  // nearly every neighbour its own key) pre-merges each G-entry row of a list on its own
+  // (one match per row instead of one step per distinct key); the pairs of a vertex may
+  // then repeat a key across rows, which the cluster merge sums.
+  const int* nclust = nullptr;
+  int64_t nfine = 0;
+  __device__ __forceinline__ bool by_rows() const { return nclust && 2LL * __ldg(nclust) >= nfine; }
   __device__ __forceinline__ void put(int64_t v, int64_t beg, int i, int32_t k, long long x) const {
     if (i < kPairSlots) {
       ckey[v * kPairSlots + i] = k;
@@ -156,10 +164,11 @@ constexpr int kMergeBlockMax = 4096;
 void cluster_stats(int64_t n, const int32_t* ccount, int* maxt, long long* pairs, cudaStream_t s);
 void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int32_t* ccount, int64_t c,
                    long long* cbase, long long* cursor, int32_t* seg_key, long long* seg_val, int64_t* coff,
-                   int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, bool big, cudaStream_t s);
+                   int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, bool big, bool sort_first,
+                   cudaStream_t s);
 
 // Builds (cid[v] << bits | cu, weight) pairs from the pre-merged lists.
-void build_pairs(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int bits,
+void build_pairs(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int bits, int64_t pairs,
                  unsigned long long* keys, long long* vals, cudaStream_t s);
 
 // From sorted pairs: merge equal keys, write the coarse CSR (offsets for c

@@ -476,6 +476,7 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restr
   constexpr int kPer = 32 / G;
   const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock * kPer;
   const int64_t first = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kPer;
+  const bool rows = out.by_rows();
   reg_pipeline<WT, G, S>(list, *count_ptr, first, stride, glane, gi, off, adj, w,
                       [&](int64_t v) { return __ldg(cid + v); },
                       [&](int64_t v, bool valid, int64_t beg, int64_t end, int32_t own, const RegIds<S>& ids) {
@@ -485,6 +486,43 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restr
     reg_keys<kModeEmit, false, G, S>(L, ids, (mine && own >= 0) ? (int)d : 0, cid, own);
     if (!(mine && own >= 0)) L.todo = 0;
     int made = 0;  // the same in the group's lanes
+    if (rows) {
+      // row r holds entries r G .. r G + G - 1: lanes holding the same key (tagged with
+      // the group) match, the lowest of them sums its peers' weights and writes the pair
+      const int ws = __reduce_max_sync(0xffffffffu, L.slots);
+#pragma unroll
+      for (int r = 0; r < S; ++r) {
+        if (r >= ws) break;
+        const bool use = (L.todo >> r) & 1u;
+        const unsigned long long tag =
+            use ? ((unsigned long long)(uint32_t)L.k[r] | ((unsigned long long)gi << 32))
+                : (0xffffffff00000000ull | (unsigned long long)lane);
+        const unsigned peers = __match_any_sync(0xffffffffu, tag);
+        const bool lead = use && (__ffs(peers) - 1) == lane;
+        long long sum;
+        if (std::is_same<WT, UnitW>::value) {
+          sum = __popc(peers);
+        } else {
+          sum = L.wt[r];
+          unsigned rest = lead ? (peers & (peers - 1u)) : 0u;
+          while (__any_sync(0xffffffffu, rest != 0u)) {
+            const long long x = __shfl_sync(0xffffffffu, L.wt[r], rest ? __ffs(rest) - 1 : lane);
+            if (rest) {
+              sum += x;
+              rest &= rest - 1u;
+            }
+          }
+        }
+        const unsigned lb = __ballot_sync(0xffffffffu, lead) & gmask;
+        if (lead) out.put(v, beg, made + __popc(lb & ((1u << lane) - 1u)), L.k[r], sum);
+        made += __popc(lb);
+      }
+      if (mine && glane == 0) {
+        cnt[v] = made;
+        if (out.ccount && made) atomicAdd(&out.ccount[own], made);
+      }
+      return;
+    }
     int32_t pk = 0;
     long long pv = 0;
     // with a bail list, a list reaching kEmitBailKeys foreign clusters is handed to the
@@ -683,6 +721,46 @@ __device__ __forceinline__ void emit_chunk(int64_t e, int64_t end, const int32_t
   }
 }
 
+// The same chunk, pre-merged with one match: the lowest lane holding each foreign key
+// sums its peers' weights and writes the pair.  The cost does not grow with the
+// distinct keys of the chunk (lists whose neighbours are nearly all in clusters of their
+// own).  `reserve(k)` returns the index of the chunk's first of k pairs.
+template <typename WT, int G, typename RESERVE>
+__device__ __forceinline__ void emit_chunk_rows(int64_t e, int64_t end, const int32_t* __restrict__ adj,
+                                                const WT* __restrict__ w, const int32_t* __restrict__ cid,
+                                                int32_t own, int lane, unsigned gmask, const PairOut& out, int64_t v,
+                                                int64_t beg, RESERVE reserve) {
+  int32_t k = -1;
+  long long wt = 0;
+  bool use = false;
+  if (e < end) {
+    k = __ldg(cid + __ldg(adj + e));
+    use = k != own;
+    wt = ldw(w, e);
+  }
+  const unsigned long long tag = use ? (unsigned long long)(uint32_t)k : (0xffffffff00000000ull | (unsigned)lane);
+  const unsigned peers = __match_any_sync(gmask, tag);
+  const bool lead = use && (__ffs(peers) - 1) == lane;
+  long long sum;
+  if (std::is_same<WT, UnitW>::value) {
+    sum = __popc(peers);
+  } else {
+    sum = wt;
+    unsigned rest = lead ? (peers & (peers - 1u)) : 0u;
+    while (__any_sync(gmask, rest != 0u)) {
+      const long long x = __shfl_sync(gmask, wt, rest ? __ffs(rest) - 1 : lane);
+      if (rest) {
+        sum += x;
+        rest &= rest - 1u;
+      }
+    }
+  }
+  const unsigned lb = __ballot_sync(gmask, lead) & gmask;
+  if (lb == 0u) return;
+  const int at = reserve(__popc(lb));
+  if (lead) out.put(v, beg, at + __popc(lb & ((1u << lane) - 1u)), k, sum);
+}
+
 // Listed vertices (the mid and block classes), G lanes per vertex: 32 / G vertices
 // per warp, each group walking its list in G-entry chunks.
 template <typename WT, int G>
@@ -696,15 +774,25 @@ __global__ void __launch_bounds__(kAggThreads) emit_warp_k(const int32_t* __rest
   const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
   const int64_t total = *count_ptr;
+  const bool rows = out.by_rows();
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; i < total; i += groups) {
     const int32_t v = __ldg(list + i);
     const int64_t beg = __ldg(off + v), end = __ldg(off + v + 1);
     const int32_t own = __ldg(cid + v);
     int made = 0;  // group-uniform
-    if (own >= 0)
-      for (int64_t base = beg; base < end; base += G)
-        emit_chunk<WT, G>(base + glane, end, adj, w, cid, own, lane, gmask, out, v, beg,
-                          [&](int) { return made++; });
+    if (own >= 0) {
+      if (rows)
+        for (int64_t base = beg; base < end; base += G)
+          emit_chunk_rows<WT, G>(base + glane, end, adj, w, cid, own, lane, gmask, out, v, beg, [&](int k) {
+            const int at = made;
+            made += k;
+            return at;
+          });
+      else
+        for (int64_t base = beg; base < end; base += G)
+          emit_chunk<WT, G>(base + glane, end, adj, w, cid, own, lane, gmask, out, v, beg,
+                            [&](int) { return made++; });
+    }
     if (glane == 0) {
       cnt[v] = made;
       if (out.ccount && made) atomicAdd(&out.ccount[own], made);
@@ -722,19 +810,29 @@ __global__ void __launch_bounds__(kAggThreads) emit_block_k(const int32_t* __res
   __shared__ int s_made;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int count = *count_ptr;
+  const bool rows = out.by_rows();
   for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
     const int32_t v = list[idx];
     const int64_t beg = off[v], end = off[v + 1];
     const int32_t own = cid[v];
     if (threadIdx.x == 0) s_made = 0;
     __syncthreads();
-    if (own >= 0)
-      for (int64_t base = beg + 32 * wib; base < end; base += 32 * kWarpsPerBlock)
-        emit_chunk<WT, 32>(base + lane, end, adj, w, cid, own, lane, 0xffffffffu, out, v, beg, [&](int leader) {
-          int at = 0;
-          if (lane == leader) at = atomicAdd(&s_made, 1);
-          return __shfl_sync(0xffffffffu, at, leader);
-        });
+    if (own >= 0) {
+      if (rows)
+        for (int64_t base = beg + 32 * wib; base < end; base += 32 * kWarpsPerBlock)
+          emit_chunk_rows<WT, 32>(base + lane, end, adj, w, cid, own, lane, 0xffffffffu, out, v, beg, [&](int k) {
+            int at = 0;
+            if (lane == 0) at = atomicAdd(&s_made, k);
+            return __shfl_sync(0xffffffffu, at, 0);
+          });
+      else
+        for (int64_t base = beg + 32 * wib; base < end; base += 32 * kWarpsPerBlock)
+          emit_chunk<WT, 32>(base + lane, end, adj, w, cid, own, lane, 0xffffffffu, out, v, beg, [&](int leader) {
+            int at = 0;
+            if (lane == leader) at = atomicAdd(&s_made, 1);
+            return __shfl_sync(0xffffffffu, at, leader);
+          });
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       cnt[v] = s_made;
