@@ -212,8 +212,8 @@ __global__ void __launch_bounds__(256) cluster_scatter_k(int64_t n, const int64_
     long long at = 0;
     if (c >= 0 && lane == leader) at = atomicAdd((unsigned long long*)&cursor[c], (unsigned long long)t);
     at = __shfl_sync(0xffffffffu, at, leader);
+    const long long dst = at + b;
     if (c >= 0) {
-      const long long dst = at + b;
       // the first kPairSlots pairs from the dense strip, all in flight at once
       int32_t kk[kPairSlots];
       long long vv[kPairSlots];
@@ -223,12 +223,18 @@ __global__ void __launch_bounds__(256) cluster_scatter_k(int64_t n, const int64_
 #pragma unroll
       for (int j = 0; j < kPairSlots; ++j)
         if (j < k) { seg_key[dst + j] = kk[j]; seg_val[dst + j] = vv[j]; }
-      if (k > kPairSlots) {
-        const int64_t src = off[v];
-        for (int j = kPairSlots; j < k; ++j) {
-          seg_key[dst + j] = in.tkey[src + j];
-          seg_val[dst + j] = in.tval[src + j];
-        }
+    }
+    // the rest of longer lists, one list at a time by the whole warp (coalesced)
+    unsigned longs = __ballot_sync(0xffffffffu, c >= 0 && k > kPairSlots);
+    while (longs) {
+      const int l = __ffs(longs) - 1;
+      longs &= longs - 1u;
+      const int kl = __shfl_sync(0xffffffffu, k, l);
+      const long long dl = __shfl_sync(0xffffffffu, dst, l);
+      const int64_t sl = off[base + l];
+      for (int j = kPairSlots + lane; j < kl; j += 32) {
+        seg_key[dl + j] = in.tkey[sl + j];
+        seg_val[dl + j] = in.tval[sl + j];
       }
     }
   }
@@ -294,7 +300,26 @@ __global__ void __launch_bounds__(256) cluster_merge_k(int64_t c, const long lon
         continue;
       }
     }
-    // many targets: sort the pairs (from registers) in shared memory
+    if (sort_first) {
+      // pairs already strictly ascending (one vertex's list over near-monotone ids)
+      // stay where they are
+      bool asc = true;
+#pragma unroll
+      for (int r = 0; r < S; ++r) {
+        if (32 * r < T) {
+          const int32_t up = __shfl_up_sync(0xffffffffu, L.k[r], 1);
+          const int32_t wrap = r > 0 ? __shfl_sync(0xffffffffu, L.k[r > 0 ? r - 1 : 0], 31) : INT_MIN;
+          const int i = lane + 32 * r;
+          if (i < T && i > 0 && (lane ? up : wrap) >= L.k[r]) asc = false;
+        }
+      }
+      if (__all_sync(0xffffffffu, asc)) {
+        if (lane == 0) dcount[x] = T;
+        continue;
+      }
+    }
+    // many targets: sort the pairs (from registers) in shared memory; each stage of the
+    // bitonic network compares N / 2 pairs (i, i + j), i with bit j clear
     int N = 32;
     while (N < T) N <<= 1;
 #pragma unroll
@@ -308,18 +333,17 @@ __global__ void __launch_bounds__(256) cluster_merge_k(int64_t c, const long lon
     __syncwarp();
     for (int k = 2; k <= N; k <<= 1) {
       for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int i = lane; i < N; i += 32) {
-          const int l = i ^ j;
-          if (l > i) {
-            const bool up = (i & k) == 0;
-            const int32_t p = sk[i], q = sk[l];
-            if ((p > q) == up) {
-              sk[i] = q;
-              sk[l] = p;
-              const long long t = sv[i];
-              sv[i] = sv[l];
-              sv[l] = t;
-            }
+        for (int p = lane; p < (N >> 1); p += 32) {
+          const int i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
+          const int l = i | j;
+          const bool up = (i & k) == 0;
+          const int32_t a = sk[i], q = sk[l];
+          if (up ? a > q : a < q) {
+            sk[i] = q;
+            sk[l] = a;
+            const long long t = sv[i];
+            sv[i] = sv[l];
+            sv[l] = t;
           }
         }
         __syncwarp();
@@ -373,18 +397,17 @@ __global__ void __launch_bounds__(256) cluster_merge_block_k(int64_t c, const lo
     __syncthreads();
     for (int k = 2; k <= N; k <<= 1) {
       for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int i = tid; i < N; i += 256) {
-          const int l = i ^ j;
-          if (l > i) {
-            const bool up = (i & k) == 0;
-            const int32_t a = sk[i], bb = sk[l];
-            if ((a > bb) == up) {
-              sk[i] = bb;
-              sk[l] = a;
-              const long long t = sv[i];
-              sv[i] = sv[l];
-              sv[l] = t;
-            }
+        for (int p = tid; p < (N >> 1); p += 256) {  // pair (i, i + j), i with bit j clear
+          const int i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
+          const int l = i | j;
+          const bool up = (i & k) == 0;
+          const int32_t a = sk[i], bb = sk[l];
+          if (up ? a > bb : a < bb) {
+            sk[i] = bb;
+            sk[l] = a;
+            const long long t = sv[i];
+            sv[i] = sv[l];
+            sv[l] = t;
           }
         }
         __syncthreads();
