@@ -166,7 +166,7 @@ __device__ __forceinline__ void group_sums(int32_t c, int k, int lane, int* sk, 
 
 // The largest pairs-per-cluster count and the total, over ccount[0, n).
 __global__ void __launch_bounds__(256) cluster_stats_k(int64_t n, const int32_t* __restrict__ ccount, int* maxt,
-                                                       long long* pairs) {
+                                                       long long* pairs, int* ngiant, long long* gpairs) {
   __shared__ int s_max;
   __shared__ unsigned long long s_sum;
   if (threadIdx.x == 0) { s_max = 0; s_sum = 0; }
@@ -177,6 +177,10 @@ __global__ void __launch_bounds__(256) cluster_stats_k(int64_t n, const int32_t*
     const int x = ccount[i];
     top = max(top, x);
     sum += x;
+    if (x > kMergeBlockMax) {  // rare
+      atomicAdd(ngiant, 1);
+      atomicAdd((unsigned long long*)gpairs, (unsigned long long)x);
+    }
   }
   const unsigned wtop = __reduce_max_sync(0xffffffffu, (unsigned)top);
   const long long w = warp_sum(sum);
@@ -387,7 +391,7 @@ __global__ void __launch_bounds__(256) cluster_merge_block_k(int64_t c, const lo
   for (int64_t x = blockIdx.x; x < c; x += gridDim.x) {
     const long long b = cbase[x];
     const int T = (int)(cbase[x + 1] - b);
-    if (T <= kMergeMax) continue;  // the same in every thread of the block
+    if (T <= kMergeMax || T > kMergeBlockMax) continue;  // the same in every thread of the block
     int N = 1;
     while (N < T) N <<= 1;
     for (int i = tid; i < N; i += 256) {
@@ -472,9 +476,91 @@ __global__ void __launch_bounds__(256) cluster_place_k(int64_t c, const long lon
   }
 }
 
-void cluster_stats(int64_t n, const int32_t* ccount, int* maxt, long long* pairs, cudaStream_t s) {
+// ---------------------------------------------------------------- giant clusters
+__global__ void giant_list_k(int64_t c, const long long* __restrict__ cbase, int* __restrict__ gcount,
+                             int32_t* __restrict__ glist, int32_t* __restrict__ gT) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < c; x += (int64_t)gridDim.x * blockDim.x) {
+    const long long T = cbase[x + 1] - cbase[x];
+    if (T > kMergeBlockMax) {
+      const int j = atomicAdd(gcount, 1);
+      glist[j] = (int32_t)x;
+      gT[j] = (int32_t)T;
+    }
+  }
+}
+
+// The giant clusters' pairs, keyed (j << bits | target) for giant j.
+__global__ void giant_gather_k(int ng, const int32_t* __restrict__ glist, const long long* __restrict__ gstart,
+                               const long long* __restrict__ cbase, const int32_t* __restrict__ seg_key,
+                               const long long* __restrict__ seg_val, int bits, unsigned long long* __restrict__ keys,
+                               long long* __restrict__ vals) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  for (int j = 0; j < ng; ++j) {
+    const long long b = cbase[glist[j]], o = gstart[j], T = gstart[j + 1] - o;
+    for (int64_t e = t0; e < T; e += st) {
+      keys[o + e] = ((unsigned long long)j << bits) | (unsigned long long)(uint32_t)seg_key[b + e];
+      vals[o + e] = seg_val[b + e];
+    }
+  }
+}
+
+// Every run head of the sorted giant pairs sums its run and writes it at its rank within
+// its cluster, at the front of the cluster's segment.
+__global__ void giant_reduce_k(int64_t m, int bits, const unsigned long long* __restrict__ keys,
+                               const long long* __restrict__ vals, const int32_t* __restrict__ heads,
+                               const long long* __restrict__ hpos, const long long* __restrict__ gstart,
+                               const int32_t* __restrict__ glist, const long long* __restrict__ cbase,
+                               int32_t* __restrict__ seg_key, long long* __restrict__ seg_val) {
+  const unsigned long long mask = (1ULL << bits) - 1ULL;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!heads[i]) continue;
+    const unsigned long long k = keys[i];
+    long long sum = vals[i];
+    for (int64_t q = i + 1; q < m && keys[q] == k; ++q) sum += vals[q];
+    const int j = (int)(k >> bits);
+    const long long at = cbase[glist[j]] + (hpos[i] - hpos[gstart[j]]);
+    seg_key[at] = (int32_t)(k & mask);
+    seg_val[at] = sum;
+  }
+}
+
+__global__ void giant_count_k(int ng, const int32_t* __restrict__ glist, const long long* __restrict__ gstart,
+                              const long long* __restrict__ hpos, int32_t* __restrict__ dcount) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ng; j += gridDim.x * blockDim.x)
+    dcount[glist[j]] = (int32_t)(hpos[gstart[j + 1]] - hpos[gstart[j]]);
+}
+
+static void giant_merge(const GiantScratch& G, int64_t c, const long long* cbase, int32_t* seg_key,
+                        long long* seg_val, int32_t* dcount, long long* scan_scr, cudaStream_t s) {
+  VC_CUDA(cudaMemsetAsync(G.gcount, 0, sizeof(int), s));
+  giant_list_k<<<grid_for(c, 256, kSMs * 8), 256, 0, s>>>(c, cbase, G.gcount, G.glist, G.gT);
+  count_launch();
+  VC_CHECK_LAUNCH();
+  exclusive_scan<int, long long>(G.gT, G.gstart, G.ngiant, G.gstart + G.ngiant, scan_scr, s);
+  int bits = ceil_log2(c);
+  if (bits < 1) bits = 1;
+  int jbits = ceil_log2(G.ngiant);
+  if (jbits < 1) jbits = 1;
+  const int grid = grid_for(G.pairs, 256, kSMs * 8);
+  giant_gather_k<<<grid, 256, 0, s>>>(G.ngiant, G.glist, G.gstart, cbase, seg_key, seg_val, bits, G.k0, G.v0);
+  count_launch();
+  VC_CHECK_LAUNCH();
+  radix_sort_pairs(G.k0, G.v0, G.k1, G.v1, G.pairs, bits + jbits, G.hist, s);
+  run_heads_k<<<grid, 256, 0, s>>>(G.k0, G.pairs, G.heads);
+  count_launch();
+  VC_CHECK_LAUNCH();
+  exclusive_scan<int, long long>(G.heads, G.hpos, G.pairs, G.hpos + G.pairs, scan_scr, s);
+  giant_reduce_k<<<grid, 256, 0, s>>>(G.pairs, bits, G.k0, G.v0, G.heads, G.hpos, G.gstart, G.glist, cbase, seg_key,
+                                      seg_val);
+  giant_count_k<<<grid_for(G.ngiant, 256, kSMs), 256, 0, s>>>(G.ngiant, G.glist, G.gstart, G.hpos, dcount);
+  count_launch(2);
+  VC_CHECK_LAUNCH();
+}
+
+void cluster_stats(int64_t n, const int32_t* ccount, int* maxt, long long* pairs, int* ngiant, long long* gpairs,
+                   cudaStream_t s) {
   if (n <= 0) return;
-  cluster_stats_k<<<grid_for(n, 256, kSMs * 4), 256, 0, s>>>(n, ccount, maxt, pairs);
+  cluster_stats_k<<<grid_for(n, 256, kSMs * 4), 256, 0, s>>>(n, ccount, maxt, pairs, ngiant, gpairs);
   count_launch();
   VC_CHECK_LAUNCH();
 }
@@ -482,7 +568,7 @@ void cluster_stats(int64_t n, const int32_t* ccount, int* maxt, long long* pairs
 void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int32_t* ccount, int64_t c,
                    long long* cbase, long long* cursor, int32_t* seg_key, long long* seg_val, int64_t* coff,
                    int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, bool big, bool sort_first,
-                   cudaStream_t s) {
+                   const GiantScratch* giant, cudaStream_t s) {
   exclusive_scan<int, long long>(ccount, cbase, c, cbase + c, cs.scan_scr, s);
   VC_CUDA(cudaMemcpyAsync(cursor, cbase, sizeof(long long) * c, cudaMemcpyDeviceToDevice, s));
   const int gv = grid_for(g.n, 256, kSMs * 8), gc = grid_for(c, 8, kSMs * 16);
@@ -508,6 +594,7 @@ void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch
     count_launch();
     VC_CHECK_LAUNCH();
   }
+  if (giant && giant->ngiant > 0) giant_merge(*giant, c, cbase, seg_key, seg_val, ccount, cs.scan_scr, s);
   exclusive_scan<int, long long>(ccount, (long long*)coff, c, (long long*)coff + c, cs.scan_scr, s);
   cluster_place_k<<<gc, 256, 0, s>>>(c, cbase, coff, seg_key, seg_val, cadj, cw, csrc);
   count_launch();

@@ -55,7 +55,8 @@ struct Counters {
   int maxt;  // largest pre-merged pair count of one cluster
   long long pairs;
   int changed;
-  int pad2;
+  int ngiant;         // clusters of more than kMergeBlockMax pairs
+  long long gpairs;   // their pairs
 };
 
 enum Phase { kPhLP = 0, kPhContract, kPhPR, kPhNOI, kPhOther, kPhCount };
@@ -69,7 +70,7 @@ struct Workspace {
   // entry-sized
   Buf tmpK, tmpV, cmpK, cmpV;
   // pair-sized
-  Buf keysA, keysB, valsA, valsB, hist, heads, hpos, cvT, ccur;
+  Buf keysA, keysB, valsA, valsB, hist, heads, hpos, cvT, ccur, giantS;
   // coarse graphs (ping-pong)
   Buf coff[2], cadj[2], cw[2], csrc[2];
   // global-class tables
@@ -323,7 +324,9 @@ struct Workspace {
     emit_cross(g, bins, gt, cid_out, po, cs.cnt, s, tune);
     VC_CUDA(cudaMemsetAsync(&ctr()->maxt, 0, sizeof(int), s));
     VC_CUDA(cudaMemsetAsync(&ctr()->pairs, 0, sizeof(long long), s));
-    cluster_stats(g.n, ccount, &ctr()->maxt, &ctr()->pairs, s);
+    VC_CUDA(cudaMemsetAsync(&ctr()->ngiant, 0, sizeof(int), s));
+    VC_CUDA(cudaMemsetAsync(&ctr()->gpairs, 0, sizeof(long long), s));
+    cluster_stats(g.n, ccount, &ctr()->maxt, &ctr()->pairs, &ctr()->ngiant, &ctr()->gpairs, s);
     VC_CUDA(cudaMemcpyAsync(h_counters, ctr(), sizeof(Counters), cudaMemcpyDeviceToHost, s));
     sync();
     const int64_t c = h_counters->c;
@@ -332,15 +335,36 @@ struct Workspace {
     int32_t* ca = cadj[slot].ensure_n<int32_t>(std::max<int64_t>(P, 1));
     long long* cwp = cw[slot].ensure_n<long long>(std::max<int64_t>(P, 1));
     int32_t* csp = csrc[slot].ensure_n<int32_t>(std::max<int64_t>(P, 1));
-    if (h_counters->maxt <= kMergeBlockMax) {
+    // the cluster merge, with the few giant clusters radix-sorted together, unless
+    // those hold most of the pairs (then one radix sort of all pairs)
+    const int ng = h_counters->maxt > kMergeBlockMax ? h_counters->ngiant : 0;
+    const int64_t GP = ng ? h_counters->gpairs : 0;
+    if (2 * GP <= P) {
       long long* cbase = pos.as<long long>();  // n + 1 >= c + 1 entries
       long long* cur = ccur.ensure_n<long long>(std::max<int64_t>(c, 1));
       auto* sk = (int32_t*)keysA.ensure_n<unsigned long long>(std::max<int64_t>(P, 1));
       auto* sv = valsA.ensure_n<long long>(std::max<int64_t>(P, 1));
-      scan64.ensure_n<long long>(scan_scratch_elems(std::max<int64_t>(c, 1)) + 1);
+      scan64.ensure_n<long long>(scan_scratch_elems(std::max<int64_t>(std::max(c, GP), 1)) + 1);
       cs.scan_scr = scan64.as<long long>();
+      GiantScratch gs;
+      if (ng) {
+        gs.ngiant = ng;
+        gs.pairs = GP;
+        auto* small = giantS.ensure_n<long long>(2 * ng + 4);
+        gs.gstart = small;                               // ng + 1
+        gs.gcount = (int*)(small + ng + 1);              // 1
+        gs.glist = (int32_t*)(small + ng + 2);           // ng ints in ng / 2 + 1 slots
+        gs.gT = gs.glist + ng + (ng & 1);                // ng ints
+        gs.k0 = keysB.ensure_n<unsigned long long>(2 * GP);
+        gs.k1 = gs.k0 + GP;
+        gs.v0 = valsB.ensure_n<long long>(2 * GP);
+        gs.v1 = gs.v0 + GP;
+        gs.heads = heads.ensure_n<int32_t>(GP);
+        gs.hpos = hpos.ensure_n<long long>(GP + 1);
+        gs.hist = hist.ensure_n<long long>(radix_hist_elems(GP));
+      }
       cluster_merge(g, cid_out, cs, ccount, c, cbase, cur, sk, sv, co, ca, cwp, csp, &st()->nnz,
-                    h_counters->maxt > kMergeMax, 2 * c >= g.n, s);
+                    h_counters->maxt > kMergeMax, 2 * c >= g.n, ng ? &gs : nullptr, s);
     } else {
       exclusive_scan<int, long long>(cs.cnt, cs.pos, g.n, &ctr()->pairs, cs.scan_scr, s);
       int bits = ceil_log2(c);

@@ -153,19 +153,35 @@ struct ContractScratch {
 // Relabel: cid[v] = rank of lab[v] among the distinct labels; *c_dev = count.
 void relabel(const int32_t* lab, int64_t n, int32_t* cid, ContractScratch& cs, int* c_dev, cudaStream_t s);
 
-// Cluster merge (every cluster holding at most kMergeBlockMax pre-merged pairs; a
-// warp merges clusters of at most kMergeMax in registers, a block the larger ones):
-// the pre-merge fills ccount[cid] (PairOut::ccount); cluster_stats reads its n entries
-// (zero beyond the c clusters) into *maxt and *pairs;
-// cluster_merge writes the coarse CSR (coff[c + 1], sorted cadj, cw, entry sources
-// csrc) and *nnz_dev; big = some cluster holds more than kMergeMax pairs.
+// Cluster merge: a warp merges clusters of at most kMergeMax pre-merged pairs in
+// registers, a block those of at most kMergeBlockMax; the few "giant" clusters beyond
+// that (GiantScratch) are merged together by one radix sort of their pairs keyed by
+// (giant index, target).  The pre-merge fills ccount[cid] (PairOut::ccount);
+// cluster_stats reads its n entries (zero beyond the c clusters) into *maxt, *pairs and
+// the giant clusters' count and pairs; cluster_merge writes the coarse CSR (coff[c + 1],
+// sorted cadj, cw, entry sources csrc) and *nnz_dev; big = some cluster holds more than
+// kMergeMax pairs.
 constexpr int kMergeMax = 512;
 constexpr int kMergeBlockMax = 4096;
-void cluster_stats(int64_t n, const int32_t* ccount, int* maxt, long long* pairs, cudaStream_t s);
+struct GiantScratch {
+  int ngiant = 0;      // clusters of more than kMergeBlockMax pairs
+  int64_t pairs = 0;   // their pairs
+  int* gcount;         // 1 int
+  int32_t* glist;      // ngiant cluster ids
+  int32_t* gT;         // ngiant pair counts
+  long long* gstart;   // ngiant + 1 offsets into the gathered pairs
+  unsigned long long *k0, *k1;  // pairs elements each
+  long long *v0, *v1;
+  int32_t* heads;      // pairs
+  long long* hpos;     // pairs + 1
+  long long* hist;     // radix_hist_elems(pairs)
+};
+void cluster_stats(int64_t n, const int32_t* ccount, int* maxt, long long* pairs, int* ngiant, long long* gpairs,
+                   cudaStream_t s);
 void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int32_t* ccount, int64_t c,
                    long long* cbase, long long* cursor, int32_t* seg_key, long long* seg_val, int64_t* coff,
                    int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, bool big, bool sort_first,
-                   cudaStream_t s);
+                   const GiantScratch* giant, cudaStream_t s);
 
 // Builds (cid[v] << bits | cu, weight) pairs from the pre-merged lists.
 void build_pairs(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int bits, int64_t pairs,

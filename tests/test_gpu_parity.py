@@ -151,6 +151,24 @@ def test_contract_parity(step_graphs, name):
         compare_contract(G, labels.astype(np.int32))
 
 
+def test_contract_giant_clusters():
+    """A few clusters of more than 4096 pre-merged pairs beside many small ones: the
+    small ones take the per-cluster merge, the giant ones one shared radix sort; both
+    with mostly singleton clusters and with clusters of four vertices."""
+    g = gg.er(30000, 12, 5, 1, 100)
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    n = G.n
+    v = np.arange(n, dtype=np.int64)
+    rnd = np.random.default_rng(4)
+    perm = rnd.permutation(n)
+    giant = np.full(n, -1, np.int64)
+    for k, lab in enumerate((perm[0], perm[1], 7)):  # three giant clusters, scattered members
+        giant[perm[2 + 800 * k: 2 + 800 * (k + 1)]] = lab
+    for rest in (v, v // 4):
+        labels = np.where(giant >= 0, giant, rest)
+        compare_contract(G, labels.astype(np.int32))
+
+
 def coarse_graphs():
     out = []
     for seed in range(4):
