@@ -197,6 +197,8 @@ __global__ void __launch_bounds__(256) cluster_stats_k(int64_t n, const int32_t*
 
 // Counting-sort scatter: the pre-merged pairs of fine vertex v move, in one piece,
 // into their cluster's segment (cursor = the segments' running write positions).
+// Lists of more than kScatterWarpMin pairs are copied by the whole warp.
+constexpr int kScatterWarpMin = 16;
 __global__ void __launch_bounds__(256) cluster_scatter_k(int64_t n, const int64_t* __restrict__ off,
                                                          const int32_t* __restrict__ cid,
                                                          const int32_t* __restrict__ cnt, PairOut in,
@@ -227,9 +229,16 @@ __global__ void __launch_bounds__(256) cluster_scatter_k(int64_t n, const int64_
 #pragma unroll
       for (int j = 0; j < kPairSlots; ++j)
         if (j < k) { seg_key[dst + j] = kk[j]; seg_val[dst + j] = vv[j]; }
+      if (k > kPairSlots && k <= kScatterWarpMin) {  // short rest: this thread
+        const int64_t src = off[v];
+        for (int j = kPairSlots; j < k; ++j) {
+          seg_key[dst + j] = in.tkey[src + j];
+          seg_val[dst + j] = in.tval[src + j];
+        }
+      }
     }
-    // the rest of longer lists, one list at a time by the whole warp (coalesced)
-    unsigned longs = __ballot_sync(0xffffffffu, c >= 0 && k > kPairSlots);
+    // the rest of long lists, one list at a time by the whole warp (coalesced)
+    unsigned longs = __ballot_sync(0xffffffffu, c >= 0 && k > kScatterWarpMin);
     while (longs) {
       const int l = __ffs(longs) - 1;
       longs &= longs - 1u;
