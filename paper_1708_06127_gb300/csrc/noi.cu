@@ -408,21 +408,43 @@ __device__ __forceinline__ int warp_argmax_vi(long long val, int idx, long long*
   return mu == 0 ? -1 : (int)wi;
 }
 
-template <typename WT>
+// Scanned flags of a round: a byte per vertex at v - sb, or a bit per vertex of the graph
+// [lo, lo + n) (one warp owns the words; a step sets one flag from one lane, then the
+// warp synchronises).
+struct ByteSeen {
+  unsigned char* p;
+  int64_t sb;
+  __device__ __forceinline__ void clear(int64_t lo, int64_t n, int lane) const {
+    for (int64_t k = lane; k < n; k += 32) p[lo + k - sb] = 0;
+  }
+  __device__ __forceinline__ bool test(int64_t v) const { return p[v - sb] != 0; }
+  __device__ __forceinline__ void set(int64_t v) const { p[v - sb] = 1; }
+};
+struct BitSeen {
+  unsigned* bits;
+  int64_t lo;
+  __device__ __forceinline__ void clear(int64_t, int64_t n, int lane) const {
+    for (int64_t k = lane; k < ((n + 31) >> 5); k += 32) bits[k] = 0;
+  }
+  __device__ __forceinline__ bool test(int64_t v) const { return (bits[(v - lo) >> 5] >> ((v - lo) & 31)) & 1u; }
+  __device__ __forceinline__ void set(int64_t v) const { bits[(v - lo) >> 5] |= 1u << ((v - lo) & 31); }
+};
+
+template <typename WT, typename SEEN>
 __device__ __forceinline__ void noi_round_warp(int64_t lo, int64_t hi, const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ adj, const WT* __restrict__ w,
-                                               long long lam, long long* r, unsigned char* seen, int32_t* parent,
+                                               long long lam, long long* r, SEEN seen, int32_t* parent,
                                                long long* cmax, int32_t* labels, int* any_out, int64_t sb) {
-  // r, seen and parent hold vertex v at v - sb (sb = 0: arrays over the whole graph;
+  // r and parent hold vertex v at v - sb (sb = 0: arrays over the whole graph;
   // sb = lo: this graph's own arrays, e.g. in shared memory)
   const int lane = threadIdx.x & 31;
   const int64_t n = hi - lo;
   const int64_t nc = (n + 31) >> 5;
   for (int64_t k = lane; k < n; k += 32) {
     r[lo + k - sb] = 0;
-    seen[lo + k - sb] = 0;
     parent[lo + k - sb] = (int32_t)(lo + k - sb);
   }
+  seen.clear(lo, n, lane);
   for (int64_t c = lane; c < nc; c += 32) cmax[c] = 0;
   __syncwarp();
   long long best;
@@ -435,16 +457,16 @@ __device__ __forceinline__ void noi_round_warp(int64_t lo, int64_t hi, const int
     }
     const int C = warp_argmax_vi(bv, bc, &best);
     const int64_t k = (int64_t)C * 32 + lane;
-    const long long rv = (k < n && !seen[lo + k - sb]) ? r[lo + k - sb] : -1;
+    const long long rv = (k < n && !seen.test(lo + k)) ? r[lo + k - sb] : -1;
     const int xl = warp_argmax_vi(rv, (int)k, &best);
     const int64_t x = lo + xl;
-    if (k == xl) seen[x - sb] = 1;
+    if (k == xl) seen.set(x);
     warp_argmax_vi(k == xl ? -1 : rv, (int)k, &best);  // the chunk's maximum without x
     if (lane == 0) cmax[C] = best;
     __syncwarp();
     for (int64_t e = off[x] + lane; e < off[x + 1]; e += 32) {
       const int y = adj[e];
-      if (seen[y - sb]) continue;
+      if (seen.test(y)) continue;
       const long long c = (long long)w[e];
       const long long ry = (long long)atomicAdd((unsigned long long*)&r[y - sb], (unsigned long long)c) + c;
       atomicMax(&cmax[(y - lo) >> 5], ry);
@@ -491,9 +513,10 @@ __global__ void __launch_bounds__(32) noi_round_smem_k(const int32_t* __restrict
     const long long n = nv ? nv[g] : (long long)ncap;
     const long long lam = glam ? glam[g] : st->lambda_hat;
     if (n <= ncap)
-      noi_round_warp<WT>(lo, lo + n, off, adj, w, lam, r, seen, parent, cmax, labels, gchanged + g, lo);
+      noi_round_warp<WT>(lo, lo + n, off, adj, w, lam, r, ByteSeen{seen, lo}, parent, cmax, labels, gchanged + g, lo);
     else
-      noi_round_warp<WT>(lo, lo + n, off, adj, w, lam, gr, gseen, gparent, gr + un + lo, labels, gchanged + g, 0);
+      noi_round_warp<WT>(lo, lo + n, off, adj, w, lam, gr, ByteSeen{gseen, 0}, gparent, gr + un + lo, labels,
+                         gchanged + g, 0);
   }
 }
 
@@ -528,7 +551,7 @@ __global__ void __launch_bounds__(32) noi_round_k(int64_t n, const int64_t* __re
                                                   const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                   const DevState* st, long long* r, unsigned char* seen,
                                                   int32_t* parent, long long* cmax, int32_t* labels, int* changed) {
-  noi_round_warp<WT>(0, n, off, adj, w, st->lambda_hat, r, seen, parent, cmax, labels, changed, 0);
+  noi_round_warp<WT>(0, n, off, adj, w, st->lambda_hat, r, ByteSeen{seen, 0}, parent, cmax, labels, changed, 0);
 }
 
 void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, unsigned char* seen,
@@ -555,7 +578,13 @@ void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, unsi
 }
 
 // Batches: one round for each listed graph, a warp per graph (persistent grid of
-// 8-warp blocks pulling graphs from the list).
+// 8-warp blocks pulling graphs from the list).  With ncap > 0 (every listed graph of at
+// most ncap vertices) each warp keeps its graph's chunk maxima and scanned bits in
+// shared memory, so that a scan step waits on fewer global reads; the attachments and
+// parents stay in global memory (every graph of the list in flight at once).
+__host__ __device__ constexpr size_t noi_batch_warp_smem(int ncap) { return (size_t)(ncap / 32 + 1) * 12; }
+constexpr size_t kNoiBatchSmemMax = 160 * 1024;
+
 template <typename WT>
 __global__ void __launch_bounds__(256) noi_round_batch_k(const int32_t* __restrict__ list, int count,
                                                          const int64_t* __restrict__ off,
@@ -563,31 +592,63 @@ __global__ void __launch_bounds__(256) noi_round_batch_k(const int32_t* __restri
                                                          const long long* vbase, const long long* nv,
                                                          const long long* glam, long long* r, unsigned char* seen,
                                                          int32_t* parent, long long* cmax, int32_t* labels,
-                                                         int* gchanged) {
+                                                         int* gchanged, int ncap) {
+  extern __shared__ __align__(16) unsigned char noi_bs[];
   const int warps = gridDim.x * (blockDim.x >> 5);
+  const int wid = threadIdx.x >> 5;
+  const int words = ncap / 32 + 1;
+  long long* wc = (long long*)noi_bs + (size_t)wid * words;
+  unsigned* wb = (unsigned*)((long long*)noi_bs + (size_t)(blockDim.x >> 5) * words) + (size_t)wid * words;
   for (int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < count; idx += warps) {
     const int g = list[idx];
     const long long lo = vbase[g];
-    noi_round_warp<WT>(lo, lo + nv[g], off, adj, w, glam[g], r, seen, parent, cmax + lo, labels, gchanged + g, 0);
+    if (ncap > 0 && nv[g] <= ncap)
+      noi_round_warp<WT>(lo, lo + nv[g], off, adj, w, glam[g], r, BitSeen{wb, lo}, parent, wc, labels, gchanged + g,
+                         0);
+    else
+      noi_round_warp<WT>(lo, lo + nv[g], off, adj, w, glam[g], r, ByteSeen{seen, 0}, parent, cmax + lo, labels,
+                         gchanged + g, 0);
   }
+}
+
+template <typename WT>
+static void noi_round_batch_launch(const GraphView& u, const int32_t* list, int count, const long long* vbase,
+                                   const long long* nv, const long long* glam, long long* r, unsigned char* seen,
+                                   int32_t* parent, long long* cmax, int32_t* labels, int* gchanged, int max_n,
+                                   cudaStream_t s) {
+  static std::mutex mu;
+  static std::unordered_map<int, bool> ready;  // per device: the shared-memory limit was raised
+  {
+    int dev = 0;
+    VC_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ready[dev]) {
+      VC_CUDA(cudaFuncSetAttribute(noi_round_batch_k<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kNoiBatchSmemMax));
+      ready[dev] = true;
+    }
+  }
+  const size_t smem = 8 * noi_batch_warp_smem(max_n);
+  const bool in_smem = max_n > 0 && smem <= kNoiBatchSmemMax;
+  const int blocks = grid_for(count, 8, kSMs * 4);
+  noi_round_batch_k<WT><<<blocks, 256, in_smem ? smem : 0, s>>>(list, count, u.off, u.adj, (const WT*)u.w, vbase, nv,
+                                                               glam, r, seen, parent, cmax, labels, gchanged,
+                                                               in_smem ? max_n : 0);
+  count_launch();
+  VC_CHECK_LAUNCH();
 }
 
 void noi_round_batch(const GraphView& u, const int32_t* list, int count, const long long* vbase, const long long* nv,
                      const long long* glam, long long* r, unsigned char* seen, int32_t* parent, int32_t* labels,
                      int* gchanged, int max_n, cudaStream_t s) {
   if (count <= 0) return;
-  (void)max_n;  // the global-array kernel: every listed graph in flight at once measured faster
   // r holds 2 x (union size) entries: attachments, then each graph's chunk maxima at its own range
   long long* cmax = r + u.n;
-  const int blocks = grid_for(count, 8, kSMs * 4);
   if (u.wbytes == 4)
-    noi_round_batch_k<int32_t><<<blocks, 256, 0, s>>>(list, count, u.off, u.adj, (const int32_t*)u.w, vbase, nv, glam,
-                                                      r, seen, parent, cmax, labels, gchanged);
+    noi_round_batch_launch<int32_t>(u, list, count, vbase, nv, glam, r, seen, parent, cmax, labels, gchanged, max_n, s);
   else
-    noi_round_batch_k<long long><<<blocks, 256, 0, s>>>(list, count, u.off, u.adj, (const long long*)u.w, vbase, nv,
-                                                        glam, r, seen, parent, cmax, labels, gchanged);
-  count_launch();
-  VC_CHECK_LAUNCH();
+    noi_round_batch_launch<long long>(u, list, count, vbase, nv, glam, r, seen, parent, cmax, labels, gchanged, max_n,
+                                      s);
 }
 
 // ------------------------------------------------------- allocation-free round
