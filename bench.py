@@ -412,6 +412,52 @@ def run_reference(args):
     return 0
 
 
+def bench_quality(local):
+    """Non-optimal cuts per label-propagation iteration count (the paper's study of
+    Sec. 5, "Random Hyperbolic Graphs", and its table of iteration counts): exact lambda
+    from the exact mode (the exact step alone), against the method with n0 = 64 so that
+    label propagation shapes every kernel.  16-cores of RHG graphs (avg deg 32, exponent
+    5) at n = 2^13..2^16, six generator seeds each, three method seeds per graph."""
+    import graphgen as gg
+    import paper_1708_06127_gb300 as vc
+    graphs = []
+    for nlog in (13, 14, 15, 16):
+        for seed in range(1, 7):
+            g = gg.core_lcc(gg.rhg(1 << nlog, 32, 100 + seed), 16)
+            if g.n >= 100:
+                graphs.append((nlog, seed, g))
+    exact, t_exact = [], 0.0
+    for _, _, g in graphs:
+        t = time.perf_counter()
+        cut, _ = vc.exact_min_cut(g.offsets, g.adj, g.w, device=local)
+        t_exact += time.perf_counter() - t
+        exact.append(cut)
+    results = {}
+    for lp in (1, 2, 3, 5, 25):
+        runs = bad = 0
+        gap = 0.0
+        t = time.perf_counter()
+        for (_, _, g), lam in zip(graphs, exact):
+            with vc.MinCut(g.offsets, g.adj, g.w, n0=64, device=local) as mc:
+                for s in (1, 2, 3):
+                    cut, _ = mc.run(s, lp)
+                    runs += 1
+                    if cut != lam:
+                        bad += 1
+                        gap += (cut - lam) / lam
+        results[f"lp_iters={lp}"] = {"runs": runs, "non_optimal": bad, "fraction": bad / runs,
+                                     "mean_relative_gap_of_non_optimal": gap / bad if bad else 0.0,
+                                     "seconds": time.perf_counter() - t}
+    nontrivial = sum(1 for (_, _, g), lam in zip(graphs, exact) if lam < int(np.diff(g.offsets).min()))
+    return {"metric": "non-optimal minimum cuts per label-propagation iteration count", "data": "synthetic",
+            "workload": "rhg(n=2^13..2^16, avg_deg=32, gamma=5) -> 16-core -> largest component, 6 seeds per n, "
+                        "unit weights; the method with n0=64, 3 seeds per graph; lp_iters=25 runs 25 rounds "
+                        "(no convergence stop)",
+            "graphs": len(graphs), "graphs_with_cut_below_min_degree": nontrivial,
+            "exact": {"api": "exact_min_cut (n0 >= n: the exact step alone)", "seconds": t_exact},
+            "results": results}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -424,7 +470,7 @@ def main():
                     help="lanes per vertex of the first label-propagation round (0: picked by timing)")
     ap.add_argument("--emit-group", type=int, default=0,
                     help="lanes per vertex of the block-class pre-merge (0: picked by timing)")
-    ap.add_argument("--mode", default="all", choices=["all", "single", "batch", "serve", "configs"],
+    ap.add_argument("--mode", default="all", choices=["all", "single", "batch", "serve", "configs", "quality"],
                     help="all: the headline line plus batch and serving summaries")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=300)
@@ -444,6 +490,11 @@ def main():
         vc.build()
         res = bench_batch(args.batch_count, args.steps, args.warmup, torch.cuda.current_stream(), local)
         print(json.dumps(res), flush=True)
+        return 0
+    if args.mode == "quality":
+        torch.cuda.set_device(local)
+        vc.build()
+        print(json.dumps(bench_quality(local)), flush=True)
         return 0
     if args.mode == "configs":
         torch.cuda.set_device(local)

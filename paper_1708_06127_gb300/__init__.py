@@ -563,3 +563,12 @@ class MinCut:
             self.close()
         except Exception:
             pass
+
+
+def exact_min_cut(offsets, adj, weights, device: int = 0, on_device: bool = False):
+    """Exact minimum cut by the rounds of Nagamochi, Ono and Ibaraki alone (Sec. 3): the
+    method with n0 at least the vertex count, so no label-propagation level runs and the
+    exact step starts on the input graph.  Returns (cut value, side bitmap)."""
+    n = int(offsets.shape[0] - 1)
+    with MinCut(offsets, adj, weights, n0=max(n, 2), device=device, on_device=on_device) as mc:
+        return mc.run(1, 0)

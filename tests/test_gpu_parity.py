@@ -259,6 +259,18 @@ def test_viecut_sparse_exact_step():
     assert_same(g, seed=1, lp=1, n0=2000)
 
 
+def test_exact_mode():
+    """exact_min_cut (the exact step alone, n0 >= n) equals the oracle's exact run and,
+    where label propagation misses it, stays below the method's value."""
+    for g in [gg.core_lcc(gg.rhg(1 << 13, 32, 1), 16), H.random_graph(300, 0.05, 8, wmax=9),
+              gg.with_pair_weights(gg.core_lcc(gg.er(2000, 10, 4), 3), 4, 1, 20), H.pr2_counterexample()]:
+        cut, bits = vc.exact_min_cut(g.offsets, g.adj, g.w)
+        ref = oracle.viecut(g.offsets, g.adj, g.w, seed=1, lp_iters=0, n0=g.n)
+        assert cut == ref.cut and np.array_equal(bits, ref.side_bits), g.name
+        for s in (1, 2, 3):
+            assert cut <= oracle.viecut(g.offsets, g.adj, g.w, seed=s, lp_iters=1, n0=64).cut
+
+
 def test_viecut_repeatable_and_seeded():
     g = gg.workload_rhg_small(3)
     with vc.MinCut(g.offsets, g.adj, g.w, n0=64) as mc:
