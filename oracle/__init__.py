@@ -60,7 +60,9 @@ def _load():
                 f.restype = i64
                 f.argtypes = [i64, vp, vp, vp, i64, vp]
             lib.orc_viecut.restype = ctypes.c_int
-            lib.orc_viecut.argtypes = [i64, vp, vp, vp, i32, u64, i32, i64, i32, vp, vp, vp, i64, vp]
+            lib.orc_viecut.argtypes = [i64, vp, vp, vp, i32, u64, i32, i64, i32, vp, vp, vp, i64, vp, i32]
+            lib.orc_correct.restype = i64
+            lib.orc_correct.argtypes = [i64, vp, vp, vp, vp, vp]
             _lib = lib
     return _lib
 
@@ -128,6 +130,14 @@ def contract(g: CsrGraph, labels):
     return h, cid
 
 
+def correct(g: CsrGraph, labels):
+    """The correcting step [R10] on a clustering: returns (cluster ids, their count)."""
+    lab, p = _c(labels, np.int32)
+    cid = np.empty(g.n, np.int32)
+    k = _load().orc_correct(g.n, g.offsets.ctypes.data, g.adj.ctypes.data, g.w.ctypes.data, p, cid.ctypes.data)
+    return cid, int(k)
+
+
 def _labels_call(name, g: CsrGraph, lambda_hat: int):
     out = np.empty(g.n, np.int32)
     cnt = getattr(_load(), name)(g.n, g.offsets.ctypes.data, g.adj.ctypes.data, g.w.ctypes.data,
@@ -161,8 +171,9 @@ class Result:
 
 
 def viecut(offsets, adj, w, seed: int = 1, lp_iters: int = 2, n0: int = 10000,
-           pr_runs_max: int = 8, trace_cap: int = 4096) -> Result:
-    """The whole deterministic method.  `w` may be int32 or int64."""
+           pr_runs_max: int = 8, trace_cap: int = 4096, correct: bool = False) -> Result:
+    """The whole deterministic method.  `w` may be int32 or int64.  correct: the
+    correcting step on every label-propagation clustering (reading [R10])."""
     off, po = _c(offsets, np.int64)
     a, pa = _c(adj, np.int32)
     w = np.asarray(w)
@@ -174,7 +185,8 @@ def viecut(offsets, adj, w, seed: int = 1, lp_iters: int = 2, n0: int = 10000,
     tr = (OrcStep * trace_cap)()
     tl = ctypes.c_int64()
     rc = _load().orc_viecut(n, po, pa, pw, wbytes, seed & (2**64 - 1), lp_iters, n0, pr_runs_max,
-                            ctypes.byref(cut), bits.ctypes.data, tr, trace_cap, ctypes.byref(tl))
+                            ctypes.byref(cut), bits.ctypes.data, tr, trace_cap, ctypes.byref(tl),
+                            1 if correct else 0)
     if rc != 0:
         raise ValueError(f"oracle rejected the input (code {rc})")
     steps = [(tr[k].kind, tr[k].level, tr[k].n, tr[k].nnz, tr[k].lambda_hat)

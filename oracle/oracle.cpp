@@ -39,6 +39,16 @@
 //  [R9] The bound improves only on a strictly smaller trivial cut (earliest found
 //       wins); a contraction that leaves one vertex ends the run.  The returned
 //       side is normalised so original vertex 0 is not in it.
+//  [R10] The correcting step (Sec. 4.1, "correcting algorithm"; fixMisplacedVertices
+//       of Algorithm 1) is optional and off unless asked for.  On a level's label
+//       propagation clustering, a cluster C with 2 <= |C| <= floor(log2 n) (n the
+//       current vertex count) has weighted degree d(C) (the weight of the edges
+//       leaving C); removing v from C gives d(C - v) = d(C) - c(v, V - C) + c(v, C - v).
+//       v is misplaced when d(C - v) < d(C) (its removal lowers the weighted degree of
+//       C's vertex in the contracted graph).  Each cluster makes at most one vertex a
+//       singleton ("single misplaced vertices"): the misplaced one of smallest
+//       d(C - v), ties to the smallest id.  The singletons take the cluster ids after
+//       all others, in ascending vertex order.
 #include <stdint.h>
 #include <string.h>
 #include <algorithm>
@@ -118,13 +128,49 @@ void lp_round(const Graph& g, const int32_t* lab_in, uint64_t key, int32_t* lab_
 // Sec. 3): each block becomes one vertex, edges inside a block vanish, parallel
 // edges between two blocks merge with summed weight.  [R4] block ids are the ranks
 // of the label values.  The coarse lists come out sorted by neighbour id.
-Graph contract(const Graph& g, const int32_t* labels, std::vector<int32_t>& cid) {
+// Cluster ids [R4]: ranks of the label values; returns the number of clusters.
+int64_t cluster_ids(const Graph& g, const int32_t* labels, std::vector<int32_t>& cid) {
   std::vector<int32_t> vals(labels, labels + g.n);
   std::sort(vals.begin(), vals.end());
   vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
   cid.assign(g.n, 0);
   for (int64_t v = 0; v < g.n; ++v)
     cid[v] = (int32_t)(std::lower_bound(vals.begin(), vals.end(), labels[v]) - vals.begin());
+  return (int64_t)vals.size();
+}
+
+// The correcting step [R10] on cluster ids cid (c clusters); returns the new count.
+int64_t correct_clusters(const Graph& g, std::vector<int32_t>& cid, int64_t c) {
+  int64_t lg = 0;
+  while ((int64_t(2) << lg) <= g.n) ++lg;  // floor(log2 n)
+  std::vector<int64_t> size(c, 0), dc(c, 0), out(g.n, 0), in(g.n, 0);
+  for (int64_t v = 0; v < g.n; ++v) size[cid[v]] += 1;
+  for (int64_t v = 0; v < g.n; ++v)
+    for (int64_t e = g.off[v]; e < g.off[v + 1]; ++e) {
+      if (cid[g.adj[e]] == cid[v]) in[v] += g.w[e];
+      else out[v] += g.w[e];
+    }
+  for (int64_t v = 0; v < g.n; ++v) dc[cid[v]] += out[v];
+  std::vector<int64_t> best(c, -1);  // the vertex each cluster gives up, or -1
+  for (int64_t v = 0; v < g.n; ++v) {
+    const int32_t C = cid[v];
+    if (size[C] < 2 || size[C] > lg) continue;
+    const int64_t without = dc[C] - out[v] + in[v];
+    if (without >= dc[C]) continue;
+    const int64_t b = best[C];
+    if (b < 0 || without < dc[C] - out[b] + in[b]) best[C] = v;  // ascending v keeps the smallest id on ties
+  }
+  std::vector<char> single(g.n, 0);
+  for (int64_t C = 0; C < c; ++C)
+    if (best[C] >= 0) single[best[C]] = 1;
+  int64_t k = c;
+  for (int64_t v = 0; v < g.n; ++v)
+    if (single[v]) cid[v] = (int32_t)k++;
+  return k;
+}
+
+// Contracts the clustering cid of c clusters.
+Graph contract_ids(const Graph& g, const std::vector<int32_t>& cid, int64_t c) {
   struct T { int32_t a, b; int64_t w; };
   std::vector<T> t;
   for (int64_t v = 0; v < g.n; ++v)
@@ -134,7 +180,7 @@ Graph contract(const Graph& g, const int32_t* labels, std::vector<int32_t>& cid)
     }
   std::sort(t.begin(), t.end(), [](const T& x, const T& y) { return x.a < y.a || (x.a == y.a && x.b < y.b); });
   Graph h;
-  h.n = (int64_t)vals.size();
+  h.n = c;
   h.off.assign(h.n + 1, 0);
   for (size_t i = 0; i < t.size();) {
     size_t j = i;
@@ -147,6 +193,12 @@ Graph contract(const Graph& g, const int32_t* labels, std::vector<int32_t>& cid)
   }
   for (int64_t v = 0; v < h.n; ++v) h.off[v + 1] += h.off[v];
   return h;
+}
+
+Graph contract(const Graph& g, const int32_t* labels, std::vector<int32_t>& cid, bool correct = false) {
+  int64_t c = cluster_ids(g, labels, cid);
+  if (correct) c = correct_clusters(g, cid, c);
+  return contract_ids(g, cid, c);
 }
 
 // Union-find with the smallest id as representative (Sec. 4.1 uses union-find to
@@ -288,9 +340,9 @@ void update_bound(Run& run, const Graph& g) {
 
 // Applies a contraction; returns false when the run must stop (one vertex left, or
 // a zero bound: an isolated vertex means a cut of weight 0, Appendix B).
-bool apply(Run& run, Graph& g, const int32_t* labels, int32_t kind) {
+bool apply(Run& run, Graph& g, const int32_t* labels, int32_t kind, bool correct = false) {
   std::vector<int32_t> cid;
-  Graph h = contract(g, labels, cid);
+  Graph h = contract(g, labels, cid, correct);
   for (auto& c : run.cur) c = cid[c];
   g = std::move(h);
   if (g.n <= 1) {
@@ -306,7 +358,7 @@ bool apply(Run& run, Graph& g, const int32_t* labels, int32_t kind) {
 // propagation + cluster contraction + Padberg-Rinaldi runs while more than n0
 // vertices remain, then Nagamochi-Ono-Ibaraki on the kernel; the bound is the
 // smallest trivial cut seen (Sec. 4, "Throughout our algorithm we maintain ...").
-void viecut(Graph g, uint64_t seed, int32_t lp_iters, int64_t n0, int32_t pr_runs_max, Run& run) {
+void viecut(Graph g, uint64_t seed, int32_t lp_iters, int64_t n0, int32_t pr_runs_max, bool correct, Run& run) {
   int64_t n = g.n;
   run.cur.resize(n);
   run.side.assign(n, 0);
@@ -328,7 +380,7 @@ void viecut(Graph g, uint64_t seed, int32_t lp_iters, int64_t n0, int32_t pr_run
       lp_round(g, lab.data(), key, nxt.data());
       lab.swap(nxt);
     }
-    if (!apply(run, g, lab.data(), 1)) return;
+    if (!apply(run, g, lab.data(), 1, correct)) return;
     for (int32_t runi = 0; runi < pr_runs_max; ++runi) {
       bool any = false;
       lab.resize(g.n);
@@ -406,6 +458,17 @@ int64_t orc_contract(int64_t n, const int64_t* off, const int32_t* adj, const in
   return (int64_t)h.adj.size();
 }
 
+// The correcting step [R10] on the clustering `labels`: cid[n] receives the corrected
+// cluster ids; returns their count.
+int64_t orc_correct(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* w, const int32_t* labels,
+                    int32_t* cid) {
+  Graph g = load(n, off, adj, w, 8);
+  std::vector<int32_t> c;
+  int64_t k = correct_clusters(g, c, cluster_ids(g, labels, c));
+  memcpy(cid, c.data(), sizeof(int32_t) * n);
+  return k;
+}
+
 int64_t orc_pr_pass_a(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* w,
                       int64_t lambda_hat, int32_t* labels) {
   Graph g = load(n, off, adj, w, 8);
@@ -430,10 +493,10 @@ int64_t orc_noi_round(int64_t n, const int64_t* off, const int32_t* adj, const i
 int orc_viecut(int64_t n, const int64_t* off, const int32_t* adj, const void* w, int32_t wbytes,
                uint64_t seed, int32_t lp_iters, int64_t n0, int32_t pr_runs_max,
                int64_t* cut, uint64_t* side_bits, orc_step* trace, int64_t trace_cap,
-               int64_t* trace_len) {
+               int64_t* trace_len, int32_t correct) {
   if (n < 2) return -1;
   Run run;
-  viecut(load(n, off, adj, w, wbytes), seed, lp_iters, n0, pr_runs_max, run);
+  viecut(load(n, off, adj, w, wbytes), seed, lp_iters, n0, pr_runs_max, correct != 0, run);
   *cut = run.lambda_hat;
   bool flip = run.side[0] != 0;
   int64_t words = (n + 63) / 64;

@@ -299,6 +299,91 @@ def test_pr_pass_b_conditions_hand():
     assert pairs == 1 and labels[1] == 0
 
 
+# ---------------------------------------------------------- correcting step
+def _as64(g):
+    return oracle.as_csr64(g.offsets, g.adj, g.w)
+
+
+def test_correct_hand():
+    """[R10] by hand: A = {0,1,2}, B = {3,4,5}, C = {6,7} (n = 8, clusters of at most
+    floor(log2 8) = 3 are checked).  Vertex 2 has weight 2 inside A and 6 to B, so
+    d(A) = 6 and d(A - 2) = 6 - 6 + 2 = 2 < 6; every other removal raises its cluster's
+    degree (d(A - 0) = 12, d(B - 3) = 14, d(B - 5) = 16, d(C - 6) = 5).  Vertex 2 becomes
+    the singleton with id 3, after the three clusters."""
+    g = gg.from_edges(8, [(0, 1, 5), (0, 2, 1), (1, 2, 1), (2, 3, 3), (2, 4, 3), (3, 4, 5), (4, 5, 5), (3, 5, 5),
+                          (6, 7, 5), (5, 6, 1)])
+    cid, k = oracle.correct(_as64(g), np.array([0, 0, 0, 3, 3, 3, 6, 6], np.int32))
+    assert k == 4 and cid.tolist() == [0, 0, 3, 1, 1, 1, 2, 2]
+    # a cluster above floor(log2 n) vertices is left as it is: A grown to 4 vertices
+    cid, k = oracle.correct(_as64(g), np.array([0, 0, 0, 3, 3, 3, 0, 0], np.int32))
+    assert k == 2 and cid.tolist() == [0, 0, 0, 1, 1, 1, 0, 0]
+
+
+def test_correct_tie_and_one_per_cluster():
+    """Two misplaced vertices of one cluster: only one leaves, the one of smaller
+    d(C - v); on equal values the smaller id.  A 4-cycle 0-1-2-3 of weight 1 inside
+    cluster {0,1,2,3} plus leaves: 1 and 3 each hang on 3 edges of weight 2 to their
+    own outside vertex (n = 16, floor(log2 16) = 4)."""
+    edges = [(0, 1, 1), (1, 2, 1), (2, 3, 1), (3, 0, 1)]
+    edges += [(1, 4 + i, 2) for i in range(3)] + [(3, 7 + i, 2) for i in range(3)]
+    edges += [(10 + i, 11 + i, 1) for i in range(5)] + [(4, 10, 1), (7, 15, 1), (4, 7, 1), (5, 6, 1), (8, 9, 1)]
+    g = gg.from_edges(16, edges)
+    lab = np.arange(16, dtype=np.int32)
+    lab[:4] = 0
+    cid, k = oracle.correct(_as64(g), lab)
+    # 13 clusters (the 4-cycle's and 12 singletons); d(C) = 12 and
+    # d(C - 1) = d(C - 3) = 12 - 6 + 2 = 8: equal, so vertex 1 leaves, as cluster 13
+    assert k == 14 and cid[1] == 13 and cid[0] == cid[2] == cid[3] == 0
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_correct_bruteforce(seed):
+    """Against the definitions: cluster cuts summed edge by edge over the vertex sets
+    (not the incremental formula), every small cluster and member enumerated."""
+    rnd = random.Random(500 + seed)
+    n = rnd.randint(8, 40)
+    g = H.random_graph(n, rnd.uniform(0.1, 0.5), 900 + seed, wmax=rnd.choice([1, 6]))
+    G = _as64(g)
+    lab = np.array([rnd.randrange(max(2, n // 3)) for _ in range(n)], np.int32)
+    cid, k = oracle.correct(G, lab)
+    lg = n.bit_length() - 1
+    vals = sorted(set(lab.tolist()))
+    want = np.array([vals.index(x) for x in lab], np.int32)
+    leave = []
+    for L in vals:
+        members = [v for v in range(n) if lab[v] == L]
+        if not 2 <= len(members) <= lg:
+            continue
+        inside = np.zeros(n, bool)
+        inside[members] = True
+        dc = H.cut_weight(g.offsets, g.adj, g.w, inside)
+        best = None
+        for v in members:
+            rest = inside.copy()
+            rest[v] = False
+            d = H.cut_weight(g.offsets, g.adj, g.w, rest)
+            if d < dc and (best is None or d < best[0]):
+                best = (d, v)
+        if best:
+            leave.append(best[1])
+    for i, v in enumerate(sorted(leave)):
+        want[v] = len(vals) + i
+    assert k == len(vals) + len(leave) and np.array_equal(cid, want)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_pipeline_with_correcting_step(seed):
+    """The whole method with the correcting step: still an upper bound whose side has
+    exactly that cut weight."""
+    rnd = random.Random(2000 + seed)
+    g = H.random_graph(rnd.randint(6, 14), rnd.uniform(0.25, 0.7), 55 + seed, wmax=rnd.choice([1, 5]))
+    lam = H.brute_lambda(g.offsets, g.adj, g.w)
+    for lp in (1, 2):
+        res = run(g, lp_iters=lp, n0=rnd.choice([1, 2]), seed=seed, correct=True)
+        assert res.cut >= lam
+        side_ok(g, res)
+
+
 # ------------------------------------------------------------- whole method
 @pytest.mark.parametrize("seed", range(30))
 def test_pipeline_upper_bound_bruteforce(seed):
