@@ -65,6 +65,12 @@ typedef struct viecut_opts {
                           8, 16 or 32, or 0 = pick by timing once per handle (default);
                           results never depend on it */
   int32_t emit_group;  /* lanes per vertex of the contraction's pre-merge kernel (same) */
+  int32_t correct;     /* 1 = the correcting step on every label-propagation clustering
+                          (Sec. 4.1, "correcting algorithm"): in each cluster of 2 to
+                          floor(log2 n) vertices, the vertex whose removal lowers the
+                          cluster's weighted degree the most becomes a singleton; 0 = off
+                          (default).  Single-graph handles only (batches and the server
+                          ignore it) */
 } viecut_opts;
 
 /* Per-run statistics (valid after viecut_run / viecut_run_device completes). */

@@ -39,7 +39,7 @@ class ViecutError(RuntimeError):
 class viecut_opts(ctypes.Structure):
     _fields_ = [("n0", ctypes.c_int64), ("pr_runs_max", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("validate", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("lp_group", ctypes.c_int32), ("emit_group", ctypes.c_int32)]
+                ("lp_group", ctypes.c_int32), ("emit_group", ctypes.c_int32), ("correct", ctypes.c_int32)]
 
 
 class viecut_stats(ctypes.Structure):
@@ -509,11 +509,12 @@ class MinCut:
 
     def __init__(self, offsets, adj, weights, n0: int = 10000, pr_runs_max: int = 8, device: int = 0,
                  stream=None, validate: int = 1, timing: bool = False, on_device: bool = False,
-                 lp_group: int = 0, emit_group: int = 0):
+                 lp_group: int = 0, emit_group: int = 0, correct: bool = False):
         n = int(offsets.shape[0] - 1)
         m = int(adj.shape[0])
         o = viecut_opts_init(n0=n0, pr_runs_max=pr_runs_max, device=device, stream=stream,
-                             validate=validate, timing=int(timing), lp_group=lp_group, emit_group=emit_group)
+                             validate=validate, timing=int(timing), lp_group=lp_group, emit_group=emit_group,
+                             correct=int(correct))
         self.n, self.m = n, m
         self._keep = (offsets, adj, weights)
         self.h = (viecut_create_device if on_device else viecut_create)(offsets, adj, n, m, weights, o)

@@ -485,6 +485,115 @@ __global__ void __launch_bounds__(256) cluster_place_k(int64_t c, const long lon
   }
 }
 
+// ---------------------------------------------------------------- correcting step
+// Sec. 4.1, "correcting algorithm" (fixMisplacedVertices of Algorithm 1), optional: in
+// every cluster C of 2..lg vertices (lg = floor(log2 n)), d(C) = weight of the edges
+// leaving C and, for a member v, d(C - v) = d(C) - c(v, V - C) + c(v, C - v); v is
+// misplaced when d(C - v) < d(C), and each cluster gives up at most its misplaced
+// vertex of smallest d(C - v) (ties: smallest id), which becomes a singleton with a
+// cluster id after all others, in ascending vertex order.
+__global__ void corr_size_k(int64_t n, const int32_t* __restrict__ cid, int* __restrict__ csize) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&csize[cid[v]], 1);
+}
+
+__device__ __forceinline__ bool corr_small(int sz, int lg) { return sz >= 2 && sz <= lg; }
+
+// Eight lanes per vertex of a small cluster: its weight to the outside and to the rest
+// of its cluster; the outside weights sum into d(C).
+template <typename WT>
+__global__ void corr_sums_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                            const WT* __restrict__ w, const int32_t* __restrict__ cid,
+                            const int* __restrict__ csize, int lg, long long* __restrict__ vout,
+                            long long* __restrict__ vin, long long* __restrict__ dc) {
+  constexpr int G = 8;
+  const int lane = threadIdx.x & 31, glane = lane & (G - 1);
+  const unsigned gmask = ((1u << G) - 1u) << (lane & ~(G - 1));
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
+    const int32_t C = cid[v];
+    if (!corr_small(csize[C], lg)) continue;  // the same in the group's lanes
+    long long o = 0, i = 0;
+    for (int64_t e = off[v] + glane; e < off[v + 1]; e += G) {
+      const long long x = ldw(w, e);
+      if (cid[adj[e]] == C) i += x;
+      else o += x;
+    }
+#pragma unroll
+    for (int k = G / 2; k > 0; k >>= 1) {
+      o += __shfl_xor_sync(gmask, o, k);
+      i += __shfl_xor_sync(gmask, i, k);
+    }
+    if (glane == 0) {
+      vout[v] = o;
+      vin[v] = i;
+      if (o) atomicAdd((unsigned long long*)&dc[C], (unsigned long long)o);
+    }
+  }
+}
+
+// pass 0: the smallest d(C - v) below d(C) per cluster; pass 1: the smallest id
+// attaining it; pass 2: flag[v] = v leaves its cluster.
+__global__ void corr_pick_k(int64_t n, const int32_t* __restrict__ cid, const int* __restrict__ csize, int lg,
+                            const long long* __restrict__ vout, const long long* __restrict__ vin,
+                            const long long* __restrict__ dc, long long* __restrict__ bestv,
+                            int* __restrict__ bestid, int* __restrict__ flag, int pass) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t C = cid[v];
+    const bool small = corr_small(csize[C], lg);
+    if (pass == 2) {
+      flag[v] = small && bestid[C] == (int)v ? 1 : 0;
+      continue;
+    }
+    if (!small) continue;
+    const long long without = dc[C] - vout[v] + vin[v];
+    if (without >= dc[C]) continue;
+    if (pass == 0) atomicMin(&bestv[C], without);
+    else if (without == bestv[C]) atomicMin(&bestid[C], (int)v);
+  }
+}
+
+__global__ void corr_apply_k(int64_t n, const int* __restrict__ flag, const int* __restrict__ rank,
+                             const int* __restrict__ c_dev, int32_t* __restrict__ cid) {
+  const int c = *c_dev;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    if (flag[v]) cid[v] = c + rank[v];
+}
+
+__global__ void corr_count_k(int* __restrict__ c_dev, const int* __restrict__ moved) { *c_dev += *moved; }
+
+void correct_clusters(const GraphView& g, int32_t* cid, int* c_dev, const CorrectScratch& cs, cudaStream_t s) {
+  const int64_t n = g.n;
+  if (n < 4) return;  // no cluster of 2..floor(log2 n) vertices below 4 vertices
+  int lg = 0;
+  while ((int64_t(2) << lg) <= n) ++lg;
+  VC_CUDA(cudaMemsetAsync(cs.csize, 0, sizeof(int) * n, s));
+  VC_CUDA(cudaMemsetAsync(cs.dc, 0, sizeof(long long) * n, s));
+  VC_CUDA(cudaMemsetAsync(cs.bestv, 0x7f, sizeof(long long) * n, s));  // above every d(C - v)
+  VC_CUDA(cudaMemsetAsync(cs.bestid, 0x7f, sizeof(int) * n, s));       // above every vertex id
+  const int grid = grid_for(n, 256, kSMs * 8);
+  corr_size_k<<<grid, 256, 0, s>>>(n, cid, cs.csize);
+  const int gs = grid_for(n, 32, kSMs * 16);
+  if (g.unit)
+    corr_sums_k<UnitW><<<gs, 256, 0, s>>>(n, g.off, g.adj, nullptr, cid, cs.csize, lg, cs.vout, cs.vin, cs.dc);
+  else if (g.wbytes == 4)
+    corr_sums_k<int32_t><<<gs, 256, 0, s>>>(n, g.off, g.adj, (const int32_t*)g.w, cid, cs.csize, lg, cs.vout,
+                                            cs.vin, cs.dc);
+  else
+    corr_sums_k<long long><<<gs, 256, 0, s>>>(n, g.off, g.adj, (const long long*)g.w, cid, cs.csize, lg, cs.vout,
+                                              cs.vin, cs.dc);
+  for (int pass = 0; pass < 3; ++pass)
+    corr_pick_k<<<grid, 256, 0, s>>>(n, cid, cs.csize, lg, cs.vout, cs.vin, cs.dc, cs.bestv, cs.bestid, cs.flag,
+                                     pass);
+  count_launch(5);
+  VC_CHECK_LAUNCH();
+  exclusive_scan<int, int>(cs.flag, cs.rank, n, cs.moved, cs.scan_scr32, s);
+  corr_apply_k<<<grid, 256, 0, s>>>(n, cs.flag, cs.rank, c_dev, cid);
+  corr_count_k<<<1, 1, 0, s>>>(c_dev, cs.moved);
+  count_launch(2);
+  VC_CHECK_LAUNCH();
+}
+
 // ---------------------------------------------------------------- giant clusters
 __global__ void giant_list_k(int64_t c, const long long* __restrict__ cbase, int* __restrict__ gcount,
                              int32_t* __restrict__ glist, int32_t* __restrict__ gT) {

@@ -70,7 +70,7 @@ struct Workspace {
   // entry-sized
   Buf tmpK, tmpV, cmpK, cmpV;
   // pair-sized
-  Buf keysA, keysB, valsA, valsB, hist, heads, hpos, cvT, ccur, giantS;
+  Buf keysA, keysB, valsA, valsB, hist, heads, hpos, cvT, ccur, giantS, corrI, corrL;
   // coarse graphs (ping-pong)
   Buf coff[2], cadj[2], cw[2], csrc[2];
   // global-class tables
@@ -299,7 +299,7 @@ struct Workspace {
 
   // Contracts g by labels into the coarse buffer `slot`; cid_out[n] receives the map.
   // Returns the coarse view; h_counters holds c and the pair count afterwards.
-  GraphView contract(const GraphView& g, const int32_t* labels, int32_t* cid_out, int slot) {
+  GraphView contract(const GraphView& g, const int32_t* labels, int32_t* cid_out, int slot, bool correct = false) {
     if (!bins_valid) build_bins(g);
     ContractScratch cs;
     cs.flags = flags.as<int32_t>();
@@ -313,6 +313,22 @@ struct Workspace {
     cs.scan_scr = scan64.as<long long>();
     cs.scan_scr32 = scan32.as<int>();
     relabel(labels, g.n, cid_out, cs, &ctr()->c, s);
+    if (correct) {
+      CorrectScratch cr;
+      int* ci = corrI.ensure_n<int>(4 * g.n + 1);
+      long long* cl = corrL.ensure_n<long long>(4 * g.n);
+      cr.csize = ci;
+      cr.bestid = ci + g.n;
+      cr.flag = ci + 2 * g.n;
+      cr.rank = ci + 3 * g.n;
+      cr.moved = ci + 4 * g.n;
+      cr.scan_scr32 = scan32.as<int>();
+      cr.dc = cl;
+      cr.bestv = cl + g.n;
+      cr.vout = cl + 2 * g.n;
+      cr.vin = cl + 3 * g.n;
+      correct_clusters(g, cid_out, &ctr()->c, cr, s);
+    }
     PairOut po{cs.tmp_key, cs.tmp_val, cs.cmp_key, cs.cmp_val};
     po.nclust = &ctr()->c;
     po.nfine = g.n;

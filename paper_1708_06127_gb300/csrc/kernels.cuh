@@ -153,6 +153,16 @@ struct ContractScratch {
 // Relabel: cid[v] = rank of lab[v] among the distinct labels; *c_dev = count.
 void relabel(const int32_t* lab, int64_t n, int32_t* cid, ContractScratch& cs, int* c_dev, cudaStream_t s);
 
+// The correcting step (Sec. 4.1, optional): the misplaced vertex of each cluster of 2 to
+// floor(log2 n) vertices becomes a singleton (cid and *c_dev updated in place).  n-sized
+// scratch: csize, bestid, flag, rank (int), dc, bestv, vout, vin (int64); moved: 1 int;
+// scan_scr32: scan_scratch_elems(n) ints.
+struct CorrectScratch {
+  int *csize, *bestid, *flag, *rank, *moved, *scan_scr32;
+  long long *dc, *bestv, *vout, *vin;
+};
+void correct_clusters(const GraphView& g, int32_t* cid, int* c_dev, const CorrectScratch& cs, cudaStream_t s);
+
 // Cluster merge: a warp merges clusters of at most kMergeMax pre-merged pairs in
 // registers, a block those of at most kMergeBlockMax; the few "giant" clusters beyond
 // that (GiantScratch) are merged together by one radix sort of their pairs keyed by

@@ -71,6 +71,7 @@ struct Handle {
   int64_t n0 = 10000;
   int pr_runs_max = 8;
   int validate = 1;
+  bool correct = false;  // the correcting step on label-propagation clusterings
   bool unit = false;    // every input weight is 1 (found by validation)
   bool simple = false;  // every input list strictly increasing (found by validation)
   bool host_input = false;  // the graph was copied from host arrays into in_*
@@ -203,7 +204,7 @@ static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, u
     cudaEvent_t a0 = W.mark();
     int32_t* cid = contracted ? W.cidT.as<int32_t>() : W.map0.as<int32_t>();
     int dst = slot == 0 ? 1 : 0;
-    GraphView h = W.contract(G, labels, cid, dst);
+    GraphView h = W.contract(G, labels, cid, dst, kind == 1 && H.correct);
     set_n_k<<<1, 1, 0, s>>>(st, h.n);
     count_launch();
     if (!contracted) {
@@ -469,6 +470,7 @@ static int create_common(viecut_t** out, int64_t n, int64_t m, const viecut_opts
   if (o.pr_runs_max < 0) throw Error{VIECUT_EINVAL, "pr_runs_max must be >= 0"};
   for (int G : {o.lp_group, o.emit_group})
     if (G != 0 && G != 8 && G != 16 && G != 32) throw Error{VIECUT_EINVAL, "lp_group and emit_group must be 0, 8, 16 or 32"};
+  if (o.correct != 0 && o.correct != 1) throw Error{VIECUT_EINVAL, "correct must be 0 or 1"};
   // validate 2 rejects a malformed host graph before any device call
   const bool checked = host_input && o.validate >= 2;
   bool unit = false, simple = false;
@@ -487,6 +489,7 @@ static int create_common(viecut_t** out, int64_t n, int64_t m, const viecut_opts
     H.n0 = o.n0;
     H.pr_runs_max = o.pr_runs_max;
     H.validate = o.validate;
+    H.correct = o.correct != 0;
     H.ws = new vc::Workspace;
     H.ws->s = H.stream;
     H.ws->timing = o.timing != 0;

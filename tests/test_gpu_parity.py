@@ -271,6 +271,24 @@ def test_exact_mode():
             assert cut <= oracle.viecut(g.offsets, g.adj, g.w, seed=s, lp_iters=1, n0=64).cut
 
 
+def test_correcting_step_parity():
+    """The method with the correcting step (Sec. 4.1) equals the oracle's reading of it
+    (trace, cut, side); on all but the isolated-vertex graph it changes the run."""
+    graphs = [gg.workload_rhg_small(2), gg.with_pair_weights(gg.core_lcc(gg.rhg(1 << 12, 20, 7), 0), 7, 1, 50),
+              gg.er(3000, 12, 3, 1, 100), hub_graph(), gg.core_lcc(gg.rhg(1 << 13, 32, 1), 16)]
+    changed = 0
+    for g in graphs:
+        for seed, lp in ((1, 1), (2, 2)):
+            ref = oracle.viecut(g.offsets, g.adj, g.w, seed=seed, lp_iters=lp, n0=64, correct=True)
+            with vc.MinCut(g.offsets, g.adj, g.w, n0=64, correct=True) as mc:
+                cut, bits = mc.run(seed, lp)
+                tr = mc.trace()
+            assert cut == ref.cut and np.array_equal(bits, ref.side_bits), (g.name, seed, lp)
+            assert tr == ref.trace, (g.name, seed, lp)
+            changed += ref.trace != oracle.viecut(g.offsets, g.adj, g.w, seed=seed, lp_iters=lp, n0=64).trace
+    assert changed >= 8
+
+
 def test_viecut_repeatable_and_seeded():
     g = gg.workload_rhg_small(3)
     with vc.MinCut(g.offsets, g.adj, g.w, n0=64) as mc:
