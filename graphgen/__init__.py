@@ -127,6 +127,20 @@ def planted(blocks: int, block_n: int, avg_deg: float, bridges: int, seed: int,
                  f"planted({blocks}x{block_n},deg={avg_deg},bridges={bridges},seed={seed})")
 
 
+def clustered_er(n: int, density: float, k: int, seed: int) -> Graph:
+    """The clustered Erdos-Renyi family of the paper's experiments (Sec. 5, "clustered
+    Erdos-Renyi graphs"): G(n, p) with p = density / 100, weights uniform in [1, 100],
+    the weight of an edge inside one of the k clusters (contiguous id ranges) multiplied
+    by n, so that the minimum cut separates clusters with high probability."""
+    g = er(n, density / 100.0 * (n - 1), seed, 1, 100)
+    part = (np.arange(g.n, dtype=np.int64) * k) // max(g.n, 1)
+    src = np.repeat(np.arange(g.n), np.diff(g.offsets))
+    w = g.w.astype(np.int64)
+    w[part[src] == part[g.adj]] *= n
+    assert w.max() < 2**31
+    return Graph(g.offsets, g.adj, w.astype(np.int32), f"clustered_er(n={n},d={density}%,k={k},seed={seed})")
+
+
 def core_lcc(g: Graph, k: int, lcc: bool = True) -> Graph:
     """k-core (peel degree < k) followed by the largest connected component."""
     h = _load().gg_core_lcc(g.offsets.ctypes.data, g.adj.ctypes.data, g.w.ctypes.data, g.n, k, int(lcc))

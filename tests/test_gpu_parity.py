@@ -271,6 +271,16 @@ def test_exact_mode():
             assert cut <= oracle.viecut(g.offsets, g.adj, g.w, seed=s, lp_iters=1, n0=64).cut
 
 
+def test_clustered_er_family():
+    """The paper's clustered Erdos-Renyi family (weights inside clusters times n): the
+    method equals the oracle, and the exact mode gives the oracle's exact value."""
+    for k, d in ((2, 10), (4, 5), (8, 20)):
+        g = gg.clustered_er(2000, d, k, 30 + k)
+        assert_same(g, seed=k, lp=2, n0=64)
+        cut, _ = vc.exact_min_cut(g.offsets, g.adj, g.w)
+        assert cut == oracle.viecut(g.offsets, g.adj, g.w, seed=1, lp_iters=0, n0=g.n).cut
+
+
 def test_correcting_step_parity():
     """The method with the correcting step (Sec. 4.1) equals the oracle's reading of it
     (trace, cut, side); on all but the isolated-vertex graph it changes the run."""

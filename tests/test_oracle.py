@@ -384,6 +384,16 @@ def test_pipeline_with_correcting_step(seed):
         side_ok(g, res)
 
 
+def test_clustered_er_exact_and_method():
+    """The clustered Erdos-Renyi family (Sec. 5): the exact step alone equals
+    Stoer-Wagner, and the method with two rounds finds the same value."""
+    for k in (2, 4):
+        g = gg.clustered_er(240, 10, k, 7 + k)
+        lam = H.stoer_wagner(g.offsets, g.adj, g.w)
+        assert run(g, lp_iters=0, n0=g.n).cut == lam
+        assert run(g, lp_iters=2, n0=32, seed=k).cut == lam
+
+
 # ------------------------------------------------------------- whole method
 @pytest.mark.parametrize("seed", range(30))
 def test_pipeline_upper_bound_bruteforce(seed):
