@@ -20,8 +20,8 @@
 //       the paper breaks ties uniformly at random.  mix64 is a bijection, so (S, H)
 //       totally orders distinct labels.
 //  [R3] A fixed number of rounds, no convergence test, no first-round restriction
-//       and no correcting step (Sec. 4.1 notes the restriction is not used in
-//       practice; the correcting step is switched off as in the paper's ER runs).
+//       (Sec. 4.1 notes the restriction is not used in practice); the correcting
+//       step is off unless asked for ([R10]), as in the paper's ER runs.
 //  [R4] Cluster ids are ranks of the final label values, ascending.
 //  [R5] Padberg-Rinaldi test 2 marks only the edge to each vertex's designated
 //       partner p(v) = argmax over neighbours u of (c(v,u), -u); marking every
