@@ -69,8 +69,8 @@ typedef struct viecut_opts {
                           (Sec. 4.1, "correcting algorithm"): in each cluster of 2 to
                           floor(log2 n) vertices, the vertex whose removal lowers the
                           cluster's weighted degree the most becomes a singleton; 0 = off
-                          (default).  Single-graph handles only (batches and the server
-                          ignore it) */
+                          (default).  Single-graph handles only: viecut_batch_create and
+                          viecut_server_start refuse it with VIECUT_EINVAL */
 } viecut_opts;
 
 /* Per-run statistics (valid after viecut_run / viecut_run_device completes). */

@@ -400,7 +400,7 @@ def viecut_server_opts_init(**kw) -> viecut_server_opts:
     o = viecut_server_opts()
     _check(lib().viecut_server_opts_init(ctypes.byref(o)))
     for k, v in kw.items():
-        if k in ("n0", "pr_runs_max", "device", "stream", "lp_group", "emit_group"):
+        if k in ("n0", "pr_runs_max", "device", "stream", "lp_group", "emit_group", "correct"):
             setattr(o.base, k, v)
         else:
             setattr(o, k, v)

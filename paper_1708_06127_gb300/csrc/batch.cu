@@ -1318,6 +1318,7 @@ int viecut_batch_create(viecut_batch** out, const viecut_graph_desc* graphs, int
   viecut_opts_init(&o);
   if (opts) o = *opts;
   if (o.n0 < 1 || o.pr_runs_max < 0) throw Error{VIECUT_EINVAL, "bad options"};
+  if (o.correct) throw Error{VIECUT_EINVAL, "correct: the correcting step runs on single-graph handles only"};
   auto* x = new viecut_batch;
   try {
     vc::batch_create(x->b, graphs, k, o);
@@ -1400,6 +1401,7 @@ int viecut_server_start(viecut_server** out, const viecut_server_opts* opts) {
   if (o.max_slots < 1 || o.hbm_budget_bytes < 1 || o.lp_iters < 0 || o.base.n0 < 1 || o.base.pr_runs_max < 0 ||
       o.solo_min_n < 0)
     throw Error{VIECUT_EINVAL, "bad server options"};
+  if (o.base.correct) throw Error{VIECUT_EINVAL, "correct: the correcting step runs on single-graph handles only"};
   auto* x = new viecut_server;
   try {
     vc::Server& S = x->s;

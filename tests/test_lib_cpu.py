@@ -54,6 +54,24 @@ def test_group_options_are_checked_before_any_device_call(lib):
         assert e.value.code == vc.VIECUT_EINVAL and "lp_group" in str(e.value)
 
 
+def test_correct_option_is_checked_before_any_device_call(lib):
+    """correct must be 0 or 1, and batches and the server refuse it (the correcting
+    step runs on single-graph handles only)."""
+    off = np.array([0, 1, 2], np.int64)
+    adj = np.array([1, 0], np.int32)
+    w = np.array([1, 1], np.int32)
+    assert vc.viecut_opts_init().correct == 0
+    with pytest.raises(vc.ViecutError) as e:
+        vc.viecut_create(off, adj, 2, 2, w, vc.viecut_opts_init(correct=2))
+    assert e.value.code == vc.VIECUT_EINVAL and "correct" in str(e.value)
+    with pytest.raises(vc.ViecutError) as e:
+        vc.viecut_batch_create([(off, adj, w)], vc.viecut_opts_init(correct=1))
+    assert e.value.code == vc.VIECUT_EINVAL and "correct" in str(e.value)
+    with pytest.raises(vc.ViecutError) as e:
+        vc.viecut_server_start(vc.viecut_server_opts_init(correct=1))
+    assert e.value.code == vc.VIECUT_EINVAL and "correct" in str(e.value)
+
+
 def test_host_validation_rejects_bad_graphs(lib):
     """Full validation of host arrays (validate = 2) happens before any device call,
     so it is testable here: every malformed input must give EINVAL with a message."""
