@@ -1,12 +1,15 @@
 // Cluster contraction (Sec. 4.1, "contract it"; contraction semantics, Sec. 3):
 // every block of a labelling becomes one vertex, intra-block edges vanish and
 // parallel edges between two blocks merge with summed weight.  Block ids are the
-// ranks of the label values.  Steps: relabel (flag + scan), pre-merge per fine
-// vertex (lp.cu), then either
-//   * the cluster merge: a counting sort of the pre-merged pairs by source cluster
-//     and a warp per cluster that merges its pairs in registers and writes the
-//     distinct targets in ascending order (every cluster holding <= kMergeMax pairs), or
-//   * pair build, LSD radix sort on (cid v, cid u) and a run reduction (otherwise).
+// ranks of the label values.  Steps: relabel (flag + scan), the optional correcting
+// step, pre-merge per fine vertex (lp.cu), then either
+//   * the cluster merge: a counting sort of the pre-merged pairs by source cluster,
+//     then a warp per cluster of at most kMergeMax pairs (registers, or a bitonic sort
+//     in shared memory), a block per cluster of at most kMergeBlockMax, and one radix
+//     sort for all larger ("giant") clusters together; each writes its distinct
+//     targets in ascending order at the front of its segment, or
+//   * pair build, LSD radix sort on (cid v, cid u) and a run reduction (when the giant
+//     clusters hold more than half of the pairs).
 #include <limits.h>
 
 #include <algorithm>
