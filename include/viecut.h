@@ -288,6 +288,13 @@ int viecut_server_get_stats(viecut_server* s, viecut_server_stats* st);
 /* Stops the thread (requests still queued or resident are abandoned) and frees all. */
 int viecut_server_stop(viecut_server* s);
 
+/* The library's sizes of its public structures, for bindings that restate them:
+ * sizes[0..6] = sizeof viecut_opts, viecut_stats, viecut_step, viecut_graph_desc,
+ * viecut_batch_stats, viecut_server_opts, viecut_server_stats (as many as count
+ * allows).  Returns the number of sizes the library knows (7), or VIECUT_EINVAL for a
+ * null array with count > 0.  Needs no device. */
+int viecut_struct_sizes(int64_t* sizes, int32_t count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,7 @@ class viecut_step(ctypes.Structure):
 _vp, _i64, _i32, _u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
 _pvp = ctypes.POINTER(ctypes.c_void_p)
 SIGNATURES = [
+    ("viecut_struct_sizes", ctypes.c_int, [_vp, ctypes.c_int32]),
     ("viecut_opts_init", ctypes.c_int, [_vp]),
     ("viecut_create", ctypes.c_int, [_pvp, _vp, _vp, _i64, _i64, _vp, _vp]),
     ("viecut_create_device", ctypes.c_int, [_pvp, _vp, _vp, _i64, _i64, _vp, _vp]),

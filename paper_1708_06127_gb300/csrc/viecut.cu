@@ -399,6 +399,17 @@ using vc::Error;
 extern "C" {
 
 const char* viecut_last_error(void) { return vc::t_last_error.c_str(); }
+
+int viecut_struct_sizes(int64_t* sizes, int32_t count) {
+  const int64_t known[] = {(int64_t)sizeof(viecut_opts),        (int64_t)sizeof(viecut_stats),
+                           (int64_t)sizeof(viecut_step),        (int64_t)sizeof(viecut_graph_desc),
+                           (int64_t)sizeof(viecut_batch_stats), (int64_t)sizeof(viecut_server_opts),
+                           (int64_t)sizeof(viecut_server_stats)};
+  const int32_t nk = (int32_t)(sizeof(known) / sizeof(known[0]));
+  if (count > 0 && !sizes) return VIECUT_EINVAL;
+  for (int32_t i = 0; i < count && i < nk; ++i) sizes[i] = known[i];
+  return nk;
+}
 int64_t viecut_launch_count(void) { return (int64_t)vc::g_launches; }
 
 int viecut_opts_init(viecut_opts* o) {

@@ -39,6 +39,19 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(declared_functions()) == bound, "Python binding and header disagree"
 
 
+def test_binding_structs_match_the_library(lib):
+    """Every structure the binding restates has the library's size (a field added on
+    one side only would shift every later field)."""
+    import ctypes
+    sizes = np.zeros(8, np.int64)
+    n = vc.lib().viecut_struct_sizes(sizes.ctypes.data, 8)
+    assert n == 7
+    mine = [vc.viecut_opts, vc.viecut_stats, vc.viecut_step, vc.viecut_graph_desc, vc.viecut_batch_stats,
+            vc.viecut_server_opts, vc.viecut_server_stats]
+    assert sizes[:7].tolist() == [ctypes.sizeof(t) for t in mine]
+    assert vc.lib().viecut_struct_sizes(None, 1) == vc.VIECUT_EINVAL
+
+
 def test_opts_defaults(lib):
     o = vc.viecut_opts_init()
     assert (o.n0, o.pr_runs_max, o.device, o.validate, o.timing) == (10000, 8, 0, 1, 0)
