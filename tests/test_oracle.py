@@ -336,6 +336,27 @@ def test_correct_tie_and_one_per_cluster():
     assert k == 14 and cid[1] == 13 and cid[0] == cid[2] == cid[3] == 0
 
 
+def test_correct_recovers_the_figure_case():
+    """The situation of the paper's figure on misplaced vertices (Sec. 4.1): vertex 3 is
+    tied to triangle A = {0,1,2} by weight 5 and to triangles B1, B2 by 3 each, so label
+    propagation puts it into A (its strongest single label) although it weighs more
+    outside; A's cut (5, the minimum cut) is then lost in the contracted graph, whose
+    cluster A + 3 has degree 6.  With one round the method returns 6 in most seeds,
+    and with the correcting step (3 becomes a singleton) always the minimum cut."""
+    E = [(0, 1, 10), (1, 2, 10), (0, 2, 10), (4, 5, 10), (5, 6, 10), (4, 6, 10), (7, 8, 10), (8, 9, 10),
+         (7, 9, 10), (3, 0, 5), (3, 4, 3), (3, 7, 3), (5, 8, 20), (6, 9, 20)]
+    g = gg.from_edges(10, E)
+    lam = H.brute_lambda(g.offsets, g.adj, g.w)
+    assert lam == 5
+    missed = 0
+    for seed in range(1, 40):
+        missed += run(g, seed=seed, lp_iters=1, n0=2).cut != lam
+        res = run(g, seed=seed, lp_iters=1, n0=2, correct=True)
+        assert res.cut == lam
+        side_ok(g, res)
+    assert missed >= 20
+
+
 @pytest.mark.parametrize("seed", range(12))
 def test_correct_bruteforce(seed):
     """Against the definitions: cluster cuts summed edge by edge over the vertex sets
