@@ -161,7 +161,9 @@ int64_t viecut_launch_count(void);
  * ------------------------------------------------------------------------- */
 typedef struct viecut_graph viecut_graph;
 
-/* Copies a host CSR (int64 weights) to the device. */
+/* Copies a host CSR (int64 weights) to the device.  A graph whose weights are all 1
+ * is marked so, and the steps then run the kernels that read no weights, as they do on
+ * an input graph of unit weights. */
 int viecut_graph_upload(viecut_graph** g, const int64_t* offsets, const int32_t* adj, const int64_t* weights,
                         int64_t n, int64_t nnz, int32_t device);
 int viecut_graph_shape(const viecut_graph* g, int64_t* n, int64_t* nnz);
@@ -193,7 +195,9 @@ int viecut_step_noi_round(viecut_graph* g, int64_t lambda_hat, int32_t* labels, 
  * passes the graph (DEVICE CSR of n vertices with merged, sorted lists and int64
  * weights, as every contracted graph is), the bound, and the DEVICE outputs
  * d_labels[n] (union-find representative, smallest id of each merged group) and
- * *d_changed (1 if anything merged).  Work space is a static device array sized
+ * *d_changed (1 if anything merged).  No pointer may be NULL, not even d_adj and
+ * d_weights of a graph without edges (the host cannot read offsets[n]): EINVAL, and
+ * nothing is launched.  Work space is a static device array sized
  * for n <= 65536 (about 0.8 MB, kept by every GPU that loads the library until the
  * process exits); larger n is rejected with VIECUT_EINVAL and nothing is launched.
  * The round runs on `stream` (NULL: the default stream) and the call returns without

@@ -38,6 +38,20 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _declare_viecut(lib):
+    vp, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+    lib.orc_viecut.restype = ctypes.c_int
+    lib.orc_viecut.argtypes = [i64, vp, vp, vp, i32, u64, i32, i64, i32, vp, vp, vp, i64, vp, i32]
+
+
+def load_variant(path: str):
+    """Loads another build of oracle.cpp (tests only: a copy with a planted mistake)
+    for ``viecut(..., _lib=...)``."""
+    lib = ctypes.CDLL(path)
+    _declare_viecut(lib)
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
@@ -59,8 +73,7 @@ def _load():
                 f = getattr(lib, name)
                 f.restype = i64
                 f.argtypes = [i64, vp, vp, vp, i64, vp]
-            lib.orc_viecut.restype = ctypes.c_int
-            lib.orc_viecut.argtypes = [i64, vp, vp, vp, i32, u64, i32, i64, i32, vp, vp, vp, i64, vp, i32]
+            _declare_viecut(lib)
             lib.orc_correct.restype = i64
             lib.orc_correct.argtypes = [i64, vp, vp, vp, vp, vp]
             _lib = lib
@@ -171,9 +184,11 @@ class Result:
 
 
 def viecut(offsets, adj, w, seed: int = 1, lp_iters: int = 2, n0: int = 10000,
-           pr_runs_max: int = 8, trace_cap: int = 4096, correct: bool = False) -> Result:
+           pr_runs_max: int = 8, trace_cap: int = 4096, correct: bool = False, _lib=None) -> Result:
     """The whole deterministic method.  `w` may be int32 or int64.  correct: the
-    correcting step on every label-propagation clustering (reading [R10])."""
+    correcting step on every label-propagation clustering (reading [R10]).  `_lib`
+    (tests only) runs another build of oracle.cpp with the same entry points, e.g. one
+    with a mistake planted to show that a pin catches it."""
     off, po = _c(offsets, np.int64)
     a, pa = _c(adj, np.int32)
     w = np.asarray(w)
@@ -184,7 +199,8 @@ def viecut(offsets, adj, w, seed: int = 1, lp_iters: int = 2, n0: int = 10000,
     bits = np.zeros((n + 63) // 64, np.uint64)
     tr = (OrcStep * trace_cap)()
     tl = ctypes.c_int64()
-    rc = _load().orc_viecut(n, po, pa, pw, wbytes, seed & (2**64 - 1), lp_iters, n0, pr_runs_max,
+    lib = _lib if _lib is not None else _load()
+    rc = lib.orc_viecut(n, po, pa, pw, wbytes, seed & (2**64 - 1), lp_iters, n0, pr_runs_max,
                             ctypes.byref(cut), bits.ctypes.data, tr, trace_cap, ctypes.byref(tl),
                             1 if correct else 0)
     if rc != 0:

@@ -701,7 +701,10 @@ extern "C" int viecut_noi_round_noalloc(const int64_t* d_offsets, const int32_t*
     if (n < 1 || n > vc::kNoAllocMaxN)
       throw vc::Error{VIECUT_EINVAL, "viecut_noi_round_noalloc: n = " + std::to_string(n) + " is outside [1, " +
                                          std::to_string(vc::kNoAllocMaxN) + "], the size of its static scratch"};
-    if (!d_offsets || !d_labels || !d_changed) throw vc::Error{VIECUT_EINVAL, "null device pointer"};
+    // the host cannot see offsets[n], so a graph with edges cannot be told apart from an
+    // edgeless one here: every array must be given
+    if (!d_offsets || !d_adj || !d_weights || !d_labels || !d_changed)
+      throw vc::Error{VIECUT_EINVAL, "viecut_noi_round_noalloc: null device pointer"};
     if (lambda_hat < 0) throw vc::Error{VIECUT_EINVAL, "lambda_hat must be >= 0"};
     unsigned char* scratch = vc::noalloc_scratch_address();
     vc::noi_round_noalloc_k<<<1, vc::kSparseThreads, 0, (cudaStream_t)stream>>>(

@@ -371,6 +371,7 @@ struct StepGraph {
   int device = 0;
   int64_t n = 0, nnz = 0;
   bool simple = false;
+  bool unit = false;  // every weight is 1: the kernels that can then read no weights
   Buf off, adj, w;
   GraphView view() const {
     GraphView g;
@@ -381,6 +382,7 @@ struct StepGraph {
     g.w = w.p;
     g.wbytes = 8;
     g.simple = simple;
+    g.unit = unit;
     return g;
   }
 };
@@ -679,6 +681,8 @@ int viecut_graph_upload(viecut_graph** g, const int64_t* offsets, const int32_t*
     for (int64_t v = 0; v < n && x->g.simple; ++v)
       for (int64_t e = offsets[v]; e + 1 < offsets[v + 1]; ++e)
         if (adj[e + 1] <= adj[e]) { x->g.simple = false; break; }
+    x->g.unit = true;
+    for (int64_t e = 0; e < nnz && x->g.unit; ++e) x->g.unit = weights[e] == 1;
     VC_CUDA(cudaMemcpy(x->g.off.ensure_n<int64_t>(n + 1), offsets, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
     x->g.adj.ensure_n<int32_t>(nnz);
     x->g.w.ensure_n<long long>(nnz);

@@ -45,8 +45,9 @@ def assert_same(g, seed=1, lp=2, n0=10000, pr=8):
 
 
 def hub_graph(seed=5):
-    """ER background plus one vertex of degree 3000 (global-table class) and a few of
-    degree 200-1500 (block class); weights in [1, 9]."""
+    """ER background plus vertices of degree 3000 and 1500 (block class: 513 to 4096
+    entries, a shared-memory table), 700 (block class) and 200 (warp class); weights in
+    [1, 9]."""
     rnd = random.Random(seed)
     n = 6000
     base = gg.er(n, 6, seed, 1, 9)
@@ -60,6 +61,32 @@ def hub_graph(seed=5):
         for u in rnd.sample(range(4, n), deg):
             E[(hub, u)] = rnd.randint(1, 9)
     return gg.from_edges(n, [(a, b, w) for (a, b), w in E.items()], "hubs")
+
+
+def giant_hub_graph(unit: bool, parallel: bool = False, seed: int = 7):
+    """ER background (n = 40000, average degree 6) plus hubs of degree 5000, 12000 and
+    20000 -- lists above 4096 entries, the global-table class (a hash table in global
+    memory per block) -- and one of 3000 (block class).  Weights in [1, 9], or all 1.
+    parallel: every hub edge to an even neighbour is listed twice (parallel entries, so
+    the lists are not strictly increasing and the first round cannot take the
+    no-aggregation path)."""
+    rnd = random.Random(seed)
+    n = 40000
+    base = gg.er(n, 6, seed, 1, 9)
+    E = {}
+    for v in range(n):
+        for e in range(base.offsets[v], base.offsets[v + 1]):
+            u = int(base.adj[e])
+            if v < u:
+                E[(v, u)] = 1 if unit else int(base.w[e])
+    for hub, deg in [(0, 20000), (1, 12000), (2, 5000), (3, 3000)]:
+        for u in rnd.sample(range(4, n), deg):
+            E[(hub, u)] = 1 if unit else rnd.randint(1, 9)
+    edges = [(a, b, w) for (a, b), w in E.items()]
+    if parallel:
+        edges += [(a, b, w) for (a, b, w) in edges if a < 4 and b % 2 == 0]
+    g = gg.core_lcc(gg.from_edges(n, edges), 3)  # 3-core, largest component
+    return gg.Graph(g.offsets, g.adj, g.w, f"giant-hubs(unit={unit},parallel={parallel})")
 
 
 def multi_edge_graph():
@@ -167,6 +194,40 @@ def test_contract_giant_clusters():
     for rest in (v, v // 4):
         labels = np.where(giant >= 0, giant, rest)
         compare_contract(G, labels.astype(np.int32))
+
+
+@pytest.mark.parametrize("unit,parallel", [(True, False), (False, False), (True, True)])
+def test_global_table_class_parity(unit, parallel):
+    """Lists of 5000 to 20000 entries take the global-table kernels: the first round on
+    strictly increasing lists (lp_first_simple_block_k), later rounds and first rounds on
+    lists with parallel entries (lp_block_k with a global table), and the contraction's
+    pre-merge (emit_block_k).  Labels after rounds 1 and 2 (from the identity and from
+    arbitrary labels) and the contracted CSR equal the oracle's element by element."""
+    g = giant_hub_graph(unit, parallel)
+    assert np.diff(g.offsets).max() > 4096 * 4
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    d = upload(G)
+    try:
+        for seed, level in [(1, 0), (9, 2)]:
+            key = oracle.level_key(seed, level)
+            got = vc.viecut_step_lp(d, None, key, 2)
+            lab = np.arange(G.n, dtype=np.int32)
+            for r in range(2):
+                lab = oracle.lp_round(G, lab, key)
+                assert np.array_equal(got[r], lab), (g.name, seed, r)
+        rnd = np.random.default_rng(5)
+        lab0 = rnd.integers(0, 64, G.n).astype(np.int32)
+        key = oracle.level_key(4, 1)
+        got = vc.viecut_step_lp(d, lab0, key, 2)
+        l1 = oracle.lp_round(G, lab0, key)
+        assert np.array_equal(got[0], l1) and np.array_equal(got[1], oracle.lp_round(G, l1, key))
+    finally:
+        vc.viecut_graph_free(d)
+    key = oracle.level_key(1, 0)
+    lp = oracle.lp_round(G, oracle.lp_round(G, np.arange(G.n, dtype=np.int32), key), key)
+    for labels in [lp, np.arange(G.n), rnd.integers(0, 2000, G.n)]:
+        compare_contract(G, labels.astype(np.int32))
+    assert_same(g, seed=2, lp=2, n0=16)
 
 
 def coarse_graphs():

@@ -468,3 +468,63 @@ def test_planted_small():
     res = run(g, n0=64)
     assert res.cut >= lam
     side_ok(g, res)
+
+
+# ------------------------------------------------------- bound tie rule (R9)
+def _cliques_with_tie():
+    """Two K_4 on {0..3} and {4..7} joined by the bridges (1,5), (2,6), (3,7).  Vertices
+    0 and 4 have degree 3, all others 4; the bridges are a cut of weight 3 too, so
+    lambda = 3 is realised by {0}, {4} and each clique.  The initial bound is the
+    trivial cut at vertex 0 (smallest argmin); every later graph in which a clique or
+    vertex 4 is a vertex of degree 3 ties with it."""
+    E = [(a, b, 1) for a in range(4) for b in range(a + 1, 4)]
+    E += [(4 + a, 4 + b, 1) for a in range(4) for b in range(a + 1, 4)]
+    E += [(1, 5, 1), (2, 6, 1), (3, 7, 1)]
+    return gg.from_edges(8, E, "2K4+3")
+
+
+TIE_CASES = [
+    (lambda: H.cycle(12), [(0, BIG_N0), (0, 1), (2, 2)]),
+    (_cliques_with_tie, [(0, BIG_N0), (1, 2), (2, 2)]),
+]
+
+
+def _tie_rule_holds(g, res):
+    """[R9]: lambda-hat improves only on a strictly smaller trivial cut, so in these
+    graphs (every trivial cut found later is at least the initial one) the returned
+    side is the first argmin, {0}, which the normalisation turns into V - {0}."""
+    want = np.ones(g.n, bool)
+    want[0] = False
+    return res.cut == int(np.diff(g.offsets).min()) and np.array_equal(res.side(g.n), want)
+
+
+def test_bound_keeps_the_earliest_of_equal_trivial_cuts():
+    for make, runs in TIE_CASES:
+        g = make()
+        lam = H.brute_lambda(g.offsets, g.adj, g.w)
+        for lp, n0 in runs:
+            res = run(g, lp_iters=lp, n0=n0, seed=3)
+            assert res.cut == lam
+            assert all(s[4] == lam for s in res.trace)
+            assert _tie_rule_holds(g, res), (g.name, lp, n0)
+
+
+def test_bound_tie_pin_catches_a_non_strict_update(tmp_path):
+    """Plants the plausible mistake (an update on equal trivial cuts) in a copy of the
+    oracle, on the CPU, and checks that the pin above rejects it."""
+    import subprocess
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.cpp")).read()
+    line = "if (dmin < run.lambda_hat) {"
+    assert src.count(line) == 1
+    mutant = tmp_path / "oracle_le.cpp"
+    mutant.write_text(src.replace(line, "if (dmin <= run.lambda_hat) {"))
+    so = tmp_path / "liboracle_le.so"
+    subprocess.run(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", str(mutant), "-o", str(so)], check=True)
+    lib = oracle.load_variant(str(so))
+    caught = 0
+    for make, runs in TIE_CASES:
+        g = make()
+        for lp, n0 in runs:
+            res = oracle.viecut(g.offsets, g.adj, g.w, seed=3, lp_iters=lp, n0=n0, _lib=lib)
+            caught += not _tie_rule_holds(g, res)
+    assert caught >= 3  # the label-propagation runs meet a tie on another side

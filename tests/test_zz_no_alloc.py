@@ -6,8 +6,9 @@ pay cudaMalloc's implicit device synchronisation.  For them the library offers a
 Nagamochi-Ono-Ibaraki round whose work space is a static device array.  These tests
 call it through the C ABI on device buffers the test owns and compare its output with
 the allocating entry point viecut_step_noi_round, twice in a row and across graphs
-of different sizes (each call runs on the scratch the previous call left behind).
-Integer results: the comparison is exact.
+of different sizes (each call runs on the scratch the previous call left behind), and
+on the first pass also with the CPU oracle's round.  Integer results: the comparison
+is exact.
 """
 import numpy as np
 import pytest
@@ -77,6 +78,9 @@ def test_noalloc_round_matches_allocating_round():
             stream.synchronize()
             assert np.array_equal(labels.cpu().numpy(), ref_labels), (call, h.n, lam)
             assert int(changed.item()) == ref_changed, (call, h.n, lam)
+            if call == 0:  # and both equal the oracle's round
+                orc_labels, orc_unions = oracle.noi_round(h, lam)
+                assert np.array_equal(ref_labels, orc_labels) and ref_changed == (orc_unions > 0), (h.n, lam)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
@@ -89,3 +93,22 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(vc.ViecutError) as e:
         vc.viecut_noi_round_noalloc(off, None, None, n, 1, labels, changed)
     assert e.value.code == vc.VIECUT_EINVAL and "65536" in str(e.value)
+
+
+def test_noalloc_rejects_null_arrays():
+    """The host cannot read offsets[n], so null adjacency or weights are refused before
+    any launch (a graph with edges would otherwise read through a null pointer)."""
+    import torch
+    dev = torch.device("cuda:0")
+    n = 8
+    off = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    adj = torch.zeros(4, dtype=torch.int32, device=dev)
+    w = torch.ones(4, dtype=torch.int64, device=dev)
+    labels = torch.zeros(n, dtype=torch.int32, device=dev)
+    changed = torch.zeros(1, dtype=torch.int32, device=dev)
+    before = vc.viecut_launch_count()
+    for a, b in ((None, w), (adj, None), (None, None)):
+        with pytest.raises(vc.ViecutError) as e:
+            vc.viecut_noi_round_noalloc(off, a, b, n, 1, labels, changed)
+        assert e.value.code == vc.VIECUT_EINVAL and "null" in str(e.value)
+    assert vc.viecut_launch_count() == before
