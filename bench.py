@@ -548,6 +548,8 @@ def main():
     lp_ms = 0.0
     lp_rounds = 0
     lp_bytes = 0
+    ct_ms = pm_ms = 0.0
+    ct_bytes = pm_bytes = ct_count = 0
     launches = 0
     phases = {"lp": 0.0, "contract": 0.0, "pr": 0.0, "noi": 0.0, "other": 0.0}
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -562,6 +564,11 @@ def main():
             lp_rounds += st["lp_launches"]
             lp_bytes += st["lp_bytes"]
             launches += st["kernel_launches"]
+            ct_ms += st["ms_contract_kernel"]
+            pm_ms += st["ms_premerge_kernel"]
+            ct_bytes += st["contract_bytes"]
+            pm_bytes += st["premerge_bytes"]
+            ct_count += st["contractions"]
             for k in phases:
                 phases[k] += st["ms_" + k]
         ev1.record(stream)
@@ -582,6 +589,13 @@ def main():
     lp_round_ms = lp_ms / max(1, lp_rounds)
     lp_round_bytes = lp_bytes / max(1, lp_rounds)
     achieved = lp_bytes / (lp_ms / 1000.0) / 1e9 if lp_ms > 0 else None
+    # the same rounds' DRAM bytes (ncu, when the kernels are unchanged since the capture):
+    # the label gather of later rounds is served by L2, so DRAM moves fewer bytes than
+    # the algorithmic count
+    achieved_dram = traffic / (lp_round_ms / 1000.0) / 1e9 if (traffic and lp_round_ms > 0) else None
+    # contraction (relabel, pre-merge, cluster merge) and its pre-merge kernel alone
+    ct_achieved = ct_bytes / (ct_ms / 1000.0) / 1e9 if ct_ms > 0 else None
+    pm_achieved = pm_bytes / (pm_ms / 1000.0) / 1e9 if pm_ms > 0 else None
 
     # ---------------- end to end through the C ABI with host buffers
     h_off = torch.from_numpy(g.offsets).pin_memory()
@@ -635,7 +649,19 @@ def main():
                      "traffic_source": "profiles/lp_round_traffic_rhg_n1048576.md (ncu DRAM bytes of a level-0 "
                                        "round at n=2^20, scaled by entries; null once lp.cu changed)",
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
-                     "round_ms": lp_round_ms, "algorithmic_bytes_per_round": lp_round_bytes},
+                     "round_ms": lp_round_ms, "algorithmic_bytes_per_round": lp_round_bytes,
+                     "achieved_dram": achieved_dram,
+                     "frac_dram": (achieved_dram / peak) if achieved_dram else None},
+        "roofline_contract": {
+            "kernel": "cluster contraction: relabel, pre-merge (emit_reg_k / emit_warp_k / emit_block_k), "
+                      "cluster merge (scatter, merge, place)",
+            "bound": "hbm", "achieved": ct_achieved, "peak": peak, "unit": "GB/s",
+            "frac": (ct_achieved / peak) if ct_achieved else None, "traffic": None,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+            "contractions_per_step": ct_count / args.steps, "ms_per_step": ct_ms / args.steps,
+            "algorithmic_bytes_per_step": ct_bytes / args.steps,
+            "premerge": {"achieved": pm_achieved, "frac": (pm_achieved / peak) if pm_achieved else None,
+                         "ms_per_step": pm_ms / args.steps, "algorithmic_bytes_per_step": pm_bytes / args.steps}},
         "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps, "api": "viecut_solve on one handle, pinned host arrays",

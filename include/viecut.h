@@ -94,6 +94,19 @@ typedef struct viecut_stats {
   int32_t first_group;   /* lanes per vertex of the first-round label-propagation kernel
                             (8, 16 or 32; picked once per handle by timing each choice) */
   int32_t emit_group;    /* lanes per vertex of the contraction's pre-merge kernel (same) */
+  double ms_contract_kernel; /* summed device time of the timed contractions (relabel,
+                                pre-merge, cluster merge; the host's read of the cluster
+                                and pair counts between them is not included) */
+  double ms_premerge_kernel; /* summed duration of the pre-merge launches alone */
+  int64_t contractions;      /* contractions timed in ms_contract_kernel */
+  int64_t contract_bytes;    /* their algorithmic bytes: fine CSR read once (offsets, ids,
+                                weights unless all are 1) + 4 per entry (cluster id of the
+                                neighbour) + 8 per fine vertex (label read, cluster id
+                                written) + coarse CSR written (offsets, int32 id + int64
+                                weight per entry) */
+  int64_t premerge_bytes;    /* the pre-merge's algorithmic bytes: 8(n+1) offsets + nnz (4 id
+                                + weight bytes + 4 cluster id) + 8n (own cluster id, pair
+                                count) + 12 per pre-merged pair written */
 } viecut_stats;
 
 /* One contraction step: kind 0 initial graph, 1 label-propagation contraction,

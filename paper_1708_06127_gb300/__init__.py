@@ -48,7 +48,10 @@ class viecut_stats(ctypes.Structure):
                 ("ms_lp_kernel", ctypes.c_double), ("lp_launches", ctypes.c_int64), ("lp_nnz", ctypes.c_int64),
                 ("lp_n", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("levels", ctypes.c_int64),
                 ("trace_len", ctypes.c_int64), ("lp_bytes", ctypes.c_int64),
-                ("first_group", ctypes.c_int32), ("emit_group", ctypes.c_int32)]
+                ("first_group", ctypes.c_int32), ("emit_group", ctypes.c_int32),
+                ("ms_contract_kernel", ctypes.c_double), ("ms_premerge_kernel", ctypes.c_double),
+                ("contractions", ctypes.c_int64), ("contract_bytes", ctypes.c_int64),
+                ("premerge_bytes", ctypes.c_int64)]
 
 
 class viecut_graph_desc(ctypes.Structure):

@@ -90,6 +90,10 @@ struct Workspace {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> spans;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> lp_spans;
   long long lp_bytes_acc = 0, lp_nnz_acc = 0, lp_n_acc = 0;
+  // contractions: device segments (the host reads the cluster and pair counts between
+  // two of them, which is not device work) and the pre-merge launches alone
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ct_spans, pm_spans;
+  long long ct_bytes_acc = 0, pm_bytes_acc = 0, ct_count = 0;
 
   Workspace() {
     VC_CUDA(cudaMallocHost(&h_state, sizeof(DevState)));
@@ -177,6 +181,9 @@ struct Workspace {
     spans.clear();
     lp_spans.clear();
     lp_bytes_acc = lp_nnz_acc = lp_n_acc = 0;
+    ct_spans.clear();
+    pm_spans.clear();
+    ct_bytes_acc = pm_bytes_acc = ct_count = 0;
   }
 
   // ---------------------------------------------------------------- launch shapes
@@ -297,10 +304,21 @@ struct Workspace {
     *out_labels = in;
   }
 
+  // Algorithmic bytes of one contraction of fine graph g into (cn vertices, cnnz
+  // entries): the fine CSR read once (offsets, ids, weights unless all are 1), the
+  // labels read and the cluster ids written (4 bytes per vertex each), the cluster id
+  // of every neighbour gathered (4 bytes per entry), and the coarse CSR written
+  // (offsets, int32 ids, int64 weights).
+  void count_contract(const GraphView& g, int64_t cn, int64_t cnnz) {
+    if (!timing) return;
+    ct_bytes_acc += 8 * (g.n + 1) + g.nnz * (4 + (g.unit ? 0 : g.wbytes) + 4) + 8 * g.n + 8 * (cn + 1) + 12 * cnnz;
+  }
+
   // Contracts g by labels into the coarse buffer `slot`; cid_out[n] receives the map.
   // Returns the coarse view; h_counters holds c and the pair count afterwards.
   GraphView contract(const GraphView& g, const int32_t* labels, int32_t* cid_out, int slot, bool correct = false) {
     if (!bins_valid) build_bins(g);
+    cudaEvent_t t0 = mark();
     ContractScratch cs;
     cs.flags = flags.as<int32_t>();
     cs.rank = rank.as<int32_t>();
@@ -337,16 +355,26 @@ struct Workspace {
     int32_t* ccount = cs.flags;
     VC_CUDA(cudaMemsetAsync(ccount, 0, sizeof(int32_t) * std::max<int64_t>(g.n, 1), s));
     po.ccount = ccount;
+    cudaEvent_t e0 = mark();
     emit_cross(g, bins, gt, cid_out, po, cs.cnt, s, tune);
+    if (timing) pm_spans.push_back({e0, mark()});
     VC_CUDA(cudaMemsetAsync(&ctr()->maxt, 0, sizeof(int), s));
     VC_CUDA(cudaMemsetAsync(&ctr()->pairs, 0, sizeof(long long), s));
     VC_CUDA(cudaMemsetAsync(&ctr()->ngiant, 0, sizeof(int), s));
     VC_CUDA(cudaMemsetAsync(&ctr()->gpairs, 0, sizeof(long long), s));
     cluster_stats(g.n, ccount, &ctr()->maxt, &ctr()->pairs, &ctr()->ngiant, &ctr()->gpairs, s);
+    if (timing) ct_spans.push_back({t0, mark()});
     VC_CUDA(cudaMemcpyAsync(h_counters, ctr(), sizeof(Counters), cudaMemcpyDeviceToHost, s));
     sync();
+    cudaEvent_t t1 = mark();
     const int64_t c = h_counters->c;
     const int64_t P = h_counters->pairs;
+    if (timing) {
+      // pre-merge: offsets, ids, weights (none when all are 1), the cluster id of every
+      // neighbour and of v, the pair count of v and the pairs (int32 key + int64 sum)
+      pm_bytes_acc += 8 * (g.n + 1) + g.nnz * (4 + (g.unit ? 0 : g.wbytes) + 4) + 4 * g.n + 4 * g.n + 12 * P;
+      ct_count += 1;
+    }
     int64_t* co = coff[slot].ensure_n<int64_t>(c + 1);
     int32_t* ca = cadj[slot].ensure_n<int32_t>(std::max<int64_t>(P, 1));
     long long* cwp = cw[slot].ensure_n<long long>(std::max<int64_t>(P, 1));
@@ -397,6 +425,7 @@ struct Workspace {
       radix_sort_pairs(kA, vA, kB, vB, P, 2 * bits, hs, s);
       reduce_pairs(kA, vA, P, bits, c, hd, hp, scan64.as<long long>(), co, ca, cwp, csp, &st()->nnz, s);
     }
+    if (timing) ct_spans.push_back({t1, mark()});
     GraphView h;
     h.n = c;
     h.nnz = P;  // upper bound until the state is read

@@ -204,6 +204,7 @@ static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, u
     cudaEvent_t a0 = W.mark();
     int32_t* cid = contracted ? W.cidT.as<int32_t>() : W.map0.as<int32_t>();
     int dst = slot == 0 ? 1 : 0;
+    const GraphView fine = G;
     GraphView h = W.contract(G, labels, cid, dst, kind == 1 && H.correct);
     set_n_k<<<1, 1, 0, s>>>(st, h.n);
     count_launch();
@@ -227,6 +228,7 @@ static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, u
     W.span(kPhOther, a1);
     W.read_state();
     G.nnz = W.h_state->nnz;
+    W.count_contract(fine, G.n, G.nnz);
     return G.n > 1 && W.h_state->lambda_hat > 0;
   };
 
@@ -341,6 +343,17 @@ static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, u
     S.lp_nnz = W.lp_nnz_acc;
     S.lp_n = W.lp_n_acc;
     S.lp_bytes = W.lp_bytes_acc;
+    for (auto& sp : W.ct_spans) {
+      VC_CUDA(cudaEventElapsedTime(&ms, sp.first, sp.second));
+      S.ms_contract_kernel += ms;
+    }
+    for (auto& sp : W.pm_spans) {
+      VC_CUDA(cudaEventElapsedTime(&ms, sp.first, sp.second));
+      S.ms_premerge_kernel += ms;
+    }
+    S.contractions = W.ct_count;
+    S.contract_bytes = W.ct_bytes_acc;
+    S.premerge_bytes = W.pm_bytes_acc;
   }
   S.first_group = W.tune.first_group;
   S.emit_group = W.tune.emit_group;
