@@ -140,6 +140,28 @@ def whole_job_rate(units_per_rank_step: float, steps: int, world: int, max_secon
     return units_per_rank_step * steps * world / max_seconds
 
 
+def host_cpu() -> dict:
+    """The host's CPU model (lscpu, else /proc/cpuinfo) and its logical core count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"cpu_model": model or "unknown", "host_cores": os.cpu_count()}
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -406,7 +428,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("2^22", "2^19") + " (bounded CPU sample)", "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "same_workload": False, **host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -674,7 +697,11 @@ def main():
         sg, sres, sdt = cpu_oracle_sample(1)
         line["cpu_baseline"] = {"value": sg.m / sdt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"whole method on rhg(n=2^19, avg_deg=64, gamma=5) -> 16-core -> lcc, "
-                                          f"m={sg.m}, {sdt:.1f} s, one host thread"}
+                                          f"m={sg.m}, {sdt:.1f} s, one host thread",
+                                "same_workload": False,
+                                "note": "cross-size: the oracle's edges/s on the n=2^19 member of the family, "
+                                        "one thread; the GPU value is at n=2^22",
+                                **host_cpu()}
     mc.close()
     if args.mode == "all" and rank == 0:
         line["batch"] = bench_batch(args.batch_count, 3, 1, stream, local)

@@ -187,10 +187,12 @@ int viecut_graph_free(viecut_graph* g);
 /* Weighted degrees c(v) (Sec. 3): deg[n]. */
 int viecut_step_degrees(viecut_graph* g, int64_t* deg);
 /* `rounds` synchronous label-propagation rounds (Sec. 4.1) from lab_in (NULL = the
- * identity labelling) with tie-break key `key`; writes every round: lab_out[rounds*n]. */
+ * identity labelling; otherwise labels in [0, n), else EINVAL) with tie-break key `key`;
+ * writes every round: lab_out[rounds*n]. */
 int viecut_step_lp(viecut_graph* g, const int32_t* lab_in, uint64_t key, int32_t rounds, int32_t* lab_out);
-/* Contraction by labels (Sec. 4.1, "contract it"): *out receives the coarse graph,
- * cid[n] the coarse id (rank of the label value) of every vertex. */
+/* Contraction by labels in [0, n) (Sec. 4.1, "contract it"; other labels: EINVAL): *out
+ * receives the coarse graph, cid[n] the coarse id (rank of the label value) of every
+ * vertex. */
 int viecut_step_contract(viecut_graph* g, const int32_t* labels, viecut_graph** out, int32_t* cid);
 /* Padberg-Rinaldi pass A (conditions 1, 2) / pass B (conditions 3, 4) with bound
  * lambda_hat: labels[n] = union-find representative (smallest id of each merged

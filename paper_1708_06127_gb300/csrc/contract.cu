@@ -391,16 +391,21 @@ __global__ void __launch_bounds__(256) cluster_merge_k(int64_t c, const long lon
 // pairs by target in shared memory (bitonic network over the next power of two,
 // padding keys INT_MAX), then every run head sums its run; the distinct targets are
 // written back in ascending order at the front of the segment.
+// With a list (list_count not null) only the listed clusters are visited.
 __global__ void __launch_bounds__(256) cluster_merge_block_k(int64_t c, const long long* __restrict__ cbase,
                                                              int32_t* __restrict__ seg_key,
                                                              long long* __restrict__ seg_val,
-                                                             int32_t* __restrict__ dcount) {
+                                                             int32_t* __restrict__ dcount,
+                                                             const int32_t* __restrict__ list = nullptr,
+                                                             const int* __restrict__ list_count = nullptr) {
   extern __shared__ __align__(16) unsigned char mb_dyn[];
   long long* sv = (long long*)mb_dyn;
   int32_t* sk = (int32_t*)(sv + kMergeBlockMax);
   __shared__ int s_warp[8];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int64_t x = blockIdx.x; x < c; x += gridDim.x) {
+  const int64_t total = list_count ? (int64_t)*list_count : c;
+  for (int64_t xi = blockIdx.x; xi < total; xi += gridDim.x) {
+    const int64_t x = list_count ? (int64_t)list[xi] : xi;
     const long long b = cbase[x];
     const int T = (int)(cbase[x + 1] - b);
     if (T <= kMergeMax || T > kMergeBlockMax) continue;  // the same in every thread of the block
@@ -686,10 +691,33 @@ void cluster_stats(int64_t n, const int32_t* ccount, int* maxt, long long* pairs
   VC_CHECK_LAUNCH();
 }
 
+// Opts cluster_merge_block_k into its shared-memory size, once per device.
+static int merge_block_smem() {
+  static std::mutex mu;
+  static std::unordered_map<int, bool> ready;  // per device: the shared-memory limit was raised
+  const int smem = kMergeBlockMax * (int)(sizeof(long long) + sizeof(int32_t));
+  int dev = 0;
+  VC_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (!ready[dev]) {
+    VC_CUDA(cudaFuncSetAttribute(cluster_merge_block_k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    ready[dev] = true;
+  }
+  return smem;
+}
+
+__global__ void block_class_list_k(int64_t c, const long long* __restrict__ cbase, int32_t* __restrict__ list,
+                                   int* __restrict__ count) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < c; x += (int64_t)gridDim.x * blockDim.x) {
+    const long long T = cbase[x + 1] - cbase[x];
+    if (T > kMergeMax && T <= kMergeBlockMax) list[atomicAdd(count, 1)] = (int32_t)x;
+  }
+}
+
 void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int32_t* ccount, int64_t c,
                    long long* cbase, long long* cursor, int32_t* seg_key, long long* seg_val, int64_t* coff,
                    int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, bool big, bool sort_first,
-                   const GiantScratch* giant, cudaStream_t s) {
+                   const GiantScratch* giant, int32_t* blist, int* blist_n, cudaStream_t s) {
   exclusive_scan<int, long long>(ccount, cbase, c, cbase + c, cs.scan_scr, s);
   VC_CUDA(cudaMemcpyAsync(cursor, cbase, sizeof(long long) * c, cudaMemcpyDeviceToDevice, s));
   const int gv = grid_for(g.n, 256, kSMs * 8), gc = grid_for(c, 8, kSMs * 16);
@@ -699,20 +727,13 @@ void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch
   count_launch(2);
   VC_CHECK_LAUNCH();
   if (big) {
-    static std::mutex mu;
-    static std::unordered_map<int, bool> ready;  // per device: the shared-memory limit was raised
-    const int smem = kMergeBlockMax * (int)(sizeof(long long) + sizeof(int32_t));
-    {
-      int dev = 0;
-      VC_CUDA(cudaGetDevice(&dev));
-      std::lock_guard<std::mutex> lk(mu);
-      if (!ready[dev]) {
-        VC_CUDA(cudaFuncSetAttribute(cluster_merge_block_k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        ready[dev] = true;
-      }
-    }
-    cluster_merge_block_k<<<grid_for(c, 1, kSMs * 2), 256, smem, s>>>(c, cbase, seg_key, seg_val, ccount);
-    count_launch();
+    // the clusters of kMergeMax < T <= kMergeBlockMax pairs listed first, so that the
+    // blocks visit only them (blist: n ints no longer needed once the scatter ran)
+    VC_CUDA(cudaMemsetAsync(blist_n, 0, sizeof(int), s));
+    block_class_list_k<<<grid_for(c, 256, kSMs * 8), 256, 0, s>>>(c, cbase, blist, blist_n);
+    const int smem = merge_block_smem();
+    cluster_merge_block_k<<<kSMs, 256, smem, s>>>(c, cbase, seg_key, seg_val, ccount, blist, blist_n);
+    count_launch(2);
     VC_CHECK_LAUNCH();
   }
   if (giant && giant->ngiant > 0) giant_merge(*giant, c, cbase, seg_key, seg_val, ccount, cs.scan_scr, s);
@@ -722,5 +743,6 @@ void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch
   VC_CHECK_LAUNCH();
   VC_CUDA(cudaMemcpyAsync(nnz_dev, coff + c, sizeof(long long), cudaMemcpyDeviceToDevice, s));
 }
+
 
 }  // namespace vc

@@ -57,6 +57,7 @@ struct Counters {
   int changed;
   int ngiant;         // clusters of more than kMergeBlockMax pairs
   long long gpairs;   // their pairs
+  int blist_n;        // clusters listed for the block-level merge
 };
 
 enum Phase { kPhLP = 0, kPhContract, kPhPR, kPhNOI, kPhOther, kPhCount };
@@ -408,7 +409,7 @@ struct Workspace {
         gs.hist = hist.ensure_n<long long>(radix_hist_elems(GP));
       }
       cluster_merge(g, cid_out, cs, ccount, c, cbase, cur, sk, sv, co, ca, cwp, csp, &st()->nnz,
-                    h_counters->maxt > kMergeMax, 2 * c >= g.n, ng ? &gs : nullptr, s);
+                    h_counters->maxt > kMergeMax, 2 * c >= g.n, ng ? &gs : nullptr, cs.cnt, &ctr()->blist_n, s);
     } else {
       exclusive_scan<int, long long>(cs.cnt, cs.pos, g.n, &ctr()->pairs, cs.scan_scr, s);
       int bits = ceil_log2(c);

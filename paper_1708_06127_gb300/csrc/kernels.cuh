@@ -191,7 +191,7 @@ void cluster_stats(int64_t n, const int32_t* ccount, int* maxt, long long* pairs
 void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int32_t* ccount, int64_t c,
                    long long* cbase, long long* cursor, int32_t* seg_key, long long* seg_val, int64_t* coff,
                    int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, bool big, bool sort_first,
-                   const GiantScratch* giant, cudaStream_t s);
+                   const GiantScratch* giant, int32_t* blist, int* blist_n, cudaStream_t s);
 
 // Builds (cid[v] << bits | cu, weight) pairs from the pre-merged lists.
 void build_pairs(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int bits, int64_t pairs,

@@ -412,11 +412,15 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
   constexpr int kPer = 32 / G;  // vertices per warp
   const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock * kPer;
   const int64_t first = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kPer;
+  // pre(v): v's own label from the previous round (INT_MIN: v is not active)
   reg_pipeline<WT, G, S>(list, *count_ptr, first, stride, glane, gi, off, adj, w,
-                      [&](int64_t v) { return vact ? (int32_t)vact[v] : 1; },
-                      [&](int64_t v, bool valid, int64_t beg, int64_t end, int32_t active, const RegIds<S>& ids) {
+                      [&](int64_t v) -> int32_t {
+                        if (vact && !vact[v]) return INT_MIN;
+                        return FIRST ? 0 : __ldg(lab + v);
+                      },
+                      [&](int64_t v, bool valid, int64_t beg, int64_t end, int32_t own, const RegIds<S>& ids) {
     const int64_t d = end - beg;
-    const bool mine = valid && active;
+    const bool mine = valid && own != INT_MIN;
     if (mine && d == 0) {
       if (glane == 0) lab_out[v] = FIRST ? (int32_t)v : __ldg(lab + v);
     }
@@ -443,6 +447,34 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
     int32_t bl = -1;
     unsigned long long bh = 0;
     bool hashed = false;
+    if (!FIRST) {
+      // the vertex's own label first: after one round most vertices see it on more than
+      // half of their weight, and then no other label can reach it (the walk is skipped);
+      // otherwise it seeds the best, and the walk visits only the other labels
+      unsigned hit = 0;
+#pragma unroll
+      for (int r = 0; r < S; ++r)
+        if (((L.todo >> r) & 1u) && L.k[r] == own) hit |= 1u << r;
+      ACC t;
+      if (std::is_same<WT, UnitW>::value) {
+        t = (ACC)__reduce_add_sync(gmask, (unsigned)__popc(hit));
+      } else {
+        long long sum = 0;
+#pragma unroll
+        for (int r = 0; r < S; ++r)
+          if ((hit >> r) & 1u) sum += L.wt[r];
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        t = (ACC)sum;
+      }
+      L.todo &= ~hit;
+      if (t > 0) {
+        left -= t;
+        bs = t;
+        bl = own;
+        if (bs > left) L.todo = 0;
+      }
+    }
     reg_visit<WT, ACC, G, S>(L, gmask, [&](int32_t kk, ACC t) {
       left -= t;
       if (bl < 0 || t > bs) {

@@ -777,9 +777,18 @@ int viecut_step_degrees(viecut_graph* g, int64_t* deg) {
   VC_API_END
 }
 
+// Labels are vertex ids of the graph: [0, n).
+static void check_labels(const int32_t* lab, int64_t n) {
+  for (int64_t v = 0; v < n; ++v)
+    if (lab[v] < 0 || lab[v] >= n)
+      throw Error{VIECUT_EINVAL, "label " + std::to_string(lab[v]) + " of vertex " + std::to_string(v) +
+                                     " is outside [0, n)"};
+}
+
 int viecut_step_lp(viecut_graph* g, const int32_t* lab_in, uint64_t key, int32_t rounds, int32_t* lab_out) {
   VC_API_BEGIN
   if (!g || !lab_out || rounds < 1) throw Error{VIECUT_EINVAL, "bad argument"};
+  if (lab_in) check_labels(lab_in, g->g.n);
   StepCtx c(g->g);
   vc::GraphView v = g->g.view();
   c.ws->build_bins(v);
@@ -808,6 +817,7 @@ int viecut_step_contract(viecut_graph* g, const int32_t* labels, viecut_graph** 
   VC_API_BEGIN
   if (!g || !labels || !out) throw Error{VIECUT_EINVAL, "null argument"};
   *out = nullptr;
+  check_labels(labels, g->g.n);
   StepCtx c(g->g);
   vc::GraphView v = g->g.view();
   int32_t* lab = c.ws->labA.as<int32_t>();

@@ -230,6 +230,21 @@ def test_global_table_class_parity(unit, parallel):
     assert_same(g, seed=2, lp=2, n0=16)
 
 
+def test_step_entry_points_refuse_labels_outside_the_vertex_range():
+    G = oracle.as_csr64(*(lambda g: (g.offsets, g.adj, g.w))(H.cycle(10)))
+    d = upload(G)
+    try:
+        for bad in (np.full(G.n, G.n, np.int32), np.full(G.n, -1, np.int32)):
+            with pytest.raises(vc.ViecutError) as e:
+                vc.viecut_step_contract(d, bad)
+            assert e.value.code == vc.VIECUT_EINVAL and "outside" in str(e.value)
+            with pytest.raises(vc.ViecutError) as e:
+                vc.viecut_step_lp(d, bad, 1, 1)
+            assert e.value.code == vc.VIECUT_EINVAL
+    finally:
+        vc.viecut_graph_free(d)
+
+
 def coarse_graphs():
     out = []
     for seed in range(4):
