@@ -1,7 +1,12 @@
 """Full-size workloads, in the launch configuration the benchmark times (inputs
 resident on the device, default options), compared with the oracle in full: cut
-value, side bitmap and the per-step trace.  The planted graph is also checked
+value, side bitmap and the per-step trace (for the planted graph with the oracle's
+stored result, which takes it half an hour).  The planted graph is also checked
 against the cut value known from its construction."""
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -58,12 +63,37 @@ def test_planted_8x2_16_exact():
     assert ref.cut >= planted_lambda(g, 8, 1 << 16)
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "planted_8x2p20.json")
+
+
+def test_planted_8x2_20_golden():
+    """8 ER blocks of 2^20 vertices (average degree 48), 64 bridges, weights [1, 100],
+    against the CPU oracle's result stored by tests/golden/make_planted.py (the oracle
+    needs about half an hour at this size): the same graph (SHA-256 of the generated
+    CSR), then every step of the contraction trace, the cut value, and the side bitmap
+    (SHA-256 and popcount)."""
+    ref = json.load(open(GOLDEN))
+    p = ref["params"]
+    g = gg.planted(p["blocks"], p["block_n"], p["avg_deg"], p["bridges"], p["graph_seed"], p["wlo"], p["whi"])
+    h = hashlib.sha256()
+    for a in (g.offsets, g.adj, g.w):
+        h.update(np.ascontiguousarray(a).tobytes())
+    assert h.hexdigest() == ref["graph_sha256"], "the generator drew another graph on this host"
+    cut, bits, trace = bench_config_run(g, seed=p["seed"], lp=p["lp_iters"])
+    want = [tuple(s) for s in ref["trace"]]
+    for k, (a, b) in enumerate(zip(trace, want)):
+        assert a == b, (k, a, b)
+    assert len(trace) == len(want)
+    assert cut == ref["cut"]
+    assert hashlib.sha256(np.ascontiguousarray(bits, dtype=np.uint64).tobytes()).hexdigest() == ref["side_sha256"]
+    side = np.unpackbits(bits.view(np.uint8), bitorder="little")[: g.n]
+    assert int(side.sum()) == ref["side_popcount"]
+
+
 def test_planted_8x2_20_properties():
-    """8 ER blocks of 2^20 vertices (average degree 48), 64 bridges, weights [1, 100].
-    At this size the oracle needs tens of minutes (label propagation on ER blocks
-    only halves the graph per level), so the GPU result is checked by properties that
-    hold at any size: the value is at least the construction's cut value and equals
-    the weight of the returned side, which is a proper subset without vertex 0."""
+    """The same workload checked by properties that hold at any size: the value is at
+    least the construction's cut value and equals the weight of the returned side,
+    which is a proper subset without vertex 0."""
     g = gg.workload_planted(1)
     cut, bits, trace = bench_config_run(g, seed=1)
     side = np.unpackbits(bits.view(np.uint8), bitorder="little")[: g.n].astype(bool)

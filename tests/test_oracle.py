@@ -528,3 +528,26 @@ def test_bound_tie_pin_catches_a_non_strict_update(tmp_path):
             res = oracle.viecut(g.offsets, g.adj, g.w, seed=3, lp_iters=lp, n0=n0, _lib=lib)
             caught += not _tie_rule_holds(g, res)
     assert caught >= 3  # the label-propagation runs meet a tie on another side
+
+
+def test_planted_golden_file_is_consistent():
+    """The stored oracle result on the full-size planted workload
+    (tests/golden/planted_8x2p20.json, written by tests/golden/make_planted.py from the
+    oracle alone) starts from the generated graph -- the same CSR hash, n, entries and
+    minimum weighted degree -- keeps lambda-hat non-increasing, ends at its cut value,
+    and that value is at least the construction's cut."""
+    import hashlib
+    import json
+    ref = json.load(open(os.path.join(GOLDEN, "planted_8x2p20.json")))
+    p = ref["params"]
+    g = gg.planted(p["blocks"], p["block_n"], p["avg_deg"], p["bridges"], p["graph_seed"], p["wlo"], p["whi"])
+    h = hashlib.sha256()
+    for a in (g.offsets, g.adj, g.w):
+        h.update(np.ascontiguousarray(a).tobytes())
+    assert h.hexdigest() == ref["graph_sha256"]
+    deg = np.add.reduceat(g.w.astype(np.int64), g.offsets[:-1])
+    assert ref["trace"][0] == [0, 0, g.n, g.nnz, int(deg.min())]
+    lh = [s[4] for s in ref["trace"]]
+    assert all(a >= b for a, b in zip(lh, lh[1:])) and lh[-1] == ref["cut"]
+    assert ref["cut"] >= planted_lambda(g, p["blocks"], p["block_n"])
+    assert 0 < ref["side_popcount"] < g.n
