@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <unordered_map>
 
 #include "kernels.cuh"
@@ -473,15 +474,19 @@ __global__ void __launch_bounds__(256) cluster_merge_block_k(int64_t c, const lo
 
 // The sorted distinct targets of every cluster, copied from the front of its segment
 // to coff[c] (a warp per cluster).
+// Clusters with skip[x] != 0 (skip may be null) are left out (their lists are written
+// by the sparse contraction's copy).
 __global__ void __launch_bounds__(256) cluster_place_k(int64_t c, const long long* __restrict__ cbase,
                                                        const int64_t* __restrict__ coff,
                                                        const int32_t* __restrict__ seg_key,
                                                        const long long* __restrict__ seg_val,
                                                        int32_t* __restrict__ cadj, long long* __restrict__ cw,
-                                                       int32_t* __restrict__ csrc) {
+                                                       int32_t* __restrict__ csrc,
+                                                       const unsigned char* __restrict__ skip) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < c; x += warps) {
+    if (skip && skip[x]) continue;
     const long long b = cbase[x];
     const int64_t o = coff[x];
     const int D = (int)(coff[x + 1] - o);
@@ -491,6 +496,247 @@ __global__ void __launch_bounds__(256) cluster_place_k(int64_t c, const long lon
       csrc[o + i] = (int32_t)x;
     }
   }
+}
+
+
+// ---------------------------------------------------------------- sparse contraction
+// Contractions by union-find roots (Padberg-Rinaldi passes, exact-step rounds) on a graph
+// with strictly increasing lists.  A vertex alone in its group is its own root, so its
+// cluster id is the rank of its own id among the roots; neighbours alone in their groups
+// keep their order and stay distinct under that renumbering.  So the coarse list of a
+// lone vertex is its fine list renumbered, except for the few entries that point into
+// merged groups (two or more members): those may repeat a target and sit out of order.
+// A warp per lone vertex sums them per target in shared memory and merges the distinct
+// ones into the renumbered list by rank -- one pass to count the coarse degree, one to
+// write.  Only the members of merged groups (and lone vertices with more than
+// kScMaxM such entries or more than kScRows x 32 entries) go through the pre-merge and
+// the cluster merge.
+constexpr int kScRows = 8;   // lists of at most 256 entries
+constexpr int kScMaxM = 32;  // entries into merged groups per lone vertex
+
+// mflag[cid[v]] = 1 for every v that is not its own root (its group has two or more
+// members); a plain store of 1 from any number of threads.
+__global__ void sc_merged_k(int64_t n, const int32_t* __restrict__ lab, const int32_t* __restrict__ cid,
+                            unsigned char* __restrict__ mflag) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    if (lab[v] != (int32_t)v) mflag[cid[v]] = 1;
+}
+
+// The entries of lone vertex v that point into merged groups, collected in the warp's
+// shared arrays mk / mw (at most kScMaxM; *nm their number, > kScMaxM: too many), and
+// the list kept in registers: k[r] the neighbour's cluster id, wt[r] the weight, inM[r]
+// whether it points into a merged group (row r = entries 32 r .. 32 r + 31).
+template <typename WT>
+__device__ __forceinline__ void sc_load_list(int64_t beg, int64_t end, int lane, const int32_t* __restrict__ adj,
+                                             const WT* __restrict__ w, const int32_t* __restrict__ cid,
+                                             const unsigned char* __restrict__ mflag, bool with_w,
+                                             int32_t (&k)[kScRows], long long (&wt)[kScRows], unsigned& inM,
+                                             int32_t* mk, long long* mw, int* nm_out) {
+  int nm = 0;
+  inM = 0;
+#pragma unroll
+  for (int r = 0; r < kScRows; ++r) {
+    const int64_t e = beg + 32 * r + lane;
+    const bool valid = e < end;
+    k[r] = valid ? __ldg(cid + __ldg(adj + e)) : -1;
+    wt[r] = (valid && with_w) ? ldw(w, e) : 0;
+  }
+#pragma unroll
+  for (int r = 0; r < kScRows; ++r) {
+    const bool m = k[r] >= 0 && mflag[k[r]];
+    const unsigned bal = __ballot_sync(0xffffffffu, m);
+    if (m) {
+      inM |= 1u << r;
+      const int at = nm + __popc(bal & ((1u << lane) - 1u));
+      if (at < kScMaxM) {
+        mk[at] = k[r];
+        mw[at] = wt[r];
+      }
+    }
+    nm += __popc(bal);
+  }
+  *nm_out = nm;
+  __syncwarp();
+}
+
+// Pass 1: the coarse degree of every lone vertex handled here (sdeg[v], else -1), and the
+// vertices left to the pre-merge flagged in dirty.
+template <typename WT>
+__global__ void __launch_bounds__(256) sc_count_k(int64_t n, const int32_t* __restrict__ cid,
+                                                  const unsigned char* __restrict__ mflag,
+                                                  const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                                                  const WT* __restrict__ w, int32_t* __restrict__ sdeg,
+                                                  unsigned char* __restrict__ dirty) {
+  __shared__ int32_t s_mk[8][kScMaxM];
+  __shared__ long long s_mw[8][kScMaxM];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int64_t beg = off[v], end = off[v + 1];
+    if (mflag[cid[v]] || end - beg > 32 * kScRows) {
+      if (lane == 0) { sdeg[v] = -1; dirty[v] = 1; }
+      continue;
+    }
+    int32_t k[kScRows];
+    long long wt[kScRows];
+    unsigned inM;
+    int nm;
+    sc_load_list<WT>(beg, end, lane, adj, w, cid, mflag, false, k, wt, inM, s_mk[wid], s_mw[wid], &nm);
+    if (nm > kScMaxM) {
+      if (lane == 0) { sdeg[v] = -1; dirty[v] = 1; }
+      continue;
+    }
+    const bool have = lane < nm;
+    const int32_t key = have ? s_mk[wid][lane] : -1 - lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int nd = __popc(__ballot_sync(0xffffffffu, have && (__ffs(peers) - 1) == lane));
+    if (lane == 0) { sdeg[v] = (int32_t)(end - beg - nm + nd); dirty[v] = 0; }
+    __syncwarp();
+  }
+}
+
+// Pass 2: the lists of the lone vertices counted in pass 1, at their coarse offsets.
+template <typename WT>
+__global__ void __launch_bounds__(256) sc_write_k(int64_t n, const int32_t* __restrict__ cid,
+                                                  const unsigned char* __restrict__ mflag,
+                                                  const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                                                  const WT* __restrict__ w, const int32_t* __restrict__ sdeg,
+                                                  const int64_t* __restrict__ coff, int32_t* __restrict__ cadj,
+                                                  long long* __restrict__ cw, int32_t* __restrict__ csrc) {
+  __shared__ int32_t s_mk[8][kScMaxM];
+  __shared__ long long s_mw[8][kScMaxM];
+  __shared__ int32_t s_dk[8][kScMaxM];
+  __shared__ long long s_dw[8][kScMaxM];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned lower = (1u << lane) - 1u;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    if (sdeg[v] < 0) continue;  // the same in every lane
+    const int64_t beg = off[v], end = off[v + 1];
+    const int32_t x = cid[v];
+    const int64_t o = coff[x];
+    int32_t k[kScRows];
+    long long wt[kScRows];
+    unsigned inM;
+    int nm;
+    sc_load_list<WT>(beg, end, lane, adj, w, cid, mflag, true, k, wt, inM, s_mk[wid], s_mw[wid], &nm);
+    // distinct targets into merged groups: the lowest lane of each target sums it and
+    // places it by its rank among the distinct targets
+    const bool have = lane < nm;
+    const int32_t key = have ? s_mk[wid][lane] : -1 - lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const bool first = have && (__ffs(peers) - 1) == lane;
+    const unsigned firsts = __ballot_sync(0xffffffffu, first);
+    const int nd = __popc(firsts);
+    if (first) {
+      long long sum = 0;
+      for (unsigned m = peers; m; m &= m - 1u) sum += s_mw[wid][__ffs(m) - 1];
+      int rank = 0;
+      for (unsigned m = firsts; m; m &= m - 1u) rank += s_mk[wid][__ffs(m) - 1] < key;
+      s_dk[wid][rank] = key;
+      s_dw[wid][rank] = sum;
+    }
+    __syncwarp();
+    // the entries into lone vertices' clusters: position among them, plus the distinct
+    // merged targets below them
+    int mbefore = 0;
+#pragma unroll
+    for (int r = 0; r < kScRows; ++r) {
+      const unsigned balM = __ballot_sync(0xffffffffu, (inM >> r) & 1u);
+      if (k[r] >= 0 && !((inM >> r) & 1u)) {
+        int below = 0;
+        for (int j = 0; j < nd; ++j) below += s_dk[wid][j] < k[r];
+        const int64_t pos = (32 * r + lane) - (mbefore + __popc(balM & lower)) + below;
+        cadj[o + pos] = k[r];
+        cw[o + pos] = wt[r];
+        csrc[o + pos] = x;
+      }
+      mbefore += __popc(balM);
+    }
+    // each distinct merged target: its rank plus the entries into lone clusters below it
+    for (int j = 0; j < nd; ++j) {
+      const int32_t dk = s_dk[wid][j];
+      int below = 0;
+#pragma unroll
+      for (int r = 0; r < kScRows; ++r)
+        below += __popc(__ballot_sync(0xffffffffu, k[r] >= 0 && !((inM >> r) & 1u) && k[r] < dk));
+      if (lane == 0) {
+        cadj[o + j + below] = dk;
+        cw[o + j + below] = s_dw[wid][j];
+        csrc[o + j + below] = x;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// The vertices left to the pre-merge, listed (in no particular order); *count their number.
+__global__ void sc_list_k(int64_t n, const unsigned char* __restrict__ dirty, int32_t* __restrict__ list,
+                          int* __restrict__ count) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; b < n;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = b + lane;
+    const bool d = v < n && dirty[v];
+    const unsigned bal = __ballot_sync(0xffffffffu, d);
+    int at = 0;
+    if (lane == 0 && bal) at = atomicAdd(count, __popc(bal));
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (d) list[at + __popc(bal & ((1u << lane) - 1u))] = (int32_t)v;
+  }
+}
+
+// After the merge of the pre-merged clusters: the coarse degree of every cluster of a
+// lone vertex handled here, and clean[x] marking those clusters.
+__global__ void sc_clean_deg_k(int64_t n, const int32_t* __restrict__ sdeg, const int32_t* __restrict__ cid,
+                               int32_t* __restrict__ ccount, unsigned char* __restrict__ clean) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (sdeg[v] < 0) continue;
+    const int32_t x = cid[v];
+    ccount[x] = sdeg[v];
+    clean[x] = 1;
+  }
+}
+
+template <typename F>
+static void sc_by_weight(const GraphView& g, F f) {
+  if (g.unit) f((const UnitW*)nullptr);
+  else if (g.wbytes == 4) f((const int32_t*)g.w);
+  else f((const long long*)g.w);
+}
+
+void sparse_mark(const GraphView& g, const int32_t* lab, const int32_t* cid, unsigned char* mflag,
+                 unsigned char* dirty, int32_t* sdeg, int32_t* list, int* count, cudaStream_t s) {
+  VC_CUDA(cudaMemsetAsync(mflag, 0, (size_t)g.n, s));
+  VC_CUDA(cudaMemsetAsync(count, 0, sizeof(int), s));
+  const int grid = grid_for(g.n, 256, kSMs * 8);
+  sc_merged_k<<<grid, 256, 0, s>>>(g.n, lab, cid, mflag);
+  sc_by_weight(g, [&](auto wp) {
+    using WT = std::remove_cv_t<std::remove_pointer_t<decltype(wp)>>;
+    sc_count_k<WT><<<grid_for(g.n, 8, kSMs * 16), 256, 0, s>>>(g.n, cid, mflag, g.off, g.adj, wp, sdeg, dirty);
+  });
+  sc_list_k<<<grid, 256, 0, s>>>(g.n, dirty, list, count);
+  count_launch(3);
+  VC_CHECK_LAUNCH();
+}
+
+static void sparse_finish_degrees(const GraphView& g, const int32_t* cid, const int32_t* sdeg, int32_t* ccount,
+                                  unsigned char* clean, int64_t c, cudaStream_t s) {
+  VC_CUDA(cudaMemsetAsync(clean, 0, (size_t)std::max<int64_t>(c, 1), s));
+  sc_clean_deg_k<<<grid_for(g.n, 256, kSMs * 8), 256, 0, s>>>(g.n, sdeg, cid, ccount, clean);
+  count_launch();
+  VC_CHECK_LAUNCH();
+}
+
+static void sparse_copy(const GraphView& g, const int32_t* cid, const unsigned char* mflag, const int32_t* sdeg,
+                        const int64_t* coff, int32_t* cadj, long long* cw, int32_t* csrc, cudaStream_t s) {
+  sc_by_weight(g, [&](auto wp) {
+    using WT = std::remove_cv_t<std::remove_pointer_t<decltype(wp)>>;
+    sc_write_k<WT><<<grid_for(g.n, 8, kSMs * 16), 256, 0, s>>>(g.n, cid, mflag, g.off, g.adj, wp, sdeg, coff, cadj,
+                                                               cw, csrc);
+  });
+  count_launch();
+  VC_CHECK_LAUNCH();
 }
 
 // ---------------------------------------------------------------- correcting step
@@ -717,7 +963,7 @@ __global__ void block_class_list_k(int64_t c, const long long* __restrict__ cbas
 void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int32_t* ccount, int64_t c,
                    long long* cbase, long long* cursor, int32_t* seg_key, long long* seg_val, int64_t* coff,
                    int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, bool big, bool sort_first,
-                   const GiantScratch* giant, int32_t* blist, int* blist_n, cudaStream_t s) {
+                   const GiantScratch* giant, int32_t* blist, int* blist_n, cudaStream_t s, const SparseCtx* sp) {
   exclusive_scan<int, long long>(ccount, cbase, c, cbase + c, cs.scan_scr, s);
   VC_CUDA(cudaMemcpyAsync(cursor, cbase, sizeof(long long) * c, cudaMemcpyDeviceToDevice, s));
   const int gv = grid_for(g.n, 256, kSMs * 8), gc = grid_for(c, 8, kSMs * 16);
@@ -737,10 +983,12 @@ void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch
     VC_CHECK_LAUNCH();
   }
   if (giant && giant->ngiant > 0) giant_merge(*giant, c, cbase, seg_key, seg_val, ccount, cs.scan_scr, s);
+  if (sp) sparse_finish_degrees(g, cid, sp->sdeg, ccount, sp->clean, c, s);
   exclusive_scan<int, long long>(ccount, (long long*)coff, c, (long long*)coff + c, cs.scan_scr, s);
-  cluster_place_k<<<gc, 256, 0, s>>>(c, cbase, coff, seg_key, seg_val, cadj, cw, csrc);
+  cluster_place_k<<<gc, 256, 0, s>>>(c, cbase, coff, seg_key, seg_val, cadj, cw, csrc, sp ? sp->clean : nullptr);
   count_launch();
   VC_CHECK_LAUNCH();
+  if (sp) sparse_copy(g, cid, sp->mflag, sp->sdeg, coff, cadj, cw, csrc, s);
   VC_CUDA(cudaMemcpyAsync(nnz_dev, coff + c, sizeof(long long), cudaMemcpyDeviceToDevice, s));
 }
 

@@ -251,6 +251,31 @@ struct Workspace {
   Bins bins;
   bool bins_valid = false;
 
+  // Reads the class counts of bins b (and counts[6] into *extra when given) and sizes
+  // the global-class tables for its longest list.
+  void read_bins(Bins& b, int* extra = nullptr) {
+    int hc[7];
+    VC_CUDA(cudaMemcpyAsync(hc, b.counts, (extra ? 7 : 6) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    sync();
+    b.h_mid = hc[0];
+    b.h_block = hc[1];
+    b.h_global = hc[2];
+    b.h_maxdeg = hc[3];
+    b.h_small = hc[4];
+    b.h_reg = hc[5];
+    if (extra) *extra = hc[6];
+    if (b.h_global > 0) {
+      int64_t cap = global_table_cap(b.h_maxdeg);
+      int blocks = std::min(b.h_global, kSMs);
+      // keep the scratch under ~2 GiB
+      while (blocks > 1 && (int64_t)blocks * cap * 12 > (int64_t(2) << 30)) blocks /= 2;
+      gt.keys = gkeys.ensure_n<int32_t>(blocks * cap);
+      gt.vals = gvals.ensure_n<long long>(blocks * cap);
+      gt.cap = cap;
+      gt.blocks = blocks;
+    }
+  }
+
   void build_bins(const GraphView& g) {
     bins.small_list = slist.as<int32_t>();
     bins.reg_list = rlist.as<int32_t>();
@@ -260,26 +285,33 @@ struct Workspace {
     bins.bail_list = bl1.as<int32_t>();
     bins.counts = bcounts.as<int>();
     bins_build(g, bins, s);
-    int hc[6];
-    VC_CUDA(cudaMemcpyAsync(hc, bins.counts, 6 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    sync();
-    bins.h_mid = hc[0];
-    bins.h_block = hc[1];
-    bins.h_global = hc[2];
-    bins.h_maxdeg = hc[3];
-    bins.h_small = hc[4];
-    bins.h_reg = hc[5];
-    if (bins.h_global > 0) {
-      int64_t cap = global_table_cap(bins.h_maxdeg);
-      int blocks = std::min(bins.h_global, kSMs);
-      // keep the scratch under ~2 GiB
-      while (blocks > 1 && (int64_t)blocks * cap * 12 > (int64_t(2) << 30)) blocks /= 2;
-      gt.keys = gkeys.ensure_n<int32_t>(blocks * cap);
-      gt.vals = gvals.ensure_n<long long>(blocks * cap);
-      gt.cap = cap;
-      gt.blocks = blocks;
-    }
+    read_bins(bins);
     bins_valid = true;
+  }
+
+  // Sparse contraction by union-find roots: counts the coarse lists of the lone vertices
+  // it handles and bins the others (members of merged groups, lone vertices with too
+  // many entries into them).  True when those are at most half of g's vertices; then
+  // dbins holds their bins.
+  Bins dbins;
+  Buf smflag, sdirty, sdeg, sclean, sdlist, dsl, drl, dml, dbl, dgl, dbail, dcounts;
+  bool mark_sparse(const GraphView& g, const int32_t* labels, const int32_t* cid) {
+    const int64_t n = g.n;
+    dbins.small_list = dsl.ensure_n<int32_t>(n);
+    dbins.reg_list = drl.ensure_n<int32_t>(n);
+    dbins.mid_list = dml.ensure_n<int32_t>(n);
+    dbins.block_list = dbl.ensure_n<int32_t>(n);
+    dbins.global_list = dgl.ensure_n<int32_t>(n);
+    dbins.bail_list = dbail.ensure_n<int32_t>(n);
+    dbins.counts = dcounts.ensure_n<int>(8);
+    int32_t* list = sdlist.ensure_n<int32_t>(n);
+    sparse_mark(g, labels, cid, smflag.ensure_n<unsigned char>(n), sdirty.ensure_n<unsigned char>(n),
+                sdeg.ensure_n<int32_t>(n), list, dbins.counts + 6, s);
+    bins_build(g, dbins, s, list, dbins.counts + 6);
+    int ndirty = 0;
+    read_bins(dbins, &ndirty);
+    sclean.ensure_n<unsigned char>(n);
+    return 2 * (int64_t)ndirty <= n;
   }
 
   void lp_rounds(const GraphView& g, uint64_t key, int rounds, int32_t** out_labels, int32_t* all_out) {
@@ -317,8 +349,11 @@ struct Workspace {
 
   // Contracts g by labels into the coarse buffer `slot`; cid_out[n] receives the map.
   // Returns the coarse view; h_counters holds c and the pair count afterwards.
-  GraphView contract(const GraphView& g, const int32_t* labels, int32_t* cid_out, int slot, bool correct = false) {
-    if (!bins_valid) build_bins(g);
+  // uf_roots: the labels are union-find roots (a vertex alone in its group is its own
+  // root); on a graph of strictly increasing lists the sparse contraction then handles
+  // the vertices a contraction leaves alone by a renumbering copy.
+  GraphView contract(const GraphView& g, const int32_t* labels, int32_t* cid_out, int slot, bool correct = false,
+                     bool uf_roots = false) {
     cudaEvent_t t0 = mark();
     ContractScratch cs;
     cs.flags = flags.as<int32_t>();
@@ -348,17 +383,21 @@ struct Workspace {
       cr.vin = cl + 3 * g.n;
       correct_clusters(g, cid_out, &ctr()->c, cr, s);
     }
+    const bool sparse = uf_roots && !correct && g.simple && g.n > 0 && mark_sparse(g, labels, cid_out);
+    if (!sparse && !bins_valid) build_bins(g);
+    const Bins& B = sparse ? dbins : bins;
     PairOut po{cs.tmp_key, cs.tmp_val, cs.cmp_key, cs.cmp_val};
     po.nclust = &ctr()->c;
     po.nfine = g.n;
-    tune_emit(g, cid_out, po, cs.cnt);  // trials: no counting
+    if (!sparse) tune_emit(g, cid_out, po, cs.cnt);  // trials: no counting
     // the pre-merge also counts pairs per cluster (flags is free again after the relabel)
     int32_t* ccount = cs.flags;
     VC_CUDA(cudaMemsetAsync(ccount, 0, sizeof(int32_t) * std::max<int64_t>(g.n, 1), s));
+    if (sparse) VC_CUDA(cudaMemsetAsync(cs.cnt, 0, sizeof(int32_t) * g.n, s));  // clean vertices: no pairs
     po.ccount = ccount;
     cudaEvent_t e0 = mark();
-    emit_cross(g, bins, gt, cid_out, po, cs.cnt, s, tune);
-    if (timing) pm_spans.push_back({e0, mark()});
+    emit_cross(g, B, gt, cid_out, po, cs.cnt, s, tune);
+    if (timing && !sparse) pm_spans.push_back({e0, mark()});  // the whole graph's pre-merge only
     VC_CUDA(cudaMemsetAsync(&ctr()->maxt, 0, sizeof(int), s));
     VC_CUDA(cudaMemsetAsync(&ctr()->pairs, 0, sizeof(long long), s));
     VC_CUDA(cudaMemsetAsync(&ctr()->ngiant, 0, sizeof(int), s));
@@ -373,18 +412,21 @@ struct Workspace {
     if (timing) {
       // pre-merge: offsets, ids, weights (none when all are 1), the cluster id of every
       // neighbour and of v, the pair count of v and the pairs (int32 key + int64 sum)
-      pm_bytes_acc += 8 * (g.n + 1) + g.nnz * (4 + (g.unit ? 0 : g.wbytes) + 4) + 4 * g.n + 4 * g.n + 12 * P;
+      if (!sparse) pm_bytes_acc += 8 * (g.n + 1) + g.nnz * (4 + (g.unit ? 0 : g.wbytes) + 4) + 4 * g.n + 4 * g.n + 12 * P;
       ct_count += 1;
     }
+    // coarse entries: at most the pairs, plus (sparse) the clean vertices' copied lists;
+    // never more than the fine entries
+    const int64_t E = sparse ? std::max<int64_t>(P, g.nnz) : P;
     int64_t* co = coff[slot].ensure_n<int64_t>(c + 1);
-    int32_t* ca = cadj[slot].ensure_n<int32_t>(std::max<int64_t>(P, 1));
-    long long* cwp = cw[slot].ensure_n<long long>(std::max<int64_t>(P, 1));
-    int32_t* csp = csrc[slot].ensure_n<int32_t>(std::max<int64_t>(P, 1));
+    int32_t* ca = cadj[slot].ensure_n<int32_t>(std::max<int64_t>(E, 1));
+    long long* cwp = cw[slot].ensure_n<long long>(std::max<int64_t>(E, 1));
+    int32_t* csp = csrc[slot].ensure_n<int32_t>(std::max<int64_t>(E, 1));
     // the cluster merge, with the few giant clusters radix-sorted together, unless
     // those hold most of the pairs (then one radix sort of all pairs)
     const int ng = h_counters->maxt > kMergeBlockMax ? h_counters->ngiant : 0;
     const int64_t GP = ng ? h_counters->gpairs : 0;
-    if (2 * GP <= P) {
+    if (2 * GP <= P || sparse) {
       long long* cbase = pos.as<long long>();  // n + 1 >= c + 1 entries
       long long* cur = ccur.ensure_n<long long>(std::max<int64_t>(c, 1));
       auto* sk = (int32_t*)keysA.ensure_n<unsigned long long>(std::max<int64_t>(P, 1));
@@ -408,8 +450,10 @@ struct Workspace {
         gs.hpos = hpos.ensure_n<long long>(GP + 1);
         gs.hist = hist.ensure_n<long long>(radix_hist_elems(GP));
       }
+      const SparseCtx sp{smflag.as<unsigned char>(), sdeg.as<int32_t>(), sclean.as<unsigned char>()};
       cluster_merge(g, cid_out, cs, ccount, c, cbase, cur, sk, sv, co, ca, cwp, csp, &st()->nnz,
-                    h_counters->maxt > kMergeMax, 2 * c >= g.n, ng ? &gs : nullptr, cs.cnt, &ctr()->blist_n, s);
+                    h_counters->maxt > kMergeMax, 2 * c >= g.n, ng ? &gs : nullptr, cs.cnt, &ctr()->blist_n, s,
+                    sparse ? &sp : nullptr);
     } else {
       exclusive_scan<int, long long>(cs.cnt, cs.pos, g.n, &ctr()->pairs, cs.scan_scr, s);
       int bits = ceil_log2(c);
@@ -429,7 +473,7 @@ struct Workspace {
     if (timing) ct_spans.push_back({t1, mark()});
     GraphView h;
     h.n = c;
-    h.nnz = P;  // upper bound until the state is read
+    h.nnz = E;  // upper bound until the state is read
     h.off = co;
     h.adj = ca;
     h.w = cwp;

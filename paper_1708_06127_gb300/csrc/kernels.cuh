@@ -64,7 +64,9 @@ struct Bins {
   int h_mid = 0, h_block = 0, h_global = 0, h_maxdeg = 0, h_small = 0, h_reg = 0;  // host copies
 };
 
-void bins_build(const GraphView& g, Bins& b, cudaStream_t s);
+// list_n not null: bins the vertices list[0, *list_n) (at most g.n of them) instead of all.
+void bins_build(const GraphView& g, Bins& b, cudaStream_t s, const int32_t* list = nullptr,
+                const int* list_n = nullptr);
 
 // Scratch for the global-class tables: blocks x cap slots.
 struct GlobalTables {
@@ -188,10 +190,24 @@ struct GiantScratch {
 };
 void cluster_stats(int64_t n, const int32_t* ccount, int* maxt, long long* pairs, int* ngiant, long long* gpairs,
                    cudaStream_t s);
+// Sparse contraction (contraction by union-find roots on a graph of strictly increasing
+// lists, see contract.cu): sparse_mark flags the merged clusters (mflag, n bytes), counts
+// the coarse degree of every lone vertex it handles (sdeg[v], -1 for the others) and
+// lists the others (dirty, n bytes; list[*count]) for the pre-merge.  With a SparseCtx,
+// cluster_merge expects pairs from the listed vertices only (the rest with no pairs) and
+// writes the handled vertices' lists itself; clean holds at least c bytes.
+struct SparseCtx {
+  const unsigned char* mflag;
+  const int32_t* sdeg;
+  unsigned char* clean;
+};
+void sparse_mark(const GraphView& g, const int32_t* lab, const int32_t* cid, unsigned char* mflag,
+                 unsigned char* dirty, int32_t* sdeg, int32_t* list, int* count, cudaStream_t s);
 void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int32_t* ccount, int64_t c,
                    long long* cbase, long long* cursor, int32_t* seg_key, long long* seg_val, int64_t* coff,
                    int32_t* cadj, long long* cw, int32_t* csrc, long long* nnz_dev, bool big, bool sort_first,
-                   const GiantScratch* giant, int32_t* blist, int* blist_n, cudaStream_t s);
+                   const GiantScratch* giant, int32_t* blist, int* blist_n, cudaStream_t s,
+                   const SparseCtx* sparse = nullptr);
 
 // Builds (cid[v] << bits | cu, weight) pairs from the pre-merged lists.
 void build_pairs(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int bits, int64_t pairs,

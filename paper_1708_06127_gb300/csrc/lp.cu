@@ -45,18 +45,27 @@ struct BinOut {
   int slot[kBinClasses];  // index of the class's count in Bins::counts
 };
 
+// With a vertex list (list_n not null), the listed vertices list[0, *list_n) are binned
+// instead of [0, n) (n is then only the list's capacity).
 __global__ void __launch_bounds__(256) bins_k(int64_t n, int64_t chunk, const int64_t* __restrict__ off, BinOut out,
-                                              int* __restrict__ counts) {
+                                              int* __restrict__ counts, const int32_t* __restrict__ list,
+                                              const int* __restrict__ list_n) {
   __shared__ int s_cnt[kBinClasses], s_base[kBinClasses], s_run[kBinClasses], s_max;
   __shared__ int s_warp[8][kBinClasses];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (list_n) {  // the list's length is known on the device only: chunks follow from it
+    n = *list_n;
+    chunk = (n + gridDim.x - 1) / gridDim.x;
+  }
   const int64_t lo = (int64_t)blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+  auto vert = [&](int64_t i) -> int64_t { return list_n ? (int64_t)list[i] : i; };
   if (tid < kBinClasses) { s_cnt[tid] = 0; s_run[tid] = 0; s_base[tid] = 0; }
   if (tid == 0) s_max = 0;
   __syncthreads();
   int c[kBinClasses] = {0, 0, 0, 0, 0};
   int dmax = 0;
-  for (int64_t v = lo + tid; v < hi; v += 256) {
+  for (int64_t i = lo + tid; i < hi; i += 256) {
+    const int64_t v = vert(i);
     const int64_t d = off[v + 1] - off[v];
     const int k = bin_class(d);
 #pragma unroll
@@ -75,8 +84,9 @@ __global__ void __launch_bounds__(256) bins_k(int64_t n, int64_t chunk, const in
   if (tid == 0 && s_max) atomicMax(&counts[3], s_max);
   __syncthreads();
   for (int64_t b0 = lo; b0 < hi; b0 += 256) {  // the same trip count in every thread
-    const int64_t v = b0 + tid;
-    const int k = v < hi ? bin_class(off[v + 1] - off[v]) : -1;
+    const int64_t i = b0 + tid;
+    const int64_t v = i < hi ? vert(i) : -1;
+    const int k = i < hi ? bin_class(off[v + 1] - off[v]) : -1;
     unsigned mine = 0;
 #pragma unroll
     for (int q = 0; q < kBinClasses; ++q) {
@@ -100,13 +110,13 @@ __global__ void __launch_bounds__(256) bins_k(int64_t n, int64_t chunk, const in
   }
 }
 
-void bins_build(const GraphView& g, Bins& b, cudaStream_t s) {
+void bins_build(const GraphView& g, Bins& b, cudaStream_t s, const int32_t* list, const int* list_n) {
   VC_CUDA(cudaMemsetAsync(b.counts, 0, 6 * sizeof(int), s));
   if (g.n <= 0) return;
   const int64_t blocks = std::min<int64_t>((g.n + 255) / 256, (int64_t)kSMs * 8);
   const int64_t chunk = (g.n + blocks - 1) / blocks;
   BinOut out{{b.small_list, b.reg_list, b.mid_list, b.block_list, b.global_list}, {4, 5, 0, 1, 2}};
-  bins_k<<<(int)blocks, 256, 0, s>>>(g.n, chunk, g.off, out, b.counts);
+  bins_k<<<(int)blocks, 256, 0, s>>>(g.n, chunk, g.off, out, b.counts, list, list_n);
   count_launch();
   VC_CHECK_LAUNCH();
 }

@@ -205,7 +205,7 @@ static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, u
     int32_t* cid = contracted ? W.cidT.as<int32_t>() : W.map0.as<int32_t>();
     int dst = slot == 0 ? 1 : 0;
     const GraphView fine = G;
-    GraphView h = W.contract(G, labels, cid, dst, kind == 1 && H.correct);
+    GraphView h = W.contract(G, labels, cid, dst, kind == 1 && H.correct, kind >= 2);
     set_n_k<<<1, 1, 0, s>>>(st, h.n);
     count_launch();
     if (!contracted) {
