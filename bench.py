@@ -272,7 +272,7 @@ def bench_serve(pool_size: int, requests: int, warm: int, device: int, budget_gb
         return [res[t] for t in tickets]
 
     # closed burst: everything submitted at once
-    burst = [pool[i % pool_size] for i in range(max(warm, 8))]
+    burst = [pool[i % pool_size] for i in range(min(max(warm, 8), 64))]
     drain([srv.submit(g.offsets, g.adj, g.w, 1 + i) for i, g in enumerate(burst)])  # warm-up
     burst = [pool[i] for i in rng.integers(0, pool_size, size=4 * pool_size)]
     t0 = time.perf_counter()
@@ -321,7 +321,7 @@ def bench_serve(pool_size: int, requests: int, warm: int, device: int, budget_gb
             seen = len(tickets)
         outstanding.update(new)
         for t in list(outstanding):
-            r = srv.poll(t)
+            r = srv.poll_info(t)
             if r is not None:
                 done_lat[t] = (r[2], time.perf_counter())
                 outstanding.discard(t)
@@ -331,11 +331,26 @@ def bench_serve(pool_size: int, requests: int, warm: int, device: int, budget_gb
     st = srv.stats()
     srv.close()
     order = tickets[warm:]
-    lats = np.array([done_lat[t][0] for t in order])
+    infos = [done_lat[t][0] for t in order]
+    lats = np.array([i["latency_ms"] for i in infos])
     window = max(done_lat[t][1] for t in order) - min(done_lat[t][1] for t in tickets[:warm + 1])
     edges = sum(sizes[warm:]) // 2
+
+    def pct(xs):
+        xs = np.asarray(xs, dtype=np.float64)
+        if xs.size == 0:
+            return None
+        return {"count": int(xs.size), "p50_ms": float(np.percentile(xs, 50)), "p99_ms": float(np.percentile(xs, 99)),
+                "mean_ms": float(xs.mean())}
+
+    by_lane = {}
+    for lane, name in ((0, "union (batched)"), (1, "solo")):
+        sel = [i for i in infos if i["lane"] == lane]
+        by_lane[name] = {"latency": pct([i["latency_ms"] for i in sel]), "queue": pct([i["queue_ms"] for i in sel]),
+                         "run": pct([i["run_ms"] for i in sel])}
     return {"metric": "served min-cut requests: p50/p99 latency and graphs/s (Poisson arrivals)",
             "p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99)),
+            "queue": pct([i["queue_ms"] for i in infos]), "by_lane": by_lane,
             "mean_ms": float(lats.mean()), "graphs_per_s": requests / max(window, 1e-9),
             "input_edges_per_s": edges / max(window, 1e-9), "saturation_graphs_per_s": sat, "rho": rho,
             "arrival_rate_per_s": rate, "requests": requests, "warmup_requests": warm,
@@ -504,7 +519,8 @@ def main():
     ap.add_argument("--mode", default="all", choices=["all", "single", "batch", "serve", "configs", "quality"],
                     help="all: the headline line plus batch and serving summaries")
     ap.add_argument("--batch-count", type=int, default=4096)
-    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-pool", type=int, default=48)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -535,7 +551,7 @@ def main():
     if args.mode == "serve":
         torch.cuda.set_device(local)
         vc.build()
-        res = bench_serve(args.serve_pool, args.serve_requests, 30, local)
+        res = bench_serve(args.serve_pool, args.serve_requests, args.serve_warmup, local)
         print(json.dumps(res), flush=True)
         return 0
     torch.cuda.set_device(local)
@@ -705,7 +721,8 @@ def main():
     mc.close()
     if args.mode == "all" and rank == 0:
         line["batch"] = bench_batch(args.batch_count, 3, 1, stream, local)
-        line["serve"] = bench_serve(args.serve_pool, args.serve_requests, 30, local)
+        line["serve"] = bench_serve(args.serve_pool, args.serve_requests, args.serve_warmup, local)
+        line["configs"] = bench_configs(local)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg is not None:

@@ -45,8 +45,8 @@ extern "C" {
 #define VIECUT_EINVAL (-1)    /* invalid argument or malformed graph */
 #define VIECUT_ENOMEM (-2)    /* device or host allocation failed */
 #define VIECUT_ECUDA (-3)     /* CUDA runtime error (message names the call) */
-#define VIECUT_ETIMEOUT (-4)  /* a bounded device wait ran out */
-#define VIECUT_ECANCELLED (-5)
+#define VIECUT_ETIMEOUT (-4)  /* a bounded wait ran out (viecut_server_wait) */
+#define VIECUT_ECANCELLED (-5) /* the request was cancelled (viecut_server_cancel) */
 #define VIECUT_EBUSY (-6)     /* result not ready yet (server poll) */
 
 typedef struct viecut_handle viecut_t;
@@ -283,7 +283,20 @@ typedef struct viecut_server_stats {
   int64_t admitted, completed, pending, max_resident, super_steps, joins, budget_used;
   int64_t solo_completed;   /* requests served on the solo lane */
   int64_t rejected;         /* requests refused by the device check (counted in completed) */
+  int64_t cancelled;        /* requests cancelled by viecut_server_cancel */
+  int64_t failed;           /* requests answered with VIECUT_ENOMEM (counted in completed) */
 } viecut_server_stats;
+
+/* Where a served request's time went (viecut_server_poll_info / viecut_server_wait). */
+typedef struct viecut_request_info {
+  double latency_ms;  /* submit -> result on the host */
+  double queue_ms;    /* submit -> the request started on the device (admitted to the union or taken
+                         by the solo lane) */
+  double run_ms;      /* started -> result on the host */
+  int32_t lane;       /* 0: batched in the resident union; 1: the solo lane */
+  int32_t pad;
+  int64_t n, m;       /* the request's graph */
+} viecut_request_info;
 
 typedef struct viecut_server viecut_server;
 
@@ -303,15 +316,39 @@ int viecut_server_submit(viecut_server* s, const viecut_graph_desc* g, uint64_t 
  * the device check refused returns EINVAL (viecut_last_error gives the reason) and its
  * ticket is forgotten too. */
 int viecut_server_poll(viecut_server* s, uint64_t ticket, int64_t* cut, uint64_t* side_bits, double* latency_ms);
+/* As viecut_server_poll, with the request's timing breakdown in *info (may be NULL). */
+int viecut_server_poll_info(viecut_server* s, uint64_t ticket, int64_t* cut, uint64_t* side_bits,
+                            viecut_request_info* info);
+/* As viecut_server_poll_info, but waits on the host for the request to finish, at most
+ * timeout_ms milliseconds: VIECUT_ETIMEOUT when it has not (the ticket stays valid; poll
+ * or wait again).  A host-side bounded wait: no device wait is involved.  EINVAL for a
+ * negative timeout. */
+int viecut_server_wait(viecut_server* s, uint64_t ticket, double timeout_ms, int64_t* cut, uint64_t* side_bits,
+                       viecut_request_info* info);
+/* Cancels a request.  A request still queued leaves the queue and never runs; one already
+ * on the device runs to its end, but its result is dropped.  Either way the next poll or
+ * wait on the ticket returns VIECUT_ECANCELLED and forgets it.  Cancelling twice is a
+ * no-op; EINVAL for an unknown ticket (already polled, or never issued). */
+int viecut_server_cancel(viecut_server* s, uint64_t ticket);
 int viecut_server_get_stats(viecut_server* s, viecut_server_stats* st);
 /* Stops the thread (requests still queued or resident are abandoned) and frees all. */
 int viecut_server_stop(viecut_server* s);
 
+/* Fault injection for tests (the paper has no counterpart): after the next `after`
+ * device allocations of this library (any handle, batch, server or thread), the
+ * following `count` fail on the host as if cudaMalloc had run out of memory, and the
+ * call that needed them returns VIECUT_ENOMEM.  No GPU fault is involved.  count = 0
+ * switches the injection off.  Handles, batches and servers stay usable afterwards: a
+ * handle whose load failed holds no graph until the next successful load, and a server
+ * answers the requests whose admission failed with VIECUT_ENOMEM.  EINVAL for negative
+ * arguments. */
+int viecut_debug_fail_device_allocs(int64_t after, int64_t count);
+
 /* The library's sizes of its public structures, for bindings that restate them:
- * sizes[0..6] = sizeof viecut_opts, viecut_stats, viecut_step, viecut_graph_desc,
- * viecut_batch_stats, viecut_server_opts, viecut_server_stats (as many as count
- * allows).  Returns the number of sizes the library knows (7), or VIECUT_EINVAL for a
- * null array with count > 0.  Needs no device. */
+ * sizes[0..7] = sizeof viecut_opts, viecut_stats, viecut_step, viecut_graph_desc,
+ * viecut_batch_stats, viecut_server_opts, viecut_server_stats, viecut_request_info (as
+ * many as count allows).  Returns the number of sizes the library knows (8), or
+ * VIECUT_EINVAL for a null array with count > 0.  Needs no device. */
 int viecut_struct_sizes(int64_t* sizes, int32_t count);
 
 #ifdef __cplusplus

@@ -72,7 +72,13 @@ class viecut_server_opts(ctypes.Structure):
 class viecut_server_stats(ctypes.Structure):
     _fields_ = [("admitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("pending", ctypes.c_int64),
                 ("max_resident", ctypes.c_int64), ("super_steps", ctypes.c_int64), ("joins", ctypes.c_int64),
-                ("budget_used", ctypes.c_int64), ("solo_completed", ctypes.c_int64), ("rejected", ctypes.c_int64)]
+                ("budget_used", ctypes.c_int64), ("solo_completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("cancelled", ctypes.c_int64), ("failed", ctypes.c_int64)]
+
+
+class viecut_request_info(ctypes.Structure):
+    _fields_ = [("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("lane", ctypes.c_int32), ("pad", ctypes.c_int32), ("n", ctypes.c_int64), ("m", ctypes.c_int64)]
 
 
 class viecut_step(ctypes.Structure):
@@ -97,6 +103,7 @@ SIGNATURES = [
     ("viecut_destroy", ctypes.c_int, [_vp]),
     ("viecut_last_error", ctypes.c_char_p, []),
     ("viecut_launch_count", ctypes.c_int64, []),
+    ("viecut_debug_fail_device_allocs", ctypes.c_int, [_i64, _i64]),
     ("viecut_graph_upload", ctypes.c_int, [_pvp, _vp, _vp, _vp, _i64, _i64, _i32]),
     ("viecut_graph_shape", ctypes.c_int, [_vp, _vp, _vp]),
     ("viecut_graph_download", ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -118,6 +125,9 @@ SIGNATURES = [
     ("viecut_server_start", ctypes.c_int, [_pvp, _vp]),
     ("viecut_server_submit", ctypes.c_int, [_vp, _vp, _u64, _vp]),
     ("viecut_server_poll", ctypes.c_int, [_vp, _u64, _vp, _vp, _vp]),
+    ("viecut_server_poll_info", ctypes.c_int, [_vp, _u64, _vp, _vp, _vp]),
+    ("viecut_server_wait", ctypes.c_int, [_vp, _u64, ctypes.c_double, _vp, _vp, _vp]),
+    ("viecut_server_cancel", ctypes.c_int, [_vp, _u64]),
     ("viecut_server_get_stats", ctypes.c_int, [_vp, _vp]),
     ("viecut_server_stop", ctypes.c_int, [_vp]),
 ]
@@ -224,6 +234,11 @@ def viecut_destroy(h):
 
 def viecut_launch_count() -> int:
     return int(lib().viecut_launch_count())
+
+
+def viecut_debug_fail_device_allocs(after: int, count: int) -> None:
+    """Test hook: after `after` more device allocations, `count` fail with VIECUT_ENOMEM."""
+    _check(lib().viecut_debug_fail_device_allocs(int(after), int(count)))
 
 
 # ----------------------------------------------------------------- step API
@@ -439,6 +454,37 @@ def viecut_server_poll(s, ticket: int, n: int):
     return int(cut.value), bits, float(lat.value)
 
 
+def _info_dict(info: viecut_request_info) -> dict:
+    return {k: getattr(info, k) for k, _ in viecut_request_info._fields_ if k != "pad"}
+
+
+def viecut_server_poll_info(s, ticket: int, n: int):
+    """None while the request runs, else (cut, side bitmap, timing dict)."""
+    cut = ctypes.c_int64()
+    info = viecut_request_info()
+    bits = np.zeros(max(1, (n + 63) // 64), np.uint64)
+    rc = lib().viecut_server_poll_info(s, ticket, ctypes.byref(cut), bits.ctypes.data, ctypes.byref(info))
+    if rc == VIECUT_EBUSY:
+        return None
+    _check(rc)
+    return int(cut.value), bits, _info_dict(info)
+
+
+def viecut_server_wait(s, ticket: int, n: int, timeout_ms: float):
+    """(cut, side bitmap, timing dict); raises ViecutError (VIECUT_ETIMEOUT) when the request
+    has not finished within timeout_ms."""
+    cut = ctypes.c_int64()
+    info = viecut_request_info()
+    bits = np.zeros(max(1, (n + 63) // 64), np.uint64)
+    _check(lib().viecut_server_wait(s, ticket, float(timeout_ms), ctypes.byref(cut), bits.ctypes.data,
+                                    ctypes.byref(info)))
+    return int(cut.value), bits, _info_dict(info)
+
+
+def viecut_server_cancel(s, ticket: int) -> None:
+    _check(lib().viecut_server_cancel(s, ticket))
+
+
 def viecut_server_get_stats(s) -> dict:
     st = viecut_server_stats()
     _check(lib().viecut_server_get_stats(s, ctypes.byref(st)))
@@ -475,16 +521,31 @@ class Server:
             del self.sizes[ticket]
         return r
 
-    def wait(self, ticket: int, timeout: float = 600.0, sleep: float = 0.0005):
-        import time
-        t0 = time.perf_counter()
-        while True:
-            r = self.poll(ticket)
-            if r is not None:
-                return r
-            if time.perf_counter() - t0 > timeout:
-                raise TimeoutError(f"ticket {ticket} not done after {timeout} s")
-            time.sleep(sleep)
+    def poll_info(self, ticket: int):
+        """None while the request runs, else (cut, side bitmap, timing dict)."""
+        try:
+            r = viecut_server_poll_info(self.s, ticket, self.sizes[ticket])
+        except ViecutError:
+            self.sizes.pop(ticket, None)  # answered once (refused, cancelled, failed)
+            raise
+        if r is not None:
+            del self.sizes[ticket]
+        return r
+
+    def wait(self, ticket: int, timeout: float = 600.0):
+        """(cut, side bitmap, latency in ms), waiting on the host at most `timeout` seconds
+        (ViecutError with VIECUT_ETIMEOUT after it; the ticket stays valid)."""
+        try:
+            cut, bits, info = viecut_server_wait(self.s, ticket, self.sizes[ticket], 1000.0 * timeout)
+        except ViecutError as e:
+            if e.code != VIECUT_ETIMEOUT:
+                self.sizes.pop(ticket, None)
+            raise
+        del self.sizes[ticket]
+        return cut, bits, info["latency_ms"]
+
+    def cancel(self, ticket: int) -> None:
+        viecut_server_cancel(self.s, ticket)
 
     def stats(self) -> dict:
         return viecut_server_get_stats(self.s)

@@ -447,6 +447,8 @@ __global__ void b_set_i64_k(int64_t* p, int64_t v) { *p = v; }
 static void grow_keep(Buf& b, size_t bytes, size_t keep, cudaStream_t s) {
   if (bytes <= b.cap) return;
   void* p = nullptr;
+  if (take_injected_alloc_failure())
+    throw Error{VIECUT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed (injected)"};
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -909,7 +911,9 @@ struct Request {
   int64_t est = 0;
   int slot = -1;
   int64_t obase = -1;
-  std::chrono::steady_clock::time_point t_submit, t_done;
+  std::chrono::steady_clock::time_point t_submit, t_start, t_done;
+  int lane = 0;            // 0: the resident union, 1: the solo lane
+  bool cancelled = false;  // viecut_server_cancel: the result is dropped
   bool done = false;
   int64_t cut = 0;
   std::vector<uint64_t> bits;
@@ -921,6 +925,7 @@ struct Server {
   int lp_iters = 2;
   std::mutex mu;
   std::condition_variable cv;
+  std::condition_variable cv_done;  // a request finished (viecut_server_wait)
   bool stopping = false;
   std::thread th;
   std::string error;  // set once the loop failed
@@ -938,6 +943,8 @@ struct Server {
   Buf st_off, st_adj, st_w;  // staging of joining graphs (grow-only)
   HostPool host;
   int64_t rejected = 0;
+  int64_t cancelled = 0;
+  int64_t failed = 0;  // requests answered with VIECUT_ENOMEM
   std::vector<long long> h_join;
   // solo lane: requests of at least solo_min_n vertices, one at a time on a handle
   // (and stream) of their own
@@ -1000,16 +1007,37 @@ static std::string invalid_reason(int bad) {
   return why;
 }
 
-// Marks a request as refused and gives back what admission took (under S.mu).
-static void refuse(Server& S, const std::shared_ptr<Request>& r, const std::string& why) {
-  r->err = VIECUT_EINVAL;
+// Marks a request as refused (VIECUT_EINVAL: its graph failed the device check;
+// VIECUT_ENOMEM: its admission could not get device memory) and gives back what
+// admission took (under S.mu).
+static void refuse(Server& S, const std::shared_ptr<Request>& r, const std::string& why, int code = VIECUT_EINVAL) {
+  r->err = code;
   r->err_msg = why;
   r->t_done = std::chrono::steady_clock::now();
   r->done = true;
   S.host.put(r->blk);
   S.budget_used -= r->est;
-  S.rejected += 1;
+  if (code == VIECUT_ENOMEM) S.failed += 1;
+  else S.rejected += 1;
   S.completed += 1;
+  S.cv_done.notify_all();
+}
+
+// A join whose device memory could not be had: its requests are answered with
+// VIECUT_ENOMEM and their slots and arena ranges given back; the resident graphs are
+// untouched (every allocation of a join comes before any change to them).
+static void fail_join(Server& S, std::vector<std::shared_ptr<Request>>& add, const std::string& why) {
+  std::lock_guard<std::mutex> lk(S.mu);
+  for (auto& r : add) {
+    if (r->obase >= 0) {
+      arena_free(S, r->obase, r->n);
+      r->obase = -1;
+    }
+    S.slot_req[r->slot].reset();
+    S.free_slots.push_back(r->slot);
+    refuse(S, r, why, VIECUT_ENOMEM);
+  }
+  add.clear();
 }
 
 // Copies the admitted requests to the device, checks them there (a refused request is
@@ -1028,9 +1056,22 @@ static void server_join(Server& S, std::vector<std::shared_ptr<Request>>& add) {
     se[j + 1] = se[j] + add[j]->m;
   }
   const int64_t sn = sv[J], sm = se[J];
-  int64_t* d_off = S.st_off.ensure_n<int64_t>(sn);
-  int32_t* d_adj = S.st_adj.ensure_n<int32_t>(std::max<int64_t>(sm, 1));
-  int32_t* d_w = S.st_w.ensure_n<int32_t>(std::max<int64_t>(sm, 1));
+  int64_t* d_off;
+  int32_t *d_adj, *d_w, *sgid;
+  long long* dsv;
+  int* derr;
+  try {
+    d_off = S.st_off.ensure_n<int64_t>(sn);
+    d_adj = S.st_adj.ensure_n<int32_t>(std::max<int64_t>(sm, 1));
+    d_w = S.st_w.ensure_n<int32_t>(std::max<int64_t>(sm, 1));
+    dsv = S.d_join.ensure_n<long long>(6 * (J + 1));
+    sgid = S.d_sgid.ensure_n<int32_t>(std::max<int64_t>(sn, 1));
+    derr = S.d_err.ensure_n<int>(J);
+  } catch (const Error& e) {
+    if (e.code != VIECUT_ENOMEM) throw;
+    fail_join(S, add, e.msg);
+    return;
+  }
   for (int j = 0; j < J; ++j) {
     const auto& r = add[j];
     VC_CUDA(cudaMemcpyAsync(d_off + sv[j], r->off, sizeof(int64_t) * r->n, cudaMemcpyHostToDevice, s));
@@ -1039,11 +1080,8 @@ static void server_join(Server& S, std::vector<std::shared_ptr<Request>>& add) {
       VC_CUDA(cudaMemcpyAsync(d_w + se[j], r->w, sizeof(int32_t) * r->m, cudaMemcpyHostToDevice, s));
     }
   }
-  long long* dsv = S.d_join.ensure_n<long long>(6 * (J + 1));
   VC_CUDA(cudaMemcpyAsync(dsv, sv.data(), sizeof(long long) * (J + 1), cudaMemcpyHostToDevice, s));
   VC_CUDA(cudaMemcpyAsync(dsv + (J + 1), se.data(), sizeof(long long) * (J + 1), cudaMemcpyHostToDevice, s));
-  int32_t* sgid = S.d_sgid.ensure_n<int32_t>(std::max<int64_t>(sn, 1));
-  int* derr = S.d_err.ensure_n<int>(J);
   VC_CUDA(cudaMemsetAsync(derr, 0, sizeof(int) * J, s));
   b_stage_gid_k<<<J < 4 * kSMs ? J : 4 * kSMs, 256, 0, s>>>(J, dsv, sgid);
   b_validate_staged_k<<<grid_for(sn, 8, kSMs * 16), 256, 0, s>>>(sn, sgid, dsv, dsv + (J + 1), d_off, d_adj, d_w,
@@ -1082,8 +1120,33 @@ static void server_join(Server& S, std::vector<std::shared_ptr<Request>>& add) {
   int64_t kn = 0, km = 0;
   for (auto& r : add) { kn += r->n; km += r->m; }
   const int64_t n_new = n_u + kn, m_new = m_u + km;
-  if (n_new > 0x7fffffffLL) throw Error{VIECUT_ENOMEM, "the resident graphs exceed 2^31 vertices"};
-  for (auto& r : add) r->obase = arena_alloc(S, r->n);
+  const int dst = E.slot == 0 ? 1 : 0;
+  const bool onA = E.gid == E.gidA.as<int32_t>() || E.gid == nullptr;
+  Buf& cur = onA ? E.gidA : E.gidB;
+  Buf& alt = onA ? E.gidB : E.gidA;
+  int64_t* off;
+  int32_t* adj;
+  long long* w;
+  // every allocation of the join before any change to the resident graphs
+  try {
+    if (n_new > 0x7fffffffLL) throw Error{VIECUT_ENOMEM, "the resident graphs would exceed 2^31 vertices"};
+    for (auto& r : add) r->obase = arena_alloc(S, r->n);
+    S.d_join.ensure_n<long long>(6 * (J + 1));
+    off = W.coff[dst].ensure_n<int64_t>(n_new + 1);
+    adj = W.cadj[dst].ensure_n<int32_t>(std::max<int64_t>(m_new, 1));
+    w = W.cw[dst].ensure_n<long long>(std::max<int64_t>(m_new, 1));
+    grow_keep(cur, sizeof(int32_t) * std::max<int64_t>(n_new, 1), sizeof(int32_t) * n_u, s);
+    E.gid = cur.as<int32_t>();
+    alt.ensure_n<int32_t>(n_new);
+    S.d_init.ensure(sizeof(SlotInit) * J);
+    W.ensure_vertices(n_new);
+    W.ensure_entries(m_new, n_new);
+    E.vact.ensure_n<unsigned char>(n_new);
+  } catch (const Error& e) {
+    if (e.code != VIECUT_ENOMEM) throw;
+    fail_join(S, add, e.msg);
+    return;
+  }
   // per kept request: union vertex and entry base, staged vertex and entry base, n, m
   S.h_join.assign(6 * (J + 1), 0);
   long long* jv = S.h_join.data();
@@ -1103,12 +1166,8 @@ static void server_join(Server& S, std::vector<std::shared_ptr<Request>>& add) {
     at_v += add[i]->n;
     at_e += add[i]->m;
   }
-  long long* dj = S.d_join.ensure_n<long long>(6 * (J + 1));  // the checks above are done with it
+  long long* dj = S.d_join.as<long long>();  // the checks above are done with it
   VC_CUDA(cudaMemcpyAsync(dj, jv, sizeof(long long) * 6 * (J + 1), cudaMemcpyHostToDevice, s));
-  const int dst = E.slot == 0 ? 1 : 0;
-  int64_t* off = W.coff[dst].ensure_n<int64_t>(n_new + 1);
-  int32_t* adj = W.cadj[dst].ensure_n<int32_t>(std::max<int64_t>(m_new, 1));
-  long long* w = W.cw[dst].ensure_n<long long>(std::max<int64_t>(m_new, 1));
   if (n_u > 0) {
     VC_CUDA(cudaMemcpyAsync(off, E.G.off, sizeof(int64_t) * n_u, cudaMemcpyDeviceToDevice, s));
     VC_CUDA(cudaMemcpyAsync(adj, E.G.adj, sizeof(int32_t) * m_u, cudaMemcpyDeviceToDevice, s));
@@ -1121,18 +1180,11 @@ static void server_join(Server& S, std::vector<std::shared_ptr<Request>>& add) {
   b_set_i64_k<<<1, 1, 0, s>>>(off + n_new, m_new);
   count_launch(2);
   VC_CHECK_LAUNCH();
-  // vertex -> slot map: keep the old entries
-  const bool onA = E.gid == E.gidA.as<int32_t>() || E.gid == nullptr;
-  Buf& cur = onA ? E.gidA : E.gidB;
-  Buf& alt = onA ? E.gidB : E.gidA;
-  grow_keep(cur, sizeof(int32_t) * std::max<int64_t>(n_new, 1), sizeof(int32_t) * n_u, s);
-  alt.ensure_n<int32_t>(n_new);
-  E.gid = cur.as<int32_t>();
   // slot records
   std::vector<SlotInit> init(J);
   for (int j = 0; j < J; ++j)
     init[j] = SlotInit{add[j]->slot, 0, jv[j], add[j]->n, add[j]->m, add[j]->obase, add[j]->seed};
-  SlotInit* di = (SlotInit*)S.d_init.ensure(sizeof(SlotInit) * J);
+  SlotInit* di = (SlotInit*)S.d_init.p;
   VC_CUDA(cudaMemcpyAsync(di, init.data(), sizeof(SlotInit) * J, cudaMemcpyHostToDevice, s));
   BState B = E.state();
   b_slot_init_k<<<(J + 255) / 256, 256, 0, s>>>(J, di, B);
@@ -1151,9 +1203,6 @@ static void server_join(Server& S, std::vector<std::shared_ptr<Request>>& add) {
   E.G.simple = S.all_simple;
   E.slot = dst;
   W.bins_valid = false;
-  W.ensure_vertices(n_new);
-  W.ensure_entries(m_new, n_new);
-  E.vact.ensure_n<unsigned char>(n_new);
   engine_start_new(E);
   VC_CUDA(cudaStreamSynchronize(s));
   S.joins += 1;
@@ -1204,6 +1253,7 @@ static void server_collect(Server& S) {
     S.completed += 1;
   }
   S.cv_solo.notify_one();  // budget came free
+  S.cv_done.notify_all();
 }
 
 static void server_loop(Server& S) {
@@ -1223,6 +1273,7 @@ static void server_loop(Server& S) {
           S.free_slots.pop_back();
           S.budget_used += r->est;
           S.slot_req[r->slot] = r;
+          r->t_start = std::chrono::steady_clock::now();
           add.push_back(r);
           S.admitted += 1;
         }
@@ -1266,13 +1317,17 @@ static void solo_loop(Server& S) {
         S.solo_pending.pop_front();
         S.budget_used += r->est;
         S.admitted += 1;
+        r->t_start = std::chrono::steady_clock::now();
+        r->lane = 1;
       }
       int rc = h ? viecut_load(h, r->off, r->adj, r->n, r->m, r->w)
                  : viecut_create(&h, r->off, r->adj, r->n, r->m, r->w, &S.solo_opts);
-      if (rc == VIECUT_EINVAL) {
+      if (rc == VIECUT_EINVAL || rc == VIECUT_ENOMEM) {
+        // a refused graph, or no device memory for it: this request fails, the lane goes on
+        // (a handle whose load failed holds no graph until the next load)
         const std::string why = viecut_last_error();
         std::lock_guard<std::mutex> lk(S.mu);
-        refuse(S, r, why);
+        refuse(S, r, why, rc);
         S.cv.notify_one();
         continue;
       }
@@ -1280,7 +1335,15 @@ static void solo_loop(Server& S) {
       S.host.put(r->blk);  // the graph is on the device now
       int64_t cut = 0;
       std::vector<uint64_t> bits((r->n + 63) / 64);
-      solo_check(viecut_run(h, r->seed, S.lp_iters, &cut, bits.data()));
+      rc = viecut_run(h, r->seed, S.lp_iters, &cut, bits.data());
+      if (rc == VIECUT_ENOMEM) {
+        const std::string why = viecut_last_error();
+        std::lock_guard<std::mutex> lk(S.mu);
+        refuse(S, r, why, rc);
+        S.cv.notify_one();
+        continue;
+      }
+      solo_check(rc);
       const auto now = std::chrono::steady_clock::now();
       {
         std::lock_guard<std::mutex> lk(S.mu);
@@ -1292,6 +1355,7 @@ static void solo_loop(Server& S) {
         S.completed += 1;
         S.solo_completed += 1;
       }
+      S.cv_done.notify_all();
       S.cv.notify_one();  // budget came free for the union
     }
   } catch (const Error& e) {
@@ -1466,26 +1530,99 @@ int viecut_server_submit(viecut_server* sv, const viecut_graph_desc* g, uint64_t
   VC_API_END
 }
 
-int viecut_server_poll(viecut_server* sv, uint64_t ticket, int64_t* cut, uint64_t* side_bits, double* latency_ms) {
-  VC_API_BEGIN
+namespace {
+// Hands a finished request's result out (and forgets the ticket), or says why not:
+// EBUSY while it runs, the request's own error, ECANCELLED after viecut_server_cancel.
+// timeout_ms < 0: no wait; otherwise waits up to that long (ETIMEOUT after it).
+int take_result(viecut_server* sv, uint64_t ticket, double timeout_ms, int64_t* cut, uint64_t* side_bits,
+                viecut_request_info* info) {
   if (!sv) throw Error{VIECUT_EINVAL, "null server"};
   vc::Server& S = sv->s;
   std::shared_ptr<vc::Request> r;
   {
-    std::lock_guard<std::mutex> lk(S.mu);
+    std::unique_lock<std::mutex> lk(S.mu);
     auto it = S.tickets.find(ticket);
     if (it == S.tickets.end()) throw Error{VIECUT_EINVAL, "unknown ticket"};
-    if (!it->second->done) {
+    r = it->second;
+    if (!r->done && timeout_ms >= 0) {
+      S.cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms),
+                         [&] { return r->done || !S.error.empty() || S.stopping; });
+    }
+    if (!r->done) {
       if (!S.error.empty()) throw Error{VIECUT_ECUDA, S.error};
+      if (timeout_ms >= 0) throw Error{VIECUT_ETIMEOUT, "request not finished within the timeout"};
       return VIECUT_EBUSY;
     }
-    r = it->second;
-    S.tickets.erase(it);
+    S.tickets.erase(ticket);
   }
+  if (r->cancelled) throw Error{VIECUT_ECANCELLED, "request cancelled"};
   if (r->err) throw Error{r->err, r->err_msg};
   if (cut) *cut = r->cut;
   if (side_bits && !r->bits.empty()) memcpy(side_bits, r->bits.data(), sizeof(uint64_t) * r->bits.size());
-  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  if (info) {
+    auto ms = [](std::chrono::steady_clock::duration d) { return std::chrono::duration<double, std::milli>(d).count(); };
+    info->latency_ms = ms(r->t_done - r->t_submit);
+    info->queue_ms = ms(r->t_start - r->t_submit);
+    info->run_ms = ms(r->t_done - r->t_start);
+    info->lane = r->lane;
+    info->n = r->n;
+    info->m = r->m;
+  }
+  return VIECUT_OK;
+}
+}  // namespace
+
+int viecut_server_poll(viecut_server* sv, uint64_t ticket, int64_t* cut, uint64_t* side_bits, double* latency_ms) {
+  VC_API_BEGIN
+  viecut_request_info info{};
+  const int rc = take_result(sv, ticket, -1.0, cut, side_bits, &info);
+  if (rc != VIECUT_OK) return rc;
+  if (latency_ms) *latency_ms = info.latency_ms;
+  VC_API_END
+}
+
+int viecut_server_poll_info(viecut_server* sv, uint64_t ticket, int64_t* cut, uint64_t* side_bits,
+                            viecut_request_info* info) {
+  VC_API_BEGIN
+  const int rc = take_result(sv, ticket, -1.0, cut, side_bits, info);
+  if (rc != VIECUT_OK) return rc;
+  VC_API_END
+}
+
+int viecut_server_wait(viecut_server* sv, uint64_t ticket, double timeout_ms, int64_t* cut, uint64_t* side_bits,
+                       viecut_request_info* info) {
+  VC_API_BEGIN
+  if (!(timeout_ms >= 0)) throw Error{VIECUT_EINVAL, "timeout_ms must be >= 0"};
+  const int rc = take_result(sv, ticket, timeout_ms, cut, side_bits, info);
+  if (rc != VIECUT_OK) return rc;
+  VC_API_END
+}
+
+int viecut_server_cancel(viecut_server* sv, uint64_t ticket) {
+  VC_API_BEGIN
+  if (!sv) throw Error{VIECUT_EINVAL, "null server"};
+  vc::Server& S = sv->s;
+  std::lock_guard<std::mutex> lk(S.mu);
+  auto it = S.tickets.find(ticket);
+  if (it == S.tickets.end()) throw Error{VIECUT_EINVAL, "unknown ticket"};
+  auto r = it->second;
+  if (r->cancelled) return VIECUT_OK;
+  r->cancelled = true;
+  S.cancelled += 1;
+  // still queued: it leaves the queue at once and never runs
+  for (auto* q : {&S.pending, &S.solo_pending}) {
+    for (auto qi = q->begin(); qi != q->end(); ++qi) {
+      if (qi->get() == r.get()) {
+        q->erase(qi);
+        r->t_start = r->t_done = std::chrono::steady_clock::now();
+        r->done = true;
+        S.host.put(r->blk);
+        S.completed += 1;
+        S.cv_done.notify_all();
+        return VIECUT_OK;
+      }
+    }
+  }
   VC_API_END
 }
 
@@ -1503,6 +1640,8 @@ int viecut_server_get_stats(viecut_server* sv, viecut_server_stats* st) {
   st->budget_used = S.budget_used;
   st->solo_completed = S.solo_completed;
   st->rejected = S.rejected;
+  st->cancelled = S.cancelled;
+  st->failed = S.failed;
   VC_API_END
 }
 
@@ -1515,6 +1654,7 @@ int viecut_server_stop(viecut_server* sv) {
   }
   sv->s.cv.notify_all();
   sv->s.cv_solo.notify_all();
+  sv->s.cv_done.notify_all();
   if (sv->s.th.joinable()) sv->s.th.join();
   if (sv->s.th_solo.joinable()) sv->s.th_solo.join();
   cudaSetDevice(sv->s.E.device);

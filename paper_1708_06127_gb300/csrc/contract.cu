@@ -89,22 +89,37 @@ __global__ void run_heads_k(const unsigned long long* __restrict__ keys, int64_t
     heads[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
 }
 
-// Each run head sums its run (runs are short: one entry per fine vertex of the
-// source cluster that touches the target cluster).
+// Every element adds its value to its run's output: run index = (heads up to and
+// including it) - 1 = hpos[i] + heads[i] - 1.  The lanes of a warp in one run add their
+// sum once (runs can be long: a giant cluster's pairs to one target); cw must be zero.
+// The run's head writes the target and source ids.
 __global__ void run_reduce_k(const unsigned long long* __restrict__ keys, const long long* __restrict__ vals,
                              int64_t m, int bits, const int32_t* __restrict__ heads,
                              const long long* __restrict__ hpos, int32_t* __restrict__ cadj,
                              long long* __restrict__ cw, int32_t* __restrict__ cv) {
   const unsigned long long mask = (bits >= 64) ? ~0ULL : ((1ULL << bits) - 1ULL);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    if (!heads[i]) continue;
-    const unsigned long long k = keys[i];
-    long long s = vals[i];
-    for (int64_t j = i + 1; j < m && keys[j] == k; ++j) s += vals[j];
-    const long long o = hpos[i];
-    cadj[o] = (int32_t)(k & mask);
-    cw[o] = s;
-    cv[o] = (int32_t)(k >> bits);
+  const int lane = threadIdx.x & 31;
+  for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; b < m;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = b + lane;
+    const bool ok = i < m;
+    const long long r = ok ? hpos[i] + heads[i] - 1 : -1 - lane;
+    const long long x = ok ? vals[i] : 0;
+    // runs are consecutive lanes: a segmented inclusive sum, added by each run's last lane
+    long long sum = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, sum, o);
+      const long long ry = __shfl_up_sync(0xffffffffu, r, o);
+      if (lane >= o && ry == r) sum += y;
+    }
+    const long long rn = __shfl_down_sync(0xffffffffu, r, 1);
+    if (ok && (lane == 31 || rn != r)) atomicAdd((unsigned long long*)(cw + r), (unsigned long long)sum);
+    if (ok && heads[i]) {
+      const unsigned long long k = keys[i];
+      cadj[r] = (int32_t)(k & mask);
+      cv[r] = (int32_t)(k >> bits);
+    }
   }
 }
 
@@ -137,6 +152,7 @@ void reduce_pairs(const unsigned long long* keys, const long long* vals, int64_t
   }
   exclusive_scan<int, long long>(heads, hpos, pairs, nnz_dev, scan_scr, s);
   if (pairs > 0) {
+    VC_CUDA(cudaMemsetAsync(cw, 0, sizeof(long long) * pairs, s));
     run_reduce_k<<<grid, 256, 0, s>>>(keys, vals, pairs, bits, heads, hpos, cadj, cw, cv_tmp);
     count_launch();
     VC_CHECK_LAUNCH();
@@ -511,7 +527,6 @@ __global__ void __launch_bounds__(256) cluster_place_k(int64_t c, const long lon
 // write.  Only the members of merged groups (and lone vertices with more than
 // kScMaxM such entries or more than kScRows x 32 entries) go through the pre-merge and
 // the cluster merge.
-constexpr int kScRows = 8;   // lists of at most 256 entries
 constexpr int kScMaxM = 32;  // entries into merged groups per lone vertex
 
 // mflag[cid[v]] = 1 for every v that is not its own root (its group has two or more
@@ -522,48 +537,57 @@ __global__ void sc_merged_k(int64_t n, const int32_t* __restrict__ lab, const in
     if (lab[v] != (int32_t)v) mflag[cid[v]] = 1;
 }
 
-// The entries of lone vertex v that point into merged groups, collected in the warp's
-// shared arrays mk / mw (at most kScMaxM; *nm their number, > kScMaxM: too many), and
-// the list kept in registers: k[r] the neighbour's cluster id, wt[r] the weight, inM[r]
-// whether it points into a merged group (row r = entries 32 r .. 32 r + 31).
+// cidm[u] = cid[u], with the sign bit set when u's group is merged: one gather per entry
+// gives both.
+__global__ void sc_pack_k(int64_t n, const int32_t* __restrict__ cid, const unsigned char* __restrict__ mflag,
+                          int32_t* __restrict__ cidm) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = cid[v];
+    cidm[v] = mflag[x] ? (int32_t)((uint32_t)x | 0x80000000u) : x;
+  }
+}
+
+constexpr int kScUnroll = 2;  // rows of 32 entries in flight per warp
+
+// The entries of lone vertex v's list that point into merged groups, collected row by
+// row in the warp's shared arrays mk / mw (at most kScMaxM kept; the return value counts
+// them all).
 template <typename WT>
-__device__ __forceinline__ void sc_load_list(int64_t beg, int64_t end, int lane, const int32_t* __restrict__ adj,
-                                             const WT* __restrict__ w, const int32_t* __restrict__ cid,
-                                             const unsigned char* __restrict__ mflag, bool with_w,
-                                             int32_t (&k)[kScRows], long long (&wt)[kScRows], unsigned& inM,
-                                             int32_t* mk, long long* mw, int* nm_out) {
+__device__ __forceinline__ int sc_collect(int64_t beg, int64_t end, int lane, const int32_t* __restrict__ adj,
+                                          const WT* __restrict__ w, const int32_t* __restrict__ cidm, bool with_w,
+                                          int32_t* mk, long long* mw) {
   int nm = 0;
-  inM = 0;
+  for (int64_t b = beg; b < end; b += 32 * kScUnroll) {
+    int32_t u[kScUnroll], k[kScUnroll];
 #pragma unroll
-  for (int r = 0; r < kScRows; ++r) {
-    const int64_t e = beg + 32 * r + lane;
-    const bool valid = e < end;
-    k[r] = valid ? __ldg(cid + __ldg(adj + e)) : -1;
-    wt[r] = (valid && with_w) ? ldw(w, e) : 0;
-  }
-#pragma unroll
-  for (int r = 0; r < kScRows; ++r) {
-    const bool m = k[r] >= 0 && mflag[k[r]];
-    const unsigned bal = __ballot_sync(0xffffffffu, m);
-    if (m) {
-      inM |= 1u << r;
-      const int at = nm + __popc(bal & ((1u << lane) - 1u));
-      if (at < kScMaxM) {
-        mk[at] = k[r];
-        mw[at] = wt[r];
-      }
+    for (int q = 0; q < kScUnroll; ++q) {
+      const int64_t e = b + 32 * q + lane;
+      u[q] = e < end ? __ldg(adj + e) : -1;
     }
-    nm += __popc(bal);
+#pragma unroll
+    for (int q = 0; q < kScUnroll; ++q) k[q] = u[q] >= 0 ? __ldg(cidm + u[q]) : 0;
+#pragma unroll
+    for (int q = 0; q < kScUnroll; ++q) {
+      const bool m = u[q] >= 0 && k[q] < 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, m);
+      if (m) {
+        const int at = nm + __popc(bal & ((1u << lane) - 1u));
+        if (at < kScMaxM) {
+          mk[at] = k[q] & 0x7fffffff;
+          mw[at] = with_w ? ldw(w, b + 32 * q + lane) : 0;
+        }
+      }
+      nm += __popc(bal);
+    }
   }
-  *nm_out = nm;
   __syncwarp();
+  return nm;
 }
 
 // Pass 1: the coarse degree of every lone vertex handled here (sdeg[v], else -1), and the
 // vertices left to the pre-merge flagged in dirty.
 template <typename WT>
-__global__ void __launch_bounds__(256) sc_count_k(int64_t n, const int32_t* __restrict__ cid,
-                                                  const unsigned char* __restrict__ mflag,
+__global__ void __launch_bounds__(256) sc_count_k(int64_t n, const int32_t* __restrict__ cidm,
                                                   const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                                                   const WT* __restrict__ w, int32_t* __restrict__ sdeg,
                                                   unsigned char* __restrict__ dirty) {
@@ -573,15 +597,11 @@ __global__ void __launch_bounds__(256) sc_count_k(int64_t n, const int32_t* __re
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
     const int64_t beg = off[v], end = off[v + 1];
-    if (mflag[cid[v]] || end - beg > 32 * kScRows) {
+    if (cidm[v] < 0) {  // a member of a merged group
       if (lane == 0) { sdeg[v] = -1; dirty[v] = 1; }
       continue;
     }
-    int32_t k[kScRows];
-    long long wt[kScRows];
-    unsigned inM;
-    int nm;
-    sc_load_list<WT>(beg, end, lane, adj, w, cid, mflag, false, k, wt, inM, s_mk[wid], s_mw[wid], &nm);
+    const int nm = sc_collect<WT>(beg, end, lane, adj, w, cidm, false, s_mk[wid], s_mw[wid]);
     if (nm > kScMaxM) {
       if (lane == 0) { sdeg[v] = -1; dirty[v] = 1; }
       continue;
@@ -597,8 +617,7 @@ __global__ void __launch_bounds__(256) sc_count_k(int64_t n, const int32_t* __re
 
 // Pass 2: the lists of the lone vertices counted in pass 1, at their coarse offsets.
 template <typename WT>
-__global__ void __launch_bounds__(256) sc_write_k(int64_t n, const int32_t* __restrict__ cid,
-                                                  const unsigned char* __restrict__ mflag,
+__global__ void __launch_bounds__(256) sc_write_k(int64_t n, const int32_t* __restrict__ cidm,
                                                   const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                                                   const WT* __restrict__ w, const int32_t* __restrict__ sdeg,
                                                   const int64_t* __restrict__ coff, int32_t* __restrict__ cadj,
@@ -613,13 +632,9 @@ __global__ void __launch_bounds__(256) sc_write_k(int64_t n, const int32_t* __re
   for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
     if (sdeg[v] < 0) continue;  // the same in every lane
     const int64_t beg = off[v], end = off[v + 1];
-    const int32_t x = cid[v];
+    const int32_t x = cidm[v];  // lone: no sign bit
     const int64_t o = coff[x];
-    int32_t k[kScRows];
-    long long wt[kScRows];
-    unsigned inM;
-    int nm;
-    sc_load_list<WT>(beg, end, lane, adj, w, cid, mflag, true, k, wt, inM, s_mk[wid], s_mw[wid], &nm);
+    const int nm = sc_collect<WT>(beg, end, lane, adj, w, cidm, true, s_mk[wid], s_mw[wid]);
     // distinct targets into merged groups: the lowest lane of each target sums it and
     // places it by its rank among the distinct targets
     const bool have = lane < nm;
@@ -638,33 +653,45 @@ __global__ void __launch_bounds__(256) sc_write_k(int64_t n, const int32_t* __re
     }
     __syncwarp();
     // the entries into lone vertices' clusters: position among them, plus the distinct
-    // merged targets below them
+    // merged targets below them; lane j < nd also counts the entries below target j
+    const int32_t myd = lane < nd ? s_dk[wid][lane] : INT_MIN;
+    int dbelow = 0;
     int mbefore = 0;
+    for (int64_t b = beg; b < end; b += 32 * kScUnroll) {
+      int32_t u[kScUnroll], k[kScUnroll];
+      long long wt[kScUnroll];
 #pragma unroll
-    for (int r = 0; r < kScRows; ++r) {
-      const unsigned balM = __ballot_sync(0xffffffffu, (inM >> r) & 1u);
-      if (k[r] >= 0 && !((inM >> r) & 1u)) {
-        int below = 0;
-        for (int j = 0; j < nd; ++j) below += s_dk[wid][j] < k[r];
-        const int64_t pos = (32 * r + lane) - (mbefore + __popc(balM & lower)) + below;
-        cadj[o + pos] = k[r];
-        cw[o + pos] = wt[r];
-        csrc[o + pos] = x;
+      for (int q = 0; q < kScUnroll; ++q) {
+        const int64_t e = b + 32 * q + lane;
+        u[q] = e < end ? __ldg(adj + e) : -1;
+        wt[q] = e < end ? ldw(w, e) : 0;
       }
-      mbefore += __popc(balM);
+#pragma unroll
+      for (int q = 0; q < kScUnroll; ++q) k[q] = u[q] >= 0 ? __ldg(cidm + u[q]) : 0;
+#pragma unroll
+      for (int q = 0; q < kScUnroll; ++q) {
+        const bool m = u[q] >= 0 && k[q] < 0;
+        const bool lone = u[q] >= 0 && k[q] >= 0;
+        const unsigned balM = __ballot_sync(0xffffffffu, m);
+        if (lone) {
+          int below = 0;
+          for (int j = 0; j < nd; ++j) below += s_dk[wid][j] < k[q];
+          const int64_t pos = (b + 32 * q - beg + lane) - (mbefore + __popc(balM & lower)) + below;
+          cadj[o + pos] = k[q];
+          cw[o + pos] = wt[q];
+          csrc[o + pos] = x;
+        }
+        mbefore += __popc(balM);
+        for (int j = 0; j < nd; ++j) {
+          const int c = __popc(__ballot_sync(0xffffffffu, lone && k[q] < s_dk[wid][j]));
+          if (lane == j) dbelow += c;
+        }
+      }
     }
-    // each distinct merged target: its rank plus the entries into lone clusters below it
-    for (int j = 0; j < nd; ++j) {
-      const int32_t dk = s_dk[wid][j];
-      int below = 0;
-#pragma unroll
-      for (int r = 0; r < kScRows; ++r)
-        below += __popc(__ballot_sync(0xffffffffu, k[r] >= 0 && !((inM >> r) & 1u) && k[r] < dk));
-      if (lane == 0) {
-        cadj[o + j + below] = dk;
-        cw[o + j + below] = s_dw[wid][j];
-        csrc[o + j + below] = x;
-      }
+    if (lane < nd) {
+      cadj[o + lane + dbelow] = myd;
+      cw[o + lane + dbelow] = s_dw[wid][lane];
+      csrc[o + lane + dbelow] = x;
     }
     __syncwarp();
   }
@@ -705,18 +732,19 @@ static void sc_by_weight(const GraphView& g, F f) {
   else f((const long long*)g.w);
 }
 
-void sparse_mark(const GraphView& g, const int32_t* lab, const int32_t* cid, unsigned char* mflag,
+void sparse_mark(const GraphView& g, const int32_t* lab, const int32_t* cid, unsigned char* mflag, int32_t* cidm,
                  unsigned char* dirty, int32_t* sdeg, int32_t* list, int* count, cudaStream_t s) {
   VC_CUDA(cudaMemsetAsync(mflag, 0, (size_t)g.n, s));
   VC_CUDA(cudaMemsetAsync(count, 0, sizeof(int), s));
   const int grid = grid_for(g.n, 256, kSMs * 8);
   sc_merged_k<<<grid, 256, 0, s>>>(g.n, lab, cid, mflag);
+  sc_pack_k<<<grid, 256, 0, s>>>(g.n, cid, mflag, cidm);
   sc_by_weight(g, [&](auto wp) {
     using WT = std::remove_cv_t<std::remove_pointer_t<decltype(wp)>>;
-    sc_count_k<WT><<<grid_for(g.n, 8, kSMs * 16), 256, 0, s>>>(g.n, cid, mflag, g.off, g.adj, wp, sdeg, dirty);
+    sc_count_k<WT><<<grid_for(g.n, 8, kSMs * 16), 256, 0, s>>>(g.n, cidm, g.off, g.adj, wp, sdeg, dirty);
   });
   sc_list_k<<<grid, 256, 0, s>>>(g.n, dirty, list, count);
-  count_launch(3);
+  count_launch(4);
   VC_CHECK_LAUNCH();
 }
 
@@ -728,12 +756,12 @@ static void sparse_finish_degrees(const GraphView& g, const int32_t* cid, const 
   VC_CHECK_LAUNCH();
 }
 
-static void sparse_copy(const GraphView& g, const int32_t* cid, const unsigned char* mflag, const int32_t* sdeg,
-                        const int64_t* coff, int32_t* cadj, long long* cw, int32_t* csrc, cudaStream_t s) {
+static void sparse_copy(const GraphView& g, const int32_t* cidm, const int32_t* sdeg, const int64_t* coff,
+                        int32_t* cadj, long long* cw, int32_t* csrc, cudaStream_t s) {
   sc_by_weight(g, [&](auto wp) {
     using WT = std::remove_cv_t<std::remove_pointer_t<decltype(wp)>>;
-    sc_write_k<WT><<<grid_for(g.n, 8, kSMs * 16), 256, 0, s>>>(g.n, cid, mflag, g.off, g.adj, wp, sdeg, coff, cadj,
-                                                               cw, csrc);
+    sc_write_k<WT><<<grid_for(g.n, 8, kSMs * 16), 256, 0, s>>>(g.n, cidm, g.off, g.adj, wp, sdeg, coff, cadj, cw,
+                                                               csrc);
   });
   count_launch();
   VC_CHECK_LAUNCH();
@@ -988,7 +1016,7 @@ void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch
   cluster_place_k<<<gc, 256, 0, s>>>(c, cbase, coff, seg_key, seg_val, cadj, cw, csrc, sp ? sp->clean : nullptr);
   count_launch();
   VC_CHECK_LAUNCH();
-  if (sp) sparse_copy(g, cid, sp->mflag, sp->sdeg, coff, cadj, cw, csrc, s);
+  if (sp) sparse_copy(g, sp->cidm, sp->sdeg, coff, cadj, cw, csrc, s);
   VC_CUDA(cudaMemcpyAsync(nnz_dev, coff + c, sizeof(long long), cudaMemcpyDeviceToDevice, s));
 }
 

@@ -17,6 +17,10 @@ namespace vc {
 // Records the message of the last failure on this thread (viecut_last_error).
 void set_last_error(const std::string& msg);
 
+// Host-side fault injection for tests (viecut_debug_fail_device_allocs): true when the
+// next device allocation is to fail as if cudaMalloc had run out of memory.
+bool take_injected_alloc_failure();
+
 // ------------------------------------------------------------- device buffers
 struct Buf {
   void* p = nullptr;
@@ -34,6 +38,8 @@ struct Buf {
     if (bytes == 0) bytes = 16;
     if (bytes > cap) {
       release();
+      if (take_injected_alloc_failure())
+        throw Error{VIECUT_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed (injected)"};
       cudaError_t e = cudaMalloc(&p, bytes);
       if (e != cudaSuccess) {
         p = nullptr;
@@ -294,7 +300,7 @@ struct Workspace {
   // many entries into them).  True when those are at most half of g's vertices; then
   // dbins holds their bins.
   Bins dbins;
-  Buf smflag, sdirty, sdeg, sclean, sdlist, dsl, drl, dml, dbl, dgl, dbail, dcounts;
+  Buf smflag, scidm, sdirty, sdeg, sclean, sdlist, dsl, drl, dml, dbl, dgl, dbail, dcounts;
   bool mark_sparse(const GraphView& g, const int32_t* labels, const int32_t* cid) {
     const int64_t n = g.n;
     dbins.small_list = dsl.ensure_n<int32_t>(n);
@@ -305,8 +311,8 @@ struct Workspace {
     dbins.bail_list = dbail.ensure_n<int32_t>(n);
     dbins.counts = dcounts.ensure_n<int>(8);
     int32_t* list = sdlist.ensure_n<int32_t>(n);
-    sparse_mark(g, labels, cid, smflag.ensure_n<unsigned char>(n), sdirty.ensure_n<unsigned char>(n),
-                sdeg.ensure_n<int32_t>(n), list, dbins.counts + 6, s);
+    sparse_mark(g, labels, cid, smflag.ensure_n<unsigned char>(n), scidm.ensure_n<int32_t>(n),
+                sdirty.ensure_n<unsigned char>(n), sdeg.ensure_n<int32_t>(n), list, dbins.counts + 6, s);
     bins_build(g, dbins, s, list, dbins.counts + 6);
     int ndirty = 0;
     read_bins(dbins, &ndirty);
@@ -450,7 +456,7 @@ struct Workspace {
         gs.hpos = hpos.ensure_n<long long>(GP + 1);
         gs.hist = hist.ensure_n<long long>(radix_hist_elems(GP));
       }
-      const SparseCtx sp{smflag.as<unsigned char>(), sdeg.as<int32_t>(), sclean.as<unsigned char>()};
+      const SparseCtx sp{scidm.as<int32_t>(), sdeg.as<int32_t>(), sclean.as<unsigned char>()};
       cluster_merge(g, cid_out, cs, ccount, c, cbase, cur, sk, sv, co, ca, cwp, csp, &st()->nnz,
                     h_counters->maxt > kMergeMax, 2 * c >= g.n, ng ? &gs : nullptr, cs.cnt, &ctr()->blist_n, s,
                     sparse ? &sp : nullptr);

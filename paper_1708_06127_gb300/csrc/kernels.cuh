@@ -197,11 +197,11 @@ void cluster_stats(int64_t n, const int32_t* ccount, int* maxt, long long* pairs
 // cluster_merge expects pairs from the listed vertices only (the rest with no pairs) and
 // writes the handled vertices' lists itself; clean holds at least c bytes.
 struct SparseCtx {
-  const unsigned char* mflag;
+  const int32_t* cidm;  // cluster ids, sign bit set for members of merged groups (n)
   const int32_t* sdeg;
   unsigned char* clean;
 };
-void sparse_mark(const GraphView& g, const int32_t* lab, const int32_t* cid, unsigned char* mflag,
+void sparse_mark(const GraphView& g, const int32_t* lab, const int32_t* cid, unsigned char* mflag, int32_t* cidm,
                  unsigned char* dirty, int32_t* sdeg, int32_t* list, int* count, cudaStream_t s);
 void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch& cs, int32_t* ccount, int64_t c,
                    long long* cbase, long long* cursor, int32_t* seg_key, long long* seg_val, int64_t* coff,

@@ -319,6 +319,7 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
 // group it already holds the next vertex's ids and the offsets of the one after.
 
 constexpr int kEmitBailKeys = 64;
+constexpr int kLpBailKeys = 16;
 
 // Neighbour ids (and weights) of one list in registers.
 template <int S>
@@ -416,7 +417,9 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
                                                         const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                         const int32_t* __restrict__ lab, int32_t* __restrict__ lab_out,
                                                         const unsigned long long* __restrict__ hv,
-                                                        const unsigned char* __restrict__ vact) {
+                                                        const unsigned char* __restrict__ vact,
+                                                        int32_t* __restrict__ bail_list,
+                                                        int* __restrict__ bail_count) {
   const int lane = threadIdx.x & 31, glane = lane & (G - 1), gi = lane / G;
   const unsigned gmask = group_mask<G>(lane);
   constexpr int kPer = 32 / G;  // vertices per warp
@@ -485,6 +488,11 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
         if (bs > left) L.todo = 0;
       }
     }
+    // with a bail list, a vertex still undecided after kLpBailKeys labels (a list whose
+    // neighbours carry many different labels, where a step per label costs slots x
+    // compares) is handed to the hash-table kernel instead
+    int visited = 0;
+    bool bailed = false;
     reg_visit<WT, ACC, G, S>(L, gmask, [&](int32_t kk, ACC t) {
       left -= t;
       if (bl < 0 || t > bs) {
@@ -496,9 +504,17 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
         const unsigned long long h = __ldg(hv + kk);
         if (h > bh || (h == bh && kk < bl)) { bh = h; bl = kk; }
       }
-      return bs > left;
+      if (bs > left) return true;
+      if (bail_list && ++visited >= kLpBailKeys) {
+        bailed = true;
+        return true;
+      }
+      return false;
     });
-    if (mine && d > 0 && glane == 0) lab_out[v] = bl;
+    if (mine && d > 0 && glane == 0) {
+      if (bailed) bail_list[atomicAdd(bail_count, 1)] = (int32_t)v;
+      else lab_out[v] = bl;
+    }
   });
 }
 
@@ -589,26 +605,54 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restr
   });
 }
 
+template <int CAP, typename ACC>
+constexpr size_t warp_smem();
+template <typename F>
+void set_smem(F kfn, size_t bytes);
+
+// The vertices a register-class kernel handed on: a warp per vertex with a hash table of
+// CAP slots in shared memory (the bail list and its count are read on the device).
+template <typename WT, typename ACC, bool FIRST, int CAP>
+void launch_lp_bailed(const GraphView& g, const Bins& b, const WT* w, const int32_t* lab, int32_t* lab_out,
+                      const unsigned long long* hv, cudaStream_t s) {
+  constexpr size_t smem = warp_smem<CAP, ACC>();
+  auto kfn = lp_warp_k<WT, ACC, FIRST, CAP, true>;
+  set_smem(kfn, smem);
+  kfn<<<kSMs * 2, kAggThreads, smem, s>>>(0, b.bail_list, b.counts + 7, g.off, g.adj, w, lab, lab_out, hv, g.vact);
+  count_launch();
+  VC_CHECK_LAUNCH();
+}
+
+// Register classes.  In rounds after the first, mid-class vertices (129..512 entries, 16
+// slots per lane, where a step per distinct label is costly) with many distinct labels
+// go on to the hash-table kernel (the bail list and counts[7] are free during label
+// propagation: the pre-merge uses them later).  Lists of at most 128 entries keep the
+// walk: four slots per lane make each step cheap, and measured, the table kernel did not
+// beat it there.
 template <typename WT, typename ACC, bool FIRST>
 void launch_lp_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t* lab, int32_t* lab_out,
                    const unsigned long long* hv, cudaStream_t s) {
+  int32_t* bl = FIRST ? nullptr : b.bail_list;
+  int* bc = FIRST ? nullptr : b.counts + 7;
   if (b.h_small > 0) {
     lp_reg_k<WT, ACC, FIRST, 16, 4><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
-        b.small_list, b.counts + 4, g.off, g.adj, w, lab, lab_out, hv, g.vact);
+        b.small_list, b.counts + 4, g.off, g.adj, w, lab, lab_out, hv, g.vact, nullptr, nullptr);
     count_launch();
     VC_CHECK_LAUNCH();
   }
   if (b.h_reg > 0) {
     lp_reg_k<WT, ACC, FIRST, 32, 4><<<grid_for(b.h_reg, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
-        b.reg_list, b.counts + 5, g.off, g.adj, w, lab, lab_out, hv, g.vact);
+        b.reg_list, b.counts + 5, g.off, g.adj, w, lab, lab_out, hv, g.vact, nullptr, nullptr);
     count_launch();
     VC_CHECK_LAUNCH();
   }
   if (b.h_mid > 0) {
+    if (bc) VC_CUDA(cudaMemsetAsync(bc, 0, sizeof(int), s));
     lp_reg_k<WT, ACC, FIRST, 32, kMidMaxDeg / 32><<<grid_for(b.h_mid, kWarpsPerBlock, kSMs * 16), kAggThreads, 0, s>>>(
-        b.mid_list, b.counts + 0, g.off, g.adj, w, lab, lab_out, hv, g.vact);
+        b.mid_list, b.counts + 0, g.off, g.adj, w, lab, lab_out, hv, g.vact, bl, bc);
     count_launch();
     VC_CHECK_LAUNCH();
+    if (bc) launch_lp_bailed<WT, ACC, FIRST, kMidCap>(g, b, w, lab, lab_out, hv, s);
   }
 }
 

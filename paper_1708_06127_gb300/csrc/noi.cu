@@ -457,14 +457,18 @@ __device__ __forceinline__ void noi_round_warp(int64_t lo, int64_t hi, const int
     }
     const int C = warp_argmax_vi(bv, bc, &best);
     const int64_t k = (int64_t)C * 32 + lane;
+    // the list bounds of the chunk's vertices load beside their attachments, so the
+    // chosen vertex's list can be read as soon as it is known
+    const int64_t kb = k < n ? __ldg(off + lo + k) : 0, ke = k < n ? __ldg(off + lo + k + 1) : 0;
     const long long rv = (k < n && !seen.test(lo + k)) ? r[lo + k - sb] : -1;
     const int xl = warp_argmax_vi(rv, (int)k, &best);
     const int64_t x = lo + xl;
+    const int64_t xb = __shfl_sync(0xffffffffu, kb, xl & 31), xe = __shfl_sync(0xffffffffu, ke, xl & 31);
     if (k == xl) seen.set(x);
     warp_argmax_vi(k == xl ? -1 : rv, (int)k, &best);  // the chunk's maximum without x
     if (lane == 0) cmax[C] = best;
     __syncwarp();
-    for (int64_t e = off[x] + lane; e < off[x + 1]; e += 32) {
+    for (int64_t e = xb + lane; e < xe; e += 32) {
       const int y = adj[e];
       if (seen.test(y)) continue;
       const long long c = (long long)w[e];

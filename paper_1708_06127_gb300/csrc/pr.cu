@@ -238,13 +238,19 @@ void pr_pass_a(const GraphView& g, const int32_t* partner, const long long* pw, 
 }
 
 // Conditions 3 and 4 on mutual partner pairs v < w = p(v), p(w) = v, through the
-// common neighbourhood (binary search of N(v)'s entries in w's sorted list).
+// common neighbourhood (binary search of N(v)'s entries in w's sorted list; a list of at
+// most kPrBStage ids is first copied into the warp's shared memory, so the searches
+// there wait on no global loads).
+constexpr int kPrBStage = 1024;
 template <typename WT>
-__global__ void pr_b_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
-                       const WT* __restrict__ w, const int32_t* __restrict__ partner,
-                       const long long* __restrict__ pw, const long long* __restrict__ deg, const DevState* st,
-                       int32_t* __restrict__ labels, int* changed, BatchCtx bc) {
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256) pr_b_k(int64_t n, const int64_t* __restrict__ off,
+                                              const int32_t* __restrict__ adj, const WT* __restrict__ w,
+                                              const int32_t* __restrict__ partner, const long long* __restrict__ pw,
+                                              const long long* __restrict__ deg, const DevState* st,
+                                              int32_t* __restrict__ labels, int* changed, BatchCtx bc) {
+  __shared__ int32_t s_list[8][kPrBStage];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t* sl = s_list[wid];
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
     long long lam;
@@ -254,17 +260,31 @@ __global__ void pr_b_k(int64_t n, const int64_t* __restrict__ off, const int32_t
     const int64_t vb = off[v], ve = off[v + 1], pb = off[p], pe = off[p + 1];
     if (ve - vb < 2 || pe - pb < 2) continue;
     const long long cvw = pw[v], dv = deg[v], dp = deg[p];
+    const bool staged = pe - pb <= kPrBStage;
+    if (staged)
+      for (int64_t i = lane; i < pe - pb; i += 32) sl[i] = adj[pb + i];
+    __syncwarp();
     bool pr3 = false;
     long long sum = 0;
     for (int64_t e = vb + lane; e < ve; e += 32) {
       const int u = adj[e];
       int64_t lo = pb, hi = pe;
-      while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (adj[mid] < u) lo = mid + 1;
-        else hi = mid;
+      if (staged) {
+        int l = 0, h = (int)(pe - pb);
+        while (l < h) {
+          const int mid = (l + h) >> 1;
+          if (sl[mid] < u) l = mid + 1;
+          else h = mid;
+        }
+        lo = pb + l;
+      } else {
+        while (lo < hi) {
+          int64_t mid = (lo + hi) >> 1;
+          if (adj[mid] < u) lo = mid + 1;
+          else hi = mid;
+        }
       }
-      if (lo < pe && adj[lo] == u) {
+      if (lo < pe && (staged ? sl[lo - pb] : adj[lo]) == u) {
         const long long cvu = (long long)w[e], cwu = (long long)w[lo];
         if (dv <= 2 * (cvw + cvu) && dp <= 2 * (cvw + cwu)) pr3 = true;
         sum += cvu < cwu ? cvu : cwu;
@@ -277,6 +297,7 @@ __global__ void pr_b_k(int64_t n, const int64_t* __restrict__ off, const int32_t
       if (changed) atomicOr(changed, 1);
       if (bc.gid) bc.gchanged[bc.gid[v]] = 1;
     }
+    __syncwarp();  // the staged list is overwritten by the warp's next pair
   }
 }
 

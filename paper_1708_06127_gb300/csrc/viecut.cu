@@ -21,6 +21,20 @@ std::atomic<unsigned long long> g_launches{0};
 static thread_local std::string t_last_error;
 void set_last_error(const std::string& msg) { t_last_error = msg; }
 
+// Injected allocation failures: the allocations after the next g_fail_skip ones fail,
+// g_fail_count of them (process-wide, every thread).
+static std::atomic<long long> g_fail_skip{0}, g_fail_count{0};
+bool take_injected_alloc_failure() {
+  if (g_fail_count.load() <= 0) return false;
+  long long sk = g_fail_skip.load();
+  while (sk > 0)
+    if (g_fail_skip.compare_exchange_weak(sk, sk - 1)) return false;
+  long long c = g_fail_count.load();
+  while (c > 0)
+    if (g_fail_count.compare_exchange_weak(c, c - 1)) return true;
+  return false;
+}
+
 __global__ void set_n_k(DevState* st, long long n) { st->n = n; }
 
 __global__ void validate_k(int64_t n, int64_t m, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
@@ -419,13 +433,21 @@ int viecut_struct_sizes(int64_t* sizes, int32_t count) {
   const int64_t known[] = {(int64_t)sizeof(viecut_opts),        (int64_t)sizeof(viecut_stats),
                            (int64_t)sizeof(viecut_step),        (int64_t)sizeof(viecut_graph_desc),
                            (int64_t)sizeof(viecut_batch_stats), (int64_t)sizeof(viecut_server_opts),
-                           (int64_t)sizeof(viecut_server_stats)};
+                           (int64_t)sizeof(viecut_server_stats), (int64_t)sizeof(viecut_request_info)};
   const int32_t nk = (int32_t)(sizeof(known) / sizeof(known[0]));
   if (count > 0 && !sizes) return VIECUT_EINVAL;
   for (int32_t i = 0; i < count && i < nk; ++i) sizes[i] = known[i];
   return nk;
 }
 int64_t viecut_launch_count(void) { return (int64_t)vc::g_launches; }
+
+int viecut_debug_fail_device_allocs(int64_t after, int64_t count) {
+  if (after < 0 || count < 0) return VIECUT_EINVAL;
+  vc::g_fail_count.store(0);
+  vc::g_fail_skip.store(after);
+  vc::g_fail_count.store(count);
+  return VIECUT_OK;
+}
 
 int viecut_opts_init(viecut_opts* o) {
   if (!o) return VIECUT_EINVAL;

@@ -43,12 +43,12 @@ def test_binding_structs_match_the_library(lib):
     """Every structure the binding restates has the library's size (a field added on
     one side only would shift every later field)."""
     import ctypes
-    sizes = np.zeros(8, np.int64)
-    n = vc.lib().viecut_struct_sizes(sizes.ctypes.data, 8)
-    assert n == 7
+    sizes = np.zeros(9, np.int64)
+    n = vc.lib().viecut_struct_sizes(sizes.ctypes.data, 9)
+    assert n == 8
     mine = [vc.viecut_opts, vc.viecut_stats, vc.viecut_step, vc.viecut_graph_desc, vc.viecut_batch_stats,
-            vc.viecut_server_opts, vc.viecut_server_stats]
-    assert sizes[:7].tolist() == [ctypes.sizeof(t) for t in mine]
+            vc.viecut_server_opts, vc.viecut_server_stats, vc.viecut_request_info]
+    assert sizes[:8].tolist() == [ctypes.sizeof(t) for t in mine]
     assert vc.lib().viecut_struct_sizes(None, 1) == vc.VIECUT_EINVAL
 
 
@@ -120,3 +120,11 @@ def test_no_device_fails_loudly(lib):
     with pytest.raises(vc.ViecutError) as e:
         vc.viecut_create(off, adj, 2, 2, np.array([3, 3], np.int32))
     assert e.value.code == vc.VIECUT_ECUDA
+
+
+def test_fault_injection_arguments(lib):
+    """The allocation-failure hook refuses negative arguments; count 0 switches it off
+    (no device is touched)."""
+    assert vc.lib().viecut_debug_fail_device_allocs(-1, 1) == vc.VIECUT_EINVAL
+    assert vc.lib().viecut_debug_fail_device_allocs(0, -1) == vc.VIECUT_EINVAL
+    assert vc.lib().viecut_debug_fail_device_allocs(0, 0) == vc.VIECUT_OK
