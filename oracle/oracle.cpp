@@ -19,9 +19,12 @@
 //       SplitMix64 output function (Steele, Lea, Flood 2014), G = 0x9e3779b97f4a7c15;
 //       the paper breaks ties uniformly at random.  mix64 is a bijection, so (S, H)
 //       totally orders distinct labels.
-//  [R3] A fixed number of rounds, no convergence test, no first-round restriction
-//       (Sec. 4.1 notes the restriction is not used in practice); the correcting
-//       step is off unless asked for ([R10]), as in the paper's ER runs.
+//  [R3] A fixed number of rounds, no first-round restriction (Sec. 4.1 notes the
+//       restriction is not used in practice); the correcting step is off unless asked
+//       for ([R10]), as in the paper's ER runs.  Optionally (converge) the rounds stop
+//       early, as in the configuration VieCut25 of App. D (Table 3): after a round in
+//       which at most 1/10000 of the vertices changed their label (changed * 10000 <=
+//       n, n the current vertex count), no further round runs.
 //  [R4] Cluster ids are ranks of the final label values, ascending.
 //  [R5] Padberg-Rinaldi test 2 marks only the edge to each vertex's designated
 //       partner p(v) = argmax over neighbours u of (c(v,u), -u); marking every
@@ -354,11 +357,30 @@ bool apply(Run& run, Graph& g, const int32_t* labels, int32_t kind, bool correct
   return run.lambda_hat > 0;
 }
 
+// The label-propagation rounds of one level from the identity labelling: lp_iters
+// rounds, or ([R3], converge) fewer when a round changes at most 1/10000 of the labels
+// (VieCut25, App. D).  Returns the number of rounds run; lab holds the final labels.
+int32_t lp_level(const Graph& g, uint64_t key, int32_t lp_iters, bool converge, std::vector<int32_t>& lab,
+                 std::vector<int32_t>& nxt) {
+  lab.resize(g.n);
+  nxt.resize(g.n);
+  for (int64_t v = 0; v < g.n; ++v) lab[v] = (int32_t)v;
+  for (int32_t r = 0; r < lp_iters; ++r) {
+    lp_round(g, lab.data(), key, nxt.data());
+    int64_t changed = 0;
+    for (int64_t v = 0; v < g.n; ++v) changed += nxt[v] != lab[v];
+    lab.swap(nxt);
+    if (converge && changed * 10000 <= g.n) return r + 1;
+  }
+  return lp_iters;
+}
+
 // Algorithm 1 (Appendix A) in the deterministic variant: levels of label
 // propagation + cluster contraction + Padberg-Rinaldi runs while more than n0
 // vertices remain, then Nagamochi-Ono-Ibaraki on the kernel; the bound is the
 // smallest trivial cut seen (Sec. 4, "Throughout our algorithm we maintain ...").
-void viecut(Graph g, uint64_t seed, int32_t lp_iters, int64_t n0, int32_t pr_runs_max, bool correct, Run& run) {
+void viecut(Graph g, uint64_t seed, int32_t lp_iters, int64_t n0, int32_t pr_runs_max, bool correct, bool converge,
+            Run& run) {
   int64_t n = g.n;
   run.cur.resize(n);
   run.side.assign(n, 0);
@@ -373,13 +395,7 @@ void viecut(Graph g, uint64_t seed, int32_t lp_iters, int64_t n0, int32_t pr_run
   while (g.n > n0) {
     int64_t n_start = g.n;
     uint64_t key = level_key(seed, run.level);
-    lab.resize(g.n);
-    nxt.resize(g.n);
-    for (int64_t v = 0; v < g.n; ++v) lab[v] = (int32_t)v;
-    for (int32_t r = 0; r < lp_iters; ++r) {
-      lp_round(g, lab.data(), key, nxt.data());
-      lab.swap(nxt);
-    }
+    lp_level(g, key, lp_iters, converge, lab, nxt);
     if (!apply(run, g, lab.data(), 1, correct)) return;
     for (int32_t runi = 0; runi < pr_runs_max; ++runi) {
       bool any = false;
@@ -442,6 +458,17 @@ void orc_lp_round(int64_t n, const int64_t* off, const int32_t* adj, const int64
   lp_round(g, lab_in, key, lab_out);
 }
 
+// One level's rounds from the identity (lp_level): lab_out[n] the final labels; returns
+// the rounds run.
+int32_t orc_lp_level(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* w, uint64_t key,
+                     int32_t lp_iters, int32_t converge, int32_t* lab_out) {
+  Graph g = load(n, off, adj, w, 8);
+  std::vector<int32_t> lab, nxt;
+  int32_t r = lp_level(g, key, lp_iters, converge != 0, lab, nxt);
+  memcpy(lab_out, lab.data(), sizeof(int32_t) * n);
+  return r;
+}
+
 // Contracts by labels.  Outputs: cid[n], coarse n in *cn, coarse CSR in coff (cap
 // n+1), cadj / cw (cap nnz).  Returns the coarse nnz.
 int64_t orc_contract(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* w,
@@ -493,10 +520,10 @@ int64_t orc_noi_round(int64_t n, const int64_t* off, const int32_t* adj, const i
 int orc_viecut(int64_t n, const int64_t* off, const int32_t* adj, const void* w, int32_t wbytes,
                uint64_t seed, int32_t lp_iters, int64_t n0, int32_t pr_runs_max,
                int64_t* cut, uint64_t* side_bits, orc_step* trace, int64_t trace_cap,
-               int64_t* trace_len, int32_t correct) {
+               int64_t* trace_len, int32_t correct, int32_t converge) {
   if (n < 2) return -1;
   Run run;
-  viecut(load(n, off, adj, w, wbytes), seed, lp_iters, n0, pr_runs_max, correct != 0, run);
+  viecut(load(n, off, adj, w, wbytes), seed, lp_iters, n0, pr_runs_max, correct != 0, converge != 0, run);
   *cut = run.lambda_hat;
   bool flip = run.side[0] != 0;
   int64_t words = (n + 63) / 64;

@@ -551,3 +551,68 @@ def test_planted_golden_file_is_consistent():
     assert all(a >= b for a, b in zip(lh, lh[1:])) and lh[-1] == ref["cut"]
     assert ref["cut"] >= planted_lambda(g, p["blocks"], p["block_n"])
     assert 0 < ref["side_popcount"] < g.n
+
+
+# ------------------------------------------- VieCut25 convergence stop (App. D)
+def _level_by_hand(g, seed, level, cap):
+    """Rounds of one level written out here: run rounds from the identity, count the
+    labels each round changes, stop after the first round with changed * 10000 <= n (or
+    after cap rounds).  Returns (labels, rounds)."""
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    key = oracle.level_key(seed, level)
+    lab = np.arange(G.n, dtype=np.int32)
+    for r in range(1, cap + 1):
+        nxt = oracle.lp_round(G, lab, key)
+        changed = int((nxt != lab).sum())
+        lab = nxt
+        if changed * 10000 <= G.n:
+            return lab, r
+    return lab, cap
+
+
+def cliques_and_edge(k=4000):
+    """k disjoint K5 (each settles on one label after a few rounds) and one edge, whose
+    two ends swap labels every round: n = 5k + 2, so from the round in which the cliques
+    are settled on, 2 of n labels change per round (the stop fires once 2 * 10000 <= n)."""
+    E = [(5 * c + a, 5 * c + b, 1) for c in range(k) for a in range(5) for b in range(a + 1, 5)]
+    E.append((5 * k, 5 * k + 1, 1))
+    return gg.from_edges(5 * k + 2, E, f"{k}xK5+edge")
+
+
+CONVERGE_GRAPHS = [
+    lambda: H.complete(5),                      # settles on one label after a few rounds
+    two_triangles,                              # oscillates with period 2: never stops early
+    lambda: gg.workload_rhg_small(3),           # n = 16,384: would stop at <= 1 change
+    cliques_and_edge,                           # stops with 2 changes per round left
+]
+
+
+@pytest.mark.parametrize("make", CONVERGE_GRAPHS)
+def test_converge_stop_rounds_and_labels(make):
+    g = make()
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    for seed, cap in ((1, 25), (2, 5)):
+        want, rounds = _level_by_hand(g, seed, 0, cap)
+        got, r = oracle.lp_level(G, oracle.level_key(seed, 0), cap, True)
+        assert r == rounds and np.array_equal(got, want), (g.name, seed)
+        fixed, r2 = oracle.lp_level(G, oracle.level_key(seed, 0), cap, False)
+        assert r2 == cap
+
+
+def test_converge_stop_whole_method():
+    """One level (n0 just below n): the method with the stop equals the method with the
+    fixed round count that the stop reaches; on the oscillating triangles every round
+    runs."""
+    for g, seed in [(gg.workload_rhg_small(3), 1), (gg.core_lcc(gg.rhg(1 << 15, 16, 4), 0), 2)]:
+        _, r = _level_by_hand(g, seed, 0, 25)
+        conv = run(g, seed=seed, lp_iters=25, n0=g.n - 1, converge=True)
+        fixed = run(g, seed=seed, lp_iters=r, n0=g.n - 1)
+        assert conv.cut == fixed.cut and conv.trace == fixed.trace
+        assert np.array_equal(conv.side_bits, fixed.side_bits)
+    tri = two_triangles()
+    _, r = _level_by_hand(tri, 1, 0, 25)
+    assert r == 25
+    ce = cliques_and_edge()
+    lab, r = _level_by_hand(ce, 1, 0, 25)
+    assert 2 <= r < 25 and int((oracle.lp_round(oracle.as_csr64(ce.offsets, ce.adj, ce.w), lab,
+                                                 oracle.level_key(1, 0)) != lab).sum()) == 2
