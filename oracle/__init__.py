@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
 def _declare_viecut(lib):
     vp, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
     lib.orc_viecut.restype = ctypes.c_int
-    lib.orc_viecut.argtypes = [i64, vp, vp, vp, i32, u64, i32, i64, i32, vp, vp, vp, i64, vp, i32, i32]
+    lib.orc_viecut.argtypes = [i64, vp, vp, vp, i32, u64, i32, i64, i32, vp, vp, vp, i64, vp, i32, i32, i32]
 
 
 def load_variant(path: str):
@@ -68,7 +68,9 @@ def _load():
             lib.orc_lp_round.restype = None
             lib.orc_lp_round.argtypes = [i64, vp, vp, vp, vp, u64, vp]
             lib.orc_lp_level.restype = i32
-            lib.orc_lp_level.argtypes = [i64, vp, vp, vp, u64, i32, i32, vp]
+            lib.orc_lp_level.argtypes = [i64, vp, vp, vp, u64, i32, i32, vp, i32]
+            lib.orc_lp_round_async.restype = None
+            lib.orc_lp_round_async.argtypes = [i64, vp, vp, vp, vp, u64, i32, i64, i64, i32]
             lib.orc_contract.restype = i64
             lib.orc_contract.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             for name in ("orc_pr_pass_a", "orc_pr_pass_b", "orc_noi_round"):
@@ -130,12 +132,23 @@ def lp_round(g: CsrGraph, labels, key: int) -> np.ndarray:
     return out
 
 
-def lp_level(g: CsrGraph, key: int, lp_iters: int, converge: bool):
-    """The rounds of one level from the identity labelling: (final labels, rounds run)."""
+def lp_level(g: CsrGraph, key: int, lp_iters: int, converge: bool, lp_async: int = 0):
+    """The rounds of one level from the identity labelling: (final labels, rounds run).
+    lp_async: 0 synchronous, 1 asynchronous [R11], 2 asynchronous with the first round's
+    restriction."""
     out = np.empty(g.n, np.int32)
     r = _load().orc_lp_level(g.n, g.offsets.ctypes.data, g.adj.ctypes.data, g.w.ctypes.data, key & (2**64 - 1),
-                             lp_iters, 1 if converge else 0, out.ctypes.data)
+                             lp_iters, 1 if converge else 0, out.ctypes.data, int(lp_async))
     return out, int(r)
+
+
+def lp_round_async(g: CsrGraph, labels, key: int, rnd: int, blk: int = 128, waves: int = 8,
+                   restrict_first: bool = False) -> np.ndarray:
+    """One asynchronous round [R11] from `labels` (blocks of blk ids in `waves` waves)."""
+    lab = np.array(labels, dtype=np.int32)
+    _load().orc_lp_round_async(g.n, g.offsets.ctypes.data, g.adj.ctypes.data, g.w.ctypes.data, lab.ctypes.data,
+                               key & (2**64 - 1), rnd, blk, waves, 1 if restrict_first else 0)
+    return lab
 
 
 def contract(g: CsrGraph, labels):
@@ -195,11 +208,13 @@ class Result:
 
 def viecut(offsets, adj, w, seed: int = 1, lp_iters: int = 2, n0: int = 10000,
            pr_runs_max: int = 8, trace_cap: int = 4096, correct: bool = False, converge: bool = False,
-           _lib=None) -> Result:
+           lp_async: int = 0, _lib=None) -> Result:
     """The whole deterministic method.  `w` may be int32 or int64.  correct: the
     correcting step on every label-propagation clustering (reading [R10]).  converge:
     at most lp_iters rounds per level, ending after a round in which at most 1/10000 of
-    the vertices changed their label (the VieCut25 configuration, App. D).  `_lib`
+    the vertices changed their label (the VieCut25 configuration, App. D).  lp_async: 1
+    asynchronous rounds in shuffled 128-vertex blocks and eight waves [R11], 2 the same
+    with the first round's restriction.  `_lib`
     (tests only) runs another build of oracle.cpp with the same entry points, e.g. one
     with a mistake planted to show that a pin catches it."""
     off, po = _c(offsets, np.int64)
@@ -215,7 +230,7 @@ def viecut(offsets, adj, w, seed: int = 1, lp_iters: int = 2, n0: int = 10000,
     lib = _lib if _lib is not None else _load()
     rc = lib.orc_viecut(n, po, pa, pw, wbytes, seed & (2**64 - 1), lp_iters, n0, pr_runs_max,
                             ctypes.byref(cut), bits.ctypes.data, tr, trace_cap, ctypes.byref(tl),
-                            1 if correct else 0, 1 if converge else 0)
+                            1 if correct else 0, 1 if converge else 0, int(lp_async))
     if rc != 0:
         raise ValueError(f"oracle rejected the input (code {rc})")
     steps = [(tr[k].kind, tr[k].level, tr[k].n, tr[k].nnz, tr[k].lambda_hat)

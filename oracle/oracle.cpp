@@ -127,6 +127,54 @@ void lp_round(const Graph& g, const int32_t* lab_in, uint64_t key, int32_t* lab_
   }
 }
 
+// [R11] Asynchronous label propagation (optional): the paper visits the vertices in a
+// random order and updates labels in place (Sec. 4.1), trading randomness for locality
+// by shuffling blocks of consecutive vertex ids and traversing the shuffled blocks one
+// after the other (Sec. 4.3; 128-vertex blocks, Sec. 5 setup).  Reading, deterministic:
+// the n vertices form ceil(n / blk) blocks of blk consecutive ids; the blocks are
+// ordered by the key mix64(key ^ mix64(round + 1) ^ b) of block b (a permutation drawn
+// from the level key); the ordered blocks are cut into `waves` consecutive groups of
+// equal count (the first B mod waves groups one block longer); the waves run one after
+// another, every vertex of a wave choosing its label from the labels as they stand
+// when the wave starts (updates of earlier waves of the round included), all vertices
+// of a wave at once.  With waves = 1 this is the synchronous round [R1].  The first
+// round's restriction (Sec. 4.1: a vertex does not change its label once another vertex
+// moved to its block) is applied across waves: in round 0, a vertex keeps its own label
+// when a vertex of an earlier wave took that label.
+void lp_round_async(const Graph& g, std::vector<int32_t>& lab, uint64_t key, int32_t round, int64_t blk,
+                    int64_t waves, bool restrict_first) {
+  const int64_t nb = (g.n + blk - 1) / blk;
+  std::vector<std::pair<uint64_t, int64_t>> order(nb);
+  const uint64_t rk = mix64((uint64_t)round + 1);
+  for (int64_t b = 0; b < nb; ++b) order[b] = {mix64(key ^ rk ^ (uint64_t)b), b};
+  std::sort(order.begin(), order.end());
+  if (waves > nb) waves = nb;
+  std::vector<char> joined(restrict_first && round == 0 ? g.n : 0, 0);
+  std::vector<int32_t> cur = lab;  // labels as they stand
+  int64_t at = 0;
+  for (int64_t k = 0; k < waves; ++k) {
+    const int64_t len = nb / waves + (k < nb % waves ? 1 : 0);
+    std::vector<int64_t> members;
+    for (int64_t i = at; i < at + len; ++i)
+      for (int64_t v = order[i].second * blk; v < std::min<int64_t>(g.n, (order[i].second + 1) * blk); ++v)
+        members.push_back(v);
+    at += len;
+    // every member chooses from cur (one synchronous step on the members)
+    std::vector<int32_t> all(g.n);
+    lp_round(g, cur.data(), key, all.data());
+    std::vector<int32_t> took;
+    for (int64_t v : members) {
+      int32_t L = all[v];
+      if (!joined.empty() && joined[v]) L = cur[v];  // someone earlier moved to v's block
+      if (L != cur[v] && L != (int32_t)v) took.push_back(L);
+      cur[v] = L;
+    }
+    for (int32_t L : took)
+      if (!joined.empty()) joined[L] = 1;
+  }
+  lab.swap(cur);
+}
+
 // Contraction of a clustering (Sec. 4.1, "contract it"; contraction semantics in
 // Sec. 3): each block becomes one vertex, edges inside a block vanish, parallel
 // edges between two blocks merge with summed weight.  [R4] block ids are the ranks
@@ -360,13 +408,20 @@ bool apply(Run& run, Graph& g, const int32_t* labels, int32_t kind, bool correct
 // The label-propagation rounds of one level from the identity labelling: lp_iters
 // rounds, or ([R3], converge) fewer when a round changes at most 1/10000 of the labels
 // (VieCut25, App. D).  Returns the number of rounds run; lab holds the final labels.
+// lp_async: 0 synchronous rounds [R1]; 1 asynchronous rounds [R11] (blocks of 128,
+// eight waves); 2 the same with the first round's restriction.
 int32_t lp_level(const Graph& g, uint64_t key, int32_t lp_iters, bool converge, std::vector<int32_t>& lab,
-                 std::vector<int32_t>& nxt) {
+                 std::vector<int32_t>& nxt, int32_t lp_async = 0) {
   lab.resize(g.n);
   nxt.resize(g.n);
   for (int64_t v = 0; v < g.n; ++v) lab[v] = (int32_t)v;
   for (int32_t r = 0; r < lp_iters; ++r) {
-    lp_round(g, lab.data(), key, nxt.data());
+    if (lp_async) {
+      nxt = lab;
+      lp_round_async(g, nxt, key, r, 128, 8, lp_async == 2);
+    } else {
+      lp_round(g, lab.data(), key, nxt.data());
+    }
     int64_t changed = 0;
     for (int64_t v = 0; v < g.n; ++v) changed += nxt[v] != lab[v];
     lab.swap(nxt);
@@ -380,7 +435,7 @@ int32_t lp_level(const Graph& g, uint64_t key, int32_t lp_iters, bool converge, 
 // vertices remain, then Nagamochi-Ono-Ibaraki on the kernel; the bound is the
 // smallest trivial cut seen (Sec. 4, "Throughout our algorithm we maintain ...").
 void viecut(Graph g, uint64_t seed, int32_t lp_iters, int64_t n0, int32_t pr_runs_max, bool correct, bool converge,
-            Run& run) {
+            int32_t lp_async, Run& run) {
   int64_t n = g.n;
   run.cur.resize(n);
   run.side.assign(n, 0);
@@ -395,7 +450,7 @@ void viecut(Graph g, uint64_t seed, int32_t lp_iters, int64_t n0, int32_t pr_run
   while (g.n > n0) {
     int64_t n_start = g.n;
     uint64_t key = level_key(seed, run.level);
-    lp_level(g, key, lp_iters, converge, lab, nxt);
+    lp_level(g, key, lp_iters, converge, lab, nxt, lp_async);
     if (!apply(run, g, lab.data(), 1, correct)) return;
     for (int32_t runi = 0; runi < pr_runs_max; ++runi) {
       bool any = false;
@@ -458,13 +513,23 @@ void orc_lp_round(int64_t n, const int64_t* off, const int32_t* adj, const int64
   lp_round(g, lab_in, key, lab_out);
 }
 
+// One asynchronous round [R11] from lab (in place) with the given block size and wave
+// count; restrict_first applies the first round's restriction.
+void orc_lp_round_async(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* w, int32_t* lab,
+                        uint64_t key, int32_t round, int64_t blk, int64_t waves, int32_t restrict_first) {
+  Graph g = load(n, off, adj, w, 8);
+  std::vector<int32_t> l(lab, lab + n);
+  lp_round_async(g, l, key, round, blk, waves, restrict_first != 0);
+  memcpy(lab, l.data(), sizeof(int32_t) * n);
+}
+
 // One level's rounds from the identity (lp_level): lab_out[n] the final labels; returns
 // the rounds run.
 int32_t orc_lp_level(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* w, uint64_t key,
-                     int32_t lp_iters, int32_t converge, int32_t* lab_out) {
+                     int32_t lp_iters, int32_t converge, int32_t* lab_out, int32_t lp_async) {
   Graph g = load(n, off, adj, w, 8);
   std::vector<int32_t> lab, nxt;
-  int32_t r = lp_level(g, key, lp_iters, converge != 0, lab, nxt);
+  int32_t r = lp_level(g, key, lp_iters, converge != 0, lab, nxt, lp_async);
   memcpy(lab_out, lab.data(), sizeof(int32_t) * n);
   return r;
 }
@@ -520,10 +585,10 @@ int64_t orc_noi_round(int64_t n, const int64_t* off, const int32_t* adj, const i
 int orc_viecut(int64_t n, const int64_t* off, const int32_t* adj, const void* w, int32_t wbytes,
                uint64_t seed, int32_t lp_iters, int64_t n0, int32_t pr_runs_max,
                int64_t* cut, uint64_t* side_bits, orc_step* trace, int64_t trace_cap,
-               int64_t* trace_len, int32_t correct, int32_t converge) {
-  if (n < 2) return -1;
+               int64_t* trace_len, int32_t correct, int32_t converge, int32_t lp_async) {
+  if (n < 2 || lp_async < 0 || lp_async > 2) return -1;
   Run run;
-  viecut(load(n, off, adj, w, wbytes), seed, lp_iters, n0, pr_runs_max, correct != 0, converge != 0, run);
+  viecut(load(n, off, adj, w, wbytes), seed, lp_iters, n0, pr_runs_max, correct != 0, converge != 0, lp_async, run);
   *cut = run.lambda_hat;
   bool flip = run.side[0] != 0;
   int64_t words = (n + 63) / 64;
