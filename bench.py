@@ -357,7 +357,9 @@ def bench_serve(pool_size: int, requests: int, warm: int, device: int, budget_gb
             "pool": f"{pool_size} RHG graphs, n log-uniform 2^10..2^20, avg deg 32, exponent 5, unit weights, lcc",
             "per_graph_loop_graphs_per_s": loop_rate, "saturation_vs_loop": sat / loop_rate,
             "identical_cut_values": bool([r[0] for r in served] == loop_cuts),
-            "saturation_burst": len(burst), "solo_min_n": 1 << 16, "solo_completed": st["solo_completed"],
+            "saturation_burst": len(burst), "solo_min_n": 1 << 16, "solo_lanes": 4,
+            "solo_exact": "graphs of 513..n0 vertices (their whole run is the exact step) run on the solo lanes",
+            "solo_completed": st["solo_completed"],
             "hbm_budget_gb": budget_gb, "max_resident": st["max_resident"], "joins": st["joins"],
             "super_steps": st["super_steps"], "wall_s": t_end - t_start}
 
@@ -471,21 +473,25 @@ def bench_quality(local):
         t_exact += time.perf_counter() - t
         exact.append(cut)
     results = {}
-    for lp in (1, 2, 3, 5, 25):
+    configs = [(lp, False, 0, f"lp_iters={lp}") for lp in (1, 2, 3, 5, 25)]
+    configs.append((25, True, 0, "VieCut25: up to 25 rounds, stop at <= 1/10000 changed"))
+    configs.append((2, False, 1, "lp_iters=2, asynchronous rounds (shuffled 128-vertex blocks, 8 waves)"))
+    configs.append((2, False, 2, "lp_iters=2, asynchronous rounds with the first round's restriction"))
+    for lp, conv, asy, name in configs:
         runs = bad = 0
         gap = 0.0
         t = time.perf_counter()
         for (_, _, g), lam in zip(graphs, exact):
-            with vc.MinCut(g.offsets, g.adj, g.w, n0=64, device=local) as mc:
+            with vc.MinCut(g.offsets, g.adj, g.w, n0=64, device=local, lp_converge=conv, lp_async=asy) as mc:
                 for s in (1, 2, 3):
                     cut, _ = mc.run(s, lp)
                     runs += 1
                     if cut != lam:
                         bad += 1
                         gap += (cut - lam) / lam
-        results[f"lp_iters={lp}"] = {"runs": runs, "non_optimal": bad, "fraction": bad / runs,
-                                     "mean_relative_gap_of_non_optimal": gap / bad if bad else 0.0,
-                                     "seconds": time.perf_counter() - t}
+        results[name] = {"runs": runs, "non_optimal": bad, "fraction": bad / runs,
+                         "mean_relative_gap_of_non_optimal": gap / bad if bad else 0.0,
+                         "seconds": time.perf_counter() - t}
     # one round with the correcting step (Sec. 4.1) on every label-propagation clustering
     runs = bad = 0
     for (_, _, g), lam in zip(graphs, exact):
@@ -497,8 +503,8 @@ def bench_quality(local):
     nontrivial = sum(1 for (_, _, g), lam in zip(graphs, exact) if lam < int(np.diff(g.offsets).min()))
     return {"metric": "non-optimal minimum cuts per label-propagation iteration count", "data": "synthetic",
             "workload": "rhg(n=2^13..2^16, avg_deg=32, gamma=5) -> 16-core -> largest component, 6 seeds per n, "
-                        "unit weights; the method with n0=64, 3 seeds per graph; lp_iters=25 runs 25 rounds "
-                        "(no convergence stop)",
+                        "unit weights; the method with n0=64, 3 seeds per graph; lp_iters=25 runs 25 rounds, "
+                        "VieCut25 stops earlier once a round changes at most 1/10000 of the labels",
             "graphs": len(graphs), "graphs_with_cut_below_min_degree": nontrivial,
             "exact": {"api": "exact_min_cut (n0 >= n: the exact step alone)", "seconds": t_exact},
             "results": results}
@@ -723,6 +729,7 @@ def main():
         line["batch"] = bench_batch(args.batch_count, 3, 1, stream, local)
         line["serve"] = bench_serve(args.serve_pool, args.serve_requests, args.serve_warmup, local)
         line["configs"] = bench_configs(local)
+        line["quality"] = bench_quality(local)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg is not None:

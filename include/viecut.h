@@ -71,6 +71,19 @@ typedef struct viecut_opts {
                           cluster's weighted degree the most becomes a singleton; 0 = off
                           (default).  Single-graph handles only: viecut_batch_create and
                           viecut_server_start refuse it with VIECUT_EINVAL */
+  int32_t lp_converge; /* 1 = lp_iters is an upper bound: a level's rounds end after the first
+                          round in which at most 1/10000 of its vertices changed their label
+                          (the VieCut25 configuration, App. D, with lp_iters = 25); 0 = exactly
+                          lp_iters rounds (default).  Single-graph handles only (EINVAL for
+                          batches and servers) */
+  int32_t lp_async;    /* 0 = synchronous rounds (default); 1 = asynchronous rounds (Sec. 4.1
+                          in-place updates, Sec. 4.3 shuffled blocks): the vertices form
+                          blocks of 128 consecutive ids, ordered by mix64(key ^ mix64(round + 1)
+                          ^ block) and cut into 8 waves that run one after another, each wave
+                          choosing from the labels as they stand when it starts; 2 = the same
+                          with the first round's restriction (Sec. 4.1: a vertex keeps its
+                          label once a vertex of an earlier wave moved to its block).
+                          Deterministic.  Single-graph handles only */
 } viecut_opts;
 
 /* Per-run statistics (valid after viecut_run / viecut_run_device completes). */
@@ -274,9 +287,14 @@ typedef struct viecut_server_opts {
   int32_t max_slots;        /* graphs resident at once (default 1024) */
   int32_t lp_iters;         /* label-propagation rounds per level for every request (default 2) */
   int64_t solo_min_n;       /* requests of at least this many vertices skip the union and run
-                               one at a time on a handle of their own, on a second stream, beside
-                               the union (each has parallelism enough alone); 0 = never
-                               (default 65536) */
+                               on the solo lanes, beside the union (each has parallelism enough
+                               alone); 0 = no solo lanes (default 65536) */
+  int32_t solo_lanes;       /* solo lanes: threads, each running one request at a time on a handle
+                               and stream of its own (1..64, default 4) */
+  int32_t solo_exact;       /* 1 = requests of 513..n0 vertices (their whole run is the exact
+                               step, a sequential scan per round) also go to the solo lanes, so that
+                               the union's lock-step super-steps never wait for such a scan
+                               (default); 0 = they join the union */
 } viecut_server_opts;
 
 typedef struct viecut_server_stats {

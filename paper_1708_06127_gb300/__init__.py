@@ -39,7 +39,8 @@ class ViecutError(RuntimeError):
 class viecut_opts(ctypes.Structure):
     _fields_ = [("n0", ctypes.c_int64), ("pr_runs_max", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("validate", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("lp_group", ctypes.c_int32), ("emit_group", ctypes.c_int32), ("correct", ctypes.c_int32)]
+                ("lp_group", ctypes.c_int32), ("emit_group", ctypes.c_int32), ("correct", ctypes.c_int32),
+                ("lp_converge", ctypes.c_int32), ("lp_async", ctypes.c_int32)]
 
 
 class viecut_stats(ctypes.Structure):
@@ -66,7 +67,8 @@ class viecut_batch_stats(ctypes.Structure):
 
 class viecut_server_opts(ctypes.Structure):
     _fields_ = [("base", viecut_opts), ("hbm_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32),
-                ("lp_iters", ctypes.c_int32), ("solo_min_n", ctypes.c_int64)]
+                ("lp_iters", ctypes.c_int32), ("solo_min_n", ctypes.c_int64), ("solo_lanes", ctypes.c_int32),
+                ("solo_exact", ctypes.c_int32)]
 
 
 class viecut_server_stats(ctypes.Structure):
@@ -419,7 +421,8 @@ def viecut_server_opts_init(**kw) -> viecut_server_opts:
     o = viecut_server_opts()
     _check(lib().viecut_server_opts_init(ctypes.byref(o)))
     for k, v in kw.items():
-        if k in ("n0", "pr_runs_max", "device", "stream", "lp_group", "emit_group", "correct"):
+        if k in ("n0", "pr_runs_max", "device", "stream", "lp_group", "emit_group", "correct", "lp_converge",
+                 "lp_async"):
             setattr(o.base, k, v)
         else:
             setattr(o, k, v)
@@ -500,9 +503,11 @@ class Server:
     """Continuous-batching min-cut server on one GPU."""
 
     def __init__(self, hbm_budget_bytes: int = 120 << 30, max_slots: int = 1024, lp_iters: int = 2,
-                 n0: int = 10000, pr_runs_max: int = 8, device: int = 0, solo_min_n: int = 1 << 16):
+                 n0: int = 10000, pr_runs_max: int = 8, device: int = 0, solo_min_n: int = 1 << 16,
+                 solo_lanes: int = 4, solo_exact: bool = True):
         o = viecut_server_opts_init(hbm_budget_bytes=hbm_budget_bytes, max_slots=max_slots, lp_iters=lp_iters,
-                                    n0=n0, pr_runs_max=pr_runs_max, device=device, solo_min_n=solo_min_n)
+                                    n0=n0, pr_runs_max=pr_runs_max, device=device, solo_min_n=solo_min_n,
+                                    solo_lanes=solo_lanes, solo_exact=int(solo_exact))
         self.s = viecut_server_start(o)
         self.sizes = {}
 
@@ -574,12 +579,13 @@ class MinCut:
 
     def __init__(self, offsets, adj, weights, n0: int = 10000, pr_runs_max: int = 8, device: int = 0,
                  stream=None, validate: int = 1, timing: bool = False, on_device: bool = False,
-                 lp_group: int = 0, emit_group: int = 0, correct: bool = False):
+                 lp_group: int = 0, emit_group: int = 0, correct: bool = False, lp_converge: bool = False,
+                 lp_async: int = 0):
         n = int(offsets.shape[0] - 1)
         m = int(adj.shape[0])
         o = viecut_opts_init(n0=n0, pr_runs_max=pr_runs_max, device=device, stream=stream,
                              validate=validate, timing=int(timing), lp_group=lp_group, emit_group=emit_group,
-                             correct=int(correct))
+                             correct=int(correct), lp_converge=int(lp_converge), lp_async=int(lp_async))
         self.n, self.m = n, m
         self._keep = (offsets, adj, weights)
         self.h = (viecut_create_device if on_device else viecut_create)(offsets, adj, n, m, weights, o)

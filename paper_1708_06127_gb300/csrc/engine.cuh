@@ -301,8 +301,8 @@ struct Workspace {
   // dbins holds their bins.
   Bins dbins;
   Buf smflag, scidm, sdirty, sdeg, sclean, sdlist, dsl, drl, dml, dbl, dgl, dbail, dcounts;
-  bool mark_sparse(const GraphView& g, const int32_t* labels, const int32_t* cid) {
-    const int64_t n = g.n;
+  // dbins' lists, for at most n listed vertices
+  void prepare_dbins(int64_t n) {
     dbins.small_list = dsl.ensure_n<int32_t>(n);
     dbins.reg_list = drl.ensure_n<int32_t>(n);
     dbins.mid_list = dml.ensure_n<int32_t>(n);
@@ -310,6 +310,11 @@ struct Workspace {
     dbins.global_list = dgl.ensure_n<int32_t>(n);
     dbins.bail_list = dbail.ensure_n<int32_t>(n);
     dbins.counts = dcounts.ensure_n<int>(8);
+  }
+
+  bool mark_sparse(const GraphView& g, const int32_t* labels, const int32_t* cid) {
+    const int64_t n = g.n;
+    prepare_dbins(n);
     int32_t* list = sdlist.ensure_n<int32_t>(n);
     sparse_mark(g, labels, cid, smflag.ensure_n<unsigned char>(n), scidm.ensure_n<int32_t>(n),
                 sdirty.ensure_n<unsigned char>(n), sdeg.ensure_n<int32_t>(n), list, dbins.counts + 6, s);
@@ -320,7 +325,69 @@ struct Workspace {
     return 2 * (int64_t)ndirty <= n;
   }
 
-  void lp_rounds(const GraphView& g, uint64_t key, int rounds, int32_t** out_labels, int32_t* all_out) {
+  // Asynchronous rounds (lp_async 1, or 2 with the first round's restriction; see
+  // async_block_order): the waves of each round run one after another, each binned and
+  // propagated on its own members, then applied in place.
+  Buf asK, asV, asH, asWave, asJoined, asTook, labC;
+  void lp_rounds_async(const GraphView& g, uint64_t key, int rounds, int32_t** out_labels, bool converge,
+                       int lp_async) {
+    const int64_t n = g.n;
+    int32_t* A = labA.as<int32_t>();
+    int32_t* B = labB.as<int32_t>();
+    iota(A, n, s);
+    hash_table(n, key, nullptr, nullptr, nullptr, hv.as<unsigned long long>(), s);
+    const int64_t nb = (n + kAsyncBlock - 1) / kAsyncBlock;
+    const int64_t waves = std::min<int64_t>(kAsyncWaves, nb);
+    auto* k0 = asK.ensure_n<unsigned long long>(2 * nb);
+    auto* v0 = asV.ensure_n<long long>(2 * nb);
+    long long* hist = asH.ensure_n<long long>(radix_hist_elems(nb));
+    unsigned char* wave_of = asWave.ensure_n<unsigned char>(nb);
+    unsigned char* joined = asJoined.ensure_n<unsigned char>(n);
+    int32_t* took = asTook.ensure_n<int32_t>(n);
+    int32_t* C = labC.ensure_n<int32_t>(n);
+    prepare_dbins(n);
+    int32_t* list = sdlist.ensure_n<int32_t>(n);
+    int* count = dbins.counts + 6;
+    for (int r = 0; r < rounds; ++r) {
+      cudaEvent_t a = mark();
+      if (converge) VC_CUDA(cudaMemcpyAsync(C, A, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+      async_block_order(n, key, r, waves, k0, k0 + nb, v0, v0 + nb, hist, wave_of, s);
+      const bool restrict_now = lp_async == 2 && r == 0;
+      if (restrict_now) VC_CUDA(cudaMemsetAsync(joined, 0, (size_t)n, s));
+      for (int k = 0; k < waves; ++k) {
+        async_wave_members(n, wave_of, k, list, count, s);
+        bins_build(g, dbins, s, list, count);
+        read_bins(dbins);
+        lp_round(g, dbins, gt, A, B, hv.as<unsigned long long>(), s, tune);
+        async_apply(list, count, n, B, A, restrict_now ? joined : nullptr, took, s);
+      }
+      if (timing) {
+        lp_spans.push_back({a, mark()});
+        lp_bytes_acc += 8 * (n + 1) + g.nnz * (4 + (g.unit ? 0 : g.wbytes) + 4) + 4 * n;
+        lp_nnz_acc += g.nnz;
+        lp_n_acc += n;
+      }
+      if (converge) {
+        long long* cnt = &ctr()->gpairs;  // free during label propagation
+        VC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(long long), s));
+        count_changed(C, A, n, cnt, s);
+        long long changed = 0;
+        VC_CUDA(cudaMemcpyAsync(&changed, cnt, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        sync();
+        if (changed * 10000 <= n) break;
+      }
+    }
+    *out_labels = A;
+  }
+
+  // `rounds` rounds; with converge, they end after the first round that changed at most
+  // n / 10000 labels (one count and host read per round).
+  void lp_rounds(const GraphView& g, uint64_t key, int rounds, int32_t** out_labels, int32_t* all_out,
+                 bool converge = false, int lp_async = 0) {
+    if (lp_async) {
+      lp_rounds_async(g, key, rounds, out_labels, converge, lp_async);
+      return;
+    }
     int32_t* in = nullptr;
     int32_t* bufs[2] = {labA.as<int32_t>(), labB.as<int32_t>()};
     hash_table(g.n, key, nullptr, nullptr, nullptr, hv.as<unsigned long long>(), s);
@@ -338,7 +405,17 @@ struct Workspace {
       }
       if (all_out)
         VC_CUDA(cudaMemcpyAsync(all_out + (int64_t)r * g.n, out, sizeof(int32_t) * g.n, cudaMemcpyDeviceToHost, s));
+      const int32_t* prev = in;
       in = out;
+      if (converge) {
+        long long* cnt = &ctr()->gpairs;  // free during label propagation
+        VC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(long long), s));
+        count_changed(prev, out, g.n, cnt, s);
+        long long changed = 0;
+        VC_CUDA(cudaMemcpyAsync(&changed, cnt, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        sync();
+        if (changed * 10000 <= g.n) break;
+      }
     }
     *out_labels = in;
   }

@@ -87,7 +87,33 @@ void hash_table(int64_t n, uint64_t key, const int32_t* gid, const unsigned long
 struct LpTuning {
   int first_group = 32;  // lanes per vertex in the first round on simple graphs (8, 16, 32)
   int emit_group = 32;   // lanes per vertex in the pre-merge of the contraction (8, 16, 32)
+  // rounds after the first: mid-class vertices with many distinct neighbouring labels
+  // go to the hash-table kernel (pays on weakly clustered graphs, where lists carry
+  // many labels; costs a launch per round elsewhere)
+  bool mid_bail = false;
 };
+
+// Asynchronous rounds (optional; Sec. 4.1 in-place updates in random order, Sec. 4.3
+// shuffled blocks): the n vertices form blocks of kAsyncBlock consecutive ids, ordered by
+// mix64(key ^ mix64(round + 1) ^ b); the ordered blocks are cut into kAsyncWaves waves
+// (the first nb % waves one block longer) that run one after another, every member of a
+// wave choosing from the labels as they stand when the wave starts.  async_block_order
+// writes each block's wave (wave_of, one byte per block; k0 / k1 / v0 / v1: nb elements,
+// hist: radix_hist_elems(nb)); async_wave_members lists wave k (list[*count]);
+// async_apply moves the members to their fresh labels, with joined (n bytes, zero at the
+// round's start) applying the first round's restriction (a member that an earlier wave
+// moved into keeps its label; took: cap ints).
+constexpr int kAsyncBlock = 128;
+constexpr int kAsyncWaves = 8;
+void async_block_order(int64_t n, uint64_t key, int round, int64_t waves, unsigned long long* k0,
+                       unsigned long long* k1, long long* v0, long long* v1, long long* hist, unsigned char* wave_of,
+                       cudaStream_t s);
+void async_wave_members(int64_t n, const unsigned char* wave_of, int k, int32_t* list, int* count, cudaStream_t s);
+void async_apply(const int32_t* list, const int* count, int64_t cap, const int32_t* fresh, int32_t* lab,
+                 unsigned char* joined, int32_t* took, cudaStream_t s);
+
+// *changed += the number of v with lab_out[v] != lab_in[v] (lab_in null: the identity).
+void count_changed(const int32_t* lab_in, const int32_t* lab_out, int64_t n, long long* changed, cudaStream_t s);
 
 // One synchronous label-propagation round; lab_in == nullptr means the identity
 // labelling (first round of a level).  hv: the level's tie-break table.

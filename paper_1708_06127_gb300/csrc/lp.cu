@@ -23,6 +23,7 @@
 #include <unordered_map>
 
 #include "kernels.cuh"
+#include "prims.cuh"
 #include "regvisit.cuh"
 
 namespace vc {
@@ -140,6 +141,115 @@ void hash_table(int64_t n, uint64_t key, const int32_t* gid, const unsigned long
   if (n <= 0) return;
   hash_table_k<<<grid_for(n, 256, kSMs * 8), 256, 0, s>>>(n, key, gid, gkey, gbase, hv);
   count_launch();
+  VC_CHECK_LAUNCH();
+}
+
+__global__ void count_changed_k(const int32_t* __restrict__ in, const int32_t* __restrict__ out, int64_t n,
+                                long long* __restrict__ changed) {
+  long long c = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    c += out[v] != (in ? in[v] : (int32_t)v);
+  c = warp_sum(c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd((unsigned long long*)changed, (unsigned long long)c);
+}
+
+void count_changed(const int32_t* lab_in, const int32_t* lab_out, int64_t n, long long* changed, cudaStream_t s) {
+  if (n <= 0) return;
+  count_changed_k<<<grid_for(n, 256, kSMs * 8), 256, 0, s>>>(lab_in, lab_out, n, changed);
+  count_launch();
+  VC_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------- asynchronous rounds
+// Rounds in shuffled blocks of kAsyncBlock consecutive ids run in waves (see the
+// declaration in kernels.cuh): the blocks' keys, each block's wave, each wave's members,
+// and after a wave the members' new labels (with the first round's restriction).
+__global__ void async_keys_k(int64_t nb, uint64_t key, uint64_t rk, unsigned long long* __restrict__ keys,
+                             long long* __restrict__ vals) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+    keys[b] = mix64(key ^ rk ^ (uint64_t)b);
+    vals[b] = b;
+  }
+}
+
+// Position i of the ordered blocks belongs to wave k: the first nb % waves waves hold
+// nb / waves + 1 blocks, the others nb / waves.
+__global__ void async_waves_k(int64_t nb, int64_t waves, const long long* __restrict__ order,
+                              unsigned char* __restrict__ wave_of) {
+  const int64_t q = nb / waves, rmd = nb % waves;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i < rmd * (q + 1) ? i / (q + 1) : rmd + (i - rmd * (q + 1)) / q;
+    wave_of[order[i]] = (unsigned char)k;
+  }
+}
+
+__global__ void async_members_k(int64_t n, const unsigned char* __restrict__ wave_of, int k, int32_t* __restrict__ list,
+                                int* __restrict__ count) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; b < n;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = b + lane;
+    const bool in = v < n && wave_of[v / kAsyncBlock] == k;
+    const unsigned bal = __ballot_sync(0xffffffffu, in);
+    int at = 0;
+    if (lane == 0 && bal) at = atomicAdd(count, __popc(bal));
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (in) list[at + __popc(bal & ((1u << lane) - 1u))] = (int32_t)v;
+  }
+}
+
+// The wave's members take their new labels; in the first round a member some earlier
+// wave moved into (joined) keeps its label.  Labels taken by a member that moved are
+// recorded in took (marked into joined after the wave).
+__global__ void async_apply_k(const int32_t* __restrict__ list, const int* __restrict__ count,
+                              const int32_t* __restrict__ fresh, int32_t* __restrict__ lab,
+                              const unsigned char* __restrict__ joined, int32_t* __restrict__ took) {
+  const int c = *count;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x) {
+    const int32_t v = list[i];
+    int32_t L = fresh[v];
+    if (joined && joined[v]) L = lab[v];
+    if (took) took[i] = (L != lab[v] && L != v) ? L : -1;
+    lab[v] = L;
+  }
+}
+
+__global__ void async_mark_k(const int* __restrict__ count, const int32_t* __restrict__ took,
+                             unsigned char* __restrict__ joined) {
+  const int c = *count;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x)
+    if (took[i] >= 0) joined[took[i]] = 1;
+}
+
+void async_block_order(int64_t n, uint64_t key, int round, int64_t waves, unsigned long long* k0,
+                       unsigned long long* k1, long long* v0, long long* v1, long long* hist, unsigned char* wave_of,
+                       cudaStream_t s) {
+  const int64_t nb = (n + kAsyncBlock - 1) / kAsyncBlock;
+  async_keys_k<<<grid_for(nb, 256, kSMs * 4), 256, 0, s>>>(nb, key, mix64((uint64_t)round + 1), k0, v0);
+  count_launch();
+  VC_CHECK_LAUNCH();
+  radix_sort_pairs(k0, v0, k1, v1, nb, 64, hist, s);
+  async_waves_k<<<grid_for(nb, 256, kSMs * 4), 256, 0, s>>>(nb, waves < nb ? waves : nb, v0, wave_of);
+  count_launch();
+  VC_CHECK_LAUNCH();
+}
+
+void async_wave_members(int64_t n, const unsigned char* wave_of, int k, int32_t* list, int* count, cudaStream_t s) {
+  VC_CUDA(cudaMemsetAsync(count, 0, sizeof(int), s));
+  async_members_k<<<grid_for(n, 256, kSMs * 8), 256, 0, s>>>(n, wave_of, k, list, count);
+  count_launch();
+  VC_CHECK_LAUNCH();
+}
+
+void async_apply(const int32_t* list, const int* count, int64_t cap, const int32_t* fresh, int32_t* lab,
+                 unsigned char* joined, int32_t* took, cudaStream_t s) {
+  const int grid = grid_for(cap, 256, kSMs * 8);
+  async_apply_k<<<grid, 256, 0, s>>>(list, count, fresh, lab, joined, joined ? took : nullptr);
+  count_launch();
+  if (joined) {
+    async_mark_k<<<grid, 256, 0, s>>>(count, took, joined);
+    count_launch();
+  }
   VC_CHECK_LAUNCH();
 }
 
@@ -631,9 +741,9 @@ void launch_lp_bailed(const GraphView& g, const Bins& b, const WT* w, const int3
 // beat it there.
 template <typename WT, typename ACC, bool FIRST>
 void launch_lp_reg(const GraphView& g, const Bins& b, const WT* w, const int32_t* lab, int32_t* lab_out,
-                   const unsigned long long* hv, cudaStream_t s) {
-  int32_t* bl = FIRST ? nullptr : b.bail_list;
-  int* bc = FIRST ? nullptr : b.counts + 7;
+                   const unsigned long long* hv, cudaStream_t s, bool mid_bail) {
+  int32_t* bl = (FIRST || !mid_bail) ? nullptr : b.bail_list;
+  int* bc = (FIRST || !mid_bail) ? nullptr : b.counts + 7;
   if (b.h_small > 0) {
     lp_reg_k<WT, ACC, FIRST, 16, 4><<<grid_for(b.h_small, kWarpsPerBlock * 2, kSMs * 16), kAggThreads, 0, s>>>(
         b.small_list, b.counts + 4, g.off, g.adj, w, lab, lab_out, hv, g.vact, nullptr, nullptr);
@@ -1031,7 +1141,7 @@ void launch_lp(const GraphView& g, const Bins& b, const GlobalTables& gt, const 
     }
     return;
   }
-  launch_lp_reg<WT, ACC, FIRST>(g, b, w, lab, lab_out, key, s);
+  launch_lp_reg<WT, ACC, FIRST>(g, b, w, lab, lab_out, key, s, tune.mid_bail);
   if (b.h_block > 0) {
     const size_t smem = (size_t)kBlockCap * (sizeof(ACC) + sizeof(int));
     auto kfn = lp_block_k<WT, ACC, FIRST, false>;

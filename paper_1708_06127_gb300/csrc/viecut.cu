@@ -86,6 +86,8 @@ struct Handle {
   int pr_runs_max = 8;
   int validate = 1;
   bool correct = false;  // the correcting step on label-propagation clusterings
+  bool lp_converge = false;  // rounds end once at most 1/10000 of the labels changed
+  int lp_async = 0;          // asynchronous rounds in shuffled blocks (2: with the first round's restriction)
   bool unit = false;    // every input weight is 1 (found by validation)
   bool simple = false;  // every input list strictly increasing (found by validation)
   bool host_input = false;  // the graph was copied from host arrays into in_*
@@ -252,14 +254,18 @@ static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, u
     return W.h_counters->changed;
   };
 
+  int64_t n_prev_level = 0;
   while (!done && G.n > H.n0) {
     const int64_t n_start = G.n;
     const uint64_t key = level_key(seed, level);
+    // a graph the last level did not halve is weakly clustered: its lists carry many labels
+    W.tune.mid_bail = n_prev_level > 0 && 2 * n_start > n_prev_level;
+    n_prev_level = n_start;
     W.build_bins(G);
     int32_t* labels = nullptr;
     cudaEvent_t a0 = W.mark();
     if (lp_iters > 0) {
-      W.lp_rounds(G, key, lp_iters, &labels, nullptr);
+      W.lp_rounds(G, key, lp_iters, &labels, nullptr, H.lp_converge, H.lp_async);
     } else {
       labels = W.labA.as<int32_t>();
       iota(labels, G.n, s);
@@ -519,6 +525,8 @@ static int create_common(viecut_t** out, int64_t n, int64_t m, const viecut_opts
   for (int G : {o.lp_group, o.emit_group})
     if (G != 0 && G != 8 && G != 16 && G != 32) throw Error{VIECUT_EINVAL, "lp_group and emit_group must be 0, 8, 16 or 32"};
   if (o.correct != 0 && o.correct != 1) throw Error{VIECUT_EINVAL, "correct must be 0 or 1"};
+  if (o.lp_converge != 0 && o.lp_converge != 1) throw Error{VIECUT_EINVAL, "lp_converge must be 0 or 1"};
+  if (o.lp_async < 0 || o.lp_async > 2) throw Error{VIECUT_EINVAL, "lp_async must be 0, 1 or 2"};
   // validate 2 rejects a malformed host graph before any device call
   const bool checked = host_input && o.validate >= 2;
   bool unit = false, simple = false;
@@ -538,6 +546,8 @@ static int create_common(viecut_t** out, int64_t n, int64_t m, const viecut_opts
     H.pr_runs_max = o.pr_runs_max;
     H.validate = o.validate;
     H.correct = o.correct != 0;
+    H.lp_converge = o.lp_converge != 0;
+    H.lp_async = o.lp_async;
     H.ws = new vc::Workspace;
     H.ws->s = H.stream;
     H.ws->timing = o.timing != 0;
@@ -814,6 +824,8 @@ int viecut_step_lp(viecut_graph* g, const int32_t* lab_in, uint64_t key, int32_t
   StepCtx c(g->g);
   vc::GraphView v = g->g.view();
   c.ws->build_bins(v);
+  c.ws->tune.mid_bail = true;  // a launch choice only: the table kernel runs here for every
+                                // mid-class list with many labels, so the tests see it
   int32_t* in = nullptr;
   if (lab_in) {
     vc::Buf tmp;

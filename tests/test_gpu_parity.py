@@ -489,3 +489,45 @@ def test_solve_equals_load_and_run():
         with pytest.raises(vc.ViecutError) as e:
             mc.run(1, 2)
         assert e.value.code == vc.VIECUT_EINVAL
+
+
+def test_lp_converge_parity():
+    """The convergence stop (at most lp_iters rounds, ending after a round that changed at
+    most 1/10000 of the labels) equals the oracle's; on 4000 K5 plus an edge whose ends
+    swap labels every round, the stop fires after the rounds the oracle's level takes."""
+    from tests.test_oracle import cliques_and_edge, two_triangles
+    graphs = [(gg.workload_rhg_small(3), 64), (cliques_and_edge(), 64), (two_triangles(), 1),
+              (gg.planted(4, 1 << 12, 16, 8, 5, 1, 100), 64)]
+    for g, n0 in graphs:
+        for seed in (1, 2):
+            ref = oracle.viecut(g.offsets, g.adj, g.w, seed=seed, lp_iters=25, n0=n0, converge=True)
+            with vc.MinCut(g.offsets, g.adj, g.w, n0=n0, lp_converge=True) as mc:
+                cut, bits = mc.run(seed, 25)
+                tr = mc.trace()
+            assert tr == ref.trace and cut == ref.cut and np.array_equal(bits, ref.side_bits), (g.name, seed)
+    g = cliques_and_edge()
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    _, rounds = oracle.lp_level(G, oracle.level_key(1, 0), 25, True)
+    with vc.MinCut(g.offsets, g.adj, g.w, n0=g.n - 1, lp_converge=True, timing=True) as mc:
+        mc.run(1, 25)
+        assert mc.stats()["lp_launches"] == rounds < 25
+    with pytest.raises(vc.ViecutError) as e:
+        vc.viecut_batch_create([(g.offsets, g.adj, g.w)], vc.viecut_opts_init(lp_converge=1))
+    assert e.value.code == vc.VIECUT_EINVAL
+
+
+@pytest.mark.parametrize("lp_async", [1, 2])
+def test_async_lp_parity(lp_async):
+    """Asynchronous rounds in shuffled 128-vertex blocks and eight waves (with the first
+    round's restriction for lp_async = 2) equal the oracle's reading of them: trace, cut
+    and side, with and without the convergence stop."""
+    graphs = [(gg.workload_rhg_small(2), 64), (gg.with_pair_weights(gg.core_lcc(gg.rhg(1 << 12, 20, 7), 0), 7, 1, 50), 32),
+              (hub_graph(), 16), (gg.planted(4, 1 << 10, 16, 8, 5, 1, 100), 64), (H.two_cliques(7, 2), 1)]
+    for g, n0 in graphs:
+        for seed, lp, conv in ((1, 2, False), (2, 1, False), (3, 25, True)):
+            ref = oracle.viecut(g.offsets, g.adj, g.w, seed=seed, lp_iters=lp, n0=n0, converge=conv,
+                                lp_async=lp_async)
+            with vc.MinCut(g.offsets, g.adj, g.w, n0=n0, lp_converge=conv, lp_async=lp_async) as mc:
+                cut, bits = mc.run(seed, lp)
+                tr = mc.trace()
+            assert tr == ref.trace and cut == ref.cut and np.array_equal(bits, ref.side_bits), (g.name, seed, lp)
