@@ -357,7 +357,7 @@ def bench_serve(pool_size: int, requests: int, warm: int, device: int, budget_gb
             "pool": f"{pool_size} RHG graphs, n log-uniform 2^10..2^20, avg deg 32, exponent 5, unit weights, lcc",
             "per_graph_loop_graphs_per_s": loop_rate, "saturation_vs_loop": sat / loop_rate,
             "identical_cut_values": bool([r[0] for r in served] == loop_cuts),
-            "saturation_burst": len(burst), "solo_min_n": 1 << 16, "solo_lanes": 4,
+            "saturation_burst": len(burst), "solo_min_n": 1 << 16, "solo_lanes": 8,
             "solo_exact": "graphs of 513..n0 vertices (their whole run is the exact step) run on the solo lanes",
             "solo_completed": st["solo_completed"],
             "hbm_budget_gb": budget_gb, "max_resident": st["max_resident"], "joins": st["joins"],

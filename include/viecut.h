@@ -290,7 +290,7 @@ typedef struct viecut_server_opts {
                                on the solo lanes, beside the union (each has parallelism enough
                                alone); 0 = no solo lanes (default 65536) */
   int32_t solo_lanes;       /* solo lanes: threads, each running one request at a time on a handle
-                               and stream of its own (1..64, default 4) */
+                               and stream of its own (1..64, default 8) */
   int32_t solo_exact;       /* 1 = requests of 513..n0 vertices (their whole run is the exact
                                step, a sequential scan per round) also go to the solo lanes, so that
                                the union's lock-step super-steps never wait for such a scan

@@ -504,7 +504,7 @@ class Server:
 
     def __init__(self, hbm_budget_bytes: int = 120 << 30, max_slots: int = 1024, lp_iters: int = 2,
                  n0: int = 10000, pr_runs_max: int = 8, device: int = 0, solo_min_n: int = 1 << 16,
-                 solo_lanes: int = 4, solo_exact: bool = True):
+                 solo_lanes: int = 8, solo_exact: bool = True):
         o = viecut_server_opts_init(hbm_budget_bytes=hbm_budget_bytes, max_slots=max_slots, lp_iters=lp_iters,
                                     n0=n0, pr_runs_max=pr_runs_max, device=device, solo_min_n=solo_min_n,
                                     solo_lanes=solo_lanes, solo_exact=int(solo_exact))

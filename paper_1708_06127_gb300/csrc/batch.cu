@@ -946,13 +946,16 @@ struct Server {
   int64_t cancelled = 0;
   int64_t failed = 0;  // requests answered with VIECUT_ENOMEM
   std::vector<long long> h_join;
-  // solo lane: requests of at least solo_min_n vertices, one at a time on a handle
-  // (and stream) of their own
+  // solo lanes: requests of at least solo_min_n vertices (and, with solo_exact, those
+  // whose whole run is the sequential exact step), each lane one request at a time on a
+  // handle (and stream) of its own
   int64_t solo_min_n = 0;
+  bool solo_exact = false;
+  int64_t n0 = 10000;
   viecut_opts solo_opts{};
   std::deque<std::shared_ptr<Request>> solo_pending;
   std::condition_variable cv_solo;
-  std::thread th_solo;
+  std::vector<std::thread> th_solo;
   int64_t solo_completed = 0;
 };
 
@@ -1383,6 +1386,8 @@ int viecut_batch_create(viecut_batch** out, const viecut_graph_desc* graphs, int
   if (opts) o = *opts;
   if (o.n0 < 1 || o.pr_runs_max < 0) throw Error{VIECUT_EINVAL, "bad options"};
   if (o.correct) throw Error{VIECUT_EINVAL, "correct: the correcting step runs on single-graph handles only"};
+  if (o.lp_converge) throw Error{VIECUT_EINVAL, "lp_converge: the convergence stop runs on single-graph handles only"};
+  if (o.lp_async) throw Error{VIECUT_EINVAL, "lp_async: asynchronous rounds run on single-graph handles only"};
   auto* x = new viecut_batch;
   try {
     vc::batch_create(x->b, graphs, k, o);
@@ -1452,6 +1457,8 @@ int viecut_server_opts_init(viecut_server_opts* o) {
   o->max_slots = 1024;
   o->lp_iters = 2;
   o->solo_min_n = 65536;
+  o->solo_lanes = 8;
+  o->solo_exact = 1;
   return VIECUT_OK;
 }
 
@@ -1463,9 +1470,12 @@ int viecut_server_start(viecut_server** out, const viecut_server_opts* opts) {
   viecut_server_opts_init(&o);
   if (opts) o = *opts;
   if (o.max_slots < 1 || o.hbm_budget_bytes < 1 || o.lp_iters < 0 || o.base.n0 < 1 || o.base.pr_runs_max < 0 ||
-      o.solo_min_n < 0)
+      o.solo_min_n < 0 || o.solo_lanes < 1 || o.solo_lanes > 64 || (o.solo_exact != 0 && o.solo_exact != 1))
     throw Error{VIECUT_EINVAL, "bad server options"};
   if (o.base.correct) throw Error{VIECUT_EINVAL, "correct: the correcting step runs on single-graph handles only"};
+  if (o.base.lp_converge)
+    throw Error{VIECUT_EINVAL, "lp_converge: the convergence stop runs on single-graph handles only"};
+  if (o.base.lp_async) throw Error{VIECUT_EINVAL, "lp_async: asynchronous rounds run on single-graph handles only"};
   auto* x = new viecut_server;
   try {
     vc::Server& S = x->s;
@@ -1481,7 +1491,10 @@ int viecut_server_start(viecut_server** out, const viecut_server_opts* opts) {
     S.solo_opts.validate = 1;      // already checked on submit; the device pass finds unit / simple
     S.solo_opts.timing = 0;
     S.th = std::thread(vc::server_loop, std::ref(S));
-    if (S.solo_min_n > 0) S.th_solo = std::thread(vc::solo_loop, std::ref(S));
+    S.solo_exact = o.solo_exact != 0;
+    S.n0 = o.base.n0;
+    if (S.solo_min_n > 0)
+      for (int i = 0; i < o.solo_lanes; ++i) S.th_solo.emplace_back(vc::solo_loop, std::ref(S));
   } catch (...) {
     delete x;
     throw;
@@ -1521,7 +1534,10 @@ int viecut_server_submit(viecut_server* sv, const viecut_graph_desc* g, uint64_t
     if (!S.error.empty()) throw Error{VIECUT_ECUDA, S.error};
     r->ticket = S.next_ticket++;
     S.tickets[r->ticket] = r;
-    if (S.solo_min_n > 0 && n >= S.solo_min_n) S.solo_pending.push_back(r);
+    // large graphs, and (solo_exact) graphs that go straight to the sequential exact step,
+    // run alone: in the lock-step union a long exact-step scan would hold every graph back
+    const bool solo = S.solo_min_n > 0 && (n >= S.solo_min_n || (S.solo_exact && n > vc::kDenseMax && n <= S.n0));
+    if (solo) S.solo_pending.push_back(r);
     else S.pending.push_back(r);
   }
   S.cv.notify_one();
@@ -1656,7 +1672,8 @@ int viecut_server_stop(viecut_server* sv) {
   sv->s.cv_solo.notify_all();
   sv->s.cv_done.notify_all();
   if (sv->s.th.joinable()) sv->s.th.join();
-  if (sv->s.th_solo.joinable()) sv->s.th_solo.join();
+  for (auto& t : sv->s.th_solo)
+    if (t.joinable()) t.join();
   cudaSetDevice(sv->s.E.device);
   if (sv->s.E.stream) cudaStreamSynchronize(sv->s.E.stream);
   delete sv;

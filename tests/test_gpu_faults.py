@@ -87,7 +87,7 @@ def test_batch_survives_failed_allocations():
 def test_server_answers_failed_admissions_and_goes_on():
     small = gg.core_lcc(gg.rhg(2000, 24, 5), 0)
     large = gg.core_lcc(gg.rhg(1 << 14, 32, 6), 0)
-    with vc.Server(max_slots=16, solo_min_n=8000) as srv:
+    with vc.Server(max_slots=16, solo_min_n=8000, solo_exact=False, solo_lanes=1) as srv:
         # the union lane: the join's first allocation (its staging buffers) fails
         vc.viecut_debug_fail_device_allocs(0, 1)
         t = srv.submit(small.offsets, small.adj, small.w, 1)

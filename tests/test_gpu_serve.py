@@ -51,7 +51,7 @@ def check_result(g, seed, res, n0=10000):
 
 def test_serve_staggered_arrivals_equal_alone():
     reqs = request_mix(40, 3)
-    with vc.Server(max_slots=64) as srv:
+    with vc.Server(max_slots=64, solo_exact=False) as srv:
         tickets = []
         for i, (g, seed) in enumerate(reqs):
             tickets.append(srv.submit(g.offsets, g.adj, g.w, seed))
@@ -135,7 +135,7 @@ def test_serve_solo_lane_beside_the_union():
     reqs = request_mix(30, 21)
     big = [gg.core_lcc(gg.rhg(1 << 13, 32, 77 + i), 0) for i in range(4)]
     reqs[3:3] = [(g, 50 + i) for i, g in enumerate(big)]
-    with vc.Server(max_slots=32, solo_min_n=4000) as srv:
+    with vc.Server(max_slots=32, solo_min_n=4000, solo_exact=False) as srv:
         tickets = [srv.submit(g.offsets, g.adj, g.w, seed) for g, seed in reqs]
         results = [srv.wait(t) for t in tickets]
         st = srv.stats()
@@ -144,6 +144,32 @@ def test_serve_solo_lane_beside_the_union():
     n_solo = sum(1 for g, _ in reqs if g.n >= 4000)
     assert st["solo_completed"] == n_solo >= 4, st
     assert st["completed"] == len(reqs) and st["budget_used"] == 0
+
+
+def test_serve_exact_step_graphs_on_parallel_solo_lanes():
+    """With solo_exact (the default), graphs whose whole run is the exact step (513..n0
+    vertices) go to the solo lanes, several of which run side by side; the union keeps
+    the small and the large graphs.  Every result equals the oracle's."""
+    reqs = request_mix(36, 13)
+    with vc.Server(max_slots=32, solo_lanes=3) as srv:
+        tickets = [srv.submit(g.offsets, g.adj, g.w, seed) for g, seed in reqs]
+        infos = {}
+        for t in tickets:
+            while True:
+                r = srv.poll_info(t)
+                if r is not None:
+                    infos[t] = r
+                    break
+                time.sleep(0.0005)
+        st = srv.stats()
+    for (g, seed), t in zip(reqs, tickets):
+        cut, bits, info = infos[t]
+        check_result(g, seed, (cut, bits, info["latency_ms"]))
+        exact_only = 512 < g.n <= 10000
+        assert info["lane"] == (1 if (exact_only or g.n >= 1 << 16) else 0), (g.n, info)
+        assert info["queue_ms"] >= 0 and info["run_ms"] >= 0 and info["n"] == g.n
+    n_solo = sum(1 for g, _ in reqs if 512 < g.n <= 10000 or g.n >= 1 << 16)
+    assert st["solo_completed"] == n_solo > 0 and st["completed"] == len(reqs)
 
 
 def test_load_reuses_a_handle_across_graphs():
