@@ -35,20 +35,32 @@ WORKLOAD = "rhg(n=2^22, avg_deg=64, gamma=5) -> 16-core -> largest component, un
 SAMPLE_N = 1 << 19  # the CPU oracle's bounded sample: same family, n = 2^19
 
 
-def committed_lp_traffic():
-    """DRAM bytes per label-propagation round from the committed ncu summary, or None when
-    the kernels' source changed since the counters were taken."""
+def committed_traffic(summary: str, field: str, sources):
+    """DRAM bytes from a committed ncu summary under profiles/, or None when one of the
+    kernels' source files changed since the counters were taken (the summary records
+    their SHA-256 prefixes, joined by '+')."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "lp_round_traffic_rhg_n1048576.md")
-    src = os.path.join(ROOT, "paper_1708_06127_gb300", "csrc", "lp.cu")
+    path = os.path.join(ROOT, "profiles", summary)
     try:
         fields = dict(line.split("=", 1) for line in open(path).read().splitlines() if "=" in line and " " not in line)
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = "+".join(hashlib.sha256(open(os.path.join(ROOT, "paper_1708_06127_gb300", "csrc", f), "rb").read())
+                       .hexdigest()[:16] for f in sources)
     except OSError:
         return None
     if fields.get("kernel_sha256_prefix") != sha:
         return None
-    return int(fields["traffic_bytes_per_round_n2p22"])
+    return int(fields[field])
+
+
+def committed_lp_traffic():
+    """DRAM bytes per label-propagation round (level 0, n = 2^22, scaled from n = 2^20)."""
+    return committed_traffic("lp_round_traffic_rhg_n1048576.md", "traffic_bytes_per_round_n2p22", ["lp.cu"])
+
+
+def committed_contract_traffic():
+    """DRAM bytes of the level-0 contraction (n = 2^22, scaled from n = 2^20)."""
+    return committed_traffic("contraction_traffic_rhg_n1048576.md", "traffic_bytes_per_contraction_n2p22",
+                             ["lp.cu", "contract.cu"])
 
 
 def dist_env():
@@ -701,7 +713,11 @@ def main():
             "kernel": "cluster contraction: relabel, pre-merge (emit_reg_k / emit_warp_k / emit_block_k), "
                       "cluster merge (scatter, merge, place)",
             "bound": "hbm", "achieved": ct_achieved, "peak": peak, "unit": "GB/s",
-            "frac": (ct_achieved / peak) if ct_achieved else None, "traffic": None,
+            "frac": (ct_achieved / peak) if ct_achieved else None,
+            "traffic": committed_contract_traffic() if args.nlog == 22 else None,
+            "traffic_source": "profiles/contraction_traffic_rhg_n1048576.md (ncu DRAM bytes of the level-0 "
+                              "contraction at n=2^20, scaled by entries; per level-0 contraction, which holds "
+                              "~98% of a step's contraction bytes; null once lp.cu or contract.cu changed)",
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
             "contractions_per_step": ct_count / args.steps, "ms_per_step": ct_ms / args.steps,
             "algorithmic_bytes_per_step": ct_bytes / args.steps,
