@@ -54,13 +54,13 @@ def committed_traffic(summary: str, field: str, sources):
 
 def committed_lp_traffic():
     """DRAM bytes per label-propagation round (level 0, n = 2^22, scaled from n = 2^20)."""
-    return committed_traffic("lp_round_traffic_rhg_n1048576.md", "traffic_bytes_per_round_n2p22", ["lp.cu"])
+    return committed_traffic("lp_round_traffic_rhg_n1048576.md", "traffic_bytes_per_round_n2p22", ["lp.cu", "regvisit.cuh"])
 
 
 def committed_contract_traffic():
     """DRAM bytes of the level-0 contraction (n = 2^22, scaled from n = 2^20)."""
     return committed_traffic("contraction_traffic_rhg_n1048576.md", "traffic_bytes_per_contraction_n2p22",
-                             ["lp.cu", "contract.cu"])
+                             ["lp.cu", "regvisit.cuh", "contract.cu"])
 
 
 def dist_env():
