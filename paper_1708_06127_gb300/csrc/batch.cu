@@ -624,7 +624,7 @@ static bool engine_step(Engine& E) {
     pr_pass_b(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), W.st(), F, nullptr, s, &bc);
   }
   if (cnt[kBNoiS] > 0) {
-    W.noi_r.ensure_n<long long>(2 * G.n + 64);
+    W.noi_r.ensure_n<long long>(noi_round_scratch(G.n));
     W.noi_seen.ensure_n<unsigned char>(G.n);
     noi_round_batch(G, S.list_nois, cnt[10], S.vbase, S.nv, S.lam, W.noi_r.as<long long>(),
                     W.noi_seen.as<unsigned char>(), W.parent.as<int32_t>(), F, S.changed, cnt[11], s);

@@ -280,6 +280,9 @@ constexpr int kDenseMax = 512;
 void noi_dense(const GraphView& g, long long* M0, long long* M1, int32_t* curK, unsigned char* sideK,
                DevState* st, TraceStep* trace, int trace_cap, int level, cudaStream_t s);
 // One round of the maximum-adjacency scan on a larger graph; labels = union-find roots.
+// Scratch of a sparse exact-step round (r of noi_round_sparse / noi_round_batch), in
+// int64 entries, for a graph (or union) of n vertices: attachments, then chunk maxima.
+inline int64_t noi_round_scratch(int64_t n) { return 2 * n + 64; }
 void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, unsigned char* seen,
                       int32_t* parent, int32_t* labels, int* changed, cudaStream_t s);
 

@@ -388,12 +388,24 @@ __device__ __forceinline__ void noi_round_body(int64_t lo, int64_t hi, const int
   __syncthreads();
 }
 
-// ---- the same round by one warp, for any n (arrays in global memory).  The next
-// vertex is found in two levels: cmax[c] holds the largest attachment r of the
-// unvisited vertices of chunk c = 32 consecutive vertices (-1: all visited); the warp
-// picks the chunk of largest cmax (ties: lower chunk, hence smaller ids), then the
-// vertex of largest r in it (ties: smallest id).  Relaxing a neighbour raises its
-// chunk's maximum with atomicMax; visiting a vertex recomputes its chunk's maximum.
+// ---- the same round by one warp, without a union-find.  The next vertex is found in
+// two levels: cmax[c] holds the largest attachment r of the unvisited vertices of
+// chunk c = 32 consecutive vertices (-1: all visited); the warp picks the chunk of
+// largest cmax (ties: lower chunk, hence smaller ids), then the vertex of largest r in
+// it (ties: smallest id).  Relaxing a neighbour raises its chunk's maximum with
+// atomicMax; visiting a vertex recomputes its chunk's maximum.
+//
+// The round's unions need no union-find.  Call a vertex "low" when it is visited with
+// r < max(lambda-hat, 1) (no edge raised it to lambda-hat; with lambda-hat <= 0: no
+// visited neighbour).  When a low vertex u is visited every unvisited r is at most
+// r(u), so no unvisited vertex has reached lambda-hat yet.  A vertex y visited later
+// and not low reached lambda-hat through the edge of some x visited after u and
+// before y, and the round unites x and y; so every vertex is joined to the last low
+// vertex before it, and every united pair (x visited after y's last low vertex, as r(y)
+// reaches lambda-hat only after it) lies within one such run.  The round's components
+// are therefore the runs of the visiting order that start at a low vertex, and the
+// union-find with smallest-id roots labels each run with its smallest id.  The scan
+// records the order (order[place]) and writes a run's labels when the next run starts.
 
 // argmax over the warp of (val, -idx) for val >= 0 (val < 0: no candidate); returns
 // idx, or -1 if no lane has a candidate; *best = the value.
@@ -430,23 +442,51 @@ struct BitSeen {
   __device__ __forceinline__ void set(int64_t v) const { bits[(v - lo) >> 5] |= 1u << ((v - lo) & 31); }
 };
 
-template <typename WT, typename SEEN>
-__device__ __forceinline__ void noi_round_warp(int64_t lo, int64_t hi, const int64_t* __restrict__ off,
-                                               const int32_t* __restrict__ adj, const WT* __restrict__ w,
-                                               long long lam, long long* r, SEEN seen, int32_t* parent,
-                                               long long* cmax, int32_t* labels, int* any_out, int64_t sb) {
-  // r and parent hold vertex v at v - sb (sb = 0: arrays over the whole graph;
-  // sb = lo: this graph's own arrays, e.g. in shared memory)
+// List bounds of vertex v: the CSR's own offsets, or a copy of the graph's offsets in
+// shared memory relative to its first entry (a step then reads only the chosen
+// vertex's list from global memory).
+struct GlobalOff {
+  const int64_t* off;
+  __device__ __forceinline__ int64_t at(int64_t v) const { return __ldg(off + v); }
+};
+struct SharedOff {
+  const int32_t* rel;  // rel[k] = off[lo + k] - base, k = 0..n
+  int64_t lo, base;
+  __device__ __forceinline__ int64_t at(int64_t v) const { return base + rel[v - lo]; }
+};
+
+constexpr int kNoiUnroll = 4;  // list entries in flight per lane while relaxing
+
+// Labels of the run of places [s0, s1): m, the run's smallest id.  Lane L holds in
+// `win` the vertex visited at the latest place p < s1 with p % 32 == L; older places
+// are read back from order.
+__device__ __forceinline__ void noi_flush_run(int64_t lo, int64_t s0, int64_t s1, int32_t m, int32_t win,
+                                              const int32_t* order, int32_t* labels) {
   const int lane = threadIdx.x & 31;
-  const int64_t n = hi - lo;
+  for (int64_t p = s0 + lane; p < s1 - 32; p += 32) labels[order[lo + p]] = m;
+  const int64_t pl = s1 - 1 - ((s1 - 1 - lane) & 31);
+  if (pl >= s0) labels[win] = m;
+}
+
+// The scan of one round over the graph [lo, lo + n) (ids global: labels, order and the
+// lists use them); r holds vertex v at v - sb, cmax the graph's chunk maxima, order
+// n places from lo.  Writes every vertex's label; returns, in every lane, whether some
+// vertex was not low (the round unites).
+template <typename WT, typename SEEN, typename OFF>
+__device__ __forceinline__ bool noi_scan_warp(int64_t lo, int64_t n, OFF offs, const int32_t* __restrict__ adj,
+                                              const WT* __restrict__ w, long long lam, long long* r, int64_t sb,
+                                              SEEN seen, long long* cmax, int32_t* order, int32_t* labels) {
+  const int lane = threadIdx.x & 31;
   const int64_t nc = (n + 31) >> 5;
-  for (int64_t k = lane; k < n; k += 32) {
-    r[lo + k - sb] = 0;
-    parent[lo + k - sb] = (int32_t)(lo + k - sb);
-  }
+  for (int64_t k = lane; k < n; k += 32) r[lo + k - sb] = 0;
   seen.clear(lo, n, lane);
   for (int64_t c = lane; c < nc; c += 32) cmax[c] = 0;
   __syncwarp();
+  const long long high = lam > 1 ? lam : 1;  // visited with r >= high: not low
+  bool unites = false;
+  int64_t s0 = 0;          // first place of the current run
+  int32_t runmin = 0;      // its smallest id
+  int32_t win = 0;         // see noi_flush_run
   long long best;
   for (int64_t step = 0; step < n; ++step) {
     long long bv = -1;
@@ -459,133 +499,131 @@ __device__ __forceinline__ void noi_round_warp(int64_t lo, int64_t hi, const int
     const int64_t k = (int64_t)C * 32 + lane;
     // the list bounds of the chunk's vertices load beside their attachments, so the
     // chosen vertex's list can be read as soon as it is known
-    const int64_t kb = k < n ? __ldg(off + lo + k) : 0, ke = k < n ? __ldg(off + lo + k + 1) : 0;
+    const int64_t kb = k < n ? offs.at(lo + k) : 0, ke = k < n ? offs.at(lo + k + 1) : 0;
     const long long rv = (k < n && !seen.test(lo + k)) ? r[lo + k - sb] : -1;
     const int xl = warp_argmax_vi(rv, (int)k, &best);
-    const int64_t x = lo + xl;
+    const long long rx = best;
+    const int32_t x = (int32_t)(lo + xl);
     const int64_t xb = __shfl_sync(0xffffffffu, kb, xl & 31), xe = __shfl_sync(0xffffffffu, ke, xl & 31);
+    if (rx < high) {  // x starts a run: the previous one is complete
+      if (step > 0) noi_flush_run(lo, s0, step, runmin, win, order, labels);
+      s0 = step;
+      runmin = x;
+    } else {
+      runmin = x < runmin ? x : runmin;
+      unites = true;
+    }
+    if (lane == (step & 31)) {
+      win = x;
+      order[lo + step] = x;
+    }
     if (k == xl) seen.set(x);
     warp_argmax_vi(k == xl ? -1 : rv, (int)k, &best);  // the chunk's maximum without x
     if (lane == 0) cmax[C] = best;
     __syncwarp();
-    for (int64_t e = xb + lane; e < xe; e += 32) {
-      const int y = adj[e];
-      if (seen.test(y)) continue;
-      const long long c = (long long)w[e];
-      const long long ry = (long long)atomicAdd((unsigned long long*)&r[y - sb], (unsigned long long)c) + c;
-      atomicMax(&cmax[(y - lo) >> 5], ry);
-      if (ry >= lam) sunite(parent, (int)(x - sb), (int)(y - sb));
+    for (int64_t e0 = xb; e0 < xe; e0 += 32 * kNoiUnroll) {
+      int32_t y[kNoiUnroll];
+      long long c[kNoiUnroll];
+#pragma unroll
+      for (int u = 0; u < kNoiUnroll; ++u) {
+        const int64_t e = e0 + lane + 32 * u;
+        y[u] = e < xe ? __ldg(adj + e) : -1;
+        c[u] = e < xe ? (long long)__ldg(w + e) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kNoiUnroll; ++u) {
+        if (y[u] < 0 || seen.test(y[u])) continue;
+        const long long ry =
+            (long long)atomicAdd((unsigned long long*)&r[y[u] - sb], (unsigned long long)c[u]) + c[u];
+        atomicMax(&cmax[(y[u] - lo) >> 5], ry);
+      }
     }
     __syncwarp();
   }
-  int any = 0;
-  for (int64_t k = lane; k < n; k += 32) {
-    const int64_t rt = sfind(parent, (int)(lo + k - sb)) + sb;
-    labels[lo + k] = (int32_t)rt;
-    any |= rt != lo + k;
-  }
-  if (__any_sync(0xffffffffu, any) && lane == 0) atomicOr(any_out, 1);
+  noi_flush_run(lo, s0, n, runmin, win, order, labels);
   __syncwarp();
+  return unites;
 }
 
-// The same round with the graph's state (attachments, chunk maxima, parents, seen
-// flags) in shared memory: a scan step then waits on one global read (the chosen
-// vertex's list) instead of several.  One warp per block; ncap = the largest graph.
+// The scan with the graph's state (attachments, chunk maxima, scanned flags and list
+// bounds) in shared memory: a step then waits on one global read (the chosen vertex's
+// list).  One warp per block.
 constexpr int kNoiSmemRoundMaxN = 15360;  // 15360 x 13 B + chunk maxima < 227 KB
 __host__ __device__ constexpr size_t noi_round_smem(int ncap) {
-  return (size_t)ncap * 13 + ((size_t)ncap / 32 + 1) * 8;
+  return (size_t)ncap * 13 + ((size_t)ncap / 32 + 1) * 8 + 16;
 }
 
-// Graphs above ncap vertices take the global arrays (gr: attachments then chunk
-// maxima over the whole union, gseen, gparent), as noi_round_batch_k does.
 template <typename WT>
-__global__ void __launch_bounds__(32) noi_round_smem_k(const int32_t* __restrict__ list, int count,
-                                                       const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(32) noi_round_smem_k(int64_t n, const int64_t* __restrict__ off,
                                                        const int32_t* __restrict__ adj, const WT* __restrict__ w,
-                                                       const long long* vbase, const long long* nv,
-                                                       const long long* glam, const DevState* st, int ncap,
-                                                       int64_t un, long long* gr, unsigned char* gseen,
-                                                       int32_t* gparent, int32_t* labels, int* gchanged) {
+                                                       const DevState* st, int32_t* order, int32_t* labels,
+                                                       int* changed) {
   extern __shared__ __align__(16) unsigned char noi_rs[];
   long long* r = (long long*)noi_rs;
-  long long* cmax = r + ncap;
-  int32_t* parent = (int32_t*)(cmax + ncap / 32 + 1);
-  unsigned char* seen = (unsigned char*)(parent + ncap);
-  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
-    const int g = list ? list[idx] : 0;
-    const long long lo = vbase ? vbase[g] : 0;
-    const long long n = nv ? nv[g] : (long long)ncap;
-    const long long lam = glam ? glam[g] : st->lambda_hat;
-    if (n <= ncap)
-      noi_round_warp<WT>(lo, lo + n, off, adj, w, lam, r, ByteSeen{seen, lo}, parent, cmax, labels, gchanged + g, lo);
-    else
-      noi_round_warp<WT>(lo, lo + n, off, adj, w, lam, gr, ByteSeen{gseen, 0}, gparent, gr + un + lo, labels,
-                         gchanged + g, 0);
-  }
+  long long* cmax = r + n;
+  int32_t* rel = (int32_t*)(cmax + n / 32 + 1);
+  unsigned char* seen = (unsigned char*)(rel + n + 1);
+  const int lane = threadIdx.x;
+  const int64_t base = off[0];
+  for (int64_t k = lane; k <= n; k += 32) rel[k] = (int32_t)(off[k] - base);
+  __syncwarp();
+  const bool any = noi_scan_warp<WT>(0, n, SharedOff{rel, 0, base}, adj, w, st->lambda_hat, r, 0, ByteSeen{seen, 0},
+                                     cmax, order, labels);
+  if (any && lane == 0) atomicOr(changed, 1);
 }
 
-template <typename WT>
-static void noi_round_smem_launch(const int32_t* list, int count, const int64_t* off, const int32_t* adj,
-                                  const WT* w, const long long* vbase, const long long* nv, const long long* glam,
-                                  const DevState* st, int ncap, int64_t un, long long* gr, unsigned char* gseen,
-                                  int32_t* gparent, int32_t* labels, int* gchanged, cudaStream_t s) {
-  static std::mutex mu;
-  static std::unordered_map<int, bool> ready;  // per device: the shared-memory limit was raised
-  {
-    int dev = 0;
-    VC_CUDA(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lk(mu);
-    if (!ready[dev]) {
-      VC_CUDA(cudaFuncSetAttribute(noi_round_smem_k<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)noi_round_smem(kNoiSmemRoundMaxN)));
-      ready[dev] = true;
-    }
-  }
-  const size_t smem = noi_round_smem(ncap);
-  const int per_sm = (int)std::max<size_t>(1, (size_t)(227 * 1024) / (smem + 1024));
-  const int blocks = std::min(count, kSMs * std::min(per_sm, 32));
-  noi_round_smem_k<WT><<<blocks, 32, smem, s>>>(list, count, off, adj, w, vbase, nv, glam, st, ncap, un, gr, gseen,
-                                                gparent, labels, gchanged);
-  count_launch();
-  VC_CHECK_LAUNCH();
-}
-
+// Above the shared-memory size: the same scan on global arrays (r holds n
+// attachments, then the chunk maxima).
 template <typename WT>
 __global__ void __launch_bounds__(32) noi_round_k(int64_t n, const int64_t* __restrict__ off,
                                                   const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                   const DevState* st, long long* r, unsigned char* seen,
-                                                  int32_t* parent, long long* cmax, int32_t* labels, int* changed) {
-  noi_round_warp<WT>(0, n, off, adj, w, st->lambda_hat, r, ByteSeen{seen, 0}, parent, cmax, labels, changed, 0);
+                                                  int32_t* order, int32_t* labels, int* changed) {
+  const bool any = noi_scan_warp<WT>(0, n, GlobalOff{off}, adj, w, st->lambda_hat, r, 0, ByteSeen{seen, 0}, r + n,
+                                     order, labels);
+  if (any && threadIdx.x == 0) atomicOr(changed, 1);
 }
 
-void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, unsigned char* seen,
-                      int32_t* parent, int32_t* labels, int* changed, cudaStream_t s) {
-  if (g.n <= kNoiSmemRoundMaxN) {
-    if (g.wbytes == 4)
-      noi_round_smem_launch<int32_t>(nullptr, 1, g.off, g.adj, (const int32_t*)g.w, nullptr, nullptr, nullptr, st,
-                                     (int)g.n, g.n, r, seen, parent, labels, changed, s);
-    else
-      noi_round_smem_launch<long long>(nullptr, 1, g.off, g.adj, (const long long*)g.w, nullptr, nullptr, nullptr, st,
-                                       (int)g.n, g.n, r, seen, parent, labels, changed, s);
-    return;
+template <typename WT>
+static void noi_scan_launch(const GraphView& g, const DevState* st, long long* r, unsigned char* seen,
+                            int32_t* order, int32_t* labels, int* changed, cudaStream_t s) {
+  // offsets relative to the first entry fit 32 bits whenever the graph has < 2^31 entries
+  if (g.n <= kNoiSmemRoundMaxN && g.nnz < INT_MAX) {
+    static std::mutex mu;
+    static std::unordered_map<int, bool> ready;  // per device: the shared-memory limit was raised
+    {
+      int dev = 0;
+      VC_CUDA(cudaGetDevice(&dev));
+      std::lock_guard<std::mutex> lk(mu);
+      if (!ready[dev]) {
+        VC_CUDA(cudaFuncSetAttribute(noi_round_smem_k<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)noi_round_smem(kNoiSmemRoundMaxN)));
+        ready[dev] = true;
+      }
+    }
+    noi_round_smem_k<WT><<<1, 32, noi_round_smem((int)g.n), s>>>(g.n, g.off, g.adj, (const WT*)g.w, st, order, labels,
+                                                                 changed);
+  } else {
+    noi_round_k<WT><<<1, 32, 0, s>>>(g.n, g.off, g.adj, (const WT*)g.w, st, r, seen, order, labels, changed);
   }
-  // r holds 2n entries: the attachments, then the chunk maxima
-  long long* cmax = r + g.n;
-  if (g.wbytes == 4)
-    noi_round_k<int32_t><<<1, 32, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, st, r, seen, parent, cmax, labels,
-                                          changed);
-  else
-    noi_round_k<long long><<<1, 32, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, st, r, seen, parent, cmax,
-                                            labels, changed);
   count_launch();
   VC_CHECK_LAUNCH();
 }
 
-// Batches: one round for each listed graph, a warp per graph (persistent grid of
-// 8-warp blocks pulling graphs from the list).  With ncap > 0 (every listed graph of at
-// most ncap vertices) each warp keeps its graph's chunk maxima and scanned bits in
-// shared memory, so that a scan step waits on fewer global reads; the attachments and
-// parents stay in global memory (every graph of the list in flight at once).
+void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, unsigned char* seen,
+                      int32_t* parent, int32_t* labels, int* changed, cudaStream_t s) {
+  // parent (n entries) holds the visiting order
+  if (g.wbytes == 4)
+    noi_scan_launch<int32_t>(g, st, r, seen, parent, labels, changed, s);
+  else
+    noi_scan_launch<long long>(g, st, r, seen, parent, labels, changed, s);
+}
+
+// Batches: the scan of each listed graph by a warp (persistent grid of 8-warp blocks
+// pulling graphs from the list).  With ncap > 0 (every listed graph of at most ncap
+// vertices) each warp keeps its graph's chunk maxima and scanned bits in shared
+// memory; the attachments stay in global memory (every graph of the list in flight
+// at once).
 __host__ __device__ constexpr size_t noi_batch_warp_smem(int ncap) { return (size_t)(ncap / 32 + 1) * 12; }
 constexpr size_t kNoiBatchSmemMax = 160 * 1024;
 
@@ -595,30 +633,32 @@ __global__ void __launch_bounds__(256) noi_round_batch_k(const int32_t* __restri
                                                          const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                          const long long* vbase, const long long* nv,
                                                          const long long* glam, long long* r, unsigned char* seen,
-                                                         int32_t* parent, long long* cmax, int32_t* labels,
+                                                         int32_t* order, long long* cmax, int32_t* labels,
                                                          int* gchanged, int ncap) {
   extern __shared__ __align__(16) unsigned char noi_bs[];
   const int warps = gridDim.x * (blockDim.x >> 5);
-  const int wid = threadIdx.x >> 5;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int words = ncap / 32 + 1;
   long long* wc = (long long*)noi_bs + (size_t)wid * words;
   unsigned* wb = (unsigned*)((long long*)noi_bs + (size_t)(blockDim.x >> 5) * words) + (size_t)wid * words;
   for (int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < count; idx += warps) {
     const int g = list[idx];
-    const long long lo = vbase[g];
-    if (ncap > 0 && nv[g] <= ncap)
-      noi_round_warp<WT>(lo, lo + nv[g], off, adj, w, glam[g], r, BitSeen{wb, lo}, parent, wc, labels, gchanged + g,
-                         0);
+    const long long lo = vbase[g], n = nv[g];
+    bool any;
+    if (ncap > 0 && n <= ncap)
+      any = noi_scan_warp<WT>(lo, n, GlobalOff{off}, adj, w, glam[g], r, 0, BitSeen{wb, lo}, wc, order, labels);
     else
-      noi_round_warp<WT>(lo, lo + nv[g], off, adj, w, glam[g], r, ByteSeen{seen, 0}, parent, cmax + lo, labels,
-                         gchanged + g, 0);
+      any = noi_scan_warp<WT>(lo, n, GlobalOff{off}, adj, w, glam[g], r, 0, ByteSeen{seen, 0}, cmax + lo, order,
+                              labels);
+    if (any && lane == 0) atomicOr(gchanged + g, 1);
+    __syncwarp();
   }
 }
 
 template <typename WT>
 static void noi_round_batch_launch(const GraphView& u, const int32_t* list, int count, const long long* vbase,
                                    const long long* nv, const long long* glam, long long* r, unsigned char* seen,
-                                   int32_t* parent, long long* cmax, int32_t* labels, int* gchanged, int max_n,
+                                   int32_t* order, long long* cmax, int32_t* labels, int* gchanged, int max_n,
                                    cudaStream_t s) {
   static std::mutex mu;
   static std::unordered_map<int, bool> ready;  // per device: the shared-memory limit was raised
@@ -636,7 +676,7 @@ static void noi_round_batch_launch(const GraphView& u, const int32_t* list, int 
   const bool in_smem = max_n > 0 && smem <= kNoiBatchSmemMax;
   const int blocks = grid_for(count, 8, kSMs * 4);
   noi_round_batch_k<WT><<<blocks, 256, in_smem ? smem : 0, s>>>(list, count, u.off, u.adj, (const WT*)u.w, vbase, nv,
-                                                               glam, r, seen, parent, cmax, labels, gchanged,
+                                                               glam, r, seen, order, cmax, labels, gchanged,
                                                                in_smem ? max_n : 0);
   count_launch();
   VC_CHECK_LAUNCH();
@@ -646,10 +686,12 @@ void noi_round_batch(const GraphView& u, const int32_t* list, int count, const l
                      const long long* glam, long long* r, unsigned char* seen, int32_t* parent, int32_t* labels,
                      int* gchanged, int max_n, cudaStream_t s) {
   if (count <= 0) return;
-  // r holds 2 x (union size) entries: attachments, then each graph's chunk maxima at its own range
+  // r holds noi_round_scratch(union size) entries: attachments, then each graph's
+  // chunk maxima at its own range; parent (union size) holds the visiting orders
   long long* cmax = r + u.n;
   if (u.wbytes == 4)
-    noi_round_batch_launch<int32_t>(u, list, count, vbase, nv, glam, r, seen, parent, cmax, labels, gchanged, max_n, s);
+    noi_round_batch_launch<int32_t>(u, list, count, vbase, nv, glam, r, seen, parent, cmax, labels, gchanged, max_n,
+                                    s);
   else
     noi_round_batch_launch<long long>(u, list, count, vbase, nv, glam, r, seen, parent, cmax, labels, gchanged, max_n,
                                       s);

@@ -310,7 +310,7 @@ static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, u
     W.span(kPhOther, a0);
     while (!done && G.n > kDenseMax) {
       cudaEvent_t an = W.mark();
-      W.noi_r.ensure_n<long long>(2 * G.n + 64);
+      W.noi_r.ensure_n<long long>(noi_round_scratch(G.n));
       W.noi_seen.ensure_n<unsigned char>(G.n);
       VC_CUDA(cudaMemsetAsync(&W.ctr()->changed, 0, sizeof(int), s));
       noi_round_sparse(G, st, W.noi_r.as<long long>(), W.noi_seen.as<unsigned char>(), W.parent.as<int32_t>(),
@@ -898,7 +898,7 @@ static int step_labels(viecut_graph* g, int64_t lambda_hat, int32_t* labels, int
     else
       vc::pr_pass_b(v, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), W.st(), lab, chg, c.s);
   } else {
-    W.noi_r.ensure_n<long long>(2 * v.n + 64);
+    W.noi_r.ensure_n<long long>(vc::noi_round_scratch(v.n));
     W.noi_seen.ensure_n<unsigned char>(v.n);
     vc::noi_round_sparse(v, W.st(), W.noi_r.as<long long>(), W.noi_seen.as<unsigned char>(), W.parent.as<int32_t>(),
                          lab, chg, c.s);

@@ -114,6 +114,56 @@ def test_noi_round_contracts_safely():
             assert lam == lhat
 
 
+def ma_runs_labels(g, lam):
+    """Labels of a NOI round derived from the scan alone: the maximum-adjacency order
+    (largest attachment, ties to the smallest id) is cut before every vertex visited
+    with attachment below max(lam, 1), and each run is labelled with its smallest id.
+    With positive weights this equals uniting every x, y with r(y) >= lam after x's
+    edge (Sec. 3): a vertex reaches lam only after the last such cut before it."""
+    n = len(g.offsets) - 1
+    r = [0] * n
+    seen = [False] * n
+    order, starts = [], []
+    for _ in range(n):
+        x = min((v for v in range(n) if not seen[v]), key=lambda v: (-r[v], v))
+        starts.append(r[x] < max(lam, 1))
+        order.append(x)
+        seen[x] = True
+        for e in range(g.offsets[x], g.offsets[x + 1]):
+            y = int(g.adj[e])
+            if not seen[y]:
+                r[y] += int(g.w[e])
+    labels = np.empty(n, dtype=np.int32)
+    i = 0
+    while i < n:
+        j = i + 1
+        while j < n and not starts[j]:
+            j += 1
+        labels[order[i:j]] = min(order[i:j])
+        i = j
+    return labels, sum(not s for s in starts)
+
+
+def test_noi_round_components_are_runs_of_the_scan_order():
+    """The union-find of a NOI round (smallest-id roots) yields exactly the runs of the
+    visiting order that start at a vertex below max(lambda-hat, 1): checked on random
+    weighted graphs, connected or not, for bounds below, at and above the minimum
+    degree (the GPU round labels runs instead of uniting)."""
+    for seed in range(120):
+        rnd = random.Random(7000 + seed)
+        n = rnd.randint(2, 40)
+        g = H.random_graph(n, rnd.choice([0.08, 0.2, 0.5]), 9000 + seed, wmax=rnd.choice([1, 3, 9]),
+                           connected=seed % 3 != 0)
+        G = oracle.as_csr64(g.offsets, g.adj, g.w)
+        deg = oracle.degrees(G)
+        dmin = int(deg.min())
+        for lam in sorted({0, 1, max(1, dmin // 2), dmin, dmin + 3, int(deg.max()) + 1}):
+            got, highs = ma_runs_labels(g, lam)
+            ref, unions = oracle.noi_round(G, lam)
+            assert np.array_equal(got, ref), (seed, lam)
+            assert (highs > 0) == (unions > 0), (seed, lam)
+
+
 # ----------------------------------------------------- label propagation pins
 def test_lp_weighted_star_hand():
     # centre 0, leaves 1..4 with weights 5, 3, 3, 1; no ties anywhere.
