@@ -535,7 +535,7 @@ static void engine_setup(Engine& E, int K, const viecut_opts& o) {
   E.list_noid.ensure_n<int32_t>(K);
   E.list_nois.ensure_n<int32_t>(K);
   E.sideK.ensure_n<unsigned char>((int64_t)K * kDenseMax);
-  E.noiCurK.ensure_n<int32_t>((int64_t)kSMs * kDenseMax);
+  E.noiCurK.ensure_n<int32_t>((int64_t)kSMs * kNoiDenseBlocksPerSM * kDenseMax);  // per dense-step block
   VC_CUDA(cudaMemsetAsync(E.phase.p, 0, sizeof(int) * K, E.stream));
   {
     std::vector<int> gone(K, kBGone);
@@ -631,7 +631,9 @@ static bool engine_step(Engine& E) {
   }
   if (cnt[kBNoiD] > 0) {
     const int64_t mcap = (int64_t)cnt[7] * cnt[7];
-    const int blocks = cnt[kBNoiD] < kSMs ? cnt[kBNoiD] : kSMs;
+    // up to four blocks per SM (a dense round waits on a row read per scan step:
+    // graphs in flight hide it); each block keeps its own two matrices
+    const int blocks = std::min(cnt[kBNoiD], kSMs * kNoiDenseBlocksPerSM);
     long long* M = E.noiM.ensure_n<long long>(2 * mcap * blocks);
     BatchNoi bn{S.lam, S.best_kind, S.nv, S.nnz, S.dmin, S.argmin, S.trace_len, S.trace, kBTraceCap, S.level};
     noi_dense_batch(G, S.list_noid, cnt[kBNoiD], S.vbase, S.nv, M, mcap, blocks, E.noiCurK.as<int32_t>(),

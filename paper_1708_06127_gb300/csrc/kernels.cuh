@@ -300,6 +300,8 @@ struct BatchNoi {
   int trace_cap;
   const int* level;
 };
+// Blocks per SM of the batches' dense exact step (512 threads and 32 registers each).
+constexpr int kNoiDenseBlocksPerSM = 4;
 // Dense rounds for the listed graphs of a union u (vertex range [vbase[g], +nv[g])),
 // `blocks` persistent blocks with 2 x mcap matrix entries and kDenseMax curK each;
 // sideK holds kDenseMax bytes per graph.
