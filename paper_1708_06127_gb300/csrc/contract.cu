@@ -313,7 +313,19 @@ __global__ void __launch_bounds__(256) cluster_merge_k(int64_t c, const long lon
         L.todo |= 1u << r;
       }
     }
-    if (!sort_first || T < kMergeSortMin) {
+    bool walk = !sort_first || T < kMergeSortMin;
+    if (walk && T >= kMergeSortMin) {
+      // probe: the distinct targets among the first row's pairs (one match); a row more
+      // than half distinct (a cluster of one or two vertices of a weakly clustered
+      // graph, or a long run of an exact-step round) is sorted without walking first
+      const bool use = lane < T;
+      const unsigned long long tag =
+          use ? (unsigned long long)(uint32_t)L.k[0] : (0xffffffff00000000ull | (unsigned long long)lane);
+      const unsigned peers = __match_any_sync(0xffffffffu, tag);
+      const int nd = __popc(__ballot_sync(0xffffffffu, use && (__ffs(peers) - 1) == lane));
+      if (2 * nd > (T < 32 ? T : 32)) walk = false;
+    }
+    if (walk) {
       int made = 0;  // warp-uniform
       int32_t ok = INT_MAX;
       long long ov = 0;

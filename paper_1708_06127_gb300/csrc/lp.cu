@@ -429,6 +429,7 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
 // group it already holds the next vertex's ids and the offsets of the one after.
 
 constexpr int kEmitBailKeys = 64;
+constexpr int kEmitWalkKeys = 6;
 constexpr int kLpBailKeys = 16;
 
 // Neighbour ids (and weights) of one list in registers.
@@ -654,9 +655,11 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restr
     reg_keys<kModeEmit, false, G, S>(L, ids, (mine && own >= 0) ? (int)d : 0, cid, own);
     if (!(mine && own >= 0)) L.todo = 0;
     int made = 0;  // the same in the group's lanes
-    if (rows) {
-      // row r holds entries r G .. r G + G - 1: lanes holding the same key (tagged with
-      // the group) match, the lowest of them sums its peers' weights and writes the pair
+    // one pass per row r (entries r G .. r G + G - 1) over the entries still to do:
+    // lanes holding the same key (tagged with the group) match, the lowest of them sums
+    // its peers' weights and writes the pair (a key met in several rows gives several
+    // pairs, which the cluster merge sums)
+    auto row_pass = [&]() {
       const int ws = __reduce_max_sync(0xffffffffu, L.slots);
 #pragma unroll
       for (int r = 0; r < S; ++r) {
@@ -685,33 +688,46 @@ __global__ void __launch_bounds__(kAggThreads) emit_reg_k(const int32_t* __restr
         if (lead) out.put(v, beg, made + __popc(lb & ((1u << lane) - 1u)), L.k[r], sum);
         made += __popc(lb);
       }
+      L.todo = 0;
+    };
+    auto finish = [&]() {
       if (mine && glane == 0) {
         cnt[v] = made;
         if (out.ccount && made) atomicAdd(&out.ccount[own], made);
       }
+    };
+    if (rows) {
+      row_pass();
+      finish();
       return;
     }
     int32_t pk = 0;
     long long pv = 0;
-    // with a bail list, a list reaching kEmitBailKeys foreign clusters is handed to the
-    // chunk kernel (a step per key costs slots x compares: long lists with many keys
-    // run faster in chunks)
+    // the walk takes one step per distinct key.  In the short classes (no bail list) a
+    // group still holding keys after kEmitWalkKeys steps (a list with many foreign
+    // clusters) finishes with the row pass; in the long class a list reaching
+    // kEmitBailKeys keys is handed to the chunk kernel.
     bool bailed = false;
+    unsigned left = 0;
     reg_visit<WT, long long, G, S>(L, gmask, [&](int32_t kk, long long t) {
       if (glane == (made & (G - 1))) { pk = kk; pv = t; }
       if ((++made & (G - 1)) == 0) out.put(v, beg, made - G + glane, pk, pv);
-      if (bail_list && made >= kEmitBailKeys) { bailed = true; return true; }
+      if (bail_list) {
+        if (made >= kEmitBailKeys) { bailed = true; return true; }
+      } else if (made >= kEmitWalkKeys) {
+        left = L.todo;
+        return true;
+      }
       return false;
     });
     if (bailed) {
       if (glane == 0) bail_list[atomicAdd(bail_count, 1)] = (int32_t)v;
-    } else {
-      if (glane < (made & (G - 1))) out.put(v, beg, (made & ~(G - 1)) + glane, pk, pv);
-      if (mine && glane == 0) {
-        cnt[v] = made;
-        if (out.ccount && made) atomicAdd(&out.ccount[own], made);
-      }
+      return;
     }
+    if (glane < (made & (G - 1))) out.put(v, beg, (made & ~(G - 1)) + glane, pk, pv);
+    L.todo = left;
+    if (__any_sync(0xffffffffu, left != 0u)) row_pass();
+    finish();
   });
 }
 
