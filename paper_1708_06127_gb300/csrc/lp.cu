@@ -431,6 +431,13 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
 constexpr int kEmitBailKeys = 64;
 constexpr int kEmitWalkKeys = 6;
 constexpr int kLpBailKeys = 16;
+constexpr int kLpWalkKeys = 8;      // short classes: labels walked before the table
+constexpr int kLpTableMaxS = 4;     // classes of at most this many slots per lane
+constexpr int kLpTableSlots = 256;  // table slots per warp (split between its groups)
+// The table serves weighted graphs only: on unit weights its registers and shared
+// memory cost an SM block of the kernel, and lists with many labels are rare there.
+template <typename WT, int S>
+constexpr bool lp_has_table() { return S <= kLpTableMaxS && !std::is_same<WT, UnitW>::value; }
 
 // Neighbour ids (and weights) of one list in registers.
 template <int S>
@@ -534,6 +541,18 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
   const int lane = threadIdx.x & 31, glane = lane & (G - 1), gi = lane / G;
   const unsigned gmask = group_mask<G>(lane);
   constexpr int kPer = 32 / G;  // vertices per warp
+  // the short classes' tables (see below), one region of kLpTableSlots per warp
+  __shared__ int32_t s_tab_k[lp_has_table<WT, S>() ? kWarpsPerBlock * kLpTableSlots : 1];
+  __shared__ ACC s_tab_v[lp_has_table<WT, S>() ? kWarpsPerBlock * kLpTableSlots : 1];
+  int32_t* tab_k = s_tab_k + (lp_has_table<WT, S>() ? (threadIdx.x >> 5) * kLpTableSlots : 0);
+  ACC* tab_v = s_tab_v + (lp_has_table<WT, S>() ? (threadIdx.x >> 5) * kLpTableSlots : 0);
+  if (lp_has_table<WT, S>()) {
+    for (int i = lane; i < kLpTableSlots; i += 32) {
+      tab_k[i] = kEmptyKey;
+      tab_v[i] = 0;
+    }
+    __syncwarp();
+  }
   const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock * kPer;
   const int64_t first = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kPer;
   // pre(v): v's own label from the previous round (INT_MIN: v is not active)
@@ -599,11 +618,14 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
         if (bs > left) L.todo = 0;
       }
     }
-    // with a bail list, a vertex still undecided after kLpBailKeys labels (a list whose
-    // neighbours carry many different labels, where a step per label costs slots x
-    // compares) is handed to the hash-table kernel instead
+    // a vertex still undecided after a number of labels (a list whose neighbours carry
+    // many different labels, where a step per label costs slots x compares) goes on
+    // elsewhere: with a bail list (long class) to the hash-table kernel after
+    // kLpBailKeys labels; in the short classes, after kLpWalkKeys labels, its remaining
+    // entries are summed in the group's shared-memory table below
     int visited = 0;
     bool bailed = false;
+    unsigned rest = 0;
     reg_visit<WT, ACC, G, S>(L, gmask, [&](int32_t kk, ACC t) {
       left -= t;
       if (bl < 0 || t > bs) {
@@ -616,12 +638,61 @@ __global__ void __launch_bounds__(kAggThreads) lp_reg_k(const int32_t* __restric
         if (h > bh || (h == bh && kk < bl)) { bh = h; bl = kk; }
       }
       if (bs > left) return true;
-      if (bail_list && ++visited >= kLpBailKeys) {
-        bailed = true;
+      ++visited;
+      if (bail_list) {
+        if (visited >= kLpBailKeys) {
+          bailed = true;
+          return true;
+        }
+      } else if (lp_has_table<WT, S>() && visited >= kLpWalkKeys) {
+        rest = L.todo;
         return true;
       }
       return false;
     });
+    if constexpr (lp_has_table<WT, S>()) if (!bail_list && __any_sync(0xffffffffu, rest != 0u)) {
+      // the group's table: CAPG slots (twice its list capacity); every remaining entry
+      // adds its weight to its label's slot, then the group takes the best slot and
+      // compares it with the walk's best; the slots are emptied for the next vertex
+      constexpr int CAPG = kLpTableSlots / (32 / G);
+      constexpr int LG = CAPG >= 256 ? 8 : 7;
+      static_assert((1 << LG) == CAPG && CAPG >= 2 * S * G, "table of twice the list capacity");
+      int32_t* tk = tab_k + gi * CAPG;
+      ACC* tv = tab_v + gi * CAPG;
+      const bool grest = (__ballot_sync(0xffffffffu, rest != 0u) & gmask) != 0u;
+#pragma unroll
+      for (int r = 0; r < S; ++r)
+        if ((rest >> r) & 1u) tbl_add<ACC>(tk, tv, LG, L.k[r], L.wt[r]);
+      __syncwarp();
+      LaneBest lb;
+      if (grest) {
+        for (int i = glane; i < CAPG; i += G) {
+          const int32_t key = tk[i];
+          if (key != kEmptyKey) {
+            lb.add((long long)tv[i], key, hv);
+            tk[i] = kEmptyKey;
+            tv[i] = 0;
+          }
+        }
+      }
+      Cand cd = lb.done(hv);
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) {
+        Cand e;
+        e.s = __shfl_xor_sync(0xffffffffu, cd.s, o);
+        e.h = __shfl_xor_sync(0xffffffffu, cd.h, o);
+        e.l = __shfl_xor_sync(0xffffffffu, cd.l, o);
+        if (better(e, cd)) cd = e;
+      }
+      if (grest) {
+        if (bl >= 0) {
+          const Cand wb{(long long)bs, hashed ? bh : __ldg(hv + bl), bl};
+          if (better(wb, cd)) cd = wb;
+        }
+        bl = cd.l;
+      }
+      __syncwarp();
+    }
     if (mine && d > 0 && glane == 0) {
       if (bailed) bail_list[atomicAdd(bail_count, 1)] = (int32_t)v;
       else lab_out[v] = bl;
