@@ -625,9 +625,9 @@ static bool engine_step(Engine& E) {
   }
   if (cnt[kBNoiS] > 0) {
     W.noi_r.ensure_n<long long>(noi_round_scratch(G.n));
-    W.noi_seen.ensure_n<unsigned char>(G.n);
+    W.noi_seen.ensure_n<int>(G.n);
     noi_round_batch(G, S.list_nois, cnt[10], S.vbase, S.nv, S.lam, W.noi_r.as<long long>(),
-                    W.noi_seen.as<unsigned char>(), W.parent.as<int32_t>(), F, S.changed, cnt[11], s);
+                    W.noi_seen.as<int>(), W.parent.as<int32_t>(), F, S.changed, cnt[11], s);
   }
   if (cnt[kBNoiD] > 0) {
     const int64_t mcap = (int64_t)cnt[7] * cnt[7];

@@ -281,9 +281,9 @@ void noi_dense(const GraphView& g, long long* M0, long long* M1, int32_t* curK, 
                DevState* st, TraceStep* trace, int trace_cap, int level, cudaStream_t s);
 // One round of the maximum-adjacency scan on a larger graph; labels = union-find roots.
 // Scratch of a sparse exact-step round (r of noi_round_sparse / noi_round_batch), in
-// int64 entries, for a graph (or union) of n vertices: attachments, then chunk maxima.
+// int64 entries, for a graph (or union) of n vertices: attachments, then chunk bounds.
 inline int64_t noi_round_scratch(int64_t n) { return 2 * n + 64; }
-void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, unsigned char* seen,
+void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, int* seen,
                       int32_t* parent, int32_t* labels, int* changed, cudaStream_t s);
 
 // Per-graph result arrays of a batch's exact step (indexed by graph; trace holds
@@ -311,6 +311,6 @@ void noi_dense_batch(const GraphView& u, const int32_t* list, int count, const l
 // One sparse round for each listed graph; labels and gchanged written per graph.
 // max_n: the largest listed graph (its state then fits in shared memory; 0 = unknown)
 void noi_round_batch(const GraphView& u, const int32_t* list, int count, const long long* vbase, const long long* nv,
-                     const long long* glam, long long* r, unsigned char* seen, int32_t* parent, int32_t* labels,
+                     const long long* glam, long long* r, int* seen, int32_t* parent, int32_t* labels,
                      int* gchanged, int max_n, cudaStream_t s);
 }  // namespace vc

@@ -388,24 +388,27 @@ __device__ __forceinline__ void noi_round_body(int64_t lo, int64_t hi, const int
   __syncthreads();
 }
 
-// ---- the same round by one warp, without a union-find.  The next vertex is found in
-// two levels: cmax[c] holds the largest attachment r of the unvisited vertices of
-// chunk c = 32 consecutive vertices (-1: all visited); the warp picks the chunk of
-// largest cmax (ties: lower chunk, hence smaller ids), then the vertex of largest r in
-// it (ties: smallest id).  Relaxing a neighbour raises its chunk's maximum with
-// atomicMax; visiting a vertex recomputes its chunk's maximum.
+// ---- the same round by one warp, as closures.  Call a vertex "low" when it is visited
+// with attachment r < max(lambda-hat, 1).  When a low vertex u is visited every
+// unvisited r is at most r(u), so no unvisited vertex has reached lambda-hat; the
+// vertices visited after u up to the next low vertex are then exactly the closure of
+// u: the smallest set R holding u such that every vertex outside R and outside the
+// earlier runs has fewer than lambda-hat of weight into the vertices visited so far.
+// Adding a vertex only raises the weights into the set, so the closure does not depend
+// on the order in which its vertices are added, and neither do the attachments of the
+// vertices left afterwards; the next low vertex (the largest r, ties to the smallest
+// id) is therefore the same as in the maximum-adjacency order.  The round unites every
+// x, y with r(y) >= lambda-hat once x's edge is added; each such pair lies within one
+// run, and every vertex of a run is joined to the vertex whose edge raised it to
+// lambda-hat (visited inside the run), so the round's components are the runs and the
+// union-find with smallest-id roots labels each run with its smallest id.
 //
-// The round's unions need no union-find.  Call a vertex "low" when it is visited with
-// r < max(lambda-hat, 1) (no edge raised it to lambda-hat; with lambda-hat <= 0: no
-// visited neighbour).  When a low vertex u is visited every unvisited r is at most
-// r(u), so no unvisited vertex has reached lambda-hat yet.  A vertex y visited later
-// and not low reached lambda-hat through the edge of some x visited after u and
-// before y, and the round unites x and y; so every vertex is joined to the last low
-// vertex before it, and every united pair (x visited after y's last low vertex, as r(y)
-// reaches lambda-hat only after it) lies within one such run.  The round's components
-// are therefore the runs of the visiting order that start at a low vertex, and the
-// union-find with smallest-id roots labels each run with its smallest id.  The scan
-// records the order (order[place]) and writes a run's labels when the next run starts.
+// So a round needs the exact order only to pick each run's first vertex (an argmax
+// over the vertices not yet taken); a run then grows level by level, the warp relaxing
+// up to 32 queued vertices at once: their lists are laid end to end over the lanes, a
+// vertex whose attachment reaches lambda-hat joins the queue, and the run's labels are
+// written when it stops growing.  queue (n entries from lo) holds the vertices in the
+// order they were taken.
 
 // argmax over the warp of (val, -idx) for val >= 0 (val < 0: no candidate); returns
 // idx, or -1 if no lane has a candidate; *best = the value.
@@ -420,17 +423,18 @@ __device__ __forceinline__ int warp_argmax_vi(long long val, int idx, long long*
   return mu == 0 ? -1 : (int)wi;
 }
 
-// Scanned flags of a round: a byte per vertex at v - sb, or a bit per vertex of the graph
-// [lo, lo + n) (one warp owns the words; a step sets one flag from one lane, then the
-// warp synchronises).
-struct ByteSeen {
-  unsigned char* p;
+// Taken flags of a round: an int per vertex at v - sb (global memory, where graphs of a
+// union sit side by side), or a bit per vertex of the graph [lo, lo + n) in words the
+// warp owns (shared memory).  claim(v) takes v and returns whether it was not taken
+// yet: a vertex joins a queue at most once, whatever the weights.
+struct WordSeen {
+  int* p;
   int64_t sb;
   __device__ __forceinline__ void clear(int64_t lo, int64_t n, int lane) const {
     for (int64_t k = lane; k < n; k += 32) p[lo + k - sb] = 0;
   }
-  __device__ __forceinline__ bool test(int64_t v) const { return p[v - sb] != 0; }
-  __device__ __forceinline__ void set(int64_t v) const { p[v - sb] = 1; }
+  __device__ __forceinline__ bool test(int64_t v) const { return ((volatile int*)p)[v - sb] != 0; }
+  __device__ __forceinline__ bool claim(int64_t v) const { return atomicExch(&p[v - sb], 1) == 0; }
 };
 struct BitSeen {
   unsigned* bits;
@@ -438,157 +442,176 @@ struct BitSeen {
   __device__ __forceinline__ void clear(int64_t, int64_t n, int lane) const {
     for (int64_t k = lane; k < ((n + 31) >> 5); k += 32) bits[k] = 0;
   }
-  __device__ __forceinline__ bool test(int64_t v) const { return (bits[(v - lo) >> 5] >> ((v - lo) & 31)) & 1u; }
-  __device__ __forceinline__ void set(int64_t v) const { bits[(v - lo) >> 5] |= 1u << ((v - lo) & 31); }
-};
-
-// List bounds of vertex v: the CSR's own offsets, or a copy of the graph's offsets in
-// shared memory relative to its first entry (a step then reads only the chosen
-// vertex's list from global memory).
-struct GlobalOff {
-  const int64_t* off;
-  __device__ __forceinline__ int64_t at(int64_t v) const { return __ldg(off + v); }
-};
-struct SharedOff {
-  const int32_t* rel;  // rel[k] = off[lo + k] - base, k = 0..n
-  int64_t lo, base;
-  __device__ __forceinline__ int64_t at(int64_t v) const { return base + rel[v - lo]; }
+  __device__ __forceinline__ bool test(int64_t v) const {
+    return (((volatile unsigned*)bits)[(v - lo) >> 5] >> ((v - lo) & 31)) & 1u;
+  }
+  __device__ __forceinline__ bool claim(int64_t v) const {
+    const unsigned bit = 1u << ((v - lo) & 31);
+    return (atomicOr(&bits[(v - lo) >> 5], bit) & bit) == 0u;
+  }
 };
 
 constexpr int kNoiUnroll = 4;  // list entries in flight per lane while relaxing
 
-// Labels of the run of places [s0, s1): m, the run's smallest id.  Lane L holds in
-// `win` the vertex visited at the latest place p < s1 with p % 32 == L; older places
-// are read back from order.
-__device__ __forceinline__ void noi_flush_run(int64_t lo, int64_t s0, int64_t s1, int32_t m, int32_t win,
-                                              const int32_t* order, int32_t* labels) {
+// One round over the graph [lo, lo + n) (ids global: labels, queue and the lists use
+// them); r holds vertex v at v - sb, queue the n taken vertices from lo (at q - qb for
+// place q: qb = 0 for a queue over the whole id range, lo for the graph's own array).
+// Writes every vertex's label; returns, in every lane, whether some run holds two or
+// more vertices (the round unites).
+template <typename WT, typename SEEN>
+__device__ __forceinline__ bool noi_closure_warp(int64_t lo, int64_t n, const int64_t* __restrict__ off,
+                                                 const int32_t* __restrict__ adj, const WT* __restrict__ w,
+                                                 long long lam, long long* r, int64_t sb, SEEN seen,
+                                                 long long* cmax, int32_t* queue, int64_t qb, int32_t* labels) {
   const int lane = threadIdx.x & 31;
-  for (int64_t p = s0 + lane; p < s1 - 32; p += 32) labels[order[lo + p]] = m;
-  const int64_t pl = s1 - 1 - ((s1 - 1 - lane) & 31);
-  if (pl >= s0) labels[win] = m;
-}
-
-// The scan of one round over the graph [lo, lo + n) (ids global: labels, order and the
-// lists use them); r holds vertex v at v - sb, cmax the graph's chunk maxima, order
-// n places from lo.  Writes every vertex's label; returns, in every lane, whether some
-// vertex was not low (the round unites).
-template <typename WT, typename SEEN, typename OFF>
-__device__ __forceinline__ bool noi_scan_warp(int64_t lo, int64_t n, OFF offs, const int32_t* __restrict__ adj,
-                                              const WT* __restrict__ w, long long lam, long long* r, int64_t sb,
-                                              SEEN seen, long long* cmax, int32_t* order, int32_t* labels) {
-  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
   const int64_t nc = (n + 31) >> 5;
   for (int64_t k = lane; k < n; k += 32) r[lo + k - sb] = 0;
-  seen.clear(lo, n, lane);
   for (int64_t c = lane; c < nc; c += 32) cmax[c] = 0;
+  seen.clear(lo, n, lane);
   __syncwarp();
-  const long long high = lam > 1 ? lam : 1;  // visited with r >= high: not low
+  int32_t* q = queue + (lo - qb);  // q[i]: the i-th taken vertex
+  int64_t qt = 0, qh = 0;          // taken / relaxed so far (the same in every lane)
   bool unites = false;
-  int64_t s0 = 0;          // first place of the current run
-  int32_t runmin = 0;      // its smallest id
-  int32_t win = 0;         // see noi_flush_run
-  long long best;
-  for (int64_t step = 0; step < n; ++step) {
-    long long bv = -1;
-    int bc = -1;
-    for (int64_t c = lane; c < nc; c += 32) {
-      const long long m = cmax[c];
-      if (m > bv) { bv = m; bc = (int)c; }
+  while (qt < n) {
+    // the run's first vertex: the untaken vertex of largest r, ties to the smallest id.
+    // cmax[c] bounds the attachments of chunk c's untaken vertices from above (raised
+    // with every relaxation; a taken vertex may leave it stale): the chunk of largest
+    // bound (ties: lower chunk) is checked exactly, and a stale bound is lowered and the
+    // choice made again.  A bound that holds is the largest attachment left.
+    int u;
+    for (;;) {
+      long long bv = -1;
+      int bc = -1;
+      for (int64_t c = lane; c < nc; c += 32) {
+        const long long m = cmax[c];
+        if (m > bv) { bv = m; bc = (int)c; }
+      }
+      long long bound, best;
+      const int C = warp_argmax_vi(bv, bc, &bound);
+      const int64_t k = (int64_t)C * 32 + lane;
+      const long long rv = (k < n && !seen.test(lo + k)) ? r[lo + k - sb] : -1;
+      const int xl = warp_argmax_vi(rv, (int)k, &best);
+      if (best == bound) {
+        u = xl;
+        break;
+      }
+      if (lane == 0) cmax[C] = best;  // -1: every vertex of the chunk is taken
+      __syncwarp();
     }
-    const int C = warp_argmax_vi(bv, bc, &best);
-    const int64_t k = (int64_t)C * 32 + lane;
-    // the list bounds of the chunk's vertices load beside their attachments, so the
-    // chosen vertex's list can be read as soon as it is known
-    const int64_t kb = k < n ? offs.at(lo + k) : 0, ke = k < n ? offs.at(lo + k + 1) : 0;
-    const long long rv = (k < n && !seen.test(lo + k)) ? r[lo + k - sb] : -1;
-    const int xl = warp_argmax_vi(rv, (int)k, &best);
-    const long long rx = best;
-    const int32_t x = (int32_t)(lo + xl);
-    const int64_t xb = __shfl_sync(0xffffffffu, kb, xl & 31), xe = __shfl_sync(0xffffffffu, ke, xl & 31);
-    if (rx < high) {  // x starts a run: the previous one is complete
-      if (step > 0) noi_flush_run(lo, s0, step, runmin, win, order, labels);
-      s0 = step;
-      runmin = x;
-    } else {
-      runmin = x < runmin ? x : runmin;
-      unites = true;
+    const int64_t rs = qt;
+    int32_t runmin = (int32_t)(lo + u);
+    if (lane == 0) {
+      q[qt] = runmin;
+      seen.claim(lo + u);
     }
-    if (lane == (step & 31)) {
-      win = x;
-      order[lo + step] = x;
-    }
-    if (k == xl) seen.set(x);
-    warp_argmax_vi(k == xl ? -1 : rv, (int)k, &best);  // the chunk's maximum without x
-    if (lane == 0) cmax[C] = best;
+    ++qt;
     __syncwarp();
-    for (int64_t e0 = xb; e0 < xe; e0 += 32 * kNoiUnroll) {
-      int32_t y[kNoiUnroll];
-      long long c[kNoiUnroll];
-#pragma unroll
-      for (int u = 0; u < kNoiUnroll; ++u) {
-        const int64_t e = e0 + lane + 32 * u;
-        y[u] = e < xe ? __ldg(adj + e) : -1;
-        c[u] = e < xe ? (long long)__ldg(w + e) : 0;
+    while (qh < qt) {
+      // up to 32 taken vertices at once, their lists end to end over the lanes
+      const int cnt = (int)(qt - qh < 32 ? qt - qh : 32);
+      int64_t fb = 0, deg = 0;
+      if (lane < cnt) {
+        const int32_t x = q[qh + lane];
+        fb = __ldg(off + x);
+        deg = __ldg(off + x + 1) - fb;
       }
+      qh += cnt;
+      int64_t incl = deg;
 #pragma unroll
-      for (int u = 0; u < kNoiUnroll; ++u) {
-        if (y[u] < 0 || seen.test(y[u])) continue;
-        const long long ry =
-            (long long)atomicAdd((unsigned long long*)&r[y[u] - sb], (unsigned long long)c[u]) + c[u];
-        atomicMax(&cmax[(y[u] - lo) >> 5], ry);
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int64_t total = __shfl_sync(0xffffffffu, incl, 31);
+      const int64_t excl = incl - deg;  // where lane j's list starts in the laid-out lists
+      for (int64_t p0 = 0; p0 < total; p0 += 32 * kNoiUnroll) {
+        int32_t y[kNoiUnroll];
+        long long c[kNoiUnroll];
+#pragma unroll
+        for (int i = 0; i < kNoiUnroll; ++i) {
+          const int64_t p = p0 + lane + 32 * i;
+          // the list holding place p: the last lane j whose list starts at or before p
+          int j = 0;
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            const int t = j + step;
+            const int64_t ex = __shfl_sync(0xffffffffu, excl, t & 31);
+            if (t < cnt && ex <= p) j = t;
+          }
+          const int64_t e = __shfl_sync(0xffffffffu, fb, j) + (p - __shfl_sync(0xffffffffu, excl, j));
+          y[i] = -1;
+          c[i] = 0;
+          if (p < total) {
+            y[i] = __ldg(adj + e);
+            c[i] = (long long)__ldg(w + e);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < kNoiUnroll; ++i) {
+          bool join = false;
+          if (y[i] >= 0 && !seen.test(y[i])) {
+            const long long ry =
+                (long long)atomicAdd((unsigned long long*)&r[y[i] - sb], (unsigned long long)c[i]) + c[i];
+            atomicMax(&cmax[(y[i] - lo) >> 5], ry);
+            // the addition that first leaves r(y) >= lambda-hat: the one that crosses it,
+            // or (lambda-hat <= 0) the first one
+            join = ry >= lam && (ry - c[i] < lam || ry - c[i] <= 0);
+          }
+          join = join && seen.claim(y[i]);
+          const unsigned b = __ballot_sync(0xffffffffu, join);
+          if (join) q[qt + __popc(b & below)] = y[i];
+          qt += __popc(b);
+          const unsigned m = __reduce_min_sync(0xffffffffu, join ? (unsigned)y[i] : 0xffffffffu);
+          if (m != 0xffffffffu && (int32_t)m < runmin) runmin = (int32_t)m;
+          __syncwarp();
+        }
       }
     }
+    for (int64_t i = rs + lane; i < qt; i += 32) labels[q[i]] = runmin;
+    if (qt - rs > 1) unites = true;
     __syncwarp();
   }
-  noi_flush_run(lo, s0, n, runmin, win, order, labels);
-  __syncwarp();
   return unites;
 }
 
-// The scan with the graph's state (attachments, chunk maxima, scanned flags and list
-// bounds) in shared memory: a step then waits on one global read (the chosen vertex's
-// list).  One warp per block.
-constexpr int kNoiSmemRoundMaxN = 15360;  // 15360 x 13 B + chunk maxima < 227 KB
+// The round with the graph's state (attachments, taken flags and queue) in shared
+// memory.  One warp per block.
+constexpr int kNoiSmemRoundMaxN = 16384;  // 16384 x 12.375 B < 227 KB
 __host__ __device__ constexpr size_t noi_round_smem(int ncap) {
-  return (size_t)ncap * 13 + ((size_t)ncap / 32 + 1) * 8 + 16;
+  return (size_t)ncap * 12 + ((size_t)ncap / 32 + 1) * 12 + 16;
 }
 
 template <typename WT>
 __global__ void __launch_bounds__(32) noi_round_smem_k(int64_t n, const int64_t* __restrict__ off,
                                                        const int32_t* __restrict__ adj, const WT* __restrict__ w,
-                                                       const DevState* st, int32_t* order, int32_t* labels,
-                                                       int* changed) {
+                                                       const DevState* st, int32_t* labels, int* changed) {
   extern __shared__ __align__(16) unsigned char noi_rs[];
   long long* r = (long long*)noi_rs;
   long long* cmax = r + n;
-  int32_t* rel = (int32_t*)(cmax + n / 32 + 1);
-  unsigned char* seen = (unsigned char*)(rel + n + 1);
-  const int lane = threadIdx.x;
-  const int64_t base = off[0];
-  for (int64_t k = lane; k <= n; k += 32) rel[k] = (int32_t)(off[k] - base);
-  __syncwarp();
-  const bool any = noi_scan_warp<WT>(0, n, SharedOff{rel, 0, base}, adj, w, st->lambda_hat, r, 0, ByteSeen{seen, 0},
-                                     cmax, order, labels);
-  if (any && lane == 0) atomicOr(changed, 1);
+  int32_t* queue = (int32_t*)(cmax + n / 32 + 1);
+  unsigned* seen = (unsigned*)(queue + n);
+  const bool any =
+      noi_closure_warp<WT>(0, n, off, adj, w, st->lambda_hat, r, 0, BitSeen{seen, 0}, cmax, queue, 0, labels);
+  if (any && threadIdx.x == 0) atomicOr(changed, 1);
 }
 
-// Above the shared-memory size: the same scan on global arrays (r holds n
-// attachments, then the chunk maxima).
+// Above the shared-memory size: the same round on global arrays.
 template <typename WT>
 __global__ void __launch_bounds__(32) noi_round_k(int64_t n, const int64_t* __restrict__ off,
                                                   const int32_t* __restrict__ adj, const WT* __restrict__ w,
-                                                  const DevState* st, long long* r, unsigned char* seen,
-                                                  int32_t* order, int32_t* labels, int* changed) {
-  const bool any = noi_scan_warp<WT>(0, n, GlobalOff{off}, adj, w, st->lambda_hat, r, 0, ByteSeen{seen, 0}, r + n,
-                                     order, labels);
+                                                  const DevState* st, long long* r, int* seen,
+                                                  int32_t* queue, int32_t* labels, int* changed) {
+  // r holds n attachments, then the chunk bounds
+  const bool any =
+      noi_closure_warp<WT>(0, n, off, adj, w, st->lambda_hat, r, 0, WordSeen{seen, 0}, r + n, queue, 0, labels);
   if (any && threadIdx.x == 0) atomicOr(changed, 1);
 }
 
 template <typename WT>
-static void noi_scan_launch(const GraphView& g, const DevState* st, long long* r, unsigned char* seen,
-                            int32_t* order, int32_t* labels, int* changed, cudaStream_t s) {
-  // offsets relative to the first entry fit 32 bits whenever the graph has < 2^31 entries
-  if (g.n <= kNoiSmemRoundMaxN && g.nnz < INT_MAX) {
+static void noi_round_launch(const GraphView& g, const DevState* st, long long* r, int* seen,
+                             int32_t* queue, int32_t* labels, int* changed, cudaStream_t s) {
+  if (g.n <= kNoiSmemRoundMaxN) {
     static std::mutex mu;
     static std::unordered_map<int, bool> ready;  // per device: the shared-memory limit was raised
     {
@@ -601,29 +624,28 @@ static void noi_scan_launch(const GraphView& g, const DevState* st, long long* r
         ready[dev] = true;
       }
     }
-    noi_round_smem_k<WT><<<1, 32, noi_round_smem((int)g.n), s>>>(g.n, g.off, g.adj, (const WT*)g.w, st, order, labels,
+    noi_round_smem_k<WT><<<1, 32, noi_round_smem((int)g.n), s>>>(g.n, g.off, g.adj, (const WT*)g.w, st, labels,
                                                                  changed);
   } else {
-    noi_round_k<WT><<<1, 32, 0, s>>>(g.n, g.off, g.adj, (const WT*)g.w, st, r, seen, order, labels, changed);
+    noi_round_k<WT><<<1, 32, 0, s>>>(g.n, g.off, g.adj, (const WT*)g.w, st, r, seen, queue, labels, changed);
   }
   count_launch();
   VC_CHECK_LAUNCH();
 }
 
-void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, unsigned char* seen,
+void noi_round_sparse(const GraphView& g, const DevState* st, long long* r, int* seen,
                       int32_t* parent, int32_t* labels, int* changed, cudaStream_t s) {
-  // parent (n entries) holds the visiting order
+  // parent (n entries) holds the queue of taken vertices
   if (g.wbytes == 4)
-    noi_scan_launch<int32_t>(g, st, r, seen, parent, labels, changed, s);
+    noi_round_launch<int32_t>(g, st, r, seen, parent, labels, changed, s);
   else
-    noi_scan_launch<long long>(g, st, r, seen, parent, labels, changed, s);
+    noi_round_launch<long long>(g, st, r, seen, parent, labels, changed, s);
 }
 
-// Batches: the scan of each listed graph by a warp (persistent grid of 8-warp blocks
+// Batches: the round of each listed graph by a warp (persistent grid of 8-warp blocks
 // pulling graphs from the list).  With ncap > 0 (every listed graph of at most ncap
-// vertices) each warp keeps its graph's chunk maxima and scanned bits in shared
-// memory; the attachments stay in global memory (every graph of the list in flight
-// at once).
+// vertices) each warp keeps its graph's taken bits in shared memory; the attachments
+// and queues stay in global memory (every graph of the list in flight at once).
 __host__ __device__ constexpr size_t noi_batch_warp_smem(int ncap) { return (size_t)(ncap / 32 + 1) * 12; }
 constexpr size_t kNoiBatchSmemMax = 160 * 1024;
 
@@ -632,8 +654,8 @@ __global__ void __launch_bounds__(256) noi_round_batch_k(const int32_t* __restri
                                                          const int64_t* __restrict__ off,
                                                          const int32_t* __restrict__ adj, const WT* __restrict__ w,
                                                          const long long* vbase, const long long* nv,
-                                                         const long long* glam, long long* r, unsigned char* seen,
-                                                         int32_t* order, long long* cmax, int32_t* labels,
+                                                         const long long* glam, long long* r, int* seen,
+                                                         long long* cmax, int32_t* queue, int32_t* labels,
                                                          int* gchanged, int ncap) {
   extern __shared__ __align__(16) unsigned char noi_bs[];
   const int warps = gridDim.x * (blockDim.x >> 5);
@@ -646,10 +668,9 @@ __global__ void __launch_bounds__(256) noi_round_batch_k(const int32_t* __restri
     const long long lo = vbase[g], n = nv[g];
     bool any;
     if (ncap > 0 && n <= ncap)
-      any = noi_scan_warp<WT>(lo, n, GlobalOff{off}, adj, w, glam[g], r, 0, BitSeen{wb, lo}, wc, order, labels);
+      any = noi_closure_warp<WT>(lo, n, off, adj, w, glam[g], r, 0, BitSeen{wb, lo}, wc, queue, 0, labels);
     else
-      any = noi_scan_warp<WT>(lo, n, GlobalOff{off}, adj, w, glam[g], r, 0, ByteSeen{seen, 0}, cmax + lo, order,
-                              labels);
+      any = noi_closure_warp<WT>(lo, n, off, adj, w, glam[g], r, 0, WordSeen{seen, 0}, cmax + lo, queue, 0, labels);
     if (any && lane == 0) atomicOr(gchanged + g, 1);
     __syncwarp();
   }
@@ -657,8 +678,8 @@ __global__ void __launch_bounds__(256) noi_round_batch_k(const int32_t* __restri
 
 template <typename WT>
 static void noi_round_batch_launch(const GraphView& u, const int32_t* list, int count, const long long* vbase,
-                                   const long long* nv, const long long* glam, long long* r, unsigned char* seen,
-                                   int32_t* order, long long* cmax, int32_t* labels, int* gchanged, int max_n,
+                                   const long long* nv, const long long* glam, long long* r, int* seen,
+                                   long long* cmax, int32_t* queue, int32_t* labels, int* gchanged, int max_n,
                                    cudaStream_t s) {
   static std::mutex mu;
   static std::unordered_map<int, bool> ready;  // per device: the shared-memory limit was raised
@@ -676,24 +697,25 @@ static void noi_round_batch_launch(const GraphView& u, const int32_t* list, int 
   const bool in_smem = max_n > 0 && smem <= kNoiBatchSmemMax;
   const int blocks = grid_for(count, 8, kSMs * 4);
   noi_round_batch_k<WT><<<blocks, 256, in_smem ? smem : 0, s>>>(list, count, u.off, u.adj, (const WT*)u.w, vbase, nv,
-                                                               glam, r, seen, order, cmax, labels, gchanged,
+                                                               glam, r, seen, cmax, queue, labels, gchanged,
                                                                in_smem ? max_n : 0);
   count_launch();
   VC_CHECK_LAUNCH();
 }
 
 void noi_round_batch(const GraphView& u, const int32_t* list, int count, const long long* vbase, const long long* nv,
-                     const long long* glam, long long* r, unsigned char* seen, int32_t* parent, int32_t* labels,
+                     const long long* glam, long long* r, int* seen, int32_t* parent, int32_t* labels,
                      int* gchanged, int max_n, cudaStream_t s) {
   if (count <= 0) return;
-  // r holds noi_round_scratch(union size) entries: attachments, then each graph's
-  // chunk maxima at its own range; parent (union size) holds the visiting orders
+  // r holds noi_round_scratch(union size) entries: the attachments, then each graph's
+  // chunk bounds at its own range; seen: the taken flags (union size); parent (union
+  // size) holds the queues
   long long* cmax = r + u.n;
   if (u.wbytes == 4)
-    noi_round_batch_launch<int32_t>(u, list, count, vbase, nv, glam, r, seen, parent, cmax, labels, gchanged, max_n,
+    noi_round_batch_launch<int32_t>(u, list, count, vbase, nv, glam, r, seen, cmax, parent, labels, gchanged, max_n,
                                     s);
   else
-    noi_round_batch_launch<long long>(u, list, count, vbase, nv, glam, r, seen, parent, cmax, labels, gchanged, max_n,
+    noi_round_batch_launch<long long>(u, list, count, vbase, nv, glam, r, seen, cmax, parent, labels, gchanged, max_n,
                                       s);
 }
 

@@ -311,9 +311,9 @@ static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, u
     while (!done && G.n > kDenseMax) {
       cudaEvent_t an = W.mark();
       W.noi_r.ensure_n<long long>(noi_round_scratch(G.n));
-      W.noi_seen.ensure_n<unsigned char>(G.n);
+      W.noi_seen.ensure_n<int>(G.n);
       VC_CUDA(cudaMemsetAsync(&W.ctr()->changed, 0, sizeof(int), s));
-      noi_round_sparse(G, st, W.noi_r.as<long long>(), W.noi_seen.as<unsigned char>(), W.parent.as<int32_t>(),
+      noi_round_sparse(G, st, W.noi_r.as<long long>(), W.noi_seen.as<int>(), W.parent.as<int32_t>(),
                        W.labA.as<int32_t>(), &W.ctr()->changed, s);
       W.span(kPhNOI, an);
       if (!read_changed()) { done = true; break; }
@@ -899,8 +899,8 @@ static int step_labels(viecut_graph* g, int64_t lambda_hat, int32_t* labels, int
       vc::pr_pass_b(v, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), W.st(), lab, chg, c.s);
   } else {
     W.noi_r.ensure_n<long long>(vc::noi_round_scratch(v.n));
-    W.noi_seen.ensure_n<unsigned char>(v.n);
-    vc::noi_round_sparse(v, W.st(), W.noi_r.as<long long>(), W.noi_seen.as<unsigned char>(), W.parent.as<int32_t>(),
+    W.noi_seen.ensure_n<int>(v.n);
+    vc::noi_round_sparse(v, W.st(), W.noi_r.as<long long>(), W.noi_seen.as<int>(), W.parent.as<int32_t>(),
                          lab, chg, c.s);
   }
   W.read_state();

@@ -164,6 +164,55 @@ def test_noi_round_components_are_runs_of_the_scan_order():
             assert (highs > 0) == (unions > 0), (seed, lam)
 
 
+def closure_runs_labels(g, lam, rnd):
+    """Labels of a NOI round built from closures: a run starts at the untaken vertex of
+    largest attachment (ties to the smallest id) and then takes, in a random order, any
+    untaken vertex whose attachment from the taken vertices reaches max(lam, 1) (for
+    lam <= 0: any untaken vertex with a taken neighbour), until none is left."""
+    n = len(g.offsets) - 1
+    r = [0] * n
+    taken = [False] * n
+    labels = np.empty(n, dtype=np.int32)
+    high = max(lam, 1)
+    left = n
+    while left:
+        u = min((v for v in range(n) if not taken[v]), key=lambda v: (-r[v], v))
+        run, ready = [], [u]
+        while ready:
+            x = ready.pop(rnd.randrange(len(ready)))
+            if taken[x]:
+                continue
+            taken[x] = True
+            run.append(x)
+            left -= 1
+            for e in range(g.offsets[x], g.offsets[x + 1]):
+                y = int(g.adj[e])
+                if not taken[y]:
+                    r[y] += int(g.w[e])
+                    if r[y] >= high:
+                        ready.append(y)
+        labels[run] = min(run)
+    return labels
+
+
+def test_noi_round_components_are_closures_in_any_order():
+    """A run of a NOI round is the closure of its first vertex under "attachment at
+    least max(lambda-hat, 1)", whatever the order inside it: the labels of runs grown in
+    random orders equal the oracle's union-find labels (the GPU grows them level by
+    level)."""
+    for seed in range(100):
+        rnd = random.Random(8000 + seed)
+        n = rnd.randint(2, 36)
+        g = H.random_graph(n, rnd.choice([0.1, 0.25, 0.5]), 11000 + seed, wmax=rnd.choice([1, 4, 9]),
+                           connected=seed % 4 != 0)
+        G = oracle.as_csr64(g.offsets, g.adj, g.w)
+        deg = oracle.degrees(G)
+        for lam in sorted({0, 1, max(1, int(deg.min()) // 2), int(deg.min()), int(deg.min()) + 4}):
+            ref, _ = oracle.noi_round(G, lam)
+            for trial in range(3):
+                assert np.array_equal(closure_runs_labels(g, lam, rnd), ref), (seed, lam, trial)
+
+
 # ----------------------------------------------------- label propagation pins
 def test_lp_weighted_star_hand():
     # centre 0, leaves 1..4 with weights 5, 3, 3, 1; no ties anywhere.
