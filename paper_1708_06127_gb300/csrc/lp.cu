@@ -430,6 +430,7 @@ __global__ void __launch_bounds__(kAggThreads) lp_warp_k(
 
 constexpr int kEmitBailKeys = 64;
 constexpr int kEmitWalkKeys = 6;
+constexpr int kEmitBlockPerVertexMax = kSMs * 8;  // block-class lists pre-merged a block each
 constexpr int kLpBailKeys = 16;
 constexpr int kLpWalkKeys = 8;      // short classes: labels walked before the table
 constexpr int kLpTableMaxS = 4;     // classes of at most this many slots per lane
@@ -1279,7 +1280,13 @@ void launch_emit(const GraphView& g, const Bins& b, const int32_t* cid, const Pa
                  cudaStream_t s) {
   const WT* w = (const WT*)g.w;
   launch_emit_reg<WT>(g, b, w, cid, out, cnt, s);
-  if (b.h_block > 0) {  // 513..4096 entries: G lanes per vertex, in G-entry chunks
+  if (b.h_block > 0 && b.h_block <= kEmitBlockPerVertexMax) {
+    // 513..4096 entries, few lists (hubs): a block per list, its warps on interleaved
+    // chunks (a group walking a 4096-entry list alone would set the kernel's length)
+    emit_block_k<WT><<<b.h_block, kAggThreads, 0, s>>>(b.block_list, b.counts + 1, g.off, g.adj, w, cid, out, cnt);
+    count_launch();
+    VC_CHECK_LAUNCH();
+  } else if (b.h_block > 0) {  // many such lists: G lanes per vertex, in G-entry chunks
     const int grid = grid_for(b.h_block, kAggThreads / G, kSMs * 16);
     const int* cp = b.counts + 1;
     if (G == 8)

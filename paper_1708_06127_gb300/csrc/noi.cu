@@ -91,7 +91,7 @@ __device__ __forceinline__ void noi_dense_body(int n, const int64_t* __restrict_
   __shared__ long long red_d[kNoiThreads / 32];
   __shared__ int red_v[kNoiThreads / 32];
   __shared__ long long red_c[kNoiThreads / 32];
-  __shared__ int s_x, s_stop, s_improved, s_nk2, s_arg;
+  __shared__ int s_x, s_stop, s_improved, s_nk2, s_arg, s_qt;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr int T = kNoiThreads;
   int nk = n;
@@ -131,30 +131,59 @@ __device__ __forceinline__ void noi_dense_body(int n, const int64_t* __restrict_
       }
       __syncthreads();
     } else {
-      for (int step = 0; step < nk; ++step) {
+      // the round as closures (see noi_closure_warp below): each run's first vertex is the
+      // untaken vertex of largest r (ties: smallest id); the run then grows level by
+      // level, every thread relaxing matrix entries of the level's vertices, and takes
+      // its smallest id as the label of all its vertices (rr holds the taken vertices)
+      int qt = 0, qh = 0;
+      while (qt < nk) {
         if (wid == 0) {
-          int x = warp_argmax_unseen(r, seen, nk);
-          if (lane == 0) { s_x = x; seen[x] = 1; }
-        }
-        __syncthreads();
-        const int x = s_x;
-        const long long* row = M + (int64_t)x * nk;
-        for (int y = tid; y < nk; y += T) {
-          if (!seen[y]) {
-            long long c = row[y];
-            if (c != 0) {
-              long long ry = r[y] + c;
-              r[y] = ry;
-              if (ry >= lam) sunite(parent, x, y);
-            }
+          const int x = warp_argmax_unseen(r, seen, nk);
+          if (lane == 0) {
+            rr[qt] = x;
+            seen[x] = 1;
+            s_qt = qt + 1;
           }
         }
         __syncthreads();
+        const int rs = qt;
+        qt = s_qt;
+        while (qh < qt) {
+          const int F = qt - qh;
+          for (int idx = tid; idx < F * nk; idx += T) {
+            const int f = idx / nk, y = idx - f * nk;
+            if (seen[y]) continue;
+            const long long c = M[(int64_t)rr[qh + f] * nk + y];
+            if (c == 0) continue;
+            const long long ry = (long long)atomicAdd((unsigned long long*)&r[y], (unsigned long long)c) + c;
+            if (ry >= lam && (ry - c < lam || ry - c <= 0) && atomicExch(&seen[y], 1) == 0)
+              rr[atomicAdd(&s_qt, 1)] = y;
+          }
+          __syncthreads();
+          qh = qt;
+          qt = s_qt;
+          __syncthreads();  // every thread has read s_qt before the next level adds to it
+        }
+        int m = INT_MAX;
+        for (int i = rs + tid; i < qt; i += T) m = rr[i] < m ? rr[i] : m;
+        m = (int)__reduce_min_sync(0xffffffffu, (unsigned)m);
+        if (lane == 0) red_v[wid] = m;
+        __syncthreads();
+        if (tid == 0) {
+          for (int q = 1; q < T / 32; ++q) m = red_v[q] < m ? red_v[q] : m;
+          s_arg = m;
+        }
+        __syncthreads();
+        m = s_arg;
+        for (int i = rs + tid; i < qt; i += T) root[rr[i]] = m;
+        __syncthreads();
       }
     }
+    if (nk <= kNoiWarpMax) {
+      for (int k = tid; k < nk; k += T) root[k] = sfind(parent, k);
+      __syncthreads();
+    }
     // roots -> ranks (every root is the minimum of its component)
-    for (int k = tid; k < nk; k += T) root[k] = sfind(parent, k);
-    __syncthreads();
     {
       int flag = (tid < nk && root[tid] == tid) ? 1 : 0;  // nk <= T
       int inc = flag;
