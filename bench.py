@@ -283,8 +283,9 @@ def bench_serve(pool_size: int, requests: int, warm: int, device: int, budget_gb
             time.sleep(0.0002)
         return [res[t] for t in tickets]
 
-    # closed burst: everything submitted at once
-    burst = [pool[i % pool_size] for i in range(min(max(warm, 8), 64))]
+    # closed burst: everything submitted at once; a warm-up burst of the same size first
+    # (the server keeps the page-locked blocks a burst needs for later requests)
+    burst = [pool[i % pool_size] for i in range(4 * pool_size)]
     drain([srv.submit(g.offsets, g.adj, g.w, 1 + i) for i, g in enumerate(burst)])  # warm-up
     burst = [pool[i] for i in rng.integers(0, pool_size, size=4 * pool_size)]
     t0 = time.perf_counter()
