@@ -288,6 +288,33 @@ def test_label_steps_parity(which):
             vc.viecut_graph_free(d)
 
 
+def test_exact_round_memory_paths():
+    """One exact-step round through each kernel: shared-memory state (up to 16,384
+    vertices) and global-memory state (above), for bounds at, below and far below the
+    minimum degree, against the oracle's scan with its union-find (labels element by
+    element); then the whole exact step on the larger graph."""
+    graphs = [gg.with_pair_weights(gg.core_lcc(gg.er(3000, 14, 21), 2), 21, 1, 9),
+              gg.with_pair_weights(gg.core_lcc(gg.er(20000, 12, 22), 2), 22, 1, 9),
+              gg.core_lcc(gg.rhg(1 << 15, 24, 23), 8)]
+    for g in graphs:
+        h = oracle.as_csr64(g.offsets, g.adj, g.w)
+        dmin = int(oracle.degrees(h).min())
+        d = upload(h)
+        try:
+            for lam in sorted({dmin, max(1, dmin // 2), 1}):
+                got, ch = vc.viecut_step_noi_round(d, lam)
+                ref, cnt = oracle.noi_round(h, lam)
+                assert np.array_equal(got, ref), (g.n, lam)
+                assert ch == (1 if cnt > 0 else 0)
+        finally:
+            vc.viecut_graph_free(d)
+    g = graphs[1]
+    assert g.n > 16384
+    cut, bits = vc.exact_min_cut(g.offsets, g.adj, g.w)
+    ref = oracle.viecut(g.offsets, g.adj, g.w, seed=1, lp_iters=0, n0=g.n)
+    assert cut == ref.cut and np.array_equal(bits[: len(ref.side_bits)], ref.side_bits)
+
+
 # ------------------------------------------------------------- whole method
 @pytest.mark.parametrize("seed", range(24))
 def test_viecut_random_small(seed):
