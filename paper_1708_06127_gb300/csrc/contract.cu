@@ -215,6 +215,58 @@ __global__ void __launch_bounds__(256) cluster_stats_k(int64_t n, const int32_t*
   }
 }
 
+// The pieces of a warp copied with the lanes on consecutive entries: lane j brings a
+// piece of len entries (0: none) read from src + i and written to dst + i (i < len);
+// load(s) reads the entry at source index s and put(d, j, value) writes it at
+// destination index d (j: the piece's lane).  kPieceUnroll entries per lane at a time,
+// all loads before the stores, so that they are in flight together.  Long lists of a
+// few lanes and short lists of many lanes keep every lane busy alike.
+constexpr int kPieceUnroll = 4;
+template <typename T, typename LOAD, typename PUT>
+__device__ __forceinline__ void warp_pieces(int64_t len, int64_t src, int64_t dst, LOAD load, PUT put) {
+  const int lane = threadIdx.x & 31;
+  int64_t incl = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const int64_t total = __shfl_sync(0xffffffffu, incl, 31);
+  const int64_t excl = incl - len;  // where lane j's piece starts among the laid-out pieces
+  for (int64_t p0 = 0; p0 < total; p0 += 32 * kPieceUnroll) {
+    int jj[kPieceUnroll];
+    int64_t sp[kPieceUnroll], dp[kPieceUnroll];
+    T val[kPieceUnroll];
+#pragma unroll
+    for (int u = 0; u < kPieceUnroll; ++u) {
+      const int64_t p = p0 + lane + 32 * u;
+      // the piece holding place p: the last lane whose piece starts at or before p
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int t = j + step;
+        const int64_t ex = __shfl_sync(0xffffffffu, excl, t & 31);
+        if (t < 32 && ex <= p) j = t;
+      }
+      const int64_t i = p - __shfl_sync(0xffffffffu, excl, j);
+      sp[u] = __shfl_sync(0xffffffffu, src, j) + i;
+      dp[u] = __shfl_sync(0xffffffffu, dst, j) + i;
+      jj[u] = p < total ? j : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < kPieceUnroll; ++u)
+      if (jj[u] >= 0) val[u] = load(sp[u]);
+#pragma unroll
+    for (int u = 0; u < kPieceUnroll; ++u)
+      if (jj[u] >= 0) put(dp[u], jj[u], val[u]);
+  }
+}
+
+struct KeyVal {
+  int32_t k;
+  long long v;
+};
+
 // Counting-sort scatter: the pre-merged pairs of fine vertex v move, in one piece,
 // into their cluster's segment (cursor = the segments' running write positions).
 // Lists of more than kScatterWarpMin pairs are copied by the whole warp.
@@ -257,18 +309,16 @@ __global__ void __launch_bounds__(256) cluster_scatter_k(int64_t n, const int64_
         }
       }
     }
-    // the rest of long lists, one list at a time by the whole warp (coalesced)
-    unsigned longs = __ballot_sync(0xffffffffu, c >= 0 && k > kScatterWarpMin);
-    while (longs) {
-      const int l = __ffs(longs) - 1;
-      longs &= longs - 1u;
-      const int kl = __shfl_sync(0xffffffffu, k, l);
-      const long long dl = __shfl_sync(0xffffffffu, dst, l);
-      const int64_t sl = off[base + l];
-      for (int j = kPairSlots + lane; j < kl; j += 32) {
-        seg_key[dl + j] = in.tkey[sl + j];
-        seg_val[dl + j] = in.tval[sl + j];
-      }
+    // the rest of the long lists, laid end to end over the lanes (coalesced)
+    const bool longl = c >= 0 && k > kScatterWarpMin;
+    if (__any_sync(0xffffffffu, longl)) {
+      warp_pieces<KeyVal>(
+          longl ? (int64_t)(k - kPairSlots) : 0, longl ? off[v] + kPairSlots : 0, dst + kPairSlots,
+          [&](int64_t at) { return KeyVal{in.tkey[at], in.tval[at]}; },
+          [&](int64_t at, int, const KeyVal& kv) {
+            seg_key[at] = kv.k;
+            seg_val[at] = kv.v;
+          });
     }
   }
 }
@@ -501,7 +551,7 @@ __global__ void __launch_bounds__(256) cluster_merge_block_k(int64_t c, const lo
 }
 
 // The sorted distinct targets of every cluster, copied from the front of its segment
-// to coff[c] (a warp per cluster).
+// to coff[c].
 // Clusters with skip[x] != 0 (skip may be null) are left out (their lists are written
 // by the sparse contraction's copy).
 __global__ void __launch_bounds__(256) cluster_place_k(int64_t c, const long long* __restrict__ cbase,
@@ -511,18 +561,22 @@ __global__ void __launch_bounds__(256) cluster_place_k(int64_t c, const long lon
                                                        int32_t* __restrict__ cadj, long long* __restrict__ cw,
                                                        int32_t* __restrict__ csrc,
                                                        const unsigned char* __restrict__ skip) {
+  // 32 clusters per warp step, their lists laid end to end over the lanes
   const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < c; x += warps) {
-    if (skip && skip[x]) continue;
-    const long long b = cbase[x];
-    const int64_t o = coff[x];
-    const int D = (int)(coff[x + 1] - o);
-    for (int i = lane; i < D; i += 32) {
-      cadj[o + i] = seg_key[b + i];
-      cw[o + i] = seg_val[b + i];
-      csrc[o + i] = (int32_t)x;
-    }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t x0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); x0 < c; x0 += stride) {
+    const int64_t x = x0 + lane;
+    const bool take = x < c && !(skip && skip[x]);
+    const long long b = take ? cbase[x] : 0;
+    const int64_t o = take ? coff[x] : 0;
+    const int64_t D = take ? coff[x + 1] - o : 0;
+    warp_pieces<KeyVal>(
+        D, b, o, [&](int64_t at) { return KeyVal{seg_key[at], seg_val[at]}; },
+        [&](int64_t at, int j, const KeyVal& kv) {
+          cadj[at] = kv.k;
+          cw[at] = kv.v;
+          csrc[at] = (int32_t)(x0 + j);
+        });
   }
 }
 
@@ -1025,7 +1079,8 @@ void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch
   if (giant && giant->ngiant > 0) giant_merge(*giant, c, cbase, seg_key, seg_val, ccount, cs.scan_scr, s);
   if (sp) sparse_finish_degrees(g, cid, sp->sdeg, ccount, sp->clean, c, s);
   exclusive_scan<int, long long>(ccount, (long long*)coff, c, (long long*)coff + c, cs.scan_scr, s);
-  cluster_place_k<<<gc, 256, 0, s>>>(c, cbase, coff, seg_key, seg_val, cadj, cw, csrc, sp ? sp->clean : nullptr);
+  cluster_place_k<<<grid_for(c, 256, kSMs * 8), 256, 0, s>>>(c, cbase, coff, seg_key, seg_val, cadj, cw, csrc,
+                                                               sp ? sp->clean : nullptr);
   count_launch();
   VC_CHECK_LAUNCH();
   if (sp) sparse_copy(g, sp->cidm, sp->sdeg, coff, cadj, cw, csrc, s);
