@@ -482,7 +482,11 @@ struct Engine {
   Buf in_off, in_adj, in_w;
   Buf gidA, gidB;
   int32_t* gid = nullptr;
-  Buf vact, sideK, noiM, noiCurK;
+  Buf vact, sideK, noiM, noiCurK, noiQ;
+  // the exact-step phases run on their own stream beside the other phases of a
+  // super-step (they touch only their graphs' vertices and state)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   Buf om0, oc1, os1;  // per original vertex
   int64_t ocap = 0;
   Workspace* ws = nullptr;
@@ -491,6 +495,9 @@ struct Engine {
   ~Engine() {
     delete ws;
     if (h_summary) cudaFreeHost(h_summary);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
   BState state() {
@@ -521,6 +528,9 @@ static void engine_setup(Engine& E, int K, const viecut_opts& o) {
     VC_CUDA(cudaStreamCreateWithFlags(&E.stream, cudaStreamNonBlocking));
     E.own_stream = true;
   }
+  VC_CUDA(cudaStreamCreateWithFlags(&E.side, cudaStreamNonBlocking));
+  VC_CUDA(cudaEventCreateWithFlags(&E.ev_fork, cudaEventDisableTiming));
+  VC_CUDA(cudaEventCreateWithFlags(&E.ev_join, cudaEventDisableTiming));
   for (Buf* b : {&E.phase, &E.level, &E.run, &E.any, &E.changed, &E.contracted, &E.first, &E.did, &E.best_kind,
                  &E.trace_len})
     b->ensure_n<int>(K);
@@ -587,7 +597,41 @@ static bool engine_step(Engine& E) {
   int32_t* Bl = W.labB.as<int32_t>();
   iota(A, G.n, s);
   iota(Bl, G.n, s);
-  int32_t* F = A;
+  // the super-step's labels: the last label-propagation round writes its graphs' into
+  // bufs[(lp_iters - 1) & 1] (below), and every other phase writes its graphs' there too
+  int32_t* F = (cnt[kBLP] > 0 && E.lp_iters > 0) ? ((E.lp_iters - 1) & 1 ? Bl : A) : A;
+  // the exact-step phases (latency-bound scans of single graphs) on the side stream,
+  // beside label propagation and Padberg-Rinaldi on the others; buffers grow first (a
+  // reallocation waits for the device)
+  const bool exact = cnt[kBNoiS] > 0 || cnt[kBNoiD] > 0;
+  if (exact) {
+    long long* M = nullptr;
+    int64_t mcap = 0;
+    int blocks = 0;
+    if (cnt[kBNoiS] > 0) {
+      W.noi_r.ensure_n<long long>(noi_round_scratch(G.n));
+      W.noi_seen.ensure_n<int>(G.n);
+      E.noiQ.ensure_n<int32_t>(G.n);
+    }
+    if (cnt[kBNoiD] > 0) {
+      mcap = (int64_t)cnt[7] * cnt[7];
+      // up to four blocks per SM (a dense round waits on a row read per scan step:
+      // graphs in flight hide it); each block keeps its own two matrices
+      blocks = std::min(cnt[kBNoiD], kSMs * kNoiDenseBlocksPerSM);
+      M = E.noiM.ensure_n<long long>(2 * mcap * blocks);
+    }
+    VC_CUDA(cudaEventRecord(E.ev_fork, s));
+    VC_CUDA(cudaStreamWaitEvent(E.side, E.ev_fork, 0));
+    if (cnt[kBNoiS] > 0)
+      noi_round_batch(G, S.list_nois, cnt[10], S.vbase, S.nv, S.lam, W.noi_r.as<long long>(),
+                      W.noi_seen.as<int>(), E.noiQ.as<int32_t>(), F, S.changed, cnt[11], E.side);
+    if (cnt[kBNoiD] > 0) {
+      BatchNoi bn{S.lam, S.best_kind, S.nv, S.nnz, S.dmin, S.argmin, S.trace_len, S.trace, kBTraceCap, S.level};
+      noi_dense_batch(G, S.list_noid, cnt[kBNoiD], S.vbase, S.nv, M, mcap, blocks, E.noiCurK.as<int32_t>(),
+                      E.sideK.as<unsigned char>(), bn, E.side);
+    }
+    VC_CUDA(cudaEventRecord(E.ev_join, E.side));
+  }
   BatchCtx bc;
   bc.gid = E.gid;
   bc.glam = S.lam;
@@ -608,7 +652,6 @@ static bool engine_step(Engine& E) {
       lp_round(Ga, W.bins, W.gt, in, bufs[r & 1], W.hv.as<unsigned long long>(), s, W.tune);
       in = bufs[r & 1];
     }
-    if (E.lp_iters > 0) F = in;
   }
   if (cnt[kBPRA] > 0) {
     b_prepare_k<<<gK, 256, 0, s>>>(K, S, kBPRA);
@@ -623,22 +666,7 @@ static bool engine_step(Engine& E) {
     pr_partners(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), s);
     pr_pass_b(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), W.st(), F, nullptr, s, &bc);
   }
-  if (cnt[kBNoiS] > 0) {
-    W.noi_r.ensure_n<long long>(noi_round_scratch(G.n));
-    W.noi_seen.ensure_n<int>(G.n);
-    noi_round_batch(G, S.list_nois, cnt[10], S.vbase, S.nv, S.lam, W.noi_r.as<long long>(),
-                    W.noi_seen.as<int>(), W.parent.as<int32_t>(), F, S.changed, cnt[11], s);
-  }
-  if (cnt[kBNoiD] > 0) {
-    const int64_t mcap = (int64_t)cnt[7] * cnt[7];
-    // up to four blocks per SM (a dense round waits on a row read per scan step:
-    // graphs in flight hide it); each block keeps its own two matrices
-    const int blocks = std::min(cnt[kBNoiD], kSMs * kNoiDenseBlocksPerSM);
-    long long* M = E.noiM.ensure_n<long long>(2 * mcap * blocks);
-    BatchNoi bn{S.lam, S.best_kind, S.nv, S.nnz, S.dmin, S.argmin, S.trace_len, S.trace, kBTraceCap, S.level};
-    noi_dense_batch(G, S.list_noid, cnt[kBNoiD], S.vbase, S.nv, M, mcap, blocks, E.noiCurK.as<int32_t>(),
-                    E.sideK.as<unsigned char>(), bn, s);
-  }
+  if (exact) VC_CUDA(cudaStreamWaitEvent(s, E.ev_join, 0));
   b_decide_k<<<gK, 256, 0, s>>>(K, S);
   count_launch();
   read_summary(E);
