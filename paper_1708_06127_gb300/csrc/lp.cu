@@ -459,7 +459,7 @@ __device__ __forceinline__ void reg_ids(RegIds<S>& R, int64_t beg, int64_t end, 
     R.u[r] = -1;
     R.wt[r] = 0;
     if (i < d) {
-      R.u[r] = __ldg(a + i);
+      R.u[r] = __ldcs(a + i);  // read once: evict first, keeping the gathered labels in L2
       R.wt[r] = ldw(w, beg + i);
     }
   }
@@ -914,7 +914,7 @@ __global__ void __launch_bounds__(kAggThreads) lp_first_simple_k(int64_t n, int 
         int u[4];
         unsigned long long h[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) u[r] = i0 + r * G < d ? __ldg(a + i0 + r * G) : -1;
+        for (int r = 0; r < 4; ++r) u[r] = i0 + r * G < d ? __ldcs(a + i0 + r * G) : -1;  // read once
 #pragma unroll
         for (int r = 0; r < 4; ++r) h[r] = u[r] >= 0 ? __ldg(hv + u[r]) : 0ULL;
 #pragma unroll
