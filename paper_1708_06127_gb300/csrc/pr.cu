@@ -135,23 +135,38 @@ __global__ void pr_a_edge_k(int64_t n, const int32_t* __restrict__ src, const in
 // Union-find start for pass A on sorted lists: each vertex points at its smallest
 // marked neighbour below it (or at itself).  Every such pointer is a union of a
 // marked edge towards a smaller id, so this is a valid forest with min-id roots,
-// shallow from the start; the per-entry pass then finds short paths.
+// shallow from the start; the per-entry pass then finds short paths.  Eight lanes per
+// vertex read its list in rows of eight ascending entries and stop at the first row
+// holding a marked entry below v or an entry at or above v.
+constexpr int kInitMinG = 8;
 template <typename WT>
 __global__ void uf_init_min_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                               const WT* __restrict__ w, const DevState* st, int32_t* __restrict__ parent,
                               BatchCtx bc) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+  constexpr int G = kInitMinG;
+  const int lane = threadIdx.x & 31, glane = lane & (G - 1);
+  const unsigned gmask = ((1u << G) - 1u) << (lane & ~(G - 1));
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
     int32_t p = (int32_t)v;
     long long lam;
     const int64_t beg = off[v], end = off[v + 1];
     if (end - beg >= 2 && pr_graph(bc, st, v, &lam)) {
-      for (int64_t e = beg; e < end; ++e) {
-        const int u = adj[e];
-        if (u >= v) break;  // sorted: no smaller neighbour follows
-        if ((long long)w[e] >= lam && off[u + 1] - off[u] >= 2) { p = u; break; }
+      for (int64_t b = beg; b < end; b += G) {
+        const int64_t e = b + glane;
+        const int u = e < end ? adj[e] : INT_MAX;
+        const bool below = u < v;
+        const bool mark = below && (long long)w[e] >= lam && off[u + 1] - off[u] >= 2;
+        const unsigned mb = __ballot_sync(gmask, mark);
+        const unsigned past = __ballot_sync(gmask, !below);
+        if (mb) {  // sorted: the lowest marked lane holds the smallest marked neighbour
+          p = __shfl_sync(gmask, u, __ffs(mb) - 1);
+          break;
+        }
+        if (past) break;  // no smaller neighbour follows
       }
     }
-    parent[v] = p;
+    if (glane == 0) parent[v] = p;
   }
 }
 
@@ -213,10 +228,11 @@ void pr_pass_a(const GraphView& g, const int32_t* partner, const long long* pw, 
   int grid = grid_for(g.n, 8, kSMs * 16);
   if (g.src) {  // contracted graph: sorted lists and entry sources
     const int ge = grid_for(g.nnz, 256, kSMs * 16);
+    const int gi = grid_for(g.n, 256 / kInitMinG, kSMs * 16);
     if (g.wbytes == 4)
-      uf_init_min_k<int32_t><<<grid1, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, st, parent, bc);
+      uf_init_min_k<int32_t><<<gi, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, st, parent, bc);
     else
-      uf_init_min_k<long long><<<grid1, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, st, parent, bc);
+      uf_init_min_k<long long><<<gi, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, st, parent, bc);
     if (g.wbytes == 4)
       pr_a_edge_k<int32_t><<<ge, 256, 0, s>>>(g.n, g.src, g.off, g.adj, (const int32_t*)g.w, st, parent, bc);
     else

@@ -214,6 +214,9 @@ static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, u
   int64_t n1 = 0;         // tier-1 vertex count
   int64_t levels = 0;
   bool done = W.h_state->lambda_hat == 0;
+  // W.partner / W.pw / W.deg hold the partners of the current G (a pass that merged
+  // nothing leaves G, and so them, as they were)
+  bool partners_ok = false;
 
   // contraction + bound update; returns false when the run ends
   auto step = [&](const int32_t* labels, int kind) -> bool {
@@ -235,8 +238,12 @@ static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, u
     slot = dst;
     W.span(kPhContract, a0);
     cudaEvent_t a1 = W.mark();
+    partners_ok = false;
     if (G.n > 1) {
-      degrees(G, W.deg.as<long long>(), s);
+      // the weighted degrees for the bound, with the partners the next Padberg-Rinaldi
+      // pass reads (the same scan of every list)
+      pr_partners(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), s);
+      partners_ok = true;
       bound_update(W.deg.as<long long>(), G.n, st, W.partial.as<long long>(), s);
       snapshot_side(W.cur1.as<int32_t>(), n1, W.side1.as<unsigned char>(), st, s);
     }
@@ -278,7 +285,8 @@ static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, u
       for (int pass = 0; pass < 2; ++pass) {
         cudaEvent_t ap = W.mark();
         VC_CUDA(cudaMemsetAsync(&W.ctr()->changed, 0, sizeof(int), s));
-        pr_partners(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), s);
+        if (!partners_ok) pr_partners(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), s);
+        partners_ok = true;
         int32_t* lab = W.labA.as<int32_t>();
         if (pass == 0)
           pr_pass_a(G, W.partner.as<int32_t>(), W.pw.as<long long>(), W.deg.as<long long>(), st,

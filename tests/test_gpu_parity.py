@@ -148,6 +148,58 @@ def test_lp_rounds_parity(step_graphs, name):
         vc.viecut_graph_free(d)
 
 
+def list_shapes_graph():
+    """Unit weights, strictly increasing lists of many shapes: a star of 1024 leaves, a
+    path (two entries per list), isolated vertices, and a star of 2999 leaves (block
+    class) with a few chords between its leaves."""
+    n = 6000
+    E = {(0, u) for u in range(1, 1025)}
+    E |= {(u, u + 1) for u in range(1100, 2100)}
+    E |= {(2200, u) for u in range(3001, 6000)}
+    rnd = random.Random(11)
+    E |= {tuple(sorted(rnd.sample(range(3001, 6000), 2))) for _ in range(400)}
+    return gg.from_edges(n, [(a, b, 1) for (a, b) in sorted(E)], "list-shapes")
+
+
+@pytest.mark.parametrize("name", ["shapes", "er_sparse", "giant_hubs"])
+def test_first_round_unit_list_shapes_parity(name):
+    """The first round from the identity on unit-weight graphs (the simple-list kernels:
+    one vertex per lane group, a block per list above 4096 entries; isolated vertices keep
+    their own label), and the second round after it, equal the oracle's rounds."""
+    g = {"shapes": list_shapes_graph, "er_sparse": lambda: gg.er(20000, 2.5, 11),
+         "giant_hubs": lambda: giant_hub_graph(True)}[name]()
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    assert (G.w == 1).all()
+    d = upload(G)
+    try:
+        for seed, level in [(1, 0), (9, 2)]:
+            key = oracle.level_key(seed, level)
+            got = vc.viecut_step_lp(d, None, key, 2)
+            l1 = oracle.lp_round(G, np.arange(G.n, dtype=np.int32), key)
+            assert np.array_equal(got[0], l1), (name, seed)
+            assert np.array_equal(got[1], oracle.lp_round(G, l1, key)), (name, seed)
+    finally:
+        vc.viecut_graph_free(d)
+
+
+def test_unaligned_caller_ids():
+    """Caller-owned device ids that start 4 bytes past a 16-byte boundary (valid for
+    int32): the whole run equals the oracle's."""
+    import torch
+    g = gg.workload_rhg_small(2)
+    dev = torch.device("cuda:0")
+    off = torch.from_numpy(g.offsets).to(dev)
+    buf = torch.zeros(g.nnz + 1, dtype=torch.int32, device=dev)
+    buf[1:] = torch.from_numpy(g.adj).to(dev)
+    adj = buf[1:]
+    assert adj.data_ptr() % 16 == 4
+    w = torch.from_numpy(g.w).to(dev)
+    ref = oracle.viecut(g.offsets, g.adj, g.w, seed=3, lp_iters=2, n0=10000)
+    with vc.MinCut(off, adj, w, on_device=True) as mc:
+        cut, bits = mc.run(3, 2)
+    assert cut == ref.cut and np.array_equal(bits, ref.side_bits)
+
+
 def compare_contract(G, labels):
     d = upload(G)
     out = None
