@@ -682,6 +682,12 @@ __global__ void __launch_bounds__(256) sc_count_k(int64_t n, const int32_t* __re
 }
 
 // Pass 2: the lists of the lone vertices counted in pass 1, at their coarse offsets.
+// The coarse list merges two ascending sequences: the entries into lone vertices' clusters
+// (in list order) and the nd distinct merged targets (sorted in s_dk).  An entry with key
+// k lands at its rank among the lone entries plus t(k), the number of targets below k (a
+// binary search of s_dk); target j lands at j plus the number of lone entries with
+// t(k) <= j, counted in a histogram over t (one shared-memory add per run of equal t in
+// a row) and summed by a scan over the targets.
 template <typename WT>
 __global__ void __launch_bounds__(256) sc_write_k(int64_t n, const int32_t* __restrict__ cidm,
                                                   const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
@@ -692,6 +698,7 @@ __global__ void __launch_bounds__(256) sc_write_k(int64_t n, const int32_t* __re
   __shared__ long long s_mw[8][kScMaxM];
   __shared__ int32_t s_dk[8][kScMaxM];
   __shared__ long long s_dw[8][kScMaxM];
+  __shared__ int s_ht[8][kScMaxM];  // lone entries per value of t below nd
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned lower = (1u << lane) - 1u;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -717,11 +724,9 @@ __global__ void __launch_bounds__(256) sc_write_k(int64_t n, const int32_t* __re
       s_dk[wid][rank] = key;
       s_dw[wid][rank] = sum;
     }
+    s_ht[wid][lane] = 0;
     __syncwarp();
-    // the entries into lone vertices' clusters: position among them, plus the distinct
-    // merged targets below them; lane j < nd also counts the entries below target j
-    const int32_t myd = lane < nd ? s_dk[wid][lane] : INT_MIN;
-    int dbelow = 0;
+    const int32_t* dk = s_dk[wid];
     int mbefore = 0;
     for (int64_t b = beg; b < end; b += 32 * kScUnroll) {
       int32_t u[kScUnroll], k[kScUnroll];
@@ -739,23 +744,37 @@ __global__ void __launch_bounds__(256) sc_write_k(int64_t n, const int32_t* __re
         const bool m = u[q] >= 0 && k[q] < 0;
         const bool lone = u[q] >= 0 && k[q] >= 0;
         const unsigned balM = __ballot_sync(0xffffffffu, m);
+        int t = 0;  // targets below k
         if (lone) {
-          int below = 0;
-          for (int j = 0; j < nd; ++j) below += s_dk[wid][j] < k[q];
-          const int64_t pos = (b + 32 * q - beg + lane) - (mbefore + __popc(balM & lower)) + below;
+          int hi = nd;
+          while (t < hi) {
+            const int mid = (t + hi) >> 1;
+            if (dk[mid] < k[q]) t = mid + 1;
+            else hi = mid;
+          }
+          const int64_t pos = (b + 32 * q - beg + lane) - (mbefore + __popc(balM & lower)) + t;
           cadj[o + pos] = k[q];
           cw[o + pos] = wt[q];
           csrc[o + pos] = x;
         }
         mbefore += __popc(balM);
-        for (int j = 0; j < nd; ++j) {
-          const int c = __popc(__ballot_sync(0xffffffffu, lone && k[q] < s_dk[wid][j]));
-          if (lane == j) dbelow += c;
+        if (nd > 0) {
+          const bool counted = lone && t < nd;
+          const unsigned run = __match_any_sync(0xffffffffu, counted ? t : -1 - lane);
+          if (counted && (__ffs(run) - 1) == lane) atomicAdd(&s_ht[wid][t], __popc(run));
         }
       }
     }
+    __syncwarp();
+    // target j: the lone entries with t <= j are below it
+    int dbelow = lane < nd ? s_ht[wid][lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, dbelow, d);
+      if (lane >= d) dbelow += y;
+    }
     if (lane < nd) {
-      cadj[o + lane + dbelow] = myd;
+      cadj[o + lane + dbelow] = dk[lane];
       cw[o + lane + dbelow] = s_dw[wid][lane];
       csrc[o + lane + dbelow] = x;
     }

@@ -33,29 +33,34 @@ __device__ __forceinline__ void uf_unite(int32_t* p, int a, int b) {
   }
 }
 
+// A warp per vertex (kPartnerG lanes; 16, two vertices per warp, measured slower on
+// the long lists of deep Padberg-Rinaldi levels).
+constexpr int kPartnerG = 32;
 template <typename WT>
 __global__ void partners_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                            const WT* __restrict__ w, int32_t* __restrict__ partner, long long* __restrict__ pw,
                            long long* __restrict__ deg) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+  constexpr int G = kPartnerG;
+  const int lane = threadIdx.x & 31, glane = lane & (G - 1);
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << (G & 31)) - 1u) << (lane & ~(G - 1));
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
     long long s = 0, bw = -1;
     int bu = INT_MAX;
-    for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32) {
+    for (int64_t e = off[v] + glane; e < off[v + 1]; e += G) {
       long long x = (long long)w[e];
       int u = adj[e];
       s += x;
       if (x > bw || (x == bw && u < bu)) { bw = x; bu = u; }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s += __shfl_xor_sync(0xffffffffu, s, o);
-      long long ow = __shfl_xor_sync(0xffffffffu, bw, o);
-      int ou = __shfl_xor_sync(0xffffffffu, bu, o);
+    for (int o = G / 2; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(gmask, s, o);
+      long long ow = __shfl_xor_sync(gmask, bw, o);
+      int ou = __shfl_xor_sync(gmask, bu, o);
       if (ow > bw || (ow == bw && ou < bu)) { bw = ow; bu = ou; }
     }
-    if (lane == 0) {
+    if (glane == 0) {
       deg[v] = s;
       partner[v] = bw < 0 ? -1 : bu;
       pw[v] = bw;
@@ -64,7 +69,7 @@ __global__ void partners_k(int64_t n, const int64_t* __restrict__ off, const int
 }
 
 void pr_partners(const GraphView& g, int32_t* partner, long long* pw, long long* deg, cudaStream_t s) {
-  int grid = grid_for(g.n, 8, kSMs * 16);
+  int grid = grid_for(g.n, 256 / kPartnerG, kSMs * 16);
   if (g.wbytes == 4) partners_k<int32_t><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, partner, pw, deg);
   else partners_k<long long><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, partner, pw, deg);
   count_launch();
@@ -136,34 +141,52 @@ __global__ void pr_a_edge_k(int64_t n, const int32_t* __restrict__ src, const in
 // marked neighbour below it (or at itself).  Every such pointer is a union of a
 // marked edge towards a smaller id, so this is a valid forest with min-id roots,
 // shallow from the start; the per-entry pass then finds short paths.  Eight lanes per
-// vertex read its list in rows of eight ascending entries and stop at the first row
-// holding a marked entry below v or an entry at or above v.
+// vertex read its list in rows of eight ascending entries (four rows at a time) and stop
+// at the first row holding a marked entry below v or an entry at or above v.
 constexpr int kInitMinG = 8;
+constexpr int kInitMinRows = 4;
 template <typename WT>
 __global__ void uf_init_min_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                               const WT* __restrict__ w, const DevState* st, int32_t* __restrict__ parent,
                               BatchCtx bc) {
   constexpr int G = kInitMinG;
   const int lane = threadIdx.x & 31, glane = lane & (G - 1);
-  const unsigned gmask = ((1u << G) - 1u) << (lane & ~(G - 1));
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << (G & 31)) - 1u) << (lane & ~(G - 1));
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
   for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
     int32_t p = (int32_t)v;
     long long lam;
     const int64_t beg = off[v], end = off[v + 1];
     if (end - beg >= 2 && pr_graph(bc, st, v, &lam)) {
-      for (int64_t b = beg; b < end; b += G) {
-        const int64_t e = b + glane;
-        const int u = e < end ? adj[e] : INT_MAX;
-        const bool below = u < v;
-        const bool mark = below && (long long)w[e] >= lam && off[u + 1] - off[u] >= 2;
-        const unsigned mb = __ballot_sync(gmask, mark);
-        const unsigned past = __ballot_sync(gmask, !below);
-        if (mb) {  // sorted: the lowest marked lane holds the smallest marked neighbour
-          p = __shfl_sync(gmask, u, __ffs(mb) - 1);
-          break;
+      bool found = false;
+      for (int64_t b = beg; b < end && !found; b += kInitMinRows * G) {
+        // kInitMinRows rows in flight: ids, then the weights of the entries below v,
+        // then the list lengths of the heavy ones
+        int u[kInitMinRows];
+        bool mk[kInitMinRows];
+#pragma unroll
+        for (int r = 0; r < kInitMinRows; ++r) {
+          const int64_t e = b + r * G + glane;
+          u[r] = e < end ? adj[e] : INT_MAX;
         }
-        if (past) break;  // no smaller neighbour follows
+#pragma unroll
+        for (int r = 0; r < kInitMinRows; ++r) mk[r] = u[r] < v && (long long)w[b + r * G + glane] >= lam;
+#pragma unroll
+        for (int r = 0; r < kInitMinRows; ++r) mk[r] = mk[r] && off[u[r] + 1] - off[u[r]] >= 2;
+#pragma unroll
+        for (int r = 0; r < kInitMinRows; ++r) {
+          const unsigned mb = __ballot_sync(gmask, mk[r]);
+          const unsigned past = __ballot_sync(gmask, !(u[r] < v));
+          if (mb) {  // sorted: the lowest marked lane holds the smallest marked neighbour
+            p = __shfl_sync(gmask, u[r], __ffs(mb) - 1);
+            found = true;
+            break;
+          }
+          if (past) {  // no smaller neighbour follows
+            found = true;
+            break;
+          }
+        }
       }
     }
     if (glane == 0) parent[v] = p;
