@@ -591,8 +591,7 @@ __global__ void __launch_bounds__(256) cluster_place_k(int64_t c, const long lon
 // A warp per lone vertex sums them per target in shared memory and merges the distinct
 // ones into the renumbered list by rank -- one pass to count the coarse degree, one to
 // write.  Only the members of merged groups (and lone vertices with more than
-// kScMaxM such entries or more than kScRows x 32 entries) go through the pre-merge and
-// the cluster merge.
+// kScMaxM such entries) go through the pre-merge and the cluster merge.
 constexpr int kScMaxM = 32;  // entries into merged groups per lone vertex
 
 // mflag[cid[v]] = 1 for every v that is not its own root (its group has two or more
