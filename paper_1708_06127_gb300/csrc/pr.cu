@@ -34,8 +34,17 @@ __device__ __forceinline__ void uf_unite(int32_t* p, int a, int b) {
 }
 
 // A warp per vertex (kPartnerG lanes; 16, two vertices per warp, measured slower on
-// the long lists of deep Padberg-Rinaldi levels).
+// the long lists of deep Padberg-Rinaldi levels); lists of more than kPartnerBlockMin
+// entries (hubs that absorbed many vertices) take a block each in partners_long_k.
 constexpr int kPartnerG = 32;
+constexpr int64_t kPartnerBlockMin = 8192;
+
+// Degree and designated partner of one list, folded into (s, bw, bu) (bu INT_MAX: none).
+__device__ __forceinline__ void partner_fold(long long& s, long long& bw, int& bu, long long x, int u) {
+  s += x;
+  if (x > bw || (x == bw && u < bu)) { bw = x; bu = u; }
+}
+
 template <typename WT>
 __global__ void partners_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                            const WT* __restrict__ w, int32_t* __restrict__ partner, long long* __restrict__ pw,
@@ -45,19 +54,17 @@ __global__ void partners_k(int64_t n, const int64_t* __restrict__ off, const int
   const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << (G & 31)) - 1u) << (lane & ~(G - 1));
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
   for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
+    const int64_t beg = off[v], end = off[v + 1];
+    if (end - beg > kPartnerBlockMin) continue;  // partners_long_k
     long long s = 0, bw = -1;
     int bu = INT_MAX;
-    for (int64_t e = off[v] + glane; e < off[v + 1]; e += G) {
-      long long x = (long long)w[e];
-      int u = adj[e];
-      s += x;
-      if (x > bw || (x == bw && u < bu)) { bw = x; bu = u; }
-    }
+    for (int64_t e = beg + glane; e < end; e += G) partner_fold(s, bw, bu, (long long)w[e], adj[e]);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
-      s += __shfl_xor_sync(gmask, s, o);
-      long long ow = __shfl_xor_sync(gmask, bw, o);
-      int ou = __shfl_xor_sync(gmask, bu, o);
+      const long long os = __shfl_xor_sync(gmask, s, o);
+      const long long ow = __shfl_xor_sync(gmask, bw, o);
+      const int ou = __shfl_xor_sync(gmask, bu, o);
+      s += os;
       if (ow > bw || (ow == bw && ou < bu)) { bw = ow; bu = ou; }
     }
     if (glane == 0) {
@@ -68,11 +75,64 @@ __global__ void partners_k(int64_t n, const int64_t* __restrict__ off, const int
   }
 }
 
+// The lists of more than kPartnerBlockMin entries: each block lists the long ones among
+// 256 consecutive vertices, then folds each of them with all its threads.
+template <typename WT>
+__global__ void __launch_bounds__(256) partners_long_k(int64_t n, const int64_t* __restrict__ off,
+                                                       const int32_t* __restrict__ adj, const WT* __restrict__ w,
+                                                       int32_t* __restrict__ partner, long long* __restrict__ pw,
+                                                       long long* __restrict__ deg) {
+  __shared__ int32_t s_list[256];
+  __shared__ int s_n;
+  __shared__ long long s_s[8], s_bw[8];
+  __shared__ int s_bu[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t base = (int64_t)blockIdx.x * 256; base < n; base += (int64_t)gridDim.x * 256) {
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    const int64_t v0 = base + threadIdx.x;
+    if (v0 < n && off[v0 + 1] - off[v0] > kPartnerBlockMin) s_list[atomicAdd(&s_n, 1)] = (int32_t)v0;
+    __syncthreads();
+    const int cnt = s_n;
+    for (int i = 0; i < cnt; ++i) {
+      const int32_t v = s_list[i];
+      long long s = 0, bw = -1;
+      int bu = INT_MAX;
+      for (int64_t e = off[v] + threadIdx.x; e < off[v + 1]; e += 256) partner_fold(s, bw, bu, (long long)w[e], adj[e]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long os = __shfl_xor_sync(0xffffffffu, s, o);
+        const long long ow = __shfl_xor_sync(0xffffffffu, bw, o);
+        const int ou = __shfl_xor_sync(0xffffffffu, bu, o);
+        s += os;
+        if (ow > bw || (ow == bw && ou < bu)) { bw = ow; bu = ou; }
+      }
+      if (lane == 0) { s_s[wid] = s; s_bw[wid] = bw; s_bu[wid] = bu; }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int k = 1; k < 8; ++k) {
+          s += s_s[k];
+          if (s_bw[k] > bw || (s_bw[k] == bw && s_bu[k] < bu)) { bw = s_bw[k]; bu = s_bu[k]; }
+        }
+        deg[v] = s;
+        partner[v] = bw < 0 ? -1 : bu;
+        pw[v] = bw;
+      }
+      __syncthreads();
+    }
+  }
+}
+
 void pr_partners(const GraphView& g, int32_t* partner, long long* pw, long long* deg, cudaStream_t s) {
-  int grid = grid_for(g.n, 256 / kPartnerG, kSMs * 16);
-  if (g.wbytes == 4) partners_k<int32_t><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, partner, pw, deg);
-  else partners_k<long long><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, partner, pw, deg);
-  count_launch();
+  const int grid = grid_for(g.n, 256 / kPartnerG, kSMs * 16), gl = grid_for(g.n, 256, kSMs * 4);
+  if (g.wbytes == 4) {
+    partners_k<int32_t><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, partner, pw, deg);
+    partners_long_k<int32_t><<<gl, 256, 0, s>>>(g.n, g.off, g.adj, (const int32_t*)g.w, partner, pw, deg);
+  } else {
+    partners_k<long long><<<grid, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, partner, pw, deg);
+    partners_long_k<long long><<<gl, 256, 0, s>>>(g.n, g.off, g.adj, (const long long*)g.w, partner, pw, deg);
+  }
+  count_launch(2);
   VC_CHECK_LAUNCH();
 }
 
@@ -277,9 +337,11 @@ void pr_pass_a(const GraphView& g, const int32_t* partner, const long long* pw, 
 }
 
 // Conditions 3 and 4 on mutual partner pairs v < w = p(v), p(w) = v, through the
-// common neighbourhood (binary search of N(v)'s entries in w's sorted list; a list of at
-// most kPrBStage ids is first copied into the warp's shared memory, so the searches
-// there wait on no global loads).
+// common neighbourhood: the warp walks the shorter of the two lists and finds each entry
+// in the longer one by binary search (a longer list of at most kPrBStage ids is first
+// copied into the warp's shared memory, so the searches there wait on no global loads).
+// Walking the shorter list keeps a pair of a hub and a small vertex as cheap as the
+// small vertex's list.
 constexpr int kPrBStage = 1024;
 template <typename WT>
 __global__ void __launch_bounds__(256) pr_b_k(int64_t n, const int64_t* __restrict__ off,
@@ -299,23 +361,26 @@ __global__ void __launch_bounds__(256) pr_b_k(int64_t n, const int64_t* __restri
     const int64_t vb = off[v], ve = off[v + 1], pb = off[p], pe = off[p + 1];
     if (ve - vb < 2 || pe - pb < 2) continue;
     const long long cvw = pw[v], dv = deg[v], dp = deg[p];
-    const bool staged = pe - pb <= kPrBStage;
+    // walk list s, search list l (s the shorter; ties: walk v's)
+    const bool swap = pe - pb < ve - vb;
+    const int64_t sb = swap ? pb : vb, se = swap ? pe : ve, lb = swap ? vb : pb, le = swap ? ve : pe;
+    const bool staged = le - lb <= kPrBStage;
     if (staged)
-      for (int64_t i = lane; i < pe - pb; i += 32) sl[i] = adj[pb + i];
+      for (int64_t i = lane; i < le - lb; i += 32) sl[i] = adj[lb + i];
     __syncwarp();
     bool pr3 = false;
     long long sum = 0;
-    for (int64_t e = vb + lane; e < ve; e += 32) {
+    for (int64_t e = sb + lane; e < se; e += 32) {
       const int u = adj[e];
-      int64_t lo = pb, hi = pe;
+      int64_t lo = lb, hi = le;
       if (staged) {
-        int l = 0, h = (int)(pe - pb);
+        int l = 0, h = (int)(le - lb);
         while (l < h) {
           const int mid = (l + h) >> 1;
           if (sl[mid] < u) l = mid + 1;
           else h = mid;
         }
-        lo = pb + l;
+        lo = lb + l;
       } else {
         while (lo < hi) {
           int64_t mid = (lo + hi) >> 1;
@@ -323,8 +388,9 @@ __global__ void __launch_bounds__(256) pr_b_k(int64_t n, const int64_t* __restri
           else hi = mid;
         }
       }
-      if (lo < pe && (staged ? sl[lo - pb] : adj[lo]) == u) {
-        const long long cvu = (long long)w[e], cwu = (long long)w[lo];
+      if (lo < le && (staged ? sl[lo - lb] : adj[lo]) == u) {
+        const long long cs = (long long)w[e], cl = (long long)w[lo];
+        const long long cvu = swap ? cl : cs, cwu = swap ? cs : cl;  // c(v, u), c(p, u)
         if (dv <= 2 * (cvw + cvu) && dp <= 2 * (cvw + cwu)) pr3 = true;
         sum += cvu < cwu ? cvu : cwu;
       }
