@@ -582,20 +582,22 @@ __global__ void __launch_bounds__(256) cluster_place_k(int64_t c, const long lon
 
 
 // ---------------------------------------------------------------- sparse contraction
-// Contractions by union-find roots (Padberg-Rinaldi passes, exact-step rounds) on a graph
-// with strictly increasing lists.  A vertex alone in its group is its own root, so its
-// cluster id is the rank of its own id among the roots; neighbours alone in their groups
-// keep their order and stay distinct under that renumbering.  So the coarse list of a
-// lone vertex is its fine list renumbered, except for the few entries that point into
-// merged groups (two or more members): those may repeat a target and sit out of order.
+// Contractions in which most vertices keep their own id as label, alone in their cluster
+// (Padberg-Rinaldi passes and exact-step rounds by union-find roots, label-propagation
+// levels that merge few vertices), on a graph with strictly increasing lists.  The
+// cluster id of such a "lone" vertex is the rank of its own id among the labels, so lone
+// neighbours keep their order and stay distinct under the renumbering.  The coarse list of
+// a lone vertex is its fine list renumbered, except for the few entries that point into
+// the other ("merged") clusters: those may repeat a target and sit out of order.
 // A warp per lone vertex sums them per target in shared memory and merges the distinct
 // ones into the renumbered list by rank -- one pass to count the coarse degree, one to
 // write.  Only the members of merged groups (and lone vertices with more than
 // kScMaxM such entries) go through the pre-merge and the cluster merge.
 constexpr int kScMaxM = 32;  // entries into merged groups per lone vertex
 
-// mflag[cid[v]] = 1 for every v that is not its own root (its group has two or more
-// members); a plain store of 1 from any number of threads.
+// mflag[cid[v]] = 1 for every v not labelled by its own id (its cluster has another
+// member, or its label is another vertex's id); a plain store of 1 from any number of
+// threads.
 __global__ void sc_merged_k(int64_t n, const int32_t* __restrict__ lab, const int32_t* __restrict__ cid,
                             unsigned char* __restrict__ mflag) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)

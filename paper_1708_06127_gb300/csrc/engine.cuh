@@ -432,11 +432,13 @@ struct Workspace {
 
   // Contracts g by labels into the coarse buffer `slot`; cid_out[n] receives the map.
   // Returns the coarse view; h_counters holds c and the pair count afterwards.
-  // uf_roots: the labels are union-find roots (a vertex alone in its group is its own
-  // root); on a graph of strictly increasing lists the sparse contraction then handles
-  // the vertices a contraction leaves alone by a renumbering copy.
+  // sparse_ok: try the sparse contraction on a graph of strictly increasing lists: a
+  // vertex labelled by its own id and alone in its cluster ("lone": the cluster ids of
+  // such vertices rise with their ids) is handled by a renumbering copy of its list.  It
+  // pays when most vertices are lone (Padberg-Rinaldi passes, weakly clustered levels);
+  // it is taken only when at most half of the vertices are left to the pre-merge.
   GraphView contract(const GraphView& g, const int32_t* labels, int32_t* cid_out, int slot, bool correct = false,
-                     bool uf_roots = false) {
+                     bool sparse_ok = false) {
     cudaEvent_t t0 = mark();
     ContractScratch cs;
     cs.flags = flags.as<int32_t>();
@@ -466,7 +468,7 @@ struct Workspace {
       cr.vin = cl + 3 * g.n;
       correct_clusters(g, cid_out, &ctr()->c, cr, s);
     }
-    const bool sparse = uf_roots && !correct && g.simple && g.n > 0 && mark_sparse(g, labels, cid_out);
+    const bool sparse = sparse_ok && !correct && g.simple && g.n > 0 && mark_sparse(g, labels, cid_out);
     if (!sparse && !bins_valid) build_bins(g);
     const Bins& B = sparse ? dbins : bins;
     PairOut po{cs.tmp_key, cs.tmp_val, cs.cmp_key, cs.cmp_val};

@@ -216,8 +216,8 @@ struct GiantScratch {
 };
 void cluster_stats(int64_t n, const int32_t* ccount, int* maxt, long long* pairs, int* ngiant, long long* gpairs,
                    cudaStream_t s);
-// Sparse contraction (contraction by union-find roots on a graph of strictly increasing
-// lists, see contract.cu): sparse_mark flags the merged clusters (mflag, n bytes), counts
+// Sparse contraction (most vertices alone in their cluster under their own id, on a graph
+// of strictly increasing lists, see contract.cu): sparse_mark flags the merged clusters (mflag, n bytes), counts
 // the coarse degree of every lone vertex it handles (sdeg[v], -1 for the others) and
 // lists the others (dirty, n bytes; list[*count]) for the pre-merge.  With a SparseCtx,
 // cluster_merge expects pairs from the listed vertices only (the rest with no pairs) and

@@ -224,7 +224,9 @@ static void run_impl(Handle& H, uint64_t seed, int lp_iters, long long* d_cut, u
     int32_t* cid = contracted ? W.cidT.as<int32_t>() : W.map0.as<int32_t>();
     int dst = slot == 0 ? 1 : 0;
     const GraphView fine = G;
-    GraphView h = W.contract(G, labels, cid, dst, kind == 1 && H.correct, kind >= 2);
+    // the sparse contraction for Padberg-Rinaldi passes and for levels the last one did
+    // not halve (most vertices keep their own label there)
+    GraphView h = W.contract(G, labels, cid, dst, kind == 1 && H.correct, kind >= 2 || W.tune.mid_bail);
     set_n_k<<<1, 1, 0, s>>>(st, h.n);
     count_launch();
     if (!contracted) {
@@ -865,7 +867,7 @@ int viecut_step_contract(viecut_graph* g, const int32_t* labels, viecut_graph** 
   int32_t* lab = c.ws->labA.as<int32_t>();
   VC_CUDA(cudaMemcpyAsync(lab, labels, sizeof(int32_t) * v.n, cudaMemcpyHostToDevice, c.s));
   int32_t* cidd = c.ws->map0.as<int32_t>();
-  vc::GraphView h = c.ws->contract(v, lab, cidd, 0);
+  vc::GraphView h = c.ws->contract(v, lab, cidd, 0, false, true);  // sparse path when it applies
   c.ws->read_state();
   const int64_t nnz = c.ws->h_state->nnz;
   auto* x = new viecut_graph;

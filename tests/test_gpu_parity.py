@@ -222,11 +222,16 @@ def test_contract_parity(step_graphs, name):
     g = step_graphs[name]
     G = oracle.as_csr64(g.offsets, g.adj, g.w)
     rnd = np.random.default_rng(11)
-    # clusterings from label propagation, random with few / many clusters, identity
+    # clusterings from label propagation, random with few / many clusters, identity, and
+    # the identity with a tenth of the vertices relabelled at random (most vertices alone
+    # under their own id: the sparse contraction, with singletons under another id)
     key = oracle.level_key(2, 0)
     lp = oracle.lp_round(G, oracle.lp_round(G, np.arange(G.n, dtype=np.int32), key), key)
+    near = np.arange(G.n)
+    moved = rnd.choice(G.n, G.n // 10, replace=False)
+    near[moved] = rnd.integers(0, G.n, len(moved))
     for labels in [lp, rnd.integers(0, 7, G.n), rnd.integers(0, G.n, G.n), np.arange(G.n),
-                   np.zeros(G.n, np.int64)]:
+                   np.zeros(G.n, np.int64), near]:
         compare_contract(G, labels.astype(np.int32))
 
 
