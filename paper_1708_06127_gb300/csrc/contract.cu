@@ -677,7 +677,7 @@ __global__ void __launch_bounds__(256) sc_count_k(int64_t n, const int32_t* __re
     const int32_t key = have ? s_mk[wid][lane] : -1 - lane;
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     const int nd = __popc(__ballot_sync(0xffffffffu, have && (__ffs(peers) - 1) == lane));
-    if (lane == 0) { sdeg[v] = (int32_t)(end - beg - nm + nd); dirty[v] = 0; }
+    if (lane == 0) { sdeg[v] = (int32_t)(end - beg - nm + nd); dirty[v] = nm == 0 ? 2 : 0; }
     __syncwarp();
   }
 }
@@ -693,6 +693,7 @@ template <typename WT>
 __global__ void __launch_bounds__(256) sc_write_k(int64_t n, const int32_t* __restrict__ cidm,
                                                   const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                                                   const WT* __restrict__ w, const int32_t* __restrict__ sdeg,
+                                                  const unsigned char* __restrict__ dirty,
                                                   const int64_t* __restrict__ coff, int32_t* __restrict__ cadj,
                                                   long long* __restrict__ cw, int32_t* __restrict__ csrc) {
   __shared__ int32_t s_mk[8][kScMaxM];
@@ -708,6 +709,27 @@ __global__ void __launch_bounds__(256) sc_write_k(int64_t n, const int32_t* __re
     const int64_t beg = off[v], end = off[v + 1];
     const int32_t x = cidm[v];  // lone: no sign bit
     const int64_t o = coff[x];
+    if (dirty[v] == 2) {  // no entry into a merged cluster: the list renumbered in place
+      for (int64_t b = beg; b < end; b += 32 * kScUnroll) {
+        int32_t u[kScUnroll];
+        long long wt[kScUnroll];
+#pragma unroll
+        for (int q = 0; q < kScUnroll; ++q) {
+          const int64_t e = b + 32 * q + lane;
+          u[q] = e < end ? __ldg(adj + e) : -1;
+          wt[q] = e < end ? ldw(w, e) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < kScUnroll; ++q)
+          if (u[q] >= 0) {
+            const int64_t at = o + (b + 32 * q + lane - beg);
+            cadj[at] = __ldg(cidm + u[q]);
+            cw[at] = wt[q];
+            csrc[at] = x;
+          }
+      }
+      continue;
+    }
     const int nm = sc_collect<WT>(beg, end, lane, adj, w, cidm, true, s_mk[wid], s_mw[wid]);
     // distinct targets into merged groups: the lowest lane of each target sums it and
     // places it by its rank among the distinct targets
@@ -790,7 +812,7 @@ __global__ void sc_list_k(int64_t n, const unsigned char* __restrict__ dirty, in
   for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; b < n;
        b += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = b + lane;
-    const bool d = v < n && dirty[v];
+    const bool d = v < n && dirty[v] == 1;
     const unsigned bal = __ballot_sync(0xffffffffu, d);
     int at = 0;
     if (lane == 0 && bal) at = atomicAdd(count, __popc(bal));
@@ -842,12 +864,12 @@ static void sparse_finish_degrees(const GraphView& g, const int32_t* cid, const 
   VC_CHECK_LAUNCH();
 }
 
-static void sparse_copy(const GraphView& g, const int32_t* cidm, const int32_t* sdeg, const int64_t* coff,
-                        int32_t* cadj, long long* cw, int32_t* csrc, cudaStream_t s) {
+static void sparse_copy(const GraphView& g, const int32_t* cidm, const int32_t* sdeg, const unsigned char* dirty,
+                        const int64_t* coff, int32_t* cadj, long long* cw, int32_t* csrc, cudaStream_t s) {
   sc_by_weight(g, [&](auto wp) {
     using WT = std::remove_cv_t<std::remove_pointer_t<decltype(wp)>>;
-    sc_write_k<WT><<<grid_for(g.n, 8, kSMs * 16), 256, 0, s>>>(g.n, cidm, g.off, g.adj, wp, sdeg, coff, cadj, cw,
-                                                               csrc);
+    sc_write_k<WT><<<grid_for(g.n, 8, kSMs * 16), 256, 0, s>>>(g.n, cidm, g.off, g.adj, wp, sdeg, dirty, coff, cadj,
+                                                               cw, csrc);
   });
   count_launch();
   VC_CHECK_LAUNCH();
@@ -1103,7 +1125,7 @@ void cluster_merge(const GraphView& g, const int32_t* cid, const ContractScratch
                                                                sp ? sp->clean : nullptr);
   count_launch();
   VC_CHECK_LAUNCH();
-  if (sp) sparse_copy(g, sp->cidm, sp->sdeg, coff, cadj, cw, csrc, s);
+  if (sp) sparse_copy(g, sp->cidm, sp->sdeg, sp->dirty, coff, cadj, cw, csrc, s);
   VC_CUDA(cudaMemcpyAsync(nnz_dev, coff + c, sizeof(long long), cudaMemcpyDeviceToDevice, s));
 }
 

@@ -535,7 +535,8 @@ struct Workspace {
         gs.hpos = hpos.ensure_n<long long>(GP + 1);
         gs.hist = hist.ensure_n<long long>(radix_hist_elems(GP));
       }
-      const SparseCtx sp{scidm.as<int32_t>(), sdeg.as<int32_t>(), sclean.as<unsigned char>()};
+      const SparseCtx sp{scidm.as<int32_t>(), sdeg.as<int32_t>(), sclean.as<unsigned char>(),
+                         sdirty.as<unsigned char>()};
       cluster_merge(g, cid_out, cs, ccount, c, cbase, cur, sk, sv, co, ca, cwp, csp, &st()->nnz,
                     h_counters->maxt > kMergeMax, 2 * c >= g.n, ng ? &gs : nullptr, cs.cnt, &ctr()->blist_n, s,
                     sparse ? &sp : nullptr);

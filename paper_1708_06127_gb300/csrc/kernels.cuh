@@ -226,6 +226,7 @@ struct SparseCtx {
   const int32_t* cidm;  // cluster ids, sign bit set for members of merged groups (n)
   const int32_t* sdeg;
   unsigned char* clean;
+  const unsigned char* dirty;  // 1: left to the pre-merge; 2: a lone list with no entry into a merged group
 };
 void sparse_mark(const GraphView& g, const int32_t* lab, const int32_t* cid, unsigned char* mflag, int32_t* cidm,
                  unsigned char* dirty, int32_t* sdeg, int32_t* list, int* count, cudaStream_t s);
