@@ -314,6 +314,37 @@ def test_contract_invariants(seed):
     assert got == acc
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_contract_near_identity_keeps_lone_lists(seed):
+    """A vertex labelled by its own id and alone in its cluster ("lone") gets a cluster id
+    that rises with its id, and when none of its neighbours is in another kind of cluster
+    its coarse list is its fine list renumbered, in the same order with the same weights
+    (the property that lets such lists be copied instead of merged)."""
+    rnd = np.random.default_rng(seed)
+    g = gg.with_pair_weights(gg.core_lcc(gg.rhg(1200, 12, seed + 3), 0), seed, 1, 9)
+    G = oracle.as_csr64(g.offsets, g.adj, g.w)
+    n = G.n
+    labels = np.arange(n, dtype=np.int32)
+    moved = rnd.choice(n, n // 20, replace=False)
+    labels[moved] = rnd.integers(0, n, len(moved))
+    h, cid = oracle.contract(G, labels)
+    size = np.bincount(labels, minlength=n)
+    lone = (labels == np.arange(n)) & (size[labels] == 1)
+    lv = np.flatnonzero(lone)
+    assert len(lv) > n // 2
+    assert np.all(np.diff(cid[lv]) > 0)
+    checked = 0
+    for v in lv:
+        nb = G.adj[G.offsets[v]:G.offsets[v + 1]]
+        if not lone[nb].all():
+            continue
+        x = cid[v]
+        assert list(h.adj[h.offsets[x]:h.offsets[x + 1]]) == list(cid[nb])
+        assert list(h.w[h.offsets[x]:h.offsets[x + 1]]) == list(G.w[G.offsets[v]:G.offsets[v + 1]])
+        checked += 1
+    assert checked > 0
+
+
 # ----------------------------------------------------- Padberg-Rinaldi pins
 def test_pr2_counterexample_designated_partner():
     g = H.pr2_counterexample()
