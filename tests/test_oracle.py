@@ -429,6 +429,28 @@ def test_pr_pass_b_conditions_hand():
     assert pairs == 1 and labels[1] == 0
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_pr_pass_b_symmetric_in_the_pair(seed):
+    """Conditions 3 and 4 read the pair {v, w} symmetrically, so with distinct edge
+    weights (designated partners without ties) reversing the vertex ids, which swaps the
+    roles of the smaller and the larger id of every mutual pair, merges the same pairs."""
+    rnd = np.random.default_rng(seed)
+    base = gg.er(300, [4, 10, 30][seed % 3], 50 + seed)
+    und = [(int(v), int(u)) for v in range(base.n)
+           for u in base.adj[base.offsets[v]:base.offsets[v + 1]] if v < u]
+    wts = rnd.permutation(len(und)) + 1
+    n = base.n
+    merged = []
+    lam = int(rnd.integers(5, 40)) * max(1, len(und) // 200)
+    for rev in (False, True):
+        f = (lambda x: n - 1 - x) if rev else (lambda x: x)
+        g = gg.from_edges(n, [(f(a), f(b), int(c)) for (a, b), c in zip(und, wts)])
+        G = oracle.as_csr64(g.offsets, g.adj, g.w)
+        labels, pairs = oracle.pr_pass_b(G, lam)
+        merged.append({frozenset((f(v), f(int(labels[v])))) for v in range(n) if labels[v] != v})
+    assert merged[0] == merged[1]
+
+
 # ---------------------------------------------------------- correcting step
 def _as64(g):
     return oracle.as_csr64(g.offsets, g.adj, g.w)
